@@ -1,0 +1,321 @@
+"""Benchmark of the ETac tactile step on GB300: node-steps/s over 4,096 environments.
+
+Workload (default): 4,096 environments x (5 curved 16x32 fingertip pads + one flat 32x64 palm
+pad) = 18,874,368 surface nodes per step, one seeded primitive per environment (sphere, box,
+cylinder or capsule), penetration 0-3 mm, seeded propagation-model parameters (seed 0).  One
+step = contact detection + Eq. 1 propagation + residual network + Eq. 4 for every node.
+
+Prints ONE JSON line (rank 0).  ``--impl reference`` times the FP64 CPU oracle on the host
+cores instead (bounded env sample per step).  Under torchrun each rank runs an independent
+replica on its own GPU (weak scaling, no collective on the data path).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import shutil
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_2604_20295_gb300 import inputs as I  # noqa: E402
+
+METRIC = "tactile node-steps/sec at 4096 envs (BF16 batched vs FP32 plain) at stated err; bwd/fwd"
+UNIT = "node-steps/s"
+H = 64
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def algorithmic_work(scene, counts):
+    """FLOPs and bytes the method itself requires per step (implementation overheads such as
+    recomputation or padding are not counted).  counts = active nodes per pad."""
+    n = scene.pad_nodes.astype(np.float64)
+    m = counts.astype(np.float64)
+    passive = np.where(m > 0, n - m, 0.0)
+    active = np.where(m > 0, m, 0.0)
+    pairs = float((passive * active).sum())
+    enc = 2.0 * (NIN_H + H * H)            # E1 + E2 per node
+    dec = 2.0 * (H * H + 3 * H)            # D1 (per-node half) + D2 per passive node
+    literal = float((n * (m > 0)).sum()) * enc + float(passive.sum()) * dec + 6.0 * pairs
+    bytes_out = 12.0 * float(n.sum())      # displacement, float32 x3
+    return dict(pairs=pairs, literal_flops=literal, bytes_out=bytes_out,
+                active=float(active.sum()), passive=float(passive.sum()))
+
+
+NIN_H = 9 * H
+
+
+class Clocks:
+    """nvidia-smi sampling of SM clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index, self.proc, self.path = index, None, None
+
+    def start(self):
+        exe = shutil.which("nvidia-smi")
+        if not exe:
+            return
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        self.proc = subprocess.Popen([exe, f"--query-gpu={self.FIELDS}", "--format=csv,noheader",
+                                      "-i", str(self.index), "-lms", "200"],
+                                     stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1].split()[0]))
+                mx.append(float(f[2].split()[0]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        os.unlink(self.path)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def cpu_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except Exception:
+        return os.cpu_count() or 1
+
+
+def oracle_rate(scene, theta, sample_envs, nthreads=0):
+    """Times the FP64 oracle (as it stands) on a bounded env sample; node-steps/s."""
+    import oracle
+    sub = scene.subset(sample_envs)
+    t0 = time.perf_counter()
+    oracle.forward(sub, theta, nthreads=nthreads)
+    dt = time.perf_counter() - t0
+    return sub.total_nodes / dt, dt, sub.total_nodes
+
+
+def run_reference(args, scene, theta, rank, world):
+    if rank != 0:
+        return
+    rng = np.random.default_rng(123)
+    times, nodes = [], 0
+    for it in range(args.warmup + args.steps):
+        envs = rng.choice(scene.num_envs, args.ref_envs, replace=False)
+        rate, dt, nn = oracle_rate(scene, theta, envs)
+        if it >= args.warmup:
+            times.append(dt)
+            nodes += nn
+    value = nodes / sum(times)
+    cores = cpu_cores()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(times) / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(args, scene),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                             "sample": f"{args.ref_envs} random envs ({args.ref_envs * 4608} nodes) "
+                                       "of the workload per step, FP64 C oracle, OpenMP over pads"},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, scene):
+    return {"workload": f"hand-{scene.num_envs}env-5tip16x32r8-palm32x64",
+            "envs": scene.num_envs, "pads_per_env": scene.pads_per_env,
+            "nodes_per_step": scene.total_nodes, "algo": args.algo, "precision": args.precision,
+            "l2": "flushed between timed steps (256 MiB write)", "params_seed": 0,
+            "scene_seed": args.seed}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--algo", default="plain", choices=["plain", "batched"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--envs", type=int, default=4096)
+    ap.add_argument("--seed", type=int, default=2)
+    ap.add_argument("--ref-envs", type=int, default=96)
+    ap.add_argument("--cpu-envs", type=int, default=256)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    theta = I.make_params(0)
+    scene = I.hand_scene(args.envs, seed=args.seed + 1000 * rank)
+
+    if args.impl == "reference":
+        return run_reference(args, scene, theta, rank, world)
+
+    import torch
+    from paper_2604_20295_gb300 import build as B
+    from paper_2604_20295_gb300 import etac as X
+
+    B.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    algo = X.ALGO_BATCHED if args.algo == "batched" else X.ALGO_PLAIN
+    prec = X.PREC_BF16 if args.precision == "bf16" else X.PREC_FP32
+    sim = X.TactileSim(scene, device=dev)
+    sim.set_model(theta, X.MODE_FULL, prec, algo)
+    stream = torch.cuda.current_stream(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def one_step():
+        sim.step(want_mask=False, want_pen=False, want_count=True)
+
+    for _ in range(args.warmup):
+        one_step()
+    torch.cuda.synchronize()
+    counts = sim.count.cpu().numpy()
+    work = algorithmic_work(scene, counts)
+
+    # ---- device-timed region: K steps, L2 flushed between steps (outside the events)
+    clocks = Clocks(local)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    for k in range(args.steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        one_step()
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    clk = clocks.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    total_s = sum(step_ms) / 1e3
+    if pg:
+        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        total_s = float(t)
+    nodes = scene.total_nodes
+    value = nodes * args.steps * world / total_s
+    ms_per_step = 1e3 * total_s / args.steps
+
+    # ---- end to end through the public API with host buffers
+    e2e = None
+    if not args.no_e2e:
+        pin = lambda a: torch.as_tensor(a).pin_memory()
+        h_in = [pin(scene.obj_type), pin(scene.obj_dims), pin(scene.obj_pose), pin(scene.pad_pose)]
+        d_in = [sim.obj_type, sim.obj_dims, sim.obj_pose, sim.pad_pose]
+        h_out = torch.empty(sim.disp.shape, dtype=torch.float32).pin_memory()
+        h2d = sum(t.numel() * t.element_size() for t in h_in)
+        d2h = h_out.numel() * 4
+        ke = max(3, args.steps // 2)
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(ke):
+            for d, h in zip(d_in, h_in):
+                d.copy_(h, non_blocking=True)
+            one_step()
+            h_out.copy_(sim.disp, non_blocking=True)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        e2e_s = e0.elapsed_time(e1) / 1e3
+        if pg:
+            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            e2e_s = float(t)
+        e2e = {"value": nodes * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h, "steps": ke}
+
+    peaks, peak_src = _peaks()
+    sm_clock = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.algo == "plain":
+        # literal FP32 network + Eq. 1 contraction on CUDA cores: ALU bound
+        fma_peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+        achieved = work["literal_flops"] / (total_s / args.steps) / 1e12
+        roof = {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
+                "frac": achieved / fma_peak, "traffic": None,
+                "kernel": "plain_forward_kernel<float>",
+                "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)}"
+                               " MHz (derived)"}
+    else:
+        achieved = work["bytes_out"] / (total_s / args.steps) / 1e9
+        roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
+                "peak_source": peak_src}
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        envs = np.random.default_rng(7).choice(scene.num_envs, min(args.cpu_envs, scene.num_envs),
+                                               replace=False)
+        rate, dt, nn = oracle_rate(scene, theta, envs)
+        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{len(envs)} random envs ({nn} nodes) of the workload, one forward, "
+                         f"FP64 C oracle, OpenMP over pads, {dt:.1f} s"}
+
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec else "f32",
+            "data": "synthetic", "config": workload_config(args, scene), "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * LAUNCHES[args.algo],
+            "clocks": clk, "active_fraction": work["active"] / nodes,
+            "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+# kernels of ours launched per step
+LAUNCHES = {"plain": 1, "batched": 1}
+
+if __name__ == "__main__":
+    main()

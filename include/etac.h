@@ -1,0 +1,171 @@
+/*
+ * etac.h -- C ABI of the GB300 (sm_103a) ETac tactile step library (libetac.so).
+ *
+ * ETac (Sec. III-A) simulates elastomer tactile pads: every surface node of every pad is
+ * tested against the environment's rigid objects with signed distance fields; nodes inside
+ * an object are "active" and take a local displacement u_hat; every other ("passive") node
+ * gets the decay-based propagation of Eq. 1 (Omega U_a) plus the PointNet residual Phi_p of
+ * Sec. III-A 2, summed as in Eq. 4.  This library runs that step for a whole batch of
+ * environments on one GPU, and its reverse mode.
+ *
+ * Conventions shared by every entry point:
+ *   - millimetres; quaternions are (x, y, z, w) and need not be normalised; a pose is
+ *     t(3) followed by q(4), 7 floats;
+ *   - a pad type is a fixed set of n surface nodes with undeformed positions P and unit
+ *     normals N in the pad frame; node order within a pad is the caller's (row-major grids);
+ *   - pad instances are env-major, pad-minor; the flat node index of node i of pad instance
+ *     p is offset[p] + i, offset being the prefix sum of the instances' node counts;
+ *   - displacements are returned in the pad frame of their pad (undeformed frame, Sec. III-A);
+ *   - "host" pointers are read during the call only; "device" pointers are borrowed: they
+ *     must stay valid, and untouched by other work, until the work enqueued on the given
+ *     stream has completed.  Nothing is retained after the call returns except where stated;
+ *   - every call returns an etac_status; on failure etac_last_error() describes it.  Calls
+ *     that enqueue GPU work never synchronise; conditions found on the GPU (bounded waits
+ *     that ran out, non-finite poses) are latched in a device status word read with
+ *     etac_poll_status().
+ *   - a context is not thread-safe; use one context per stream.
+ */
+#ifndef ETAC_H_
+#define ETAC_H_
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define ETAC_HIDDEN 64          /* hidden width of every network layer (global feature: 64) */
+#define ETAC_MAX_OBJECTS 8      /* rigid objects per environment                            */
+#define ETAC_MAX_PAD_NODES 4096 /* nodes per pad type                                       */
+
+typedef enum {
+  ETAC_OK = 0,
+  ETAC_ERR_INVALID_ARG = 1,  /* bad pointer, size, alignment or value                      */
+  ETAC_ERR_STATE = 2,        /* call out of order (e.g. step before set_model)             */
+  ETAC_ERR_CUDA = 3,         /* a CUDA call failed; the context should be destroyed        */
+  ETAC_ERR_OOM = 4,          /* device allocation failed                                   */
+  ETAC_ERR_TIMEOUT = 5,      /* device status: a bounded wait gave up                      */
+  ETAC_ERR_NONFINITE = 6,    /* device status: a pose held NaN / Inf (those pads output 0) */
+  ETAC_ERR_UNSUPPORTED = 7   /* valid request this build does not implement                */
+} etac_status;
+
+enum { ETAC_OBJ_NONE = 0, ETAC_OBJ_SPHERE = 1, ETAC_OBJ_BOX = 2, ETAC_OBJ_CYLINDER = 3,
+       ETAC_OBJ_CAPSULE = 4 };
+
+/* which terms of Eq. 4 are evaluated (the ablations of Table II) */
+enum { ETAC_MODE_FULL = 0, ETAC_MODE_LINEAR_ONLY = 1, ETAC_MODE_RESIDUAL_ONLY = 2 };
+
+/* arithmetic of the dense contractions: FP32, or BF16 operands with FP32 accumulation */
+enum { ETAC_PREC_FP32 = 0, ETAC_PREC_BF16 = 1 };
+
+/* ETAC_ALGO_PLAIN: one CTA per pad, Eq. 1 / Eq. 4 evaluated literally on every node with the
+ * exponential computed per pair (the unoptimised reference form).
+ * ETAC_ALGO_BATCHED: one persistent launch over all pads, per-pad-type tables, the network
+ * factored through the passive nodes' constant inputs, FP32 or BF16 contractions. */
+enum { ETAC_ALGO_PLAIN = 0, ETAC_ALGO_BATCHED = 1 };
+
+typedef struct etac_ctx etac_ctx;   /* opaque, owned by the library */
+
+/* Pads of the whole batch (host arrays, read during etac_create_pads only). */
+typedef struct {
+  int32_t num_types;               /* >= 1                                                 */
+  const int32_t* type_num_nodes;   /* [num_types], each in [1, ETAC_MAX_PAD_NODES]          */
+  const float* type_pos;           /* [sum n, 3] undeformed positions, pad frame (mm)       */
+  const float* type_nrm;           /* [sum n, 3] unit outward normals, pad frame            */
+  int32_t num_envs;                /* >= 1                                                 */
+  int32_t pads_per_env;            /* >= 1                                                 */
+  const int32_t* pad_type;         /* [num_envs * pads_per_env], each in [0, num_types)     */
+  int32_t max_objects;             /* K, objects per environment, in [1, ETAC_MAX_OBJECTS]  */
+} etac_pads_desc;
+
+/* Propagation model configuration.  Parameters are one flat FP32 vector (etac_param_count
+ * floats): alpha (1/mm, > 0), then for each layer W (row-major, out x in) followed by b, in
+ * the order E1 (9->64), E2 (64->64), G1 (64->64), D1 (128->64, input [f_i ; g]),
+ * D2 (64->3).  Activations are ReLU except after D2. */
+typedef struct {
+  int32_t hidden;      /* must be ETAC_HIDDEN                                              */
+  int32_t mode;        /* ETAC_MODE_*                                                      */
+  int32_t precision;   /* ETAC_PREC_*                                                      */
+  int32_t algo;        /* ETAC_ALGO_*                                                      */
+} etac_model_desc;
+
+/* Per-step inputs (device pointers, borrowed). */
+typedef struct {
+  const int32_t* obj_type;   /* [E*K] ETAC_OBJ_*; ETAC_OBJ_NONE slots are ignored           */
+  const float* obj_dims;     /* [E*K*3] sphere (r,-,-); box half-extents (hx,hy,hz);
+                                cylinder / capsule (r, half-length along local z, -)       */
+  const float* obj_pose;     /* [E*K*7] world pose of each object                           */
+  const float* pad_pose;     /* [E*P*7] world pose of each pad instance                     */
+} etac_step_in;
+
+/* Per-step outputs (device pointers, borrowed; NULL = not wanted, except disp). */
+typedef struct {
+  float* disp;               /* [N*3] node displacement, pad frame (required)               */
+  uint8_t* active_mask;      /* [N] 1 if the node is in contact                             */
+  float* penetration;        /* [N] max(0, -signed distance)                                */
+  int32_t* active_count;     /* [E*P] active nodes per pad (the n_a of the contact reward)  */
+} etac_step_out;
+
+/* Number of floats in the flat parameter vector for this configuration (0 if invalid). */
+size_t etac_param_count(const etac_model_desc* desc);
+
+/* Total node count N of a pad description (0 if invalid). */
+int64_t etac_total_nodes(const etac_pads_desc* desc);
+
+/* Create a context for a fixed batch of pads.  Copies the geometry to the device and
+ * allocates every buffer a later step needs (steps never allocate).  `stream` orders the
+ * copies.  On success *out owns device memory until etac_destroy. */
+etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* desc, void* stream);
+
+/* Set (or replace) the propagation model.  `params` is a device FP32 vector of
+ * etac_param_count(desc) floats, copied on `stream` (the caller may reuse it once the call
+ * returns).  Synchronises `stream` once to validate alpha (finite and > 0, else
+ * ETAC_ERR_INVALID_ARG and the previous model stays).  Rebuilds the per-pad-type tables of
+ * the batched algorithm.  Not capturable in a CUDA graph. */
+etac_status etac_set_model(etac_ctx* ctx, const etac_model_desc* desc, const float* params,
+                           void* stream);
+
+/* One forward step (ETac Sec. III-A, Eq. 1 and Eq. 4) for every pad of the batch.  Enqueues
+ * work on `stream` only (no host synchronisation, no allocation), so it can be captured in
+ * a CUDA graph.  Pads whose env has no object in contact output zero displacement.  Keeps
+ * a device copy of the poses for etac_step_backward. */
+etac_status etac_step_forward(etac_ctx* ctx, const etac_step_in* in, const etac_step_out* out,
+                              void* stream);
+
+/* Reverse mode of the last etac_step_forward on this context (FP32, hand-written).
+ * grad_disp [N*3] is dL/d(disp).  Outputs are overwritten (not accumulated); any may be
+ * NULL: grad_obj_pose [E*K*6] = (dL/dt world, dL/d omega) with the rotation increment
+ * exp([omega]x) applied on the left about the object origin; grad_uhat [N*3] = dL/d u_hat of
+ * active nodes (pad frame, 0 on passive nodes); grad_penetration [N] = dL/d(penetration)
+ * with u_hat = penetration * outward normal (0 on passive nodes); grad_params [P] for the
+ * flat parameter vector.  The contact set is held fixed.  ETAC_ERR_STATE without a prior
+ * forward. */
+etac_status etac_step_backward(etac_ctx* ctx, const float* grad_disp, float* grad_obj_pose,
+                               float* grad_uhat, float* grad_penetration, float* grad_params,
+                               void* stream);
+
+/* Reads and clears the device status word (synchronises `stream`).  *device_status receives
+ * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE. */
+etac_status etac_poll_status(etac_ctx* ctx, int32_t* device_status, void* stream);
+
+/* FP64 evaluation of the plain algorithm, for finite-difference gradient checks only.
+ * Device arrays as in etac_step_in but double; params [etac_param_count] double; writes
+ * disp [N*3] double.  Uses the context's pads and the mode of `desc`. */
+etac_status etac_forward_f64(etac_ctx* ctx, const etac_model_desc* desc,
+                             const int32_t* obj_type, const double* obj_dims,
+                             const double* obj_pose, const double* pad_pose,
+                             const double* params, double* disp, void* stream);
+
+/* Message of the last failed call on this context (or of the last failed create when
+ * ctx is NULL).  Valid until the next call on the same context. */
+const char* etac_last_error(const etac_ctx* ctx);
+
+/* Frees the context and its device memory (synchronises the device first). NULL is a no-op. */
+void etac_destroy(etac_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* ETAC_H_ */

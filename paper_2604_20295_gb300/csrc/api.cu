@@ -1,0 +1,368 @@
+// api.cu -- C ABI of libetac (declared in include/etac.h): validation, device buffers and
+// the stream-ordered launch sequences.  No function here allocates device memory after
+// etac_create_pads / etac_set_model, and no step call synchronises the host.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "etac.h"
+#include "etac_common.cuh"
+#include "etac_kernels.h"
+
+struct etac_ctx {
+  std::string err;
+  int T = 0, E = 0, P = 0, K = 0, nmax = 0;
+  int64_t N = 0;
+  std::vector<int> type_n, type_off;
+  std::vector<int> pad_type;
+  std::vector<long long> pad_off;
+  std::vector<float> type_pmax;
+  // device geometry
+  float* d_type_pos = nullptr;
+  float* d_type_nrm = nullptr;
+  float* d_type_pmax = nullptr;
+  int* d_type_off = nullptr;
+  int* d_pad_type = nullptr;
+  long long* d_pad_off = nullptr;
+  int* d_status = nullptr;
+  // model
+  bool has_model = false;
+  etac_model_desc model{};
+  float* d_params = nullptr;
+  // state of the last forward (device copies of its inputs)
+  bool has_forward = false;
+  int* d_saved_obj_type = nullptr;
+  float* d_saved_obj_dims = nullptr;
+  float* d_saved_obj_pose = nullptr;
+  float* d_saved_pad_pose = nullptr;
+  int num_sms = 0;
+};
+
+namespace {
+
+thread_local std::string g_create_err;
+
+etac_status fail(etac_ctx* c, etac_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  if (c) c->err = buf;
+  else g_create_err = buf;
+  return s;
+}
+
+etac_status cuda_fail(etac_ctx* c, cudaError_t e, const char* what) {
+  return fail(c, e == cudaErrorMemoryAllocation ? ETAC_ERR_OOM : ETAC_ERR_CUDA, "%s: %s", what,
+              cudaGetErrorString(e));
+}
+
+#define ETAC_CUDA(ctx, expr, what)                       \
+  do {                                                   \
+    cudaError_t e_ = (expr);                             \
+    if (e_ != cudaSuccess) return cuda_fail(ctx, e_, what); \
+  } while (0)
+
+bool aligned(const void* p, size_t a) { return (reinterpret_cast<uintptr_t>(p) % a) == 0; }
+
+template <typename X>
+cudaError_t dalloc(X** p, size_t count) {
+  return cudaMalloc(reinterpret_cast<void**>(p), std::max<size_t>(1, count) * sizeof(X));
+}
+
+void free_ctx(etac_ctx* c) {
+  if (!c) return;
+  void* ptrs[] = {c->d_type_pos, c->d_type_nrm, c->d_type_pmax, c->d_type_off, c->d_pad_type,
+                  c->d_pad_off, c->d_status, c->d_params, c->d_saved_obj_type,
+                  c->d_saved_obj_dims, c->d_saved_obj_pose, c->d_saved_pad_pose};
+  for (void* p : ptrs)
+    if (p) cudaFree(p);
+  delete c;
+}
+
+bool valid_model(const etac_model_desc* d) {
+  return d && d->hidden == ETAC_HIDDEN && d->mode >= ETAC_MODE_FULL &&
+         d->mode <= ETAC_MODE_RESIDUAL_ONLY && (d->precision == ETAC_PREC_FP32 ||
+         d->precision == ETAC_PREC_BF16) && (d->algo == ETAC_ALGO_PLAIN ||
+         d->algo == ETAC_ALGO_BATCHED);
+}
+
+}  // namespace
+
+extern "C" {
+
+size_t etac_param_count(const etac_model_desc* desc) {
+  if (desc && desc->hidden != ETAC_HIDDEN) return 0;
+  return (size_t)etac::NPARAM;
+}
+
+int64_t etac_total_nodes(const etac_pads_desc* d) {
+  if (!d || d->num_types < 1 || !d->type_num_nodes || !d->pad_type || d->num_envs < 1 ||
+      d->pads_per_env < 1)
+    return 0;
+  int64_t N = 0;
+  for (int64_t p = 0; p < (int64_t)d->num_envs * d->pads_per_env; ++p) {
+    int t = d->pad_type[p];
+    if (t < 0 || t >= d->num_types) return 0;
+    int n = d->type_num_nodes[t];
+    if (n < 1 || n > ETAC_MAX_PAD_NODES) return 0;
+    N += n;
+  }
+  return N;
+}
+
+etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stream) {
+  if (!out) return fail(nullptr, ETAC_ERR_INVALID_ARG, "out is NULL");
+  *out = nullptr;
+  if (!d) return fail(nullptr, ETAC_ERR_INVALID_ARG, "desc is NULL");
+  if (d->num_types < 1 || !d->type_num_nodes || !d->type_pos || !d->type_nrm || !d->pad_type)
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "pad types: num_types < 1 or NULL array");
+  if (d->num_envs < 1 || d->pads_per_env < 1)
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "num_envs and pads_per_env must be >= 1");
+  if (d->max_objects < 1 || d->max_objects > ETAC_MAX_OBJECTS)
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "max_objects must be in [1, %d]",
+                ETAC_MAX_OBJECTS);
+  int64_t np = (int64_t)d->num_envs * d->pads_per_env;
+  if (np > (int64_t)INT32_MAX / 2)
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "too many pads");
+  etac_ctx* c = new etac_ctx();
+  c->T = d->num_types;
+  c->E = d->num_envs;
+  c->P = d->pads_per_env;
+  c->K = d->max_objects;
+  c->type_n.assign(d->type_num_nodes, d->type_num_nodes + c->T);
+  c->type_off.resize(c->T + 1, 0);
+  for (int t = 0; t < c->T; ++t) {
+    int n = c->type_n[t];
+    if (n < 1 || n > ETAC_MAX_PAD_NODES) {
+      free_ctx(c);
+      return fail(nullptr, ETAC_ERR_INVALID_ARG, "pad type %d has %d nodes (allowed 1..%d)", t,
+                  n, ETAC_MAX_PAD_NODES);
+    }
+    c->type_off[t + 1] = c->type_off[t] + n;
+    c->nmax = std::max(c->nmax, n);
+  }
+  const int total_type_nodes = c->type_off[c->T];
+  c->type_pmax.assign(c->T, 0.f);
+  for (int t = 0; t < c->T; ++t)
+    for (int i = c->type_off[t]; i < c->type_off[t + 1]; ++i) {
+      for (int q = 0; q < 3; ++q) {
+        float v = d->type_pos[3 * i + q], w = d->type_nrm[3 * i + q];
+        if (!std::isfinite(v) || !std::isfinite(w)) {
+          free_ctx(c);
+          return fail(nullptr, ETAC_ERR_INVALID_ARG, "non-finite node geometry (type %d)", t);
+        }
+        c->type_pmax[t] = std::max(c->type_pmax[t], std::fabs(v));
+      }
+    }
+  c->pad_type.assign(d->pad_type, d->pad_type + np);
+  c->pad_off.resize(np + 1, 0);
+  for (int64_t p = 0; p < np; ++p) {
+    int t = c->pad_type[p];
+    if (t < 0 || t >= c->T) {
+      free_ctx(c);
+      return fail(nullptr, ETAC_ERR_INVALID_ARG, "pad %lld has type %d (num_types %d)",
+                  (long long)p, t, c->T);
+    }
+    c->pad_off[p + 1] = c->pad_off[p] + c->type_n[t];
+  }
+  c->N = c->pad_off[np];
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, dev);
+  if (e == cudaSuccess) e = dalloc(&c->d_type_pos, 3 * (size_t)total_type_nodes);
+  if (e == cudaSuccess) e = dalloc(&c->d_type_nrm, 3 * (size_t)total_type_nodes);
+  if (e == cudaSuccess) e = dalloc(&c->d_type_pmax, c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_type_off, c->T + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_type, np);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_off, np + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_status, 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_params, etac::NPARAM);
+  if (e == cudaSuccess) e = dalloc(&c->d_saved_obj_type, (size_t)c->E * c->K);
+  if (e == cudaSuccess) e = dalloc(&c->d_saved_obj_dims, (size_t)c->E * c->K * 3);
+  if (e == cudaSuccess) e = dalloc(&c->d_saved_obj_pose, (size_t)c->E * c->K * 7);
+  if (e == cudaSuccess) e = dalloc(&c->d_saved_pad_pose, (size_t)np * 7);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_type_pos, d->type_pos, sizeof(float) * 3 * total_type_nodes,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_type_nrm, d->type_nrm, sizeof(float) * 3 * total_type_nodes,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_type_pmax, c->type_pmax.data(), sizeof(float) * c->T,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_type_off, c->type_off.data(), sizeof(int) * (c->T + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_pad_type, c->pad_type.data(), sizeof(int) * np,
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_pad_off, c->pad_off.data(), sizeof(long long) * (np + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_status, 0, sizeof(int), s);
+  // host vectors are pageable: the copies above complete before returning
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) {
+    etac_status st = cuda_fail(nullptr, e, "etac_create_pads");
+    free_ctx(c);
+    return st;
+  }
+  if (etac::plain_smem_f32(c->nmax, c->K) > 227 * 1024) {
+    free_ctx(c);
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "pad type too large for the plain algorithm");
+  }
+  *out = c;
+  return ETAC_OK;
+}
+
+etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float* params,
+                           void* stream) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!valid_model(desc))
+    return fail(c, ETAC_ERR_INVALID_ARG,
+                "model desc: hidden must be %d; mode, precision, algo must be known values",
+                ETAC_HIDDEN);
+  if (!params || !aligned(params, 4)) return fail(c, ETAC_ERR_INVALID_ARG, "params NULL/misaligned");
+  if (desc->algo == ETAC_ALGO_BATCHED || desc->precision == ETAC_PREC_BF16)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "batched / BF16 algorithm not built yet");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  float alpha = 0.f;
+  ETAC_CUDA(c, cudaMemcpyAsync(&alpha, params, sizeof(float), cudaMemcpyDeviceToHost, s),
+            "read alpha");
+  ETAC_CUDA(c, cudaStreamSynchronize(s), "read alpha");
+  if (!(std::isfinite(alpha) && alpha > 0.f))
+    return fail(c, ETAC_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
+  ETAC_CUDA(c, cudaMemcpyAsync(c->d_params, params, sizeof(float) * etac::NPARAM,
+                               cudaMemcpyDeviceToDevice, s), "copy params");
+  c->model = *desc;
+  c->has_model = true;
+  return ETAC_OK;
+}
+
+etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_step_out* out,
+                              void* stream) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_model) return fail(c, ETAC_ERR_STATE, "etac_set_model has not been called");
+  if (!in || !out) return fail(c, ETAC_ERR_INVALID_ARG, "in/out is NULL");
+  if (!in->obj_type || !in->obj_dims || !in->obj_pose || !in->pad_pose || !out->disp)
+    return fail(c, ETAC_ERR_INVALID_ARG, "required input/output pointer is NULL");
+  if (!aligned(in->obj_type, 4) || !aligned(in->obj_dims, 4) || !aligned(in->obj_pose, 4) ||
+      !aligned(in->pad_pose, 4) || !aligned(out->disp, 4) ||
+      (out->penetration && !aligned(out->penetration, 4)) ||
+      (out->active_count && !aligned(out->active_count, 4)))
+    return fail(c, ETAC_ERR_INVALID_ARG, "pointer not 4-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  const size_t EK = (size_t)c->E * c->K, EP = (size_t)c->E * c->P;
+  // keep this step's inputs for the reverse mode
+  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_type, in->obj_type, sizeof(int) * EK,
+                               cudaMemcpyDeviceToDevice, s), "save inputs");
+  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_dims, in->obj_dims, sizeof(float) * EK * 3,
+                               cudaMemcpyDeviceToDevice, s), "save inputs");
+  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_pose, in->obj_pose, sizeof(float) * EK * 7,
+                               cudaMemcpyDeviceToDevice, s), "save inputs");
+  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_pad_pose, in->pad_pose, sizeof(float) * EP * 7,
+                               cudaMemcpyDeviceToDevice, s), "save inputs");
+  etac::PlainArgs<float> a{};
+  a.type_pos = c->d_type_pos;
+  a.type_nrm = c->d_type_nrm;
+  a.type_pmax = c->d_type_pmax;
+  a.type_off = c->d_type_off;
+  a.pad_type = c->d_pad_type;
+  a.pad_off = c->d_pad_off;
+  a.P = c->P;
+  a.K = c->K;
+  a.nmax = c->nmax;
+  a.obj_type = c->d_saved_obj_type;
+  a.obj_dims = c->d_saved_obj_dims;
+  a.obj_pose = c->d_saved_obj_pose;
+  a.pad_pose = c->d_saved_pad_pose;
+  a.params = c->d_params;
+  a.mode = c->model.mode;
+  a.disp = out->disp;
+  a.mask = out->active_mask;
+  a.pen = out->penetration;
+  a.count = out->active_count;
+  a.status = c->d_status;
+  ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
+  c->has_forward = true;
+  return ETAC_OK;
+}
+
+etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_obj_pose,
+                               float* grad_uhat, float* grad_penetration, float* grad_params,
+                               void* stream) {
+  (void)grad_disp; (void)grad_obj_pose; (void)grad_uhat; (void)grad_penetration;
+  (void)grad_params; (void)stream;
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_forward) return fail(c, ETAC_ERR_STATE, "no forward step to differentiate");
+  return fail(c, ETAC_ERR_UNSUPPORTED, "reverse mode not built yet");
+}
+
+etac_status etac_poll_status(etac_ctx* c, int32_t* device_status, void* stream) {
+  if (!c || !device_status) return fail(c, ETAC_ERR_INVALID_ARG, "NULL argument");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  int v = 0;
+  ETAC_CUDA(c, cudaMemcpyAsync(&v, c->d_status, sizeof(int), cudaMemcpyDeviceToHost, s),
+            "read status");
+  ETAC_CUDA(c, cudaMemsetAsync(c->d_status, 0, sizeof(int), s), "clear status");
+  ETAC_CUDA(c, cudaStreamSynchronize(s), "read status");
+  *device_status = v;
+  return ETAC_OK;
+}
+
+etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int32_t* obj_type,
+                             const double* obj_dims, const double* obj_pose,
+                             const double* pad_pose, const double* params, double* disp,
+                             void* stream) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!valid_model(desc)) return fail(c, ETAC_ERR_INVALID_ARG, "bad model desc");
+  if (!obj_type || !obj_dims || !obj_pose || !pad_pose || !params || !disp ||
+      !aligned(obj_dims, 8) || !aligned(obj_pose, 8) || !aligned(pad_pose, 8) ||
+      !aligned(params, 8) || !aligned(disp, 8) || !aligned(obj_type, 4))
+    return fail(c, ETAC_ERR_INVALID_ARG, "NULL or misaligned pointer");
+  if (etac::plain_smem_f64(c->nmax, c->K) > 227 * 1024)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "pad type too large for the FP64 check (max ~1500 nodes)");
+  etac::PlainArgs<double> a{};
+  a.type_pos = c->d_type_pos;
+  a.type_nrm = c->d_type_nrm;
+  a.type_pmax = c->d_type_pmax;
+  a.type_off = c->d_type_off;
+  a.pad_type = c->d_pad_type;
+  a.pad_off = c->d_pad_off;
+  a.P = c->P;
+  a.K = c->K;
+  a.nmax = c->nmax;
+  a.obj_type = obj_type;
+  a.obj_dims = obj_dims;
+  a.obj_pose = obj_pose;
+  a.pad_pose = pad_pose;
+  a.params = params;
+  a.mode = desc->mode;
+  a.disp = disp;
+  a.status = c->d_status;
+  ETAC_CUDA(c, etac::launch_plain_forward<double>(a, c->E * c->P,
+                                                  reinterpret_cast<cudaStream_t>(stream)),
+            "fp64 forward launch");
+  return ETAC_OK;
+}
+
+const char* etac_last_error(const etac_ctx* c) {
+  return c ? c->err.c_str() : g_create_err.c_str();
+}
+
+void etac_destroy(etac_ctx* c) {
+  if (!c) return;
+  cudaDeviceSynchronize();
+  free_ctx(c);
+}
+
+}  // extern "C"

@@ -1,0 +1,232 @@
+"""ctypes binding of libetac (``include/etac.h``).
+
+The ``etac_*`` functions carry the C names and only marshal arguments: integers are device
+or host addresses, structures mirror the C ones, every GPU step runs in the library's CUDA
+kernels.  ``TactileSim`` is a convenience owner of a context plus the torch tensors that
+hold its inputs and outputs (torch is used for device memory and streams only).  There is no
+CPU fallback: if the library is missing or no GPU is present the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from . import build as _build
+
+ETAC_OK = 0
+STATUS_NAMES = {0: "ETAC_OK", 1: "ETAC_ERR_INVALID_ARG", 2: "ETAC_ERR_STATE", 3: "ETAC_ERR_CUDA",
+                4: "ETAC_ERR_OOM", 5: "ETAC_ERR_TIMEOUT", 6: "ETAC_ERR_NONFINITE",
+                7: "ETAC_ERR_UNSUPPORTED"}
+MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY = 0, 1, 2
+PREC_FP32, PREC_BF16 = 0, 1
+ALGO_PLAIN, ALGO_BATCHED = 0, 1
+HIDDEN = 64
+
+EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
+           "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
+           "etac_last_error", "etac_destroy")
+
+_vp = ctypes.c_void_p
+
+
+class etac_pads_desc(ctypes.Structure):
+    _fields_ = [("num_types", ctypes.c_int32), ("type_num_nodes", _vp), ("type_pos", _vp),
+                ("type_nrm", _vp), ("num_envs", ctypes.c_int32), ("pads_per_env", ctypes.c_int32),
+                ("pad_type", _vp), ("max_objects", ctypes.c_int32)]
+
+
+class etac_model_desc(ctypes.Structure):
+    _fields_ = [("hidden", ctypes.c_int32), ("mode", ctypes.c_int32),
+                ("precision", ctypes.c_int32), ("algo", ctypes.c_int32)]
+
+
+class etac_step_in(ctypes.Structure):
+    _fields_ = [("obj_type", _vp), ("obj_dims", _vp), ("obj_pose", _vp), ("pad_pose", _vp)]
+
+
+class etac_step_out(ctypes.Structure):
+    _fields_ = [("disp", _vp), ("active_mask", _vp), ("penetration", _vp),
+                ("active_count", _vp)]
+
+
+class EtacError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS_NAMES.get(status, status)}: {msg}")
+        self.status = status
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libetac.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        path = _build.LIB
+        if not os.path.exists(path):
+            raise RuntimeError(f"{path} is missing: build it with paper_2604_20295_gb300.build.build()"
+                               " (CUDA toolkit required); there is no CPU fallback")
+        L = ctypes.CDLL(path)
+        L.etac_param_count.restype = ctypes.c_size_t
+        L.etac_param_count.argtypes = [_vp]
+        L.etac_total_nodes.restype = ctypes.c_int64
+        L.etac_total_nodes.argtypes = [_vp]
+        L.etac_create_pads.restype = ctypes.c_int
+        L.etac_create_pads.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
+        L.etac_set_model.restype = ctypes.c_int
+        L.etac_set_model.argtypes = [_vp, _vp, _vp, _vp]
+        L.etac_step_forward.restype = ctypes.c_int
+        L.etac_step_forward.argtypes = [_vp, _vp, _vp, _vp]
+        L.etac_step_backward.restype = ctypes.c_int
+        L.etac_step_backward.argtypes = [_vp] * 7
+        L.etac_poll_status.restype = ctypes.c_int
+        L.etac_poll_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), _vp]
+        L.etac_forward_f64.restype = ctypes.c_int
+        L.etac_forward_f64.argtypes = [_vp] * 9
+        L.etac_last_error.restype = ctypes.c_char_p
+        L.etac_last_error.argtypes = [_vp]
+        L.etac_destroy.restype = None
+        L.etac_destroy.argtypes = [_vp]
+        _lib = L
+    return _lib
+
+
+def _check(ctx, status, what):
+    if status != ETAC_OK:
+        msg = lib().etac_last_error(ctx)
+        raise EtacError(status, f"{what}: {msg.decode() if msg else ''}")
+
+
+# ------------------------------------------------------------------ C entry points
+
+
+def etac_param_count(desc: etac_model_desc) -> int:
+    return int(lib().etac_param_count(ctypes.addressof(desc)))
+
+
+def etac_total_nodes(desc: etac_pads_desc) -> int:
+    return int(lib().etac_total_nodes(ctypes.addressof(desc)))
+
+
+def etac_create_pads(desc: etac_pads_desc, stream: int = 0) -> int:
+    out = _vp()
+    _check(None, lib().etac_create_pads(ctypes.byref(out), ctypes.addressof(desc), stream),
+           "etac_create_pads")
+    return out.value
+
+
+def etac_set_model(ctx: int, desc: etac_model_desc, params: int, stream: int = 0) -> None:
+    _check(ctx, lib().etac_set_model(ctx, ctypes.addressof(desc), params, stream), "etac_set_model")
+
+
+def etac_step_forward(ctx: int, sin: etac_step_in, sout: etac_step_out, stream: int = 0) -> None:
+    _check(ctx, lib().etac_step_forward(ctx, ctypes.addressof(sin), ctypes.addressof(sout), stream),
+           "etac_step_forward")
+
+
+def etac_step_backward(ctx: int, grad_disp: int, grad_obj_pose: int = 0, grad_uhat: int = 0,
+                       grad_penetration: int = 0, grad_params: int = 0, stream: int = 0) -> None:
+    _check(ctx, lib().etac_step_backward(ctx, grad_disp, grad_obj_pose or None, grad_uhat or None,
+                                         grad_penetration or None, grad_params or None, stream),
+           "etac_step_backward")
+
+
+def etac_poll_status(ctx: int, stream: int = 0) -> int:
+    v = ctypes.c_int32(0)
+    _check(ctx, lib().etac_poll_status(ctx, ctypes.byref(v), stream), "etac_poll_status")
+    return int(v.value)
+
+
+def etac_forward_f64(ctx: int, desc: etac_model_desc, obj_type: int, obj_dims: int,
+                     obj_pose: int, pad_pose: int, params: int, disp: int, stream: int = 0) -> None:
+    _check(ctx, lib().etac_forward_f64(ctx, ctypes.addressof(desc), obj_type, obj_dims, obj_pose,
+                                       pad_pose, params, disp, stream), "etac_forward_f64")
+
+
+def etac_last_error(ctx: int = 0) -> str:
+    m = lib().etac_last_error(ctx or None)
+    return m.decode() if m else ""
+
+
+def etac_destroy(ctx: int) -> None:
+    if ctx:
+        lib().etac_destroy(ctx)
+
+
+# ------------------------------------------------------------------ convenience owner
+
+
+class TactileSim:
+    """Owns an etac context for one batch of pads (a ``Scene`` from ``inputs``) together with
+    device tensors for its inputs and outputs.  ``step()`` runs one forward on the current
+    torch stream; inputs can be replaced in place between steps (e.g. under a CUDA graph)."""
+
+    def __init__(self, scene, device="cuda"):
+        import torch
+        self.torch = torch
+        self.scene = scene
+        self.device = torch.device(device)
+        self._host = dict(type_n=np.ascontiguousarray(scene.type_num_nodes, np.int32),
+                          type_pos=np.ascontiguousarray(scene.type_pos, np.float32),
+                          type_nrm=np.ascontiguousarray(scene.type_nrm, np.float32),
+                          pad_type=np.ascontiguousarray(scene.pad_type, np.int32))
+        h = self._host
+        self.pads_desc = etac_pads_desc(len(scene.types), h["type_n"].ctypes.data,
+                                        h["type_pos"].ctypes.data, h["type_nrm"].ctypes.data,
+                                        scene.num_envs, scene.pads_per_env,
+                                        h["pad_type"].ctypes.data, scene.max_objects)
+        self.N = etac_total_nodes(self.pads_desc)
+        stream = torch.cuda.current_stream(self.device).cuda_stream
+        self.ctx = etac_create_pads(self.pads_desc, stream)
+        E, P, K = scene.num_envs, scene.pads_per_env, scene.max_objects
+        f32, i32, dev = torch.float32, torch.int32, self.device
+        self.obj_type = torch.as_tensor(scene.obj_type, dtype=i32).to(dev)
+        self.obj_dims = torch.as_tensor(scene.obj_dims, dtype=f32).to(dev)
+        self.obj_pose = torch.as_tensor(scene.obj_pose, dtype=f32).to(dev)
+        self.pad_pose = torch.as_tensor(scene.pad_pose, dtype=f32).to(dev)
+        self.disp = torch.zeros(self.N, 3, dtype=f32, device=dev)
+        self.mask = torch.zeros(self.N, dtype=torch.uint8, device=dev)
+        self.pen = torch.zeros(self.N, dtype=f32, device=dev)
+        self.count = torch.zeros(E * P, dtype=i32, device=dev)
+        self.model = None
+
+    def set_model(self, params, mode=MODE_FULL, precision=PREC_FP32, algo=ALGO_PLAIN):
+        torch = self.torch
+        self.params = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
+        self.model = etac_model_desc(HIDDEN, mode, precision, algo)
+        etac_set_model(self.ctx, self.model, self.params.data_ptr(),
+                       torch.cuda.current_stream(self.device).cuda_stream)
+
+    def step_in(self) -> etac_step_in:
+        return etac_step_in(self.obj_type.data_ptr(), self.obj_dims.data_ptr(),
+                            self.obj_pose.data_ptr(), self.pad_pose.data_ptr())
+
+    def step_out(self, want_mask=True, want_pen=True, want_count=True) -> etac_step_out:
+        return etac_step_out(self.disp.data_ptr(), self.mask.data_ptr() if want_mask else None,
+                             self.pen.data_ptr() if want_pen else None,
+                             self.count.data_ptr() if want_count else None)
+
+    def step(self, want_mask=True, want_pen=True, want_count=True):
+        etac_step_forward(self.ctx, self.step_in(), self.step_out(want_mask, want_pen, want_count),
+                          self.torch.cuda.current_stream(self.device).cuda_stream)
+        return self.disp
+
+    def poll_status(self) -> int:
+        return etac_poll_status(self.ctx, self.torch.cuda.current_stream(self.device).cuda_stream)
+
+    def close(self):
+        if getattr(self, "ctx", 0):
+            etac_destroy(self.ctx)
+            self.ctx = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# (algo, precision, relative tolerance) exercised by the smoke check
+SMOKE_CONFIGS = ((ALGO_PLAIN, PREC_FP32, 1e-5),)

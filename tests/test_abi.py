@@ -1,0 +1,71 @@
+"""The C-ABI library builds for sm_103a, loads, and exports every entry point that
+include/etac.h declares; host-side argument checks work without a GPU (CPU only)."""
+import ctypes
+import os
+import re
+
+import numpy as np
+import pytest
+
+from paper_2604_20295_gb300 import build as B
+from paper_2604_20295_gb300 import etac as X
+from paper_2604_20295_gb300 import inputs as I
+
+HEADER = os.path.join(B.ROOT, "include", "etac.h")
+
+
+def _declared():
+    src = open(HEADER).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(etac_[a-z0-9_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    B.build()
+    return X.lib()
+
+
+def test_every_declared_symbol_is_exported(lib):
+    names = _declared()
+    assert len(names) >= 10
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(X.EXPORTS)
+
+
+def test_param_count_matches_layout(lib):
+    d = X.etac_model_desc(64, 0, 0, 0)
+    assert X.etac_param_count(d) == I.param_count() == 17412
+    assert X.etac_param_count(X.etac_model_desc(32, 0, 0, 0)) == 0
+
+
+def test_total_nodes_and_validation(lib):
+    sc = I.hand_scene(2, seed=0)
+    tn = np.ascontiguousarray(sc.type_num_nodes, np.int32)
+    pt = np.ascontiguousarray(sc.pad_type, np.int32)
+    pos = np.ascontiguousarray(sc.type_pos)
+    d = X.etac_pads_desc(2, tn.ctypes.data, pos.ctypes.data, pos.ctypes.data, 2, 6,
+                         pt.ctypes.data, 1)
+    assert X.etac_total_nodes(d) == sc.total_nodes == 2 * (5 * 512 + 2048)
+    bad = np.array([0, 0, 0, 0, 0, 7] * 2, np.int32)
+    d.pad_type = bad.ctypes.data
+    assert X.etac_total_nodes(d) == 0
+    # create rejects a bad description on the host, before touching any GPU
+    with pytest.raises(X.EtacError) as e:
+        X.etac_create_pads(d)
+    assert e.value.status == 1
+    assert X.lib().etac_create_pads(None, None, None) == 1
+    d.pad_type = pt.ctypes.data
+    d.max_objects = 99
+    with pytest.raises(X.EtacError) as e:
+        X.etac_create_pads(d)
+    assert e.value.status == 1 and "max_objects" in X.etac_last_error(0)
+
+
+def test_null_context_calls_fail_cleanly(lib):
+    m = X.etac_model_desc(64, 0, 0, 0)
+    assert lib.etac_set_model(None, ctypes.addressof(m), None, None) == 1
+    assert lib.etac_step_forward(None, None, None, None) == 1
+    assert lib.etac_step_backward(None, None, None, None, None, None, None) == 1
+    lib.etac_destroy(None)
