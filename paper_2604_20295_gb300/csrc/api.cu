@@ -42,6 +42,20 @@ struct etac_ctx {
   float* d_saved_obj_pose = nullptr;
   float* d_saved_pad_pose = nullptr;
   int num_sms = 0;
+  // batched algorithm: per-type tables, work queue
+  std::vector<long long> omega_off;
+  std::vector<int> item_pad;
+  long long* d_omega_off = nullptr;
+  int* d_item_pad = nullptr;
+  int* d_ticket = nullptr;
+  float* d_ctab = nullptr;
+  float* d_f0tab = nullptr;
+  float* d_h0tab = nullptr;
+  int16_t* d_order = nullptr;
+  float* d_omega = nullptr;
+  void* d_omega_bf16 = nullptr;
+  bool tables_ready = false;
+  int batched_grid = 0;
 };
 
 namespace {
@@ -81,7 +95,9 @@ void free_ctx(etac_ctx* c) {
   if (!c) return;
   void* ptrs[] = {c->d_type_pos, c->d_type_nrm, c->d_type_pmax, c->d_type_off, c->d_pad_type,
                   c->d_pad_off, c->d_status, c->d_params, c->d_saved_obj_type,
-                  c->d_saved_obj_dims, c->d_saved_obj_pose, c->d_saved_pad_pose};
+                  c->d_saved_obj_dims, c->d_saved_obj_pose, c->d_saved_pad_pose,
+                  c->d_omega_off, c->d_item_pad, c->d_ticket, c->d_ctab, c->d_f0tab,
+                  c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -92,6 +108,49 @@ bool valid_model(const etac_model_desc* d) {
          d->mode <= ETAC_MODE_RESIDUAL_ONLY && (d->precision == ETAC_PREC_FP32 ||
          d->precision == ETAC_PREC_BF16) && (d->algo == ETAC_ALGO_PLAIN ||
          d->algo == ETAC_ALGO_BATCHED);
+}
+
+etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t s) {
+  const size_t tn = (size_t)c->type_off[c->T];
+  const size_t om = (size_t)c->omega_off[c->T];
+  cudaError_t e = cudaSuccess;
+  if (!c->d_ctab) {
+    e = dalloc(&c->d_ctab, tn * etac::H);
+    if (e == cudaSuccess) e = dalloc(&c->d_f0tab, tn * etac::H);
+    if (e == cudaSuccess) e = dalloc(&c->d_h0tab, tn * etac::H);
+    if (e == cudaSuccess) e = dalloc(&c->d_order, tn * etac::H);
+    if (e != cudaSuccess) return cuda_fail(c, e, "allocate per-type tables");
+  }
+  const bool need32 = desc->precision == ETAC_PREC_FP32;
+  if (need32 && !c->d_omega) {
+    e = dalloc(&c->d_omega, om);
+    if (e != cudaSuccess) return cuda_fail(c, e, "allocate Omega table");
+  }
+  if (!c->batched_grid) {
+    int per_sm = 0;
+    e = etac::batched_occupancy(c->nmax, c->K, &per_sm);
+    if (e != cudaSuccess) return cuda_fail(c, e, "batched occupancy");
+    if (per_sm < 1) return fail(c, ETAC_ERR_UNSUPPORTED, "batched kernel does not fit an SM");
+    c->batched_grid = per_sm * c->num_sms;
+  }
+  etac::TablesArgs a{};
+  a.type_pos = c->d_type_pos;
+  a.type_nrm = c->d_type_nrm;
+  a.type_off = c->d_type_off;
+  a.omega_off = c->d_omega_off;
+  a.num_types = c->T;
+  a.total_nodes = (int)tn;
+  a.params = c->d_params;
+  a.ctab = c->d_ctab;
+  a.f0tab = c->d_f0tab;
+  a.h0tab = c->d_h0tab;
+  a.order = c->d_order;
+  a.omega = need32 ? c->d_omega : nullptr;
+  a.omega_bf16 = need32 ? nullptr : c->d_omega_bf16;
+  e = etac::launch_tables(a, c->nmax, s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
+  c->tables_ready = true;
+  return ETAC_OK;
 }
 
 }  // namespace
@@ -174,6 +233,15 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
     c->pad_off[p + 1] = c->pad_off[p] + c->type_n[t];
   }
   c->N = c->pad_off[np];
+  // work items of the batched algorithm: pads by decreasing node count (stable)
+  c->item_pad.resize(np);
+  for (int64_t p = 0; p < np; ++p) c->item_pad[p] = (int)p;
+  std::stable_sort(c->item_pad.begin(), c->item_pad.end(), [&](int x, int y) {
+    return c->type_n[c->pad_type[x]] > c->type_n[c->pad_type[y]];
+  });
+  c->omega_off.assign(c->T + 1, 0);
+  for (int t = 0; t < c->T; ++t)
+    c->omega_off[t + 1] = c->omega_off[t] + (long long)c->type_n[t] * c->type_n[t];
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
@@ -190,6 +258,15 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
   if (e == cudaSuccess) e = dalloc(&c->d_saved_obj_dims, (size_t)c->E * c->K * 3);
   if (e == cudaSuccess) e = dalloc(&c->d_saved_obj_pose, (size_t)c->E * c->K * 7);
   if (e == cudaSuccess) e = dalloc(&c->d_saved_pad_pose, (size_t)np * 7);
+  if (e == cudaSuccess) e = dalloc(&c->d_omega_off, c->T + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_item_pad, np);
+  if (e == cudaSuccess) e = dalloc(&c->d_ticket, 4);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_omega_off, c->omega_off.data(), sizeof(long long) * (c->T + 1),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_item_pad, c->item_pad.data(), sizeof(int) * np,
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_type_pos, d->type_pos, sizeof(float) * 3 * total_type_nodes,
                         cudaMemcpyHostToDevice, s);
@@ -232,8 +309,8 @@ etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float
                 "model desc: hidden must be %d; mode, precision, algo must be known values",
                 ETAC_HIDDEN);
   if (!params || !aligned(params, 4)) return fail(c, ETAC_ERR_INVALID_ARG, "params NULL/misaligned");
-  if (desc->algo == ETAC_ALGO_BATCHED || desc->precision == ETAC_PREC_BF16)
-    return fail(c, ETAC_ERR_UNSUPPORTED, "batched / BF16 algorithm not built yet");
+  if (desc->precision == ETAC_PREC_BF16)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 algorithm not built yet");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float alpha = 0.f;
   ETAC_CUDA(c, cudaMemcpyAsync(&alpha, params, sizeof(float), cudaMemcpyDeviceToHost, s),
@@ -243,6 +320,10 @@ etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float
     return fail(c, ETAC_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
   ETAC_CUDA(c, cudaMemcpyAsync(c->d_params, params, sizeof(float) * etac::NPARAM,
                                cudaMemcpyDeviceToDevice, s), "copy params");
+  if (desc->algo == ETAC_ALGO_BATCHED) {
+    etac_status st = build_tables(c, desc, s);
+    if (st != ETAC_OK) return st;
+  }
   c->model = *desc;
   c->has_model = true;
   return ETAC_OK;
@@ -271,6 +352,43 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
                                cudaMemcpyDeviceToDevice, s), "save inputs");
   ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_pad_pose, in->pad_pose, sizeof(float) * EP * 7,
                                cudaMemcpyDeviceToDevice, s), "save inputs");
+  if (c->model.algo == ETAC_ALGO_BATCHED) {
+    etac::BatchedArgs b{};
+    b.type_pos = c->d_type_pos;
+    b.type_nrm = c->d_type_nrm;
+    b.type_pmax = c->d_type_pmax;
+    b.type_off = c->d_type_off;
+    b.omega_off = c->d_omega_off;
+    b.pad_type = c->d_pad_type;
+    b.pad_off = c->d_pad_off;
+    b.item_pad = c->d_item_pad;
+    b.num_items = (int)EP;
+    b.P = c->P;
+    b.K = c->K;
+    b.nmax = c->nmax;
+    b.obj_type = c->d_saved_obj_type;
+    b.obj_dims = c->d_saved_obj_dims;
+    b.obj_pose = c->d_saved_obj_pose;
+    b.pad_pose = c->d_saved_pad_pose;
+    b.params = c->d_params;
+    b.ctab = c->d_ctab;
+    b.f0tab = c->d_f0tab;
+    b.h0tab = c->d_h0tab;
+    b.order = c->d_order;
+    b.omega = c->d_omega;
+    b.mode = c->model.mode;
+    b.disp = out->disp;
+    b.mask = out->active_mask;
+    b.pen = out->penetration;
+    b.count = out->active_count;
+    b.ticket = c->d_ticket;
+    b.status = c->d_status;
+    ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
+    ETAC_CUDA(c, etac::launch_batched_forward(b, std::min<int>(c->batched_grid, (int)EP), s),
+              "batched forward launch");
+    c->has_forward = true;
+    return ETAC_OK;
+  }
   etac::PlainArgs<float> a{};
   a.type_pos = c->d_type_pos;
   a.type_nrm = c->d_type_nrm;

@@ -1,0 +1,342 @@
+// batched.cu -- the batched FP32 ETac step: one persistent launch over every pad of the batch.
+//
+// Work items are pad instances ordered heaviest first (largest node count); persistent CTAs
+// take them from a device ticket counter, so pads of uneven size balance across the SMs.
+// Per pad (ETac Sec. III-A):
+//   1. contact on every node (df32 decisions), active set compacted in node order with warp
+//      ballots; active nodes keep u_hat (Eq. 4 only covers passive ones);
+//   2. residual network, factored through the per-type tables: only active nodes run the
+//      encoder (their first layer is c_i + W1[:, 6:9] u_hat_i); passive nodes' encoder
+//      outputs f0_i are table entries, so the channel max-pool over them is the first
+//      passive node in the table's per-channel order; global MLP; decoder global half
+//      beta = D1[:, 64:128] g;
+//   3. every passive node: Omega U_a (Eq. 1, Omega from the per-type table) plus
+//      Phi_p = D2 ReLU(h0_i + beta) + b (Eq. 4).
+// The algebra equals the literal network exactly; only rounding order differs.
+#include "etac_common.cuh"
+#include "etac_kernels.h"
+
+namespace etac {
+
+constexpr int BT = 256;
+constexpr int BW = BT / 32;
+
+struct BatchedSmem {
+  // byte offsets of every shared array for a given nmax / K
+  size_t w2, b2, w1u, w4, b4, g, beta, red, actu, actidx, mask, warp, po, total;
+  __host__ __device__ BatchedSmem(int nmax, int K) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      size_t r = o;
+      o = (o + bytes + 15) & ~size_t(15);
+      return r;
+    };
+    w2 = take(sizeof(float) * H * H);
+    b2 = take(sizeof(float) * H);
+    w1u = take(sizeof(float) * H * 4);
+    w4 = take(sizeof(float) * 3 * H);
+    b4 = take(sizeof(float) * 4);
+    g = take(sizeof(float) * H);
+    beta = take(sizeof(float) * H);
+    red = take(sizeof(float) * BW * H);
+    actu = take(sizeof(float4) * (size_t)nmax);
+    actidx = take(sizeof(int16_t) * (size_t)nmax);
+    mask = take(sizeof(uint8_t) * (size_t)nmax);
+    warp = take(sizeof(int) * (BW + 4));
+    po = take(sizeof(PadObj) * (size_t)K);
+    total = o;
+  }
+};
+
+__global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  __shared__ int s_item;
+  const BatchedSmem L(a.nmax, a.K);
+  float* sW2 = reinterpret_cast<float*>(smem + L.w2);
+  float* sB2 = reinterpret_cast<float*>(smem + L.b2);
+  float* sW1u = reinterpret_cast<float*>(smem + L.w1u);   // [H][4]: weights on u_hat
+  float* sW4 = reinterpret_cast<float*>(smem + L.w4);
+  float* sB4 = reinterpret_cast<float*>(smem + L.b4);
+  float* sG = reinterpret_cast<float*>(smem + L.g);
+  float* sBeta = reinterpret_cast<float*>(smem + L.beta);
+  float* sRed = reinterpret_cast<float*>(smem + L.red);
+  float4* sActU = reinterpret_cast<float4*>(smem + L.actu);
+  int16_t* sActIdx = reinterpret_cast<int16_t*>(smem + L.actidx);
+  uint8_t* sMask = reinterpret_cast<uint8_t*>(smem + L.mask);
+  int* sWarp = reinterpret_cast<int*>(smem + L.warp);
+  PadObj* spo = reinterpret_cast<PadObj*>(smem + L.po);
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* W = a.params;
+  for (int i = tid; i < H * H; i += BT) sW2[i] = W[OFF_W2 + i];
+  for (int i = tid; i < H; i += BT) {
+    sB2[i] = W[OFF_B2 + i];
+    sW1u[4 * i + 0] = W[OFF_W1 + i * NIN + 6];
+    sW1u[4 * i + 1] = W[OFF_W1 + i * NIN + 7];
+    sW1u[4 * i + 2] = W[OFF_W1 + i * NIN + 8];
+    sW1u[4 * i + 3] = 0.f;
+  }
+  for (int i = tid; i < 3 * H; i += BT) sW4[i] = W[OFF_W4 + i];
+  if (tid < 3) sB4[tid] = W[OFF_B4 + tid];
+  const unsigned lt_mask = (1u << lane) - 1u;
+
+  for (;;) {
+    __syncthreads();
+    if (tid == 0) {
+      s_item = atomicAdd(a.ticket, 1);
+      sWarp[BW] = 0;   // invalid-input flag
+    }
+    __syncthreads();
+    const int item = s_item;
+    if (item >= a.num_items) break;
+    const int pad = a.item_pad[item];
+    const int env = pad / a.P;
+    const int ty = a.pad_type[pad];
+    const int o = a.type_off[ty];
+    const int n = a.type_off[ty + 1] - o;
+    const long long base = a.pad_off[pad];
+    const float* tpos = a.type_pos + 3 * (size_t)o;
+    const float* tnrm = a.type_nrm + 3 * (size_t)o;
+
+    if (tid < a.K) {
+      const int ob = env * a.K + tid;
+      const float* op = a.obj_pose + 7 * (size_t)ob;
+      const float* pp = a.pad_pose + 7 * (size_t)pad;
+      const float* od = a.obj_dims + 3 * (size_t)ob;
+      int type = a.obj_type[ob];
+      if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+      bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
+                isfinite(od[2]);
+      if (!ok && type != OBJ_NONE) {
+        sWarp[BW] = 1;
+        type = OBJ_NONE;
+      }
+      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
+    }
+    __syncthreads();
+    if (sWarp[BW]) {
+      if (tid == 0) latch_status(a.status, STATUS_NONFINITE);
+      for (int i = tid; i < n; i += BT) {
+        float* d = a.disp + 3 * (base + i);
+        d[0] = d[1] = d[2] = 0.f;
+        if (a.mask) a.mask[base + i] = 0;
+        if (a.pen) a.pen[base + i] = 0.f;
+      }
+      if (tid == 0 && a.count) a.count[pad] = 0;
+      continue;
+    }
+
+    // ---- 1. contact; active set in node order
+    int m = 0;
+    for (int r0 = 0; r0 < n; r0 += BT) {
+      const int i = r0 + tid;
+      NodeContact c;
+      c.active = false;
+      c.phi = 0.f;
+      if (i < n) {
+        float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+        float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+        c = contact_node(spo, a.K, p, nr);
+      }
+      const unsigned bal = __ballot_sync(0xffffffffu, c.active);
+      if (lane == 0) sWarp[warp] = __popc(bal);
+      __syncthreads();
+      int woff = 0, tot = 0;
+#pragma unroll
+      for (int w = 0; w < BW; ++w) {
+        const int v = sWarp[w];
+        woff += w < warp ? v : 0;
+        tot += v;
+      }
+      if (i < n) {
+        sMask[i] = c.active ? 1 : 0;
+        if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
+        if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
+        if (c.active) {
+          const int slot = m + woff + __popc(bal & lt_mask);
+          sActIdx[slot] = (int16_t)i;
+          sActU[slot] = make_float4(c.u[0], c.u[1], c.u[2], 0.f);
+          float* d = a.disp + 3 * (base + i);
+          d[0] = c.u[0];
+          d[1] = c.u[1];
+          d[2] = c.u[2];
+        }
+      }
+      m += tot;
+      __syncthreads();
+    }
+    if (tid == 0 && a.count) a.count[pad] = m;
+    if (m == 0) {   // no contact: the whole pad is at rest
+      for (int i = tid; i < n; i += BT) {
+        float* d = a.disp + 3 * (base + i);
+        d[0] = d[1] = d[2] = 0.f;
+      }
+      continue;
+    }
+
+    // ---- 2. residual network (factored)
+    if (a.mode != MODE_LINEAR_ONLY) {
+      float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
+      for (int a0 = 0; a0 < m; a0 += BT) {
+        const int aa = a0 + tid;
+        const bool live = aa < m;
+        float z1[H];
+        if (live) {
+          const int i = sActIdx[aa];
+          const float4 u = sActU[aa];
+          const float4* crow = reinterpret_cast<const float4*>(a.ctab + (size_t)(o + i) * H);
+#pragma unroll
+          for (int c4 = 0; c4 < H / 4; ++c4) {
+            const float4 cv = __ldg(crow + c4);
+            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {
+              const int c = 4 * c4 + q;
+              const float4 w = *reinterpret_cast<const float4*>(sW1u + 4 * c);
+              z1[c] = fmaxf(fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, cc[q]))), 0.f);
+            }
+          }
+        } else {
+#pragma unroll
+          for (int c = 0; c < H; ++c) z1[c] = 0.f;
+        }
+#pragma unroll
+        for (int c = 0; c < H; ++c) {
+          float acc = sB2[c];
+          const float4* wr = reinterpret_cast<const float4*>(sW2 + c * H);
+#pragma unroll
+          for (int k4 = 0; k4 < H / 4; ++k4) {
+            const float4 w = wr[k4];
+            acc = fmaf(w.x, z1[4 * k4 + 0], acc);
+            acc = fmaf(w.y, z1[4 * k4 + 1], acc);
+            acc = fmaf(w.z, z1[4 * k4 + 2], acc);
+            acc = fmaf(w.w, z1[4 * k4 + 3], acc);
+          }
+          const float f = live ? fmaxf(acc, 0.f) : 0.f;
+          // f >= 0, so unsigned order of the bit patterns is the float order
+          const float mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f)));
+          if (c < 32) {
+            if (lane == c) fm0 = fmaxf(fm0, mx);
+          } else {
+            if (lane == c - 32) fm1 = fmaxf(fm1, mx);
+          }
+        }
+      }
+      sRed[warp * H + lane] = fm0;
+      sRed[warp * H + 32 + lane] = fm1;
+      __syncthreads();
+      if (tid < H) {
+        float g0 = 0.f;
+#pragma unroll
+        for (int w = 0; w < BW; ++w) g0 = fmaxf(g0, sRed[w * H + tid]);
+        // passive maximum: first passive node in this channel's descending order of f0
+        const int16_t* ord = a.order + (size_t)H * o + (size_t)tid * n;
+        for (int r = 0; r < n; ++r) {
+          const int idx = ord[r];
+          if (!sMask[idx]) {
+            g0 = fmaxf(g0, __ldg(a.f0tab + (size_t)(o + idx) * H + tid));
+            break;
+          }
+        }
+        sG[tid] = g0;
+      }
+      __syncthreads();
+      float gv = 0.f;
+      if (tid < H) {
+        float acc = W[OFF_BG + tid];
+        const float4* wr = reinterpret_cast<const float4*>(W + OFF_WG + tid * H);
+        for (int k4 = 0; k4 < H / 4; ++k4) {
+          const float4 w = __ldg(wr + k4);
+          acc = fmaf(w.x, sG[4 * k4], fmaf(w.y, sG[4 * k4 + 1],
+                     fmaf(w.z, sG[4 * k4 + 2], fmaf(w.w, sG[4 * k4 + 3], acc))));
+        }
+        gv = fmaxf(acc, 0.f);
+      }
+      __syncthreads();
+      if (tid < H) sG[tid] = gv;
+      __syncthreads();
+      if (tid < H) {
+        float acc = 0.f;
+        const float* wr = W + OFF_WD + tid * 2 * H + H;
+        for (int k = 0; k < H; ++k) acc = fmaf(__ldg(wr + k), sG[k], acc);
+        sBeta[tid] = acc;
+      }
+      __syncthreads();
+    }
+
+    // ---- 3. passive nodes: Eq. 4
+    const float* Om = a.omega + a.omega_off[ty];
+    for (int i = tid; i < n; i += BT) {
+      if (sMask[i]) continue;
+      float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+      if (a.mode != MODE_RESIDUAL_ONLY) {
+        const float* col = Om + i;
+#pragma unroll 4
+        for (int aa = 0; aa < m; ++aa) {
+          const int j = sActIdx[aa];
+          const float4 u = sActU[aa];
+          const float w = __ldg(col + (size_t)j * n);
+          l0 = fmaf(w, u.x, l0);
+          l1 = fmaf(w, u.y, l1);
+          l2 = fmaf(w, u.z, l2);
+        }
+      }
+      if (a.mode != MODE_LINEAR_ONLY) {
+        float r0 = sB4[0], r1 = sB4[1], r2 = sB4[2];
+        const float4* hrow = reinterpret_cast<const float4*>(a.h0tab + (size_t)(o + i) * H);
+#pragma unroll
+        for (int c4 = 0; c4 < H / 4; ++c4) {
+          const float4 hv = __ldg(hrow + c4);
+          const float hh[4] = {hv.x, hv.y, hv.z, hv.w};
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const int c = 4 * c4 + q;
+            const float z = fmaxf(hh[q] + sBeta[c], 0.f);
+            r0 = fmaf(sW4[c], z, r0);
+            r1 = fmaf(sW4[H + c], z, r1);
+            r2 = fmaf(sW4[2 * H + c], z, r2);
+          }
+        }
+        l0 += r0;
+        l1 += r1;
+        l2 += r2;
+      }
+      float* d = a.disp + 3 * (base + i);
+      d[0] = l0;
+      d[1] = l1;
+      d[2] = l2;
+    }
+  }
+}
+
+size_t batched_smem_bytes(int nmax, int K) { return BatchedSmem(nmax, K).total; }
+int batched_threads() { return BT; }
+
+static cudaError_t configure(size_t smem) {
+  static size_t configured = 0;
+  if (smem > configured) {
+    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    configured = smem;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
+  size_t smem = batched_smem_bytes(nmax, K);
+  cudaError_t e = configure(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel, BT,
+                                                       smem);
+}
+
+cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s) {
+  size_t smem = batched_smem_bytes(a.nmax, a.K);
+  cudaError_t e = configure(smem);
+  if (e != cudaSuccess) return e;
+  batched_forward_kernel<<<grid, BT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace etac

@@ -1,6 +1,7 @@
-"""GPU parity of the plain algorithm (one CTA per pad, literal Eq. 1 / Eq. 4) against the
-FP64 oracle, through the C ABI.  Contact sets bit-exact outside the 1e-6 mm band,
-displacements within 1e-5 normwise per pad."""
+"""GPU parity of the FP32 forward algorithms against the FP64 oracle, through the C ABI:
+the plain algorithm (one CTA per pad, literal Eq. 1 / Eq. 4) and the batched algorithm (one
+persistent launch, per-type tables, factored network).  Contact sets bit-exact outside the
+1e-6 mm band, displacements within 1e-5 normwise per pad."""
 import numpy as np
 import pytest
 import torch
@@ -36,6 +37,9 @@ def run(scene, theta, mode=X.MODE_FULL, algo=X.ALGO_PLAIN, precision=X.PREC_FP32
     return out
 
 
+ALGOS = [X.ALGO_PLAIN, X.ALGO_BATCHED]
+
+
 def check(scene, theta, mode=X.MODE_FULL, **kw):
     got = run(scene, theta, mode, **kw)
     ref, nband = PT.oracle_forward_matching(scene, theta, mode, got["mask"])
@@ -48,28 +52,32 @@ def check(scene, theta, mode=X.MODE_FULL, **kw):
     return got, ref, err, nband
 
 
+@pytest.mark.parametrize("algo", ALGOS)
 @pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY])
-def test_sphere_press_100_steps(mode):
+def test_sphere_press_100_steps(mode, algo):
     """16x16 flat pad, sphere r = 5 mm pressed 0-2 mm, 100 seeded steps (one env each)."""
     sc = I.sphere_press_scene(100, seed=0)
-    got, ref, err, _ = check(sc, I.make_params(0), mode)
+    got, ref, err, _ = check(sc, I.make_params(0), mode, algo=algo)
     assert got["mask"].sum() > 100
 
 
-def test_hand_scene_sampled_envs():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_hand_scene_sampled_envs(algo):
     """Curved 16x32 fingertips + flat 32x64 palm, random primitives; 40 sampled envs."""
     full = I.hand_scene(512, seed=3)
     sc = full.subset(np.random.default_rng(0).choice(512, 40, replace=False))
-    got, ref, err, nband = check(sc, I.make_params(0))
+    got, ref, err, nband = check(sc, I.make_params(0), algo=algo)
     frac = got["count"] / sc.pad_nodes
     assert 0.05 < frac.mean() < 0.45
 
 
-def test_hand_scene_full_size_sampled_outputs():
-    """4,096 environments (18.9 M nodes) in one launch; outputs of sampled envs vs oracle."""
+@pytest.mark.parametrize("algo", ALGOS)
+def test_hand_scene_full_size_sampled_outputs(algo):
+    """4,096 environments (18.9 M nodes) in one launch, the benchmark's configuration;
+    outputs of sampled envs vs oracle."""
     full = I.hand_scene(4096, seed=2)
     th = I.make_params(0)
-    got = run(full, th)
+    got = run(full, th, algo=algo)
     envs = np.sort(np.random.default_rng(1).choice(4096, 12, replace=False))
     offs = full.node_offsets
     for e in envs:
@@ -80,31 +88,34 @@ def test_hand_scene_full_size_sampled_outputs():
         np.testing.assert_array_equal(got["count"][e * 6:e * 6 + 6], ref["active_count"])
 
 
-def test_uneven_pads_and_multiple_objects():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_uneven_pads_and_multiple_objects(algo):
     """Pads of 8x8 .. 64x64 nodes at 0.5-2 mm pitch, 1-3 primitives per env (union SDF)."""
     full = I.uneven_scene(64, seed=5)
     sc = full.subset(np.arange(0, 64, 4))
-    check(sc, I.make_params(1))
+    check(sc, I.make_params(1), algo=algo)
 
 
-def test_no_contact_gives_zero_and_edge_sizes():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_no_contact_gives_zero_and_edge_sizes(algo):
     """Objects far away: zero displacement, zero counts; single-node and 1xN pads."""
     types = [I.flat_pad(1, 1, 1.0), I.flat_pad(1, 7, 1.0), I.flat_pad(5, 3, 0.5)]
     objs = {0: (I.OBJ_SPHERE, (3, 0, 0), (0, 0, 50, 0, 0, 0, 1)),
             1: (I.OBJ_BOX, (2, 2, 2), (0.1, 0.1, 1.5, 0, 0, 0, 1))}
     poses = [[0, 0, 0, 0, 0, 0, 1]] * 6
     sc = I.custom_scene(types, [0, 1, 2, 0, 1, 2], objs, poses, 2, 1)
-    got, ref, _, _ = check(sc, I.make_params(2))
+    got, ref, _, _ = check(sc, I.make_params(2), algo=algo)
     assert np.all(got["disp"][:sc.node_offsets[3]] == 0)
     assert got["count"][3:].sum() > 0
 
 
-def test_nonfinite_pose_is_latched():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_nonfinite_pose_is_latched(algo):
     """A NaN object pose zeroes that env's pads and latches ETAC_ERR_NONFINITE; other envs
     are unaffected."""
     sc = I.sphere_press_scene(4, seed=1)
     sc.obj_pose[7 * 2 + 1] = np.nan
-    got = run(sc, I.make_params(0))
+    got = run(sc, I.make_params(0), algo=algo)
     assert got["status"] == 6
     offs = sc.node_offsets
     assert np.all(got["disp"][offs[2]:offs[3]] == 0)
@@ -114,11 +125,45 @@ def test_nonfinite_pose_is_latched():
     PT.assert_disp_close(good, g, ref["disp"])
 
 
-def test_repeat_is_bitwise_deterministic():
+@pytest.mark.parametrize("algo", ALGOS)
+def test_repeat_is_bitwise_deterministic(algo):
     sc = I.hand_scene(16, seed=9)
-    a = run(sc, I.make_params(0))
-    b = run(sc, I.make_params(0))
+    a = run(sc, I.make_params(0), algo=algo)
+    b = run(sc, I.make_params(0), algo=algo, steps=2)
     assert np.array_equal(a["disp"], b["disp"]) and np.array_equal(a["mask"], b["mask"])
+
+
+@pytest.mark.parametrize("algo", ALGOS)
+def test_cuda_graph_replay_with_new_inputs(algo):
+    """The step captured once in a CUDA graph and replayed after the input poses are
+    overwritten in place gives the same result as an eager step on those inputs."""
+    sc0 = I.hand_scene(24, seed=21)
+    sc1 = I.hand_scene(24, seed=22)
+    th = I.make_params(0)
+    sim = X.TactileSim(sc0)
+    try:
+        sim.set_model(th, X.MODE_FULL, X.PREC_FP32, algo)
+        s = torch.cuda.Stream()
+        s.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(s):
+            sim.step()          # warm-up outside capture
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(g, stream=s):
+                sim.step()
+        torch.cuda.current_stream().wait_stream(s)
+        for sc in (sc1, sc0, sc1):
+            sim.obj_type.copy_(torch.as_tensor(sc.obj_type))
+            sim.obj_dims.copy_(torch.as_tensor(sc.obj_dims))
+            sim.obj_pose.copy_(torch.as_tensor(sc.obj_pose))
+            sim.pad_pose.copy_(torch.as_tensor(sc.pad_pose))
+            sim.disp.zero_()
+            g.replay()
+            torch.cuda.synchronize()
+            got = sim.disp.cpu().numpy().astype(np.float64)
+            eager = run(sc, th, algo=algo)
+            assert np.array_equal(got, eager["disp"])
+    finally:
+        sim.close()
 
 
 def test_fp64_forward_matches_oracle():
