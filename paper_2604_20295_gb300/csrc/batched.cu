@@ -243,13 +243,11 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       __syncthreads();
       float gv = 0.f;
       if (tid < H) {
+        // the flat parameter vector starts with alpha, so its tensors are only 4-byte
+        // aligned: scalar loads here
         float acc = W[OFF_BG + tid];
-        const float4* wr = reinterpret_cast<const float4*>(W + OFF_WG + tid * H);
-        for (int k4 = 0; k4 < H / 4; ++k4) {
-          const float4 w = __ldg(wr + k4);
-          acc = fmaf(w.x, sG[4 * k4], fmaf(w.y, sG[4 * k4 + 1],
-                     fmaf(w.z, sG[4 * k4 + 2], fmaf(w.w, sG[4 * k4 + 3], acc))));
-        }
+        const float* wr = W + OFF_WG + tid * H;
+        for (int k = 0; k < H; ++k) acc = fmaf(__ldg(wr + k), sG[k], acc);
         gv = fmaxf(acc, 0.f);
       }
       __syncthreads();
