@@ -157,12 +157,60 @@ etac_status etac_forward_f64(etac_ctx* ctx, const etac_model_desc* desc,
                              const double* obj_pose, const double* pad_pose,
                              const double* params, double* disp, void* stream);
 
-/* Message of the last failed call on this context (or of the last failed create when
- * ctx is NULL).  Valid until the next call on the same context. */
+/* Message of the last failed call on this context (or, when ctx is NULL, of the last failed
+ * etac_create_pads / etac_step_forward_noalloc on this thread).  Valid until the next call
+ * on the same context. */
 const char* etac_last_error(const etac_ctx* ctx);
 
 /* Frees the context and its device memory (synchronises the device first). NULL is a no-op. */
 void etac_destroy(etac_ctx* ctx);
+
+/* ---- Forward step for callers that cannot allocate device memory.
+ *
+ * The paper has no counterpart: this entry point exists for integration.  Some callers must
+ * not allocate GPU memory while they run: a host application that hands the whole device
+ * heap to its own pool allocator up front (physics engines commonly do), a real-time
+ * control loop in which an allocation's latency or failure is not acceptable, or code that
+ * is being recorded into a CUDA graph, where cudaMalloc is not permitted.  Such callers
+ * cannot use etac_create_pads / etac_set_model, which allocate.
+ *
+ * etac_step_forward_noalloc runs the batched FP32 forward (ETAC_ALGO_BATCHED,
+ * ETAC_PREC_FP32) from device pointers only.  The caller passes every input (pad geometry,
+ * parameters, poses) and every output; the scratch the step needs (work-queue counter, status
+ * word, per-pad-type tables) lives in one static device array of ETAC_NOALLOC_SCRATCH_BYTES
+ * inside the library, which every GPU that loads the library holds until the process exits.
+ * The call allocates and frees nothing.  Limits: the scratch must hold
+ * 896 bytes per pad-type node, 4 bytes per (node, node) pair of every pad type, and 4 bytes
+ * per pad instance (plus alignment); larger batches are rejected with ETAC_ERR_INVALID_ARG
+ * and a message giving the bytes needed.
+ *
+ * The first call on each device looks up the device address of the static array (once, with
+ * that device current), so make that first call before any stream capture.  Every call
+ * rebuilds the tables from `params` and clears the counter it needs, so calls are
+ * independent, but all calls share the one array: calls that overlap on the GPU (different
+ * streams, or different host threads on one device) race and give wrong results.
+ * Non-finite poses zero the affected pads but are not reported (there is no context to hold
+ * the status word).  Errors are read with etac_last_error(NULL). */
+#define ETAC_NOALLOC_SCRATCH_BYTES (32u << 20)
+
+typedef struct {
+  int32_t num_types;             /* T >= 1                                                    */
+  const int32_t* type_num_nodes; /* HOST [T] node count per pad type (sizes and validation)    */
+  const int32_t* type_off;       /* device [T+1] prefix sums of type_num_nodes                  */
+  const float* type_pos;         /* device [sum n, 3] undeformed positions, pad frame (mm)     */
+  const float* type_nrm;         /* device [sum n, 3] unit outward normals                      */
+  int32_t num_envs;              /* >= 1                                                        */
+  int32_t pads_per_env;          /* >= 1                                                        */
+  int32_t max_objects;           /* K in [1, ETAC_MAX_OBJECTS]                                  */
+  const int32_t* pad_type;       /* device [E*P] pad type of each pad instance                  */
+  const int64_t* pad_off;        /* device [E*P+1] first flat node index of each pad instance   */
+} etac_noalloc_pads;
+
+/* mode: ETAC_MODE_*; params: device FP32 [etac_param_count] (alpha must be > 0, unchecked);
+ * in / out as for etac_step_forward (device pointers).  Enqueues work on `stream` only. */
+etac_status etac_step_forward_noalloc(const etac_noalloc_pads* pads, int32_t mode,
+                                      const float* params, const etac_step_in* in,
+                                      const etac_step_out* out, void* stream);
 
 #ifdef __cplusplus
 }

@@ -155,6 +155,11 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
 
 }  // namespace
 
+namespace etac {
+// message of a failed call that has no context (read back with etac_last_error(NULL))
+void set_context_free_error(const std::string& msg) { g_create_err = msg; }
+}  // namespace etac
+
 extern "C" {
 
 size_t etac_param_count(const etac_model_desc* desc) {

@@ -26,7 +26,7 @@ HIDDEN = 64
 
 EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
            "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
-           "etac_last_error", "etac_destroy")
+           "etac_last_error", "etac_destroy", "etac_step_forward_noalloc")
 
 _vp = ctypes.c_void_p
 
@@ -49,6 +49,13 @@ class etac_step_in(ctypes.Structure):
 class etac_step_out(ctypes.Structure):
     _fields_ = [("disp", _vp), ("active_mask", _vp), ("penetration", _vp),
                 ("active_count", _vp)]
+
+
+class etac_noalloc_pads(ctypes.Structure):
+    _fields_ = [("num_types", ctypes.c_int32), ("type_num_nodes", _vp), ("type_off", _vp),
+                ("type_pos", _vp), ("type_nrm", _vp), ("num_envs", ctypes.c_int32),
+                ("pads_per_env", ctypes.c_int32), ("max_objects", ctypes.c_int32),
+                ("pad_type", _vp), ("pad_off", _vp)]
 
 
 class EtacError(RuntimeError):
@@ -89,6 +96,8 @@ def lib():
         L.etac_last_error.argtypes = [_vp]
         L.etac_destroy.restype = None
         L.etac_destroy.argtypes = [_vp]
+        L.etac_step_forward_noalloc.restype = ctypes.c_int
+        L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
         _lib = L
     return _lib
 
@@ -153,6 +162,14 @@ def etac_last_error(ctx: int = 0) -> str:
 def etac_destroy(ctx: int) -> None:
     if ctx:
         lib().etac_destroy(ctx)
+
+
+def etac_step_forward_noalloc(pads: etac_noalloc_pads, mode: int, params: int,
+                              sin: etac_step_in, sout: etac_step_out, stream: int = 0) -> None:
+    """Batched FP32 forward that allocates nothing (scratch in a static device array)."""
+    _check(None, lib().etac_step_forward_noalloc(ctypes.addressof(pads), mode, params,
+                                                 ctypes.addressof(sin), ctypes.addressof(sout),
+                                                 stream), "etac_step_forward_noalloc")
 
 
 # ------------------------------------------------------------------ convenience owner
