@@ -56,6 +56,20 @@ struct etac_ctx {
   void* d_omega_bf16 = nullptr;
   bool tables_ready = false;
   int batched_grid = 0;
+  // BF16 tensor-core algorithm
+  void* d_h0bf16 = nullptr;
+  void* d_bt = nullptr;
+  long long* d_bt_off = nullptr;
+  int* d_pad_inst = nullptr;
+  int* d_inst_off = nullptr;
+  int* d_inst_pad = nullptr;
+  void* d_negbeta = nullptr;
+  float4* d_c0m = nullptr;
+  uint8_t* d_maskbuf = nullptr;
+  etac::GemmTile* d_tiles = nullptr;
+  etac::GemmParams gemm{};
+  int front_grid = 0, gemm_grid = 0;
+  bool bf16_ready = false;
 };
 
 namespace {
@@ -97,7 +111,9 @@ void free_ctx(etac_ctx* c) {
                   c->d_pad_off, c->d_status, c->d_params, c->d_saved_obj_type,
                   c->d_saved_obj_dims, c->d_saved_obj_pose, c->d_saved_pad_pose,
                   c->d_omega_off, c->d_item_pad, c->d_ticket, c->d_ctab, c->d_f0tab,
-                  c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16};
+                  c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
+                  c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
+                  c->d_c0m, c->d_maskbuf, c->d_tiles};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -108,6 +124,124 @@ bool valid_model(const etac_model_desc* d) {
          d->mode <= ETAC_MODE_RESIDUAL_ONLY && (d->precision == ETAC_PREC_FP32 ||
          d->precision == ETAC_PREC_BF16) && (d->algo == ETAC_ALGO_PLAIN ||
          d->algo == ETAC_ALGO_BATCHED);
+}
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                  const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                  const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                  CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+// 2-D BF16 tensor [rows][cols] (cols contiguous), box of 64 columns x box_rows rows, 128B swizzle
+bool encode_bf16_2d(EncodeTiledFn fn, CUtensorMap* m, const void* base, uint64_t cols,
+                    uint64_t rows, uint32_t box_rows) {
+  cuuint64_t dims[2] = {cols, rows};
+  cuuint64_t strides[1] = {cols * 2};
+  cuuint32_t box[2] = {64, box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box,
+            estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
+// Buffers, tile list and tensor maps of the BF16 tensor-core algorithm (once per context).
+etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
+  if (c->bf16_ready) return ETAC_OK;
+  if (c->T > etac::GEMM_MAX_TYPES)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 algorithm supports at most %d pad types",
+                etac::GEMM_MAX_TYPES);
+  for (int t = 0; t < c->T; ++t)
+    if (c->type_n[t] % 8 != 0)
+      return fail(c, ETAC_ERR_UNSUPPORTED,
+                  "BF16 algorithm needs node counts that are multiples of 8 (type %d has %d)", t,
+                  c->type_n[t]);
+  const int np = c->E * c->P;
+  std::vector<int> inst_off(c->T + 1, 0), pad_inst(np), ninst(c->T, 0);
+  for (int p = 0; p < np; ++p) pad_inst[p] = ninst[c->pad_type[p]]++;
+  for (int t = 0; t < c->T; ++t) inst_off[t + 1] = inst_off[t] + ninst[t];
+  std::vector<int> inst_pad(np), fill(c->T, 0);
+  for (int p = 0; p < np; ++p) {
+    const int t = c->pad_type[p];
+    inst_pad[inst_off[t] + fill[t]++] = p;
+  }
+  std::vector<long long> bt_off(c->T, 0);
+  long long bt_total = 0;
+  for (int t = 0; t < c->T; ++t) {
+    bt_off[t] = bt_total;
+    bt_total += ((3LL * ninst[t] * c->type_n[t]) + 127) / 128 * 128;
+  }
+  std::vector<etac::GemmTile> tiles;
+  for (int t = 0; t < c->T; ++t) {
+    if (!ninst[t]) continue;
+    const int n = c->type_n[t];
+    for (int m0 = 0; m0 < n; m0 += 128)
+      for (int k0 = 0; k0 < ninst[t]; k0 += 64) tiles.push_back({t, m0, k0, (n + 63) / 64});
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const etac::GemmTile& x,
+                                                  const etac::GemmTile& y) {
+    return x.nkb > y.nkb;   // heaviest tiles first
+  });
+  const size_t tn = (size_t)c->type_off[c->T];
+  cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_omega_bf16), 2 * (size_t)c->omega_off[c->T]);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_h0bf16), 2 * tn * etac::H);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bt), 2 * (size_t)bt_total);
+  if (e == cudaSuccess) e = dalloc(&c->d_bt_off, c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_inst, np);
+  if (e == cudaSuccess) e = dalloc(&c->d_inst_off, c->T + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_inst_pad, np);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
+  if (e == cudaSuccess) e = dalloc(&c->d_maskbuf, (size_t)c->N);
+  if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_bt_off, bt_off.data(), sizeof(long long) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pad_inst, pad_inst.data(), sizeof(int) * np,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_off, inst_off.data(),
+                                            sizeof(int) * (c->T + 1), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_pad, inst_pad.data(), sizeof(int) * np,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess && !tiles.empty())
+    e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(etac::GemmTile) * tiles.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors are pageable
+  if (e != cudaSuccess) return cuda_fail(c, e, "BF16 buffers");
+  void* fn = nullptr;
+  cudaDriverEntryPointQueryResult qr;
+  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
+                                       &qr);
+  if (e != cudaSuccess || !fn || qr != cudaDriverEntryPointSuccess)
+    return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  etac::GemmParams& g = c->gemm;
+  memset(&g, 0, sizeof g);
+  for (int t = 0; t < c->T; ++t) {
+    const int n = c->type_n[t];
+    const char* om = reinterpret_cast<const char*>(c->d_omega_bf16) + 2 * (size_t)c->omega_off[t];
+    const char* bt = reinterpret_cast<const char*>(c->d_bt) + 2 * (size_t)bt_off[t];
+    if (!encode_bf16_2d(reinterpret_cast<EncodeTiledFn>(fn), &g.tmA[t], om, n, n, 128) ||
+        !encode_bf16_2d(reinterpret_cast<EncodeTiledFn>(fn), &g.tmB[t], bt, n,
+                        std::max(1, 3 * ninst[t]), 192))
+      return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
+  }
+  g.tiles = c->d_tiles;
+  g.num_tiles = (int)tiles.size();
+  g.type_off = c->d_type_off;
+  g.inst_off = c->d_inst_off;
+  g.inst_pad = c->d_inst_pad;
+  g.pad_off = c->d_pad_off;
+  g.h0bf16 = c->d_h0bf16;
+  g.negbeta = c->d_negbeta;
+  g.c0m = c->d_c0m;
+  g.maskbuf = c->d_maskbuf;
+  g.params = c->d_params;
+  g.status = c->d_status;
+  g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
+  int per_sm = 0;
+  e = etac::batched_front_occupancy(c->nmax, c->K, &per_sm);
+  if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "front kernel occupancy");
+  c->front_grid = per_sm * c->num_sms;
+  c->gemm_grid = std::max(1, std::min(c->num_sms, (int)tiles.size()));
+  c->bf16_ready = true;
+  return ETAC_OK;
 }
 
 etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t s) {
@@ -125,6 +259,10 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   if (need32 && !c->d_omega) {
     e = dalloc(&c->d_omega, om);
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate Omega table");
+  }
+  if (!need32) {
+    etac_status st = setup_bf16(c, s);
+    if (st != ETAC_OK) return st;
   }
   if (!c->batched_grid) {
     int per_sm = 0;
@@ -147,6 +285,7 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   a.order = c->d_order;
   a.omega = need32 ? c->d_omega : nullptr;
   a.omega_bf16 = need32 ? nullptr : c->d_omega_bf16;
+  a.h0bf16 = need32 ? nullptr : c->d_h0bf16;
   e = etac::launch_tables(a, c->nmax, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
   c->tables_ready = true;
@@ -314,8 +453,8 @@ etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float
                 "model desc: hidden must be %d; mode, precision, algo must be known values",
                 ETAC_HIDDEN);
   if (!params || !aligned(params, 4)) return fail(c, ETAC_ERR_INVALID_ARG, "params NULL/misaligned");
-  if (desc->precision == ETAC_PREC_BF16)
-    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 algorithm not built yet");
+  if (desc->precision == ETAC_PREC_BF16 && desc->algo != ETAC_ALGO_BATCHED)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 precision is implemented by the batched algorithm");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   float alpha = 0.f;
   ETAC_CUDA(c, cudaMemcpyAsync(&alpha, params, sizeof(float), cudaMemcpyDeviceToHost, s),
@@ -389,6 +528,23 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.ticket = c->d_ticket;
     b.status = c->d_status;
     ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
+    if (c->model.precision == ETAC_PREC_BF16) {
+      b.bt = c->d_bt;
+      b.bt_off = c->d_bt_off;
+      b.pad_inst = c->d_pad_inst;
+      b.negbeta = c->d_negbeta;
+      b.c0m = c->d_c0m;
+      b.maskbuf = c->d_maskbuf;
+      ETAC_CUDA(c, etac::launch_batched_front_bf16(b, std::min<int>(c->front_grid, (int)EP), s),
+                "BF16 front launch");
+      etac::GemmParams& g = c->gemm;
+      g.disp = out->disp;
+      g.use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
+      g.use_r = c->model.mode != ETAC_MODE_LINEAR_ONLY;
+      ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s), "BF16 propagation GEMM launch");
+      c->has_forward = true;
+      return ETAC_OK;
+    }
     ETAC_CUDA(c, etac::launch_batched_forward(b, std::min<int>(c->batched_grid, (int)EP), s),
               "batched forward launch");
     c->has_forward = true;

@@ -13,6 +13,8 @@
 //   3. every passive node: Omega U_a (Eq. 1, Omega from the per-type table) plus
 //      Phi_p = D2 ReLU(h0_i + beta) + b (Eq. 4).
 // The algebra equals the literal network exactly; only rounding order differs.
+#include <cuda_bf16.h>
+
 #include "etac_common.cuh"
 #include "etac_kernels.h"
 
@@ -48,6 +50,10 @@ struct BatchedSmem {
   }
 };
 
+// kBF16 = false: the whole FP32 step.  kBF16 = true: the front half of the BF16 tensor-core
+// step -- contact, encoder, pooling and global MLP -- writing the GEMM's B operand (u_hat in
+// BF16, zero on passive nodes), the contact mask and each pad's decoder record.
+template <bool kBF16>
 __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -114,6 +120,9 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
     }
     __syncthreads();
+    __nv_bfloat16* btrow = nullptr;   // BF16 variant: rows 3k..3k+2 of the B operand
+    if constexpr (kBF16)
+      btrow = reinterpret_cast<__nv_bfloat16*>(a.bt) + a.bt_off[ty] + (size_t)3 * a.pad_inst[pad] * n;
     if (sWarp[BW]) {
       if (tid == 0) latch_status(a.status, STATUS_NONFINITE);
       for (int i = tid; i < n; i += BT) {
@@ -121,8 +130,17 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         d[0] = d[1] = d[2] = 0.f;
         if (a.mask) a.mask[base + i] = 0;
         if (a.pen) a.pen[base + i] = 0.f;
+        if constexpr (kBF16) {
+          const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
+          btrow[i] = z;
+          btrow[n + i] = z;
+          btrow[2 * n + i] = z;
+          a.maskbuf[base + i] = 0;
+        }
       }
       if (tid == 0 && a.count) a.count[pad] = 0;
+      if constexpr (kBF16)
+        if (tid == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
       continue;
     }
 
@@ -151,6 +169,12 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       if (i < n) {
         sMask[i] = c.active ? 1 : 0;
         if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
+        if constexpr (kBF16) {
+          a.maskbuf[base + i] = c.active ? 1 : 0;
+          btrow[i] = __float2bfloat16_rn(c.u[0]);
+          btrow[n + i] = __float2bfloat16_rn(c.u[1]);
+          btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
+        }
         if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
         if (c.active) {
           const int slot = m + woff + __popc(bal & lt_mask);
@@ -171,6 +195,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         float* d = a.disp + 3 * (base + i);
         d[0] = d[1] = d[2] = 0.f;
       }
+      if constexpr (kBF16)
+        if (tid == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
       continue;
     }
 
@@ -262,6 +288,25 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       __syncthreads();
     }
 
+    if constexpr (kBF16) {
+      // decoder record: ReLU(h0 + beta) = max(h0, -beta) + beta, so the GEMM epilogue needs
+      // -beta (BF16) and the constant D2 beta + b_D2 of this pad
+      if (a.mode != MODE_LINEAR_ONLY && tid < H)
+        reinterpret_cast<__nv_bfloat16*>(a.negbeta)[(size_t)pad * H + tid] =
+            __float2bfloat16_rn(-sBeta[tid]);
+      if (tid == 0) {
+        float c0[3] = {0.f, 0.f, 0.f};
+        if (a.mode != MODE_LINEAR_ONLY)
+          for (int q = 0; q < 3; ++q) {
+            float acc = sB4[q];
+            for (int u = 0; u < H; ++u) acc = fmaf(sW4[q * H + u], sBeta[u], acc);
+            c0[q] = acc;
+          }
+        a.c0m[pad] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
+      }
+      continue;
+    }
+
     // ---- 3. passive nodes: Eq. 4
     const float* Om = a.omega + a.omega_off[ty];
     for (int i = tid; i < n; i += BT) {
@@ -310,10 +355,11 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 size_t batched_smem_bytes(int nmax, int K) { return BatchedSmem(nmax, K).total; }
 int batched_threads() { return BT; }
 
+template <bool kBF16>
 static cudaError_t configure(size_t smem) {
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel,
+    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel<kBF16>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
@@ -323,17 +369,33 @@ static cudaError_t configure(size_t smem) {
 
 cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
   size_t smem = batched_smem_bytes(nmax, K);
-  cudaError_t e = configure(smem);
+  cudaError_t e = configure<false>(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel, BT,
-                                                       smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
+                                                       batched_forward_kernel<false>, BT, smem);
+}
+
+cudaError_t batched_front_occupancy(int nmax, int K, int* blocks_per_sm) {
+  size_t smem = batched_smem_bytes(nmax, K);
+  cudaError_t e = configure<true>(smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel<true>,
+                                                       BT, smem);
 }
 
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s) {
   size_t smem = batched_smem_bytes(a.nmax, a.K);
-  cudaError_t e = configure(smem);
+  cudaError_t e = configure<false>(smem);
   if (e != cudaSuccess) return e;
-  batched_forward_kernel<<<grid, BT, smem, s>>>(a);
+  batched_forward_kernel<false><<<grid, BT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_batched_front_bf16(const BatchedArgs& a, int grid, cudaStream_t s) {
+  size_t smem = batched_smem_bytes(a.nmax, a.K);
+  cudaError_t e = configure<true>(smem);
+  if (e != cudaSuccess) return e;
+  batched_forward_kernel<true><<<grid, BT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

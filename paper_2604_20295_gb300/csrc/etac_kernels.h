@@ -53,6 +53,7 @@ struct TablesArgs {
   int16_t* order;               // [64 * sum n]: type t at 64*type_off[t], channel-major
   float* omega;                 // [sum n^2] FP32 (optional)
   void* omega_bf16;             // [sum n^2] BF16 (optional)
+  void* h0bf16;                 // [sum n][64] BF16 copy of h0 (optional)
 };
 cudaError_t launch_tables(const TablesArgs& a, int nmax, cudaStream_t s);
 
@@ -84,10 +85,56 @@ struct BatchedArgs {
   int* count;
   int* ticket;                  // work-queue counter, zero at launch
   int* status;
+  // BF16 tensor-core variant only: this kernel stops after the global MLP and hands the
+  // propagation + decoder to the GEMM kernel through these buffers
+  void* bt;                     // BF16 B operand, type t at bt_off[t]: [3 * I_t][n_t]
+  const long long* bt_off;      // [T]
+  const int* pad_inst;          // [E*P] instance index of each pad within its type
+  void* negbeta;                // [E*P][64] BF16, -beta of each pad
+  float4* c0m;                  // [E*P] (D2 beta + b_D2, active count as int bits)
+  uint8_t* maskbuf;             // [N] internal contact mask
 };
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_batched_front_bf16(const BatchedArgs& a, int grid, cudaStream_t s);
+cudaError_t batched_front_occupancy(int nmax, int K, int* blocks_per_sm);
 size_t batched_smem_bytes(int nmax, int K);
 int batched_threads();
 cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm);
+
+}  // namespace etac
+
+#include <cuda.h>
+
+namespace etac {
+
+// ---------------------------------------------------------------- BF16 propagation GEMM
+constexpr int GEMM_MAX_TYPES = 16;
+
+struct GemmTile {
+  int type, m0, k0, nkb;   // pad type, first node row, first instance, K blocks of 64 nodes
+};
+
+struct GemmParams {
+  CUtensorMap tmA[GEMM_MAX_TYPES];   // Omega_t BF16 [n_t][n_t], box 64 x 128, 128B swizzle
+  CUtensorMap tmB[GEMM_MAX_TYPES];   // B_t BF16 [3 I_t][n_t], box 64 x 192, 128B swizzle
+  const GemmTile* tiles;
+  int num_tiles;
+  const int* type_off;               // [T+1]
+  const int* inst_off;               // [T+1]
+  const int* inst_pad;               // [sum I_t] pad index of instance k of type t
+  const long long* pad_off;
+  const void* h0bf16;                // [sum n][64]
+  const void* negbeta;               // [E*P][64]
+  const float4* c0m;                 // [E*P]
+  const uint8_t* maskbuf;            // [N]
+  const float* params;
+  float* disp;
+  int use_l, use_r;
+  int* status;
+  unsigned long long timeout_ns;
+};
+
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s);
+size_t prop_gemm_smem_bytes();
 
 }  // namespace etac

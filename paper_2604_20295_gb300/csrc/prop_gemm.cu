@@ -1,0 +1,386 @@
+// prop_gemm.cu -- BF16 tensor-core propagation of the batched ETac step (tcgen05 + TMA + TMEM),
+// with the residual decoder and Eq. 4 fused into the epilogue.
+//
+// Eq. 1 sums exp(-alpha |p_j - p_i|) u_hat_j over active nodes j; passive nodes carry
+// u_hat = 0 (the same zero padding the residual network uses, Sec. III-A 2), so for all
+// instances k of one pad type t the propagation is the dense contraction
+//     L_t[i, (k, c)] = sum_j Omega_t[i, j] * Uhat[k, j, c],
+// one GEMM with M = nodes i, K = nodes j, N = 3 x instances.  Omega_t is shared by every
+// instance of the type and L2-resident; the B operand (u_hat in BF16) is written by the front
+// kernel.  Accumulation is FP32 in tensor memory.
+//
+// Per CTA (persistent, one per SM): warp 8 issues TMA loads into a 4-stage shared-memory
+// ring, warp 9 issues tcgen05.mma (M = 128, N = 192, K = 16) into one of two TMEM
+// accumulators, warps 0-7 drain the other accumulator.  The epilogue evaluates, for every
+// passive node i and instance k, the decoder residual
+//     Phi = D2 ReLU(h0_i + beta_k) + b = D2 max(h0_i, -beta_k) + (D2 beta_k + b)
+// with a warp-level BF16 MMA (m16n8k16) per instance, adds the propagated term and stores
+// the displacement (Eq. 4).  Every wait is bounded; a timeout latches ETAC_ERR_TIMEOUT and
+// the CTA winds down (waiting, bounded, for its in-flight copies and MMAs before freeing TMEM).
+#include <cuda_bf16.h>
+
+#include "etac_common.cuh"
+#include "etac_kernels.h"
+#include "sm100_ptx.cuh"
+
+namespace etac {
+using namespace sm100;
+
+namespace {
+
+constexpr int GM = 128;                 // node rows per tile
+constexpr int GI = 64;                  // instances per tile
+constexpr int GN = 3 * GI;              // 192 accumulator columns
+constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
+constexpr int STAGES = 4;
+constexpr int EPI_WARPS = 8;
+constexpr int TMA_WARP = 8, MMA_WARP = 9;
+constexpr int THREADS = 10 * 32;
+constexpr int A_BYTES = GM * GK * 2;    // 16 KiB
+constexpr int B_BYTES = GN * GK * 2;    // 24 KiB
+constexpr uint32_t TMEM_COLS = 512;
+constexpr uint32_t ACC_STRIDE = 256;    // column offset of accumulator 1
+constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
+
+// shared-memory layout (offsets from a 1024-byte aligned base)
+constexpr size_t SM_A = 0;
+constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
+constexpr size_t SM_Z = SM_B + (size_t)STAGES * B_BYTES;          // 8 x 32 rows x 128 B
+constexpr size_t SM_R = SM_Z + (size_t)EPI_WARPS * 32 * 128;      // 8 x 32 x float4
+constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 32 * 16;      // 64 x 64 BF16
+constexpr size_t SM_C0 = SM_NB + (size_t)GI * H * 2;              // 64 x float4
+constexpr size_t SM_BASE = SM_C0 + (size_t)GI * 16;               // 64 x int64
+constexpr size_t SM_BAR = SM_BASE + (size_t)GI * 8;               // barriers
+constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
+constexpr size_t SM_TOTAL = SM_MISC + 16;
+constexpr size_t SM_ALLOC = SM_TOTAL + 1024;                      // alignment slack
+
+__device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_constant__ GemmParams p) {
+  extern __shared__ unsigned char smem_raw[];
+  unsigned char* smem = reinterpret_cast<unsigned char*>(
+      (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + SM_BAR);
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* drain = acc_empty + 2;
+  uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + SM_MISC);
+  volatile int* s_abort = reinterpret_cast<volatile int*>(smem + SM_MISC + 4);
+  volatile int* s_never = reinterpret_cast<volatile int*>(smem + SM_MISC + 8);      // stays 0
+  volatile int* s_epi_stop = reinterpret_cast<volatile int*>(smem + SM_MISC + 12);  // epilogue
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(&full[s], 1);
+      mbar_init(&empty[s], 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(&acc_full[b], 1);
+      mbar_init(&acc_empty[b], EPI_WARPS);
+    }
+    mbar_init(drain, 1);
+    *s_abort = 0;
+    *s_never = 0;
+    *s_epi_stop = 0;
+    fence_mbar_init();
+  }
+  if (warp == TMA_WARP && lane == 0) {
+    for (int t = 0; t < GEMM_MAX_TYPES; ++t) {
+      prefetch_tmap(&p.tmA[t]);
+      prefetch_tmap(&p.tmB[t]);
+    }
+  }
+  if (warp == MMA_WARP) {
+    tmem_alloc(s_tmem, TMEM_COLS);
+    tmem_relinquish();
+  }
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *s_tmem;
+  const uint64_t limit = p.timeout_ns;
+
+  if (warp == TMA_WARP) {
+    // ---------------------------------------------------------------- producer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int issued = 0;
+      for (int tile = blockIdx.x; tile < p.num_tiles && !*s_abort; tile += gridDim.x) {
+        const GemmTile T = p.tiles[tile];
+        for (int kb = 0; kb < T.nkb; ++kb) {
+          if (!mbar_wait(&empty[stage], phase ^ 1u, s_abort, limit)) {
+            *s_abort = 1;
+            break;
+          }
+          mbar_expect_tx(&full[stage], A_BYTES + B_BYTES);
+          tma_load_2d(smem + SM_A + (size_t)stage * A_BYTES, &p.tmA[T.type], kb * GK, T.m0,
+                      &full[stage]);
+          tma_load_2d(smem + SM_B + (size_t)stage * B_BYTES, &p.tmB[T.type], kb * GK, 3 * T.k0,
+                      &full[stage]);
+          ++issued;
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+      }
+      if (*s_abort) {
+        // let the copies already issued land before shared memory goes away
+        int st = stage;
+        uint32_t ph = phase;
+        for (int q = 0; q < STAGES && q < issued; ++q) {
+          if (--st < 0) {
+            st = STAGES - 1;
+            ph ^= 1u;
+          }
+          mbar_wait(&full[st], ph, s_never, limit);
+        }
+      }
+    }
+  } else if (warp == MMA_WARP) {
+    // ---------------------------------------------------------------- MMA issuer
+    if (lane == 0) {
+      int stage = 0;
+      uint32_t phase = 0;
+      int local = 0;
+      bool any = false;
+      for (int tile = blockIdx.x; tile < p.num_tiles && !*s_abort; tile += gridDim.x, ++local) {
+        const GemmTile T = p.tiles[tile];
+        const int b = local & 1;
+        const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
+        if (!mbar_wait(&acc_empty[b], acc_phase ^ 1u, s_abort, limit)) {
+          *s_abort = 1;
+          break;
+        }
+        tc_fence_after();
+        const uint32_t d_tmem = tmem + (uint32_t)b * ACC_STRIDE;
+        bool ok = true;
+        for (int kb = 0; kb < T.nkb; ++kb) {
+          if (!mbar_wait(&full[stage], phase, s_abort, limit)) {
+            ok = false;
+            break;
+          }
+          tc_fence_after();
+          const uint32_t a_base = smem_u32(smem + SM_A + (size_t)stage * A_BYTES);
+          const uint32_t b_base = smem_u32(smem + SM_B + (size_t)stage * B_BYTES);
+#pragma unroll
+          for (int k = 0; k < GK / 16; ++k) {
+            tc_mma_bf16(d_tmem, smem_desc_sw128(a_base + 32u * k), smem_desc_sw128(b_base + 32u * k),
+                        IDESC, (kb | k) != 0 ? 1u : 0u);
+          }
+          any = true;
+          tc_commit(&empty[stage]);
+          if (++stage == STAGES) {
+            stage = 0;
+            phase ^= 1u;
+          }
+        }
+        if (!ok) {
+          *s_abort = 1;
+          break;
+        }
+        tc_commit(&acc_full[b]);
+      }
+      if (any) {
+        // every MMA issued by this thread has completed once the drain barrier flips
+        tc_commit(drain);
+        mbar_wait(drain, 0u, s_never, limit);
+      }
+    }
+  } else {
+    // ---------------------------------------------------------------- epilogue (warps 0-7)
+    const int q = warp & 3, half = warp >> 2, etid = threadIdx.x;   // etid in [0, 256)
+    const int grp = lane >> 2, tig = lane & 3;
+    unsigned char* zbuf = smem + SM_Z + (size_t)warp * 32 * 128;
+    float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * 32 * 16);
+    __nv_bfloat16* s_nb = reinterpret_cast<__nv_bfloat16*>(smem + SM_NB);
+    float4* s_c0 = reinterpret_cast<float4*>(smem + SM_C0);
+    long long* s_base = reinterpret_cast<long long*>(smem + SM_BASE);
+    const float* W4 = p.params + OFF_W4;
+    // decoder weights as constant B fragments: B[k = hidden][n = output component]
+    uint32_t bw[4][2];
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      const int k0 = 16 * s + 2 * tig;
+      const bool live = grp < 3;
+      bw[s][0] = live ? pack_bf16x2(W4[grp * H + k0], W4[grp * H + k0 + 1]) : 0u;
+      bw[s][1] = live ? pack_bf16x2(W4[grp * H + k0 + 8], W4[grp * H + k0 + 9]) : 0u;
+    }
+    int local = 0;
+    for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++local) {
+      const GemmTile T = p.tiles[tile];
+      const int b = local & 1;
+      const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
+      const int t = T.type;
+      const int n_t = p.type_off[t + 1] - p.type_off[t];
+      const int ninst = p.inst_off[t + 1] - p.inst_off[t];
+      // per-instance records of this tile
+      named_bar_sync(1, EPI_WARPS * 32);
+      for (int idx = etid; idx < GI * 8; idx += EPI_WARPS * 32) {
+        const int inst = idx >> 3, chunk = idx & 7;
+        const int k = T.k0 + inst;
+        uint4 v = make_uint4(0u, 0u, 0u, 0u);
+        if (k < ninst) {
+          const int pad = p.inst_pad[p.inst_off[t] + k];
+          v = reinterpret_cast<const uint4*>(p.negbeta)[(size_t)pad * 8 + chunk];
+          if (chunk == 0) {
+            s_c0[inst] = p.c0m[pad];
+            s_base[inst] = p.pad_off[pad];
+          }
+        } else if (chunk == 0) {
+          s_c0[inst] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+          s_base[inst] = 0;
+        }
+        reinterpret_cast<uint4*>(s_nb)[inst * 8 + chunk] = v;
+      }
+      named_bar_sync(1, EPI_WARPS * 32);
+      const int i = T.m0 + 32 * q + lane;   // my node row within the pad type
+      const bool row_ok = i < n_t;
+      uint32_t h0[32];
+      {
+        const uint4* src = reinterpret_cast<const uint4*>(p.h0bf16) +
+                           (size_t)(p.type_off[t] + (row_ok ? i : 0)) * 8;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const uint4 v = row_ok ? src[c] : make_uint4(0u, 0u, 0u, 0u);
+          h0[4 * c + 0] = v.x;
+          h0[4 * c + 1] = v.y;
+          h0[4 * c + 2] = v.z;
+          h0[4 * c + 3] = v.w;
+        }
+      }
+      if (!mbar_wait(&acc_full[b], acc_phase, s_abort, limit)) {
+        *s_abort = 1;
+        *s_epi_stop = 1;
+      }
+      // every epilogue warp takes the same decision (the flag is only written before here)
+      named_bar_sync(2, EPI_WARPS * 32);
+      if (*s_epi_stop) break;
+      tc_fence_after();
+      const uint32_t tbase = tmem + (uint32_t)b * ACC_STRIDE + ((uint32_t)(32 * q) << 16);
+#pragma unroll 1
+      for (int g = 0; g < 4; ++g) {
+        const int inst0 = 32 * half + 8 * g;
+        uint32_t lv[24];
+        {
+          uint32_t r8[8];
+          tc_ld_32x32b_x8(tbase + 3u * inst0, r8);
+#pragma unroll
+          for (int x = 0; x < 8; ++x) lv[x] = r8[x];
+          tc_ld_32x32b_x8(tbase + 3u * inst0 + 8u, r8);
+#pragma unroll
+          for (int x = 0; x < 8; ++x) lv[8 + x] = r8[x];
+          tc_ld_32x32b_x8(tbase + 3u * inst0 + 16u, r8);
+#pragma unroll
+          for (int x = 0; x < 8; ++x) lv[16 + x] = r8[x];
+          tc_wait_ld();
+        }
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          const int inst = inst0 + j;
+          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+          if (p.use_r) {
+            // Z row = max(h0_i, -beta_k), 128-byte row, 16-byte chunks XOR-swizzled by row
+            const uint4* nb = reinterpret_cast<const uint4*>(s_nb + inst * H);
+#pragma unroll
+            for (int c = 0; c < 8; ++c) {
+              const uint4 v = nb[c];
+              uint4 z;
+              z.x = bf16x2_max(h0[4 * c + 0], v.x);
+              z.y = bf16x2_max(h0[4 * c + 1], v.y);
+              z.z = bf16x2_max(h0[4 * c + 2], v.z);
+              z.w = bf16x2_max(h0[4 * c + 3], v.w);
+              *reinterpret_cast<uint4*>(zbuf + lane * 128 + ((c ^ (lane & 7)) << 4)) = z;
+            }
+            __syncwarp();
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg) {
+              float acc[4] = {0.f, 0.f, 0.f, 0.f};
+              const int mi = lane >> 3;
+              const int row = rg * 16 + (lane & 7) + (mi & 1) * 8;
+#pragma unroll
+              for (int s = 0; s < 4; ++s) {
+                const int chunk = 2 * s + (mi >> 1);
+                uint32_t a[4];
+                ldmatrix_x4(smem_u32(zbuf + row * 128 + ((chunk ^ (row & 7)) << 4)), a[0], a[1],
+                            a[2], a[3]);
+                mma_bf16_16816(acc, a, bw[s][0], bw[s][1], acc);
+              }
+              float* rb = reinterpret_cast<float*>(rbuf);
+              const int r0 = rg * 16 + grp;
+              if (tig == 0) {
+                rb[r0 * 4 + 0] = acc[0];
+                rb[r0 * 4 + 1] = acc[1];
+                rb[(r0 + 8) * 4 + 0] = acc[2];
+                rb[(r0 + 8) * 4 + 1] = acc[3];
+              } else if (tig == 1) {
+                rb[r0 * 4 + 2] = acc[0];
+                rb[(r0 + 8) * 4 + 2] = acc[2];
+              }
+            }
+            __syncwarp();
+            r = rbuf[lane];
+            __syncwarp();
+          }
+          const float4 cm = s_c0[inst];
+          if (row_ok && __float_as_int(cm.w) > 0) {
+            const long long node = s_base[inst] + i;
+            if (!p.maskbuf[node]) {
+              float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+              if (p.use_l) {
+                u0 = __uint_as_float(lv[3 * j + 0]);
+                u1 = __uint_as_float(lv[3 * j + 1]);
+                u2 = __uint_as_float(lv[3 * j + 2]);
+              }
+              if (p.use_r) {
+                u0 += r.x + cm.x;
+                u1 += r.y + cm.y;
+                u2 += r.z + cm.z;
+              }
+              float* d = p.disp + 3 * node;
+              d[0] = u0;
+              d[1] = u1;
+              d[2] = u2;
+            }
+          }
+        }
+      }
+      tc_fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&acc_empty[b]);
+    }
+  }
+
+  __syncthreads();
+  if (*s_abort && threadIdx.x == 0) latch_status(p.status, STATUS_TIMEOUT);
+  if (warp == MMA_WARP) {
+    tc_fence_after();
+    tmem_dealloc(tmem, TMEM_COLS);
+  }
+}
+
+}  // namespace
+
+size_t prop_gemm_smem_bytes() { return SM_ALLOC; }
+
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s) {
+  static bool configured = false;
+  if (!configured) {
+    cudaError_t e = cudaFuncSetAttribute(prop_gemm_kernel,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)SM_ALLOC);
+    if (e != cudaSuccess) return e;
+    configured = true;
+  }
+  prop_gemm_kernel<<<grid, THREADS, SM_ALLOC, s>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace etac

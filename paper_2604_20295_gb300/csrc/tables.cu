@@ -48,6 +48,7 @@ __global__ void __launch_bounds__(128) tables_node_kernel(TablesArgs a) {
 #pragma unroll
     for (int k = 0; k < H; ++k) acc = fmaf(W[OFF_WD + c * 2 * H + k], f[k], acc);
     a.h0tab[(size_t)i * H + c] = acc;
+    if (a.h0bf16) reinterpret_cast<__nv_bfloat16*>(a.h0bf16)[(size_t)i * H + c] = __float2bfloat16_rn(acc);
   }
 }
 

@@ -246,4 +246,5 @@ class TactileSim:
 
 
 # (algo, precision, relative tolerance) exercised by the smoke check
-SMOKE_CONFIGS = ((ALGO_PLAIN, PREC_FP32, 1e-5), (ALGO_BATCHED, PREC_FP32, 1e-5))
+SMOKE_CONFIGS = ((ALGO_PLAIN, PREC_FP32, 1e-5), (ALGO_BATCHED, PREC_FP32, 1e-5),
+                 (ALGO_BATCHED, PREC_BF16, 2e-2))
