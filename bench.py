@@ -161,20 +161,40 @@ def workload_config(args, scene):
             "scene_seed": args.seed}
 
 
+def timed_steps(sim, steps, stream, flush, torch, step_kw):
+    """K steps, L2 flushed between them outside the events; returns per-step ms."""
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    for k in range(steps):
+        flush.fill_(k & 0xFF)
+        starts[k].record(stream)
+        sim.step(**step_kw)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    return [a.elapsed_time(b) for a, b in zip(starts, ends)]
+
+
+def executed_gemm_flops(scene):
+    """Dense FLOPs the tensor-core propagation executes: 2 n_t^2 * 3 per instance."""
+    n = scene.pad_nodes.astype(np.float64)
+    return float((2.0 * n * n * 3.0).sum())
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--algo", default="plain", choices=["plain", "batched"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16"])
+    ap.add_argument("--algo", default="batched", choices=["plain", "batched"])
+    ap.add_argument("--precision", default="bf16", choices=["fp32", "bf16"])
     ap.add_argument("--envs", type=int, default=4096)
     ap.add_argument("--seed", type=int, default=2)
     ap.add_argument("--ref-envs", type=int, default=96)
-    ap.add_argument("--cpu-envs", type=int, default=256)
+    ap.add_argument("--cpu-envs", type=int, default=2048)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-compare", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -205,34 +225,27 @@ def main():
     sim.set_model(theta, X.MODE_FULL, prec, algo)
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    step_kw = dict(want_mask=False, want_pen=False, want_count=True)
 
-    def one_step():
-        sim.step(want_mask=False, want_pen=False, want_count=True)
-
+    clocks = Clocks(local)
+    clocks.start()    # sampled from before warm-up until after the timed region
     for _ in range(args.warmup):
-        one_step()
+        sim.step(**step_kw)
     torch.cuda.synchronize()
     counts = sim.count.cpu().numpy()
     work = algorithmic_work(scene, counts)
 
-    # ---- device-timed region: K steps, L2 flushed between steps (outside the events)
-    clocks = Clocks(local)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # ---- device-timed region: K steps, per-kernel events on the launching stream
+    X.etac_enable_timing(sim.ctx, True)
     if pg:
         pg.barrier()
     torch.cuda.synchronize()
-    clocks.start()
-    for k in range(args.steps):
-        flush.fill_(k & 0xFF)
-        starts[k].record(stream)
-        one_step()
-        ends[k].record(stream)
-    torch.cuda.synchronize()
+    step_ms = timed_steps(sim, args.steps, stream, flush, torch, step_kw)
     if pg:
         pg.barrier()
     clk = clocks.stop()
-    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ktimes = X.etac_kernel_times(sim.ctx)
+    X.etac_enable_timing(sim.ctx, False)
     total_s = sum(step_ms) / 1e3
     if pg:
         t = torch.tensor([total_s], device=dev, dtype=torch.float64)
@@ -261,7 +274,7 @@ def main():
         for _ in range(ke):
             for d, h in zip(d_in, h_in):
                 d.copy_(h, non_blocking=True)
-            one_step()
+            sim.step(**step_kw)
             h_out.copy_(sim.disp, non_blocking=True)
         e1.record(stream)
         torch.cuda.synchronize()
@@ -273,39 +286,100 @@ def main():
         e2e = {"value": nodes * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke}
 
+    # ---- the other rungs on the same GPU and scene (the metric compares BF16 batched with
+    # FP32 plain; FP32 batched is the intermediate rung)
+    compare = {}
+    if not args.no_compare:
+        for name, a2, p2, k2 in (("fp32_plain", X.ALGO_PLAIN, X.PREC_FP32, 3),
+                                 ("fp32_batched", X.ALGO_BATCHED, X.PREC_FP32, 5),
+                                 ("bf16_batched", X.ALGO_BATCHED, X.PREC_BF16, 5)):
+            if (a2, p2) == (algo, prec):
+                continue
+            s2 = X.TactileSim(scene, device=dev)
+            s2.set_model(theta, X.MODE_FULL, p2, a2)
+            for _ in range(2):
+                s2.step(**step_kw)
+            ms = timed_steps(s2, k2, stream, flush, torch, step_kw)
+            compare[name] = {"value": nodes * 1e3 / (sum(ms) / k2), "unit": UNIT,
+                             "ms_per_step": sum(ms) / k2, "steps": k2}
+            s2.close()
+        compare[f"{args.precision}_{args.algo}"] = {"value": value, "unit": UNIT,
+                                                    "ms_per_step": ms_per_step}
+
     peaks, peak_src = _peaks()
-    sm_clock = (clk or {}).get("sm_mhz") or peaks.get("sm_max_mhz", 2070.0)
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    kern = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1)} for k, v in ktimes.items()}
     if args.algo == "plain":
-        # literal FP32 network + Eq. 1 contraction on CUDA cores: ALU bound
+        name = "plain_forward_kernel<float>"
         fma_peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-        achieved = work["literal_flops"] / (total_s / args.steps) / 1e12
+        t_launch = kern[name]["ms_per_launch"] / 1e3
+        achieved = work["literal_flops"] / t_launch / 1e12
         roof = {"bound": "alu", "achieved": achieved, "peak": fma_peak, "unit": "TFLOP/s",
-                "frac": achieved / fma_peak, "traffic": None,
-                "kernel": "plain_forward_kernel<float>",
-                "peak_source": f"{nsm} SMs x 128 FP32 lanes x 2 x {peaks.get('sm_max_mhz', 2070.0)}"
-                               " MHz (derived)"}
-    else:
-        achieved = work["bytes_out"] / (total_s / args.steps) / 1e9
+                "frac": achieved / fma_peak, "traffic": None, "kernel": name,
+                "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x "
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}
+    elif args.precision == "fp32":
+        name = "batched_forward_kernel<fp32>"
+        t_launch = kern[name]["ms_per_launch"] / 1e3
+        achieved = work["bytes_out"] / t_launch / 1e9
         roof = {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-                "frac": achieved / peaks["hbm_gbs"], "traffic": None,
-                "peak_source": peak_src}
+                "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": name,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)"}
+    else:
+        name = "prop_gemm_kernel"
+        t_launch = kern[name]["ms_per_launch"] / 1e3
+        alg = 6.0 * work["pairs"] + 2.0 * 3 * H * work["passive"]
+        exe = executed_gemm_flops(scene)
+        peak = peaks["bf16_tflops"]
+        achieved = alg / t_launch / 1e12
+        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": name,
+                "executed_dense_tflops": exe / t_launch / 1e12,
+                "executed_frac": exe / t_launch / 1e12 / peak,
+                "peak_source": f"{peak_src} bf16_tflops (burst)",
+                "note": "achieved counts the Eq. 1 contraction over (passive, active) pairs and "
+                        "the decoder output layer; the kernel executes the dense per-type "
+                        "contraction (executed_dense_tflops)"}
 
     cpu = None
+    err = None
     if not args.no_cpu and rank == 0:
-        envs = np.random.default_rng(7).choice(scene.num_envs, min(args.cpu_envs, scene.num_envs),
-                                               replace=False)
-        rate, dt, nn = oracle_rate(scene, theta, envs)
-        cpu = {"value": rate, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
-               "sample": f"{len(envs)} random envs ({nn} nodes) of the workload, one forward, "
-                         f"FP64 C oracle, OpenMP over pads, {dt:.1f} s"}
+        envs = np.sort(np.random.default_rng(7).choice(scene.num_envs,
+                                                       min(args.cpu_envs, scene.num_envs),
+                                                       replace=False))
+        import oracle
+        sub = scene.subset(envs)
+        t0 = time.perf_counter()
+        ref = oracle.forward(sub, theta)
+        dt = time.perf_counter() - t0
+        cpu = {"value": sub.total_nodes / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
+               "sample": f"{len(envs)} random envs ({sub.total_nodes} nodes) of the workload, one "
+                         f"forward step, FP64 C oracle, OpenMP over pads, {dt:.1f} s"}
+        # stated error of this run's output on the same envs (mask-matched pads)
+        sim.step(want_mask=True, want_pen=False, want_count=True)
+        torch.cuda.synchronize()
+        offs = scene.node_offsets
+        idx = np.concatenate([np.arange(offs[e * 6], offs[e * 6 + 6]) for e in envs])
+        got = sim.disp.cpu().numpy()[idx].astype(np.float64)
+        gm = sim.mask.cpu().numpy()[idx]
+        same = gm == ref["mask"]
+        d = np.linalg.norm(got - ref["disp"], axis=1)
+        so = sub.node_offsets
+        pad_err = np.maximum.reduceat(d, so[:-1])
+        pad_scale = np.maximum.reduceat(np.linalg.norm(ref["disp"], axis=1), so[:-1])
+        err = {"max_abs_mm": float(d.max()), "rms_mm": float(np.sqrt((d ** 2).mean())),
+               "max_pad_rel": float((pad_err / np.maximum(pad_scale, 1e-30)).max()),
+               "mask_mismatch_nodes": int((~same).sum()), "envs": len(envs)}
 
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "bf16" if prec else "f32",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": "bf16" if prec == X.PREC_BF16 else "f32",
             "data": "synthetic", "config": workload_config(args, scene), "roofline": roof,
-            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": args.steps * LAUNCHES[args.algo],
-            "clocks": clk, "active_fraction": work["active"] / nodes,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+            "clocks": clk, "error_vs_oracle": err, "rungs": compare, "kernels": kern,
+            "active_fraction": work["active"] / nodes,
             "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -313,9 +387,6 @@ def main():
     if pg:
         pg.destroy_process_group()
 
-
-# kernels of ours launched per step
-LAUNCHES = {"plain": 1, "batched": 1}
 
 if __name__ == "__main__":
     main()

@@ -149,6 +149,21 @@ etac_status etac_step_backward(etac_ctx* ctx, const float* grad_disp, float* gra
  * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE. */
 etac_status etac_poll_status(etac_ctx* ctx, int32_t* device_status, void* stream);
 
+/* ---- Per-kernel timing (profiling aid; the paper has no counterpart).
+ * When enabled, every later step records a CUDA event pair on its stream around each kernel
+ * it launches (at most ETAC_TIMING_SLOTS launches are kept until read).  etac_kernel_times
+ * synchronises the device, writes up to `max` entries (kernel name, launches, summed
+ * milliseconds) and clears the record.  Enabling creates events (do it outside any stream
+ * capture); timing adds event records to captured graphs. */
+#define ETAC_TIMING_SLOTS 4096
+typedef struct {
+  char name[48];
+  int32_t launches;
+  float total_ms;
+} etac_kernel_time;
+etac_status etac_enable_timing(etac_ctx* ctx, int32_t enable);
+etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max, int32_t* count);
+
 /* FP64 evaluation of the plain algorithm, for finite-difference gradient checks only.
  * Device arrays as in etac_step_in but double; params [etac_param_count] double; writes
  * disp [N*3] double.  Uses the context's pads and the mode of `desc`. */

@@ -70,7 +70,30 @@ struct etac_ctx {
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
   bool bf16_ready = false;
+  // profiling: event pairs around kernel launches
+  bool timing = false;
+  std::vector<cudaEvent_t> ev;       // 2 * ETAC_TIMING_SLOTS
+  std::vector<int> ev_kernel;        // kernel id per used slot
+  int ev_used = 0;
 };
+
+namespace {
+const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
+                              "batched_forward_kernel<bf16 front>", "prop_gemm_kernel"};
+enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_COUNT = 4 };
+
+// records the start event of a timed launch; returns the slot or -1
+int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
+  if (!c->timing || c->ev_used >= ETAC_TIMING_SLOTS) return -1;
+  const int slot = c->ev_used++;
+  c->ev_kernel[slot] = kernel;
+  cudaEventRecord(c->ev[2 * slot], s);
+  return slot;
+}
+void timing_end(etac_ctx* c, int slot, cudaStream_t s) {
+  if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+}
+}  // namespace
 
 namespace {
 
@@ -107,6 +130,8 @@ cudaError_t dalloc(X** p, size_t count) {
 
 void free_ctx(etac_ctx* c) {
   if (!c) return;
+  for (cudaEvent_t e : c->ev)
+    if (e) cudaEventDestroy(e);
   void* ptrs[] = {c->d_type_pos, c->d_type_nrm, c->d_type_pmax, c->d_type_off, c->d_pad_type,
                   c->d_pad_off, c->d_status, c->d_params, c->d_saved_obj_type,
                   c->d_saved_obj_dims, c->d_saved_obj_pose, c->d_saved_pad_pose,
@@ -535,18 +560,24 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       b.negbeta = c->d_negbeta;
       b.c0m = c->d_c0m;
       b.maskbuf = c->d_maskbuf;
+      int ts = timing_begin(c, K_FRONT, s);
       ETAC_CUDA(c, etac::launch_batched_front_bf16(b, std::min<int>(c->front_grid, (int)EP), s),
                 "BF16 front launch");
+      timing_end(c, ts, s);
       etac::GemmParams& g = c->gemm;
       g.disp = out->disp;
       g.use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
       g.use_r = c->model.mode != ETAC_MODE_LINEAR_ONLY;
+      ts = timing_begin(c, K_GEMM, s);
       ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s), "BF16 propagation GEMM launch");
+      timing_end(c, ts, s);
       c->has_forward = true;
       return ETAC_OK;
     }
+    const int ts = timing_begin(c, K_BATCHED, s);
     ETAC_CUDA(c, etac::launch_batched_forward(b, std::min<int>(c->batched_grid, (int)EP), s),
               "batched forward launch");
+    timing_end(c, ts, s);
     c->has_forward = true;
     return ETAC_OK;
   }
@@ -571,7 +602,9 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
   a.pen = out->penetration;
   a.count = out->active_count;
   a.status = c->d_status;
+  const int ts = timing_begin(c, K_PLAIN, s);
   ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
+  timing_end(c, ts, s);
   c->has_forward = true;
   return ETAC_OK;
 }
@@ -631,6 +664,45 @@ etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int
   ETAC_CUDA(c, etac::launch_plain_forward<double>(a, c->E * c->P,
                                                   reinterpret_cast<cudaStream_t>(stream)),
             "fp64 forward launch");
+  return ETAC_OK;
+}
+
+etac_status etac_enable_timing(etac_ctx* c, int32_t enable) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (enable && c->ev.empty()) {
+    c->ev.assign(2 * ETAC_TIMING_SLOTS, nullptr);
+    c->ev_kernel.assign(ETAC_TIMING_SLOTS, 0);
+    for (auto& e : c->ev) ETAC_CUDA(c, cudaEventCreate(&e), "create timing events");
+  }
+  c->timing = enable != 0;
+  c->ev_used = 0;
+  return ETAC_OK;
+}
+
+etac_status etac_kernel_times(etac_ctx* c, etac_kernel_time* out, int32_t max, int32_t* count) {
+  if (!c || !count || (max > 0 && !out)) return fail(c, ETAC_ERR_INVALID_ARG, "NULL argument");
+  ETAC_CUDA(c, cudaDeviceSynchronize(), "synchronise for timing");
+  int launches[K_COUNT] = {0};
+  double total[K_COUNT] = {0};
+  for (int i = 0; i < c->ev_used; ++i) {
+    float ms = 0.f;
+    ETAC_CUDA(c, cudaEventElapsedTime(&ms, c->ev[2 * i], c->ev[2 * i + 1]), "event time");
+    launches[c->ev_kernel[i]] += 1;
+    total[c->ev_kernel[i]] += ms;
+  }
+  int n = 0;
+  for (int k = 0; k < K_COUNT; ++k) {
+    if (!launches[k]) continue;
+    if (n < max) {
+      memset(&out[n], 0, sizeof(out[n]));
+      snprintf(out[n].name, sizeof(out[n].name), "%s", kKernelNames[k]);
+      out[n].launches = launches[k];
+      out[n].total_ms = (float)total[k];
+    }
+    ++n;
+  }
+  *count = n < max ? n : max;
+  c->ev_used = 0;
   return ETAC_OK;
 }
 

@@ -26,7 +26,8 @@ HIDDEN = 64
 
 EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
            "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
-           "etac_last_error", "etac_destroy", "etac_step_forward_noalloc")
+           "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
+           "etac_enable_timing", "etac_kernel_times")
 
 _vp = ctypes.c_void_p
 
@@ -56,6 +57,11 @@ class etac_noalloc_pads(ctypes.Structure):
                 ("type_pos", _vp), ("type_nrm", _vp), ("num_envs", ctypes.c_int32),
                 ("pads_per_env", ctypes.c_int32), ("max_objects", ctypes.c_int32),
                 ("pad_type", _vp), ("pad_off", _vp)]
+
+
+class etac_kernel_time(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int32),
+                ("total_ms", ctypes.c_float)]
 
 
 class EtacError(RuntimeError):
@@ -96,6 +102,10 @@ def lib():
         L.etac_last_error.argtypes = [_vp]
         L.etac_destroy.restype = None
         L.etac_destroy.argtypes = [_vp]
+        L.etac_enable_timing.restype = ctypes.c_int
+        L.etac_enable_timing.argtypes = [_vp, ctypes.c_int32]
+        L.etac_kernel_times.restype = ctypes.c_int
+        L.etac_kernel_times.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
         L.etac_step_forward_noalloc.restype = ctypes.c_int
         L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
         _lib = L
@@ -162,6 +172,20 @@ def etac_last_error(ctx: int = 0) -> str:
 def etac_destroy(ctx: int) -> None:
     if ctx:
         lib().etac_destroy(ctx)
+
+
+def etac_enable_timing(ctx: int, enable: bool = True) -> None:
+    _check(ctx, lib().etac_enable_timing(ctx, int(bool(enable))), "etac_enable_timing")
+
+
+def etac_kernel_times(ctx: int) -> dict:
+    """{kernel name: (launches, summed ms)} since timing was enabled or last read."""
+    buf = (etac_kernel_time * 16)()
+    n = ctypes.c_int32(0)
+    _check(ctx, lib().etac_kernel_times(ctx, ctypes.addressof(buf), 16, ctypes.byref(n)),
+           "etac_kernel_times")
+    return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
+            for i in range(n.value)}
 
 
 def etac_step_forward_noalloc(pads: etac_noalloc_pads, mode: int, params: int,
