@@ -33,8 +33,9 @@ def check_bf16(scene, theta, mode=X.MODE_FULL):
     rel = errs / np.maximum(scale, 1e-30)
     assert np.all(errs <= BF16_REL * scale + 1e-6), f"worst pad rel err {rel.max():.3e}"
     act = got["mask"] > 0
-    # active nodes keep u_hat computed in FP32 (not BF16)
-    np.testing.assert_allclose(got["disp"][act], ref["disp"][act], rtol=1e-5, atol=1e-7)
+    # active nodes keep u_hat computed in FP32 (not BF16): per-node normwise FP32 accuracy
+    du = np.linalg.norm(got["disp"][act] - ref["disp"][act], axis=1)
+    assert np.all(du <= 1e-5 * np.linalg.norm(ref["disp"][act], axis=1) + 1e-7), du.max()
     d = np.linalg.norm(got["disp"] - ref["disp"], axis=1)
     print(f"BF16 {scene.name} mode {mode}: max err {d.max():.3e} mm, rms {np.sqrt((d**2).mean()):.3e}"
           f" mm, worst pad rel {rel.max():.3e}")
