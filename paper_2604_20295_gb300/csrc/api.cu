@@ -65,7 +65,8 @@ struct etac_ctx {
   int* d_inst_pad = nullptr;
   void* d_negbeta = nullptr;
   float4* d_c0m = nullptr;
-  uint8_t* d_maskbuf = nullptr;
+  uint32_t* d_maskbits = nullptr;
+  long long* d_mask_woff = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
@@ -138,7 +139,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_omega_off, c->d_item_pad, c->d_ticket, c->d_ctab, c->d_f0tab,
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
-                  c->d_c0m, c->d_maskbuf, c->d_tiles};
+                  c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -188,18 +189,22 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
     const int t = c->pad_type[p];
     inst_pad[inst_off[t] + fill[t]++] = p;
   }
+  std::vector<long long> woff(np + 1, 0);   // per-pad offsets of the contact bit words
+  for (int p = 0; p < np; ++p) woff[p + 1] = woff[p] + (c->type_n[c->pad_type[p]] + 31) / 32;
   std::vector<long long> bt_off(c->T, 0);
   long long bt_total = 0;
   for (int t = 0; t < c->T; ++t) {
     bt_off[t] = bt_total;
     bt_total += ((3LL * ninst[t] * c->type_n[t]) + 127) / 128 * 128;
   }
+  // tiles: node-row tiles innermost, so the CTAs working at one time share each B tile (the
+  // instances' u_hat) through L2 instead of re-reading it from DRAM per row tile
   std::vector<etac::GemmTile> tiles;
   for (int t = 0; t < c->T; ++t) {
     if (!ninst[t]) continue;
     const int n = c->type_n[t];
-    for (int m0 = 0; m0 < n; m0 += 128)
-      for (int k0 = 0; k0 < ninst[t]; k0 += 64) tiles.push_back({t, m0, k0, (n + 63) / 64});
+    for (int k0 = 0; k0 < ninst[t]; k0 += 64)
+      for (int m0 = 0; m0 < n; m0 += 128) tiles.push_back({t, m0, k0, (n + 63) / 64});
   }
   std::stable_sort(tiles.begin(), tiles.end(), [](const etac::GemmTile& x,
                                                   const etac::GemmTile& y) {
@@ -215,7 +220,10 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_inst_pad, np);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
-  if (e == cudaSuccess) e = dalloc(&c->d_maskbuf, (size_t)c->N);
+  if (e == cudaSuccess) e = dalloc(&c->d_maskbits, (size_t)woff[np]);
+  if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
+                                            cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_bt_off, bt_off.data(), sizeof(long long) * c->T,
                                             cudaMemcpyHostToDevice, s);
@@ -256,7 +264,8 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   g.h0bf16 = c->d_h0bf16;
   g.negbeta = c->d_negbeta;
   g.c0m = c->d_c0m;
-  g.maskbuf = c->d_maskbuf;
+  g.maskbits = c->d_maskbits;
+  g.mask_woff = c->d_mask_woff;
   g.params = c->d_params;
   g.status = c->d_status;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
@@ -559,7 +568,6 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       b.pad_inst = c->d_pad_inst;
       b.negbeta = c->d_negbeta;
       b.c0m = c->d_c0m;
-      b.maskbuf = c->d_maskbuf;
       int ts = timing_begin(c, K_FRONT, s);
       ETAC_CUDA(c, etac::launch_batched_front_bf16(b, std::min<int>(c->front_grid, (int)EP), s),
                 "BF16 front launch");

@@ -17,6 +17,7 @@
 
 #include "etac_common.cuh"
 #include "etac_kernels.h"
+#include "sm100_ptx.cuh"
 
 namespace etac {
 
@@ -25,7 +26,7 @@ constexpr int BW = BT / 32;
 
 struct BatchedSmem {
   // byte offsets of every shared array for a given nmax / K
-  size_t w2, b2, w1u, w4, b4, g, beta, red, actu, actidx, mask, warp, po, total;
+  size_t w2, b2, w1u, w4, b4, g, beta, red, w2frag, actu, actidx, mask, warp, po, total;
   __host__ __device__ BatchedSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -41,6 +42,7 @@ struct BatchedSmem {
     g = take(sizeof(float) * H);
     beta = take(sizeof(float) * H);
     red = take(sizeof(float) * BW * H);
+    w2frag = take(sizeof(uint2) * 8 * 4 * 32);
     actu = take(sizeof(float4) * (size_t)nmax);
     actidx = take(sizeof(int16_t) * (size_t)nmax);
     mask = take(sizeof(uint8_t) * (size_t)nmax);
@@ -71,6 +73,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   uint8_t* sMask = reinterpret_cast<uint8_t*>(smem + L.mask);
   int* sWarp = reinterpret_cast<int*>(smem + L.warp);
   PadObj* spo = reinterpret_cast<PadObj*>(smem + L.po);
+  uint2* sW2f = reinterpret_cast<uint2*>(smem + L.w2frag);  // BF16 B fragments of E2
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* W = a.params;
@@ -84,6 +87,18 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   }
   for (int i = tid; i < 3 * H; i += BT) sW4[i] = W[OFF_W4 + i];
   if (tid < 3) sB4[tid] = W[OFF_B4 + tid];
+  if constexpr (kBF16) {
+    // E2 as m16n8k16 B fragments: B[k = input unit][n = output unit] = W2[n][k]; entry
+    // (nt, s, l) holds lane l's two registers for output tile nt and input step s
+    for (int e = tid; e < 8 * 4 * 32; e += BT) {
+      const int l = e & 31, s4 = (e >> 5) & 3, nt = e >> 7;
+      const int n = 8 * nt + (l >> 2), k = 16 * s4 + 2 * (l & 3);
+      __nv_bfloat162 lo = __floats2bfloat162_rn(W[OFF_W2 + n * H + k], W[OFF_W2 + n * H + k + 1]);
+      __nv_bfloat162 hi =
+          __floats2bfloat162_rn(W[OFF_W2 + n * H + k + 8], W[OFF_W2 + n * H + k + 9]);
+      sW2f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+    }
+  }
   const unsigned lt_mask = (1u << lane) - 1u;
 
   for (;;) {
@@ -135,9 +150,10 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
           btrow[i] = z;
           btrow[n + i] = z;
           btrow[2 * n + i] = z;
-          a.maskbuf[base + i] = 0;
         }
       }
+      if constexpr (kBF16)
+        for (int w = tid; w < (n + 31) / 32; w += BT) a.maskbits[a.mask_woff[pad] + w] = 0u;
       if (tid == 0 && a.count) a.count[pad] = 0;
       if constexpr (kBF16)
         if (tid == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
@@ -158,6 +174,10 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       }
       const unsigned bal = __ballot_sync(0xffffffffu, c.active);
       if (lane == 0) sWarp[warp] = __popc(bal);
+      if constexpr (kBF16) {
+        const int w = (r0 >> 5) + warp;
+        if (lane == 0 && w < (n + 31) / 32) a.maskbits[a.mask_woff[pad] + w] = bal;
+      }
       __syncthreads();
       int woff = 0, tot = 0;
 #pragma unroll
@@ -170,7 +190,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         sMask[i] = c.active ? 1 : 0;
         if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
         if constexpr (kBF16) {
-          a.maskbuf[base + i] = c.active ? 1 : 0;
           btrow[i] = __float2bfloat16_rn(c.u[0]);
           btrow[n + i] = __float2bfloat16_rn(c.u[1]);
           btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
@@ -202,6 +221,69 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 
     // ---- 2. residual network (factored)
     if (a.mode != MODE_LINEAR_ONLY) {
+      if constexpr (kBF16) {
+        // encoder on tensor cores: 16 active nodes per warp step; E1 (c_i + W1u u_hat) is
+        // evaluated directly in the A-fragment layout of m16n8k16, E2 by 32 BF16 MMAs with
+        // FP32 accumulators, then ReLU and a running channel maximum per thread
+        const int grp = lane >> 2, tig = lane & 3;
+        float fm[8][2];
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt) fm[nt][0] = fm[nt][1] = 0.f;
+        for (int g = warp; g * 16 < m; g += BW) {
+          const int s0 = 16 * g + grp, s1 = s0 + 8;
+          const bool v0 = s0 < m, v1 = s1 < m;
+          const int n0 = v0 ? sActIdx[s0] : 0, n1 = v1 ? sActIdx[s1] : 0;
+          const float4 u0 = v0 ? sActU[s0] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float4 u1 = v1 ? sActU[s1] : make_float4(0.f, 0.f, 0.f, 0.f);
+          const float* c0r = a.ctab + (size_t)(o + n0) * H;
+          const float* c1r = a.ctab + (size_t)(o + n1) * H;
+          uint32_t af[4][4];
+#pragma unroll
+          for (int s4 = 0; s4 < 4; ++s4) {
+#pragma unroll
+            for (int hh = 0; hh < 2; ++hh) {
+              const int col = 16 * s4 + 8 * hh + 2 * tig;
+              const float2 ca = __ldg(reinterpret_cast<const float2*>(c0r + col));
+              const float2 cb = __ldg(reinterpret_cast<const float2*>(c1r + col));
+              const float4 w0 = *reinterpret_cast<const float4*>(sW1u + 4 * col);
+              const float4 w1 = *reinterpret_cast<const float4*>(sW1u + 4 * (col + 1));
+              const float z00 = fmaxf(fmaf(w0.x, u0.x, fmaf(w0.y, u0.y, fmaf(w0.z, u0.z, ca.x))), 0.f);
+              const float z01 = fmaxf(fmaf(w1.x, u0.x, fmaf(w1.y, u0.y, fmaf(w1.z, u0.z, ca.y))), 0.f);
+              const float z10 = fmaxf(fmaf(w0.x, u1.x, fmaf(w0.y, u1.y, fmaf(w0.z, u1.z, cb.x))), 0.f);
+              const float z11 = fmaxf(fmaf(w1.x, u1.x, fmaf(w1.y, u1.y, fmaf(w1.z, u1.z, cb.y))), 0.f);
+              __nv_bfloat162 p0 = __floats2bfloat162_rn(z00, z01);
+              __nv_bfloat162 p1 = __floats2bfloat162_rn(z10, z11);
+              af[s4][2 * hh + 0] = *reinterpret_cast<uint32_t*>(&p0);
+              af[s4][2 * hh + 1] = *reinterpret_cast<uint32_t*>(&p1);
+            }
+          }
+#pragma unroll
+          for (int nt = 0; nt < 8; ++nt) {
+            const float bx = sB2[8 * nt + 2 * tig], by = sB2[8 * nt + 2 * tig + 1];
+            float acc[4] = {bx, by, bx, by};
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+              const uint2 bb = sW2f[(nt * 4 + s4) * 32 + lane];
+              sm100::mma_bf16_16816(acc, af[s4], bb.x, bb.y, acc);
+            }
+            const float f00 = v0 ? fmaxf(acc[0], 0.f) : 0.f, f01 = v0 ? fmaxf(acc[1], 0.f) : 0.f;
+            const float f10 = v1 ? fmaxf(acc[2], 0.f) : 0.f, f11 = v1 ? fmaxf(acc[3], 0.f) : 0.f;
+            fm[nt][0] = fmaxf(fm[nt][0], fmaxf(f00, f10));
+            fm[nt][1] = fmaxf(fm[nt][1], fmaxf(f01, f11));
+          }
+        }
+#pragma unroll
+        for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+          for (int e = 0; e < 2; ++e) {
+            float v = fm[nt][e];
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
+            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
+            if (grp == 0) sRed[warp * H + 8 * nt + 2 * tig + e] = v;
+          }
+        __syncthreads();
+      } else {
       float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
       for (int a0 = 0; a0 < m; a0 += BT) {
         const int aa = a0 + tid;
@@ -251,6 +333,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       sRed[warp * H + lane] = fm0;
       sRed[warp * H + 32 + lane] = fm1;
       __syncthreads();
+      }
+
       if (tid < H) {
         float g0 = 0.f;
 #pragma unroll
@@ -267,25 +351,30 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         sG[tid] = g0;
       }
       __syncthreads();
-      float gv = 0.f;
-      if (tid < H) {
-        // the flat parameter vector starts with alpha, so its tensors are only 4-byte
-        // aligned: scalar loads here
-        float acc = W[OFF_BG + tid];
-        const float* wr = W + OFF_WG + tid * H;
-        for (int k = 0; k < H; ++k) acc = fmaf(__ldg(wr + k), sG[k], acc);
-        gv = fmaxf(acc, 0.f);
-      }
-      __syncthreads();
-      if (tid < H) sG[tid] = gv;
-      __syncthreads();
-      if (tid < H) {
+      {
+        // global MLP and the decoder's global half, 4 partial sums per output on 256 threads
+        const int u = tid & (H - 1), part = tid >> 6;
         float acc = 0.f;
-        const float* wr = W + OFF_WD + tid * 2 * H + H;
-        for (int k = 0; k < H; ++k) acc = fmaf(__ldg(wr + k), sG[k], acc);
-        sBeta[tid] = acc;
+        const float* wr = W + OFF_WG + u * H + part * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fmaf(__ldg(wr + k), sG[part * 16 + k], acc);
+        sRed[part * H + u] = acc;
+        __syncthreads();
+        if (tid < H) {
+          const float gsum = W[OFF_BG + tid] + sRed[tid] + sRed[H + tid] + sRed[2 * H + tid] +
+                             sRed[3 * H + tid];
+          sG[tid] = fmaxf(gsum, 0.f);
+        }
+        __syncthreads();
+        acc = 0.f;
+        const float* wd = W + OFF_WD + u * 2 * H + H + part * 16;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) acc = fmaf(__ldg(wd + k), sG[part * 16 + k], acc);
+        sRed[part * H + u] = acc;
+        __syncthreads();
+        if (tid < H) sBeta[tid] = sRed[tid] + sRed[H + tid] + sRed[2 * H + tid] + sRed[3 * H + tid];
+        __syncthreads();
       }
-      __syncthreads();
     }
 
     if constexpr (kBF16) {
@@ -294,16 +383,16 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       if (a.mode != MODE_LINEAR_ONLY && tid < H)
         reinterpret_cast<__nv_bfloat16*>(a.negbeta)[(size_t)pad * H + tid] =
             __float2bfloat16_rn(-sBeta[tid]);
-      if (tid == 0) {
-        float c0[3] = {0.f, 0.f, 0.f};
+      if (warp < 3) {
+        float acc = 0.f;
         if (a.mode != MODE_LINEAR_ONLY)
-          for (int q = 0; q < 3; ++q) {
-            float acc = sB4[q];
-            for (int u = 0; u < H; ++u) acc = fmaf(sW4[q * H + u], sBeta[u], acc);
-            c0[q] = acc;
-          }
-        a.c0m[pad] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
+          acc = fmaf(sW4[warp * H + lane], sBeta[lane], sW4[warp * H + 32 + lane] * sBeta[32 + lane]);
+#pragma unroll
+        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
+        if (lane == 0) sRed[warp] = a.mode != MODE_LINEAR_ONLY ? acc + sB4[warp] : 0.f;
       }
+      __syncthreads();
+      if (tid == 0) a.c0m[pad] = make_float4(sRed[0], sRed[1], sRed[2], __int_as_float(m));
       continue;
     }
 

@@ -92,7 +92,8 @@ struct BatchedArgs {
   const int* pad_inst;          // [E*P] instance index of each pad within its type
   void* negbeta;                // [E*P][64] BF16, -beta of each pad
   float4* c0m;                  // [E*P] (D2 beta + b_D2, active count as int bits)
-  uint8_t* maskbuf;             // [N] internal contact mask
+  uint32_t* maskbits;           // contact bits, pad p's word w at mask_woff[p] + w
+  const long long* mask_woff;   // [E*P+1]
 };
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_batched_front_bf16(const BatchedArgs& a, int grid, cudaStream_t s);
@@ -126,7 +127,8 @@ struct GemmParams {
   const void* h0bf16;                // [sum n][64]
   const void* negbeta;               // [E*P][64]
   const float4* c0m;                 // [E*P]
-  const uint8_t* maskbuf;            // [N]
+  const uint32_t* maskbits;          // contact bits per pad (32 nodes per word)
+  const long long* mask_woff;        // [E*P+1]
   const float* params;
   float* disp;
   int use_l, use_r;

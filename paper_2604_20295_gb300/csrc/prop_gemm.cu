@@ -32,7 +32,7 @@ constexpr int GM = 128;                 // node rows per tile
 constexpr int GI = 64;                  // instances per tile
 constexpr int GN = 3 * GI;              // 192 accumulator columns
 constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 8;
 constexpr int TMA_WARP = 8, MMA_WARP = 9;
 constexpr int THREADS = 10 * 32;
@@ -45,12 +45,13 @@ constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
 // shared-memory layout (offsets from a 1024-byte aligned base)
 constexpr size_t SM_A = 0;
 constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
-constexpr size_t SM_Z = SM_B + (size_t)STAGES * B_BYTES;          // 8 x 32 rows x 128 B
-constexpr size_t SM_R = SM_Z + (size_t)EPI_WARPS * 32 * 128;      // 8 x 32 x float4
-constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 32 * 16;      // 64 x 64 BF16
+constexpr size_t SM_Z = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x 2 x 32 x 128 B
+constexpr size_t SM_R = SM_Z + (size_t)EPI_WARPS * 2 * 32 * 128;  // 8 warps x 2 x 32 x float4
+constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 2 * 32 * 16;  // 64 x 64 BF16
 constexpr size_t SM_C0 = SM_NB + (size_t)GI * H * 2;              // 64 x float4
 constexpr size_t SM_BASE = SM_C0 + (size_t)GI * 16;               // 64 x int64
-constexpr size_t SM_BAR = SM_BASE + (size_t)GI * 8;               // barriers
+constexpr size_t SM_BITS = SM_BASE + (size_t)GI * 8;              // 64 x 4 contact words
+constexpr size_t SM_BAR = SM_BITS + (size_t)GI * 16;              // barriers
 constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
 constexpr size_t SM_TOTAL = SM_MISC + 16;
 constexpr size_t SM_ALLOC = SM_TOTAL + 1024;                      // alignment slack
@@ -198,11 +199,12 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     // ---------------------------------------------------------------- epilogue (warps 0-7)
     const int q = warp & 3, half = warp >> 2, etid = threadIdx.x;   // etid in [0, 256)
     const int grp = lane >> 2, tig = lane & 3;
-    unsigned char* zbuf = smem + SM_Z + (size_t)warp * 32 * 128;
-    float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * 32 * 16);
+    unsigned char* zbuf = smem + SM_Z + (size_t)warp * 2 * 32 * 128;
+    float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * 2 * 32 * 16);
     __nv_bfloat16* s_nb = reinterpret_cast<__nv_bfloat16*>(smem + SM_NB);
     float4* s_c0 = reinterpret_cast<float4*>(smem + SM_C0);
     long long* s_base = reinterpret_cast<long long*>(smem + SM_BASE);
+    uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + SM_BITS);
     const float* W4 = p.params + OFF_W4;
     // decoder weights as constant B fragments: B[k = hidden][n = output component]
     uint32_t bw[4][2];
@@ -220,8 +222,9 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
       const int t = T.type;
       const int n_t = p.type_off[t + 1] - p.type_off[t];
+      const int nwords = (n_t + 31) >> 5;
       const int ninst = p.inst_off[t + 1] - p.inst_off[t];
-      // per-instance records of this tile
+      // per-instance records of this tile: -beta, (c0, m), node base, contact bits of the rows
       named_bar_sync(1, EPI_WARPS * 32);
       for (int idx = etid; idx < GI * 8; idx += EPI_WARPS * 32) {
         const int inst = idx >> 3, chunk = idx & 7;
@@ -234,9 +237,16 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
             s_c0[inst] = p.c0m[pad];
             s_base[inst] = p.pad_off[pad];
           }
-        } else if (chunk == 0) {
-          s_c0[inst] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
-          s_base[inst] = 0;
+          if (chunk < 4) {
+            const int w = (T.m0 >> 5) + chunk;
+            s_bits[inst * 4 + chunk] = w < nwords ? p.maskbits[p.mask_woff[pad] + w] : 0u;
+          }
+        } else {
+          if (chunk == 0) {
+            s_c0[inst] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
+            s_base[inst] = 0;
+          }
+          if (chunk < 4) s_bits[inst * 4 + chunk] = 0u;
         }
         reinterpret_cast<uint4*>(s_nb)[inst * 8 + chunk] = v;
       }
@@ -283,56 +293,77 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
           tc_wait_ld();
         }
 #pragma unroll
-        for (int j = 0; j < 8; ++j) {
-          const int inst = inst0 + j;
-          float4 r = make_float4(0.f, 0.f, 0.f, 0.f);
+        for (int jj = 0; jj < 8; jj += 2) {
+          // two instances at a time: independent MMA chains for latency hiding
+          float4 r[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
           if (p.use_r) {
-            // Z row = max(h0_i, -beta_k), 128-byte row, 16-byte chunks XOR-swizzled by row
-            const uint4* nb = reinterpret_cast<const uint4*>(s_nb + inst * H);
 #pragma unroll
-            for (int c = 0; c < 8; ++c) {
-              const uint4 v = nb[c];
-              uint4 z;
-              z.x = bf16x2_max(h0[4 * c + 0], v.x);
-              z.y = bf16x2_max(h0[4 * c + 1], v.y);
-              z.z = bf16x2_max(h0[4 * c + 2], v.z);
-              z.w = bf16x2_max(h0[4 * c + 3], v.w);
-              *reinterpret_cast<uint4*>(zbuf + lane * 128 + ((c ^ (lane & 7)) << 4)) = z;
-            }
-            __syncwarp();
+            for (int x = 0; x < 2; ++x) {
+              // Z row = max(h0_i, -beta_k): 128-byte row, 16-byte chunks XOR-swizzled by row
+              const uint4* nb = reinterpret_cast<const uint4*>(s_nb + (inst0 + jj + x) * H);
+              unsigned char* zb = zbuf + x * 32 * 128;
 #pragma unroll
-            for (int rg = 0; rg < 2; ++rg) {
-              float acc[4] = {0.f, 0.f, 0.f, 0.f};
-              const int mi = lane >> 3;
-              const int row = rg * 16 + (lane & 7) + (mi & 1) * 8;
-#pragma unroll
-              for (int s = 0; s < 4; ++s) {
-                const int chunk = 2 * s + (mi >> 1);
-                uint32_t a[4];
-                ldmatrix_x4(smem_u32(zbuf + row * 128 + ((chunk ^ (row & 7)) << 4)), a[0], a[1],
-                            a[2], a[3]);
-                mma_bf16_16816(acc, a, bw[s][0], bw[s][1], acc);
-              }
-              float* rb = reinterpret_cast<float*>(rbuf);
-              const int r0 = rg * 16 + grp;
-              if (tig == 0) {
-                rb[r0 * 4 + 0] = acc[0];
-                rb[r0 * 4 + 1] = acc[1];
-                rb[(r0 + 8) * 4 + 0] = acc[2];
-                rb[(r0 + 8) * 4 + 1] = acc[3];
-              } else if (tig == 1) {
-                rb[r0 * 4 + 2] = acc[0];
-                rb[(r0 + 8) * 4 + 2] = acc[2];
+              for (int c = 0; c < 8; ++c) {
+                const uint4 v = nb[c];
+                uint4 z;
+                z.x = bf16x2_max(h0[4 * c + 0], v.x);
+                z.y = bf16x2_max(h0[4 * c + 1], v.y);
+                z.z = bf16x2_max(h0[4 * c + 2], v.z);
+                z.w = bf16x2_max(h0[4 * c + 3], v.w);
+                *reinterpret_cast<uint4*>(zb + lane * 128 + ((c ^ (lane & 7)) << 4)) = z;
               }
             }
             __syncwarp();
-            r = rbuf[lane];
+            float acc[2][2][4];
+#pragma unroll
+            for (int x = 0; x < 2; ++x)
+#pragma unroll
+              for (int rg = 0; rg < 2; ++rg)
+#pragma unroll
+                for (int e = 0; e < 4; ++e) acc[x][rg][e] = 0.f;
+            const int mi = lane >> 3;
+#pragma unroll
+            for (int s = 0; s < 4; ++s) {
+              const int chunk = 2 * s + (mi >> 1);
+#pragma unroll
+              for (int x = 0; x < 2; ++x)
+#pragma unroll
+                for (int rg = 0; rg < 2; ++rg) {
+                  const int row = rg * 16 + (lane & 7) + (mi & 1) * 8;
+                  uint32_t a[4];
+                  ldmatrix_x4(smem_u32(zbuf + x * 32 * 128 + row * 128 + ((chunk ^ (row & 7)) << 4)),
+                              a[0], a[1], a[2], a[3]);
+                  mma_bf16_16816(acc[x][rg], a, bw[s][0], bw[s][1], acc[x][rg]);
+                }
+            }
+#pragma unroll
+            for (int x = 0; x < 2; ++x) {
+              float* rb = reinterpret_cast<float*>(rbuf + x * 32);
+#pragma unroll
+              for (int rg = 0; rg < 2; ++rg) {
+                const int r0 = rg * 16 + grp;
+                if (tig == 0) {
+                  rb[r0 * 4 + 0] = acc[x][rg][0];
+                  rb[r0 * 4 + 1] = acc[x][rg][1];
+                  rb[(r0 + 8) * 4 + 0] = acc[x][rg][2];
+                  rb[(r0 + 8) * 4 + 1] = acc[x][rg][3];
+                } else if (tig == 1) {
+                  rb[r0 * 4 + 2] = acc[x][rg][0];
+                  rb[(r0 + 8) * 4 + 2] = acc[x][rg][2];
+                }
+              }
+            }
+            __syncwarp();
+            r[0] = rbuf[lane];
+            r[1] = rbuf[32 + lane];
             __syncwarp();
           }
-          const float4 cm = s_c0[inst];
-          if (row_ok && __float_as_int(cm.w) > 0) {
-            const long long node = s_base[inst] + i;
-            if (!p.maskbuf[node]) {
+#pragma unroll
+          for (int x = 0; x < 2; ++x) {
+            const int j = jj + x, inst = inst0 + j;
+            const float4 cm = s_c0[inst];
+            const bool passive = ((s_bits[inst * 4 + q] >> lane) & 1u) == 0u;
+            if (row_ok && passive && __float_as_int(cm.w) > 0) {
               float u0 = 0.f, u1 = 0.f, u2 = 0.f;
               if (p.use_l) {
                 u0 = __uint_as_float(lv[3 * j + 0]);
@@ -340,11 +371,11 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
                 u2 = __uint_as_float(lv[3 * j + 2]);
               }
               if (p.use_r) {
-                u0 += r.x + cm.x;
-                u1 += r.y + cm.y;
-                u2 += r.z + cm.z;
+                u0 += r[x].x + cm.x;
+                u1 += r[x].y + cm.y;
+                u2 += r[x].z + cm.z;
               }
-              float* d = p.disp + 3 * node;
+              float* d = p.disp + 3 * (s_base[inst] + i);
               d[0] = u0;
               d[1] = u1;
               d[2] = u2;
