@@ -568,6 +568,11 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       b.pad_inst = c->d_pad_inst;
       b.negbeta = c->d_negbeta;
       b.c0m = c->d_c0m;
+      b.maskbits = c->d_maskbits;
+      b.mask_woff = c->d_mask_woff;
+      if (!b.bt || !b.bt_off || !b.pad_inst || !b.negbeta || !b.c0m || !b.maskbits ||
+          !b.mask_woff || !c->gemm.tiles || !c->gemm.h0bf16 || !c->gemm.maskbits)
+        return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");
       int ts = timing_begin(c, K_FRONT, s);
       ETAC_CUDA(c, etac::launch_batched_front_bf16(b, std::min<int>(c->front_grid, (int)EP), s),
                 "BF16 front launch");
