@@ -67,6 +67,8 @@ struct etac_ctx {
   float4* d_c0m = nullptr;
   uint32_t* d_maskbits = nullptr;
   long long* d_mask_woff = nullptr;
+  int* d_pad_m = nullptr;
+  float* d_g0a = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
@@ -80,8 +82,8 @@ struct etac_ctx {
 
 namespace {
 const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
-                              "batched_forward_kernel<bf16 front>", "prop_gemm_kernel"};
-enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_COUNT = 4 };
+                              "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel"};
+enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_COUNT = 5 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -139,7 +141,8 @@ void free_ctx(etac_ctx* c) {
                   c->d_omega_off, c->d_item_pad, c->d_ticket, c->d_ctab, c->d_f0tab,
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
-                  c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff};
+                  c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
+                  c->d_g0a};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -222,6 +225,8 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
   if (e == cudaSuccess) e = dalloc(&c->d_maskbits, (size_t)woff[np]);
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
@@ -270,7 +275,7 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   g.status = c->d_status;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
   int per_sm = 0;
-  e = etac::batched_front_occupancy(c->nmax, c->K, &per_sm);
+  e = etac::front_occupancy(c->nmax, c->K, &per_sm);
   if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "front kernel occupancy");
   c->front_grid = per_sm * c->num_sms;
   c->gemm_grid = std::max(1, std::min(c->num_sms, (int)tiles.size()));
@@ -563,19 +568,54 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.status = c->d_status;
     ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
     if (c->model.precision == ETAC_PREC_BF16) {
-      b.bt = c->d_bt;
-      b.bt_off = c->d_bt_off;
-      b.pad_inst = c->d_pad_inst;
-      b.negbeta = c->d_negbeta;
-      b.c0m = c->d_c0m;
-      b.maskbits = c->d_maskbits;
-      b.mask_woff = c->d_mask_woff;
-      if (!b.bt || !b.bt_off || !b.pad_inst || !b.negbeta || !b.c0m || !b.maskbits ||
-          !b.mask_woff || !c->gemm.tiles || !c->gemm.h0bf16 || !c->gemm.maskbits)
+      etac::FrontArgs f{};
+      f.type_pos = c->d_type_pos;
+      f.type_nrm = c->d_type_nrm;
+      f.type_pmax = c->d_type_pmax;
+      f.type_off = c->d_type_off;
+      f.pad_type = c->d_pad_type;
+      f.pad_off = c->d_pad_off;
+      f.item_pad = c->d_item_pad;
+      f.num_items = (int)EP;
+      f.P = c->P;
+      f.K = c->K;
+      f.nmax = c->nmax;
+      f.obj_type = c->d_saved_obj_type;
+      f.obj_dims = c->d_saved_obj_dims;
+      f.obj_pose = c->d_saved_obj_pose;
+      f.pad_pose = c->d_saved_pad_pose;
+      f.params = c->d_params;
+      f.ctab = c->d_ctab;
+      f.f0tab = c->d_f0tab;
+      f.order = c->d_order;
+      f.mode = c->model.mode;
+      f.disp = out->disp;
+      f.mask = out->active_mask;
+      f.pen = out->penetration;
+      f.count = out->active_count;
+      f.ticket = c->d_ticket;
+      f.status = c->d_status;
+      f.bt = c->d_bt;
+      f.bt_off = c->d_bt_off;
+      f.pad_inst = c->d_pad_inst;
+      f.maskbits = c->d_maskbits;
+      f.mask_woff = c->d_mask_woff;
+      f.pad_m = c->d_pad_m;
+      f.g0a = c->d_g0a;
+      f.negbeta = c->d_negbeta;
+      f.c0m = c->d_c0m;
+      if (!f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
+          !f.mask_woff || !f.pad_m || !f.g0a || !c->gemm.tiles || !c->gemm.h0bf16 ||
+          !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");
       int ts = timing_begin(c, K_FRONT, s);
-      ETAC_CUDA(c, etac::launch_batched_front_bf16(b, std::min<int>(c->front_grid, (int)EP), s),
+      ETAC_CUDA(c, etac::launch_front_contact(f, std::min<int>(c->front_grid, (int)EP), s),
                 "BF16 front launch");
+      timing_end(c, ts, s);
+      ts = timing_begin(c, K_GLOBAL, s);
+      ETAC_CUDA(c, etac::launch_front_global(f, std::max(1, std::min<int>(4 * c->num_sms,
+                                                                           ((int)EP + 7) / 8)), s),
+                "BF16 global-feature launch");
       timing_end(c, ts, s);
       etac::GemmParams& g = c->gemm;
       g.disp = out->disp;

@@ -13,11 +13,8 @@
 //   3. every passive node: Omega U_a (Eq. 1, Omega from the per-type table) plus
 //      Phi_p = D2 ReLU(h0_i + beta) + b (Eq. 4).
 // The algebra equals the literal network exactly; only rounding order differs.
-#include <cuda_bf16.h>
-
 #include "etac_common.cuh"
 #include "etac_kernels.h"
-#include "sm100_ptx.cuh"
 
 namespace etac {
 
@@ -26,7 +23,7 @@ constexpr int BW = BT / 32;
 
 struct BatchedSmem {
   // byte offsets of every shared array for a given nmax / K
-  size_t w2, b2, w1u, w4, b4, g, beta, red, w2frag, actu, actidx, mask, warp, po, total;
+  size_t w2, b2, w1u, w4, b4, g, beta, red, actu, actidx, mask, warp, po, total;
   __host__ __device__ BatchedSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -42,7 +39,6 @@ struct BatchedSmem {
     g = take(sizeof(float) * H);
     beta = take(sizeof(float) * H);
     red = take(sizeof(float) * BW * H);
-    w2frag = take(sizeof(uint2) * 8 * 4 * 32);
     actu = take(sizeof(float4) * (size_t)nmax);
     actidx = take(sizeof(int16_t) * (size_t)nmax);
     mask = take(sizeof(uint8_t) * (size_t)nmax);
@@ -52,10 +48,6 @@ struct BatchedSmem {
   }
 };
 
-// kBF16 = false: the whole FP32 step.  kBF16 = true: the front half of the BF16 tensor-core
-// step -- contact, encoder, pooling and global MLP -- writing the GEMM's B operand (u_hat in
-// BF16, zero on passive nodes), the contact mask and each pad's decoder record.
-template <bool kBF16>
 __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -73,7 +65,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   uint8_t* sMask = reinterpret_cast<uint8_t*>(smem + L.mask);
   int* sWarp = reinterpret_cast<int*>(smem + L.warp);
   PadObj* spo = reinterpret_cast<PadObj*>(smem + L.po);
-  uint2* sW2f = reinterpret_cast<uint2*>(smem + L.w2frag);  // BF16 B fragments of E2
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* W = a.params;
@@ -87,18 +78,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   }
   for (int i = tid; i < 3 * H; i += BT) sW4[i] = W[OFF_W4 + i];
   if (tid < 3) sB4[tid] = W[OFF_B4 + tid];
-  if constexpr (kBF16) {
-    // E2 as m16n8k16 B fragments: B[k = input unit][n = output unit] = W2[n][k]; entry
-    // (nt, s, l) holds lane l's two registers for output tile nt and input step s
-    for (int e = tid; e < 8 * 4 * 32; e += BT) {
-      const int l = e & 31, s4 = (e >> 5) & 3, nt = e >> 7;
-      const int n = 8 * nt + (l >> 2), k = 16 * s4 + 2 * (l & 3);
-      __nv_bfloat162 lo = __floats2bfloat162_rn(W[OFF_W2 + n * H + k], W[OFF_W2 + n * H + k + 1]);
-      __nv_bfloat162 hi =
-          __floats2bfloat162_rn(W[OFF_W2 + n * H + k + 8], W[OFF_W2 + n * H + k + 9]);
-      sW2f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
-    }
-  }
   const unsigned lt_mask = (1u << lane) - 1u;
 
   for (;;) {
@@ -135,9 +114,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
     }
     __syncthreads();
-    __nv_bfloat16* btrow = nullptr;   // BF16 variant: rows 3k..3k+2 of the B operand
-    if constexpr (kBF16)
-      btrow = reinterpret_cast<__nv_bfloat16*>(a.bt) + a.bt_off[ty] + (size_t)3 * a.pad_inst[pad] * n;
     if (sWarp[BW]) {
       if (tid == 0) latch_status(a.status, STATUS_NONFINITE);
       for (int i = tid; i < n; i += BT) {
@@ -145,18 +121,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         d[0] = d[1] = d[2] = 0.f;
         if (a.mask) a.mask[base + i] = 0;
         if (a.pen) a.pen[base + i] = 0.f;
-        if constexpr (kBF16) {
-          const __nv_bfloat16 z = __float2bfloat16_rn(0.f);
-          btrow[i] = z;
-          btrow[n + i] = z;
-          btrow[2 * n + i] = z;
-        }
       }
-      if constexpr (kBF16)
-        for (int w = tid; w < (n + 31) / 32; w += BT) a.maskbits[a.mask_woff[pad] + w] = 0u;
       if (tid == 0 && a.count) a.count[pad] = 0;
-      if constexpr (kBF16)
-        if (tid == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
       continue;
     }
 
@@ -174,10 +140,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       }
       const unsigned bal = __ballot_sync(0xffffffffu, c.active);
       if (lane == 0) sWarp[warp] = __popc(bal);
-      if constexpr (kBF16) {
-        const int w = (r0 >> 5) + warp;
-        if (lane == 0 && w < (n + 31) / 32) a.maskbits[a.mask_woff[pad] + w] = bal;
-      }
       __syncthreads();
       int woff = 0, tot = 0;
 #pragma unroll
@@ -189,11 +151,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       if (i < n) {
         sMask[i] = c.active ? 1 : 0;
         if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
-        if constexpr (kBF16) {
-          btrow[i] = __float2bfloat16_rn(c.u[0]);
-          btrow[n + i] = __float2bfloat16_rn(c.u[1]);
-          btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
-        }
         if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
         if (c.active) {
           const int slot = m + woff + __popc(bal & lt_mask);
@@ -214,126 +171,61 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         float* d = a.disp + 3 * (base + i);
         d[0] = d[1] = d[2] = 0.f;
       }
-      if constexpr (kBF16)
-        if (tid == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
       continue;
     }
 
     // ---- 2. residual network (factored)
     if (a.mode != MODE_LINEAR_ONLY) {
-      if constexpr (kBF16) {
-        // encoder on tensor cores: 16 active nodes per warp step; E1 (c_i + W1u u_hat) is
-        // evaluated directly in the A-fragment layout of m16n8k16, E2 by 32 BF16 MMAs with
-        // FP32 accumulators, then ReLU and a running channel maximum per thread
-        const int grp = lane >> 2, tig = lane & 3;
-        float fm[8][2];
+    float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
+    for (int a0 = 0; a0 < m; a0 += BT) {
+      const int aa = a0 + tid;
+      const bool live = aa < m;
+      float z1[H];
+      if (live) {
+        const int i = sActIdx[aa];
+        const float4 u = sActU[aa];
+        const float4* crow = reinterpret_cast<const float4*>(a.ctab + (size_t)(o + i) * H);
 #pragma unroll
-        for (int nt = 0; nt < 8; ++nt) fm[nt][0] = fm[nt][1] = 0.f;
-        for (int g = warp; g * 16 < m; g += BW) {
-          const int s0 = 16 * g + grp, s1 = s0 + 8;
-          const bool v0 = s0 < m, v1 = s1 < m;
-          const int n0 = v0 ? sActIdx[s0] : 0, n1 = v1 ? sActIdx[s1] : 0;
-          const float4 u0 = v0 ? sActU[s0] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float4 u1 = v1 ? sActU[s1] : make_float4(0.f, 0.f, 0.f, 0.f);
-          const float* c0r = a.ctab + (size_t)(o + n0) * H;
-          const float* c1r = a.ctab + (size_t)(o + n1) * H;
-          uint32_t af[4][4];
+        for (int c4 = 0; c4 < H / 4; ++c4) {
+          const float4 cv = __ldg(crow + c4);
+          const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
 #pragma unroll
-          for (int s4 = 0; s4 < 4; ++s4) {
-#pragma unroll
-            for (int hh = 0; hh < 2; ++hh) {
-              const int col = 16 * s4 + 8 * hh + 2 * tig;
-              const float2 ca = __ldg(reinterpret_cast<const float2*>(c0r + col));
-              const float2 cb = __ldg(reinterpret_cast<const float2*>(c1r + col));
-              const float4 w0 = *reinterpret_cast<const float4*>(sW1u + 4 * col);
-              const float4 w1 = *reinterpret_cast<const float4*>(sW1u + 4 * (col + 1));
-              const float z00 = fmaxf(fmaf(w0.x, u0.x, fmaf(w0.y, u0.y, fmaf(w0.z, u0.z, ca.x))), 0.f);
-              const float z01 = fmaxf(fmaf(w1.x, u0.x, fmaf(w1.y, u0.y, fmaf(w1.z, u0.z, ca.y))), 0.f);
-              const float z10 = fmaxf(fmaf(w0.x, u1.x, fmaf(w0.y, u1.y, fmaf(w0.z, u1.z, cb.x))), 0.f);
-              const float z11 = fmaxf(fmaf(w1.x, u1.x, fmaf(w1.y, u1.y, fmaf(w1.z, u1.z, cb.y))), 0.f);
-              __nv_bfloat162 p0 = __floats2bfloat162_rn(z00, z01);
-              __nv_bfloat162 p1 = __floats2bfloat162_rn(z10, z11);
-              af[s4][2 * hh + 0] = *reinterpret_cast<uint32_t*>(&p0);
-              af[s4][2 * hh + 1] = *reinterpret_cast<uint32_t*>(&p1);
-            }
-          }
-#pragma unroll
-          for (int nt = 0; nt < 8; ++nt) {
-            const float bx = sB2[8 * nt + 2 * tig], by = sB2[8 * nt + 2 * tig + 1];
-            float acc[4] = {bx, by, bx, by};
-#pragma unroll
-            for (int s4 = 0; s4 < 4; ++s4) {
-              const uint2 bb = sW2f[(nt * 4 + s4) * 32 + lane];
-              sm100::mma_bf16_16816(acc, af[s4], bb.x, bb.y, acc);
-            }
-            const float f00 = v0 ? fmaxf(acc[0], 0.f) : 0.f, f01 = v0 ? fmaxf(acc[1], 0.f) : 0.f;
-            const float f10 = v1 ? fmaxf(acc[2], 0.f) : 0.f, f11 = v1 ? fmaxf(acc[3], 0.f) : 0.f;
-            fm[nt][0] = fmaxf(fm[nt][0], fmaxf(f00, f10));
-            fm[nt][1] = fmaxf(fm[nt][1], fmaxf(f01, f11));
+          for (int q = 0; q < 4; ++q) {
+            const int c = 4 * c4 + q;
+            const float4 w = *reinterpret_cast<const float4*>(sW1u + 4 * c);
+            z1[c] = fmaxf(fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, cc[q]))), 0.f);
           }
         }
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-          for (int e = 0; e < 2; ++e) {
-            float v = fm[nt][e];
-            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
-            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
-            v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
-            if (grp == 0) sRed[warp * H + 8 * nt + 2 * tig + e] = v;
-          }
-        __syncthreads();
       } else {
-      float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
-      for (int a0 = 0; a0 < m; a0 += BT) {
-        const int aa = a0 + tid;
-        const bool live = aa < m;
-        float z1[H];
-        if (live) {
-          const int i = sActIdx[aa];
-          const float4 u = sActU[aa];
-          const float4* crow = reinterpret_cast<const float4*>(a.ctab + (size_t)(o + i) * H);
 #pragma unroll
-          for (int c4 = 0; c4 < H / 4; ++c4) {
-            const float4 cv = __ldg(crow + c4);
-            const float cc[4] = {cv.x, cv.y, cv.z, cv.w};
+        for (int c = 0; c < H; ++c) z1[c] = 0.f;
+      }
 #pragma unroll
-            for (int q = 0; q < 4; ++q) {
-              const int c = 4 * c4 + q;
-              const float4 w = *reinterpret_cast<const float4*>(sW1u + 4 * c);
-              z1[c] = fmaxf(fmaf(w.x, u.x, fmaf(w.y, u.y, fmaf(w.z, u.z, cc[q]))), 0.f);
-            }
-          }
+      for (int c = 0; c < H; ++c) {
+        float acc = sB2[c];
+        const float4* wr = reinterpret_cast<const float4*>(sW2 + c * H);
+#pragma unroll
+        for (int k4 = 0; k4 < H / 4; ++k4) {
+          const float4 w = wr[k4];
+          acc = fmaf(w.x, z1[4 * k4 + 0], acc);
+          acc = fmaf(w.y, z1[4 * k4 + 1], acc);
+          acc = fmaf(w.z, z1[4 * k4 + 2], acc);
+          acc = fmaf(w.w, z1[4 * k4 + 3], acc);
+        }
+        const float f = live ? fmaxf(acc, 0.f) : 0.f;
+        // f >= 0, so unsigned order of the bit patterns is the float order
+        const float mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f)));
+        if (c < 32) {
+          if (lane == c) fm0 = fmaxf(fm0, mx);
         } else {
-#pragma unroll
-          for (int c = 0; c < H; ++c) z1[c] = 0.f;
-        }
-#pragma unroll
-        for (int c = 0; c < H; ++c) {
-          float acc = sB2[c];
-          const float4* wr = reinterpret_cast<const float4*>(sW2 + c * H);
-#pragma unroll
-          for (int k4 = 0; k4 < H / 4; ++k4) {
-            const float4 w = wr[k4];
-            acc = fmaf(w.x, z1[4 * k4 + 0], acc);
-            acc = fmaf(w.y, z1[4 * k4 + 1], acc);
-            acc = fmaf(w.z, z1[4 * k4 + 2], acc);
-            acc = fmaf(w.w, z1[4 * k4 + 3], acc);
-          }
-          const float f = live ? fmaxf(acc, 0.f) : 0.f;
-          // f >= 0, so unsigned order of the bit patterns is the float order
-          const float mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f)));
-          if (c < 32) {
-            if (lane == c) fm0 = fmaxf(fm0, mx);
-          } else {
-            if (lane == c - 32) fm1 = fmaxf(fm1, mx);
-          }
+          if (lane == c - 32) fm1 = fmaxf(fm1, mx);
         }
       }
-      sRed[warp * H + lane] = fm0;
-      sRed[warp * H + 32 + lane] = fm1;
-      __syncthreads();
-      }
+    }
+    sRed[warp * H + lane] = fm0;
+    sRed[warp * H + 32 + lane] = fm1;
+    __syncthreads();
+    
 
       if (tid < H) {
         float g0 = 0.f;
@@ -377,24 +269,6 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       }
     }
 
-    if constexpr (kBF16) {
-      // decoder record: ReLU(h0 + beta) = max(h0, -beta) + beta, so the GEMM epilogue needs
-      // -beta (BF16) and the constant D2 beta + b_D2 of this pad
-      if (a.mode != MODE_LINEAR_ONLY && tid < H)
-        reinterpret_cast<__nv_bfloat16*>(a.negbeta)[(size_t)pad * H + tid] =
-            __float2bfloat16_rn(-sBeta[tid]);
-      if (warp < 3) {
-        float acc = 0.f;
-        if (a.mode != MODE_LINEAR_ONLY)
-          acc = fmaf(sW4[warp * H + lane], sBeta[lane], sW4[warp * H + 32 + lane] * sBeta[32 + lane]);
-#pragma unroll
-        for (int d = 16; d > 0; d >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, d);
-        if (lane == 0) sRed[warp] = a.mode != MODE_LINEAR_ONLY ? acc + sB4[warp] : 0.f;
-      }
-      __syncthreads();
-      if (tid == 0) a.c0m[pad] = make_float4(sRed[0], sRed[1], sRed[2], __int_as_float(m));
-      continue;
-    }
 
     // ---- 3. passive nodes: Eq. 4
     const float* Om = a.omega + a.omega_off[ty];
@@ -444,11 +318,10 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 size_t batched_smem_bytes(int nmax, int K) { return BatchedSmem(nmax, K).total; }
 int batched_threads() { return BT; }
 
-template <bool kBF16>
 static cudaError_t configure(size_t smem) {
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel<kBF16>,
+    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
@@ -458,33 +331,17 @@ static cudaError_t configure(size_t smem) {
 
 cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
   size_t smem = batched_smem_bytes(nmax, K);
-  cudaError_t e = configure<false>(smem);
+  cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm,
-                                                       batched_forward_kernel<false>, BT, smem);
-}
-
-cudaError_t batched_front_occupancy(int nmax, int K, int* blocks_per_sm) {
-  size_t smem = batched_smem_bytes(nmax, K);
-  cudaError_t e = configure<true>(smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel<true>,
-                                                       BT, smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel, BT,
+                                                       smem);
 }
 
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s) {
   size_t smem = batched_smem_bytes(a.nmax, a.K);
-  cudaError_t e = configure<false>(smem);
+  cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  batched_forward_kernel<false><<<grid, BT, smem, s>>>(a);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_batched_front_bf16(const BatchedArgs& a, int grid, cudaStream_t s) {
-  size_t smem = batched_smem_bytes(a.nmax, a.K);
-  cudaError_t e = configure<true>(smem);
-  if (e != cudaSuccess) return e;
-  batched_forward_kernel<true><<<grid, BT, smem, s>>>(a);
+  batched_forward_kernel<<<grid, BT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

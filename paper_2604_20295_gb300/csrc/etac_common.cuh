@@ -75,12 +75,12 @@ __device__ __forceinline__ df two_prod(float a, float b) {
   return {p, e};
 }
 
+// Dekker's double-length addition: the absolute error is below ~2^-47 (|a| + |b|), i.e.
+// ~1e-12 mm for coordinates of 100 mm, far inside the 1e-6 mm contact band; cancellation in
+// the result (phi = |q| - r near the surface) costs relative, not absolute, accuracy.
 __device__ __forceinline__ df df_add(df a, df b) {
   df s = two_sum(a.hi, b.hi);
-  df t = two_sum(a.lo, b.lo);
-  s.lo = __fadd_rn(s.lo, t.hi);
-  s = quick_two_sum(s.hi, s.lo);
-  s.lo = __fadd_rn(s.lo, t.lo);
+  s.lo = __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo));
   return quick_two_sum(s.hi, s.lo);
 }
 
@@ -349,14 +349,10 @@ struct NodeContact {
   bool active;
 };
 
-// Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).
-__device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, float3 nrm,
-                                           SdfIn* detail = nullptr) {
-  NodeContact r;
-  r.phi = INFINITY;
-  r.u[0] = r.u[1] = r.u[2] = 0.f;
-  r.k = -1;
-  r.active = false;
+// FP32 screen: false when the node is certainly outside every object (|error| < tau);
+// *phi32 receives the FP32 minimum signed distance.
+__device__ inline bool contact_screen(const PadObj* po, int K, float3 p, float* phi32) {
+  float best = INFINITY;
   bool maybe = false;
   for (int k = 0; k < K; ++k) {
     const PadObj& o = po[k];
@@ -365,12 +361,22 @@ __device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, fl
     q.x = fmaf(o.R[0], p.x, fmaf(o.R[1], p.y, fmaf(o.R[2], p.z, o.t[0])));
     q.y = fmaf(o.R[3], p.x, fmaf(o.R[4], p.y, fmaf(o.R[5], p.z, o.t[1])));
     q.z = fmaf(o.R[6], p.x, fmaf(o.R[7], p.y, fmaf(o.R[8], p.z, o.t[2])));
-    float ph = sdf_f32(o.type, o.dims, q);
-    r.phi = fminf(r.phi, ph);
+    const float ph = sdf_f32(o.type, o.dims, q);
+    best = fminf(best, ph);
     maybe |= ph < o.tau;
   }
-  if (!maybe) return r;
-  // df32 path: every object, exact decisions
+  *phi32 = best;
+  return maybe;
+}
+
+// Exact (df32) contact decision and displacement of a node that passed the screen.
+__device__ inline NodeContact contact_refine(const PadObj* po, int K, float3 p, float3 nrm,
+                                             float phi32, SdfIn* detail = nullptr) {
+  NodeContact r;
+  r.phi = phi32;
+  r.u[0] = r.u[1] = r.u[2] = 0.f;
+  r.k = -1;
+  r.active = false;
   df best = df_from(0.f);
   SdfIn bs;
   for (int k = 0; k < K; ++k) {
@@ -403,13 +409,28 @@ __device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, fl
     bs.g[1] = -(o.R[3] * nrm.x + o.R[4] * nrm.y + o.R[5] * nrm.z);
     bs.g[2] = -(o.R[6] * nrm.x + o.R[7] * nrm.y + o.R[8] * nrm.z);
   }
-  float s = -r.phi;
+  const float s = -r.phi;
   // u_hat (pad frame) = R^T (-phi g)
   r.u[0] = s * (o.R[0] * bs.g[0] + o.R[3] * bs.g[1] + o.R[6] * bs.g[2]);
   r.u[1] = s * (o.R[1] * bs.g[0] + o.R[4] * bs.g[1] + o.R[7] * bs.g[2]);
   r.u[2] = s * (o.R[2] * bs.g[0] + o.R[5] * bs.g[1] + o.R[8] * bs.g[2]);
   if (detail) *detail = bs;
   return r;
+}
+
+// Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).
+__device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, float3 nrm,
+                                           SdfIn* detail = nullptr) {
+  float phi32;
+  if (!contact_screen(po, K, p, &phi32)) {
+    NodeContact r;
+    r.phi = phi32;
+    r.u[0] = r.u[1] = r.u[2] = 0.f;
+    r.k = -1;
+    r.active = false;
+    return r;
+  }
+  return contact_refine(po, K, p, nrm, phi32, detail);
 }
 
 // ------------------------------------------------------------------ FP64 variant

@@ -85,19 +85,49 @@ struct BatchedArgs {
   int* count;
   int* ticket;                  // work-queue counter, zero at launch
   int* status;
-  // BF16 tensor-core variant only: this kernel stops after the global MLP and hands the
-  // propagation + decoder to the GEMM kernel through these buffers
-  void* bt;                     // BF16 B operand, type t at bt_off[t]: [3 * I_t][n_t]
-  const long long* bt_off;      // [T]
-  const int* pad_inst;          // [E*P] instance index of each pad within its type
-  void* negbeta;                // [E*P][64] BF16, -beta of each pad
-  float4* c0m;                  // [E*P] (D2 beta + b_D2, active count as int bits)
-  uint32_t* maskbits;           // contact bits, pad p's word w at mask_woff[p] + w
-  const long long* mask_woff;   // [E*P+1]
 };
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_batched_front_bf16(const BatchedArgs& a, int grid, cudaStream_t s);
-cudaError_t batched_front_occupancy(int nmax, int K, int* blocks_per_sm);
+
+// ---------------------------------------------------------------- BF16 front kernels
+struct FrontArgs {
+  const float* type_pos;
+  const float* type_nrm;
+  const float* type_pmax;
+  const int* type_off;
+  const int* pad_type;
+  const long long* pad_off;
+  const int* item_pad;
+  int num_items, P, K, nmax;
+  const int* obj_type;
+  const float* obj_dims;
+  const float* obj_pose;
+  const float* pad_pose;
+  const float* params;
+  const float* ctab;
+  const float* f0tab;
+  const int16_t* order;
+  int mode;
+  float* disp;
+  uint8_t* mask;
+  float* pen;
+  int* count;
+  int* ticket;
+  int* status;
+  void* bt;                     // BF16 B operand, type t at bt_off[t]: [3 * I_t][n_t]
+  const long long* bt_off;
+  const int* pad_inst;
+  uint32_t* maskbits;
+  const long long* mask_woff;
+  int* pad_m;                   // [E*P] active count
+  float* g0a;                   // [E*P][64] channel maxima over active nodes
+  void* negbeta;                // [E*P][64] BF16
+  float4* c0m;                  // [E*P]
+};
+size_t front_smem_bytes(int nmax, int K);
+cudaError_t front_occupancy(int nmax, int K, int* blocks_per_sm);
+cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_front_global(const FrontArgs& a, int grid, cudaStream_t s);
+
 size_t batched_smem_bytes(int nmax, int K);
 int batched_threads();
 cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm);
