@@ -69,6 +69,7 @@ struct etac_ctx {
   long long* d_mask_woff = nullptr;
   int* d_pad_m = nullptr;
   float* d_g0a = nullptr;
+  float2* d_ranked = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
@@ -142,7 +143,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
                   c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
-                  c->d_g0a};
+                  c->d_g0a, c->d_ranked};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -227,6 +228,7 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_ranked, tn * etac::H);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
@@ -325,6 +327,7 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   a.omega = need32 ? c->d_omega : nullptr;
   a.omega_bf16 = need32 ? nullptr : c->d_omega_bf16;
   a.h0bf16 = need32 ? nullptr : c->d_h0bf16;
+  a.ranked = need32 ? nullptr : c->d_ranked;
   e = etac::launch_tables(a, c->nmax, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
   c->tables_ready = true;
@@ -588,6 +591,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.ctab = c->d_ctab;
       f.f0tab = c->d_f0tab;
       f.order = c->d_order;
+      f.ranked = c->d_ranked;
       f.mode = c->model.mode;
       f.disp = out->disp;
       f.mask = out->active_mask;
@@ -605,7 +609,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.negbeta = c->d_negbeta;
       f.c0m = c->d_c0m;
       if (!f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
-          !f.mask_woff || !f.pad_m || !f.g0a || !c->gemm.tiles || !c->gemm.h0bf16 ||
+          !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");
       int ts = timing_begin(c, K_FRONT, s);

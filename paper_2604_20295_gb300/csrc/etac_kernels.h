@@ -54,6 +54,7 @@ struct TablesArgs {
   float* omega;                 // [sum n^2] FP32 (optional)
   void* omega_bf16;             // [sum n^2] BF16 (optional)
   void* h0bf16;                 // [sum n][64] BF16 copy of h0 (optional)
+  float2* ranked;               // [64 * sum n] (f0 value, node as int bits) in rank order (optional)
 };
 cudaError_t launch_tables(const TablesArgs& a, int nmax, cudaStream_t s);
 
@@ -106,6 +107,7 @@ struct FrontArgs {
   const float* ctab;
   const float* f0tab;
   const int16_t* order;
+  const float2* ranked;         // per type and channel: (f0, node) in descending f0 order
   int mode;
   float* disp;
   uint8_t* mask;
@@ -119,7 +121,7 @@ struct FrontArgs {
   uint32_t* maskbits;
   const long long* mask_woff;
   int* pad_m;                   // [E*P] active count
-  float* g0a;                   // [E*P][64] channel maxima over active nodes
+  float* g0a;                   // [E*P][64] max-pooled global feature g0 of each pad
   void* negbeta;                // [E*P][64] BF16
   float4* c0m;                  // [E*P]
 };

@@ -10,9 +10,10 @@
 //   3. the encoder on the active nodes on tensor cores (E1 evaluated straight into the
 //      m16n8k16 A-fragment layout, E2 as BF16 MMAs with FP32 accumulation), channel maxima
 //      per pad written out.  Passive nodes need no encoder: their outputs are table entries.
-//   Three block barriers per pad.
-// front_global_kernel (one warp per pad): max-pool over the passive nodes through the
-//   per-channel table order, global MLP g = ReLU(G1 g0), the decoder's global half
+//   Four block barriers per pad.
+//   4. the max-pool over the passive nodes: the first passive node of each channel's table
+//      order (ranked f0 values), 32 ranks per warp-wide test.
+// front_global_kernel (one warp per pad): global MLP g = ReLU(G1 g0), the decoder's global half
 //   beta = D1[:, 64:] g, and the record the propagation GEMM's epilogue needs: -beta in BF16
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
 #include <cuda_bf16.h>
@@ -262,11 +263,49 @@ __global__ void __launch_bounds__(FT, 2) front_contact_kernel(FrontArgs a) {
         }
     }
     __syncthreads();
-    if (tid < H) {
-      float v = 0.f;
+    // max-pool over the passive nodes: the first passive node in each channel's descending
+    // order of f0; a warp tests 32 ranks per load for 8 channels at a time
+    {
+      float best[8];
+      bool done[8];
 #pragma unroll
-      for (int w = 0; w < FW; ++w) v = fmaxf(v, sRed[w * H + tid]);
-      a.g0a[(size_t)pad * H + tid] = v;
+      for (int c = 0; c < 8; ++c) {
+        best[c] = 0.f;
+        done[c] = false;
+      }
+      for (int r0 = 0; r0 < n; r0 += 32) {
+        const int r = r0 + lane;
+        float2 e[8];
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int u = warp * 8 + c;
+          e[c] = (!done[c] && r < n) ? __ldg(a.ranked + (size_t)H * o + (size_t)u * n + r)
+                                      : make_float2(0.f, __int_as_float(0));
+        }
+        bool all = true;
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          const int idx = __float_as_int(e[c].y);
+          const bool passive = !done[c] && r < n && !((sActBits[idx >> 5] >> (idx & 31)) & 1u);
+          const unsigned bal = __ballot_sync(0xffffffffu, passive);
+          if (bal) {
+            best[c] = __shfl_sync(0xffffffffu, e[c].x, __ffs(bal) - 1);
+            done[c] = true;
+          }
+          all &= done[c];
+        }
+        if (all) break;
+      }
+      if (lane < 8) {
+        float v = 0.f;
+#pragma unroll
+        for (int c = 0; c < 8; ++c)
+          if (c == lane) v = best[c];
+        const int u = warp * 8 + lane;
+#pragma unroll
+        for (int w = 0; w < FW; ++w) v = fmaxf(v, sRed[w * H + u]);
+        a.g0a[(size_t)pad * H + u] = v;
+      }
     }
   }
 }
@@ -297,26 +336,9 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
       if (lane == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
       continue;
     }
-    const int ty = a.pad_type[pad];
-    const int o = a.type_off[ty];
-    const int n = a.type_off[ty + 1] - o;
-    const long long woff = a.mask_woff[pad];
     float g0[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = lane + 32 * h;
-      float v = a.g0a[(size_t)pad * H + u];
-      // passive maximum: first passive node in this channel's descending order of f0
-      const int16_t* ord = a.order + (size_t)H * o + (size_t)u * n;
-      for (int r = 0; r < n; ++r) {
-        const int idx = ord[r];
-        if (!((a.maskbits[woff + (idx >> 5)] >> (idx & 31)) & 1u)) {
-          v = fmaxf(v, a.f0tab[(size_t)(o + idx) * H + u]);
-          break;
-        }
-      }
-      g0[h] = v;
-    }
+    g0[0] = a.g0a[(size_t)pad * H + lane];
+    g0[1] = a.g0a[(size_t)pad * H + 32 + lane];
     float g[2], beta[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {

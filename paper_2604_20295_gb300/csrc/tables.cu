@@ -68,6 +68,7 @@ __global__ void __launch_bounds__(256) tables_order_kernel(TablesArgs a) {
       rank += (w > v) || (w == v && j < i);
     }
     ord[rank] = (int16_t)i;
+    if (a.ranked) a.ranked[(size_t)H * o + (size_t)u * n + rank] = make_float2(v, __int_as_float(i));
   }
 }
 
