@@ -145,6 +145,14 @@ etac_status etac_step_backward(etac_ctx* ctx, const float* grad_disp, float* gra
                                float* grad_uhat, float* grad_penetration, float* grad_params,
                                void* stream);
 
+/* Chain rule from the pose gradient of etac_step_backward to the 7-float pose layout: given
+ * poses [count*7] (t, q) and their twist gradients [count*6] (dL/dt, dL/d omega with the
+ * left world-frame rotation increment), writes dL/d(pose) [count*7], where the quaternion
+ * part is the gradient with respect to the raw (not normalised) quaternion components.
+ * Device pointers; enqueued on `stream`. */
+etac_status etac_pose_grad_to_quat(const float* poses, const float* twist_grad, float* pose_grad,
+                                   int64_t count, void* stream);
+
 /* Reads and clears the device status word (synchronises `stream`).  *device_status receives
  * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE. */
 etac_status etac_poll_status(etac_ctx* ctx, int32_t* device_status, void* stream);

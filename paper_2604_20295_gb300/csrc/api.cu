@@ -75,6 +75,13 @@ struct etac_ctx {
   int front_grid = 0, gemm_grid = 0;
   bool bf16_ready = false;
   // profiling: event pairs around kernel launches
+  // reverse mode workspace
+  int* d_ws_idx = nullptr;
+  float4* d_ws_u = nullptr;
+  float4* d_ws_du = nullptr;
+  float* d_pose_part = nullptr;
+  float* d_param_part = nullptr;
+  int bwd_grid = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;       // 2 * ETAC_TIMING_SLOTS
   std::vector<int> ev_kernel;        // kernel id per used slot
@@ -83,8 +90,9 @@ struct etac_ctx {
 
 namespace {
 const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
-                              "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel"};
-enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_COUNT = 5 };
+                              "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel",
+                              "backward_kernel"};
+enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_COUNT = 6 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -143,7 +151,8 @@ void free_ctx(etac_ctx* c) {
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
                   c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
-                  c->d_g0a, c->d_ranked};
+                  c->d_g0a, c->d_ranked, c->d_ws_idx, c->d_ws_u,
+                  c->d_ws_du, c->d_pose_part, c->d_param_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -296,16 +305,18 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     if (e == cudaSuccess) e = dalloc(&c->d_order, tn * etac::H);
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate per-type tables");
   }
-  const bool need32 = desc->precision == ETAC_PREC_FP32;
+  const bool batched = desc->algo == ETAC_ALGO_BATCHED;
+  const bool need32 = batched && desc->precision == ETAC_PREC_FP32;
+  const bool need16 = batched && desc->precision == ETAC_PREC_BF16;
   if (need32 && !c->d_omega) {
     e = dalloc(&c->d_omega, om);
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate Omega table");
   }
-  if (!need32) {
+  if (need16) {
     etac_status st = setup_bf16(c, s);
     if (st != ETAC_OK) return st;
   }
-  if (!c->batched_grid) {
+  if (batched && !c->batched_grid) {
     int per_sm = 0;
     e = etac::batched_occupancy(c->nmax, c->K, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched occupancy");
@@ -325,9 +336,9 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   a.h0tab = c->d_h0tab;
   a.order = c->d_order;
   a.omega = need32 ? c->d_omega : nullptr;
-  a.omega_bf16 = need32 ? nullptr : c->d_omega_bf16;
-  a.h0bf16 = need32 ? nullptr : c->d_h0bf16;
-  a.ranked = need32 ? nullptr : c->d_ranked;
+  a.omega_bf16 = need16 ? c->d_omega_bf16 : nullptr;
+  a.h0bf16 = need16 ? c->d_h0bf16 : nullptr;
+  a.ranked = need16 ? c->d_ranked : nullptr;
   e = etac::launch_tables(a, c->nmax, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
   c->tables_ready = true;
@@ -506,9 +517,19 @@ etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float
     return fail(c, ETAC_ERR_INVALID_ARG, "alpha must be finite and > 0 (got %g)", alpha);
   ETAC_CUDA(c, cudaMemcpyAsync(c->d_params, params, sizeof(float) * etac::NPARAM,
                                cudaMemcpyDeviceToDevice, s), "copy params");
-  if (desc->algo == ETAC_ALGO_BATCHED) {
-    etac_status st = build_tables(c, desc, s);
-    if (st != ETAC_OK) return st;
+  etac_status st = build_tables(c, desc, s);   // also used by the reverse mode
+  if (st != ETAC_OK) return st;
+  if (!c->d_ws_idx) {
+    const size_t np = (size_t)c->E * c->P;
+    if (etac::backward_smem_bytes(c->nmax, c->K) > 227 * 1024)
+      return fail(c, ETAC_ERR_UNSUPPORTED, "pad type too large for the reverse mode");
+    c->bwd_grid = c->num_sms;
+    cudaError_t e = dalloc(&c->d_ws_idx, (size_t)c->N);
+    if (e == cudaSuccess) e = dalloc(&c->d_ws_u, (size_t)c->N);
+    if (e == cudaSuccess) e = dalloc(&c->d_ws_du, (size_t)c->N);
+    if (e == cudaSuccess) e = dalloc(&c->d_pose_part, np * c->K * 6);
+    if (e == cudaSuccess) e = dalloc(&c->d_param_part, (size_t)c->bwd_grid * etac::NPARAM);
+    if (e != cudaSuccess) return cuda_fail(c, e, "reverse-mode workspace");
   }
   c->model = *desc;
   c->has_model = true;
@@ -669,11 +690,62 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
 etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_obj_pose,
                                float* grad_uhat, float* grad_penetration, float* grad_params,
                                void* stream) {
-  (void)grad_disp; (void)grad_obj_pose; (void)grad_uhat; (void)grad_penetration;
-  (void)grad_params; (void)stream;
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->has_forward) return fail(c, ETAC_ERR_STATE, "no forward step to differentiate");
-  return fail(c, ETAC_ERR_UNSUPPORTED, "reverse mode not built yet");
+  if (!grad_disp) return fail(c, ETAC_ERR_INVALID_ARG, "grad_disp is NULL");
+  if (!aligned(grad_disp, 4) || (grad_obj_pose && !aligned(grad_obj_pose, 4)) ||
+      (grad_uhat && !aligned(grad_uhat, 4)) || (grad_penetration && !aligned(grad_penetration, 4)) ||
+      (grad_params && !aligned(grad_params, 4)))
+    return fail(c, ETAC_ERR_INVALID_ARG, "pointer not 4-byte aligned");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  etac::BackwardArgs b{};
+  b.type_pos = c->d_type_pos;
+  b.type_nrm = c->d_type_nrm;
+  b.type_pmax = c->d_type_pmax;
+  b.type_off = c->d_type_off;
+  b.pad_type = c->d_pad_type;
+  b.pad_off = c->d_pad_off;
+  b.item_pad = c->d_item_pad;
+  b.num_items = c->E * c->P;
+  b.E = c->E;
+  b.P = c->P;
+  b.K = c->K;
+  b.nmax = c->nmax;
+  b.obj_type = c->d_saved_obj_type;
+  b.obj_dims = c->d_saved_obj_dims;
+  b.obj_pose = c->d_saved_obj_pose;
+  b.pad_pose = c->d_saved_pad_pose;
+  b.params = c->d_params;
+  b.ctab = c->d_ctab;
+  b.f0tab = c->d_f0tab;
+  b.h0tab = c->d_h0tab;
+  b.order = c->d_order;
+  b.mode = c->model.mode;
+  b.grad_disp = grad_disp;
+  b.grad_uhat = grad_uhat;
+  b.grad_pen = grad_penetration;
+  b.grad_params = grad_params;
+  b.grad_obj_pose = grad_obj_pose;
+  b.ws_idx = c->d_ws_idx;
+  b.ws_u = c->d_ws_u;
+  b.ws_du = c->d_ws_du;
+  b.pose_part = c->d_pose_part;
+  b.param_part = c->d_param_part;
+  const int ts = timing_begin(c, K_BWD, s);
+  ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
+  timing_end(c, ts, s);
+  return ETAC_OK;
+}
+
+etac_status etac_pose_grad_to_quat(const float* poses, const float* twist_grad, float* pose_grad,
+                                   int64_t count, void* stream) {
+  if (!poses || !twist_grad || !pose_grad || count < 0 || !aligned(poses, 4) ||
+      !aligned(twist_grad, 4) || !aligned(pose_grad, 4))
+    return fail(nullptr, ETAC_ERR_INVALID_ARG, "etac_pose_grad_to_quat: bad argument");
+  cudaError_t e = etac::launch_pose_grad_to_quat(poses, twist_grad, pose_grad, (long long)count,
+                                                 reinterpret_cast<cudaStream_t>(stream));
+  if (e != cudaSuccess) return cuda_fail(nullptr, e, "etac_pose_grad_to_quat");
+  return ETAC_OK;
 }
 
 etac_status etac_poll_status(etac_ctx* c, int32_t* device_status, void* stream) {

@@ -172,3 +172,43 @@ cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s);
 size_t prop_gemm_smem_bytes();
 
 }  // namespace etac
+
+namespace etac {
+
+// ---------------------------------------------------------------- reverse mode (FP32)
+struct BackwardArgs {
+  const float* type_pos;
+  const float* type_nrm;
+  const float* type_pmax;
+  const int* type_off;
+  const int* pad_type;
+  const long long* pad_off;
+  const int* item_pad;
+  int num_items, E, P, K, nmax;
+  const int* obj_type;
+  const float* obj_dims;
+  const float* obj_pose;
+  const float* pad_pose;
+  const float* params;
+  const float* ctab;
+  const float* f0tab;
+  const float* h0tab;
+  const int16_t* order;
+  int mode;
+  const float* grad_disp;      // [N*3]
+  float* grad_uhat;            // [N*3] or null
+  float* grad_pen;             // [N] or null
+  float* grad_params;          // [NPARAM] or null
+  float* grad_obj_pose;        // [E*K*6] or null
+  int* ws_idx;                 // [N] active lists (per pad at its node offset)
+  float4* ws_u;                // [N]
+  float4* ws_du;               // [N]
+  float* pose_part;            // [E*P*K*6]
+  float* param_part;           // [grid * NPARAM]
+};
+size_t backward_smem_bytes(int nmax, int K);
+cudaError_t launch_backward(const BackwardArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_pose_grad_to_quat(const float* poses, const float* tw, float* out,
+                                     long long count, cudaStream_t s);
+
+}  // namespace etac

@@ -27,7 +27,7 @@ HIDDEN = 64
 EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
            "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
            "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
-           "etac_enable_timing", "etac_kernel_times")
+           "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat")
 
 _vp = ctypes.c_void_p
 
@@ -106,6 +106,8 @@ def lib():
         L.etac_enable_timing.argtypes = [_vp, ctypes.c_int32]
         L.etac_kernel_times.restype = ctypes.c_int
         L.etac_kernel_times.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.etac_pose_grad_to_quat.restype = ctypes.c_int
+        L.etac_pose_grad_to_quat.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
         L.etac_step_forward_noalloc.restype = ctypes.c_int
         L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
         _lib = L
@@ -188,6 +190,12 @@ def etac_kernel_times(ctx: int) -> dict:
             for i in range(n.value)}
 
 
+def etac_pose_grad_to_quat(poses: int, twist_grad: int, pose_grad: int, count: int,
+                           stream: int = 0) -> None:
+    _check(None, lib().etac_pose_grad_to_quat(poses, twist_grad, pose_grad, count, stream),
+           "etac_pose_grad_to_quat")
+
+
 def etac_step_forward_noalloc(pads: etac_noalloc_pads, mode: int, params: int,
                               sin: etac_step_in, sout: etac_step_out, stream: int = 0) -> None:
     """Batched FP32 forward that allocates nothing (scratch in a static device array)."""
@@ -254,6 +262,29 @@ class TactileSim:
                           self.torch.cuda.current_stream(self.device).cuda_stream)
         return self.disp
 
+    def backward(self, grad_disp, want=("params", "obj_pose", "uhat", "pen")):
+        """Reverse mode of the last step for dL/d(disp) = grad_disp [N,3] (device tensor).
+        Returns a dict with any of: params [P], obj_pose [E*K, 6] (dL/dt, dL/d omega),
+        uhat [N, 3], pen [N]."""
+        torch = self.torch
+        g = grad_disp.contiguous().to(torch.float32)
+        out = {}
+        f32 = dict(dtype=torch.float32, device=self.device)
+        sc = self.scene
+        if "params" in want:
+            out["params"] = torch.empty(self.params.numel(), **f32)
+        if "obj_pose" in want:
+            out["obj_pose"] = torch.empty(sc.num_envs * sc.max_objects, 6, **f32)
+        if "uhat" in want:
+            out["uhat"] = torch.empty(self.N, 3, **f32)
+        if "pen" in want:
+            out["pen"] = torch.empty(self.N, **f32)
+        ptr = lambda k: out[k].data_ptr() if k in out else 0
+        etac_step_backward(self.ctx, g.data_ptr(), ptr("obj_pose"), ptr("uhat"), ptr("pen"),
+                           ptr("params"), torch.cuda.current_stream(self.device).cuda_stream)
+        self._grad_keepalive = g
+        return out
+
     def poll_status(self) -> int:
         return etac_poll_status(self.ctx, self.torch.cuda.current_stream(self.device).cuda_stream)
 
@@ -272,3 +303,39 @@ class TactileSim:
 # (algo, precision, relative tolerance) exercised by the smoke check
 SMOKE_CONFIGS = ((ALGO_PLAIN, PREC_FP32, 1e-5), (ALGO_BATCHED, PREC_FP32, 1e-5),
                  (ALGO_BATCHED, PREC_BF16, 2e-2))
+
+
+def make_step_function():
+    """torch.autograd.Function over one tactile step: (params, obj_pose) -> displacement.
+
+    ``ETacStep.apply(sim, params, obj_pose)`` copies params and poses into ``sim`` (the
+    model is re-set when params change), runs the forward and returns a copy of the
+    displacement; backward returns dL/dparams and dL/d(obj_pose) in the 7-float pose layout.
+    All arithmetic runs in the library's kernels."""
+    import torch
+
+    class ETacStep(torch.autograd.Function):
+        @staticmethod
+        def forward(ctx, sim, params, obj_pose):
+            stream = torch.cuda.current_stream(sim.device).cuda_stream
+            p = params.detach().contiguous().to(torch.float32)
+            if getattr(sim, "params", None) is None or not torch.equal(sim.params, p):
+                m = sim.model
+                sim.set_model(p, m.mode, m.precision, m.algo)
+            sim.obj_pose.copy_(obj_pose.detach().reshape(-1))
+            disp = sim.step().clone()
+            ctx.sim = sim
+            ctx.stream = stream
+            return disp
+
+        @staticmethod
+        def backward(ctx, grad_disp):
+            sim = ctx.sim
+            g = sim.backward(grad_disp, want=("params", "obj_pose"))
+            pose7 = torch.empty(sim.obj_pose.numel(), dtype=torch.float32, device=sim.device)
+            etac_pose_grad_to_quat(sim.obj_pose.data_ptr(), g["obj_pose"].data_ptr(),
+                                   pose7.data_ptr(), sim.obj_pose.numel() // 7,
+                                   torch.cuda.current_stream(sim.device).cuda_stream)
+            return None, g["params"], pose7.reshape(-1)
+
+    return ETacStep
