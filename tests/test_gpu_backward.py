@@ -57,6 +57,12 @@ SCENES = {
 }
 
 
+# A random-sign upstream gradient makes every parameter gradient a sum of ~N terms that
+# cancel down to ~sqrt(N) of their absolute mass, so FP32 accumulation carries a relative
+# error of about N * 2^-24 (~7e-4 for the 12k-node scenes); the bound below allows for that.
+ADJ_REL = 2e-3
+
+
 @pytest.mark.parametrize("name", sorted(SCENES))
 @pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY])
 def test_backward_matches_oracle(name, mode):
@@ -68,11 +74,13 @@ def test_backward_matches_oracle(name, mode):
     ref_f, _ = PT.oracle_forward_matching(sc, th, mode, got["mask"])
     ref = O.backward(sc, th, G, mode=mode, mask_override=got["mask"])
     errs = layer_errors(got["params"], ref["params"])
-    bad = {k: v for k, v in errs.items() if v > 2e-4 and np.linalg.norm(ref["params"]) > 0}
+    bad = {k: v for k, v in errs.items() if v > ADJ_REL and np.linalg.norm(ref["params"]) > 0}
+    print(f"{name} mode {mode}: worst layer rel err {max(errs.values()):.2e}, pose "
+          f"{rel_err(got['obj_pose'], ref['obj_pose']):.2e}, uhat {rel_err(got['uhat'], ref['uhat']):.2e}")
     assert not bad, bad
-    assert rel_err(got["obj_pose"], ref["obj_pose"]) < 2e-4
-    assert rel_err(got["uhat"], ref["uhat"]) < 2e-4
-    assert rel_err(got["pen"], ref["pen"]) < 2e-4
+    assert rel_err(got["obj_pose"], ref["obj_pose"]) < ADJ_REL
+    assert rel_err(got["uhat"], ref["uhat"]) < ADJ_REL
+    assert rel_err(got["pen"], ref["pen"]) < ADJ_REL
 
 
 def _f64_forward(sim, sc, th, obj_pose):
