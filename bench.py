@@ -195,6 +195,7 @@ def main():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
+    ap.add_argument("--no-bwd", action="store_true")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -306,6 +307,44 @@ def main():
         compare[f"{args.precision}_{args.algo}"] = {"value": value, "unit": UNIT,
                                                     "ms_per_step": ms_per_step}
 
+    # ---- reverse mode (FP32 adjoint): bwd/fwd on this workload and on the 1,024-env layout
+    # of 16x16 flat pads (forward FP32 batched there)
+    bwd = None
+    if not args.no_bwd:
+        def time_bwd(s_, G_, k):
+            for _ in range(2):
+                s_.backward(G_)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            ms = []
+            for _ in range(k):
+                flush.fill_(1)
+                e0.record(stream)
+                s_.backward(G_)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                ms.append(e0.elapsed_time(e1))
+            return sum(ms) / k
+        gen = torch.Generator(device=dev).manual_seed(3)
+        G = torch.randn(sim.disp.shape, device=dev, generator=gen)
+        sim.step(**step_kw)
+        b_ms = time_bwd(sim, G, 3)
+        small = I.sphere_press_scene(1024, seed=7)
+        s4 = X.TactileSim(small, device=dev)
+        s4.set_model(theta, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+        for _ in range(3):
+            s4.step(**step_kw)
+        f4 = timed_steps(s4, 10, stream, flush, torch, step_kw)
+        G4 = torch.randn(s4.disp.shape, device=dev, generator=gen)
+        b4 = time_bwd(s4, G4, 10)
+        s4.close()
+        bwd = {"workload": {"fwd_ms": ms_per_step, "bwd_ms": b_ms, "bwd_fwd": b_ms / ms_per_step,
+                            "fwd": f"{args.precision} {args.algo}", "bwd": "fp32 adjoint"},
+               "flat16x16_1024env": {"fwd_ms": sum(f4) / len(f4), "bwd_ms": b4,
+                                     "bwd_fwd": b4 / (sum(f4) / len(f4)),
+                                     "fwd": "fp32 batched", "bwd": "fp32 adjoint"}}
+
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     kern = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1)} for k, v in ktimes.items()}
@@ -379,6 +418,7 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "error_vs_oracle": err, "rungs": compare, "kernels": kern,
+            "bwd_fwd": bwd,
             "active_fraction": work["active"] / nodes,
             "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
     if rank == 0:
