@@ -237,7 +237,6 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
-  if (e == cudaSuccess) e = dalloc(&c->d_ranked, tn * etac::H);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
@@ -303,6 +302,7 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     if (e == cudaSuccess) e = dalloc(&c->d_f0tab, tn * etac::H);
     if (e == cudaSuccess) e = dalloc(&c->d_h0tab, tn * etac::H);
     if (e == cudaSuccess) e = dalloc(&c->d_order, tn * etac::H);
+    if (e == cudaSuccess) e = dalloc(&c->d_ranked, tn * etac::H);
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate per-type tables");
   }
   const bool batched = desc->algo == ETAC_ALGO_BATCHED;
@@ -338,7 +338,7 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   a.omega = need32 ? c->d_omega : nullptr;
   a.omega_bf16 = need16 ? c->d_omega_bf16 : nullptr;
   a.h0bf16 = need16 ? c->d_h0bf16 : nullptr;
-  a.ranked = need16 ? c->d_ranked : nullptr;
+  a.ranked = c->d_ranked;
   e = etac::launch_tables(a, c->nmax, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
   c->tables_ready = true;
@@ -720,6 +720,7 @@ etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_
   b.f0tab = c->d_f0tab;
   b.h0tab = c->d_h0tab;
   b.order = c->d_order;
+  b.ranked = c->d_ranked;
   b.mode = c->model.mode;
   b.grad_disp = grad_disp;
   b.grad_uhat = grad_uhat;

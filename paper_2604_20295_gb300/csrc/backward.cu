@@ -31,11 +31,13 @@ namespace {
 
 constexpr int BB = 256;
 constexpr int BBW = BB / 32;
-constexpr int CH = 64;   // nodes per chunk
+constexpr int CH = 64;        // nodes per chunk
+constexpr int LD = H + 4;     // padded row stride of staged 64 x 64 tiles (16-byte aligned)
 
 // shared-memory layout
 struct BwdSmem {
-  size_t acc, wdf, w2, da, db, dc, xr, gr, vec, bits, route, rnode, cnt, po, total;
+  size_t acc, wdf, w2, w2t, sp, sq, sm, sd, sdt, xr, gr, vec, bits, route, rnode, best, cnt, po,
+      total;
   __host__ __device__ BwdSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -44,28 +46,55 @@ struct BwdSmem {
       return r;
     };
     acc = take(sizeof(float) * NPARAM);
-    wdf = take(sizeof(float) * H * H);      // D1[:, 0:64] as [c][k]
-    w2 = take(sizeof(float) * H * H);       // E2 as [c][k]
-    da = take(sizeof(float) * CH * H);      // dA3 / dA1 staging
-    db = take(sizeof(float) * CH * H);      // F0 / Z1 staging
-    dc = take(sizeof(float) * CH * H);      // Z3 / dA2 staging
-    xr = take(sizeof(float) * CH * 12);     // per-row inputs X (9) and flags
+    wdf = take(sizeof(float) * H * LD);     // D1[:, 0:64] as [c][k]
+    w2 = take(sizeof(float) * H * LD);      // E2 as [c][k]
+    w2t = take(sizeof(float) * H * LD);     // E2 transposed, [k][c]
+    sp = take(sizeof(float) * CH * LD);     // staging tiles (see the phases)
+    sq = take(sizeof(float) * CH * LD);
+    sm = take(sizeof(float) * CH * LD);
+    sd = take(sizeof(float) * CH * LD);
+    sdt = take(sizeof(float) * CH * LD);
+    xr = take(sizeof(float) * CH * 12);     // per-row inputs X (9), valid flag, node
     gr = take(sizeof(float4) * CH);         // per-row G
-    vec = take(sizeof(float) * 16 * H);     // g0, ag, g, beta, S, dg, dag, dg0, alpha partials ...
+    vec = take(sizeof(float) * 16 * H);     // g0, ag, g, beta, S, dg0, dag, tmp, alpha partials
     bits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
     route = take(sizeof(int) * H);          // argmax node per channel
     rnode = take(sizeof(int) * (H + 4));    // distinct active argmax nodes
+    best = take(sizeof(float2) * 16 * H);   // per (row block, channel) best (value, node)
     cnt = take(sizeof(int) * 16);
     po = take(sizeof(PadObj) * (size_t)K);
     total = o;
   }
 };
 
-// vec slots (each H floats)
-enum { V_G0 = 0, V_AG = 1, V_G = 2, V_BETA = 3, V_S = 4, V_DG0 = 5, V_DAG = 6, V_GMAXA = 7,
-       V_GMAXP = 8, V_TMP = 9, V_ALPHA = 10 };
+enum { V_G0 = 0, V_AG = 1, V_G = 2, V_BETA = 3, V_S = 4, V_DG0 = 5, V_DAG = 6, V_TMP = 9,
+       V_ALPHA = 10, V_BV = 11, V_BI = 12 };
 
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
+
+// acc[i][j] += sum_k A[k][4 ti + i] * B[k][4 tj + j], both operands k-major with stride LD
+__device__ __forceinline__ void tile_acc(const float* A, const float* B, int ti, int tj,
+                                         float (&acc)[4][4]) {
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(A + k * LD + 4 * ti);
+    const float4 b = *reinterpret_cast<const float4*>(B + k * LD + 4 * tj);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+__device__ __forceinline__ int find_slot(const int* idx, int m, int i) {
+  int lo = 0, hi = m - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi) >> 1;
+    if (idx[mid] < i) lo = mid + 1; else hi = mid;
+  }
+  return lo;
+}
 
 __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
@@ -73,15 +102,19 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
   float* sAcc = reinterpret_cast<float*>(smem + L.acc);      // per-CTA parameter gradient
   float* sWdf = reinterpret_cast<float*>(smem + L.wdf);
   float* sW2 = reinterpret_cast<float*>(smem + L.w2);
-  float* sA = reinterpret_cast<float*>(smem + L.da);
-  float* sB = reinterpret_cast<float*>(smem + L.db);
-  float* sC = reinterpret_cast<float*>(smem + L.dc);
-  float* sX = reinterpret_cast<float*>(smem + L.xr);         // [CH][12]: X(9), valid, node
+  float* sW2T = reinterpret_cast<float*>(smem + L.w2t);
+  float* sP = reinterpret_cast<float*>(smem + L.sp);
+  float* sQ = reinterpret_cast<float*>(smem + L.sq);
+  float* sM = reinterpret_cast<float*>(smem + L.sm);
+  float* sD = reinterpret_cast<float*>(smem + L.sd);
+  float* sDT = reinterpret_cast<float*>(smem + L.sdt);
+  float* sX = reinterpret_cast<float*>(smem + L.xr);
   float4* sGr = reinterpret_cast<float4*>(smem + L.gr);
   float* sV = reinterpret_cast<float*>(smem + L.vec);
   uint32_t* sBits = reinterpret_cast<uint32_t*>(smem + L.bits);
   int* sRoute = reinterpret_cast<int*>(smem + L.route);
   int* sRNode = reinterpret_cast<int*>(smem + L.rnode);
+  float2* sBest = reinterpret_cast<float2*>(smem + L.best);
   int* sCnt = reinterpret_cast<int*>(smem + L.cnt);
   PadObj* spo = reinterpret_cast<PadObj*>(smem + L.po);
 
@@ -91,12 +124,19 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
   for (int i = tid; i < NPARAM; i += BB) sAcc[i] = 0.f;
   for (int i = tid; i < H * H; i += BB) {
     const int c = i >> 6, k = i & (H - 1);
-    sWdf[i] = W[OFF_WD + c * 2 * H + k];
-    sW2[i] = W[OFF_W2 + c * H + k];
+    sWdf[c * LD + k] = W[OFF_WD + c * 2 * H + k];
+    sW2[c * LD + k] = W[OFF_W2 + c * H + k];
+    sW2T[k * LD + c] = W[OFF_W2 + c * H + k];
   }
-  // thread -> (row r, 16-channel block) for chunk work; (c, 16-column block) for accumulators
+  // staging threads: row tr, 16 columns from tq; GEMM threads: 4 x 4 tile (ti, tj)
   const int tr = tid >> 2, tq = (tid & 3) * 16;
+  const int ti = tid >> 4, tj = tid & 15;
   const bool use_l = a.mode != MODE_RESIDUAL_ONLY, use_r = a.mode != MODE_LINEAR_ONLY;
+  float accWdf[4][4], accW2[4][4];   // per-CTA gradient tiles of D1[:, 0:64] and E2
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) accWdf[i][j] = accW2[i][j] = 0.f;
 
   for (int item = blockIdx.x; item < a.num_items; item += gridDim.x) {
     __syncthreads();
@@ -109,8 +149,8 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
     const long long base = a.pad_off[pad];
     const float* tpos = a.type_pos + 3 * (size_t)o;
     const float* tnrm = a.type_nrm + 3 * (size_t)o;
-    int* wIdx = a.ws_idx + base;         // active node list of this pad
-    float4* wU = a.ws_u + base;          // their u_hat
+    int* wIdx = a.ws_idx + base;         // active node list of this pad (node order)
+    float4* wU = a.ws_u + base;          // their u_hat (w = phi)
     float4* wDU = a.ws_du + base;        // their dL/du_hat
     if (tid == 0) {
       sCnt[0] = 0;   // active count
@@ -138,7 +178,7 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
     __syncthreads();
     const bool invalid = sCnt[1] != 0;
 
-    // ---- 0a. contact (node order kept in the active list for a fixed summation order)
+    // ---- 0a. contact (the active list keeps node order: fixed summation order)
     for (int r0 = 0; r0 < n; r0 += BB) {
       const int i = r0 + tid;
       NodeContact c;
@@ -185,76 +225,101 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
     }
 
     if (use_r) {
-      // ---- 0b. forward of the network: active-node encoder maxima (lowest index on ties)
-      // thread (tr, tq): active row chunk, 16 channels; values and argmax per channel
-      float bestv[16];
-      int besti[16];
-#pragma unroll
-      for (int x = 0; x < 16; ++x) {
-        bestv[x] = -1.f;
-        besti[x] = 0x7fffffff;
+      // ---- 0b. forward of the network: encoder of the active nodes (4 x 4 GEMM tiles),
+      // channel maxima and their lowest-index argmax
+      if (tid < H) {
+        sV[V_BV * H + tid] = -1.f;
+        reinterpret_cast<int*>(sV)[V_BI * H + tid] = 0x7fffffff;
       }
       for (int s0 = 0; s0 < m; s0 += CH) {
-        const int s = s0 + tr;
-        const bool valid = s < m;
-        const int i = valid ? wIdx[s] : 0;
-        const float4 u = valid ? wU[s] : make_float4(0.f, 0.f, 0.f, 0.f);
-        // z1 row i staged in sB (16 channels by each of the row's 4 threads)
-        for (int x = 0; x < 16; ++x) {
-          const int c = tq + x;
-          const float a1 = a.ctab[(size_t)(o + i) * H + c] + W[OFF_W1 + c * NIN + 6] * u.x +
-                           W[OFF_W1 + c * NIN + 7] * u.y + W[OFF_W1 + c * NIN + 8] * u.z;
-          sB[tr * H + c] = relu(a1);
-        }
-        __syncthreads();
-        for (int x = 0; x < 16; ++x) {
-          const int c = tq + x;
-          float acc = W[OFF_B2 + c];
-          for (int k = 0; k < H; ++k) acc = fmaf(sW2[c * H + k], sB[tr * H + k], acc);
-          const float f = relu(acc);
-          if (valid && (f > bestv[x] || (f == bestv[x] && i < besti[x]))) {
-            bestv[x] = f;
-            besti[x] = i;
+        {
+          const int s = s0 + tr;
+          const bool valid = s < m;
+          const int i = valid ? wIdx[s] : 0;
+          const float4 u = valid ? wU[s] : make_float4(0.f, 0.f, 0.f, 0.f);
+          for (int x = 0; x < 16; ++x) {
+            const int c = tq + x;
+            const float a1 = a.ctab[(size_t)(o + i) * H + c] + W[OFF_W1 + c * NIN + 6] * u.x +
+                             W[OFF_W1 + c * NIN + 7] * u.y + W[OFF_W1 + c * NIN + 8] * u.z;
+            sP[c * LD + tr] = relu(a1);   // Z1^T [k][r]
           }
         }
         __syncthreads();
-      }
-      // reduce over the 64 row slots that share a channel block: stage in sA / sC
-      for (int x = 0; x < 16; ++x) {
-        sA[tr * H + tq + x] = bestv[x];
-        reinterpret_cast<int*>(sC)[tr * H + tq + x] = besti[x];
-      }
-      __syncthreads();
-      if (tid < H) {
-        const int c = tid;
-        float bv = -1.f;
-        int bi = 0x7fffffff;
-        for (int r = 0; r < CH; ++r) {
-          const float v = sA[r * H + c];
-          const int ii = reinterpret_cast<int*>(sC)[r * H + c];
-          if (v > bv || (v == bv && ii < bi)) {
-            bv = v;
-            bi = ii;
+        float acc[4][4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+        tile_acc(sP, sW2T, ti, tj, acc);   // a2[r][c] - b2[c], rows 4ti.., channels 4tj..
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int c = 4 * tj + j;
+          float bv = -1.f;
+          int bi = 0x7fffffff;
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int s = s0 + 4 * ti + i;
+            if (s < m) {
+              const float f = relu(acc[i][j] + W[OFF_B2 + c]);
+              const int node = wIdx[s];
+              if (f > bv || (f == bv && node < bi)) {
+                bv = f;
+                bi = node;
+              }
+            }
           }
+          sBest[ti * H + c] = make_float2(bv, __int_as_float(bi));
         }
-        // passive candidate: first passive node in the channel's order (ties: lower index)
-        const int16_t* ord = a.order + (size_t)H * o + (size_t)c * n;
+        __syncthreads();
+        if (tid < H) {
+          float bv = sV[V_BV * H + tid];
+          int bi = reinterpret_cast<int*>(sV)[V_BI * H + tid];
+          for (int r = 0; r < 16; ++r) {
+            const float2 e = sBest[r * H + tid];
+            const int node = __float_as_int(e.y);
+            if (e.x > bv || (e.x == bv && node < bi)) {
+              bv = e.x;
+              bi = node;
+            }
+          }
+          sV[V_BV * H + tid] = bv;
+          reinterpret_cast<int*>(sV)[V_BI * H + tid] = bi;
+        }
+        __syncthreads();
+      }
+      // passive candidate: first passive node in each channel's ranked order (ties to the
+      // lower index), 32 ranks per warp-wide test, 8 channels per warp
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = warp * 8 + cc;
         float pv = -1.f;
         int pi = 0x7fffffff;
-        for (int r = 0; r < n; ++r) {
-          const int idx = ord[r];
-          if (!((sBits[idx >> 5] >> (idx & 31)) & 1u)) {
-            pv = a.f0tab[(size_t)(o + idx) * H + c];
-            pi = idx;
+        for (int r0 = 0; r0 < n; r0 += 32) {
+          const int r = r0 + lane;
+          float2 e = make_float2(0.f, __int_as_float(0));
+          bool passive = false;
+          if (r < n) {
+            e = a.ranked[(size_t)H * o + (size_t)c * n + r];
+            const int idx = __float_as_int(e.y);
+            passive = !((sBits[idx >> 5] >> (idx & 31)) & 1u);
+          }
+          const unsigned bal = __ballot_sync(0xffffffffu, passive);
+          if (bal) {
+            const int src = __ffs(bal) - 1;
+            pv = __shfl_sync(0xffffffffu, e.x, src);
+            pi = __float_as_int(__shfl_sync(0xffffffffu, e.y, src));
             break;
           }
         }
-        if (pv > bv || (pv == bv && pi < bi)) {
-          bv = pv;
-          bi = pi;
+        if (lane == 0) {
+          float bv = sV[V_BV * H + c];
+          int bi = reinterpret_cast<int*>(sV)[V_BI * H + c];
+          if (pv > bv || (pv == bv && pi < bi)) {
+            bv = pv;
+            bi = pi;
+          }
+          sV[V_G0 * H + c] = bv;
+          sRoute[c] = bi;
         }
-        sV[V_G0 * H + c] = bv;
-        sRoute[c] = bi;
       }
       __syncthreads();
       if (tid < H) {
@@ -295,47 +360,35 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
               z3 = relu(h);
               f0 = a.f0tab[(size_t)(o + i) * H + c];
             }
-            sA[tr * H + c] = da3;
-            sC[tr * H + c] = z3;
-            sB[tr * H + c] = f0;
+            sD[tr * LD + c] = da3;   // dA3 [r][c]
+            sM[tr * LD + c] = z3;    // Z3 [r][c]
+            sQ[tr * LD + c] = f0;    // F0 [r][k]
           }
         }
         __syncthreads();
-        {
-          // dD1[:, 0:64] (c = tr, k in my block) += sum_r dA3[r][c] F0[r][k]
-          float acc[16];
-#pragma unroll
-          for (int x = 0; x < 16; ++x) acc[x] = 0.f;
+        tile_acc(sD, sQ, ti, tj, accWdf);   // dD1_f[c][k] += sum_r dA3[r][c] F0[r][k]
+        if (tid < H) {
+          float sd = 0.f;
+          for (int r = 0; r < CH; ++r) sd += sD[r * LD + tid];
+          sAcc[OFF_BD + tid] += sd;
+          sV[V_S * H + tid] += sd;
+        }
+        if (tid < 3 * H) {
+          const int q = tid / H, c = tid % H;
+          float s2 = 0.f;
           for (int r = 0; r < CH; ++r) {
-            const float d = sA[r * H + tr];
-#pragma unroll
-            for (int x = 0; x < 16; ++x) acc[x] = fmaf(d, sB[r * H + tq + x], acc[x]);
+            const float4 g = sGr[r];
+            s2 = fmaf(q == 0 ? g.x : (q == 1 ? g.y : g.z), sM[r * LD + c], s2);
           }
-#pragma unroll
-          for (int x = 0; x < 16; ++x) sAcc[OFF_WD + tr * 2 * H + tq + x] += acc[x];
-          if (tid < H) {
-            float sd = 0.f;
-            for (int r = 0; r < CH; ++r) sd += sA[r * H + tid];
-            sAcc[OFF_BD + tid] += sd;
-            sV[V_S * H + tid] += sd;
+          sAcc[OFF_W4 + q * H + c] += s2;
+        }
+        if (tid < 3) {
+          float sb = 0.f;
+          for (int r = 0; r < CH; ++r) {
+            const float4 g = sGr[r];
+            sb += tid == 0 ? g.x : (tid == 1 ? g.y : g.z);
           }
-          if (tid < 3 * H) {
-            const int q = tid / H, c = tid % H;
-            float s2 = 0.f;
-            for (int r = 0; r < CH; ++r) {
-              const float4 g = sGr[r];
-              s2 = fmaf(q == 0 ? g.x : (q == 1 ? g.y : g.z), sC[r * H + c], s2);
-            }
-            sAcc[OFF_W4 + q * H + c] += s2;
-          }
-          if (tid < 3) {
-            float sb = 0.f;
-            for (int r = 0; r < CH; ++r) {
-              const float4 g = sGr[r];
-              sb += tid == 0 ? g.x : (tid == 1 ? g.y : g.z);
-            }
-            sAcc[OFF_B4 + tid] += sb;
-          }
+          sAcc[OFF_B4 + tid] += sb;
         }
         __syncthreads();
       }
@@ -348,7 +401,6 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
       }
       __syncthreads();
       {
-        // dD1[:, 64:] += S g^T ; dG1 += dag g0^T   (row tr, my 16 columns)
         const float sr = sV[V_S * H + tr], dr = sV[V_DAG * H + tr];
 #pragma unroll
         for (int x = 0; x < 16; ++x) {
@@ -364,7 +416,6 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
         sV[V_DG0 * H + tid] = dg0;
       }
       __syncthreads();
-      // distinct active argmax nodes (their encoder gradient is the routed one only)
       if (tid == 0) {
         int cnt = 0;
         for (int c = 0; c < H; ++c) {
@@ -393,15 +444,7 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
           } else {
             valid = tr < sCnt[2];
             i = valid ? sRNode[tr] : 0;
-            if (valid) {
-              // u_hat of this active node (search the node-ordered active list)
-              int lo = 0, hi = m - 1;
-              while (lo < hi) {
-                const int mid = (lo + hi) >> 1;
-                if (wIdx[mid] < i) lo = mid + 1; else hi = mid;
-              }
-              u = wU[lo];
-            }
+            if (valid) u = wU[find_slot(wIdx, m, i)];
           }
           if (tq == 0) {
             float* xr = sX + tr * 12;
@@ -415,7 +458,6 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
             xr[9] = valid ? 1.f : 0.f;
             xr[10] = __int_as_float(i);
           }
-          // dA3 of this row (passive rows), z1 = ReLU(a1), a1 = c_i + W1u u_hat
           float G0 = 0.f, G1 = 0.f, G2 = 0.f;
           if (valid && !act_chunk) {
             const float* G = a.grad_disp + 3 * (base + i);
@@ -425,72 +467,92 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
           }
           for (int x = 0; x < 16; ++x) {
             const int c = tq + x;
-            float da3 = 0.f, z1 = 0.f;
+            float da3 = 0.f, z1 = 0.f, f0 = 0.f;
             if (valid) {
               if (!act_chunk) {
                 const float h = a.h0tab[(size_t)(o + i) * H + c] + sV[V_BETA * H + c];
                 const float dz3 = W[OFF_W4 + c] * G0 + W[OFF_W4 + H + c] * G1 + W[OFF_W4 + 2 * H + c] * G2;
                 da3 = h > 0.f ? dz3 : 0.f;
+                f0 = a.f0tab[(size_t)(o + i) * H + c];   // passive: f0 > 0 <=> a2 > 0
               }
               const float a1 = a.ctab[(size_t)(o + i) * H + c] + W[OFF_W1 + c * NIN + 6] * u.x +
                                W[OFF_W1 + c * NIN + 7] * u.y + W[OFF_W1 + c * NIN + 8] * u.z;
               z1 = relu(a1);
             }
-            sA[tr * H + c] = da3;
-            sB[tr * H + c] = z1;
+            sP[c * LD + tr] = da3;   // dA3^T [c][r]
+            sQ[tr * LD + c] = z1;    // Z1 [r][k]
+            sM[tr * LD + c] = f0;    // mask source [r][k]
           }
         }
         __syncthreads();
-        {
-          // dF = D1_f^T dA3 + routed dg0 ; dA2 = dF * [a2 > 0]   (row tr, my 16 units)
-          const int i = __float_as_int(sX[tr * 12 + 10]);
-          const bool valid = sX[tr * 12 + 9] != 0.f;
+        if (act_chunk) {
+          // active rows: a2 = E2 z1 + b2 recomputed (routed gradient only, few rows)
           for (int x = 0; x < 16; ++x) {
             const int k = tq + x;
-            float df = 0.f;
-            for (int c = 0; c < H; ++c) df = fmaf(sWdf[c * H + k], sA[tr * H + c], df);
-            if (sRoute[k] == i) df += sV[V_DG0 * H + k];
-            // a2 = E2 z1 + b2 (recomputed; positive exactly when the forward's f > 0)
             float a2 = W[OFF_B2 + k];
-            for (int c = 0; c < H; ++c) a2 = fmaf(sW2[k * H + c], sB[tr * H + c], a2);
-            sC[tr * H + k] = (valid && a2 > 0.f) ? df : 0.f;
+            for (int c = 0; c < H; ++c) a2 = fmaf(sW2[k * LD + c], sQ[tr * LD + c], a2);
+            sM[tr * LD + k] = relu(a2);
+          }
+          __syncthreads();
+        }
+        {
+          // dF = dA3 D1_f (+ routed dg0); dA2 = dF * [a2 > 0] in both layouts
+          float acc[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+          tile_acc(sP, sWdf, ti, tj, acc);
+#pragma unroll
+          for (int i = 0; i < 4; ++i) {
+            const int r = 4 * ti + i;
+            const int node = __float_as_int(sX[r * 12 + 10]);
+            const bool valid = sX[r * 12 + 9] != 0.f;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int k = 4 * tj + j;
+              float df = acc[i][j];
+              if (sRoute[k] == node) df += sV[V_DG0 * H + k];
+              const float da2 = (valid && sM[r * LD + k] > 0.f) ? df : 0.f;
+              sD[r * LD + k] = da2;
+              sDT[k * LD + r] = da2;
+            }
           }
         }
         __syncthreads();
         {
-          // dE2 += dA2^T Z1 ; db2 ; and dZ1 = E2^T dA2 -> dA1 = dZ1 * [a1 > 0] into sA
-          float acc[16];
-#pragma unroll
-          for (int x = 0; x < 16; ++x) acc[x] = 0.f;
-          for (int r = 0; r < CH; ++r) {
-            const float d = sC[r * H + tr];
-#pragma unroll
-            for (int x = 0; x < 16; ++x) acc[x] = fmaf(d, sB[r * H + tq + x], acc[x]);
-          }
-#pragma unroll
-          for (int x = 0; x < 16; ++x) sAcc[OFF_W2 + tr * H + tq + x] += acc[x];
+          tile_acc(sD, sQ, ti, tj, accW2);   // dE2[c][k] += sum_r dA2[r][c] Z1[r][k]
           if (tid < H) {
             float sd = 0.f;
-            for (int r = 0; r < CH; ++r) sd += sC[r * H + tid];
+            for (int r = 0; r < CH; ++r) sd += sD[r * LD + tid];
             sAcc[OFF_B2 + tid] += sd;
           }
-          for (int x = 0; x < 16; ++x) {
-            const int k = tq + x;
-            float dz = 0.f;
-            for (int c = 0; c < H; ++c) dz = fmaf(sW2[c * H + k], sC[tr * H + c], dz);
-            sA[tr * H + k] = sB[tr * H + k] > 0.f ? dz : 0.f;   // z1 > 0 <=> a1 > 0
-          }
+          // dZ1 = dA2 E2 ; dA1 = dZ1 * [z1 > 0] (into sP as [r][k]; dA3^T is no longer needed)
+          float acc[4][4];
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+          tile_acc(sDT, sW2, ti, tj, acc);
+          __syncthreads();
+#pragma unroll
+          for (int i = 0; i < 4; ++i)
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+              const int r = 4 * ti + i, k = 4 * tj + j;
+              sP[r * LD + k] = sQ[r * LD + k] > 0.f ? acc[i][j] : 0.f;
+            }
         }
         __syncthreads();
         {
-          // dE1 += dA1^T X ; db1 ; and for active rows dL/du_hat += E1[:, 6:9]^T dA1
+          // dE1 += dA1^T X ; db1 ; for active rows dL/du_hat += E1[:, 6:9]^T dA1
           for (int e = tid; e < H * 10; e += BB) {
             const int c = e / 10, col = e % 10;
             if (!act_chunk && col >= 6 && col < 9) continue;   // passive u_hat is zero
             float s = 0.f;
             for (int r = 0; r < CH; ++r) {
               const float xv = col < 9 ? sX[r * 12 + col] : 1.f;
-              s = fmaf(sA[r * H + c], xv, s);
+              s = fmaf(sP[r * LD + c], xv, s);
             }
             if (col < 9) sAcc[OFF_W1 + c * NIN + col] += s;
             else sAcc[OFF_B1 + c] += s;
@@ -498,15 +560,10 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
           if (act_chunk && tid < sCnt[2] * 3) {
             const int r = tid / 3, q = tid % 3;
             float s = 0.f;
-            for (int c = 0; c < H; ++c) s = fmaf(W[OFF_W1 + c * NIN + 6 + q], sA[r * H + c], s);
+            for (int c = 0; c < H; ++c) s = fmaf(W[OFF_W1 + c * NIN + 6 + q], sP[r * LD + c], s);
             const int i = __float_as_int(sX[r * 12 + 10]);
-            int lo = 0, hi = m - 1;
-            while (lo < hi) {
-              const int mid = (lo + hi) >> 1;
-              if (wIdx[mid] < i) lo = mid + 1; else hi = mid;
-            }
-            float* du = reinterpret_cast<float*>(&wDU[lo]);
-            du[q] += s;   // rows are distinct nodes: no two threads share (lo, q)
+            float* du = reinterpret_cast<float*>(&wDU[find_slot(wIdx, m, i)]);
+            du[q] += s;   // rows are distinct nodes: no two threads share (slot, q)
           }
         }
         __syncthreads();
@@ -671,6 +728,15 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
       }
     }
   }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * ti + i, k = 4 * tj + j;
+      sAcc[OFF_WD + c * 2 * H + k] += accWdf[i][j];
+      sAcc[OFF_W2 + c * H + k] += accW2[i][j];
+    }
   __syncthreads();
   for (int i = tid; i < NPARAM; i += BB) a.param_part[(size_t)blockIdx.x * NPARAM + i] = sAcc[i];
 }

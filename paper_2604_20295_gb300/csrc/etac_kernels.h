@@ -194,6 +194,7 @@ struct BackwardArgs {
   const float* f0tab;
   const float* h0tab;
   const int16_t* order;
+  const float2* ranked;        // per type and channel: (f0, node) in descending f0 order
   int mode;
   const float* grad_disp;      // [N*3]
   float* grad_uhat;            // [N*3] or null
