@@ -418,6 +418,98 @@ __device__ inline NodeContact contact_refine(const PadObj* po, int K, float3 p, 
   return r;
 }
 
+// FP32 contact of a node whose screened distance is certainly negative (phi32 < -tau).  Returns
+// false -- and the caller must use contact_refine -- when any discrete choice that u_hat depends
+// on is within `gap` of a tie: the nearest object, the nearest box face, radial vs. end wall of
+// a cylinder.  Otherwise the choices equal the exact ones (|FP32 error| < tau < gap / 2) and
+// u_hat carries only FP32 rounding of phi (~1e-5 mm) and of the normal.
+__device__ inline bool contact_fast(const PadObj* po, int K, float3 p, float3 nrm, float gap,
+                                    NodeContact* r) {
+  float best = INFINITY, second = INFINITY, bmargin = INFINITY;
+  float g[3] = {0.f, 0.f, 0.f};
+  bool bdeg = false;
+  int bk = -1;
+  for (int k = 0; k < K; ++k) {
+    const PadObj& o = po[k];
+    if (o.type == OBJ_NONE) continue;
+    float3 q;
+    q.x = fmaf(o.R[0], p.x, fmaf(o.R[1], p.y, fmaf(o.R[2], p.z, o.t[0])));
+    q.y = fmaf(o.R[3], p.x, fmaf(o.R[4], p.y, fmaf(o.R[5], p.z, o.t[1])));
+    q.z = fmaf(o.R[6], p.x, fmaf(o.R[7], p.y, fmaf(o.R[8], p.z, o.t[2])));
+    float ph, gk[3] = {0.f, 0.f, 0.f}, margin = INFINITY;
+    bool deg = false;
+    if (o.type == OBJ_SPHERE || o.type == OBJ_CAPSULE) {
+      float vz = q.z;
+      if (o.type == OBJ_CAPSULE) vz = q.z - fminf(fmaxf(q.z, -o.dims[1]), o.dims[1]);
+      const float L = sqrtf(q.x * q.x + q.y * q.y + vz * vz);
+      ph = L - o.dims[0];
+      if (L > 0.f) {
+        gk[0] = q.x / L;
+        gk[1] = q.y / L;
+        gk[2] = vz / L;
+      } else {
+        deg = true;
+      }
+    } else if (o.type == OBJ_BOX) {
+      const float d[3] = {fabsf(q.x) - o.dims[0], fabsf(q.y) - o.dims[1], fabsf(q.z) - o.dims[2]};
+      const float qa[3] = {q.x, q.y, q.z};
+      int am = 0;
+      for (int a = 1; a < 3; ++a)
+        if (d[a] > d[am]) am = a;
+      float sec = -INFINITY;
+      for (int a = 0; a < 3; ++a)
+        if (a != am) sec = fmaxf(sec, d[a]);
+      ph = d[am];
+      if (ph >= 0.f) ph = sdf_f32(o.type, o.dims, q);   // outside this box
+      margin = d[am] - sec;
+      gk[am] = qa[am] >= 0.f ? 1.f : -1.f;
+    } else {   // cylinder
+      const float rho = sqrtf(q.x * q.x + q.y * q.y);
+      const float dr = rho - o.dims[0], dz = fabsf(q.z) - o.dims[1];
+      ph = fmaxf(dr, dz);
+      if (ph >= 0.f) ph = sdf_f32(o.type, o.dims, q);
+      margin = fabsf(dr - dz);
+      if (dr >= dz) {
+        if (rho > 0.f) {
+          gk[0] = q.x / rho;
+          gk[1] = q.y / rho;
+        } else {
+          deg = true;
+        }
+      } else {
+        gk[2] = q.z >= 0.f ? 1.f : -1.f;
+      }
+    }
+    if (ph < best) {
+      second = best;
+      best = ph;
+      bk = k;
+      bmargin = margin;
+      bdeg = deg;
+      g[0] = gk[0];
+      g[1] = gk[1];
+      g[2] = gk[2];
+    } else if (ph < second) {
+      second = ph;
+    }
+  }
+  if (bk < 0 || !(best < -gap) || second - best < gap || bmargin < gap) return false;
+  const PadObj& o = po[bk];
+  if (bdeg) {
+    g[0] = -(o.R[0] * nrm.x + o.R[1] * nrm.y + o.R[2] * nrm.z);
+    g[1] = -(o.R[3] * nrm.x + o.R[4] * nrm.y + o.R[5] * nrm.z);
+    g[2] = -(o.R[6] * nrm.x + o.R[7] * nrm.y + o.R[8] * nrm.z);
+  }
+  r->active = true;
+  r->k = bk;
+  r->phi = best;
+  const float s = -best;
+  r->u[0] = s * (o.R[0] * g[0] + o.R[3] * g[1] + o.R[6] * g[2]);
+  r->u[1] = s * (o.R[1] * g[0] + o.R[4] * g[1] + o.R[7] * g[2]);
+  r->u[2] = s * (o.R[2] * g[0] + o.R[5] * g[1] + o.R[8] * g[2]);
+  return true;
+}
+
 // Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).
 __device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, float3 nrm,
                                            SdfIn* detail = nullptr) {

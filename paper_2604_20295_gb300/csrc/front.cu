@@ -13,6 +13,9 @@
 //   Four block barriers per pad.
 //   4. the max-pool over the passive nodes: the first passive node of each channel's table
 //      order (ranked f0 values), 32 ranks per warp-wide test.
+//   Nodes certainly inside an object, with no near-tie among the discrete choices, take u_hat
+//   from FP32 arithmetic (the BF16 step's error budget); the exact df32 path decides the thin
+//   band near surfaces and ties, so contact sets still equal the exact ones.
 // front_global_kernel (one warp per pad): global MLP g = ReLU(G1 g0), the decoder's global half
 //   beta = D1[:, 64:] g, and the record the propagation GEMM's epilogue needs: -beta in BF16
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
@@ -26,8 +29,9 @@ namespace etac {
 
 namespace {
 
-constexpr int FT = 256;
+constexpr int FT = 128;
 constexpr int FW = FT / 32;
+constexpr int CPW = H / FW;   // channels per warp in the passive max-pool search
 
 struct FrontSmem {
   size_t w2f, b2, w1u, red, cand, actidx, actu, actbits, cnt, po, total;
@@ -64,7 +68,7 @@ __device__ __forceinline__ int warp_append(bool flag, int* counter) {
   return flag ? base + __popc(bal & ((1u << lane) - 1u)) : -1;
 }
 
-__global__ void __launch_bounds__(FT, 2) front_contact_kernel(FrontArgs a) {
+__global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
   const FrontSmem L(a.nmax, a.K);
@@ -135,29 +139,50 @@ __global__ void __launch_bounds__(FT, 2) front_contact_kernel(FrontArgs a) {
     for (int w = tid; w < nwords; w += FT) sActBits[w] = 0u;
     __syncthreads();
     const bool invalid = sCnt[2] != 0;
+    float gap = 0.f;   // twice the largest FP32 error bound over the pad's objects
+    for (int k = 0; k < a.K; ++k) gap = fmaxf(gap, 2.f * spo[k].tau);
 
-    // ---- 1. FP32 screen of every node
+    // ---- 1. FP32 screen of every node.  Nodes certainly outside stay passive; nodes certainly
+    // inside with no near-tie in their discrete choices take the FP32 u_hat (BF16 accuracy is
+    // the budget here); only the thin band near a surface or a tie goes to the exact df32 path.
     for (int r0 = 0; r0 < n; r0 += FT) {
       const int i = r0 + tid;
       bool cand = false;
+      NodeContact c;
+      c.active = false;
       if (i < n && !invalid) {
+        const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         float phi32;
-        cand = contact_screen(spo, a.K, make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]),
-                              &phi32);
+        if (contact_screen(spo, a.K, p, &phi32)) {
+          const float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+          cand = !contact_fast(spo, a.K, p, nr, gap, &c);
+        }
       }
       if (i < n && !cand) {
-        btrow[i] = zero16;
-        btrow[n + i] = zero16;
-        btrow[2 * n + i] = zero16;
-        if (a.mask) a.mask[base + i] = 0;
-        if (a.pen) a.pen[base + i] = 0.f;
+        btrow[i] = __float2bfloat16_rn(c.u[0]);
+        btrow[n + i] = __float2bfloat16_rn(c.u[1]);
+        btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
+        if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
+        if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
+        if (c.active) {
+          float* d = a.disp + 3 * (base + i);
+          d[0] = c.u[0];
+          d[1] = c.u[1];
+          d[2] = c.u[2];
+          atomicOr(&sActBits[i >> 5], 1u << (i & 31));
+        }
       }
       const int slot = warp_append(cand, &sCnt[0]);
       if (slot >= 0) sCand[slot] = (int16_t)i;
+      const int aslot = warp_append(c.active, &sCnt[1]);
+      if (aslot >= 0) {
+        sActIdx[aslot] = (int16_t)i;
+        sActU[aslot] = make_float4(c.u[0], c.u[1], c.u[2], 0.f);
+      }
     }
     __syncthreads();
 
-    // ---- 2. exact contact of the candidates
+    // ---- 2. exact contact of the band candidates
     const int nc = sCnt[0];
     for (int s0 = 0; s0 < nc; s0 += FT) {
       const int s = s0 + tid;
@@ -266,25 +291,25 @@ __global__ void __launch_bounds__(FT, 2) front_contact_kernel(FrontArgs a) {
     // max-pool over the passive nodes: the first passive node in each channel's descending
     // order of f0; a warp tests 32 ranks per load for 8 channels at a time
     {
-      float best[8];
-      bool done[8];
+      float best[CPW];
+      bool done[CPW];
 #pragma unroll
-      for (int c = 0; c < 8; ++c) {
+      for (int c = 0; c < CPW; ++c) {
         best[c] = 0.f;
         done[c] = false;
       }
       for (int r0 = 0; r0 < n; r0 += 32) {
         const int r = r0 + lane;
-        float2 e[8];
+        float2 e[CPW];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const int u = warp * 8 + c;
+        for (int c = 0; c < CPW; ++c) {
+          const int u = warp * CPW + c;
           e[c] = (!done[c] && r < n) ? __ldg(a.ranked + (size_t)H * o + (size_t)u * n + r)
                                       : make_float2(0.f, __int_as_float(0));
         }
         bool all = true;
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < CPW; ++c) {
           const int idx = __float_as_int(e[c].y);
           const bool passive = !done[c] && r < n && !((sActBits[idx >> 5] >> (idx & 31)) & 1u);
           const unsigned bal = __ballot_sync(0xffffffffu, passive);
@@ -296,12 +321,12 @@ __global__ void __launch_bounds__(FT, 2) front_contact_kernel(FrontArgs a) {
         }
         if (all) break;
       }
-      if (lane < 8) {
+      if (lane < CPW) {
         float v = 0.f;
 #pragma unroll
-        for (int c = 0; c < 8; ++c)
+        for (int c = 0; c < CPW; ++c)
           if (c == lane) v = best[c];
-        const int u = warp * 8 + lane;
+        const int u = warp * CPW + lane;
 #pragma unroll
         for (int w = 0; w < FW; ++w) v = fmaxf(v, sRed[w * H + u]);
         a.g0a[(size_t)pad * H + u] = v;
