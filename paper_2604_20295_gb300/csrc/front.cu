@@ -150,6 +150,9 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       bool cand = false;
       NodeContact c;
       c.active = false;
+      c.phi = 0.f;
+      c.k = -1;
+      c.u[0] = c.u[1] = c.u[2] = 0.f;
       if (i < n && !invalid) {
         const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         float phi32;
@@ -188,6 +191,9 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       const int s = s0 + tid;
       NodeContact c;
       c.active = false;
+      c.phi = 0.f;
+      c.k = -1;
+      c.u[0] = c.u[1] = c.u[2] = 0.f;
       int i = 0;
       if (s < nc) {
         i = sCand[s];
