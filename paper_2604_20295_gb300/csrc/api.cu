@@ -70,6 +70,8 @@ struct etac_ctx {
   int* d_pad_m = nullptr;
   float* d_g0a = nullptr;
   float2* d_ranked = nullptr;
+  etac::PadObj* d_padobj = nullptr;
+  int* d_pad_bad = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
@@ -91,8 +93,9 @@ struct etac_ctx {
 namespace {
 const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
                               "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel",
-                              "backward_kernel"};
-enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_COUNT = 6 };
+                              "backward_kernel", "pad_obj_kernel"};
+enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_PADOBJ = 6,
+       K_COUNT = 7 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -151,7 +154,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
                   c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
-                  c->d_g0a, c->d_ranked, c->d_ws_idx, c->d_ws_u,
+                  c->d_g0a, c->d_ranked, c->d_padobj, c->d_pad_bad, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -237,6 +240,8 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_padobj, (size_t)np * c->K);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_bad, (size_t)np);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
@@ -629,11 +634,16 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.g0a = c->d_g0a;
       f.negbeta = c->d_negbeta;
       f.c0m = c->d_c0m;
-      if (!f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
+      f.padobj = c->d_padobj;
+      f.pad_bad = c->d_pad_bad;
+      if (!f.padobj || !f.pad_bad || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
           !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");
-      int ts = timing_begin(c, K_FRONT, s);
+      int ts = timing_begin(c, K_PADOBJ, s);
+      ETAC_CUDA(c, etac::launch_pad_obj(f, s), "pad transforms launch");
+      timing_end(c, ts, s);
+      ts = timing_begin(c, K_FRONT, s);
       ETAC_CUDA(c, etac::launch_front_contact(f, std::min<int>(c->front_grid, (int)EP), s),
                 "BF16 front launch");
       timing_end(c, ts, s);

@@ -5,6 +5,8 @@
 #include <stddef.h>
 #include <stdint.h>
 
+#include "etac_common.cuh"
+
 namespace etac {
 
 // ---------------------------------------------------------------- plain algorithm
@@ -124,8 +126,11 @@ struct FrontArgs {
   float* g0a;                   // [E*P][64] max-pooled global feature g0 of each pad
   void* negbeta;                // [E*P][64] BF16
   float4* c0m;                  // [E*P]
+  PadObj* padobj;               // [E*P][K] pad -> object transforms
+  int* pad_bad;                 // [E*P] 1 when a pose or size held NaN / Inf
 };
 size_t front_smem_bytes(int nmax, int K);
+cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s);
 cudaError_t front_occupancy(int nmax, int K, int* blocks_per_sm);
 cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_front_global(const FrontArgs& a, int grid, cudaStream_t s);

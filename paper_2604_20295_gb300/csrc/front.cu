@@ -68,6 +68,34 @@ __device__ __forceinline__ int warp_append(bool flag, int* counter) {
   return flag ? base + __popc(bal & ((1u << lane) - 1u)) : -1;
 }
 
+// every pad's relative transforms and screening margins, one thread per pad (object slots in
+// turn); pad_bad[pad] = 1 when one of its poses or sizes is not finite
+__global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
+  const int pad = blockIdx.x * blockDim.x + threadIdx.x;
+  if (pad >= a.num_items) return;
+  const int env = pad / a.P;
+  const float* pp = a.pad_pose + 7 * (size_t)pad;
+  const float pmax = a.type_pmax[a.pad_type[pad]];
+  int bad = 0;
+  for (int k = 0; k < a.K; ++k) {
+    const int ob = env * a.K + k;
+    const float* op = a.obj_pose + 7 * (size_t)ob;
+    const float* od = a.obj_dims + 3 * (size_t)ob;
+    int type = a.obj_type[ob];
+    if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+    const bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
+                    isfinite(od[2]);
+    if (!ok && type != OBJ_NONE) {
+      bad = 1;
+      type = OBJ_NONE;
+    }
+    PadObj po;
+    setup_pad_obj(op, type, od, pp, pmax, &po);
+    a.padobj[(size_t)pad * a.K + k] = po;
+  }
+  a.pad_bad[pad] = bad;
+}
+
 __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   __shared__ int s_item;
@@ -100,17 +128,20 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
                           0.f);
   }
 
+  // the next work item is fetched while the current one is processed
+  __shared__ int s_next;
+  if (tid == 0) s_next = atomicAdd(a.ticket, 1);
   for (;;) {
     __syncthreads();
     if (tid == 0) {
-      s_item = atomicAdd(a.ticket, 1);
+      s_item = s_next;
       sCnt[0] = sCnt[1] = sCnt[2] = 0;
     }
     __syncthreads();
     const int item = s_item;
     if (item >= a.num_items) break;
+    if (tid == 0) s_next = atomicAdd(a.ticket, 1);
     const int pad = a.item_pad[item];
-    const int env = pad / a.P;
     const int ty = a.pad_type[pad];
     const int o = a.type_off[ty];
     const int n = a.type_off[ty + 1] - o;
@@ -120,21 +151,12 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
     const float* tnrm = a.type_nrm + 3 * (size_t)o;
     __nv_bfloat16* btrow =
         reinterpret_cast<__nv_bfloat16*>(a.bt) + a.bt_off[ty] + (size_t)3 * a.pad_inst[pad] * n;
-    const __nv_bfloat16 zero16 = __float2bfloat16_rn(0.f);
-    if (tid < a.K) {
-      const int ob = env * a.K + tid;
-      const float* op = a.obj_pose + 7 * (size_t)ob;
-      const float* pp = a.pad_pose + 7 * (size_t)pad;
-      const float* od = a.obj_dims + 3 * (size_t)ob;
-      int type = a.obj_type[ob];
-      if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
-      const bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
-                      isfinite(od[2]);
-      if (!ok && type != OBJ_NONE) {
-        sCnt[2] = 1;
-        type = OBJ_NONE;
-      }
-      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
+    {
+      const int* src = reinterpret_cast<const int*>(a.padobj + (size_t)pad * a.K);
+      int* dst = reinterpret_cast<int*>(spo);
+      const int words = a.K * (int)(sizeof(PadObj) / 4);
+      for (int e = tid; e < words; e += FT) dst[e] = src[e];
+      if (tid == 0 && a.pad_bad[pad]) sCnt[2] = 1;
     }
     for (int w = tid; w < nwords; w += FT) sActBits[w] = 0u;
     __syncthreads();
@@ -429,6 +451,11 @@ cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s) {
     configured = smem;
   }
   front_contact_kernel<<<grid, FT, smem, s>>>(a);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s) {
+  pad_obj_kernel<<<(unsigned)((a.num_items + 255) / 256), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
