@@ -418,17 +418,21 @@ __device__ inline NodeContact contact_refine(const PadObj* po, int K, float3 p, 
   return r;
 }
 
-// FP32 contact of a node whose screened distance is certainly negative (phi32 < -tau).  Returns
-// false -- and the caller must use contact_refine -- when any discrete choice that u_hat depends
-// on is within `gap` of a tie: the nearest object, the nearest box face, radial vs. end wall of
-// a cylinder.  Otherwise the choices equal the exact ones (|FP32 error| < tau < gap / 2) and
-// u_hat carries only FP32 rounding of phi (~1e-5 mm) and of the normal.
-__device__ inline bool contact_fast(const PadObj* po, int K, float3 p, float3 nrm, float gap,
-                                    NodeContact* r) {
-  float best = INFINITY, second = INFINITY, bmargin = INFINITY;
-  float g[3] = {0.f, 0.f, 0.f};
-  bool bdeg = false;
+// One FP32 pass over a node's objects that sorts it into three classes:
+//   CONTACT_OUT   phi32 >= tau for every object: certainly outside, passive;
+//   CONTACT_FAST  certainly inside (phi32 < -gap) and no discrete choice that u_hat depends on
+//                 (the nearest object, the nearest box face, radial vs. end wall of a
+//                 cylinder) is within `gap` of a tie: the choices equal the exact ones
+//                 (|FP32 error| < tau <= gap / 2) and *r holds u_hat from FP32 arithmetic;
+//   CONTACT_BAND  anything else: contact_refine decides exactly.
+enum { CONTACT_OUT = 0, CONTACT_FAST = 1, CONTACT_BAND = 2 };
+__device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3 nrm, float gap,
+                                       NodeContact* r) {
+  // pass 1: FP32 distance to every object; far-outside nodes stop here
+  float best = INFINITY, second = INFINITY;
+  bool maybe = false;
   int bk = -1;
+  float3 bq = make_float3(0.f, 0.f, 0.f);
   for (int k = 0; k < K; ++k) {
     const PadObj& o = po[k];
     if (o.type == OBJ_NONE) continue;
@@ -436,78 +440,88 @@ __device__ inline bool contact_fast(const PadObj* po, int K, float3 p, float3 nr
     q.x = fmaf(o.R[0], p.x, fmaf(o.R[1], p.y, fmaf(o.R[2], p.z, o.t[0])));
     q.y = fmaf(o.R[3], p.x, fmaf(o.R[4], p.y, fmaf(o.R[5], p.z, o.t[1])));
     q.z = fmaf(o.R[6], p.x, fmaf(o.R[7], p.y, fmaf(o.R[8], p.z, o.t[2])));
-    float ph, gk[3] = {0.f, 0.f, 0.f}, margin = INFINITY;
-    bool deg = false;
-    if (o.type == OBJ_SPHERE || o.type == OBJ_CAPSULE) {
-      float vz = q.z;
-      if (o.type == OBJ_CAPSULE) vz = q.z - fminf(fmaxf(q.z, -o.dims[1]), o.dims[1]);
-      const float L = sqrtf(q.x * q.x + q.y * q.y + vz * vz);
-      ph = L - o.dims[0];
-      if (L > 0.f) {
-        gk[0] = q.x / L;
-        gk[1] = q.y / L;
-        gk[2] = vz / L;
-      } else {
-        deg = true;
-      }
-    } else if (o.type == OBJ_BOX) {
-      const float d[3] = {fabsf(q.x) - o.dims[0], fabsf(q.y) - o.dims[1], fabsf(q.z) - o.dims[2]};
-      const float qa[3] = {q.x, q.y, q.z};
-      int am = 0;
-      for (int a = 1; a < 3; ++a)
-        if (d[a] > d[am]) am = a;
-      float sec = -INFINITY;
-      for (int a = 0; a < 3; ++a)
-        if (a != am) sec = fmaxf(sec, d[a]);
-      ph = d[am];
-      if (ph >= 0.f) ph = sdf_f32(o.type, o.dims, q);   // outside this box
-      margin = d[am] - sec;
-      gk[am] = qa[am] >= 0.f ? 1.f : -1.f;
-    } else {   // cylinder
-      const float rho = sqrtf(q.x * q.x + q.y * q.y);
-      const float dr = rho - o.dims[0], dz = fabsf(q.z) - o.dims[1];
-      ph = fmaxf(dr, dz);
-      if (ph >= 0.f) ph = sdf_f32(o.type, o.dims, q);
-      margin = fabsf(dr - dz);
-      if (dr >= dz) {
-        if (rho > 0.f) {
-          gk[0] = q.x / rho;
-          gk[1] = q.y / rho;
-        } else {
-          deg = true;
-        }
-      } else {
-        gk[2] = q.z >= 0.f ? 1.f : -1.f;
-      }
-    }
+    const float ph = sdf_f32(o.type, o.dims, q);
+    maybe |= ph < o.tau;
     if (ph < best) {
       second = best;
       best = ph;
       bk = k;
-      bmargin = margin;
-      bdeg = deg;
-      g[0] = gk[0];
-      g[1] = gk[1];
-      g[2] = gk[2];
+      bq = q;
     } else if (ph < second) {
       second = ph;
     }
   }
-  if (bk < 0 || !(best < -gap) || second - best < gap || bmargin < gap) return false;
+  if (!maybe) return CONTACT_OUT;
+  if (bk < 0 || !(best < -gap) || second - best < gap) return CONTACT_BAND;
+  // pass 2: the nearest object's outward normal and the margin of its discrete choice
   const PadObj& o = po[bk];
-  if (bdeg) {
-    g[0] = -(o.R[0] * nrm.x + o.R[1] * nrm.y + o.R[2] * nrm.z);
-    g[1] = -(o.R[3] * nrm.x + o.R[4] * nrm.y + o.R[5] * nrm.z);
-    g[2] = -(o.R[6] * nrm.x + o.R[7] * nrm.y + o.R[8] * nrm.z);
+  const float3 q = bq;
+  float g0 = 0.f, g1 = 0.f, g2 = 0.f, margin = INFINITY;
+  bool deg = false;
+  if (o.type == OBJ_SPHERE || o.type == OBJ_CAPSULE) {
+    float vz = q.z;
+    if (o.type == OBJ_CAPSULE) vz = q.z - fminf(fmaxf(q.z, -o.dims[1]), o.dims[1]);
+    const float L = sqrtf(q.x * q.x + q.y * q.y + vz * vz);
+    if (L > 0.f) {
+      const float il = 1.f / L;
+      g0 = q.x * il;
+      g1 = q.y * il;
+      g2 = vz * il;
+    } else {
+      deg = true;
+    }
+  } else if (o.type == OBJ_BOX) {
+    // nearest face: the largest of d = |q| - half size, lowest axis on ties (selects, so
+    // nothing is indexed at run time); inside, phi = max d
+    const float dx = fabsf(q.x) - o.dims[0], dy = fabsf(q.y) - o.dims[1],
+                dz = fabsf(q.z) - o.dims[2];
+    int am = 0;
+    float dm = dx;
+    if (dy > dm) {
+      am = 1;
+      dm = dy;
+    }
+    if (dz > dm) {
+      am = 2;
+      dm = dz;
+    }
+    const float sec = am == 0 ? fmaxf(dy, dz) : (am == 1 ? fmaxf(dx, dz) : fmaxf(dx, dy));
+    margin = dm - sec;
+    const float qs = am == 0 ? q.x : (am == 1 ? q.y : q.z);
+    const float sg = qs >= 0.f ? 1.f : -1.f;
+    g0 = am == 0 ? sg : 0.f;
+    g1 = am == 1 ? sg : 0.f;
+    g2 = am == 2 ? sg : 0.f;
+  } else {   // cylinder: radial wall or end cap, whichever is nearer (phi = max(dr, dz))
+    const float rho = sqrtf(q.x * q.x + q.y * q.y);
+    const float dr = rho - o.dims[0], dz = fabsf(q.z) - o.dims[1];
+    margin = fabsf(dr - dz);
+    if (dr >= dz) {
+      if (rho > 0.f) {
+        const float ir = 1.f / rho;
+        g0 = q.x * ir;
+        g1 = q.y * ir;
+      } else {
+        deg = true;
+      }
+    } else {
+      g2 = q.z >= 0.f ? 1.f : -1.f;
+    }
+  }
+  if (margin < gap) return CONTACT_BAND;
+  if (deg) {
+    g0 = -(o.R[0] * nrm.x + o.R[1] * nrm.y + o.R[2] * nrm.z);
+    g1 = -(o.R[3] * nrm.x + o.R[4] * nrm.y + o.R[5] * nrm.z);
+    g2 = -(o.R[6] * nrm.x + o.R[7] * nrm.y + o.R[8] * nrm.z);
   }
   r->active = true;
   r->k = bk;
   r->phi = best;
   const float s = -best;
-  r->u[0] = s * (o.R[0] * g[0] + o.R[3] * g[1] + o.R[6] * g[2]);
-  r->u[1] = s * (o.R[1] * g[0] + o.R[4] * g[1] + o.R[7] * g[2]);
-  r->u[2] = s * (o.R[2] * g[0] + o.R[5] * g[1] + o.R[8] * g[2]);
-  return true;
+  r->u[0] = s * (o.R[0] * g0 + o.R[3] * g1 + o.R[6] * g2);
+  r->u[1] = s * (o.R[1] * g0 + o.R[4] * g1 + o.R[7] * g2);
+  r->u[2] = s * (o.R[2] * g0 + o.R[5] * g1 + o.R[8] * g2);
+  return CONTACT_FAST;
 }
 
 // Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).

@@ -1,21 +1,23 @@
 // front.cu -- front half of the BF16 tensor-core ETac step (ETac Sec. III-A).
 //
-// front_contact_kernel (persistent, one CTA per pad from a work queue, heaviest pads first):
-//   1. FP32 screen of every node; nodes certainly outside all objects are passive (their B
-//      operand entries are zeroed); the rest become a compact candidate list;
-//   2. the candidates' exact (df32) contact decision and u_hat -- candidates are dense in the
-//      list, so warps do not diverge on the long df32 chains; active nodes keep u_hat (Eq. 4
-//      covers passive nodes only), their u_hat goes to the B operand, their contact bits to a
-//      per-pad bit field;
-//   3. the encoder on the active nodes on tensor cores (E1 evaluated straight into the
-//      m16n8k16 A-fragment layout, E2 as BF16 MMAs with FP32 accumulation), channel maxima
-//      per pad written out.  Passive nodes need no encoder: their outputs are table entries.
-//   Four block barriers per pad.
-//   4. the max-pool over the passive nodes: the first passive node of each channel's table
-//      order (ranked f0 values), 32 ranks per warp-wide test.
-//   Nodes certainly inside an object, with no near-tie among the discrete choices, take u_hat
-//   from FP32 arithmetic (the BF16 step's error budget); the exact df32 path decides the thin
-//   band near surfaces and ties, so contact sets still equal the exact ones.
+// pad_obj_kernel (one thread per pad): the pad -> object relative transforms (FP32 and df32)
+//   and the FP32 screening margins, so that no pad's work starts with a serial setup chain.
+// front_contact_kernel (persistent, one WARP per pad from a work queue, heaviest pads first;
+//   warps never wait on each other, so the latency of one pad's chain hides behind the others):
+//   the warp streams over its pad's nodes, 32 per step:
+//   * one FP32 pass sorts each node: certainly outside every object (passive), certainly inside
+//     with no near-tie among the discrete choices (u_hat from FP32 arithmetic, the BF16 step's
+//     error budget), or undecided (a thin band near a surface or a tie);
+//   * undecided nodes go to a short list and take the exact df32 decision 32 at a time, so
+//     contact sets equal the exact ones;
+//   * active nodes keep u_hat (Eq. 4 covers passive nodes only), their u_hat goes to the
+//     propagation GEMM's B operand, their contact bit to a per-pad bit field, and they are
+//     pushed on a short stack that the encoder drains 16 at a time on tensor cores (E1
+//     evaluated straight into the m16n8k16 A-fragment layout, E2 as BF16 MMAs with FP32
+//     accumulation); channel maxima stay in registers.  Passive nodes need no encoder: their
+//     outputs are table entries;
+//   * at the end, the max-pool over the passive nodes: the first passive node of each
+//     channel's table order (ranked f0 values), 32 ranks per warp-wide test.
 // front_global_kernel (one warp per pad): global MLP g = ReLU(G1 g0), the decoder's global half
 //   beta = D1[:, 64:] g, and the record the propagation GEMM's epilogue needs: -beta in BF16
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
@@ -29,12 +31,15 @@ namespace etac {
 
 namespace {
 
-constexpr int FT = 128;
+constexpr int FT = 256;      // threads per CTA: eight independent pad warps
 constexpr int FW = FT / 32;
-constexpr int CPW = H / FW;   // channels per warp in the passive max-pool search
+constexpr int PEND = 48;     // per-warp stack of active nodes awaiting the encoder (<= 15 + 32)
+constexpr int CANDCAP = 64;  // per-warp list of undecided nodes awaiting the exact path
+constexpr unsigned FULL = 0xffffffffu;
 
+// shared weights, then one region per warp
 struct FrontSmem {
-  size_t w2f, b2, w1u, red, cand, actidx, actu, actbits, cnt, po, total;
+  size_t w2f, w1f, b2, warp0, warp_bytes, po, bits, pend_a, cand, fmax, total;
   __host__ __device__ FrontSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -43,30 +48,19 @@ struct FrontSmem {
       return r;
     };
     w2f = take(sizeof(uint2) * 8 * 4 * 32);
+    w1f = take(sizeof(uint2) * 2 * 8 * 32);
     b2 = take(sizeof(float) * H);
-    w1u = take(sizeof(float4) * H);
-    red = take(sizeof(float) * FW * H);
-    cand = take(sizeof(int16_t) * (size_t)nmax);
-    actidx = take(sizeof(int16_t) * (size_t)nmax);
-    actu = take(sizeof(float4) * (size_t)nmax);
-    actbits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
-    cnt = take(sizeof(int) * 8);
+    warp0 = o;
+    o = 0;
     po = take(sizeof(PadObj) * (size_t)K);
-    total = o;
+    bits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
+    pend_a = take(sizeof(uint4) * 2 * PEND);
+    cand = take(sizeof(int16_t) * CANDCAP);
+    fmax = take(sizeof(float) * H);
+    warp_bytes = o;
+    total = warp0 + FW * warp_bytes;
   }
 };
-
-// appends the lanes of a warp whose flag is set to a shared list; returns each lane's slot
-__device__ __forceinline__ int warp_append(bool flag, int* counter) {
-  const unsigned bal = __ballot_sync(0xffffffffu, flag);
-  if (!bal) return -1;
-  const int lane = threadIdx.x & 31;
-  const int leader = __ffs(bal) - 1;
-  int base = 0;
-  if (lane == leader) base = atomicAdd(counter, __popc(bal));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  return flag ? base + __popc(bal & ((1u << lane) - 1u)) : -1;
-}
 
 // every pad's relative transforms and screening margins, one thread per pad (object slots in
 // turn); pad_bad[pad] = 1 when one of its poses or sizes is not finite
@@ -96,21 +90,97 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
   a.pad_bad[pad] = bad;
 }
 
-__global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
+// Writes a decided node's outputs: the B-operand row entries, mask, penetration and, for an
+// active node, its displacement (= u_hat).
+__device__ __forceinline__ void front_write_node(const FrontArgs& a, __nv_bfloat16* btrow, int n,
+                                                 long long base, int i, const NodeContact& c) {
+  btrow[i] = __float2bfloat16_rn(c.u[0]);
+  btrow[n + i] = __float2bfloat16_rn(c.u[1]);
+  btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
+  if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
+  if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
+  if (c.active) {
+    float* d = a.disp + 3 * (base + i);
+    d[0] = c.u[0];
+    d[1] = c.u[1];
+    d[2] = c.u[2];
+  }
+}
+
+// E1 input row of an active node, 16 BF16 values: [p_hi, p_lo, n_hi, n_lo, u_hat, 1].  The
+// position and normal are split into two BF16 parts (p = p_hi + p_lo to 16 bits), so with W1
+// split the same way the first layer is evaluated to about FP32 accuracy on tensor cores;
+// u_hat enters rounded to BF16.
+__device__ __forceinline__ uint32_t bf2_bits(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bf_rest(float x) {   // x - BF16(x), itself rounded later
+  return x - __bfloat162float(__float2bfloat16_rn(x));
+}
+__device__ __forceinline__ void front_pack_row(uint4* dst, float3 p, float3 nr, const float* u) {
+  dst[0] = make_uint4(bf2_bits(p.x, p.y), bf2_bits(p.z, bf_rest(p.x)),
+                      bf2_bits(bf_rest(p.y), bf_rest(p.z)), bf2_bits(nr.x, nr.y));
+  dst[1] = make_uint4(bf2_bits(nr.z, bf_rest(nr.x)), bf2_bits(bf_rest(nr.y), bf_rest(nr.z)),
+                      bf2_bits(u[0], u[1]), bf2_bits(u[2], 1.f));
+}
+
+// Encoder of up to 16 active nodes on tensor cores, rows = E1 input rows (front_pack_row) at
+// shared address `rows` (16 consecutive 32-byte rows; rows at or beyond cnt are ignored):
+// h = ReLU(W1 x + b1) as 2 x 8 m16n8k16 MMAs (W1 hi and lo parts, bias in the constant
+// column), whose accumulators are the A fragments of y = E2 h (32 MMAs); y is folded into the
+// per-lane running channel maxima fm (the bias and the outer ReLU commute with the max:
+// max ReLU(y + b) = ReLU(max y + b)).  Lane (grp, tig) holds rows grp and grp + 8 and channels
+// 8 nt + 2 tig + {0, 1}.
+__device__ __forceinline__ void front_encode(float (&fm)[8][2], uint32_t rows, int cnt,
+                                             const uint2* sW1f, const uint2* sW2f, int lane) {
+  const int grp = lane >> 2;
+  const bool v0 = grp < cnt, v1 = grp + 8 < cnt;
+  uint32_t ax[4];
+  sm100::ldmatrix_x4(rows + (uint32_t)((lane & 15) * 32 + (lane >> 4) * 16), ax[0], ax[1], ax[2],
+                     ax[3]);
+  uint32_t af[4][4];
+#pragma unroll
+  for (int s4 = 0; s4 < 4; ++s4) {
+    float h[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int nt = 2 * s4 + t;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+      const uint2 bh = sW1f[nt * 32 + lane], bl = sW1f[(8 + nt) * 32 + lane];
+      sm100::mma_bf16_16816(acc, ax, bh.x, bh.y, acc);
+      sm100::mma_bf16_16816(acc, ax, bl.x, bl.y, acc);
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[t][q] = fmaxf(acc[q], 0.f);
+    }
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(h[0][0], h[0][1]);
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(h[0][2], h[0][3]);
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(h[1][0], h[1][1]);
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(h[1][2], h[1][3]);
+    af[s4][0] = *reinterpret_cast<uint32_t*>(&p0);
+    af[s4][1] = *reinterpret_cast<uint32_t*>(&p1);
+    af[s4][2] = *reinterpret_cast<uint32_t*>(&p2);
+    af[s4][3] = *reinterpret_cast<uint32_t*>(&p3);
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const uint2 bb = sW2f[(nt * 4 + s4) * 32 + lane];
+      sm100::mma_bf16_16816(acc, af[s4], bb.x, bb.y, acc);
+    }
+    fm[nt][0] = fmaxf(fm[nt][0], fmaxf(v0 ? acc[0] : -INFINITY, v1 ? acc[2] : -INFINITY));
+    fm[nt][1] = fmaxf(fm[nt][1], fmaxf(v0 ? acc[1] : -INFINITY, v1 ? acc[3] : -INFINITY));
+  }
+}
+
+__global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  __shared__ int s_item;
   const FrontSmem L(a.nmax, a.K);
   uint2* sW2f = reinterpret_cast<uint2*>(smem + L.w2f);
+  uint2* sW1f = reinterpret_cast<uint2*>(smem + L.w1f);
   float* sB2 = reinterpret_cast<float*>(smem + L.b2);
-  float4* sW1u = reinterpret_cast<float4*>(smem + L.w1u);
-  float* sRed = reinterpret_cast<float*>(smem + L.red);
-  int16_t* sCand = reinterpret_cast<int16_t*>(smem + L.cand);
-  int16_t* sActIdx = reinterpret_cast<int16_t*>(smem + L.actidx);
-  float4* sActU = reinterpret_cast<float4*>(smem + L.actu);
-  uint32_t* sActBits = reinterpret_cast<uint32_t*>(smem + L.actbits);
-  int* sCnt = reinterpret_cast<int*>(smem + L.cnt);   // [0] candidates [1] actives [2] invalid
-  PadObj* spo = reinterpret_cast<PadObj*>(smem + L.po);
-
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* W = a.params;
   // E2 as m16n8k16 B fragments: B[k = input unit][n = output unit] = W2[n][k]; entry
@@ -122,25 +192,42 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
     __nv_bfloat162 hi = __floats2bfloat162_rn(W[OFF_W2 + n * H + k + 8], W[OFF_W2 + n * H + k + 9]);
     sW2f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
   }
-  for (int i = tid; i < H; i += FT) {
-    sB2[i] = W[OFF_B2 + i];
-    sW1u[i] = make_float4(W[OFF_W1 + i * NIN + 6], W[OFF_W1 + i * NIN + 7], W[OFF_W1 + i * NIN + 8],
-                          0.f);
+  // E1 as B fragments over the 16-wide input row [p_hi, p_lo, n_hi, n_lo, u, 1]: input k reads
+  // W1 column kcol(k) (b1 for k = 15); entry (part, nt, l): part 0 = BF16(W), 1 = BF16(W - hi)
+  for (int e = tid; e < 2 * 8 * 32; e += FT) {
+    const int l = e & 31, nt = (e >> 5) & 7, part = e >> 8;
+    const int n = 8 * nt + (l >> 2), k0 = 2 * (l & 3);
+    auto wv = [&](int k) {
+      const int col = k < 6 ? k % 3 : (k < 12 ? 3 + (k - 6) % 3 : 6 + (k - 12));
+      const float w = k == 15 ? W[OFF_B1 + n] : W[OFF_W1 + n * NIN + col];
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      return part == 0 ? h : __float2bfloat16_rn(w - __bfloat162float(h));
+    };
+    __nv_bfloat162 lo = __halves2bfloat162(wv(k0), wv(k0 + 1));
+    __nv_bfloat162 hi = __halves2bfloat162(wv(k0 + 8), wv(k0 + 9));
+    sW1f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
   }
+  for (int i = tid; i < H; i += FT) sB2[i] = W[OFF_B2 + i];
+  __syncthreads();   // the only block barrier: from here on every warp runs its own pads
+
+  unsigned char* wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+  PadObj* spo = reinterpret_cast<PadObj*>(wb + L.po);
+  uint32_t* sBits = reinterpret_cast<uint32_t*>(wb + L.bits);
+  uint4* sPendA = reinterpret_cast<uint4*>(wb + L.pend_a);
+  const uint32_t sPendA_addr = (uint32_t)__cvta_generic_to_shared(sPendA);
+  int16_t* sCand = reinterpret_cast<int16_t*>(wb + L.cand);
+  float* sFmax = reinterpret_cast<float*>(wb + L.fmax);
+  const unsigned lt = (1u << lane) - 1u;
+  const bool enc = a.mode != MODE_LINEAR_ONLY;
 
   // the next work item is fetched while the current one is processed
-  __shared__ int s_next;
-  if (tid == 0) s_next = atomicAdd(a.ticket, 1);
+  int next = 0;
+  if (lane == 0) next = atomicAdd(a.ticket, 1);
   for (;;) {
-    __syncthreads();
-    if (tid == 0) {
-      s_item = s_next;
-      sCnt[0] = sCnt[1] = sCnt[2] = 0;
-    }
-    __syncthreads();
-    const int item = s_item;
+    __syncwarp();   // the previous pad's shared-memory reads are done
+    const int item = __shfl_sync(FULL, next, 0);
     if (item >= a.num_items) break;
-    if (tid == 0) s_next = atomicAdd(a.ticket, 1);
+    if (lane == 0) next = atomicAdd(a.ticket, 1);
     const int pad = a.item_pad[item];
     const int ty = a.pad_type[pad];
     const int o = a.type_off[ty];
@@ -155,211 +242,197 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       const int* src = reinterpret_cast<const int*>(a.padobj + (size_t)pad * a.K);
       int* dst = reinterpret_cast<int*>(spo);
       const int words = a.K * (int)(sizeof(PadObj) / 4);
-      for (int e = tid; e < words; e += FT) dst[e] = src[e];
-      if (tid == 0 && a.pad_bad[pad]) sCnt[2] = 1;
+      for (int e = lane; e < words; e += 32) dst[e] = src[e];
     }
-    for (int w = tid; w < nwords; w += FT) sActBits[w] = 0u;
-    __syncthreads();
-    const bool invalid = sCnt[2] != 0;
+    const bool invalid = a.pad_bad[pad] != 0;
+    __syncwarp();
     float gap = 0.f;   // twice the largest FP32 error bound over the pad's objects
     for (int k = 0; k < a.K; ++k) gap = fmaxf(gap, 2.f * spo[k].tau);
 
-    // ---- 1. FP32 screen of every node.  Nodes certainly outside stay passive; nodes certainly
-    // inside with no near-tie in their discrete choices take the FP32 u_hat (BF16 accuracy is
-    // the budget here); only the thin band near a surface or a tie goes to the exact df32 path.
-    for (int r0 = 0; r0 < n; r0 += FT) {
-      const int i = r0 + tid;
-      bool cand = false;
-      NodeContact c;
-      c.active = false;
-      c.phi = 0.f;
-      c.k = -1;
-      c.u[0] = c.u[1] = c.u[2] = 0.f;
-      if (i < n && !invalid) {
-        const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
-        float phi32;
-        if (contact_screen(spo, a.K, p, &phi32)) {
-          const float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-          cand = !contact_fast(spo, a.K, p, nr, gap, &c);
-        }
-      }
-      if (i < n && !cand) {
-        btrow[i] = __float2bfloat16_rn(c.u[0]);
-        btrow[n + i] = __float2bfloat16_rn(c.u[1]);
-        btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
-        if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
-        if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
-        if (c.active) {
-          float* d = a.disp + 3 * (base + i);
-          d[0] = c.u[0];
-          d[1] = c.u[1];
-          d[2] = c.u[2];
-          atomicOr(&sActBits[i >> 5], 1u << (i & 31));
-        }
-      }
-      const int slot = warp_append(cand, &sCnt[0]);
-      if (slot >= 0) sCand[slot] = (int16_t)i;
-      const int aslot = warp_append(c.active, &sCnt[1]);
-      if (aslot >= 0) {
-        sActIdx[aslot] = (int16_t)i;
-        sActU[aslot] = make_float4(c.u[0], c.u[1], c.u[2], 0.f);
-      }
-    }
-    __syncthreads();
+    float fm[8][2];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt) fm[nt][0] = fm[nt][1] = -INFINITY;
+    int npend = 0, ncand = 0, m = 0;   // warp-uniform
 
-    // ---- 2. exact contact of the band candidates
-    const int nc = sCnt[0];
-    for (int s0 = 0; s0 < nc; s0 += FT) {
-      const int s = s0 + tid;
+    // exact decision of the top (up to) 32 undecided nodes; the active ones join the stack
+    auto refine_batch = [&]() {
+      const int cnt = min(32, ncand);
+      const bool has = lane < cnt;
       NodeContact c;
       c.active = false;
       c.phi = 0.f;
       c.k = -1;
       c.u[0] = c.u[1] = c.u[2] = 0.f;
       int i = 0;
-      if (s < nc) {
-        i = sCand[s];
-        const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
-        const float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+      float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
+      if (has) {
+        i = sCand[ncand - cnt + lane];
+        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
         c = contact_refine(spo, a.K, p, nr, 0.f);
-        btrow[i] = __float2bfloat16_rn(c.u[0]);
-        btrow[n + i] = __float2bfloat16_rn(c.u[1]);
-        btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
-        if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
-        if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
-        if (c.active) {
-          float* d = a.disp + 3 * (base + i);
-          d[0] = c.u[0];
-          d[1] = c.u[1];
-          d[2] = c.u[2];
-          atomicOr(&sActBits[i >> 5], 1u << (i & 31));
-        }
+        front_write_node(a, btrow, n, base, i, c);
+        if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       }
-      const int slot = warp_append(c.active, &sCnt[1]);
-      if (slot >= 0) {
-        sActIdx[slot] = (int16_t)i;
-        sActU[slot] = make_float4(c.u[0], c.u[1], c.u[2], 0.f);
+      ncand -= cnt;
+      const unsigned b = __ballot_sync(FULL, c.active);
+      if (c.active && enc) {
+        const int q = npend + __popc(b & lt);
+        front_pack_row(sPendA + 2 * q, p, nr, c.u);
+      }
+      m += __popc(b);
+      if (enc) npend += __popc(b);
+      __syncwarp();
+    };
+    auto drain = [&](int keep) {   // encode full tiles until at most `keep` remain
+      while (npend > keep) {
+        const int cnt = min(16, npend);
+        front_encode(fm, sPendA_addr + 32u * (uint32_t)(npend - cnt), cnt, sW1f, sW2f, lane);
+        npend -= cnt;
+      }
+      __syncwarp();
+    };
+
+    for (int r0 = 0; r0 < n; r0 += 32) {
+      const int i = r0 + lane;
+      int cls = CONTACT_OUT;
+      NodeContact c;
+      c.active = false;
+      c.phi = 0.f;
+      c.k = -1;
+      c.u[0] = c.u[1] = c.u[2] = 0.f;
+      float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
+      if (i < n && !invalid) {
+        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+        cls = contact_classify(spo, a.K, p, nr, gap, &c);
+      }
+      if (i < n && cls != CONTACT_BAND) front_write_node(a, btrow, n, base, i, c);
+      const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
+      const unsigned bC = __ballot_sync(FULL, cls == CONTACT_BAND);
+      if (lane == 0) sBits[r0 >> 5] = bA;
+      if (cls == CONTACT_FAST && enc) {
+        const int q = npend + __popc(bA & lt);
+        front_pack_row(sPendA + 2 * q, p, nr, c.u);
+      }
+      if (cls == CONTACT_BAND) sCand[ncand + __popc(bC & lt)] = (int16_t)i;
+      m += __popc(bA);
+      if (enc) npend += __popc(bA);
+      ncand += __popc(bC);
+      __syncwarp();
+      drain(15);
+      if (ncand > CANDCAP - 32) {
+        refine_batch();
+        drain(15);
       }
     }
-    __syncthreads();
-    const int m = sCnt[1];
-    for (int w = tid; w < nwords; w += FT) a.maskbits[a.mask_woff[pad] + w] = sActBits[w];
-    if (tid == 0) {
+    while (ncand > 0) {
+      refine_batch();
+      drain(15);
+    }
+    drain(0);
+
+    for (int w = lane; w < nwords; w += 32) a.maskbits[a.mask_woff[pad] + w] = sBits[w];
+    if (lane == 0) {
       if (a.count) a.count[pad] = m;
       a.pad_m[pad] = m;
       if (invalid) latch_status(a.status, STATUS_NONFINITE);
     }
     if (m == 0) {   // no contact (or invalid pose): the whole pad is at rest
-      for (int i = tid; i < n; i += FT) {
-        float* d = a.disp + 3 * (base + i);
-        d[0] = d[1] = d[2] = 0.f;
-      }
+      float* d = a.disp + 3 * base;
+      for (int e = lane; e < 3 * n; e += 32) d[e] = 0.f;
       continue;
     }
-    if (a.mode == MODE_LINEAR_ONLY) continue;
+    if (!enc) continue;
 
-    // ---- 3. encoder of the active nodes on tensor cores, channel maxima
-    {
-      const int grp = lane >> 2, tig = lane & 3;
-      float fm[8][2];
+    // channel maxima of the active nodes: reduce over the tile rows (lane groups), then park
+    // them in shared memory by channel
 #pragma unroll
-      for (int nt = 0; nt < 8; ++nt) fm[nt][0] = fm[nt][1] = 0.f;   // ReLU outputs are >= 0
-      for (int g = warp; g * 16 < m; g += FW) {
-        const int s0 = 16 * g + grp, s1 = s0 + 8;
-        const bool v0 = s0 < m, v1 = s1 < m;
-        const int n0 = v0 ? sActIdx[s0] : 0, n1 = v1 ? sActIdx[s1] : 0;
-        const float4 u0 = v0 ? sActU[s0] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float4 u1 = v1 ? sActU[s1] : make_float4(0.f, 0.f, 0.f, 0.f);
-        const float* c0r = a.ctab + (size_t)(o + n0) * H;
-        const float* c1r = a.ctab + (size_t)(o + n1) * H;
-        uint32_t af[4][4];
+    for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
-        for (int s4 = 0; s4 < 4; ++s4) {
-#pragma unroll
-          for (int hh = 0; hh < 2; ++hh) {
-            const int col = 16 * s4 + 8 * hh + 2 * tig;
-            const float2 ca = __ldg(reinterpret_cast<const float2*>(c0r + col));
-            const float2 cb = __ldg(reinterpret_cast<const float2*>(c1r + col));
-            const float4 w0 = sW1u[col], w1 = sW1u[col + 1];
-            const float z00 = fmaxf(fmaf(w0.x, u0.x, fmaf(w0.y, u0.y, fmaf(w0.z, u0.z, ca.x))), 0.f);
-            const float z01 = fmaxf(fmaf(w1.x, u0.x, fmaf(w1.y, u0.y, fmaf(w1.z, u0.z, ca.y))), 0.f);
-            const float z10 = fmaxf(fmaf(w0.x, u1.x, fmaf(w0.y, u1.y, fmaf(w0.z, u1.z, cb.x))), 0.f);
-            const float z11 = fmaxf(fmaf(w1.x, u1.x, fmaf(w1.y, u1.y, fmaf(w1.z, u1.z, cb.y))), 0.f);
-            __nv_bfloat162 p0 = __floats2bfloat162_rn(z00, z01);
-            __nv_bfloat162 p1 = __floats2bfloat162_rn(z10, z11);
-            af[s4][2 * hh + 0] = *reinterpret_cast<uint32_t*>(&p0);
-            af[s4][2 * hh + 1] = *reinterpret_cast<uint32_t*>(&p1);
-          }
-        }
-#pragma unroll
-        for (int nt = 0; nt < 8; ++nt) {
-          const float bx = sB2[8 * nt + 2 * tig], by = sB2[8 * nt + 2 * tig + 1];
-          float acc[4] = {bx, by, bx, by};
-#pragma unroll
-          for (int s4 = 0; s4 < 4; ++s4) {
-            const uint2 bb = sW2f[(nt * 4 + s4) * 32 + lane];
-            sm100::mma_bf16_16816(acc, af[s4], bb.x, bb.y, acc);
-          }
-          fm[nt][0] = fmaxf(fm[nt][0], fmaxf(v0 ? acc[0] : 0.f, v1 ? acc[2] : 0.f));
-          fm[nt][1] = fmaxf(fm[nt][1], fmaxf(v0 ? acc[1] : 0.f, v1 ? acc[3] : 0.f));
-        }
+      for (int e = 0; e < 2; ++e) {
+        float v = fm[nt][e];
+        v = fmaxf(v, __shfl_xor_sync(FULL, v, 4));
+        v = fmaxf(v, __shfl_xor_sync(FULL, v, 8));
+        v = fmaxf(v, __shfl_xor_sync(FULL, v, 16));
+        if (lane < 4) sFmax[8 * nt + 2 * lane + e] = fmaxf(v + sB2[8 * nt + 2 * lane + e], 0.f);
       }
-#pragma unroll
-      for (int nt = 0; nt < 8; ++nt)
-#pragma unroll
-        for (int e = 0; e < 2; ++e) {
-          float v = fm[nt][e];
-          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 4));
-          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 8));
-          v = fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 16));
-          if (grp == 0) sRed[warp * H + 8 * nt + 2 * tig + e] = v;
-        }
-    }
-    __syncthreads();
+    __syncwarp();
     // max-pool over the passive nodes: the first passive node in each channel's descending
-    // order of f0; a warp tests 32 ranks per load for 8 channels at a time
+    // order of f0.  First step: lane l tests ranks 0..3 of channels l and l + 32, which settles
+    // most channels.  Walks are long-tailed (the top of a channel's order can sit inside the
+    // contact patch), so the rest go warp-wide: 8 channels per batch, 32 ranks per test.
     {
-      float best[CPW];
-      bool done[CPW];
+      const float2* rk = a.ranked + (size_t)H * o;
+      const float2* row0 = rk + (size_t)lane * n;
+      const float2* row1 = rk + (size_t)(lane + 32) * n;
+      float best0 = 0.f, best1 = 0.f;   // empty passive set: features are >= 0
+      bool done0 = false, done1 = false;
+      {
+        float2 e0[4], e1[4];
 #pragma unroll
-      for (int c = 0; c < CPW; ++c) {
-        best[c] = 0.f;
-        done[c] = false;
-      }
-      for (int r0 = 0; r0 < n; r0 += 32) {
-        const int r = r0 + lane;
-        float2 e[CPW];
-#pragma unroll
-        for (int c = 0; c < CPW; ++c) {
-          const int u = warp * CPW + c;
-          e[c] = (!done[c] && r < n) ? __ldg(a.ranked + (size_t)H * o + (size_t)u * n + r)
-                                      : make_float2(0.f, __int_as_float(0));
+        for (int j = 0; j < 4; ++j) {
+          const bool in = j < n;
+          e0[j] = in ? __ldg(row0 + j) : make_float2(0.f, __int_as_float(-1));
+          e1[j] = in ? __ldg(row1 + j) : make_float2(0.f, __int_as_float(-1));
         }
-        bool all = true;
 #pragma unroll
-        for (int c = 0; c < CPW; ++c) {
-          const int idx = __float_as_int(e[c].y);
-          const bool passive = !done[c] && r < n && !((sActBits[idx >> 5] >> (idx & 31)) & 1u);
-          const unsigned bal = __ballot_sync(0xffffffffu, passive);
-          if (bal) {
-            best[c] = __shfl_sync(0xffffffffu, e[c].x, __ffs(bal) - 1);
-            done[c] = true;
+        for (int j = 0; j < 4; ++j) {
+          const int i0 = __float_as_int(e0[j].y), i1 = __float_as_int(e1[j].y);
+          if (!done0 && i0 >= 0 && !((sBits[i0 >> 5] >> (i0 & 31)) & 1u)) {
+            best0 = e0[j].x;
+            done0 = true;
           }
-          all &= done[c];
+          if (!done1 && i1 >= 0 && !((sBits[i1 >> 5] >> (i1 & 31)) & 1u)) {
+            best1 = e1[j].x;
+            done1 = true;
+          }
         }
-        if (all) break;
+        if (n <= 4) done0 = done1 = true;
       }
-      if (lane < CPW) {
-        float v = 0.f;
+      unsigned long long open = (unsigned long long)__ballot_sync(FULL, !done0) |
+                                ((unsigned long long)__ballot_sync(FULL, !done1) << 32);
+      while (open) {   // warp-uniform
+        int ch[8];
+        bool dn[8];
+        float bv[8];
 #pragma unroll
-        for (int c = 0; c < CPW; ++c)
-          if (c == lane) v = best[c];
-        const int u = warp * CPW + lane;
+        for (int c = 0; c < 8; ++c) {
+          ch[c] = open ? __ffsll((long long)open) - 1 : -1;
+          if (open) open &= open - 1;
+          dn[c] = ch[c] < 0;
+          bv[c] = 0.f;
+        }
+        for (int q0 = 4; q0 < n; q0 += 32) {
+          const int r = q0 + lane;
+          float2 e[8];
 #pragma unroll
-        for (int w = 0; w < FW; ++w) v = fmaxf(v, sRed[w * H + u]);
-        a.g0a[(size_t)pad * H + u] = v;
+          for (int c = 0; c < 8; ++c)
+            e[c] = (!dn[c] && r < n) ? __ldg(rk + (size_t)ch[c] * n + r)
+                                     : make_float2(0.f, __int_as_float(0));
+          bool all = true;
+#pragma unroll
+          for (int c = 0; c < 8; ++c) {
+            const int idx = __float_as_int(e[c].y);
+            const bool passive = !dn[c] && r < n && !((sBits[idx >> 5] >> (idx & 31)) & 1u);
+            const unsigned bal = __ballot_sync(FULL, passive);
+            if (bal) {
+              bv[c] = __shfl_sync(FULL, e[c].x, __ffs(bal) - 1);
+              dn[c] = true;
+            }
+            all &= dn[c];
+          }
+          if (all) break;
+        }
+#pragma unroll
+        for (int c = 0; c < 8; ++c) {
+          if (ch[c] == lane) best0 = bv[c];
+          if (ch[c] == lane + 32) best1 = bv[c];
+        }
       }
+      a.g0a[(size_t)pad * H + lane] = fmaxf(best0, sFmax[lane]);
+      a.g0a[(size_t)pad * H + lane + 32] = fmaxf(best1, sFmax[lane + 32]);
     }
+    __syncwarp();
   }
 }
 
