@@ -217,10 +217,12 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
   o->dims[0] = dims[0];
   o->dims[1] = dims[1];
   o->dims[2] = dims[2];
-  // FP32 evaluation of q = R p + t and of the SDF has relative error below ~1e-6 of the
-  // magnitudes involved; 3e-6 * (|t| + |p| + size) is a >= 3x margin, plus 10 um absolute.
+  // FP32 error of phi: R rounded to FP32 (u |p|), the three FMAs of q = R p + t
+  // (3u (sqrt(3) |p| + |t|) per component), the SDF's squares, root and differences
+  // (~2.5u |q| + u (|q| + size)) and |q| <= |p| + |t| give |phi32 - phi| < 16u (|t| + |p| + size)
+  // with u = 2^-24; tau = 3e-6 (~50u) of those magnitudes is a 3x margin (plus 1e-5 mm).
   float size = fmaxf(fmaxf(fabsf(dims[0]), fabsf(dims[1])), fabsf(dims[2]));
-  o->tau = 1e-2f + 3e-6f * (tmax + pmax + size);
+  o->tau = 1e-5f + 3e-6f * (tmax + pmax + size);
 }
 
 // ------------------------------------------------------------------ signed distances

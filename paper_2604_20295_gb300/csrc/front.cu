@@ -39,7 +39,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 // shared weights, then one region per warp
 struct FrontSmem {
-  size_t w2f, w1f, b2, warp0, warp_bytes, po, bits, pend_a, cand, fmax, total;
+  size_t w2f, w1f, b2, warp0, warp_bytes, po, bits, pend_a, cand, fmax, fmlane, total;
   __host__ __device__ FrontSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -57,6 +57,7 @@ struct FrontSmem {
     pend_a = take(sizeof(uint4) * 2 * PEND);
     cand = take(sizeof(int16_t) * CANDCAP);
     fmax = take(sizeof(float) * H);
+    fmlane = take(sizeof(float) * 16 * 32);
     warp_bytes = o;
     total = warp0 + FW * warp_bytes;
   }
@@ -175,7 +176,7 @@ __device__ __forceinline__ void front_encode(float (&fm)[8][2], uint32_t rows, i
   }
 }
 
-__global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
+__global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FrontSmem L(a.nmax, a.K);
   uint2* sW2f = reinterpret_cast<uint2*>(smem + L.w2f);
@@ -217,6 +218,7 @@ __global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
   const uint32_t sPendA_addr = (uint32_t)__cvta_generic_to_shared(sPendA);
   int16_t* sCand = reinterpret_cast<int16_t*>(wb + L.cand);
   float* sFmax = reinterpret_cast<float*>(wb + L.fmax);
+  float* sFm = reinterpret_cast<float*>(wb + L.fmlane) + lane;   // lane's maxima, stride 32
   const unsigned lt = (1u << lane) - 1u;
   const bool enc = a.mode != MODE_LINEAR_ONLY;
 
@@ -249,9 +251,10 @@ __global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
     float gap = 0.f;   // twice the largest FP32 error bound over the pad's objects
     for (int k = 0; k < a.K; ++k) gap = fmaxf(gap, 2.f * spo[k].tau);
 
-    float fm[8][2];
+    // running channel maxima live in shared memory between drains (registers go to the
+    // contact pass)
 #pragma unroll
-    for (int nt = 0; nt < 8; ++nt) fm[nt][0] = fm[nt][1] = -INFINITY;
+    for (int q = 0; q < 16; ++q) sFm[32 * q] = -INFINITY;
     int npend = 0, ncand = 0, m = 0;   // warp-uniform
 
     // exact decision of the top (up to) 32 undecided nodes; the active ones join the stack
@@ -284,10 +287,17 @@ __global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
       __syncwarp();
     };
     auto drain = [&](int keep) {   // encode full tiles until at most `keep` remain
-      while (npend > keep) {
-        const int cnt = min(16, npend);
-        front_encode(fm, sPendA_addr + 32u * (uint32_t)(npend - cnt), cnt, sW1f, sW2f, lane);
-        npend -= cnt;
+      if (npend > keep) {
+        float fm[8][2];
+#pragma unroll
+        for (int q = 0; q < 16; ++q) fm[q >> 1][q & 1] = sFm[32 * q];
+        while (npend > keep) {
+          const int cnt = min(16, npend);
+          front_encode(fm, sPendA_addr + 32u * (uint32_t)(npend - cnt), cnt, sW1f, sW2f, lane);
+          npend -= cnt;
+        }
+#pragma unroll
+        for (int q = 0; q < 16; ++q) sFm[32 * q] = fm[q >> 1][q & 1];
       }
       __syncwarp();
     };
@@ -350,7 +360,7 @@ __global__ void __launch_bounds__(FT, 3) front_contact_kernel(FrontArgs a) {
     for (int nt = 0; nt < 8; ++nt)
 #pragma unroll
       for (int e = 0; e < 2; ++e) {
-        float v = fm[nt][e];
+        float v = sFm[32 * (2 * nt + e)];
         v = fmaxf(v, __shfl_xor_sync(FULL, v, 4));
         v = fmaxf(v, __shfl_xor_sync(FULL, v, 8));
         v = fmaxf(v, __shfl_xor_sync(FULL, v, 16));
