@@ -14,8 +14,9 @@
 // accumulators, warps 0-7 drain the other accumulator.  The epilogue evaluates, for every
 // passive node i and instance k, the decoder residual
 //     Phi = D2 ReLU(h0_i + beta_k) + b = D2 max(h0_i, -beta_k) + (D2 beta_k + b)
-// with a warp-level BF16 MMA (m16n8k16) per instance, adds the propagated term and stores
-// the displacement (Eq. 4).  Every wait is bounded; a timeout latches ETAC_ERR_TIMEOUT and
+// with warp-level BF16 MMAs (m16n8k16) per instance, adds the propagated term and stores the
+// displacement (Eq. 4).  h0 is held in registers in the MMA A-fragment layout, so the
+// operand max(h0, -beta) is formed in registers (no shared-memory staging).  Every wait is bounded; a timeout latches ETAC_ERR_TIMEOUT and
 // the CTA winds down (waiting, bounded, for its in-flight copies and MMAs before freeing TMEM).
 #include <cuda_bf16.h>
 
@@ -32,7 +33,7 @@ constexpr int GM = 128;                 // node rows per tile
 constexpr int GI = 64;                  // instances per tile
 constexpr int GN = 3 * GI;              // 192 accumulator columns
 constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
-constexpr int STAGES = 3;
+constexpr int STAGES = 4;
 constexpr int EPI_WARPS = 8;
 constexpr int TMA_WARP = 8, MMA_WARP = 9;
 constexpr int THREADS = 10 * 32;
@@ -45,9 +46,8 @@ constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
 // shared-memory layout (offsets from a 1024-byte aligned base)
 constexpr size_t SM_A = 0;
 constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
-constexpr size_t SM_Z = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x 2 x 32 x 128 B
-constexpr size_t SM_R = SM_Z + (size_t)EPI_WARPS * 2 * 32 * 128;  // 8 warps x 2 x 32 x float4
-constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 2 * 32 * 16;  // 64 x 64 BF16
+constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x 2 x 32 x float4
+constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 2 * 32 * 16;  // 64 x 64 BF16, fragment order
 constexpr size_t SM_C0 = SM_NB + (size_t)GI * H * 2;              // 64 x float4
 constexpr size_t SM_BASE = SM_C0 + (size_t)GI * 16;               // 64 x int64
 constexpr size_t SM_BITS = SM_BASE + (size_t)GI * 8;              // 64 x 4 contact words
@@ -199,7 +199,6 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     // ---------------------------------------------------------------- epilogue (warps 0-7)
     const int q = warp & 3, half = warp >> 2, etid = threadIdx.x;   // etid in [0, 256)
     const int grp = lane >> 2, tig = lane & 3;
-    unsigned char* zbuf = smem + SM_Z + (size_t)warp * 2 * 32 * 128;
     float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * 2 * 32 * 16);
     __nv_bfloat16* s_nb = reinterpret_cast<__nv_bfloat16*>(smem + SM_NB);
     float4* s_c0 = reinterpret_cast<float4*>(smem + SM_C0);
@@ -248,23 +247,39 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
           }
           if (chunk < 4) s_bits[inst * 4 + chunk] = 0u;
         }
-        reinterpret_cast<uint4*>(s_nb)[inst * 8 + chunk] = v;
+        // fragment order: word w = 8 s + 4 h + t (columns 16 s + 8 h + 2 t, +1) goes to
+        // position 8 t + 2 s + h, so lane (., t) reads its 8 words as two 16-byte loads
+        {
+          uint32_t* dst = reinterpret_cast<uint32_t*>(s_nb) + inst * 32;
+          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const int w = 4 * chunk + e, s4 = w >> 3, hh = (w >> 2) & 1, tt = w & 3;
+            dst[8 * tt + 2 * s4 + hh] = wv[e];
+          }
+        }
       }
       named_bar_sync(1, EPI_WARPS * 32);
       const int i = T.m0 + 32 * q + lane;   // my node row within the pad type
       const bool row_ok = i < n_t;
-      uint32_t h0[32];
+      // h0 of the warp's 32 rows in A-fragment layout: hf[rg][s][e] holds rows
+      // 16 rg + grp (+ 8 for e = 1, 3), columns 16 s + 2 tig (+ 8 for e = 2, 3), BF16 pairs
+      uint32_t hf[2][4][4];
       {
-        const uint4* src = reinterpret_cast<const uint4*>(p.h0bf16) +
-                           (size_t)(p.type_off[t] + (row_ok ? i : 0)) * 8;
+        const uint32_t* hw = reinterpret_cast<const uint32_t*>(p.h0bf16);
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
-          const uint4 v = row_ok ? src[c] : make_uint4(0u, 0u, 0u, 0u);
-          h0[4 * c + 0] = v.x;
-          h0[4 * c + 1] = v.y;
-          h0[4 * c + 2] = v.z;
-          h0[4 * c + 3] = v.w;
-        }
+        for (int rg = 0; rg < 2; ++rg)
+#pragma unroll
+          for (int e2 = 0; e2 < 2; ++e2) {
+            const int r = T.m0 + 32 * q + 16 * rg + grp + 8 * e2;
+            const bool ok = r < n_t;
+            const uint32_t* src = hw + (size_t)(p.type_off[t] + (ok ? r : 0)) * 32 + tig;
+#pragma unroll
+            for (int s4 = 0; s4 < 4; ++s4) {
+              hf[rg][s4][e2] = ok ? src[8 * s4] : 0u;
+              hf[rg][s4][2 + e2] = ok ? src[8 * s4 + 4] : 0u;
+            }
+          }
       }
       if (!mbar_wait(&acc_full[b], acc_phase, s_abort, limit)) {
         *s_abort = 1;
@@ -297,23 +312,6 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
           // two instances at a time: independent MMA chains for latency hiding
           float4 r[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
           if (p.use_r) {
-#pragma unroll
-            for (int x = 0; x < 2; ++x) {
-              // Z row = max(h0_i, -beta_k): 128-byte row, 16-byte chunks XOR-swizzled by row
-              const uint4* nb = reinterpret_cast<const uint4*>(s_nb + (inst0 + jj + x) * H);
-              unsigned char* zb = zbuf + x * 32 * 128;
-#pragma unroll
-              for (int c = 0; c < 8; ++c) {
-                const uint4 v = nb[c];
-                uint4 z;
-                z.x = bf16x2_max(h0[4 * c + 0], v.x);
-                z.y = bf16x2_max(h0[4 * c + 1], v.y);
-                z.z = bf16x2_max(h0[4 * c + 2], v.z);
-                z.w = bf16x2_max(h0[4 * c + 3], v.w);
-                *reinterpret_cast<uint4*>(zb + lane * 128 + ((c ^ (lane & 7)) << 4)) = z;
-              }
-            }
-            __syncwarp();
             float acc[2][2][4];
 #pragma unroll
             for (int x = 0; x < 2; ++x)
@@ -321,19 +319,22 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
               for (int rg = 0; rg < 2; ++rg)
 #pragma unroll
                 for (int e = 0; e < 4; ++e) acc[x][rg][e] = 0.f;
-            const int mi = lane >> 3;
 #pragma unroll
-            for (int s = 0; s < 4; ++s) {
-              const int chunk = 2 * s + (mi >> 1);
+            for (int x = 0; x < 2; ++x) {
+              // -beta_k for this lane's columns: nb[2 s + h] = columns 16 s + 8 h + 2 tig, +1
+              const uint4* nbp = reinterpret_cast<const uint4*>(s_nb + (inst0 + jj + x) * H) + 2 * tig;
+              const uint4 n0 = nbp[0], n1 = nbp[1];
+              const uint32_t nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
-              for (int x = 0; x < 2; ++x)
+              for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
                 for (int rg = 0; rg < 2; ++rg) {
-                  const int row = rg * 16 + (lane & 7) + (mi & 1) * 8;
                   uint32_t a[4];
-                  ldmatrix_x4(smem_u32(zbuf + x * 32 * 128 + row * 128 + ((chunk ^ (row & 7)) << 4)),
-                              a[0], a[1], a[2], a[3]);
-                  mma_bf16_16816(acc[x][rg], a, bw[s][0], bw[s][1], acc[x][rg]);
+                  a[0] = bf16x2_max(hf[rg][s4][0], nb[2 * s4]);
+                  a[1] = bf16x2_max(hf[rg][s4][1], nb[2 * s4]);
+                  a[2] = bf16x2_max(hf[rg][s4][2], nb[2 * s4 + 1]);
+                  a[3] = bf16x2_max(hf[rg][s4][3], nb[2 * s4 + 1]);
+                  mma_bf16_16816(acc[x][rg], a, bw[s4][0], bw[s4][1], acc[x][rg]);
                 }
             }
 #pragma unroll
