@@ -72,6 +72,9 @@ struct etac_ctx {
   float2* d_ranked = nullptr;
   etac::PadObj* d_padobj = nullptr;
   int* d_pad_bad = nullptr;
+  int* d_pad_gi = nullptr;
+  long long* d_inst_base = nullptr;
+  long long* d_type_woff = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0;
@@ -154,7 +157,8 @@ void free_ctx(etac_ctx* c) {
                   c->d_h0tab, c->d_order, c->d_omega, c->d_omega_bf16, c->d_h0bf16, c->d_bt,
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
                   c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
-                  c->d_g0a, c->d_ranked, c->d_padobj, c->d_pad_bad, c->d_ws_idx, c->d_ws_u,
+                  c->d_g0a, c->d_ranked, c->d_padobj, c->d_pad_bad, c->d_pad_gi, c->d_inst_base,
+                  c->d_type_woff, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -205,8 +209,22 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
     const int t = c->pad_type[p];
     inst_pad[inst_off[t] + fill[t]++] = p;
   }
-  std::vector<long long> woff(np + 1, 0);   // per-pad offsets of the contact bit words
-  for (int p = 0; p < np; ++p) woff[p + 1] = woff[p] + (c->type_n[c->pad_type[p]] + 31) / 32;
+  // contact bit words in instance order: type t's instances one after another, so a GEMM tile
+  // finds its rows' words at computable addresses; by-instance record indices for the same
+  std::vector<long long> type_woff(c->T, 0), woff(np + 1, 0), inst_base(np);
+  std::vector<int> pad_gi(np);
+  long long wtot = 0;
+  for (int t = 0; t < c->T; ++t) {
+    type_woff[t] = wtot;
+    wtot += (long long)ninst[t] * ((c->type_n[t] + 31) / 32);
+  }
+  for (int p = 0; p < np; ++p) {
+    const int t = c->pad_type[p];
+    woff[p] = type_woff[t] + (long long)pad_inst[p] * ((c->type_n[t] + 31) / 32);
+    pad_gi[p] = inst_off[t] + pad_inst[p];
+    inst_base[pad_gi[p]] = c->pad_off[p];
+  }
+  woff[np] = wtot;
   std::vector<long long> bt_off(c->T, 0);
   long long bt_total = 0;
   for (int t = 0; t < c->T; ++t) {
@@ -242,6 +260,15 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_padobj, (size_t)np * c->K);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_bad, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->d_pad_gi, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->d_inst_base, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->d_type_woff, (size_t)c->T);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pad_gi, pad_gi.data(), sizeof(int) * np,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_base, inst_base.data(),
+                                            sizeof(long long) * np, cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_type_woff, type_woff.data(),
+                                            sizeof(long long) * c->T, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
@@ -281,11 +308,12 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   g.inst_off = c->d_inst_off;
   g.inst_pad = c->d_inst_pad;
   g.pad_off = c->d_pad_off;
+  g.inst_base = c->d_inst_base;
+  g.type_woff = c->d_type_woff;
   g.h0bf16 = c->d_h0bf16;
   g.negbeta = c->d_negbeta;
   g.c0m = c->d_c0m;
   g.maskbits = c->d_maskbits;
-  g.mask_woff = c->d_mask_woff;
   g.params = c->d_params;
   g.status = c->d_status;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
@@ -634,9 +662,10 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.g0a = c->d_g0a;
       f.negbeta = c->d_negbeta;
       f.c0m = c->d_c0m;
+      f.pad_gi = c->d_pad_gi;
       f.padobj = c->d_padobj;
       f.pad_bad = c->d_pad_bad;
-      if (!f.padobj || !f.pad_bad || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
+      if (!f.padobj || !f.pad_bad || !f.pad_gi || !c->gemm.inst_base || !c->gemm.type_woff || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
           !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");

@@ -124,8 +124,9 @@ struct FrontArgs {
   const long long* mask_woff;
   int* pad_m;                   // [E*P] active count
   float* g0a;                   // [E*P][64] max-pooled global feature g0 of each pad
-  void* negbeta;                // [E*P][64] BF16
-  float4* c0m;                  // [E*P]
+  const int* pad_gi;            // [E*P] global instance index (type's first instance + k)
+  void* negbeta;                // [sum I_t][64] BF16 in MMA-fragment word order (by instance)
+  float4* c0m;                  // [sum I_t] by instance
   PadObj* padobj;               // [E*P][K] pad -> object transforms
   int* pad_bad;                 // [E*P] 1 when a pose or size held NaN / Inf
 };
@@ -162,10 +163,11 @@ struct GemmParams {
   const int* inst_pad;               // [sum I_t] pad index of instance k of type t
   const long long* pad_off;
   const void* h0bf16;                // [sum n][64]
-  const void* negbeta;               // [E*P][64]
-  const float4* c0m;                 // [E*P]
-  const uint32_t* maskbits;          // contact bits per pad (32 nodes per word)
-  const long long* mask_woff;        // [E*P+1]
+  const void* negbeta;               // [sum I_t][64] BF16 by instance, MMA-fragment word order
+  const float4* c0m;                 // [sum I_t] (D2 beta + b_D2, m) by instance
+  const long long* inst_base;        // [sum I_t] first node of each instance's pad
+  const uint32_t* maskbits;          // contact bits, instance order: type t, instance k at
+  const long long* type_woff;        //   type_woff[t] + k * ceil(n_t / 32)
   const float* params;
   float* disp;
   int use_l, use_r;

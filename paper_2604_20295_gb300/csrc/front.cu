@@ -468,8 +468,9 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
   const int np = a.num_items;
   for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < np; pad += gridDim.x * wpb) {
     const int m = a.pad_m[pad];
+    const int gi = a.pad_gi[pad];
     if (m == 0 || a.mode == MODE_LINEAR_ONLY) {
-      if (lane == 0) a.c0m[pad] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
+      if (lane == 0) a.c0m[gi] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
       continue;
     }
     float g0[2];
@@ -497,7 +498,16 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
       for (int k = 0; k < 32; ++k)
         acc = fmaf(sWdT[(32 + k) * H + u], __shfl_sync(0xffffffffu, g[1], k), acc);
       beta[h] = acc;
-      reinterpret_cast<__nv_bfloat16*>(a.negbeta)[(size_t)pad * H + u] = __float2bfloat16_rn(-acc);
+      // -beta in BF16, words (channels 2w, 2w + 1) stored in MMA-fragment order: word
+      // w = 8 s + 4 hh + t goes to position 8 t + 2 s + hh (see the propagation GEMM)
+      __nv_bfloat16 nbv = __float2bfloat16_rn(-acc);
+      const unsigned short mine = *reinterpret_cast<unsigned short*>(&nbv);
+      const unsigned short odd = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)mine, 1);
+      if ((lane & 1) == 0) {
+        const int w = u >> 1, s4 = w >> 3, hh = (w >> 2) & 1, t = w & 3;
+        reinterpret_cast<uint32_t*>(a.negbeta)[(size_t)gi * 32 + 8 * t + 2 * s4 + hh] =
+            (uint32_t)mine | ((uint32_t)odd << 16);
+      }
     }
     float c0[3];
 #pragma unroll
@@ -507,7 +517,7 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
       for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
       c0[q] = v + sB4[q];
     }
-    if (lane == 0) a.c0m[pad] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
+    if (lane == 0) a.c0m[gi] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
   }
 }
 

@@ -33,7 +33,7 @@ constexpr int GM = 128;                 // node rows per tile
 constexpr int GI = 64;                  // instances per tile
 constexpr int GN = 3 * GI;              // 192 accumulator columns
 constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
-constexpr int STAGES = 4;
+constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 8;
 constexpr int TMA_WARP = 8, MMA_WARP = 9;
 constexpr int THREADS = 10 * 32;
@@ -44,17 +44,26 @@ constexpr uint32_t ACC_STRIDE = 256;    // column offset of accumulator 1
 constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
 
 // shared-memory layout (offsets from a 1024-byte aligned base)
+constexpr int DEC = 4;                  // instances per decoder pass (independent MMA chains)
 constexpr size_t SM_A = 0;
 constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
-constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x 2 x 32 x float4
-constexpr size_t SM_NB = SM_R + (size_t)EPI_WARPS * 2 * 32 * 16;  // 64 x 64 BF16, fragment order
-constexpr size_t SM_C0 = SM_NB + (size_t)GI * H * 2;              // 64 x float4
-constexpr size_t SM_BASE = SM_C0 + (size_t)GI * 16;               // 64 x int64
-constexpr size_t SM_BITS = SM_BASE + (size_t)GI * 8;              // 64 x 4 contact words
-constexpr size_t SM_BAR = SM_BITS + (size_t)GI * 16;              // barriers
+constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x DEC x 32 x float4
+// per-tile epilogue records, double-buffered (filled one tile ahead with cp.async):
+// -beta (fragment order), (c0, m), node bases, contact words, h0 rows (16-byte chunks
+// XOR-swizzled by row so fragment reads are conflict-free)
+constexpr size_t STG_NB = 0;                                      // 64 x 64 BF16
+constexpr size_t STG_C0 = STG_NB + (size_t)GI * H * 2;            // 64 x float4
+constexpr size_t STG_BASE = STG_C0 + (size_t)GI * 16;             // 64 x int64
+constexpr size_t STG_BITS = STG_BASE + (size_t)GI * 8;            // 64 x 4 words
+constexpr size_t STG_H0 = STG_BITS + (size_t)GI * 16;             // 128 rows x 128 B
+constexpr size_t STG_BYTES = STG_H0 + (size_t)GM * 128;
+constexpr size_t SM_STG = SM_R + (size_t)EPI_WARPS * DEC * 32 * 16;
+constexpr size_t SM_BAR = SM_STG + 2 * STG_BYTES;                 // barriers
 constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
 constexpr size_t SM_TOTAL = SM_MISC + 16;
 constexpr size_t SM_ALLOC = SM_TOTAL + 1024;                      // alignment slack
+static_assert(STG_H0 % 128 == 0, "h0 staging rows must be 128-byte aligned");
+static_assert(SM_ALLOC <= 227 * 1024, "shared memory budget");
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -199,11 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     // ---------------------------------------------------------------- epilogue (warps 0-7)
     const int q = warp & 3, half = warp >> 2, etid = threadIdx.x;   // etid in [0, 256)
     const int grp = lane >> 2, tig = lane & 3;
-    float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * 2 * 32 * 16);
-    __nv_bfloat16* s_nb = reinterpret_cast<__nv_bfloat16*>(smem + SM_NB);
-    float4* s_c0 = reinterpret_cast<float4*>(smem + SM_C0);
-    long long* s_base = reinterpret_cast<long long*>(smem + SM_BASE);
-    uint32_t* s_bits = reinterpret_cast<uint32_t*>(smem + SM_BITS);
+    float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * DEC * 32 * 16);
     const float* W4 = p.params + OFF_W4;
     // decoder weights as constant B fragments: B[k = hidden][n = output component]
     uint32_t bw[4][2];
@@ -214,6 +219,43 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       bw[s][0] = live ? pack_bf16x2(W4[grp * H + k0], W4[grp * H + k0 + 1]) : 0u;
       bw[s][1] = live ? pack_bf16x2(W4[grp * H + k0 + 8], W4[grp * H + k0 + 9]) : 0u;
     }
+    // issues the asynchronous copies of one tile's records into staging buffer sb
+    auto stage = [&](const GemmTile& T, unsigned char* sb) {
+      const int t = T.type;
+      const int n_t = p.type_off[t + 1] - p.type_off[t];
+      const int nw = (n_t + 31) >> 5;
+      const int ninst = p.inst_off[t + 1] - p.inst_off[t];
+      const int gi0 = p.inst_off[t] + T.k0;
+      const uint32_t s0 = smem_u32(sb);
+      for (int idx = etid; idx < GI * 8; idx += EPI_WARPS * 32) {
+        const int inst = idx >> 3, ch = idx & 7;
+        const bool ok = T.k0 + inst < ninst;
+        cp_async16(s0 + (uint32_t)(STG_NB + 16 * idx),
+                   reinterpret_cast<const uint4*>(p.negbeta) + (size_t)(gi0 + (ok ? inst : 0)) * 8 + ch,
+                   ok ? 16u : 0u);
+      }
+      for (int idx = etid; idx < GI; idx += EPI_WARPS * 32) {
+        const bool ok = T.k0 + idx < ninst;
+        const int g = gi0 + (ok ? idx : 0);
+        cp_async16(s0 + (uint32_t)(STG_C0 + 16 * idx), p.c0m + g, ok ? 16u : 0u);
+        cp_async8(s0 + (uint32_t)(STG_BASE + 8 * idx), p.inst_base + g, ok ? 8u : 0u);
+      }
+      for (int idx = etid; idx < GI * 4; idx += EPI_WARPS * 32) {
+        const int inst = idx >> 2, w = (T.m0 >> 5) + (idx & 3);
+        const bool ok = T.k0 + inst < ninst && w < nw;
+        const long long off = ok ? p.type_woff[t] + (long long)(T.k0 + inst) * nw + w : 0;
+        cp_async4(s0 + (uint32_t)(STG_BITS + 4 * idx), p.maskbits + off, ok ? 4u : 0u);
+      }
+      for (int idx = etid; idx < GM * 8; idx += EPI_WARPS * 32) {
+        const int r = idx >> 3, ch = idx & 7, row = T.m0 + r;
+        const bool ok = row < n_t;
+        cp_async16(s0 + (uint32_t)(STG_H0 + 128 * r + ((ch ^ (r & 7)) << 4)),
+                   reinterpret_cast<const uint4*>(p.h0bf16) + (size_t)(p.type_off[t] + (ok ? row : 0)) * 8 + ch,
+                   ok ? 16u : 0u);
+      }
+      cp_async_commit();
+    };
+    if ((int)blockIdx.x < p.num_tiles) stage(p.tiles[blockIdx.x], smem + SM_STG);
     int local = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++local) {
       const GemmTile T = p.tiles[tile];
@@ -221,66 +263,34 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       const uint32_t acc_phase = (uint32_t)(local >> 1) & 1u;
       const int t = T.type;
       const int n_t = p.type_off[t + 1] - p.type_off[t];
-      const int nwords = (n_t + 31) >> 5;
-      const int ninst = p.inst_off[t + 1] - p.inst_off[t];
-      // per-instance records of this tile: -beta, (c0, m), node base, contact bits of the rows
+      unsigned char* sb = smem + SM_STG + (size_t)(local & 1) * STG_BYTES;
+      // this tile's records have landed; every warp is done with the other buffer
+      cp_async_wait_all();
       named_bar_sync(1, EPI_WARPS * 32);
-      for (int idx = etid; idx < GI * 8; idx += EPI_WARPS * 32) {
-        const int inst = idx >> 3, chunk = idx & 7;
-        const int k = T.k0 + inst;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (k < ninst) {
-          const int pad = p.inst_pad[p.inst_off[t] + k];
-          v = reinterpret_cast<const uint4*>(p.negbeta)[(size_t)pad * 8 + chunk];
-          if (chunk == 0) {
-            s_c0[inst] = p.c0m[pad];
-            s_base[inst] = p.pad_off[pad];
-          }
-          if (chunk < 4) {
-            const int w = (T.m0 >> 5) + chunk;
-            s_bits[inst * 4 + chunk] = w < nwords ? p.maskbits[p.mask_woff[pad] + w] : 0u;
-          }
-        } else {
-          if (chunk == 0) {
-            s_c0[inst] = make_float4(0.f, 0.f, 0.f, __int_as_float(0));
-            s_base[inst] = 0;
-          }
-          if (chunk < 4) s_bits[inst * 4 + chunk] = 0u;
-        }
-        // fragment order: word w = 8 s + 4 h + t (columns 16 s + 8 h + 2 t, +1) goes to
-        // position 8 t + 2 s + h, so lane (., t) reads its 8 words as two 16-byte loads
-        {
-          uint32_t* dst = reinterpret_cast<uint32_t*>(s_nb) + inst * 32;
-          const uint32_t wv[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const int w = 4 * chunk + e, s4 = w >> 3, hh = (w >> 2) & 1, tt = w & 3;
-            dst[8 * tt + 2 * s4 + hh] = wv[e];
-          }
-        }
-      }
-      named_bar_sync(1, EPI_WARPS * 32);
+      if (tile + (int)gridDim.x < p.num_tiles)
+        stage(p.tiles[tile + gridDim.x], smem + SM_STG + (size_t)((local + 1) & 1) * STG_BYTES);
+      const uint4* s_nb = reinterpret_cast<const uint4*>(sb + STG_NB);
+      const float4* s_c0 = reinterpret_cast<const float4*>(sb + STG_C0);
+      const long long* s_base = reinterpret_cast<const long long*>(sb + STG_BASE);
+      const uint32_t* s_bits = reinterpret_cast<const uint32_t*>(sb + STG_BITS);
       const int i = T.m0 + 32 * q + lane;   // my node row within the pad type
       const bool row_ok = i < n_t;
       // h0 of the warp's 32 rows in A-fragment layout: hf[rg][s][e] holds rows
       // 16 rg + grp (+ 8 for e = 1, 3), columns 16 s + 2 tig (+ 8 for e = 2, 3), BF16 pairs
       uint32_t hf[2][4][4];
-      {
-        const uint32_t* hw = reinterpret_cast<const uint32_t*>(p.h0bf16);
 #pragma unroll
-        for (int rg = 0; rg < 2; ++rg)
+      for (int rg = 0; rg < 2; ++rg)
 #pragma unroll
-          for (int e2 = 0; e2 < 2; ++e2) {
-            const int r = T.m0 + 32 * q + 16 * rg + grp + 8 * e2;
-            const bool ok = r < n_t;
-            const uint32_t* src = hw + (size_t)(p.type_off[t] + (ok ? r : 0)) * 32 + tig;
+        for (int e2 = 0; e2 < 2; ++e2) {
+          const int r = 32 * q + 16 * rg + grp + 8 * e2;
+          const unsigned char* hr = sb + STG_H0 + 128 * r + 4 * tig;
 #pragma unroll
-            for (int s4 = 0; s4 < 4; ++s4) {
-              hf[rg][s4][e2] = ok ? src[8 * s4] : 0u;
-              hf[rg][s4][2 + e2] = ok ? src[8 * s4 + 4] : 0u;
-            }
+          for (int s4 = 0; s4 < 4; ++s4) {
+            hf[rg][s4][e2] = *reinterpret_cast<const uint32_t*>(hr + (((2 * s4) ^ (r & 7)) << 4));
+            hf[rg][s4][2 + e2] =
+                *reinterpret_cast<const uint32_t*>(hr + (((2 * s4 + 1) ^ (r & 7)) << 4));
           }
-      }
+        }
       if (!mbar_wait(&acc_full[b], acc_phase, s_abort, limit)) {
         *s_abort = 1;
         *s_epi_stop = 1;
@@ -291,96 +301,92 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       tc_fence_after();
       const uint32_t tbase = tmem + (uint32_t)b * ACC_STRIDE + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-      for (int g = 0; g < 4; ++g) {
-        const int inst0 = 32 * half + 8 * g;
-        uint32_t lv[24];
+      for (int g4 = 0; g4 < 32 / DEC; ++g4) {
+        const int inst0 = 32 * half + DEC * g4;
+        uint32_t lv[3 * DEC];
         {
-          uint32_t r8[8];
+          uint32_t r8[8], r4[4];
           tc_ld_32x32b_x8(tbase + 3u * inst0, r8);
+          tc_ld_32x32b_x4(tbase + 3u * inst0 + 8u, r4);
+          tc_wait_ld();
 #pragma unroll
           for (int x = 0; x < 8; ++x) lv[x] = r8[x];
-          tc_ld_32x32b_x8(tbase + 3u * inst0 + 8u, r8);
 #pragma unroll
-          for (int x = 0; x < 8; ++x) lv[8 + x] = r8[x];
-          tc_ld_32x32b_x8(tbase + 3u * inst0 + 16u, r8);
-#pragma unroll
-          for (int x = 0; x < 8; ++x) lv[16 + x] = r8[x];
-          tc_wait_ld();
+          for (int x = 0; x < 4; ++x) lv[8 + x] = r4[x];
         }
+        float4 r[DEC];
 #pragma unroll
-        for (int jj = 0; jj < 8; jj += 2) {
-          // two instances at a time: independent MMA chains for latency hiding
-          float4 r[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
-          if (p.use_r) {
-            float acc[2][2][4];
+        for (int x = 0; x < DEC; ++x) r[x] = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (p.use_r) {
+          float acc[DEC][2][4];
 #pragma unroll
-            for (int x = 0; x < 2; ++x)
+          for (int x = 0; x < DEC; ++x)
 #pragma unroll
-              for (int rg = 0; rg < 2; ++rg)
+            for (int rg = 0; rg < 2; ++rg)
 #pragma unroll
-                for (int e = 0; e < 4; ++e) acc[x][rg][e] = 0.f;
+              for (int e = 0; e < 4; ++e) acc[x][rg][e] = 0.f;
 #pragma unroll
-            for (int x = 0; x < 2; ++x) {
-              // -beta_k for this lane's columns: nb[2 s + h] = columns 16 s + 8 h + 2 tig, +1
-              const uint4* nbp = reinterpret_cast<const uint4*>(s_nb + (inst0 + jj + x) * H) + 2 * tig;
-              const uint4 n0 = nbp[0], n1 = nbp[1];
-              const uint32_t nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
+          for (int x = 0; x < DEC; ++x) {
+            // -beta_k for this lane's columns: nb[2 s + h] = columns 16 s + 8 h + 2 tig, +1
+            const uint4 n0 = s_nb[(inst0 + x) * 8 + 2 * tig], n1 = s_nb[(inst0 + x) * 8 + 2 * tig + 1];
+            const uint32_t nb[8] = {n0.x, n0.y, n0.z, n0.w, n1.x, n1.y, n1.z, n1.w};
 #pragma unroll
-              for (int s4 = 0; s4 < 4; ++s4)
-#pragma unroll
-                for (int rg = 0; rg < 2; ++rg) {
-                  uint32_t a[4];
-                  a[0] = bf16x2_max(hf[rg][s4][0], nb[2 * s4]);
-                  a[1] = bf16x2_max(hf[rg][s4][1], nb[2 * s4]);
-                  a[2] = bf16x2_max(hf[rg][s4][2], nb[2 * s4 + 1]);
-                  a[3] = bf16x2_max(hf[rg][s4][3], nb[2 * s4 + 1]);
-                  mma_bf16_16816(acc[x][rg], a, bw[s4][0], bw[s4][1], acc[x][rg]);
-                }
-            }
-#pragma unroll
-            for (int x = 0; x < 2; ++x) {
-              float* rb = reinterpret_cast<float*>(rbuf + x * 32);
+            for (int s4 = 0; s4 < 4; ++s4)
 #pragma unroll
               for (int rg = 0; rg < 2; ++rg) {
-                const int r0 = rg * 16 + grp;
-                if (tig == 0) {
-                  rb[r0 * 4 + 0] = acc[x][rg][0];
-                  rb[r0 * 4 + 1] = acc[x][rg][1];
-                  rb[(r0 + 8) * 4 + 0] = acc[x][rg][2];
-                  rb[(r0 + 8) * 4 + 1] = acc[x][rg][3];
-                } else if (tig == 1) {
-                  rb[r0 * 4 + 2] = acc[x][rg][0];
-                  rb[(r0 + 8) * 4 + 2] = acc[x][rg][2];
-                }
+                uint32_t a[4];
+                a[0] = bf16x2_max(hf[rg][s4][0], nb[2 * s4]);
+                a[1] = bf16x2_max(hf[rg][s4][1], nb[2 * s4]);
+                a[2] = bf16x2_max(hf[rg][s4][2], nb[2 * s4 + 1]);
+                a[3] = bf16x2_max(hf[rg][s4][3], nb[2 * s4 + 1]);
+                mma_bf16_16816(acc[x][rg], a, bw[s4][0], bw[s4][1], acc[x][rg]);
               }
-            }
-            __syncwarp();
-            r[0] = rbuf[lane];
-            r[1] = rbuf[32 + lane];
-            __syncwarp();
           }
+          // components 0..2 of the 16 x 8 results live in lanes tig 0 (0, 1) and 1 (2): pass
+          // them to the lane that owns the node row
 #pragma unroll
-          for (int x = 0; x < 2; ++x) {
-            const int j = jj + x, inst = inst0 + j;
-            const float4 cm = s_c0[inst];
-            const bool passive = ((s_bits[inst * 4 + q] >> lane) & 1u) == 0u;
-            if (row_ok && passive && __float_as_int(cm.w) > 0) {
-              float u0 = 0.f, u1 = 0.f, u2 = 0.f;
-              if (p.use_l) {
-                u0 = __uint_as_float(lv[3 * j + 0]);
-                u1 = __uint_as_float(lv[3 * j + 1]);
-                u2 = __uint_as_float(lv[3 * j + 2]);
+          for (int x = 0; x < DEC; ++x) {
+            float* rb = reinterpret_cast<float*>(rbuf + x * 32);
+#pragma unroll
+            for (int rg = 0; rg < 2; ++rg) {
+              const int r0 = rg * 16 + grp;
+              if (tig == 0) {
+                rb[r0 * 4 + 0] = acc[x][rg][0];
+                rb[r0 * 4 + 1] = acc[x][rg][1];
+                rb[(r0 + 8) * 4 + 0] = acc[x][rg][2];
+                rb[(r0 + 8) * 4 + 1] = acc[x][rg][3];
+              } else if (tig == 1) {
+                rb[r0 * 4 + 2] = acc[x][rg][0];
+                rb[(r0 + 8) * 4 + 2] = acc[x][rg][2];
               }
-              if (p.use_r) {
-                u0 += r[x].x + cm.x;
-                u1 += r[x].y + cm.y;
-                u2 += r[x].z + cm.z;
-              }
-              float* d = p.disp + 3 * (s_base[inst] + i);
-              d[0] = u0;
-              d[1] = u1;
-              d[2] = u2;
             }
+          }
+          __syncwarp();
+#pragma unroll
+          for (int x = 0; x < DEC; ++x) r[x] = rbuf[x * 32 + lane];
+          __syncwarp();
+        }
+#pragma unroll
+        for (int x = 0; x < DEC; ++x) {
+          const int inst = inst0 + x;
+          const float4 cm = s_c0[inst];
+          const bool passive = ((s_bits[inst * 4 + q] >> lane) & 1u) == 0u;
+          if (row_ok && passive && __float_as_int(cm.w) > 0) {
+            float u0 = 0.f, u1 = 0.f, u2 = 0.f;
+            if (p.use_l) {
+              u0 = __uint_as_float(lv[3 * x + 0]);
+              u1 = __uint_as_float(lv[3 * x + 1]);
+              u2 = __uint_as_float(lv[3 * x + 2]);
+            }
+            if (p.use_r) {
+              u0 += r[x].x + cm.x;
+              u1 += r[x].y + cm.y;
+              u2 += r[x].z + cm.z;
+            }
+            float* d = p.disp + 3 * (s_base[inst] + i);
+            d[0] = u0;
+            d[1] = u1;
+            d[2] = u2;
           }
         }
       }
@@ -388,6 +394,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       __syncwarp();
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
+    cp_async_wait_all();   // no copy may still target shared memory when the CTA ends
   }
 
   __syncthreads();
