@@ -9,9 +9,10 @@
 // instance of the type and L2-resident; the B operand (u_hat in BF16) is written by the front
 // kernel.  Accumulation is FP32 in tensor memory.
 //
-// Per CTA (persistent, one per SM): warp 8 issues TMA loads into a 4-stage shared-memory
-// ring, warp 9 issues tcgen05.mma (M = 128, N = 192, K = 16) into one of two TMEM
-// accumulators, warps 0-7 drain the other accumulator.  The epilogue evaluates, for every
+// Per CTA (persistent, one per SM): warp 16 issues TMA loads into a 3-stage shared-memory
+// ring, warp 17 issues tcgen05.mma (M = 128, N = 192, K = 16) into one of two TMEM
+// accumulators, warps 0-15 drain the other accumulator (four per TMEM lane quarter, 16
+// instances each).  The epilogue evaluates, for every
 // passive node i and instance k, the decoder residual
 //     Phi = D2 ReLU(h0_i + beta_k) + b = D2 max(h0_i, -beta_k) + (D2 beta_k + b)
 // with warp-level BF16 MMAs (m16n8k16) per instance, adds the propagated term and stores the
@@ -34,9 +35,9 @@ constexpr int GI = 64;                  // instances per tile
 constexpr int GN = 3 * GI;              // 192 accumulator columns
 constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
 constexpr int STAGES = 3;
-constexpr int EPI_WARPS = 8;
-constexpr int TMA_WARP = 8, MMA_WARP = 9;
-constexpr int THREADS = 10 * 32;
+constexpr int EPI_WARPS = 16;
+constexpr int TMA_WARP = 16, MMA_WARP = 17;
+constexpr int THREADS = 18 * 32;
 constexpr int A_BYTES = GM * GK * 2;    // 16 KiB
 constexpr int B_BYTES = GN * GK * 2;    // 24 KiB
 constexpr uint32_t TMEM_COLS = 512;
@@ -44,10 +45,10 @@ constexpr uint32_t ACC_STRIDE = 256;    // column offset of accumulator 1
 constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
 
 // shared-memory layout (offsets from a 1024-byte aligned base)
-constexpr int DEC = 4;                  // instances per decoder pass (independent MMA chains)
+constexpr int DEC = 2;                  // instances per decoder pass (independent MMA chains)
+constexpr int INST_PER_WARP = GI / (EPI_WARPS / 4);
 constexpr size_t SM_A = 0;
 constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
-constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 8 warps x DEC x 32 x float4
 // per-tile epilogue records, double-buffered (filled one tile ahead with cp.async):
 // -beta (fragment order), (c0, m), node bases, contact words, h0 rows (16-byte chunks
 // XOR-swizzled by row so fragment reads are conflict-free)
@@ -57,6 +58,7 @@ constexpr size_t STG_BASE = STG_C0 + (size_t)GI * 16;             // 64 x int64
 constexpr size_t STG_BITS = STG_BASE + (size_t)GI * 8;            // 64 x 4 words
 constexpr size_t STG_H0 = STG_BITS + (size_t)GI * 16;             // 128 rows x 128 B
 constexpr size_t STG_BYTES = STG_H0 + (size_t)GM * 128;
+constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 16 warps x DEC x 32 x float4
 constexpr size_t SM_STG = SM_R + (size_t)EPI_WARPS * DEC * 32 * 16;
 constexpr size_t SM_BAR = SM_STG + 2 * STG_BYTES;                 // barriers
 constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
@@ -206,7 +208,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     }
   } else {
     // ---------------------------------------------------------------- epilogue (warps 0-7)
-    const int q = warp & 3, half = warp >> 2, etid = threadIdx.x;   // etid in [0, 256)
+    const int q = warp & 3, part = warp >> 2, etid = threadIdx.x;   // etid < 32 EPI_WARPS
     const int grp = lane >> 2, tig = lane & 3;
     float4* rbuf = reinterpret_cast<float4*>(smem + SM_R + (size_t)warp * DEC * 32 * 16);
     const float* W4 = p.params + OFF_W4;
@@ -273,8 +275,6 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       const float4* s_c0 = reinterpret_cast<const float4*>(sb + STG_C0);
       const long long* s_base = reinterpret_cast<const long long*>(sb + STG_BASE);
       const uint32_t* s_bits = reinterpret_cast<const uint32_t*>(sb + STG_BITS);
-      const int i = T.m0 + 32 * q + lane;   // my node row within the pad type
-      const bool row_ok = i < n_t;
       // h0 of the warp's 32 rows in A-fragment layout: hf[rg][s][e] holds rows
       // 16 rg + grp (+ 8 for e = 1, 3), columns 16 s + 2 tig (+ 8 for e = 2, 3), BF16 pairs
       uint32_t hf[2][4][4];
@@ -291,6 +291,8 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
                 *reinterpret_cast<const uint32_t*>(hr + (((2 * s4 + 1) ^ (r & 7)) << 4));
           }
         }
+      const int i = T.m0 + 32 * q + lane;   // my node row within the pad type
+      const bool row_ok = i < n_t;
       if (!mbar_wait(&acc_full[b], acc_phase, s_abort, limit)) {
         *s_abort = 1;
         *s_epi_stop = 1;
@@ -301,19 +303,24 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       tc_fence_after();
       const uint32_t tbase = tmem + (uint32_t)b * ACC_STRIDE + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
-      for (int g4 = 0; g4 < 32 / DEC; ++g4) {
-        const int inst0 = 32 * half + DEC * g4;
-        uint32_t lv[3 * DEC];
+      for (int g4 = 0; g4 < INST_PER_WARP / 4; ++g4) {
+        // the propagated terms of four instances (columns 3 k .. 3 k + 11, k a multiple of 4)
+        const int inst4 = INST_PER_WARP * part + 4 * g4;
+        uint32_t lv4[12];
         {
           uint32_t r8[8], r4[4];
-          tc_ld_32x32b_x8(tbase + 3u * inst0, r8);
-          tc_ld_32x32b_x4(tbase + 3u * inst0 + 8u, r4);
+          tc_ld_32x32b_x8(tbase + 3u * inst4, r8);
+          tc_ld_32x32b_x4(tbase + 3u * inst4 + 8u, r4);
           tc_wait_ld();
 #pragma unroll
-          for (int x = 0; x < 8; ++x) lv[x] = r8[x];
+          for (int x = 0; x < 8; ++x) lv4[x] = r8[x];
 #pragma unroll
-          for (int x = 0; x < 4; ++x) lv[8 + x] = r4[x];
+          for (int x = 0; x < 4; ++x) lv4[8 + x] = r4[x];
         }
+#pragma unroll
+      for (int sub = 0; sub < 4 / DEC; ++sub) {
+        const int inst0 = inst4 + DEC * sub;
+        const uint32_t* lv = lv4 + 3 * DEC * sub;
         float4 r[DEC];
 #pragma unroll
         for (int x = 0; x < DEC; ++x) r[x] = make_float4(0.f, 0.f, 0.f, 0.f);
@@ -389,6 +396,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
             d[2] = u2;
           }
         }
+      }
       }
       tc_fence_before();
       __syncwarp();
