@@ -60,6 +60,26 @@ def algorithmic_work(scene, counts):
 
 
 NIN_H = 9 * H
+SDF_FLOPS = 40.0   # pad -> object transform (18) + one primitive's SDF and test, per node
+
+# dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel
+# named, valid only for the source hash recorded with it (null once the kernel changes)
+TRAFFIC = {}
+
+
+def traffic_for(name):
+    """Recorded DRAM bytes per launch of kernel `name`, or None when the kernel's source file
+    no longer has the hash the capture was taken with."""
+    import hashlib
+    rec = TRAFFIC.get(name)
+    if not rec:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["file"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["bytes"] if sha == rec["sha"] else None
 
 
 class Clocks:
@@ -348,6 +368,7 @@ def main():
     peaks, peak_src = _peaks()
     nsm = torch.cuda.get_device_properties(dev).multi_processor_count
     kern = {k: {"launches": v[0], "ms_per_launch": v[1] / max(v[0], 1)} for k, v in ktimes.items()}
+    roof_all = None
     if args.algo == "plain":
         name = "plain_forward_kernel<float>"
         fma_peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
@@ -365,21 +386,41 @@ def main():
                 "frac": achieved / peaks["hbm_gbs"], "traffic": None, "kernel": name,
                 "peak_source": f"{peak_src} (MEASURED_PEAKS hbm_gbs)"}
     else:
-        name = "prop_gemm_kernel"
-        t_launch = kern[name]["ms_per_launch"] / 1e3
+        # per-kernel rooflines of the BF16 step; the top-level entry is the kernel with the
+        # largest share of the step
+        peak = peaks["bf16_tflops"]
+        per = {}
+        t = kern["front_contact_kernel"]["ms_per_launch"] / 1e3
+        alg = (2.0 * (NIN_H + H * H) * work["active"]      # encoder (E1, E2) on active nodes
+               + (SDF_FLOPS + H) * nodes)                  # contact + 64-channel max-pool
+        per["front_contact_kernel"] = {
+            "bound": "tensor", "achieved": alg / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": alg / t / 1e12 / peak, "traffic": traffic_for("front_contact_kernel"),
+            "ms": t * 1e3, "peak_source": f"{peak_src} bf16_tflops (burst)",
+            "note": "encoder on active nodes (mma.sync) + SDF and max-pool per node; "
+                    "HBM bytes are small here (12 B per active node + 4 B per pad)"}
+        t = kern["prop_gemm_kernel"]["ms_per_launch"] / 1e3
         alg = 6.0 * work["pairs"] + 2.0 * 3 * H * work["passive"]
         exe = executed_gemm_flops(scene)
-        peak = peaks["bf16_tflops"]
-        achieved = alg / t_launch / 1e12
-        roof = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": name,
-                "executed_dense_tflops": exe / t_launch / 1e12,
-                "executed_frac": exe / t_launch / 1e12 / peak,
-                "peak_source": f"{peak_src} bf16_tflops (burst)",
-                "note": "achieved counts the Eq. 1 contraction over (passive, active) pairs and "
-                        "the decoder output layer; the kernel executes the dense per-type "
-                        "contraction (executed_dense_tflops)"}
-
+        per["prop_gemm_kernel"] = {
+            "bound": "tensor", "achieved": alg / t / 1e12, "peak": peak, "unit": "TFLOP/s",
+            "frac": alg / t / 1e12 / peak, "traffic": traffic_for("prop_gemm_kernel"),
+            "ms": t * 1e3, "executed_dense_tflops": exe / t / 1e12,
+            "executed_frac": exe / t / 1e12 / peak,
+            "peak_source": f"{peak_src} bf16_tflops (burst)",
+            "note": "achieved counts the Eq. 1 contraction over (passive, active) pairs and "
+                    "the decoder output layer; the kernel executes the dense per-type "
+                    "contraction (executed_dense_tflops)"}
+        t = kern["front_global_kernel"]["ms_per_launch"] / 1e3
+        npads = scene.num_envs * scene.pads_per_env
+        byts = npads * (4 * H + 2 * H + 16)               # g0 in, -beta (BF16) and (c0, m) out
+        per["front_global_kernel"] = {
+            "bound": "hbm", "achieved": byts / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+            "frac": byts / t / 1e9 / peaks["hbm_gbs"], "traffic": None, "ms": t * 1e3,
+            "peak_source": f"{peak_src} hbm_gbs"}
+        name = max(per, key=lambda k: per[k]["ms"])
+        roof = dict(per[name], kernel=name)
+        roof_all = per
     cpu = None
     err = None
     if not args.no_cpu and rank == 0:
@@ -415,6 +456,7 @@ def main():
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if prec == X.PREC_BF16 else "f32",
             "data": "synthetic", "config": workload_config(args, scene), "roofline": roof,
+            "roofline_by_kernel": roof_all,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "error_vs_oracle": err, "rungs": compare, "kernels": kern,
