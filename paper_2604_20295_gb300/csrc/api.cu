@@ -77,8 +77,33 @@ struct etac_ctx {
   long long* d_type_woff = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
-  int front_grid = 0, gemm_grid = 0;
-  bool bf16_ready = false;
+  int front_grid = 0, gemm_grid = 0, num_tiles = 0;
+  bool bf16_ready = false, inst_ready = false;
+  std::vector<long long> bt_off_h;
+  std::vector<int> ninst_h;
+  long long bt_total = 0;
+  // staged batched reverse mode
+  bool bwdb_ready = false;
+  void* d_om_hi = nullptr;
+  void* d_om_lo = nullptr;
+  void* d_dom_hi = nullptr;
+  void* d_dom_lo = nullptr;
+  void* d_bg_hi = nullptr;
+  void* d_bg_lo = nullptr;
+  float* d_pr = nullptr;
+  int* d_inst_m = nullptr;
+  etac::R3Group* d_r3g = nullptr;
+  float* d_a3part = nullptr;
+  long long* d_a3_toff = nullptr;
+  int* d_a3_tg = nullptr;
+  float* d_a3 = nullptr;
+  float* d_d2part = nullptr;
+  float* d_r4part = nullptr;
+  float* d_r4bpart = nullptr;
+  float* d_r5part = nullptr;
+  float* d_alpha_part = nullptr;
+  int r3_parts = 0, r4_parts = 0, r4b_parts = 0, r5_parts = 0, alpha_parts = 0;
+  etac::GemmParams gemm_bu{}, gemm_ba{};
   // profiling: event pairs around kernel launches
   // reverse mode workspace
   int* d_ws_idx = nullptr;
@@ -158,7 +183,10 @@ void free_ctx(etac_ctx* c) {
                   c->d_bt_off, c->d_pad_inst, c->d_inst_off, c->d_inst_pad, c->d_negbeta,
                   c->d_c0m, c->d_tiles, c->d_maskbits, c->d_mask_woff, c->d_pad_m,
                   c->d_g0a, c->d_ranked, c->d_padobj, c->d_pad_bad, c->d_pad_gi, c->d_inst_base,
-                  c->d_type_woff, c->d_ws_idx, c->d_ws_u,
+                  c->d_type_woff, c->d_om_hi, c->d_om_lo, c->d_dom_hi, c->d_dom_lo,
+                  c->d_bg_hi, c->d_bg_lo, c->d_pr, c->d_inst_m, c->d_r3g, c->d_a3part,
+                  c->d_a3_toff, c->d_a3_tg, c->d_a3, c->d_d2part, c->d_r4part, c->d_r4bpart,
+                  c->d_r5part, c->d_alpha_part, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -189,17 +217,11 @@ bool encode_bf16_2d(EncodeTiledFn fn, CUtensorMap* m, const void* base, uint64_t
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
-// Buffers, tile list and tensor maps of the BF16 tensor-core algorithm (once per context).
-etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
-  if (c->bf16_ready) return ETAC_OK;
-  if (c->T > etac::GEMM_MAX_TYPES)
-    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 algorithm supports at most %d pad types",
-                etac::GEMM_MAX_TYPES);
-  for (int t = 0; t < c->T; ++t)
-    if (c->type_n[t] % 8 != 0)
-      return fail(c, ETAC_ERR_UNSUPPORTED,
-                  "BF16 algorithm needs node counts that are multiples of 8 (type %d has %d)", t,
-                  c->type_n[t]);
+// Instance bookkeeping shared by the tensor-core forward and the batched reverse mode (once
+// per context): instance order per pad type, per-instance records' indices, contact bit words
+// in instance order, the GEMM tile list, per-pad transform buffers.
+etac_status setup_instances(etac_ctx* c, cudaStream_t s) {
+  if (c->inst_ready) return ETAC_OK;
   const int np = c->E * c->P;
   std::vector<int> inst_off(c->T + 1, 0), pad_inst(np), ninst(c->T, 0);
   for (int p = 0; p < np; ++p) pad_inst[p] = ninst[c->pad_type[p]]++;
@@ -225,12 +247,14 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
     inst_base[pad_gi[p]] = c->pad_off[p];
   }
   woff[np] = wtot;
-  std::vector<long long> bt_off(c->T, 0);
+  c->bt_off_h.assign(c->T, 0);
   long long bt_total = 0;
   for (int t = 0; t < c->T; ++t) {
-    bt_off[t] = bt_total;
+    c->bt_off_h[t] = bt_total;
     bt_total += ((3LL * ninst[t] * c->type_n[t]) + 127) / 128 * 128;
   }
+  c->bt_total = bt_total;
+  c->ninst_h = ninst;
   // tiles: node-row tiles innermost, so the CTAs working at one time share each B tile (the
   // instances' u_hat) through L2 instead of re-reading it from DRAM per row tile
   std::vector<etac::GemmTile> tiles;
@@ -244,25 +268,20 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
                                                   const etac::GemmTile& y) {
     return x.nkb > y.nkb;   // heaviest tiles first
   });
-  const size_t tn = (size_t)c->type_off[c->T];
-  cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_omega_bf16), 2 * (size_t)c->omega_off[c->T]);
-  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_h0bf16), 2 * tn * etac::H);
-  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bt), 2 * (size_t)bt_total);
-  if (e == cudaSuccess) e = dalloc(&c->d_bt_off, c->T);
+  c->num_tiles = (int)tiles.size();
+  cudaError_t e = dalloc(&c->d_bt_off, c->T);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_inst, np);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_off, c->T + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_pad, np);
-  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
-  if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
   if (e == cudaSuccess) e = dalloc(&c->d_maskbits, (size_t)woff[np]);
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
-  if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_padobj, (size_t)np * c->K);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_bad, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_gi, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_base, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_type_woff, (size_t)c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pad_gi, pad_gi.data(), sizeof(int) * np,
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_base, inst_base.data(),
@@ -271,9 +290,8 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
                                             sizeof(long long) * c->T, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_mask_woff, woff.data(), sizeof(long long) * (np + 1),
                                             cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_bt_off, bt_off.data(), sizeof(long long) * c->T,
-                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_bt_off, c->bt_off_h.data(),
+                                            sizeof(long long) * c->T, cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pad_inst, pad_inst.data(), sizeof(int) * np,
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_off, inst_off.data(),
@@ -284,45 +302,168 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
     e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(etac::GemmTile) * tiles.size(),
                         cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors are pageable
-  if (e != cudaSuccess) return cuda_fail(c, e, "BF16 buffers");
+  if (e != cudaSuccess) return cuda_fail(c, e, "instance buffers");
+  c->gemm_grid = std::max(1, std::min(c->num_sms, c->num_tiles));
+  c->inst_ready = true;
+  return ETAC_OK;
+}
+
+bool tensor_core_shapes_ok(const etac_ctx* c) {
+  if (c->T > etac::GEMM_MAX_TYPES) return false;
+  for (int t = 0; t < c->T; ++t)
+    if (c->type_n[t] % 8 != 0) return false;
+  return true;
+}
+
+EncodeTiledFn get_encode_fn() {
   void* fn = nullptr;
   cudaDriverEntryPointQueryResult qr;
-  e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault,
-                                       &qr);
-  if (e != cudaSuccess || !fn || qr != cudaDriverEntryPointSuccess)
-    return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
-  etac::GemmParams& g = c->gemm;
-  memset(&g, 0, sizeof g);
-  for (int t = 0; t < c->T; ++t) {
-    const int n = c->type_n[t];
-    const char* om = reinterpret_cast<const char*>(c->d_omega_bf16) + 2 * (size_t)c->omega_off[t];
-    const char* bt = reinterpret_cast<const char*>(c->d_bt) + 2 * (size_t)bt_off[t];
-    if (!encode_bf16_2d(reinterpret_cast<EncodeTiledFn>(fn), &g.tmA[t], om, n, n, 128) ||
-        !encode_bf16_2d(reinterpret_cast<EncodeTiledFn>(fn), &g.tmB[t], bt, n,
-                        std::max(1, 3 * ninst[t]), 192))
-      return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
-  }
+  const cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000,
+                                                         cudaEnableDefault, &qr);
+  if (e != cudaSuccess || !fn || qr != cudaDriverEntryPointSuccess) return nullptr;
+  return reinterpret_cast<EncodeTiledFn>(fn);
+}
+
+// common GEMM fields (tile list, per-instance records) of a parameter block
+void fill_gemm_common(etac_ctx* c, etac::GemmParams& g) {
   g.tiles = c->d_tiles;
-  g.num_tiles = (int)tiles.size();
+  g.num_tiles = c->num_tiles;
   g.type_off = c->d_type_off;
   g.inst_off = c->d_inst_off;
   g.inst_pad = c->d_inst_pad;
   g.pad_off = c->d_pad_off;
   g.inst_base = c->d_inst_base;
   g.type_woff = c->d_type_woff;
-  g.h0bf16 = c->d_h0bf16;
-  g.negbeta = c->d_negbeta;
-  g.c0m = c->d_c0m;
   g.maskbits = c->d_maskbits;
   g.params = c->d_params;
   g.status = c->d_status;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
+}
+
+// Buffers and tensor maps of the BF16 tensor-core forward (once per context).
+etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
+  if (c->bf16_ready) return ETAC_OK;
+  if (c->T > etac::GEMM_MAX_TYPES)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "BF16 algorithm supports at most %d pad types",
+                etac::GEMM_MAX_TYPES);
+  for (int t = 0; t < c->T; ++t)
+    if (c->type_n[t] % 8 != 0)
+      return fail(c, ETAC_ERR_UNSUPPORTED,
+                  "BF16 algorithm needs node counts that are multiples of 8 (type %d has %d)", t,
+                  c->type_n[t]);
+  etac_status st = setup_instances(c, s);
+  if (st != ETAC_OK) return st;
+  const int np = c->E * c->P;
+  const size_t tn = (size_t)c->type_off[c->T];
+  cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_omega_bf16), 2 * (size_t)c->omega_off[c->T]);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_h0bf16), 2 * tn * etac::H);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bt), 2 * (size_t)c->bt_total);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
+  if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
+  if (e != cudaSuccess) return cuda_fail(c, e, "BF16 buffers");
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  etac::GemmParams& g = c->gemm;
+  memset(&g, 0, sizeof g);
+  for (int t = 0; t < c->T; ++t) {
+    const int n = c->type_n[t];
+    const char* om = reinterpret_cast<const char*>(c->d_omega_bf16) + 2 * (size_t)c->omega_off[t];
+    const char* bt = reinterpret_cast<const char*>(c->d_bt) + 2 * (size_t)c->bt_off_h[t];
+    if (!encode_bf16_2d(fn, &g.tmA[t], om, n, n, 128) ||
+        !encode_bf16_2d(fn, &g.tmB[t], bt, n, std::max(1, 3 * c->ninst_h[t]), 192))
+      return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
+  }
+  fill_gemm_common(c, g);
+  g.h0bf16 = c->d_h0bf16;
+  g.negbeta = c->d_negbeta;
+  g.c0m = c->d_c0m;
   int per_sm = 0;
   e = etac::front_occupancy(c->nmax, c->K, &per_sm);
   if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "front kernel occupancy");
   c->front_grid = per_sm * c->num_sms;
-  c->gemm_grid = std::max(1, std::min(c->num_sms, (int)tiles.size()));
   c->bf16_ready = true;
+  return ETAC_OK;
+}
+
+// Buffers and tensor maps of the staged batched reverse mode (once per context).
+etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
+  if (c->bwdb_ready) return ETAC_OK;
+  etac_status st = setup_instances(c, s);
+  if (st != ETAC_OK) return st;
+  const int np = c->E * c->P;
+  const size_t tn = (size_t)c->type_off[c->T];
+  const size_t om = (size_t)c->omega_off[c->T];
+  // decoder-reverse groups (64 instances each), heaviest types first
+  std::vector<etac::R3Group> groups;
+  std::vector<long long> a3_toff(c->T, 0);
+  std::vector<int> a3_tg(c->T, 0);
+  long long a3tot = 0;
+  for (int t = 0; t < c->T; ++t) {
+    a3_toff[t] = a3tot;
+    a3_tg[t] = (c->ninst_h[t] + 63) / 64;
+    a3tot += (long long)a3_tg[t] * c->type_n[t] * etac::H;
+  }
+  for (int t = 0; t < c->T; ++t)
+    for (int g = 0; g < a3_tg[t]; ++g)
+      groups.push_back({t, 64 * g, a3_toff[t] + (long long)g * c->type_n[t] * etac::H});
+  std::stable_sort(groups.begin(), groups.end(), [&](const etac::R3Group& x, const etac::R3Group& y) {
+    return c->type_n[x.type] > c->type_n[y.type];
+  });
+  c->r3_parts = (int)groups.size();
+  c->r4_parts = 4 * 2 * c->num_sms;                     // warps of the R4 grid
+  c->r4b_parts = (np + 63) / 64;
+  c->r5_parts = (int)((tn + 63) / 64);
+  c->alpha_parts = c->gemm_grid;
+  cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_om_hi), 2 * om);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_om_lo), 2 * om);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_dom_hi), 2 * om);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_dom_lo), 2 * om);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bg_hi), 2 * (size_t)c->bt_total);
+  if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bg_lo), 2 * (size_t)c->bt_total);
+  if (e == cudaSuccess) e = dalloc(&c->d_pr, (size_t)np * etac::PR_STRIDE);
+  if (e == cudaSuccess) e = dalloc(&c->d_inst_m, (size_t)np);
+  if (e == cudaSuccess) e = dalloc(&c->d_r3g, groups.size());
+  if (e == cudaSuccess) e = dalloc(&c->d_a3part, (size_t)a3tot);
+  if (e == cudaSuccess) e = dalloc(&c->d_a3_toff, (size_t)c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_a3_tg, (size_t)c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_a3, tn * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_d2part, (size_t)c->r3_parts * 3 * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_r4part, (size_t)c->r4_parts * (etac::OFF_B2 + etac::H - etac::OFF_W1));
+  if (e == cudaSuccess) e = dalloc(&c->d_r4bpart, (size_t)c->r4b_parts * (etac::OFF_W4 - etac::OFF_WG));
+  if (e == cudaSuccess) e = dalloc(&c->d_r5part, (size_t)c->r5_parts * (etac::OFF_W4 - etac::OFF_W1));
+  if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->alpha_parts);
+  if (e == cudaSuccess && !groups.empty())
+    e = cudaMemcpyAsync(c->d_r3g, groups.data(), sizeof(etac::R3Group) * groups.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_toff, a3_toff.data(), sizeof(long long) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_tg, a3_tg.data(), sizeof(int) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "reverse-mode buffers");
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  for (int which = 0; which < 2; ++which) {
+    etac::GemmParams& g = which == 0 ? c->gemm_bu : c->gemm_ba;
+    memset(&g, 0, sizeof g);
+    const char* ah = reinterpret_cast<const char*>(which == 0 ? c->d_om_hi : c->d_dom_hi);
+    const char* al = reinterpret_cast<const char*>(which == 0 ? c->d_om_lo : c->d_dom_lo);
+    for (int t = 0; t < c->T; ++t) {
+      const int n = c->type_n[t];
+      const size_t oo = 2 * (size_t)c->omega_off[t], bo = 2 * (size_t)c->bt_off_h[t];
+      const uint64_t rows = std::max(1, 3 * c->ninst_h[t]);
+      if (!encode_bf16_2d(fn, &g.tmA[t], ah + oo, n, n, 128) ||
+          !encode_bf16_2d(fn, &g.tmA2[t], al + oo, n, n, 128) ||
+          !encode_bf16_2d(fn, &g.tmB[t], reinterpret_cast<const char*>(c->d_bg_hi) + bo, n, rows, 192) ||
+          !encode_bf16_2d(fn, &g.tmB2[t], reinterpret_cast<const char*>(c->d_bg_lo) + bo, n, rows, 192))
+        return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
+    }
+    fill_gemm_common(c, g);
+    g.inst_m = c->d_inst_m;
+    g.alpha_part = c->d_alpha_part;   // ws_u / ws_du are bound at launch (allocated later)
+  }
+  c->bwdb_ready = true;
   return ETAC_OK;
 }
 
@@ -349,6 +490,11 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     etac_status st = setup_bf16(c, s);
     if (st != ETAC_OK) return st;
   }
+  const bool needb = batched && tensor_core_shapes_ok(c);   // staged reverse mode
+  if (needb) {
+    etac_status st = setup_bwdb(c, s);
+    if (st != ETAC_OK) return st;
+  }
   if (batched && !c->batched_grid) {
     int per_sm = 0;
     e = etac::batched_occupancy(c->nmax, c->K, &per_sm);
@@ -372,9 +518,129 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
   a.omega_bf16 = need16 ? c->d_omega_bf16 : nullptr;
   a.h0bf16 = need16 ? c->d_h0bf16 : nullptr;
   a.ranked = c->d_ranked;
+  a.om_hi = needb ? c->d_om_hi : nullptr;
+  a.om_lo = needb ? c->d_om_lo : nullptr;
+  a.dom_hi = needb ? c->d_dom_hi : nullptr;
+  a.dom_lo = needb ? c->d_dom_lo : nullptr;
   e = etac::launch_tables(a, c->nmax, s);
   if (e != cudaSuccess) return cuda_fail(c, e, "per-type tables");
   c->tables_ready = true;
+  return ETAC_OK;
+}
+
+// The staged reverse mode of the batched algorithms (bwd_batched.cu, prop_gemm.cu).
+etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_obj_pose,
+                             float* grad_uhat, float* grad_pen, float* grad_params,
+                             cudaStream_t s) {
+  const int EP = c->E * c->P;
+  const bool use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
+  // pad -> object transforms of the differentiated step
+  etac::FrontArgs f{};
+  f.type_pmax = c->d_type_pmax;
+  f.pad_type = c->d_pad_type;
+  f.num_items = EP;
+  f.P = c->P;
+  f.K = c->K;
+  f.obj_type = c->d_saved_obj_type;
+  f.obj_dims = c->d_saved_obj_dims;
+  f.obj_pose = c->d_saved_obj_pose;
+  f.pad_pose = c->d_saved_pad_pose;
+  f.padobj = c->d_padobj;
+  f.pad_bad = c->d_pad_bad;
+  const int ts = timing_begin(c, K_BWD, s);
+  ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
+  ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
+  etac::BwdBatchedArgs b{};
+  b.type_pos = c->d_type_pos;
+  b.type_nrm = c->d_type_nrm;
+  b.type_off = c->d_type_off;
+  b.pad_type = c->d_pad_type;
+  b.pad_off = c->d_pad_off;
+  b.item_pad = c->d_item_pad;
+  b.num_items = EP;
+  b.P = c->P;
+  b.K = c->K;
+  b.nmax = c->nmax;
+  b.total_nodes = c->type_off[c->T];
+  b.pad_pose = c->d_saved_pad_pose;
+  b.obj_pose = c->d_saved_obj_pose;
+  b.params = c->d_params;
+  b.ctab = c->d_ctab;
+  b.f0tab = c->d_f0tab;
+  b.h0tab = c->d_h0tab;
+  b.ranked = c->d_ranked;
+  b.padobj = c->d_padobj;
+  b.pad_bad = c->d_pad_bad;
+  b.pad_inst = c->d_pad_inst;
+  b.inst_off = c->d_inst_off;
+  b.inst_pad = c->d_inst_pad;
+  b.pad_gi = c->d_pad_gi;
+  b.inst_base = c->d_inst_base;
+  b.type_woff = c->d_type_woff;
+  b.mask_woff = c->d_mask_woff;
+  b.maskbits = c->d_maskbits;
+  b.bg_off = c->d_bt_off;
+  b.bg_hi = c->d_bg_hi;
+  b.bg_lo = c->d_bg_lo;
+  b.mode = c->model.mode;
+  b.grad_disp = grad_disp;
+  b.grad_uhat = grad_uhat;
+  b.grad_pen = grad_pen;
+  b.ws_u = c->d_ws_u;
+  b.ws_du = c->d_ws_du;
+  b.pr = c->d_pr;
+  b.pad_m = c->d_pad_m;
+  b.inst_m = c->d_inst_m;
+  b.r3_groups = c->d_r3g;
+  b.r3_parts = c->r3_parts;
+  b.a3part = c->d_a3part;
+  b.a3_toff = c->d_a3_toff;
+  b.a3_tgroups = c->d_a3_tg;
+  b.a3 = c->d_a3;
+  b.d2part = c->d_d2part;
+  b.r4part = c->d_r4part;
+  b.r4_parts = c->r4_parts;
+  b.r4bpart = c->d_r4bpart;
+  b.r4b_parts = c->r4b_parts;
+  b.r5part = c->d_r5part;
+  b.r5_parts = c->r5_parts;
+  b.alpha_part = c->d_alpha_part;
+  b.alpha_parts = use_l ? c->alpha_parts : 0;
+  b.pose_part = c->d_pose_part;
+  b.ticket = c->d_ticket;
+  if (c->model.mode == ETAC_MODE_LINEAR_ONLY) {   // no network: only alpha has a gradient
+    b.r3_parts = b.r4_parts = b.r4b_parts = b.r5_parts = 0;
+  }
+  {
+    const void* need[] = {b.ws_u, b.ws_du, b.pr, b.pad_m, b.inst_m, b.padobj, b.pad_bad,
+                          b.maskbits, b.mask_woff, b.bg_hi, b.bg_lo, b.r3_groups, b.a3part,
+                          b.a3, b.d2part, b.r4part, b.r4bpart, b.r5part, b.alpha_part,
+                          b.pose_part, b.ranked, b.h0tab, b.ctab, b.f0tab};
+    for (const void* q : need)
+      if (!q) return fail(c, ETAC_ERR_STATE, "reverse-mode buffers are not set up");
+  }
+  etac::BwdBatchedLaunch l{};
+  l.r1_grid = 2 * c->num_sms;
+  l.r2_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
+  l.r7_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
+  ETAC_CUDA(c, etac::launch_backward_batched(b, l, s), "reverse mode: pad stages");
+  if (use_l) {
+    for (etac::GemmParams* g : {&c->gemm_bu, &c->gemm_ba}) {
+      g->ws_u = c->d_ws_u;
+      g->ws_du = c->d_ws_du;
+      if (!g->ws_u || !g->ws_du || !g->inst_m || !g->alpha_part || !g->tiles)
+        return fail(c, ETAC_ERR_STATE, "reverse-mode GEMM buffers are not set up");
+    }
+    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U),
+              "reverse mode: propagation GEMM");
+    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA),
+              "reverse mode: alpha GEMM");
+  }
+  ETAC_CUDA(c, etac::launch_backward_batched_tail(b, l, grad_params, s), "reverse mode: outputs");
+  if (grad_obj_pose)
+    ETAC_CUDA(c, etac::launch_reduce_pose(c->d_pose_part, c->E, c->P, c->K, grad_obj_pose, s),
+              "reverse mode: pose sums");
+  timing_end(c, ts, s);
   return ETAC_OK;
 }
 
@@ -737,6 +1003,8 @@ etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_
       (grad_params && !aligned(grad_params, 4)))
     return fail(c, ETAC_ERR_INVALID_ARG, "pointer not 4-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (c->model.algo == ETAC_ALGO_BATCHED && c->bwdb_ready)
+    return backward_batched(c, grad_disp, grad_obj_pose, grad_uhat, grad_penetration, grad_params, s);
   etac::BackwardArgs b{};
   b.type_pos = c->d_type_pos;
   b.type_nrm = c->d_type_nrm;

@@ -22,6 +22,7 @@
 //      dalpha += -sum_i d_ij Omega_ij (G_i . u_hat_j) over passive i;
 //   5. pose and penetration: u_hat = -phi n (object outward normal n), differentiated through
 //      the primitive's SDF gradient and Hessian.
+#include "bwd_common.cuh"
 #include "etac_common.cuh"
 #include "etac_kernels.h"
 
@@ -32,7 +33,7 @@ namespace {
 constexpr int BB = 256;
 constexpr int BBW = BB / 32;
 constexpr int CH = 64;        // nodes per chunk
-constexpr int LD = H + 4;     // padded row stride of staged 64 x 64 tiles (16-byte aligned)
+constexpr int LD = TLD;
 
 // shared-memory layout
 struct BwdSmem {
@@ -71,21 +72,6 @@ enum { V_G0 = 0, V_AG = 1, V_G = 2, V_BETA = 3, V_S = 4, V_DG0 = 5, V_DAG = 6, V
        V_ALPHA = 10, V_BV = 11, V_BI = 12 };
 
 __device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
-
-// acc[i][j] += sum_k A[k][4 ti + i] * B[k][4 tj + j], both operands k-major with stride LD
-__device__ __forceinline__ void tile_acc(const float* A, const float* B, int ti, int tj,
-                                         float (&acc)[4][4]) {
-#pragma unroll 8
-  for (int k = 0; k < 64; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(A + k * LD + 4 * ti);
-    const float4 b = *reinterpret_cast<const float4*>(B + k * LD + 4 * tj);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-  }
-}
 
 __device__ __forceinline__ int find_slot(const int* idx, int m, int i) {
   int lo = 0, hi = m - 1;
@@ -637,77 +623,21 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
       const float4 du = wDU[s];
       const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
       const float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-      SdfIn sd;
-      const NodeContact c = contact_node(spo, a.K, p, nr, &sd);
-      const PadObj& po = spo[c.k];
-      // outward normal in the pad frame: R_rel^T g
-      const float npx = po.R[0] * sd.g[0] + po.R[3] * sd.g[1] + po.R[6] * sd.g[2];
-      const float npy = po.R[1] * sd.g[0] + po.R[4] * sd.g[1] + po.R[7] * sd.g[2];
-      const float npz = po.R[2] * sd.g[0] + po.R[5] * sd.g[1] + po.R[8] * sd.g[2];
+      const NodePoseGrad pg = node_pose_grad(spo, a.K, p, nr, make_float3(du.x, du.y, du.z), Rp, pp,
+                                             a.obj_pose + 7 * (size_t)env * a.K);
       if (a.grad_uhat) {
         float* g = a.grad_uhat + 3 * (base + i);
         g[0] = du.x;
         g[1] = du.y;
         g[2] = du.z;
       }
-      if (a.grad_pen) a.grad_pen[base + i] = npx * du.x + npy * du.y + npz * du.z;
-      // v = R_pad du (world); vo = R_k^T v (object frame)
-      const float* op = a.obj_pose + 7 * (size_t)(env * a.K + c.k);
-      float Rk[3][3];
-      quat_to_mat<float>(op + 3, Rk);
-      float v[3], vo[3], gw[3];
-      for (int q = 0; q < 3; ++q) v[q] = Rp[q][0] * du.x + Rp[q][1] * du.y + Rp[q][2] * du.z;
-      for (int q = 0; q < 3; ++q) vo[q] = Rk[0][q] * v[0] + Rk[1][q] * v[1] + Rk[2][q] * v[2];
-      for (int q = 0; q < 3; ++q) gw[q] = Rk[q][0] * sd.g[0] + Rk[q][1] * sd.g[1] + Rk[q][2] * sd.g[2];
-      // A v = g (g . vo) + phi H vo, object frame
-      const float phi = c.phi;
-      const float gv = sd.g[0] * vo[0] + sd.g[1] * vo[1] + sd.g[2] * vo[2];
-      float Av[3] = {sd.g[0] * gv, sd.g[1] * gv, sd.g[2] * gv};
-      if (!sd.deg && sd.hk != 0) {
-        const PadObj& ob = po;
-        float Hv[3];
-        if (sd.hk == 1) {
-          // spherical: (P - g g^T) vo / L, P = I except on a capsule's side (z row dropped)
-          float L;
-          bool side = false;
-          if (ob.type == OBJ_CAPSULE) {
-            const float h = ob.dims[1];
-            const float qz = sd.qf[2];
-            side = qz > -h && qz < h;
-            const float cz = qz < -h ? -h : (qz > h ? h : qz);
-            const float vz = qz - cz;
-            L = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1] + vz * vz);
-          } else {
-            L = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1] + sd.qf[2] * sd.qf[2]);
-          }
-          Hv[0] = (vo[0] - sd.g[0] * gv) / L;
-          Hv[1] = (vo[1] - sd.g[1] * gv) / L;
-          Hv[2] = ((side ? 0.f : vo[2]) - sd.g[2] * gv) / L;
-        } else {
-          // radial about the z axis: (I_xy - g g^T) vo / rho
-          const float rho = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1]);
-          Hv[0] = (vo[0] - sd.g[0] * gv) / rho;
-          Hv[1] = (vo[1] - sd.g[1] * gv) / rho;
-          Hv[2] = 0.f;
-        }
-        for (int q = 0; q < 3; ++q) Av[q] = fmaf(phi, Hv[q], Av[q]);
-      }
-      float sw[3];
-      for (int q = 0; q < 3; ++q) sw[q] = Rk[q][0] * Av[0] + Rk[q][1] * Av[1] + Rk[q][2] * Av[2];
-      // r = x - t_k, x = R_pad p + t_pad (world)
-      float r[3];
-      for (int q = 0; q < 3; ++q)
-        r[q] = Rp[q][0] * p.x + Rp[q][1] * p.y + Rp[q][2] * p.z + pp[q] - op[q];
-      const float c1[3] = {r[1] * sw[2] - r[2] * sw[1], r[2] * sw[0] - r[0] * sw[2],
-                           r[0] * sw[1] - r[1] * sw[0]};
-      const float c2[3] = {gw[1] * v[2] - gw[2] * v[1], gw[2] * v[0] - gw[0] * v[2],
-                           gw[0] * v[1] - gw[1] * v[0]};
+      if (a.grad_pen) a.grad_pen[base + i] = pg.pen;
 #pragma unroll
       for (int k = 0; k < MAX_K; ++k) {
-        if (k != c.k) continue;
+        if (k != pg.k) continue;
         for (int q = 0; q < 3; ++q) {
-          pose[k][q] += sw[q];
-          pose[k][3 + q] += c1[q] - phi * c2[q];
+          pose[k][q] += pg.t[q];
+          pose[k][3 + q] += pg.w[q];
         }
       }
     }
@@ -793,6 +723,13 @@ cudaError_t launch_pose_grad_to_quat(const float* poses, const float* tw, float*
 }
 
 size_t backward_smem_bytes(int nmax, int K) { return BwdSmem(nmax, K).total; }
+
+cudaError_t launch_reduce_pose(const float* part, int E, int P, int K, float* out, cudaStream_t s) {
+  const long long tot = (long long)E * K * 6;
+  if (tot <= 0) return cudaSuccess;
+  reduce_pose_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(part, E, P, K, out);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_backward(const BackwardArgs& a, int grid, cudaStream_t s) {
   const size_t smem = backward_smem_bytes(a.nmax, a.K);

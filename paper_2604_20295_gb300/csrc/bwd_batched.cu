@@ -1,0 +1,1132 @@
+// bwd_batched.cu -- FP32 reverse mode of the batched ETac step as a staged pipeline (ETac
+// Sec. III-A, Eq. 1, Eq. 4; the calibration of Eq. 5 differentiates the same quantities).
+//
+// Passive nodes feed the network constant inputs [p, n, 0], so their encoder activations are
+// per pad type, and the reverse of the encoder for the decoder path can be summed over all
+// instances of a type before it is run: once per type node instead of once per pad node.
+// The stages:
+//   R1 bwd_pad_kernel (warp per pad): contact (same decisions as the forward), u_hat and phi
+//      of the active nodes, dL/du_hat's direct term, the passive upstream gradient G as the
+//      split BF16 B operand of the propagation reverse, sum G over passive nodes, and the
+//      channel maxima of f with their lowest-index argmax: the active nodes' encoder to FP32
+//      accuracy on tensor cores (inputs, activations and weights split into BF16 hi / lo
+//      parts), the passive candidate from the ranked f0 table;
+//   R2 bwd_global_kernel (warp per pad): ag = G1 g0 + b, g = ReLU(ag), beta = D1_g g;
+//   R3 bwd_decoder_kernel (type x 64-instance groups): for every passive (instance k, node
+//      i), dz = D2^T G_ki and dA3 = dz [h0_i + beta_k > 0]; sums S_k = sum_i dA3 (per pad,
+//      complete), A3_i = sum_k dA3 (per type node, partial per group) and
+//      dD2 = sum G (x) ReLU(h0 + beta);
+//   R3b reduce the A3 partials in group order;
+//   R4 bwd_padrev_kernel (warp per pad): dg = D1_g^T S, dag = dg [ag > 0], dg0 = G1^T dag,
+//      routed to each channel's argmax node, and that node's encoder reverse (E1, E2, and
+//      for an active node dL/du_hat);
+//   R4b sums over pads of S g^T, dag g0^T, S and dag (D1_g, G1 and their biases);
+//   R5 bwd_typenode_kernel (64 type nodes per CTA): the decoder path's encoder reverse from
+//      A3 (dD1_f, dE2, dE1, biases);
+//   R6 the propagation reverse on tensor cores (prop_gemm.cu, backward modes);
+//   R7 bwd_pose_kernel (warp per pad): outputs dL/du_hat, dL/dpen and the pose partials.
+// Every sum runs in a fixed order (static work assignment, partials reduced in index order),
+// so the result is bitwise repeatable.
+#include <cuda_bf16.h>
+
+#include "bwd_common.cuh"
+#include "etac_common.cuh"
+#include "etac_kernels.h"
+#include "sm100_ptx.cuh"
+
+namespace etac {
+
+namespace {
+
+constexpr unsigned FULL = 0xffffffffu;
+constexpr int RT = 256;            // threads per CTA of the warp-per-pad kernels
+constexpr int RW = RT / 32;
+constexpr int RPEND = 48;          // active rows awaiting the encoder (<= 15 + 32)
+constexpr int RCAND = 64;          // undecided nodes awaiting the exact contact path
+
+__device__ __forceinline__ float relu(float x) { return x > 0.f ? x : 0.f; }
+
+__device__ __forceinline__ uint32_t bf2(float a, float b) {
+  __nv_bfloat162 v = __floats2bfloat162_rn(a, b);
+  return *reinterpret_cast<uint32_t*>(&v);
+}
+__device__ __forceinline__ float bfr(float x) {   // x - BF16(x)
+  return x - __bfloat162float(__float2bfloat16_rn(x));
+}
+// hi = BF16 pair of (a, b), lo = BF16 pair of the remainders: a ~ hi + lo to ~16 bits
+__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
+  hi = bf2(a, b);
+  lo = bf2(bfr(a), bfr(b));
+}
+
+// ----------------------------------------------------------------------------- R1
+struct R1Smem {
+  size_t w1f, w2h, w2l, b2, warp0, warp_bytes, po, bits, pend, pnode, cand, fmv, fmi, total;
+  __host__ __device__ R1Smem(int nmax, int K) {
+    size_t o = 0;
+    auto take = [&](size_t bytes) {
+      size_t r = o;
+      o = (o + bytes + 15) & ~size_t(15);
+      return r;
+    };
+    w1f = take(sizeof(uint2) * 2 * 2 * 8 * 32);   // [part][k step][n tile][lane]
+    w2h = take(sizeof(uint2) * 8 * 4 * 32);       // [n tile][k step][lane]
+    w2l = take(sizeof(uint2) * 8 * 4 * 32);
+    b2 = take(sizeof(float) * H);
+    warp0 = o;
+    o = 0;
+    po = take(sizeof(PadObj) * (size_t)K);
+    bits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
+    pend = take(64 * RPEND);                      // E1 input rows: 32 BF16 each
+    pnode = take(sizeof(int) * RPEND);
+    cand = take(sizeof(int16_t) * RCAND);
+    fmv = take(sizeof(float) * H);
+    fmi = take(sizeof(int) * H);
+    warp_bytes = o;
+    total = warp0 + RW * warp_bytes;
+  }
+};
+
+// E1 input row of an active node, 32 BF16: [p_hi, p_lo, n_hi, n_lo, u_hi, u_lo, 1, 0 ...]
+__device__ __forceinline__ void pack_row32(uint4* dst, float3 p, float3 nr, const float* u) {
+  dst[0] = make_uint4(bf2(p.x, p.y), bf2(p.z, bfr(p.x)), bf2(bfr(p.y), bfr(p.z)), bf2(nr.x, nr.y));
+  dst[1] = make_uint4(bf2(nr.z, bfr(nr.x)), bf2(bfr(nr.y), bfr(nr.z)), bf2(u[0], u[1]),
+                      bf2(u[2], bfr(u[0])));
+  dst[2] = make_uint4(bf2(bfr(u[1]), bfr(u[2])), bf2(1.f, 0.f), 0u, 0u);
+  dst[3] = make_uint4(0u, 0u, 0u, 0u);
+}
+
+// W1 column read by E1 input k of the 32-wide row (-1: bias, -2: zero)
+__device__ __forceinline__ int w1_col(int k) {
+  if (k < 6) return k % 3;
+  if (k < 12) return 3 + (k - 6) % 3;
+  if (k < 18) return 6 + (k - 12) % 3;
+  return k == 18 ? -1 : -2;
+}
+
+// Encoder of up to 16 active rows to FP32 accuracy: h1 = ReLU(W1 x + b1) (x and W1 split), the
+// E2 input split into BF16 hi + lo and E2 split, three products (hi hi, lo hi, hi lo); then
+// f = ReLU(E2 h1 + b2) folded into the per-lane running maxima with their node (lowest index
+// wins ties).
+__device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], uint32_t rows,
+                                           const int* node, int cnt, const uint2* sW1f,
+                                           const uint2* sW2h, const uint2* sW2l,
+                                           const float* sB2, int lane) {
+  const int grp = lane >> 2, tig = lane & 3;
+  const bool v0 = grp < cnt, v1 = grp + 8 < cnt;
+  const int n0 = v0 ? node[grp] : 0x7fffffff, n1 = v1 ? node[grp + 8] : 0x7fffffff;
+  uint32_t ax[2][4];
+#pragma unroll
+  for (int ks = 0; ks < 2; ++ks)
+    sm100::ldmatrix_x4(rows + (uint32_t)((lane & 15) * 64 + (lane >> 4) * 16 + ks * 32), ax[ks][0],
+                       ax[ks][1], ax[ks][2], ax[ks][3]);
+  uint32_t ah[4][4], al[4][4];
+#pragma unroll
+  for (int s4 = 0; s4 < 4; ++s4) {
+    float h[2][4];
+#pragma unroll
+    for (int t = 0; t < 2; ++t) {
+      const int nt = 2 * s4 + t;
+      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+        for (int part = 0; part < 2; ++part) {
+          const uint2 bb = sW1f[((part * 2 + ks) * 8 + nt) * 32 + lane];
+          sm100::mma_bf16_16816(acc, ax[ks], bb.x, bb.y, acc);
+        }
+#pragma unroll
+      for (int q = 0; q < 4; ++q) h[t][q] = relu(acc[q]);
+    }
+    split2(h[0][0], h[0][1], ah[s4][0], al[s4][0]);
+    split2(h[0][2], h[0][3], ah[s4][1], al[s4][1]);
+    split2(h[1][0], h[1][1], ah[s4][2], al[s4][2]);
+    split2(h[1][2], h[1][3], ah[s4][3], al[s4][3]);
+  }
+#pragma unroll
+  for (int nt = 0; nt < 8; ++nt) {
+    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4) {
+      const uint2 bh = sW2h[(nt * 4 + s4) * 32 + lane], bl = sW2l[(nt * 4 + s4) * 32 + lane];
+      sm100::mma_bf16_16816(acc, ah[s4], bh.x, bh.y, acc);
+      sm100::mma_bf16_16816(acc, al[s4], bh.x, bh.y, acc);
+      sm100::mma_bf16_16816(acc, ah[s4], bl.x, bl.y, acc);
+    }
+#pragma unroll
+    for (int e = 0; e < 2; ++e) {
+      const float b = sB2[8 * nt + 2 * tig + e];
+      const float f0 = relu(acc[e] + b), f1 = relu(acc[2 + e] + b);
+      if (v0 && (f0 > fv[nt][e] || (f0 == fv[nt][e] && n0 < fi[nt][e]))) {
+        fv[nt][e] = f0;
+        fi[nt][e] = n0;
+      }
+      if (v1 && (f1 > fv[nt][e] || (f1 == fv[nt][e] && n1 < fi[nt][e]))) {
+        fv[nt][e] = f1;
+        fi[nt][e] = n1;
+      }
+    }
+  }
+}
+
+__global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const R1Smem L(a.nmax, a.K);
+  uint2* sW1f = reinterpret_cast<uint2*>(smem + L.w1f);
+  uint2* sW2h = reinterpret_cast<uint2*>(smem + L.w2h);
+  uint2* sW2l = reinterpret_cast<uint2*>(smem + L.w2l);
+  float* sB2 = reinterpret_cast<float*>(smem + L.b2);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float* W = a.params;
+  for (int e = tid; e < 2 * 2 * 8 * 32; e += RT) {
+    const int l = e & 31, nt = (e >> 5) & 7, ks = (e >> 8) & 1, part = e >> 9;
+    const int n = 8 * nt + (l >> 2), k0 = 16 * ks + 2 * (l & 3);
+    auto wv = [&](int k) {
+      const int col = w1_col(k);
+      const float w = col == -1 ? W[OFF_B1 + n] : (col == -2 ? 0.f : W[OFF_W1 + n * NIN + col]);
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      return part == 0 ? h : __float2bfloat16_rn(w - __bfloat162float(h));
+    };
+    __nv_bfloat162 lo = __halves2bfloat162(wv(k0), wv(k0 + 1));
+    __nv_bfloat162 hi = __halves2bfloat162(wv(k0 + 8), wv(k0 + 9));
+    sW1f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
+  }
+  for (int e = tid; e < 8 * 4 * 32; e += RT) {
+    const int l = e & 31, s4 = (e >> 5) & 3, nt = e >> 7;
+    const int n = 8 * nt + (l >> 2), k = 16 * s4 + 2 * (l & 3);
+    const float w[4] = {W[OFF_W2 + n * H + k], W[OFF_W2 + n * H + k + 1], W[OFF_W2 + n * H + k + 8],
+                        W[OFF_W2 + n * H + k + 9]};
+    uint32_t h01, l01, h89, l89;
+    split2(w[0], w[1], h01, l01);
+    split2(w[2], w[3], h89, l89);
+    sW2h[e] = make_uint2(h01, h89);
+    sW2l[e] = make_uint2(l01, l89);
+  }
+  for (int i = tid; i < H; i += RT) sB2[i] = W[OFF_B2 + i];
+  __syncthreads();
+
+  unsigned char* wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
+  PadObj* spo = reinterpret_cast<PadObj*>(wb + L.po);
+  uint32_t* sBits = reinterpret_cast<uint32_t*>(wb + L.bits);
+  uint4* sPend = reinterpret_cast<uint4*>(wb + L.pend);
+  const uint32_t sPend_addr = (uint32_t)__cvta_generic_to_shared(sPend);
+  int* sPNode = reinterpret_cast<int*>(wb + L.pnode);
+  int16_t* sCand = reinterpret_cast<int16_t*>(wb + L.cand);
+  float* sFv = reinterpret_cast<float*>(wb + L.fmv);
+  int* sFi = reinterpret_cast<int*>(wb + L.fmi);
+  const unsigned lt = (1u << lane) - 1u;
+  const bool use_r = a.mode != MODE_LINEAR_ONLY, use_l = a.mode != MODE_RESIDUAL_ONLY;
+
+  int next = 0;
+  if (lane == 0) next = atomicAdd(a.ticket, 1);
+  for (;;) {
+    __syncwarp();
+    const int item = __shfl_sync(FULL, next, 0);
+    if (item >= a.num_items) break;
+    if (lane == 0) next = atomicAdd(a.ticket, 1);
+    const int pad = a.item_pad[item];
+    const int ty = a.pad_type[pad];
+    const int o = a.type_off[ty];
+    const int n = a.type_off[ty + 1] - o;
+    const int nwords = (n + 31) >> 5;
+    const long long base = a.pad_off[pad];
+    const float* tpos = a.type_pos + 3 * (size_t)o;
+    const float* tnrm = a.type_nrm + 3 * (size_t)o;
+    const float* G = a.grad_disp + 3 * base;
+    const size_t brow = (size_t)a.bg_off[ty] + (size_t)3 * a.pad_inst[pad] * n;
+    __nv_bfloat16* bgh = reinterpret_cast<__nv_bfloat16*>(a.bg_hi) + brow;
+    __nv_bfloat16* bgl = reinterpret_cast<__nv_bfloat16*>(a.bg_lo) + brow;
+    {
+      const int* src = reinterpret_cast<const int*>(a.padobj + (size_t)pad * a.K);
+      int* dst = reinterpret_cast<int*>(spo);
+      const int words = a.K * (int)(sizeof(PadObj) / 4);
+      for (int e = lane; e < words; e += 32) dst[e] = src[e];
+    }
+    const bool invalid = a.pad_bad[pad] != 0;
+    __syncwarp();
+    float gap = 0.f;
+    for (int k = 0; k < a.K; ++k) gap = fmaxf(gap, 2.f * spo[k].tau);
+
+    float fv[8][2];
+    int fi[8][2];
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        fv[nt][e] = -1.f;   // features are >= 0
+        fi[nt][e] = 0x7fffffff;
+      }
+    float gs0 = 0.f, gs1 = 0.f, gs2 = 0.f;   // sum of G over this lane's passive nodes
+    int npend = 0, ncand = 0, m = 0;         // warp-uniform
+
+    // a decided node: its workspace entries, the B operand of the propagation reverse, and
+    // (active) a row for the encoder
+    auto decided = [&](int i, const NodeContact& c, float3 p, float3 nr, bool push) {
+      const float g0 = G[3 * i], g1 = G[3 * i + 1], g2 = G[3 * i + 2];
+      if (c.active) {
+        a.ws_u[base + i] = make_float4(c.u[0], c.u[1], c.u[2], c.phi);
+        a.ws_du[base + i] = make_float4(g0, g1, g2, 0.f);   // U_i = u_hat_i: direct term
+      } else {
+        gs0 += g0;
+        gs1 += g1;
+        gs2 += g2;
+      }
+      if (use_l) {
+        const float q0 = c.active ? 0.f : g0, q1 = c.active ? 0.f : g1, q2 = c.active ? 0.f : g2;
+        bgh[i] = __float2bfloat16_rn(q0);
+        bgh[n + i] = __float2bfloat16_rn(q1);
+        bgh[2 * n + i] = __float2bfloat16_rn(q2);
+        bgl[i] = __float2bfloat16_rn(bfr(q0));
+        bgl[n + i] = __float2bfloat16_rn(bfr(q1));
+        bgl[2 * n + i] = __float2bfloat16_rn(bfr(q2));
+      }
+      (void)push;
+    };
+    auto refine_batch = [&]() {
+      const int cnt = min(32, ncand);
+      const bool has = lane < cnt;
+      NodeContact c;
+      c.active = false;
+      c.phi = 0.f;
+      c.k = -1;
+      c.u[0] = c.u[1] = c.u[2] = 0.f;
+      int i = 0;
+      float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
+      if (has) {
+        i = sCand[ncand - cnt + lane];
+        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+        c = contact_refine(spo, a.K, p, nr, 0.f);
+        decided(i, c, p, nr, true);
+        if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
+      }
+      ncand -= cnt;
+      const unsigned b = __ballot_sync(FULL, c.active);
+      if (c.active && use_r) {
+        const int q = npend + __popc(b & lt);
+        sPNode[q] = i;
+        pack_row32(sPend + 4 * q, p, nr, c.u);
+      }
+      m += __popc(b);
+      if (use_r) npend += __popc(b);
+      __syncwarp();
+    };
+    auto drain = [&](int keep) {
+      while (npend > keep) {
+        const int cnt = min(16, npend);
+        bwd_encode(fv, fi, sPend_addr + 64u * (uint32_t)(npend - cnt), sPNode + npend - cnt, cnt,
+                   sW1f, sW2h, sW2l, sB2, lane);
+        npend -= cnt;
+      }
+      __syncwarp();
+    };
+
+    for (int r0 = 0; r0 < n; r0 += 32) {
+      const int i = r0 + lane;
+      int cls = CONTACT_OUT;
+      NodeContact c;
+      c.active = false;
+      c.phi = 0.f;
+      c.k = -1;
+      c.u[0] = c.u[1] = c.u[2] = 0.f;
+      float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
+      if (i < n && !invalid) {
+        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+        cls = contact_classify(spo, a.K, p, nr, gap, &c);
+      }
+      if (i < n && cls != CONTACT_BAND) decided(i, c, p, nr, false);
+      const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
+      const unsigned bC = __ballot_sync(FULL, cls == CONTACT_BAND);
+      if (lane == 0) sBits[r0 >> 5] = bA;
+      if (cls == CONTACT_FAST && use_r) {
+        const int q = npend + __popc(bA & lt);
+        sPNode[q] = i;
+        pack_row32(sPend + 4 * q, p, nr, c.u);
+      }
+      if (cls == CONTACT_BAND) sCand[ncand + __popc(bC & lt)] = (int16_t)i;
+      m += __popc(bA);
+      if (use_r) npend += __popc(bA);
+      ncand += __popc(bC);
+      __syncwarp();
+      drain(15);
+      if (ncand > RCAND - 32) {
+        refine_batch();
+        drain(15);
+      }
+    }
+    while (ncand > 0) {
+      refine_batch();
+      drain(15);
+    }
+    drain(0);
+
+    const int gi = a.pad_gi[pad];
+    for (int w = lane; w < nwords; w += 32) a.maskbits[a.mask_woff[pad] + w] = sBits[w];
+#pragma unroll
+    for (int sh = 16; sh > 0; sh >>= 1) {
+      gs0 += __shfl_xor_sync(FULL, gs0, sh);
+      gs1 += __shfl_xor_sync(FULL, gs1, sh);
+      gs2 += __shfl_xor_sync(FULL, gs2, sh);
+    }
+    float* pr = a.pr + (size_t)pad * PR_STRIDE;
+    if (lane == 0) {
+      a.pad_m[pad] = m;
+      a.inst_m[gi] = m;
+      // dL/db_D2 sums G over passive nodes of pads with contact (no decoder in LINEAR_ONLY)
+      const bool dec = m > 0 && use_r;
+      pr[PR_GSUM + 0] = dec ? gs0 : 0.f;
+      pr[PR_GSUM + 1] = dec ? gs1 : 0.f;
+      pr[PR_GSUM + 2] = dec ? gs2 : 0.f;
+    }
+    if (m == 0 || !use_r) continue;
+
+    // channel maxima of the active nodes: reduce (value, node) over the row groups
+#pragma unroll
+    for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        float v = fv[nt][e];
+        int id = fi[nt][e];
+#pragma unroll
+        for (int sh = 4; sh < 32; sh <<= 1) {
+          const float ov = __shfl_xor_sync(FULL, v, sh);
+          const int oi = __shfl_xor_sync(FULL, id, sh);
+          if (ov > v || (ov == v && oi < id)) {
+            v = ov;
+            id = oi;
+          }
+        }
+        if (lane < 4) {
+          sFv[8 * nt + 2 * lane + e] = v;
+          sFi[8 * nt + 2 * lane + e] = id;
+        }
+      }
+    __syncwarp();
+    // passive candidate of each channel: the first passive node of the ranked f0 order
+    // (equal values are ranked by node index); lane l walks channels l and l + 32, and the
+    // channels still open go warp-wide, 32 ranks per test
+    const float2* rk = a.ranked + (size_t)H * o;
+    float pv[2] = {-1.f, -1.f};
+    int pi[2] = {0x7fffffff, 0x7fffffff};
+    bool done[2] = {false, false};
+    {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const float2* row = rk + (size_t)(lane + 32 * h) * n;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          if (done[h] || j >= n) continue;
+          const float2 e = __ldg(row + j);
+          const int idx = __float_as_int(e.y);
+          if (!((sBits[idx >> 5] >> (idx & 31)) & 1u)) {
+            pv[h] = e.x;
+            pi[h] = idx;
+            done[h] = true;
+          }
+        }
+        if (n <= 4) done[h] = true;
+      }
+    }
+    unsigned long long open = (unsigned long long)__ballot_sync(FULL, !done[0]) |
+                              ((unsigned long long)__ballot_sync(FULL, !done[1]) << 32);
+    while (open) {
+      const int ch = __ffsll((long long)open) - 1;
+      open &= open - 1;
+      float bv = -1.f;
+      int bi = 0x7fffffff;
+      for (int q0 = 4; q0 < n; q0 += 32) {
+        const int r = q0 + lane;
+        float2 e = make_float2(0.f, __int_as_float(0));
+        bool passive = false;
+        if (r < n) {
+          e = __ldg(rk + (size_t)ch * n + r);
+          const int idx = __float_as_int(e.y);
+          passive = !((sBits[idx >> 5] >> (idx & 31)) & 1u);
+        }
+        const unsigned bal = __ballot_sync(FULL, passive);
+        if (bal) {
+          const int src = __ffs(bal) - 1;
+          bv = __shfl_sync(FULL, e.x, src);
+          bi = __float_as_int(__shfl_sync(FULL, e.y, src));
+          break;
+        }
+      }
+      if (ch == lane) {
+        pv[0] = bv;
+        pi[0] = bi;
+      }
+      if (ch == lane + 32) {
+        pv[1] = bv;
+        pi[1] = bi;
+      }
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      float v = sFv[c];
+      int id = sFi[c];
+      if (pv[h] > v || (pv[h] == v && pi[h] < id)) {
+        v = pv[h];
+        id = pi[h];
+      }
+      pr[PR_G0 + c] = v;
+      reinterpret_cast<int*>(pr)[PR_ROUTE + c] = id;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- R2
+// warp per pad: ag = G1 g0 + b_G1, g = ReLU(ag), beta = D1[:, 64:] g (FP32; the decoder's
+// bias rides in the h0 table)
+__global__ void __launch_bounds__(256) bwd_global_kernel(BwdBatchedArgs a) {
+  __shared__ float sGT[H * H];   // [k][c] = G1[c][k]
+  __shared__ float sDT[H * H];   // [k][c] = D1[c][64 + k]
+  const float* W = a.params;
+  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+    const int c = e >> 6, k = e & (H - 1);
+    sGT[k * H + c] = W[OFF_WG + c * H + k];
+    sDT[k * H + c] = W[OFF_WD + c * 2 * H + H + k];
+  }
+  __syncthreads();
+  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
+  for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < a.num_items; pad += gridDim.x * wpb) {
+    if (a.pad_m[pad] == 0) continue;
+    float* pr = a.pr + (size_t)pad * PR_STRIDE;
+    const float x0 = pr[PR_G0 + lane], x1 = pr[PR_G0 + 32 + lane];
+    float ag[2], g[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      float acc = W[OFF_BG + c];
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fmaf(sGT[k * H + c], __shfl_sync(FULL, x0, k), acc);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fmaf(sGT[(32 + k) * H + c], __shfl_sync(FULL, x1, k), acc);
+      ag[h] = acc;
+      g[h] = relu(acc);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int c = lane + 32 * h;
+      float acc = 0.f;   // the D1 bias is part of the h0 table (h0 = D1_f f0 + b_D1)
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fmaf(sDT[k * H + c], __shfl_sync(FULL, g[0], k), acc);
+#pragma unroll 8
+      for (int k = 0; k < 32; ++k) acc = fmaf(sDT[(32 + k) * H + c], __shfl_sync(FULL, g[1], k), acc);
+      pr[PR_AG + c] = ag[h];
+      pr[PR_G + c] = g[h];
+      pr[PR_BETA + c] = acc;
+    }
+  }
+}
+
+// ----------------------------------------------------------------------------- R3
+// CTA = (pad type, 64 instances); warp w takes instances 8 w .. 8 w + 7 of the group and all
+// the type's nodes, eight at a time in lock step with the other warps; lane l owns channels
+// 2 l and 2 l + 1.
+constexpr int R3_INST = 64;
+constexpr int R3_IPW = R3_INST / 8;
+constexpr int R3_NODES = 8;
+
+__global__ void __launch_bounds__(256) bwd_decoder_kernel(BwdBatchedArgs a) {
+  __shared__ float2 sA3[8][R3_NODES][32];   // per-warp A3 partials of the current node chunk
+  __shared__ float sD2[8][3][H];            // per-warp dD2 partials
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const R3Group grp = a.r3_groups[blockIdx.x];
+  const int t = grp.type;
+  const int o = a.type_off[t], n = a.type_off[t + 1] - o;
+  const int ninst = a.inst_off[t + 1] - a.inst_off[t];
+  const int nw = (n + 31) >> 5;
+  const float* W = a.params;
+  const float2 w4a = make_float2(W[OFF_W4 + 2 * lane], W[OFF_W4 + 2 * lane + 1]);
+  const float2 w4b = make_float2(W[OFF_W4 + H + 2 * lane], W[OFF_W4 + H + 2 * lane + 1]);
+  const float2 w4c = make_float2(W[OFF_W4 + 2 * H + 2 * lane], W[OFF_W4 + 2 * H + 2 * lane + 1]);
+  // this warp's instances
+  float2 beta[R3_IPW], S[R3_IPW];
+  long long ibase[R3_IPW];
+  long long iwoff[R3_IPW];
+  bool live[R3_IPW];
+#pragma unroll
+  for (int x = 0; x < R3_IPW; ++x) {
+    const int k = grp.k0 + R3_IPW * warp + x;
+    live[x] = k < ninst;
+    const int gi = a.inst_off[t] + (live[x] ? k : 0);
+    const int pad = a.inst_pad[gi];
+    live[x] = live[x] && a.inst_m[gi] > 0;
+    const float* pr = a.pr + (size_t)pad * PR_STRIDE;
+    beta[x] = live[x] ? make_float2(pr[PR_BETA + 2 * lane], pr[PR_BETA + 2 * lane + 1])
+                      : make_float2(0.f, 0.f);
+    S[x] = make_float2(0.f, 0.f);
+    ibase[x] = a.inst_base[gi];
+    iwoff[x] = a.type_woff[t] + (long long)(live[x] ? k : 0) * nw;
+  }
+  float2 d2a = make_float2(0.f, 0.f), d2b = d2a, d2c = d2a;   // dD2 rows 0..2, my channels
+  for (int i0 = 0; i0 < n; i0 += R3_NODES) {
+    float2 h0[R3_NODES], A3[R3_NODES];
+#pragma unroll
+    for (int r = 0; r < R3_NODES; ++r) {
+      const int i = i0 + r;
+      h0[r] = i < n ? *reinterpret_cast<const float2*>(a.h0tab + (size_t)(o + i) * H + 2 * lane)
+                    : make_float2(0.f, 0.f);
+      A3[r] = make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int x = 0; x < R3_IPW; ++x) {
+      if (!live[x]) continue;
+      const uint32_t word = a.maskbits[iwoff[x] + (i0 >> 5)] >> (i0 & 31);
+      const float* Gk = a.grad_disp + 3 * (ibase[x] + i0);
+#pragma unroll
+      for (int r = 0; r < R3_NODES; ++r) {
+        if (i0 + r >= n || ((word >> r) & 1u)) continue;   // active nodes have no decoder term
+        const float g0 = Gk[3 * r], g1 = Gk[3 * r + 1], g2 = Gk[3 * r + 2];
+        float2 dz = __fmul2_rn(w4a, make_float2(g0, g0));
+        dz = __ffma2_rn(w4b, make_float2(g1, g1), dz);
+        dz = __ffma2_rn(w4c, make_float2(g2, g2), dz);
+        const float2 z = __fadd2_rn(h0[r], beta[x]);
+        const float2 da = make_float2(z.x > 0.f ? dz.x : 0.f, z.y > 0.f ? dz.y : 0.f);
+        const float2 rz = make_float2(relu(z.x), relu(z.y));
+        S[x] = __fadd2_rn(S[x], da);
+        A3[r] = __fadd2_rn(A3[r], da);
+        d2a = __ffma2_rn(make_float2(g0, g0), rz, d2a);
+        d2b = __ffma2_rn(make_float2(g1, g1), rz, d2b);
+        d2c = __ffma2_rn(make_float2(g2, g2), rz, d2c);
+      }
+    }
+    // A3 of these nodes over the group's 64 instances: warps in order
+#pragma unroll
+    for (int r = 0; r < R3_NODES; ++r) sA3[warp][r][lane] = A3[r];
+    __syncthreads();
+    for (int e = threadIdx.x; e < R3_NODES * 32; e += blockDim.x) {
+      const int r = e >> 5, l = e & 31;
+      if (i0 + r >= n) continue;
+      float2 s = sA3[0][r][l];
+      for (int w = 1; w < 8; ++w) s = __fadd2_rn(s, sA3[w][r][l]);
+      *reinterpret_cast<float2*>(a.a3part + grp.a3off + (size_t)(i0 + r) * H + 2 * l) = s;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int x = 0; x < R3_IPW; ++x) {
+    if (!live[x]) continue;
+    const int gi = a.inst_off[t] + grp.k0 + R3_IPW * warp + x;
+    float* pr = a.pr + (size_t)a.inst_pad[gi] * PR_STRIDE;
+    pr[PR_S + 2 * lane] = S[x].x;
+    pr[PR_S + 2 * lane + 1] = S[x].y;
+  }
+  sD2[warp][0][2 * lane] = d2a.x;
+  sD2[warp][0][2 * lane + 1] = d2a.y;
+  sD2[warp][1][2 * lane] = d2b.x;
+  sD2[warp][1][2 * lane + 1] = d2b.y;
+  sD2[warp][2][2 * lane] = d2c.x;
+  sD2[warp][2][2 * lane + 1] = d2c.y;
+  __syncthreads();
+  for (int e = threadIdx.x; e < 3 * H; e += blockDim.x) {
+    float s = 0.f;
+    for (int w = 0; w < 8; ++w) s += sD2[w][e / H][e % H];
+    a.d2part[(size_t)blockIdx.x * 3 * H + e] = s;
+  }
+}
+
+// A3[type node][c] = sum over the type's groups (in order) of the partials
+__global__ void bwd_reduce_a3_kernel(BwdBatchedArgs a) {
+  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+  const long long total = (long long)a.total_nodes * H;
+  if (e >= total) return;
+  const int node = (int)(e / H), c = (int)(e % H);
+  int t = 0;
+  while (node >= a.type_off[t + 1]) ++t;
+  const int o = a.type_off[t], n = a.type_off[t + 1] - o;
+  const float* src = a.a3part + a.a3_toff[t] + (size_t)(node - o) * H + c;
+  float s = 0.f;
+  for (int g = 0; g < a.a3_tgroups[t]; ++g) s += src[(size_t)g * n * H];
+  a.a3[e] = s;
+}
+
+// ----------------------------------------------------------------------------- R4
+// warp per pad (static assignment): global MLP reverse and the encoder reverse of each
+// channel's argmax node, into per-warp partials of params [OFF_W1, OFF_B2 + 64)
+constexpr int R4_WARPS = 4;
+constexpr int R4_LEN = OFF_B2 + H - OFF_W1;   // E1, b1, E2, b2
+
+constexpr size_t R4_SMEM = sizeof(float) * (3 * H * H + R4_WARPS * (R4_LEN + 2 * H));
+
+__global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* sD1g = reinterpret_cast<float*>(smem);   // [c][k] = D1[c][64 + k]
+  float* sG1 = sD1g + H * H;                       // [c][k] = G1[c][k]
+  float* sW2 = sG1 + H * H;                        // [c][k] = E2[c][k]
+  float* sAccAll = sW2 + H * H;                    // [warp][R4_LEN]
+  float* sH1All = sAccAll + R4_WARPS * R4_LEN;     // [warp][64]
+  int* sNodeAll = reinterpret_cast<int*>(sH1All + R4_WARPS * H);   // [warp][64]
+  const float* W = a.params;
+  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+    const int c = e >> 6, k = e & (H - 1);
+    sD1g[e] = W[OFF_WD + c * 2 * H + H + k];
+    sG1[e] = W[OFF_WG + e];
+    sW2[e] = W[OFF_W2 + e];
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  float* acc = sAccAll + (size_t)warp * R4_LEN;
+  float* sH1w = sH1All + warp * H;
+  int* sNodeW = sNodeAll + warp * H;
+  for (int e = lane; e < R4_LEN; e += 32) acc[e] = 0.f;
+  __syncthreads();
+  const int gw = blockIdx.x * R4_WARPS + warp, nwarps = gridDim.x * R4_WARPS;
+  for (int pad = gw; pad < a.num_items; pad += nwarps) {
+    if (a.pad_m[pad] == 0) continue;
+    const float* pr = a.pr + (size_t)pad * PR_STRIDE;
+    const int ty = a.pad_type[pad];
+    const int o = a.type_off[ty];
+    const long long base = a.pad_off[pad];
+    // dg = D1_g^T S ; dag = dg [ag > 0] ; dg0 = G1^T dag
+    const float s0 = pr[PR_S + lane], s1 = pr[PR_S + 32 + lane];
+    float dag[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      float v = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(sD1g[c * H + k], __shfl_sync(FULL, s0, c), v);
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(sD1g[(32 + c) * H + k], __shfl_sync(FULL, s1, c), v);
+      dag[h] = pr[PR_AG + k] > 0.f ? v : 0.f;
+    }
+    float* prw = a.pr + (size_t)pad * PR_STRIDE;
+    prw[PR_DAG + lane] = dag[0];
+    prw[PR_DAG + 32 + lane] = dag[1];
+    float dg0[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = lane + 32 * h;
+      float v = 0.f;
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(sG1[c * H + k], __shfl_sync(FULL, dag[0], c), v);
+#pragma unroll 8
+      for (int c = 0; c < 32; ++c) v = fmaf(sG1[(32 + c) * H + k], __shfl_sync(FULL, dag[1], c), v);
+      dg0[h] = v;
+    }
+    // routes: distinct argmax nodes, first appearance in channel order
+    const int rt0 = reinterpret_cast<const int*>(pr)[PR_ROUTE + lane];
+    const int rt1 = reinterpret_cast<const int*>(pr)[PR_ROUTE + 32 + lane];
+    int nd = 0;
+    for (int c = 0; c < H; ++c) {
+      const int node = __shfl_sync(FULL, c < 32 ? rt0 : rt1, c & 31);
+      bool seen = false;
+      for (int q = lane; q < nd; q += 32) seen |= sNodeW[q] == node;
+      if (!__any_sync(FULL, seen)) {
+        if (lane == 0) sNodeW[nd] = node;
+        ++nd;
+      }
+      __syncwarp();
+    }
+    const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+    for (int q = 0; q < nd; ++q) {
+      const int node = sNodeW[q];
+      const bool act = (bits[node >> 5] >> (node & 31)) & 1u;
+      const float4 u = act ? a.ws_u[base + node] : make_float4(0.f, 0.f, 0.f, 0.f);
+      float x[NIN];
+      x[0] = a.type_pos[3 * (size_t)(o + node)];
+      x[1] = a.type_pos[3 * (size_t)(o + node) + 1];
+      x[2] = a.type_pos[3 * (size_t)(o + node) + 2];
+      x[3] = a.type_nrm[3 * (size_t)(o + node)];
+      x[4] = a.type_nrm[3 * (size_t)(o + node) + 1];
+      x[5] = a.type_nrm[3 * (size_t)(o + node) + 2];
+      x[6] = u.x;
+      x[7] = u.y;
+      x[8] = u.z;
+      // forward of this node: a1, h1 (lanes own units k = lane, lane + 32)
+      float a1[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        float v = W[OFF_B1 + k];
+#pragma unroll
+        for (int q2 = 0; q2 < NIN; ++q2) v = fmaf(W[OFF_W1 + k * NIN + q2], x[q2], v);
+        a1[h] = v;
+        sH1w[k] = relu(v);
+      }
+      __syncwarp();
+      // routed gradient of this node: dA2[c] = dg0[c] [a2_c > 0] for its channels
+      float da2[2];
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        const bool routed = (h == 0 ? rt0 : rt1) == node;
+        float a2 = W[OFF_B2 + c];
+        if (routed) {
+#pragma unroll 8
+          for (int k = 0; k < H; ++k) a2 = fmaf(sW2[c * H + k], sH1w[k], a2);
+        }
+        da2[h] = (routed && a2 > 0.f) ? dg0[h] : 0.f;
+      }
+      // dE2[c][k] += dA2[c] h1[k] (lanes over k), db2, dh1 = E2^T dA2
+      float dh1[2] = {0.f, 0.f};
+      for (int c = 0; c < H; ++c) {
+        const float d = __shfl_sync(FULL, c < 32 ? da2[0] : da2[1], c & 31);
+        if (d == 0.f) continue;   // warp-uniform
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+          const int k = lane + 32 * h;
+          acc[OFF_W2 - OFF_W1 + c * H + k] += d * sH1w[k];
+          dh1[h] = fmaf(sW2[c * H + k], d, dh1[h]);
+        }
+        if (lane == 0) acc[OFF_B2 - OFF_W1 + c] += d;
+      }
+      // dA1 = dh1 [a1 > 0]; dE1 += dA1 x^T; db1; du_hat = E1[:, 6:9]^T dA1 (active)
+      float du0 = 0.f, du1 = 0.f, du2 = 0.f;
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int k = lane + 32 * h;
+        const float d1 = a1[h] > 0.f ? dh1[h] : 0.f;
+#pragma unroll
+        for (int q2 = 0; q2 < NIN; ++q2) acc[k * NIN + q2] += d1 * x[q2];
+        acc[OFF_B1 - OFF_W1 + k] += d1;
+        du0 = fmaf(W[OFF_W1 + k * NIN + 6], d1, du0);
+        du1 = fmaf(W[OFF_W1 + k * NIN + 7], d1, du1);
+        du2 = fmaf(W[OFF_W1 + k * NIN + 8], d1, du2);
+      }
+      if (act) {
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) {
+          du0 += __shfl_xor_sync(FULL, du0, sh);
+          du1 += __shfl_xor_sync(FULL, du1, sh);
+          du2 += __shfl_xor_sync(FULL, du2, sh);
+        }
+        if (lane == 0) {
+          float4 d = a.ws_du[base + node];
+          d.x += du0;
+          d.y += du1;
+          d.z += du2;
+          a.ws_du[base + node] = d;
+        }
+      }
+      __syncwarp();
+    }
+  }
+  __syncwarp();
+  for (int e = lane; e < R4_LEN; e += 32) a.r4part[(size_t)gw * R4_LEN + e] = acc[e];
+}
+
+// ----------------------------------------------------------------------------- R4b
+// sums over pads (chunks of 64 pads, in order): dD1_g = sum S g^T, db_D1 = sum S,
+// dG1 = sum dag g0^T, db_G1 = sum dag.  Partial layout per chunk: params [OFF_WG, OFF_W4).
+constexpr int R4B_PADS = 64;
+constexpr int R4B_LEN = OFF_W4 - OFF_WG;
+
+__global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
+  __shared__ float sA[R4B_PADS][TLD];   // S or dag per pad
+  __shared__ float sB[R4B_PADS][TLD];   // g or g0 per pad
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const int p0 = blockIdx.x * R4B_PADS;
+  float* out = a.r4bpart + (size_t)blockIdx.x * R4B_LEN;
+  for (int which = 0; which < 2; ++which) {
+    const int oa = which == 0 ? PR_S : PR_DAG, ob = which == 0 ? PR_G : PR_G0;
+    for (int e = tid; e < R4B_PADS * H; e += 256) {
+      const int r = e >> 6, c = e & (H - 1);
+      const int pad = p0 + r;
+      const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
+      const float* pr = a.pr + (size_t)(ok ? pad : 0) * PR_STRIDE;
+      sA[r][c] = ok ? pr[oa + c] : 0.f;
+      sB[r][c] = ok ? pr[ob + c] : 0.f;
+    }
+    __syncthreads();
+    float acc[4][4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+    for (int r0 = 0; r0 < R4B_PADS; r0 += 64) tile_acc(&sA[r0][0], &sB[r0][0], ti, tj, acc);
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const int c = 4 * ti + i, k = 4 * tj + j;
+        if (which == 0) out[OFF_WD - OFF_WG + c * 2 * H + H + k] = acc[i][j];
+        else out[c * H + k] = acc[i][j];
+      }
+    if (tid < H) {
+      float s = 0.f;
+      for (int r = 0; r < R4B_PADS; ++r) s += sA[r][tid];
+      if (which == 0) out[OFF_BD - OFF_WG + tid] = s;
+      else out[OFF_BG - OFF_WG + tid] = s;
+    }
+    if (which == 0) {   // the local half of D1 belongs to R5: zeros here
+      for (int e = tid; e < H * H; e += 256) out[OFF_WD - OFF_WG + (e >> 6) * 2 * H + (e & 63)] = 0.f;
+    }
+    __syncthreads();
+  }
+}
+
+// ----------------------------------------------------------------------------- R5
+// 64 type nodes per CTA: the decoder path's encoder reverse with passive inputs [p, n, 0]:
+// dD1_f += A3^T F0 ; dF = A3 D1_f ; dA2 = dF [f0 > 0] ; dE2 += dA2^T H1 ; dH1 = dA2 E2 ;
+// dA1 = dH1 [c > 0] ; dE1[:, 0:6] += dA1^T [P N] ; biases.  Partial layout per CTA: params
+// [OFF_W1, OFF_W4) (the global half of D1 and G1 stay zero).
+constexpr int R5_LEN = OFF_W4 - OFF_W1;
+
+__global__ void __launch_bounds__(256) bwd_typenode_kernel(BwdBatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  float* sA3 = reinterpret_cast<float*>(smem);        // [r][c]
+  float* sA3T = sA3 + 64 * TLD;                        // [c][r]
+  float* sF0 = sA3T + 64 * TLD;                        // [r][k]
+  float* sH1 = sF0 + 64 * TLD;                         // [r][k]
+  float* sWd = sH1 + 64 * TLD;                         // D1_f [c][k]
+  float* sW2 = sWd + 64 * TLD;                         // E2 [c][k]
+  float* sD = sW2 + 64 * TLD;                          // dA2 [r][c]
+  float* sDT = sD + 64 * TLD;                          // dA2 [c][r]
+  float* sX = sDT + 64 * TLD;                          // [r][6]
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const float* W = a.params;
+  const int r0 = blockIdx.x * 64;
+  float* out = a.r5part + (size_t)blockIdx.x * R5_LEN;
+  for (int e = tid; e < R5_LEN; e += 256) out[e] = 0.f;
+  for (int e = tid; e < 64 * H; e += 256) {
+    const int r = e >> 6, c = e & (H - 1);
+    const int node = r0 + r;
+    const bool ok = node < a.total_nodes;
+    const float v = ok ? a.a3[(size_t)node * H + c] : 0.f;
+    sA3[r * TLD + c] = v;
+    sA3T[c * TLD + r] = v;
+    sF0[r * TLD + c] = ok ? a.f0tab[(size_t)node * H + c] : 0.f;
+    sH1[r * TLD + c] = ok ? relu(a.ctab[(size_t)node * H + c]) : 0.f;
+    sWd[r * TLD + c] = W[OFF_WD + r * 2 * H + c];
+    sW2[r * TLD + c] = W[OFF_W2 + r * H + c];
+  }
+  for (int e = tid; e < 64 * 6; e += 256) {
+    const int r = e / 6, q = e % 6;
+    const int node = r0 + r;
+    const bool ok = node < a.total_nodes;
+    sX[e] = ok ? (q < 3 ? a.type_pos[3 * (size_t)node + q] : a.type_nrm[3 * (size_t)node + q - 3]) : 0.f;
+  }
+  __syncthreads();
+  float acc[4][4];
+  // dD1_f[c][k] = sum_r A3[r][c] F0[r][k]
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sA3, sF0, ti, tj, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[OFF_WD - OFF_W1 + (4 * ti + i) * 2 * H + 4 * tj + j] = acc[i][j];
+  // dF[r][k] = sum_c A3[r][c] D1_f[c][k] ; dA2 = dF [f0 > 0]
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sA3T, sWd, ti, tj, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = 4 * ti + i, k = 4 * tj + j;
+      const float d = sF0[r * TLD + k] > 0.f ? acc[i][j] : 0.f;
+      sD[r * TLD + k] = d;
+      sDT[k * TLD + r] = d;
+    }
+  __syncthreads();
+  // dE2[c][k] = sum_r dA2[r][c] H1[r][k] ; db2
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sD, sH1, ti, tj, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) out[OFF_W2 - OFF_W1 + (4 * ti + i) * H + 4 * tj + j] = acc[i][j];
+  if (tid < H) {
+    float s = 0.f;
+    for (int r = 0; r < 64; ++r) s += sD[r * TLD + tid];
+    out[OFF_B2 - OFF_W1 + tid] = s;
+  }
+  // dH1[r][k] = sum_c dA2[r][c] E2[c][k] ; dA1 = dH1 [c > 0] (into sA3, no longer needed)
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sDT, sW2, ti, tj, acc);
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int r = 4 * ti + i, k = 4 * tj + j;
+      sA3[r * TLD + k] = sH1[r * TLD + k] > 0.f ? acc[i][j] : 0.f;
+    }
+  __syncthreads();
+  // dE1[c][q] = sum_r dA1[r][c] X[r][q] (q < 6) ; db1
+  for (int e = tid; e < H * 7; e += 256) {
+    const int c = e / 7, q = e % 7;
+    float s = 0.f;
+    for (int r = 0; r < 64; ++r) s = fmaf(sA3[r * TLD + c], q < 6 ? sX[r * 6 + q] : 1.f, s);
+    if (q < 6) out[c * NIN + q] = s;
+    else out[OFF_B1 - OFF_W1 + c] = s;
+  }
+}
+
+// ----------------------------------------------------------------------------- R7
+// warp per pad: dL/du_hat and dL/dpen per node, and the pose partials (active nodes in
+// node order)
+__global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  PadObj* spo = reinterpret_cast<PadObj*>(smem) + (size_t)warp * a.K;
+  for (int pad = blockIdx.x * wpb + warp; pad < a.num_items; pad += gridDim.x * wpb) {
+    const int ty = a.pad_type[pad];
+    const int o = a.type_off[ty];
+    const int n = a.type_off[ty + 1] - o;
+    const int env = pad / a.P;
+    const long long base = a.pad_off[pad];
+    const int m = a.pad_m[pad];
+    {
+      const int* src = reinterpret_cast<const int*>(a.padobj + (size_t)pad * a.K);
+      int* dst = reinterpret_cast<int*>(spo);
+      const int words = a.K * (int)(sizeof(PadObj) / 4);
+      for (int e = lane; e < words; e += 32) dst[e] = src[e];
+    }
+    __syncwarp();
+    const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+    const float* pp = a.pad_pose + 7 * (size_t)pad;
+    float Rp[3][3];
+    quat_to_mat<float>(pp + 3, Rp);
+    float pose[MAX_K][6];
+#pragma unroll
+    for (int k = 0; k < MAX_K; ++k)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) pose[k][q] = 0.f;
+    for (int i = lane; i < n; i += 32) {
+      const bool act = m > 0 && ((bits[i >> 5] >> (i & 31)) & 1u);
+      float3 du = make_float3(0.f, 0.f, 0.f);
+      float pen = 0.f;
+      if (act) {
+        const float4 d = a.ws_du[base + i];
+        du = make_float3(d.x, d.y, d.z);
+        const float3 p = make_float3(a.type_pos[3 * (size_t)(o + i)], a.type_pos[3 * (size_t)(o + i) + 1],
+                                     a.type_pos[3 * (size_t)(o + i) + 2]);
+        const float3 nr = make_float3(a.type_nrm[3 * (size_t)(o + i)], a.type_nrm[3 * (size_t)(o + i) + 1],
+                                      a.type_nrm[3 * (size_t)(o + i) + 2]);
+        const NodePoseGrad pg =
+            node_pose_grad(spo, a.K, p, nr, du, Rp, pp, a.obj_pose + 7 * (size_t)env * a.K);
+        pen = pg.pen;
+#pragma unroll
+        for (int k = 0; k < MAX_K; ++k) {
+          if (k != pg.k) continue;
+#pragma unroll
+          for (int q = 0; q < 3; ++q) {
+            pose[k][q] += pg.t[q];
+            pose[k][3 + q] += pg.w[q];
+          }
+        }
+      }
+      if (a.grad_uhat) {
+        float* g = a.grad_uhat + 3 * (base + i);
+        g[0] = du.x;
+        g[1] = du.y;
+        g[2] = du.z;
+      }
+      if (a.grad_pen) a.grad_pen[base + i] = pen;
+    }
+    for (int k = 0; k < a.K; ++k)
+#pragma unroll
+      for (int q = 0; q < 6; ++q) {
+        float v = 0.f;
+#pragma unroll
+        for (int kk = 0; kk < MAX_K; ++kk)
+          if (kk == k) v = pose[kk][q];
+#pragma unroll
+        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(FULL, v, sh);
+        if (lane == 0) a.pose_part[((size_t)pad * a.K + k) * 6 + q] = v;
+      }
+    __syncwarp();
+  }
+}
+
+// ----------------------------------------------------------------------------- final sums
+// grad_params[q]: the sums of every stage's partials that cover q, each in partial order
+__global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
+  const int q = blockIdx.x * blockDim.x + threadIdx.x;
+  if (q >= NPARAM) return;
+  float s = 0.f;
+  if (q >= OFF_W1 && q < OFF_B2 + H)
+    for (int w = 0; w < a.r4_parts; ++w) s += a.r4part[(size_t)w * R4_LEN + q - OFF_W1];
+  if (q >= OFF_W1 && q < OFF_W4)
+    for (int b = 0; b < a.r5_parts; ++b) s += a.r5part[(size_t)b * R5_LEN + q - OFF_W1];
+  if (q >= OFF_WG && q < OFF_W4)
+    for (int b = 0; b < a.r4b_parts; ++b) s += a.r4bpart[(size_t)b * R4B_LEN + q - OFF_WG];
+  if (q >= OFF_W4 && q < OFF_W4 + 3 * H)
+    for (int b = 0; b < a.r3_parts; ++b) s += a.d2part[(size_t)b * 3 * H + q - OFF_W4];
+  if (q >= OFF_B4 && q < OFF_B4 + 3)
+    for (int p = 0; p < a.num_items; ++p) s += a.pr[(size_t)p * PR_STRIDE + PR_GSUM + q - OFF_B4];
+  if (q == OFF_ALPHA)
+    for (int b = 0; b < a.alpha_parts; ++b) s -= a.alpha_part[b];
+  out[q] = s;
+}
+
+}  // namespace
+
+size_t bwd_pad_smem_bytes(int nmax, int K) { return R1Smem(nmax, K).total; }
+
+cudaError_t launch_backward_batched(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
+                                    cudaStream_t s) {
+  cudaError_t e;
+  {
+    const size_t smem = R1Smem(a.nmax, a.K).total;
+    static size_t configured = 0;
+    if (smem > configured) {
+      e = cudaFuncSetAttribute(bwd_pad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)smem);
+      if (e != cudaSuccess) return e;
+      configured = smem;
+    }
+    bwd_pad_kernel<<<l.r1_grid, RT, smem, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  if (a.mode != MODE_LINEAR_ONLY) {
+    bwd_global_kernel<<<l.r2_grid, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bwd_decoder_kernel<<<a.r3_parts, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const long long tot = (long long)a.total_nodes * H;
+    bwd_reduce_a3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    static bool c4 = false;
+    if (!c4) {
+      e = cudaFuncSetAttribute(bwd_padrev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)R4_SMEM);
+      if (e != cudaSuccess) return e;
+      c4 = true;
+    }
+    bwd_padrev_kernel<<<a.r4_parts / R4_WARPS, R4_WARPS * 32, R4_SMEM, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    bwd_padsum_kernel<<<a.r4b_parts, 256, 0, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const size_t s5 = sizeof(float) * (8 * 64 * TLD + 64 * 6);
+    static bool c5 = false;
+    if (!c5) {
+      e = cudaFuncSetAttribute(bwd_typenode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                               (int)s5);
+      if (e != cudaSuccess) return e;
+      c5 = true;
+    }
+    bwd_typenode_kernel<<<a.r5_parts, 256, s5, s>>>(a);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+cudaError_t launch_backward_batched_tail(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
+                                         float* grad_params, cudaStream_t s) {
+  cudaError_t e;
+  bwd_pose_kernel<<<l.r7_grid, 256, sizeof(PadObj) * 8 * a.K, s>>>(a);
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  if (grad_params) {
+    bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+}  // namespace etac

@@ -1,0 +1,109 @@
+// bwd_common.cuh -- pieces shared by the two reverse-mode implementations (per-pad kernel of
+// the plain algorithm, staged pipeline of the batched algorithms): a register-tiled FP32
+// 64 x 64 x 64 product over staged tiles, and the reverse of one active node's contact
+// displacement u_hat = -phi n through its primitive's SDF (ETac Sec. III-A) to the
+// penetration and the object pose.
+#pragma once
+#include "etac_common.cuh"
+
+namespace etac {
+
+constexpr int TLD = H + 4;   // padded row stride of staged 64 x 64 tiles (16-byte aligned)
+
+// acc[i][j] += sum_k A[k][4 ti + i] * B[k][4 tj + j], both operands k-major with stride TLD
+__device__ __forceinline__ void tile_acc(const float* A, const float* B, int ti, int tj,
+                                         float (&acc)[4][4]) {
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(A + k * TLD + 4 * ti);
+    const float4 b = *reinterpret_cast<const float4*>(B + k * TLD + 4 * tj);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
+// Reverse of u_hat = -phi n for one active node (p, nrm) of a pad: du = dL/du_hat in the pad
+// frame.  Returns the object slot, dL/d(penetration) = n . du (n the outward normal, pad
+// frame), and the object's pose gradient: translation t and the world-frame rotation
+// increment w applied on the left about the object origin.  Rp is the pad's rotation, pp its
+// pose, op_env the env's object poses (K x 7).
+struct NodePoseGrad {
+  int k;
+  float pen;
+  float t[3], w[3];
+};
+
+__device__ inline NodePoseGrad node_pose_grad(const PadObj* spo, int K, float3 p, float3 nr,
+                                              float3 du, const float (&Rp)[3][3],
+                                              const float* pp, const float* op_env) {
+  NodePoseGrad out;
+  SdfIn sd;
+  const NodeContact c = contact_node(spo, K, p, nr, &sd);
+  out.k = c.k;
+  const PadObj& po = spo[c.k];
+  // outward normal in the pad frame: R_rel^T g
+  const float npx = po.R[0] * sd.g[0] + po.R[3] * sd.g[1] + po.R[6] * sd.g[2];
+  const float npy = po.R[1] * sd.g[0] + po.R[4] * sd.g[1] + po.R[7] * sd.g[2];
+  const float npz = po.R[2] * sd.g[0] + po.R[5] * sd.g[1] + po.R[8] * sd.g[2];
+  out.pen = npx * du.x + npy * du.y + npz * du.z;
+  // v = R_pad du (world); vo = R_k^T v (object frame)
+  const float* op = op_env + 7 * c.k;
+  float Rk[3][3];
+  quat_to_mat<float>(op + 3, Rk);
+  float v[3], vo[3], gw[3];
+  for (int q = 0; q < 3; ++q) v[q] = Rp[q][0] * du.x + Rp[q][1] * du.y + Rp[q][2] * du.z;
+  for (int q = 0; q < 3; ++q) vo[q] = Rk[0][q] * v[0] + Rk[1][q] * v[1] + Rk[2][q] * v[2];
+  for (int q = 0; q < 3; ++q) gw[q] = Rk[q][0] * sd.g[0] + Rk[q][1] * sd.g[1] + Rk[q][2] * sd.g[2];
+  // A v = g (g . vo) + phi H vo, object frame
+  const float phi = c.phi;
+  const float gv = sd.g[0] * vo[0] + sd.g[1] * vo[1] + sd.g[2] * vo[2];
+  float Av[3] = {sd.g[0] * gv, sd.g[1] * gv, sd.g[2] * gv};
+  if (!sd.deg && sd.hk != 0) {
+    float Hv[3];
+    if (sd.hk == 1) {
+      // spherical: (P - g g^T) vo / L, P = I except on a capsule's side (z row dropped)
+      float L;
+      bool side = false;
+      if (po.type == OBJ_CAPSULE) {
+        const float h = po.dims[1];
+        const float qz = sd.qf[2];
+        side = qz > -h && qz < h;
+        const float cz = qz < -h ? -h : (qz > h ? h : qz);
+        const float vz = qz - cz;
+        L = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1] + vz * vz);
+      } else {
+        L = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1] + sd.qf[2] * sd.qf[2]);
+      }
+      Hv[0] = (vo[0] - sd.g[0] * gv) / L;
+      Hv[1] = (vo[1] - sd.g[1] * gv) / L;
+      Hv[2] = ((side ? 0.f : vo[2]) - sd.g[2] * gv) / L;
+    } else {
+      // radial about the z axis: (I_xy - g g^T) vo / rho
+      const float rho = sqrtf(sd.qf[0] * sd.qf[0] + sd.qf[1] * sd.qf[1]);
+      Hv[0] = (vo[0] - sd.g[0] * gv) / rho;
+      Hv[1] = (vo[1] - sd.g[1] * gv) / rho;
+      Hv[2] = 0.f;
+    }
+    for (int q = 0; q < 3; ++q) Av[q] = fmaf(phi, Hv[q], Av[q]);
+  }
+  float sw[3];
+  for (int q = 0; q < 3; ++q) sw[q] = Rk[q][0] * Av[0] + Rk[q][1] * Av[1] + Rk[q][2] * Av[2];
+  // r = x - t_k, x = R_pad p + t_pad (world)
+  float r[3];
+  for (int q = 0; q < 3; ++q)
+    r[q] = Rp[q][0] * p.x + Rp[q][1] * p.y + Rp[q][2] * p.z + pp[q] - op[q];
+  const float c1[3] = {r[1] * sw[2] - r[2] * sw[1], r[2] * sw[0] - r[0] * sw[2],
+                       r[0] * sw[1] - r[1] * sw[0]};
+  const float c2[3] = {gw[1] * v[2] - gw[2] * v[1], gw[2] * v[0] - gw[0] * v[2],
+                       gw[0] * v[1] - gw[1] * v[0]};
+  for (int q = 0; q < 3; ++q) {
+    out.t[q] = sw[q];
+    out.w[q] = c1[q] - phi * c2[q];
+  }
+  return out;
+}
+
+}  // namespace etac

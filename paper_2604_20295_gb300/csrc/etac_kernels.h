@@ -57,6 +57,12 @@ struct TablesArgs {
   void* omega_bf16;             // [sum n^2] BF16 (optional)
   void* h0bf16;                 // [sum n][64] BF16 copy of h0 (optional)
   float2* ranked;               // [64 * sum n] (f0 value, node as int bits) in rank order (optional)
+  // reverse mode of the batched algorithms (optional): Omega and d * Omega split into BF16
+  // hi and lo parts
+  void* om_hi;
+  void* om_lo;
+  void* dom_hi;
+  void* dom_lo;
 };
 cudaError_t launch_tables(const TablesArgs& a, int nmax, cudaStream_t s);
 
@@ -156,6 +162,10 @@ struct GemmTile {
 struct GemmParams {
   CUtensorMap tmA[GEMM_MAX_TYPES];   // Omega_t BF16 [n_t][n_t], box 64 x 128, 128B swizzle
   CUtensorMap tmB[GEMM_MAX_TYPES];   // B_t BF16 [3 I_t][n_t], box 64 x 192, 128B swizzle
+  // reverse modes only: the low BF16 parts (A: Omega_t or d * Omega_t, B: dL/dU of passive
+  // nodes); the K loop runs the segments (A hi, B hi), (A hi, B lo), (A lo, B hi)
+  CUtensorMap tmA2[GEMM_MAX_TYPES];
+  CUtensorMap tmB2[GEMM_MAX_TYPES];
   const GemmTile* tiles;
   int num_tiles;
   const int* type_off;               // [T+1]
@@ -173,9 +183,15 @@ struct GemmParams {
   int use_l, use_r;
   int* status;
   unsigned long long timeout_ns;
+  // reverse modes
+  const int* inst_m;                 // [sum I_t] active count by instance
+  const float4* ws_u;                // [N] (u_hat, phi) of active nodes
+  float4* ws_du;                     // [N] dL/du_hat of active nodes (accumulated into)
+  float* alpha_part;                 // [grid] per-CTA sums of u_hat . (d Omega G)
 };
 
-cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s);
+enum { GEMM_FWD = 0, GEMM_BWD_U = 1, GEMM_BWD_ALPHA = 2 };
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode = GEMM_FWD);
 size_t prop_gemm_smem_bytes();
 
 }  // namespace etac
@@ -218,5 +234,80 @@ size_t backward_smem_bytes(int nmax, int K);
 cudaError_t launch_backward(const BackwardArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_pose_grad_to_quat(const float* poses, const float* tw, float* out,
                                      long long count, cudaStream_t s);
+cudaError_t launch_reduce_pose(const float* part, int E, int P, int K, float* out, cudaStream_t s);
+
+// ---------------------------------------------------------------- batched reverse mode (FP32)
+// per-pad records of the staged reverse mode (floats; PR_ROUTE holds int bits)
+constexpr int PR_G0 = 0, PR_AG = 64, PR_G = 128, PR_BETA = 192, PR_S = 256, PR_DAG = 320,
+              PR_ROUTE = 384, PR_GSUM = 448, PR_STRIDE = 452;
+
+struct R3Group {
+  int type, k0;        // pad type, first instance of the 64-instance group
+  long long a3off;     // float offset of the group's A3 partial block [n_t][64]
+};
+
+struct BwdBatchedArgs {
+  const float* type_pos;
+  const float* type_nrm;
+  const int* type_off;
+  const int* pad_type;
+  const long long* pad_off;
+  const int* item_pad;
+  int num_items, P, K, nmax, total_nodes;
+  const float* pad_pose;
+  const float* obj_pose;
+  const float* params;
+  const float* ctab;
+  const float* f0tab;
+  const float* h0tab;
+  const float2* ranked;
+  const PadObj* padobj;
+  const int* pad_bad;
+  const int* pad_inst;
+  const int* inst_off;
+  const int* inst_pad;
+  const int* pad_gi;
+  const long long* inst_base;
+  const long long* type_woff;
+  const long long* mask_woff;
+  uint32_t* maskbits;
+  const long long* bg_off;     // [T] element offset of each type's [3 I_t][n_t] block
+  void* bg_hi;                 // passive dL/dU, BF16 hi part, propagation-reverse B operand
+  void* bg_lo;                 // the BF16 remainders
+  int mode;
+  const float* grad_disp;
+  float* grad_uhat;
+  float* grad_pen;
+  float4* ws_u;                // [N] (u_hat, phi) of active nodes
+  float4* ws_du;               // [N] dL/du_hat of active nodes
+  float* pr;                   // [E*P][PR_STRIDE]
+  int* pad_m;
+  int* inst_m;                 // [sum I_t] active count by instance
+  const R3Group* r3_groups;
+  int r3_parts;
+  float* a3part;
+  const long long* a3_toff;    // [T] float offset of type t's first group block
+  const int* a3_tgroups;       // [T] groups of type t
+  float* a3;                   // [sum n][64]
+  float* d2part;               // [r3_parts][3 * 64]
+  float* r4part;
+  int r4_parts;
+  float* r4bpart;
+  int r4b_parts;
+  float* r5part;
+  int r5_parts;
+  float* alpha_part;
+  int alpha_parts;
+  float* pose_part;
+  int* ticket;
+};
+struct BwdBatchedLaunch {
+  int r1_grid, r2_grid, r7_grid;
+};
+size_t bwd_pad_smem_bytes(int nmax, int K);
+cudaError_t launch_backward_batched(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
+                                    cudaStream_t s);
+cudaError_t launch_backward_batched_tail(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
+                                         float* grad_params, cudaStream_t s);
 
 }  // namespace etac

@@ -72,7 +72,14 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   return *reinterpret_cast<uint32_t*>(&v);
 }
 
+// MODE GEMM_FWD: the forward step above.  The reverse modes contract the same Omega_t-shaped
+// tables with the passive nodes' dL/dU (B operand, split BF16 hi / lo, three K segments for
+// FP32-level accuracy): GEMM_BWD_U adds sum_i Omega_ij G_i to dL/du_hat of every active node j;
+// GEMM_BWD_ALPHA accumulates sum_j u_hat_j . sum_i d_ij Omega_ij G_i into per-CTA partials
+// (dL/dalpha is minus their sum).
+template <int MODE>
 __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_constant__ GemmParams p) {
+  constexpr int SEG = MODE == GEMM_FWD ? 1 : 3;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -106,6 +113,10 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     for (int t = 0; t < GEMM_MAX_TYPES; ++t) {
       prefetch_tmap(&p.tmA[t]);
       prefetch_tmap(&p.tmB[t]);
+      if (MODE != GEMM_FWD) {
+        prefetch_tmap(&p.tmA2[t]);
+        prefetch_tmap(&p.tmB2[t]);
+      }
     }
   }
   if (warp == MMA_WARP) {
@@ -126,16 +137,17 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       int issued = 0;
       for (int tile = blockIdx.x; tile < p.num_tiles && !*s_abort; tile += gridDim.x) {
         const GemmTile T = p.tiles[tile];
-        for (int kb = 0; kb < T.nkb; ++kb) {
+        for (int kb = 0; kb < SEG * T.nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, s_abort, limit)) {
             *s_abort = 1;
             break;
           }
+          const int seg = kb / T.nkb, kk = kb - seg * T.nkb;
+          const CUtensorMap* ta = seg == 2 ? &p.tmA2[T.type] : &p.tmA[T.type];
+          const CUtensorMap* tb = seg == 1 ? &p.tmB2[T.type] : &p.tmB[T.type];
           mbar_expect_tx(&full[stage], A_BYTES + B_BYTES);
-          tma_load_2d(smem + SM_A + (size_t)stage * A_BYTES, &p.tmA[T.type], kb * GK, T.m0,
-                      &full[stage]);
-          tma_load_2d(smem + SM_B + (size_t)stage * B_BYTES, &p.tmB[T.type], kb * GK, 3 * T.k0,
-                      &full[stage]);
+          tma_load_2d(smem + SM_A + (size_t)stage * A_BYTES, ta, kk * GK, T.m0, &full[stage]);
+          tma_load_2d(smem + SM_B + (size_t)stage * B_BYTES, tb, kk * GK, 3 * T.k0, &full[stage]);
           ++issued;
           if (++stage == STAGES) {
             stage = 0;
@@ -174,7 +186,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
         tc_fence_after();
         const uint32_t d_tmem = tmem + (uint32_t)b * ACC_STRIDE;
         bool ok = true;
-        for (int kb = 0; kb < T.nkb; ++kb) {
+        for (int kb = 0; kb < SEG * T.nkb; ++kb) {
           if (!mbar_wait(&full[stage], phase, s_abort, limit)) {
             ok = false;
             break;
@@ -229,7 +241,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       const int ninst = p.inst_off[t + 1] - p.inst_off[t];
       const int gi0 = p.inst_off[t] + T.k0;
       const uint32_t s0 = smem_u32(sb);
-      for (int idx = etid; idx < GI * 8; idx += EPI_WARPS * 32) {
+      for (int idx = etid; MODE == GEMM_FWD && idx < GI * 8; idx += EPI_WARPS * 32) {
         const int inst = idx >> 3, ch = idx & 7;
         const bool ok = T.k0 + inst < ninst;
         cp_async16(s0 + (uint32_t)(STG_NB + 16 * idx),
@@ -239,7 +251,8 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       for (int idx = etid; idx < GI; idx += EPI_WARPS * 32) {
         const bool ok = T.k0 + idx < ninst;
         const int g = gi0 + (ok ? idx : 0);
-        cp_async16(s0 + (uint32_t)(STG_C0 + 16 * idx), p.c0m + g, ok ? 16u : 0u);
+        if (MODE == GEMM_FWD) cp_async16(s0 + (uint32_t)(STG_C0 + 16 * idx), p.c0m + g, ok ? 16u : 0u);
+        else cp_async4(s0 + (uint32_t)(STG_C0 + 16 * idx), p.inst_m + g, ok ? 4u : 0u);
         cp_async8(s0 + (uint32_t)(STG_BASE + 8 * idx), p.inst_base + g, ok ? 8u : 0u);
       }
       for (int idx = etid; idx < GI * 4; idx += EPI_WARPS * 32) {
@@ -248,7 +261,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
         const long long off = ok ? p.type_woff[t] + (long long)(T.k0 + inst) * nw + w : 0;
         cp_async4(s0 + (uint32_t)(STG_BITS + 4 * idx), p.maskbits + off, ok ? 4u : 0u);
       }
-      for (int idx = etid; idx < GM * 8; idx += EPI_WARPS * 32) {
+      for (int idx = etid; MODE == GEMM_FWD && idx < GM * 8; idx += EPI_WARPS * 32) {
         const int r = idx >> 3, ch = idx & 7, row = T.m0 + r;
         const bool ok = row < n_t;
         cp_async16(s0 + (uint32_t)(STG_H0 + 128 * r + ((ch ^ (r & 7)) << 4)),
@@ -258,6 +271,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       cp_async_commit();
     };
     if ((int)blockIdx.x < p.num_tiles) stage(p.tiles[blockIdx.x], smem + SM_STG);
+    float alpha_acc = 0.f;   // GEMM_BWD_ALPHA: this thread's sum, tiles in order
     int local = 0;
     for (int tile = blockIdx.x; tile < p.num_tiles; tile += gridDim.x, ++local) {
       const GemmTile T = p.tiles[tile];
@@ -281,7 +295,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
 #pragma unroll
       for (int rg = 0; rg < 2; ++rg)
 #pragma unroll
-        for (int e2 = 0; e2 < 2; ++e2) {
+        for (int e2 = 0; e2 < 2 && MODE == GEMM_FWD; ++e2) {
           const int r = 32 * q + 16 * rg + grp + 8 * e2;
           const unsigned char* hr = sb + STG_H0 + 128 * r + 4 * tig;
 #pragma unroll
@@ -316,6 +330,30 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
           for (int x = 0; x < 8; ++x) lv4[x] = r8[x];
 #pragma unroll
           for (int x = 0; x < 4; ++x) lv4[8 + x] = r4[x];
+        }
+        if constexpr (MODE != GEMM_FWD) {
+          // reverse modes: active rows of instances with contact
+#pragma unroll
+          for (int x = 0; x < 4; ++x) {
+            const int inst = inst4 + x;
+            const int m = *reinterpret_cast<const int*>(s_c0 + inst);
+            const bool act = ((s_bits[inst * 4 + q] >> lane) & 1u) != 0u;
+            if (!(row_ok && act && m > 0)) continue;
+            const float l0 = __uint_as_float(lv4[3 * x]), l1 = __uint_as_float(lv4[3 * x + 1]),
+                        l2 = __uint_as_float(lv4[3 * x + 2]);
+            const long long node = s_base[inst] + i;
+            if constexpr (MODE == GEMM_BWD_U) {
+              float4 d = p.ws_du[node];
+              d.x += l0;
+              d.y += l1;
+              d.z += l2;
+              p.ws_du[node] = d;
+            } else {
+              const float4 u = p.ws_u[node];
+              alpha_acc = fmaf(u.x, l0, fmaf(u.y, l1, fmaf(u.z, l2, alpha_acc)));
+            }
+          }
+          continue;
         }
 #pragma unroll
       for (int sub = 0; sub < 4 / DEC; ++sub) {
@@ -403,6 +441,19 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       if (lane == 0) mbar_arrive(&acc_empty[b]);
     }
     cp_async_wait_all();   // no copy may still target shared memory when the CTA ends
+    if constexpr (MODE == GEMM_BWD_ALPHA) {
+      // fixed-order reduction of the epilogue threads' sums: lanes, then warps in order
+      float* red = reinterpret_cast<float*>(smem + SM_R);
+#pragma unroll
+      for (int sh = 16; sh > 0; sh >>= 1) alpha_acc += __shfl_xor_sync(0xffffffffu, alpha_acc, sh);
+      if (lane == 0) red[warp] = alpha_acc;
+      named_bar_sync(1, EPI_WARPS * 32);
+      if (threadIdx.x == 0) {
+        float t = 0.f;
+        for (int w = 0; w < EPI_WARPS; ++w) t += red[w];
+        p.alpha_part[blockIdx.x] = t;
+      }
+    }
   }
 
   __syncthreads();
@@ -417,17 +468,24 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
 
 size_t prop_gemm_smem_bytes() { return SM_ALLOC; }
 
-cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s) {
+template <int MODE>
+cudaError_t launch_mode(const GemmParams& p, int grid, cudaStream_t s) {
   static bool configured = false;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(prop_gemm_kernel,
+    cudaError_t e = cudaFuncSetAttribute(prop_gemm_kernel<MODE>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)SM_ALLOC);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  prop_gemm_kernel<<<grid, THREADS, SM_ALLOC, s>>>(p);
+  prop_gemm_kernel<MODE><<<grid, THREADS, SM_ALLOC, s>>>(p);
   return cudaGetLastError();
+}
+
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode) {
+  if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U>(p, grid, s);
+  if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA>(p, grid, s);
+  return launch_mode<GEMM_FWD>(p, grid, s);
 }
 
 }  // namespace etac

@@ -85,9 +85,19 @@ __global__ void __launch_bounds__(256) tables_omega_kernel(TablesArgs a) {
     const float* pj = a.type_pos + 3 * (size_t)(o + j);
     const float* pi = a.type_pos + 3 * (size_t)(o + i);
     const float dx = pj[0] - pi[0], dy = pj[1] - pi[1], dz = pj[2] - pi[2];
-    const float w = expf(-alpha * sqrtf(dx * dx + dy * dy + dz * dz));
+    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float w = expf(-alpha * d);
     if (a.omega) a.omega[idx] = w;
     if (a.omega_bf16) reinterpret_cast<__nv_bfloat16*>(a.omega_bf16)[idx] = __float2bfloat16_rn(w);
+    if (a.om_hi) {
+      const __nv_bfloat16 h = __float2bfloat16_rn(w);
+      reinterpret_cast<__nv_bfloat16*>(a.om_hi)[idx] = h;
+      reinterpret_cast<__nv_bfloat16*>(a.om_lo)[idx] = __float2bfloat16_rn(w - __bfloat162float(h));
+      const float dw = d * w;
+      const __nv_bfloat16 dh = __float2bfloat16_rn(dw);
+      reinterpret_cast<__nv_bfloat16*>(a.dom_hi)[idx] = dh;
+      reinterpret_cast<__nv_bfloat16*>(a.dom_lo)[idx] = __float2bfloat16_rn(dw - __bfloat162float(dh));
+    }
   }
 }
 
@@ -98,7 +108,7 @@ cudaError_t launch_tables(const TablesArgs& a, int nmax, cudaStream_t s) {
   tables_order_kernel<<<dim3(a.num_types, H), 256, sizeof(float) * nmax, s>>>(a);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  if (a.omega || a.omega_bf16) {
+  if (a.omega || a.omega_bf16 || a.om_hi) {
     tables_omega_kernel<<<1024, 256, 0, s>>>(a);
     e = cudaGetLastError();
   }
