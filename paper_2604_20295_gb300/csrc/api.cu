@@ -102,6 +102,10 @@ struct etac_ctx {
   float* d_r4bpart = nullptr;
   float* d_r5part = nullptr;
   float* d_alpha_part = nullptr;
+  float* d_gsum_part = nullptr;
+  float* d_spart = nullptr;
+  long long* d_s_toff = nullptr;
+  int* d_s_nr = nullptr;
   int r3_parts = 0, r4_parts = 0, r4b_parts = 0, r5_parts = 0, alpha_parts = 0;
   etac::GemmParams gemm_bu{}, gemm_ba{};
   // profiling: event pairs around kernel launches
@@ -121,9 +125,14 @@ struct etac_ctx {
 namespace {
 const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
                               "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel",
-                              "backward_kernel", "pad_obj_kernel"};
+                              "backward_kernel", "pad_obj_kernel", "bwd_pad_kernel",
+                              "bwd_global_kernel", "bwd_decoder_kernel(+a3 sums)",
+                              "bwd_padrev_kernel(+pad sums)", "bwd_typenode_kernel",
+                              "prop_gemm_kernel<bwd_u>", "prop_gemm_kernel<bwd_alpha>",
+                              "bwd_pose_kernel(+param sums)"};
 enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_PADOBJ = 6,
-       K_COUNT = 7 };
+       K_BWD_PAD = 7, K_BWD_GLOBAL = 8, K_BWD_DECODER = 9, K_BWD_PADREV = 10, K_BWD_TYPENODE = 11,
+       K_BWD_GEMM_U = 12, K_BWD_GEMM_A = 13, K_BWD_POSE = 14, K_COUNT = 15 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -186,7 +195,8 @@ void free_ctx(etac_ctx* c) {
                   c->d_type_woff, c->d_om_hi, c->d_om_lo, c->d_dom_hi, c->d_dom_lo,
                   c->d_bg_hi, c->d_bg_lo, c->d_pr, c->d_inst_m, c->d_r3g, c->d_a3part,
                   c->d_a3_toff, c->d_a3_tg, c->d_a3, c->d_d2part, c->d_r4part, c->d_r4bpart,
-                  c->d_r5part, c->d_alpha_part, c->d_ws_idx, c->d_ws_u,
+                  c->d_r5part, c->d_alpha_part, c->d_gsum_part, c->d_spart, c->d_s_toff,
+                  c->d_s_nr, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part};
   for (void* p : ptrs)
     if (p) cudaFree(p);
@@ -404,11 +414,30 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
     a3_tg[t] = (c->ninst_h[t] + 63) / 64;
     a3tot += (long long)a3_tg[t] * c->type_n[t] * etac::H;
   }
+  // node range per work unit: 256 nodes, halved (down to 16) until there are at least four
+  // units per SM
+  int range = etac::R3_RANGE;
+  auto units = [&](int rg) {
+    long long u = 0;
+    for (int t = 0; t < c->T; ++t) u += (long long)a3_tg[t] * ((c->type_n[t] + rg - 1) / rg);
+    return u;
+  };
+  while (range > 16 && units(range) < 4LL * c->num_sms) range /= 2;
+  std::vector<long long> s_toff(c->T, 0);
+  std::vector<int> s_nr(c->T, 0);
+  long long stot = 0;
+  for (int t = 0; t < c->T; ++t) {
+    s_toff[t] = stot;
+    s_nr[t] = (c->type_n[t] + range - 1) / range;
+    stot += (long long)s_nr[t] * c->ninst_h[t];
+  }
   for (int t = 0; t < c->T; ++t)
     for (int g = 0; g < a3_tg[t]; ++g)
-      groups.push_back({t, 64 * g, a3_toff[t] + (long long)g * c->type_n[t] * etac::H});
-  std::stable_sort(groups.begin(), groups.end(), [&](const etac::R3Group& x, const etac::R3Group& y) {
-    return c->type_n[x.type] > c->type_n[y.type];
+      for (int r = 0; r < s_nr[t]; ++r)
+        groups.push_back({t, 64 * g, r * range, std::min(c->type_n[t], (r + 1) * range), r,
+                          a3_toff[t] + (long long)g * c->type_n[t] * etac::H});
+  std::stable_sort(groups.begin(), groups.end(), [](const etac::R3Group& x, const etac::R3Group& y) {
+    return x.i1 - x.i0 > y.i1 - y.i0;   // largest units first
   });
   c->r3_parts = (int)groups.size();
   c->r4_parts = 4 * 2 * c->num_sms;                     // warps of the R4 grid
@@ -428,11 +457,19 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_a3_toff, (size_t)c->T);
   if (e == cudaSuccess) e = dalloc(&c->d_a3_tg, (size_t)c->T);
   if (e == cudaSuccess) e = dalloc(&c->d_a3, tn * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_spart, (size_t)stot * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_s_toff, (size_t)c->T);
+  if (e == cudaSuccess) e = dalloc(&c->d_s_nr, (size_t)c->T);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_toff, s_toff.data(), sizeof(long long) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_nr, s_nr.data(), sizeof(int) * c->T,
+                                            cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = dalloc(&c->d_d2part, (size_t)c->r3_parts * 3 * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_r4part, (size_t)c->r4_parts * (etac::OFF_B2 + etac::H - etac::OFF_W1));
   if (e == cudaSuccess) e = dalloc(&c->d_r4bpart, (size_t)c->r4b_parts * (etac::OFF_W4 - etac::OFF_WG));
   if (e == cudaSuccess) e = dalloc(&c->d_r5part, (size_t)c->r5_parts * (etac::OFF_W4 - etac::OFF_W1));
   if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->alpha_parts);
+  if (e == cudaSuccess) e = dalloc(&c->d_gsum_part, (size_t)c->r4b_parts * 3);
   if (e == cudaSuccess && !groups.empty())
     e = cudaMemcpyAsync(c->d_r3g, groups.data(), sizeof(etac::R3Group) * groups.size(),
                         cudaMemcpyHostToDevice, s);
@@ -490,7 +527,8 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     etac_status st = setup_bf16(c, s);
     if (st != ETAC_OK) return st;
   }
-  const bool needb = batched && tensor_core_shapes_ok(c);   // staged reverse mode
+  // staged reverse mode (32-bit node offsets inside its kernels; otherwise the per-pad kernel)
+  const bool needb = batched && tensor_core_shapes_ok(c) && 3 * c->N < (1LL << 31);
   if (needb) {
     etac_status st = setup_bwdb(c, s);
     if (st != ETAC_OK) return st;
@@ -547,8 +585,9 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   f.pad_pose = c->d_saved_pad_pose;
   f.padobj = c->d_padobj;
   f.pad_bad = c->d_pad_bad;
-  const int ts = timing_begin(c, K_BWD, s);
+  int ts = timing_begin(c, K_PADOBJ, s);
   ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
+  timing_end(c, ts, s);
   ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
   etac::BwdBatchedArgs b{};
   b.type_pos = c->d_type_pos;
@@ -597,11 +636,15 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   b.a3_toff = c->d_a3_toff;
   b.a3_tgroups = c->d_a3_tg;
   b.a3 = c->d_a3;
+  b.spart = c->d_spart;
+  b.s_toff = c->d_s_toff;
+  b.s_nr = c->d_s_nr;
   b.d2part = c->d_d2part;
   b.r4part = c->d_r4part;
   b.r4_parts = c->r4_parts;
   b.r4bpart = c->d_r4bpart;
   b.r4b_parts = c->r4b_parts;
+  b.gsum_part = c->d_gsum_part;
   b.r5part = c->d_r5part;
   b.r5_parts = c->r5_parts;
   b.alpha_part = c->d_alpha_part;
@@ -614,7 +657,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   {
     const void* need[] = {b.ws_u, b.ws_du, b.pr, b.pad_m, b.inst_m, b.padobj, b.pad_bad,
                           b.maskbits, b.mask_woff, b.bg_hi, b.bg_lo, b.r3_groups, b.a3part,
-                          b.a3, b.d2part, b.r4part, b.r4bpart, b.r5part, b.alpha_part,
+                          b.a3, b.d2part, b.r4part, b.r4bpart, b.r5part, b.alpha_part, b.gsum_part, b.spart, b.s_toff, b.s_nr,
                           b.pose_part, b.ranked, b.h0tab, b.ctab, b.f0tab};
     for (const void* q : need)
       if (!q) return fail(c, ETAC_ERR_STATE, "reverse-mode buffers are not set up");
@@ -623,7 +666,21 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   l.r1_grid = 2 * c->num_sms;
   l.r2_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
   l.r7_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
-  ETAC_CUDA(c, etac::launch_backward_batched(b, l, s), "reverse mode: pad stages");
+  auto stage = [&](int st, int slot, const char* what) -> etac_status {
+    const int t0 = timing_begin(c, slot, s);
+    ETAC_CUDA(c, etac::launch_backward_stage(b, l, st, grad_params, s), what);
+    timing_end(c, t0, s);
+    return ETAC_OK;
+  };
+  etac_status st = stage(etac::BWD_STAGE_PAD, K_BWD_PAD, "reverse mode: pad stage");
+  if (st != ETAC_OK) return st;
+  if (c->model.mode != ETAC_MODE_LINEAR_ONLY) {
+    if ((st = stage(etac::BWD_STAGE_GLOBAL, K_BWD_GLOBAL, "reverse mode: global MLP")) != ETAC_OK ||
+        (st = stage(etac::BWD_STAGE_DECODER, K_BWD_DECODER, "reverse mode: decoder")) != ETAC_OK ||
+        (st = stage(etac::BWD_STAGE_PADREV, K_BWD_PADREV, "reverse mode: pad reverse")) != ETAC_OK ||
+        (st = stage(etac::BWD_STAGE_TYPENODE, K_BWD_TYPENODE, "reverse mode: type nodes")) != ETAC_OK)
+      return st;
+  }
   if (use_l) {
     for (etac::GemmParams* g : {&c->gemm_bu, &c->gemm_ba}) {
       g->ws_u = c->d_ws_u;
@@ -631,16 +688,21 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
       if (!g->ws_u || !g->ws_du || !g->inst_m || !g->alpha_part || !g->tiles)
         return fail(c, ETAC_ERR_STATE, "reverse-mode GEMM buffers are not set up");
     }
+    int t0 = timing_begin(c, K_BWD_GEMM_U, s);
     ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U),
               "reverse mode: propagation GEMM");
+    timing_end(c, t0, s);
+    t0 = timing_begin(c, K_BWD_GEMM_A, s);
     ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA),
               "reverse mode: alpha GEMM");
+    timing_end(c, t0, s);
   }
-  ETAC_CUDA(c, etac::launch_backward_batched_tail(b, l, grad_params, s), "reverse mode: outputs");
+  if ((st = stage(etac::BWD_STAGE_POSE, K_BWD_POSE, "reverse mode: outputs")) != ETAC_OK ||
+      (st = stage(etac::BWD_STAGE_PARAMS, K_BWD_POSE, "reverse mode: parameter sums")) != ETAC_OK)
+    return st;
   if (grad_obj_pose)
     ETAC_CUDA(c, etac::launch_reduce_pose(c->d_pose_part, c->E, c->P, c->K, grad_obj_pose, s),
               "reverse mode: pose sums");
-  timing_end(c, ts, s);
   return ETAC_OK;
 }
 

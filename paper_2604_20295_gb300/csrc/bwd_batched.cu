@@ -522,16 +522,28 @@ __global__ void __launch_bounds__(256) bwd_global_kernel(BwdBatchedArgs a) {
 }
 
 // ----------------------------------------------------------------------------- R3
-// CTA = (pad type, 64 instances); warp w takes instances 8 w .. 8 w + 7 of the group and all
-// the type's nodes, eight at a time in lock step with the other warps; lane l owns channels
-// 2 l and 2 l + 1.
+// CTA = (pad type, 64 instances, a range of up to 256 nodes); warp w takes instances
+// 8 w .. 8 w + 7; the CTA walks its nodes 16 at a time, node-outer / instance-inner, so the
+// running A3 of a node is two registers per lane; lane l owns channels 2 l and 2 l + 1.  S is
+// partial per node range (summed in range order by the global-MLP reverse).
 constexpr int R3_INST = 64;
 constexpr int R3_IPW = R3_INST / 8;
-constexpr int R3_NODES = 8;
+constexpr int R3_NODES = 16;
 
-__global__ void __launch_bounds__(256) bwd_decoder_kernel(BwdBatchedArgs a) {
-  __shared__ float2 sA3[8][R3_NODES][32];   // per-warp A3 partials of the current node chunk
-  __shared__ float sD2[8][3][H];            // per-warp dD2 partials
+struct R3Smem {
+  float2 A3[8][R3_NODES][32];          // per-warp A3 of the current node chunk
+  float D2[8][3][H];                   // per-warp dD2 partials
+  float H0[R3_NODES][H];               // h0 rows of the chunk
+  float G[8][R3_IPW][R3_NODES * 3];    // per-warp dL/dU of the chunk
+};
+
+__global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_r3[];
+  R3Smem& sm = *reinterpret_cast<R3Smem*>(smem_r3);
+  auto& sA3 = sm.A3;
+  auto& sD2 = sm.D2;
+  auto& sH0 = sm.H0;
+  auto& sG = sm.G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const R3Group grp = a.r3_groups[blockIdx.x];
   const int t = grp.type;
@@ -542,77 +554,85 @@ __global__ void __launch_bounds__(256) bwd_decoder_kernel(BwdBatchedArgs a) {
   const float2 w4a = make_float2(W[OFF_W4 + 2 * lane], W[OFF_W4 + 2 * lane + 1]);
   const float2 w4b = make_float2(W[OFF_W4 + H + 2 * lane], W[OFF_W4 + H + 2 * lane + 1]);
   const float2 w4c = make_float2(W[OFF_W4 + 2 * H + 2 * lane], W[OFF_W4 + 2 * H + 2 * lane + 1]);
-  // this warp's instances
+  // this warp's instances: beta, running S, node base and contact-word offset
   float2 beta[R3_IPW], S[R3_IPW];
-  long long ibase[R3_IPW];
-  long long iwoff[R3_IPW];
-  bool live[R3_IPW];
+  int gofs[R3_IPW], mofs[R3_IPW];   // 3 x node base, contact-word offset (both < 2^31)
+  unsigned live = 0u;
 #pragma unroll
   for (int x = 0; x < R3_IPW; ++x) {
     const int k = grp.k0 + R3_IPW * warp + x;
-    live[x] = k < ninst;
-    const int gi = a.inst_off[t] + (live[x] ? k : 0);
-    const int pad = a.inst_pad[gi];
-    live[x] = live[x] && a.inst_m[gi] > 0;
-    const float* pr = a.pr + (size_t)pad * PR_STRIDE;
-    beta[x] = live[x] ? make_float2(pr[PR_BETA + 2 * lane], pr[PR_BETA + 2 * lane + 1])
-                      : make_float2(0.f, 0.f);
+    const bool in = k < ninst;
+    const int gi = a.inst_off[t] + (in ? k : 0);
+    const bool lv = in && a.inst_m[gi] > 0;
+    const float* pr = a.pr + (size_t)a.inst_pad[gi] * PR_STRIDE;
+    beta[x] = lv ? make_float2(pr[PR_BETA + 2 * lane], pr[PR_BETA + 2 * lane + 1]) : make_float2(0.f, 0.f);
     S[x] = make_float2(0.f, 0.f);
-    ibase[x] = a.inst_base[gi];
-    iwoff[x] = a.type_woff[t] + (long long)(live[x] ? k : 0) * nw;
+    gofs[x] = (int)(3 * a.inst_base[gi]);
+    mofs[x] = (int)(a.type_woff[t] + (long long)(in ? k : 0) * nw);
+    live |= lv ? 1u << x : 0u;
   }
   float2 d2a = make_float2(0.f, 0.f), d2b = d2a, d2c = d2a;   // dD2 rows 0..2, my channels
-  for (int i0 = 0; i0 < n; i0 += R3_NODES) {
-    float2 h0[R3_NODES], A3[R3_NODES];
+  for (int i0 = grp.i0; i0 < grp.i1; i0 += R3_NODES) {
+    const int cn = min(R3_NODES, grp.i1 - i0);   // nodes in this chunk
+    uint32_t word[R3_IPW];   // the chunk's contact bits of each instance
 #pragma unroll
-    for (int r = 0; r < R3_NODES; ++r) {
-      const int i = i0 + r;
-      h0[r] = i < n ? *reinterpret_cast<const float2*>(a.h0tab + (size_t)(o + i) * H + 2 * lane)
-                    : make_float2(0.f, 0.f);
-      A3[r] = make_float2(0.f, 0.f);
-    }
+    for (int x = 0; x < R3_IPW; ++x)
+      word[x] = ((live >> x) & 1u) ? (a.maskbits[mofs[x] + (i0 >> 5)] >> (i0 & 31)) : 0xffffffffu;
+    // stage the chunk: h0 rows (whole CTA, 16-byte loads) and each warp's dL/dU rows
+    for (int e = threadIdx.x; e < cn * (H / 4); e += blockDim.x)
+      reinterpret_cast<float4*>(&sH0[0][0])[e] =
+          __ldg(reinterpret_cast<const float4*>(a.h0tab + (size_t)(o + i0) * H) + e);
 #pragma unroll
     for (int x = 0; x < R3_IPW; ++x) {
-      if (!live[x]) continue;
-      const uint32_t word = a.maskbits[iwoff[x] + (i0 >> 5)] >> (i0 & 31);
-      const float* Gk = a.grad_disp + 3 * (ibase[x] + i0);
+      if (!((live >> x) & 1u)) continue;
+      const float* g = a.grad_disp + gofs[x] + 3 * i0;
+      for (int e = lane; e < 3 * cn; e += 32) sG[warp][x][e] = __ldg(g + e);
+    }
+    __syncthreads();
+#pragma unroll 2
+    for (int r = 0; r < R3_NODES; ++r) {
+      const int i = i0 + r;
+      float2 A3 = make_float2(0.f, 0.f);
+      if (r < cn) {
+        const float2 h0 = *reinterpret_cast<const float2*>(&sH0[r][2 * lane]);
 #pragma unroll
-      for (int r = 0; r < R3_NODES; ++r) {
-        if (i0 + r >= n || ((word >> r) & 1u)) continue;   // active nodes have no decoder term
-        const float g0 = Gk[3 * r], g1 = Gk[3 * r + 1], g2 = Gk[3 * r + 2];
-        float2 dz = __fmul2_rn(w4a, make_float2(g0, g0));
-        dz = __ffma2_rn(w4b, make_float2(g1, g1), dz);
-        dz = __ffma2_rn(w4c, make_float2(g2, g2), dz);
-        const float2 z = __fadd2_rn(h0[r], beta[x]);
-        const float2 da = make_float2(z.x > 0.f ? dz.x : 0.f, z.y > 0.f ? dz.y : 0.f);
-        const float2 rz = make_float2(relu(z.x), relu(z.y));
-        S[x] = __fadd2_rn(S[x], da);
-        A3[r] = __fadd2_rn(A3[r], da);
-        d2a = __ffma2_rn(make_float2(g0, g0), rz, d2a);
-        d2b = __ffma2_rn(make_float2(g1, g1), rz, d2b);
-        d2c = __ffma2_rn(make_float2(g2, g2), rz, d2c);
+        for (int x = 0; x < R3_IPW; ++x) {
+          if ((word[x] >> r) & 1u) continue;   // active node or no contact: no decoder term
+          const float g0 = sG[warp][x][3 * r], g1 = sG[warp][x][3 * r + 1],
+                      g2 = sG[warp][x][3 * r + 2];
+          float2 dz = __fmul2_rn(w4a, make_float2(g0, g0));
+          dz = __ffma2_rn(w4b, make_float2(g1, g1), dz);
+          dz = __ffma2_rn(w4c, make_float2(g2, g2), dz);
+          const float2 z = __fadd2_rn(h0, beta[x]);
+          const float2 da = make_float2(z.x > 0.f ? dz.x : 0.f, z.y > 0.f ? dz.y : 0.f);
+          const float2 rz = make_float2(relu(z.x), relu(z.y));
+          S[x] = __fadd2_rn(S[x], da);
+          A3 = __fadd2_rn(A3, da);
+          d2a = __ffma2_rn(make_float2(g0, g0), rz, d2a);
+          d2b = __ffma2_rn(make_float2(g1, g1), rz, d2b);
+          d2c = __ffma2_rn(make_float2(g2, g2), rz, d2c);
+        }
       }
+      sA3[warp][r][lane] = A3;
     }
     // A3 of these nodes over the group's 64 instances: warps in order
-#pragma unroll
-    for (int r = 0; r < R3_NODES; ++r) sA3[warp][r][lane] = A3[r];
     __syncthreads();
     for (int e = threadIdx.x; e < R3_NODES * 32; e += blockDim.x) {
       const int r = e >> 5, l = e & 31;
-      if (i0 + r >= n) continue;
-      float2 s = sA3[0][r][l];
-      for (int w = 1; w < 8; ++w) s = __fadd2_rn(s, sA3[w][r][l]);
-      *reinterpret_cast<float2*>(a.a3part + grp.a3off + (size_t)(i0 + r) * H + 2 * l) = s;
+      if (r >= cn) continue;
+      float2 s2 = sA3[0][r][l];
+#pragma unroll
+      for (int w = 1; w < 8; ++w) s2 = __fadd2_rn(s2, sA3[w][r][l]);
+      *reinterpret_cast<float2*>(a.a3part + grp.a3off + (size_t)(i0 + r) * H + 2 * l) = s2;
     }
     __syncthreads();
   }
 #pragma unroll
   for (int x = 0; x < R3_IPW; ++x) {
-    if (!live[x]) continue;
-    const int gi = a.inst_off[t] + grp.k0 + R3_IPW * warp + x;
-    float* pr = a.pr + (size_t)a.inst_pad[gi] * PR_STRIDE;
-    pr[PR_S + 2 * lane] = S[x].x;
-    pr[PR_S + 2 * lane + 1] = S[x].y;
+    const int k = grp.k0 + R3_IPW * warp + x;
+    if (k >= ninst) continue;
+    float* sp = a.spart + ((size_t)(a.s_toff[t] + (long long)grp.srange * ninst) + k) * H;
+    *reinterpret_cast<float2*>(sp + 2 * lane) = S[x];   // zero for instances without contact
   }
   sD2[warp][0][2 * lane] = d2a.x;
   sD2[warp][0][2 * lane + 1] = d2a.y;
@@ -622,9 +642,9 @@ __global__ void __launch_bounds__(256) bwd_decoder_kernel(BwdBatchedArgs a) {
   sD2[warp][2][2 * lane + 1] = d2c.y;
   __syncthreads();
   for (int e = threadIdx.x; e < 3 * H; e += blockDim.x) {
-    float s = 0.f;
-    for (int w = 0; w < 8; ++w) s += sD2[w][e / H][e % H];
-    a.d2part[(size_t)blockIdx.x * 3 * H + e] = s;
+    float s2 = 0.f;
+    for (int w = 0; w < 8; ++w) s2 += sD2[w][e / H][e % H];
+    a.d2part[(size_t)blockIdx.x * 3 * H + e] = s2;
   }
 }
 
@@ -648,30 +668,19 @@ __global__ void bwd_reduce_a3_kernel(BwdBatchedArgs a) {
 // channel's argmax node, into per-warp partials of params [OFF_W1, OFF_B2 + 64)
 constexpr int R4_WARPS = 4;
 constexpr int R4_LEN = OFF_B2 + H - OFF_W1;   // E1, b1, E2, b2
-
-constexpr size_t R4_SMEM = sizeof(float) * (3 * H * H + R4_WARPS * (R4_LEN + 2 * H));
+constexpr size_t R4_SMEM = sizeof(float) * (R4_WARPS * (R4_LEN + H)) + sizeof(int) * R4_WARPS * H;
 
 __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
-  float* sD1g = reinterpret_cast<float*>(smem);   // [c][k] = D1[c][64 + k]
-  float* sG1 = sD1g + H * H;                       // [c][k] = G1[c][k]
-  float* sW2 = sG1 + H * H;                        // [c][k] = E2[c][k]
-  float* sAccAll = sW2 + H * H;                    // [warp][R4_LEN]
-  float* sH1All = sAccAll + R4_WARPS * R4_LEN;     // [warp][64]
-  int* sNodeAll = reinterpret_cast<int*>(sH1All + R4_WARPS * H);   // [warp][64]
+  float* sAccAll = reinterpret_cast<float*>(smem);               // [warp][R4_LEN]
+  float* sH1All = sAccAll + R4_WARPS * R4_LEN;                    // [warp][64]
+  int* sNodeAll = reinterpret_cast<int*>(sH1All + R4_WARPS * H);  // [warp][64]
   const float* W = a.params;
-  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
-    const int c = e >> 6, k = e & (H - 1);
-    sD1g[e] = W[OFF_WD + c * 2 * H + H + k];
-    sG1[e] = W[OFF_WG + e];
-    sW2[e] = W[OFF_W2 + e];
-  }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   float* acc = sAccAll + (size_t)warp * R4_LEN;
-  float* sH1w = sH1All + warp * H;
   int* sNodeW = sNodeAll + warp * H;
   for (int e = lane; e < R4_LEN; e += 32) acc[e] = 0.f;
-  __syncthreads();
+  __syncwarp();
   const int gw = blockIdx.x * R4_WARPS + warp, nwarps = gridDim.x * R4_WARPS;
   for (int pad = gw; pad < a.num_items; pad += nwarps) {
     if (a.pad_m[pad] == 0) continue;
@@ -679,17 +688,32 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
     const int ty = a.pad_type[pad];
     const int o = a.type_off[ty];
     const long long base = a.pad_off[pad];
-    // dg = D1_g^T S ; dag = dg [ag > 0] ; dg0 = G1^T dag
-    const float s0 = pr[PR_S + lane], s1 = pr[PR_S + 32 + lane];
+    // S = dL/dbeta: the decoder partials of the type's node ranges, in range order
+    float s0 = 0.f, s1 = 0.f;
+    {
+      const int ninst = a.inst_off[ty + 1] - a.inst_off[ty];
+      const float* sp = a.spart + ((size_t)a.s_toff[ty] + a.pad_inst[pad]) * H;
+      for (int r = 0; r < a.s_nr[ty]; ++r) {
+        s0 += sp[(size_t)r * ninst * H + lane];
+        s1 += sp[(size_t)r * ninst * H + 32 + lane];
+      }
+      float* prs = a.pr + (size_t)pad * PR_STRIDE;
+      prs[PR_S + lane] = s0;
+      prs[PR_S + 32 + lane] = s1;
+    }
+    // dg = D1_g^T S ; dag = dg [ag > 0] ; dg0 = G1^T dag (weights through L1: rows are
+    // read with consecutive lanes on consecutive columns)
     float dag[2];
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = lane + 32 * h;
       float v = 0.f;
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(sD1g[c * H + k], __shfl_sync(FULL, s0, c), v);
+      for (int c = 0; c < 32; ++c)
+        v = fmaf(__ldg(W + OFF_WD + c * 2 * H + H + k), __shfl_sync(FULL, s0, c), v);
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(sD1g[(32 + c) * H + k], __shfl_sync(FULL, s1, c), v);
+      for (int c = 0; c < 32; ++c)
+        v = fmaf(__ldg(W + OFF_WD + (32 + c) * 2 * H + H + k), __shfl_sync(FULL, s1, c), v);
       dag[h] = pr[PR_AG + k] > 0.f ? v : 0.f;
     }
     float* prw = a.pr + (size_t)pad * PR_STRIDE;
@@ -701,9 +725,10 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
       const int k = lane + 32 * h;
       float v = 0.f;
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(sG1[c * H + k], __shfl_sync(FULL, dag[0], c), v);
+      for (int c = 0; c < 32; ++c) v = fmaf(__ldg(W + OFF_WG + c * H + k), __shfl_sync(FULL, dag[0], c), v);
 #pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(sG1[(32 + c) * H + k], __shfl_sync(FULL, dag[1], c), v);
+      for (int c = 0; c < 32; ++c)
+        v = fmaf(__ldg(W + OFF_WG + (32 + c) * H + k), __shfl_sync(FULL, dag[1], c), v);
       dg0[h] = v;
     }
     // routes: distinct argmax nodes, first appearance in channel order
@@ -736,43 +761,38 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
       x[7] = u.y;
       x[8] = u.z;
       // forward of this node: a1, h1 (lanes own units k = lane, lane + 32)
-      float a1[2];
+      float a1[2], h1[2];
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = lane + 32 * h;
-        float v = W[OFF_B1 + k];
+        float v = __ldg(W + OFF_B1 + k);
 #pragma unroll
-        for (int q2 = 0; q2 < NIN; ++q2) v = fmaf(W[OFF_W1 + k * NIN + q2], x[q2], v);
+        for (int q2 = 0; q2 < NIN; ++q2) v = fmaf(__ldg(W + OFF_W1 + k * NIN + q2), x[q2], v);
         a1[h] = v;
-        sH1w[k] = relu(v);
+        h1[h] = relu(v);
       }
-      __syncwarp();
-      // routed gradient of this node: dA2[c] = dg0[c] [a2_c > 0] for its channels
-      float da2[2];
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int c = lane + 32 * h;
-        const bool routed = (h == 0 ? rt0 : rt1) == node;
-        float a2 = W[OFF_B2 + c];
-        if (routed) {
-#pragma unroll 8
-          for (int k = 0; k < H; ++k) a2 = fmaf(sW2[c * H + k], sH1w[k], a2);
-        }
-        da2[h] = (routed && a2 > 0.f) ? dg0[h] : 0.f;
-      }
-      // dE2[c][k] += dA2[c] h1[k] (lanes over k), db2, dh1 = E2^T dA2
+      // the channels routed to this node, one at a time (lanes over units k)
+      unsigned long long cm = (unsigned long long)__ballot_sync(FULL, rt0 == node) |
+                              ((unsigned long long)__ballot_sync(FULL, rt1 == node) << 32);
       float dh1[2] = {0.f, 0.f};
-      for (int c = 0; c < H; ++c) {
-        const float d = __shfl_sync(FULL, c < 32 ? da2[0] : da2[1], c & 31);
-        if (d == 0.f) continue;   // warp-uniform
+      while (cm) {
+        const int c = __ffsll((long long)cm) - 1;
+        cm &= cm - 1;
+        const float w0 = __ldg(W + OFF_W2 + c * H + lane), w1 = __ldg(W + OFF_W2 + c * H + 32 + lane);
+        float a2 = fmaf(w0, h1[0], w1 * h1[1]);
 #pragma unroll
-        for (int h = 0; h < 2; ++h) {
-          const int k = lane + 32 * h;
-          acc[OFF_W2 - OFF_W1 + c * H + k] += d * sH1w[k];
-          dh1[h] = fmaf(sW2[c * H + k], d, dh1[h]);
-        }
+        for (int sh = 16; sh > 0; sh >>= 1) a2 += __shfl_xor_sync(FULL, a2, sh);
+        a2 += __ldg(W + OFF_B2 + c);
+        const float g = __shfl_sync(FULL, c < 32 ? dg0[0] : dg0[1], c & 31);
+        const float d = a2 > 0.f ? g : 0.f;   // dA2[c]
+        if (d == 0.f) continue;                // warp-uniform
+        acc[OFF_W2 - OFF_W1 + c * H + lane] += d * h1[0];
+        acc[OFF_W2 - OFF_W1 + c * H + 32 + lane] += d * h1[1];
         if (lane == 0) acc[OFF_B2 - OFF_W1 + c] += d;
+        dh1[0] = fmaf(w0, d, dh1[0]);
+        dh1[1] = fmaf(w1, d, dh1[1]);
       }
+      if (!__any_sync(FULL, dh1[0] != 0.f || dh1[1] != 0.f)) continue;   // warp-uniform
       // dA1 = dh1 [a1 > 0]; dE1 += dA1 x^T; db1; du_hat = E1[:, 6:9]^T dA1 (active)
       float du0 = 0.f, du1 = 0.f, du2 = 0.f;
 #pragma unroll
@@ -782,9 +802,9 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
 #pragma unroll
         for (int q2 = 0; q2 < NIN; ++q2) acc[k * NIN + q2] += d1 * x[q2];
         acc[OFF_B1 - OFF_W1 + k] += d1;
-        du0 = fmaf(W[OFF_W1 + k * NIN + 6], d1, du0);
-        du1 = fmaf(W[OFF_W1 + k * NIN + 7], d1, du1);
-        du2 = fmaf(W[OFF_W1 + k * NIN + 8], d1, du2);
+        du0 = fmaf(__ldg(W + OFF_W1 + k * NIN + 6), d1, du0);
+        du1 = fmaf(__ldg(W + OFF_W1 + k * NIN + 7), d1, du1);
+        du2 = fmaf(__ldg(W + OFF_W1 + k * NIN + 8), d1, du2);
       }
       if (act) {
 #pragma unroll
@@ -850,6 +870,14 @@ __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
       for (int r = 0; r < R4B_PADS; ++r) s += sA[r][tid];
       if (which == 0) out[OFF_BD - OFF_WG + tid] = s;
       else out[OFF_BG - OFF_WG + tid] = s;
+    }
+    if (which == 0 && tid < 3) {   // sum of G over passive nodes (dL/db_D2), this chunk
+      float g = 0.f;
+      for (int r = 0; r < R4B_PADS; ++r) {
+        const int pad = p0 + r;
+        if (pad < a.num_items) g += a.pr[(size_t)pad * PR_STRIDE + PR_GSUM + tid];
+      }
+      a.gsum_part[(size_t)blockIdx.x * 3 + tid] = g;
     }
     if (which == 0) {   // the local half of D1 belongs to R5: zeros here
       for (int e = tid; e < H * H; e += 256) out[OFF_WD - OFF_WG + (e >> 6) * 2 * H + (e & 63)] = 0.f;
@@ -1059,7 +1087,7 @@ __global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
   if (q >= OFF_W4 && q < OFF_W4 + 3 * H)
     for (int b = 0; b < a.r3_parts; ++b) s += a.d2part[(size_t)b * 3 * H + q - OFF_W4];
   if (q >= OFF_B4 && q < OFF_B4 + 3)
-    for (int p = 0; p < a.num_items; ++p) s += a.pr[(size_t)p * PR_STRIDE + PR_GSUM + q - OFF_B4];
+    for (int b = 0; b < a.r4b_parts; ++b) s += a.gsum_part[(size_t)b * 3 + q - OFF_B4];
   if (q == OFF_ALPHA)
     for (int b = 0; b < a.alpha_parts; ++b) s -= a.alpha_part[b];
   out[q] = s;
@@ -1069,64 +1097,77 @@ __global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
 
 size_t bwd_pad_smem_bytes(int nmax, int K) { return R1Smem(nmax, K).total; }
 
-cudaError_t launch_backward_batched(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
-                                    cudaStream_t s) {
-  cudaError_t e;
-  {
-    const size_t smem = R1Smem(a.nmax, a.K).total;
-    static size_t configured = 0;
-    if (smem > configured) {
-      e = cudaFuncSetAttribute(bwd_pad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)smem);
-      if (e != cudaSuccess) return e;
-      configured = smem;
+// one stage of the staged reverse mode (BWD_STAGE_*), launched on stream s
+cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunch& l, int stage,
+                                  float* grad_params, cudaStream_t s) {
+  switch (stage) {
+    case BWD_STAGE_PAD: {
+      const size_t smem = R1Smem(a.nmax, a.K).total;
+      static size_t configured = 0;
+      if (smem > configured) {
+        cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+      }
+      bwd_pad_kernel<<<l.r1_grid, RT, smem, s>>>(a);
+      break;
     }
-    bwd_pad_kernel<<<l.r1_grid, RT, smem, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  if (a.mode != MODE_LINEAR_ONLY) {
-    bwd_global_kernel<<<l.r2_grid, 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bwd_decoder_kernel<<<a.r3_parts, 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const long long tot = (long long)a.total_nodes * H;
-    bwd_reduce_a3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    static bool c4 = false;
-    if (!c4) {
-      e = cudaFuncSetAttribute(bwd_padrev_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)R4_SMEM);
+    case BWD_STAGE_GLOBAL:
+      bwd_global_kernel<<<l.r2_grid, 256, 0, s>>>(a);
+      break;
+    case BWD_STAGE_DECODER: {
+      static bool c3 = false;
+      if (!c3) {
+        cudaError_t e = cudaFuncSetAttribute(bwd_decoder_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(R3Smem));
+        if (e != cudaSuccess) return e;
+        c3 = true;
+      }
+      bwd_decoder_kernel<<<a.r3_parts, 256, sizeof(R3Smem), s>>>(a);
+      cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      c4 = true;
+      const long long tot = (long long)a.total_nodes * H;
+      bwd_reduce_a3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a);
+      break;
     }
-    bwd_padrev_kernel<<<a.r4_parts / R4_WARPS, R4_WARPS * 32, R4_SMEM, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    bwd_padsum_kernel<<<a.r4b_parts, 256, 0, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const size_t s5 = sizeof(float) * (8 * 64 * TLD + 64 * 6);
-    static bool c5 = false;
-    if (!c5) {
-      e = cudaFuncSetAttribute(bwd_typenode_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                               (int)s5);
+    case BWD_STAGE_PADREV: {
+      static bool c4 = false;
+      if (!c4) {
+        cudaError_t e = cudaFuncSetAttribute(bwd_padrev_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R4_SMEM);
+        if (e != cudaSuccess) return e;
+        c4 = true;
+      }
+      bwd_padrev_kernel<<<a.r4_parts / R4_WARPS, R4_WARPS * 32, R4_SMEM, s>>>(a);
+      cudaError_t e = cudaGetLastError();
       if (e != cudaSuccess) return e;
-      c5 = true;
+      bwd_padsum_kernel<<<a.r4b_parts, 256, 0, s>>>(a);
+      break;
     }
-    bwd_typenode_kernel<<<a.r5_parts, 256, s5, s>>>(a);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    case BWD_STAGE_TYPENODE: {
+      const size_t s5 = sizeof(float) * (8 * 64 * TLD + 64 * 6);
+      static bool c5 = false;
+      if (!c5) {
+        cudaError_t e = cudaFuncSetAttribute(bwd_typenode_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)s5);
+        if (e != cudaSuccess) return e;
+        c5 = true;
+      }
+      bwd_typenode_kernel<<<a.r5_parts, 256, s5, s>>>(a);
+      break;
+    }
+    case BWD_STAGE_POSE:
+      bwd_pose_kernel<<<l.r7_grid, 256, sizeof(PadObj) * 8 * a.K, s>>>(a);
+      break;
+    case BWD_STAGE_PARAMS:
+      if (grad_params) bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
+      break;
+    default:
+      return cudaErrorInvalidValue;
   }
-  return cudaSuccess;
-}
-
-cudaError_t launch_backward_batched_tail(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
-                                         float* grad_params, cudaStream_t s) {
-  cudaError_t e;
-  bwd_pose_kernel<<<l.r7_grid, 256, sizeof(PadObj) * 8 * a.K, s>>>(a);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  if (grad_params) {
-    bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  return cudaSuccess;
+  return cudaGetLastError();
 }
 
 }  // namespace etac

@@ -243,8 +243,11 @@ constexpr int PR_G0 = 0, PR_AG = 64, PR_G = 128, PR_BETA = 192, PR_S = 256, PR_D
 
 struct R3Group {
   int type, k0;        // pad type, first instance of the 64-instance group
+  int i0, i1;          // node range of this work unit
+  int srange;          // index of the node range within the type
   long long a3off;     // float offset of the group's A3 partial block [n_t][64]
 };
+constexpr int R3_RANGE = 256;   // nodes per decoder-reverse work unit (at most; host picks)
 
 struct BwdBatchedArgs {
   const float* type_pos;
@@ -288,12 +291,16 @@ struct BwdBatchedArgs {
   float* a3part;
   const long long* a3_toff;    // [T] float offset of type t's first group block
   const int* a3_tgroups;       // [T] groups of type t
+  float* spart;                // dL/dbeta partials per (node range, instance) [.][64]
+  const long long* s_toff;     // [T] first partial row of type t (rows: range-major, then instance)
+  const int* s_nr;             // [T] node ranges of type t
   float* a3;                   // [sum n][64]
   float* d2part;               // [r3_parts][3 * 64]
   float* r4part;
   int r4_parts;
   float* r4bpart;
   int r4b_parts;
+  float* gsum_part;            // [r4b_parts][3] sums of G over passive nodes per pad chunk
   float* r5part;
   int r5_parts;
   float* alpha_part;
@@ -305,9 +312,9 @@ struct BwdBatchedLaunch {
   int r1_grid, r2_grid, r7_grid;
 };
 size_t bwd_pad_smem_bytes(int nmax, int K);
-cudaError_t launch_backward_batched(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
-                                    cudaStream_t s);
-cudaError_t launch_backward_batched_tail(const BwdBatchedArgs& a, const BwdBatchedLaunch& l,
-                                         float* grad_params, cudaStream_t s);
+enum { BWD_STAGE_PAD = 0, BWD_STAGE_GLOBAL, BWD_STAGE_DECODER, BWD_STAGE_PADREV,
+       BWD_STAGE_TYPENODE, BWD_STAGE_POSE, BWD_STAGE_PARAMS };
+cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunch& l, int stage,
+                                  float* grad_params, cudaStream_t s);
 
 }  // namespace etac
