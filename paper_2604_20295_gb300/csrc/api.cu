@@ -106,6 +106,7 @@ struct etac_ctx {
   float* d_spart = nullptr;
   long long* d_s_toff = nullptr;
   int* d_s_nr = nullptr;
+  int bwd_r1_grid = 0;
   int r3_parts = 0, r4_parts = 0, r4b_parts = 0, r5_parts = 0, alpha_parts = 0;
   etac::GemmParams gemm_bu{}, gemm_ba{};
   // profiling: event pairs around kernel launches
@@ -500,6 +501,10 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
     g.inst_m = c->d_inst_m;
     g.alpha_part = c->d_alpha_part;   // ws_u / ws_du are bound at launch (allocated later)
   }
+  int per_sm = 0;
+  e = etac::bwd_pad_occupancy(c->nmax, c->K, &per_sm);
+  if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "reverse-mode pad kernel occupancy");
+  c->bwd_r1_grid = per_sm * c->num_sms;
   c->bwdb_ready = true;
   return ETAC_OK;
 }
@@ -663,7 +668,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
       if (!q) return fail(c, ETAC_ERR_STATE, "reverse-mode buffers are not set up");
   }
   etac::BwdBatchedLaunch l{};
-  l.r1_grid = 2 * c->num_sms;
+  l.r1_grid = c->bwd_r1_grid;
   l.r2_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
   l.r7_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
   auto stage = [&](int st, int slot, const char* what) -> etac_status {

@@ -430,7 +430,7 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
     }
     unsigned long long open = (unsigned long long)__ballot_sync(FULL, !done[0]) |
                               ((unsigned long long)__ballot_sync(FULL, !done[1]) << 32);
-    while (open) {
+    while (open) {   // warp-uniform: one open channel at a time, 32 ranks per test
       const int ch = __ffsll((long long)open) - 1;
       open &= open - 1;
       float bv = -1.f;
@@ -731,18 +731,22 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
         v = fmaf(__ldg(W + OFF_WG + (32 + c) * H + k), __shfl_sync(FULL, dag[1], c), v);
       dg0[h] = v;
     }
-    // routes: distinct argmax nodes, first appearance in channel order
+    // routes: the distinct argmax nodes, channels 0..31 first (lowest lane of each node),
+    // then nodes of channels 32..63 that no channel below 32 routes to
     const int rt0 = reinterpret_cast<const int*>(pr)[PR_ROUTE + lane];
     const int rt1 = reinterpret_cast<const int*>(pr)[PR_ROUTE + 32 + lane];
     int nd = 0;
-    for (int c = 0; c < H; ++c) {
-      const int node = __shfl_sync(FULL, c < 32 ? rt0 : rt1, c & 31);
-      bool seen = false;
-      for (int q = lane; q < nd; q += 32) seen |= sNodeW[q] == node;
-      if (!__any_sync(FULL, seen)) {
-        if (lane == 0) sNodeW[nd] = node;
-        ++nd;
-      }
+    {
+      const unsigned lt = (1u << lane) - 1u;
+      const unsigned m0 = __match_any_sync(FULL, rt0), m1 = __match_any_sync(FULL, rt1);
+      const bool lead0 = (m0 & lt) == 0u;
+      bool in0 = false;   // does rt1 appear among the channels 0..31?
+      for (int l = 0; l < 32; ++l) in0 |= __shfl_sync(FULL, rt0, l) == rt1;
+      const bool lead1 = (m1 & lt) == 0u && !in0;
+      const unsigned b0 = __ballot_sync(FULL, lead0), b1 = __ballot_sync(FULL, lead1);
+      if (lead0) sNodeW[__popc(b0 & lt)] = rt0;
+      if (lead1) sNodeW[__popc(b0) + __popc(b1 & lt)] = rt1;
+      nd = __popc(b0) + __popc(b1);
       __syncwarp();
     }
     const uint32_t* bits = a.maskbits + a.mask_woff[pad];
@@ -1096,6 +1100,14 @@ __global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
 }  // namespace
 
 size_t bwd_pad_smem_bytes(int nmax, int K) { return R1Smem(nmax, K).total; }
+
+cudaError_t bwd_pad_occupancy(int nmax, int K, int* blocks_per_sm) {
+  const size_t smem = R1Smem(nmax, K).total;
+  cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bwd_pad_kernel, RT, smem);
+}
 
 // one stage of the staged reverse mode (BWD_STAGE_*), launched on stream s
 cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunch& l, int stage,

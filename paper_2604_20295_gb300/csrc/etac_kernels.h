@@ -312,6 +312,7 @@ struct BwdBatchedLaunch {
   int r1_grid, r2_grid, r7_grid;
 };
 size_t bwd_pad_smem_bytes(int nmax, int K);
+cudaError_t bwd_pad_occupancy(int nmax, int K, int* blocks_per_sm);
 enum { BWD_STAGE_PAD = 0, BWD_STAGE_GLOBAL, BWD_STAGE_DECODER, BWD_STAGE_PADREV,
        BWD_STAGE_TYPENODE, BWD_STAGE_POSE, BWD_STAGE_PARAMS };
 cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunch& l, int stage,
