@@ -200,6 +200,147 @@ def executed_gemm_flops(scene):
     return float((2.0 * n * n * 3.0).sum())
 
 
+def _stats(got, ref_disp, mask_got, mask_ref):
+    d = np.linalg.norm(got.astype(np.float64) - ref_disp, axis=1)
+    return {"max_abs_mm": float(d.max()), "rms_mm": float(np.sqrt((d ** 2).mean())),
+            "mask_mismatch_nodes": int((mask_got != mask_ref).sum())}
+
+
+def config_c3(X, I, torch, dev, stream, flush, theta, with_oracle):
+    """The single-pad sphere-press workload (100 seeded steps, flat 16x16 pad) in FP32 plain and
+    with the BF16 tensor-core propagation: time per launch of all 100 steps as 100 problems,
+    the one-step latency, and the error of each against the FP64 oracle."""
+    sc = I.sphere_press_scene(100, seed=0)
+    out = {"workload": "sphere-press 16x16 flat pad, 100 seeded steps as 100 problems per launch"}
+    runs = {}
+    for name, prec, algo in [("fp32_plain", X.PREC_FP32, X.ALGO_PLAIN),
+                             ("bf16_batched", X.PREC_BF16, X.ALGO_BATCHED)]:
+        sim = X.TactileSim(sc, device=dev)
+        sim.set_model(theta, X.MODE_FULL, prec, algo)
+        for _ in range(3):
+            sim.step()
+        ms = timed_steps(sim, 20, stream, flush, torch, {})
+        sim.step()
+        torch.cuda.synchronize()
+        runs[name] = {"us_per_launch": 1e3 * sum(ms) / len(ms),
+                      "disp": sim.disp.cpu().numpy(), "mask": sim.mask.cpu().numpy()}
+        sim.close()
+        one = X.TactileSim(sc.subset([0]), device=dev)
+        one.set_model(theta, X.MODE_FULL, prec, algo)
+        for _ in range(3):
+            one.step()
+        ms1 = timed_steps(one, 20, stream, flush, torch, {})
+        runs[name]["us_one_step"] = 1e3 * sum(ms1) / len(ms1)
+        one.close()
+    out["fp32_plain_us_per_launch"] = runs["fp32_plain"]["us_per_launch"]
+    out["bf16_us_per_launch"] = runs["bf16_batched"]["us_per_launch"]
+    out["fp32_plain_us_one_step"] = runs["fp32_plain"]["us_one_step"]
+    out["bf16_us_one_step"] = runs["bf16_batched"]["us_one_step"]
+    out["throughput_ratio_bf16_over_fp32"] = (runs["fp32_plain"]["us_per_launch"] /
+                                              runs["bf16_batched"]["us_per_launch"])
+    if with_oracle:
+        import oracle
+        ref = oracle.forward(sc, theta)
+        for name in runs:
+            out[f"{name}_error"] = _stats(runs[name]["disp"], ref["disp"], runs[name]["mask"],
+                                          ref["mask"])
+    return out
+
+
+def config_c4_fit(I, theta0, with_oracle):
+    """Eq. 5 calibration over 1,024 envs of the single-pad layout: Adam, 200 iterations, from
+    seed-0 parameters to oracle targets made with seed-42 parameters."""
+    if not with_oracle:
+        return None
+    import oracle
+    from paper_2604_20295_gb300 import fit as F
+    sc = I.sphere_press_scene(1024, seed=7)
+    tht = I.make_params(42)
+    target = oracle.forward(sc, tht)["disp"]
+    h = F.fit(sc, theta0, target, iters=200, lr=1e-3)
+    err = {k: float(np.linalg.norm(h["params"][a:a + n] - tht[a:a + n]) /
+                    max(np.linalg.norm(tht[a:a + n]), 1e-30))
+           for k, (a, n, _) in I.param_slices().items()}
+    err0 = {k: float(np.linalg.norm(theta0[a:a + n] - tht[a:a + n]) /
+                     max(np.linalg.norm(tht[a:a + n]), 1e-30))
+            for k, (a, n, _) in I.param_slices().items()}
+    return {"workload": "1024 envs x sphere-press 16x16, Adam lr 1e-3, 200 iterations",
+            "loss_first": h["loss"][0], "loss_last": h["loss"][-1],
+            "norm_first": h["norm"][0], "norm_last": h["norm"][-1],
+            "alpha_start": float(theta0[0]), "alpha_end": h["alpha"][-1],
+            "alpha_target": float(tht[0]), "param_rel_error": err,
+            "param_rel_error_start": err0, "seconds": h["seconds"]}
+
+
+def config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle):
+    """Scale and unevenness: 16,384 envs x 6 flat pads of 8x8 .. 64x64 nodes (16 pad types),
+    1-3 primitives per env; BF16 forward and FP32 reverse mode."""
+    sc = I.uneven_scene(16384, seed=5)
+    sim = X.TactileSim(sc, device=dev)
+    sim.set_model(theta, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+    kw = dict(want_mask=False, want_pen=False, want_count=True)
+    for _ in range(3):
+        sim.step(**kw)
+    torch.cuda.synchronize()
+    counts = sim.count.cpu().numpy()
+    work = algorithmic_work(sc, counts)
+    X.etac_enable_timing(sim.ctx, True)
+    ms = timed_steps(sim, 5, stream, flush, torch, kw)
+    kt = X.etac_kernel_times(sim.ctx)
+    fwd_ms = sum(ms) / len(ms)
+    G = torch.randn(sim.disp.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(4))
+    sim.step(**kw)
+    for _ in range(2):
+        sim.backward(G)
+    torch.cuda.synchronize()
+    bms = []
+    for _ in range(3):
+        flush.fill_(1)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        sim.backward(G)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        bms.append(e0.elapsed_time(e1))
+    kt2 = X.etac_kernel_times(sim.ctx)
+    X.etac_enable_timing(sim.ctx, False)
+    nodes = sc.total_nodes
+    gk = kt.get("prop_gemm_kernel", (1, 0.0))
+    t_gemm = gk[1] / max(gk[0], 1) / 1e3
+    alg = 6.0 * work["pairs"] + 2.0 * 3 * H * work["passive"]
+    exe = executed_gemm_flops(sc)
+    out = {"workload": "uneven-16384env-6pads-8x8..64x64-16types", "nodes_per_step": nodes,
+           "fwd_ms": fwd_ms, "fwd_node_steps_per_s": nodes * 1e3 / fwd_ms,
+           "bwd_ms": sum(bms) / len(bms), "bwd_fwd": sum(bms) / len(bms) / fwd_ms,
+           "active_fraction": work["active"] / nodes,
+           "fwd_kernels": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+           "bwd_kernels": {k: v[1] / max(v[0], 1) for k, v in kt2.items()},
+           "roofline_prop_gemm": {"bound": "tensor", "achieved": alg / t_gemm / 1e12,
+                                  "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                                  "frac": alg / t_gemm / 1e12 / peaks["bf16_tflops"],
+                                  "executed_dense_tflops": exe / t_gemm / 1e12,
+                                  "executed_frac": exe / t_gemm / 1e12 / peaks["bf16_tflops"]},
+           "roofline_step_hbm": {"bound": "hbm", "achieved": work["bytes_out"] * 1e3 / fwd_ms / 1e9,
+                                 "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                                 "frac": work["bytes_out"] * 1e3 / fwd_ms / 1e9 / peaks["hbm_gbs"],
+                                 "note": "12 B of displacement out per node over the whole step"}}
+    if with_oracle:
+        import oracle
+        envs = np.sort(np.random.default_rng(9).choice(sc.num_envs, 48, replace=False))
+        sub = sc.subset(envs)
+        sim.step(want_mask=True, want_pen=False, want_count=True)
+        torch.cuda.synchronize()
+        offs = sc.node_offsets
+        idx = np.concatenate([np.arange(offs[e * 6], offs[e * 6 + 6]) for e in envs])
+        ref = oracle.forward(sub, theta)
+        out["error_vs_oracle"] = dict(_stats(sim.disp.cpu().numpy()[idx], ref["disp"],
+                                             sim.mask.cpu().numpy()[idx], ref["mask"]),
+                                      envs=len(envs))
+    sim.close()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,6 +357,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-bwd", action="store_true")
+    ap.add_argument("--no-configs", action="store_true",
+                    help="skip the single-pad BF16, calibration and 16,384-env uneven sections")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -451,6 +594,16 @@ def main():
                "max_pad_rel": float((pad_err / np.maximum(pad_scale, 1e-30)).max()),
                "mask_mismatch_nodes": int((~same).sum()), "envs": len(envs)}
 
+    configs = None
+    if not args.no_configs and rank == 0:
+        sim.close()
+        sim = None
+        with_oracle = not args.no_cpu
+        configs = {"c3_bf16_single_pad": config_c3(X, I, torch, dev, stream, flush, theta, with_oracle),
+                   "c4_fit": config_c4_fit(I, theta, with_oracle),
+                   "c5_uneven_16384": config_c5(X, I, torch, dev, stream, flush, theta, peaks,
+                                                with_oracle)}
+
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
@@ -460,12 +613,13 @@ def main():
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
             "clocks": clk, "error_vs_oracle": err, "rungs": compare, "kernels": kern,
-            "bwd_fwd": bwd,
+            "bwd_fwd": bwd, "configs": configs,
             "active_fraction": work["active"] / nodes,
             "step_ms_min": min(step_ms), "step_ms_max": max(step_ms)}
     if rank == 0:
         print(json.dumps(line), flush=True)
-    sim.close()
+    if sim is not None:
+        sim.close()
     if pg:
         pg.destroy_process_group()
 
