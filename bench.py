@@ -357,6 +357,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-bwd", action="store_true")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the default tile / block shapes instead of measuring them")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the single-pad BF16, calibration and 16,384-env uneven sections")
     args = ap.parse_args()
@@ -390,6 +392,12 @@ def main():
     stream = torch.cuda.current_stream(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     step_kw = dict(want_mask=False, want_pen=False, want_count=True)
+
+    tuning = None
+    if not args.no_autotune and algo == X.ALGO_BATCHED:
+        gt = torch.randn(sim.disp.shape, device=dev, generator=torch.Generator(device=dev).manual_seed(5))
+        tuning = sim.autotune(None if args.no_bwd else gt)
+        del gt
 
     clocks = Clocks(local)
     clocks.start()    # sampled from before warm-up until after the timed region
@@ -608,7 +616,8 @@ def main():
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
             "dtype": "bf16" if prec == X.PREC_BF16 else "f32",
-            "data": "synthetic", "config": workload_config(args, scene), "roofline": roof,
+            "data": "synthetic", "config": dict(workload_config(args, scene), tuning=tuning),
+            "roofline": roof,
             "roofline_by_kernel": roof_all,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),

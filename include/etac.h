@@ -172,6 +172,37 @@ typedef struct {
 etac_status etac_enable_timing(etac_ctx* ctx, int32_t enable);
 etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max, int32_t* count);
 
+/* ---- Tile and block shapes picked by measurement (the paper has no counterpart).
+ * gemm_inst_per_tile: pad instances per tile of the BF16 propagation GEMM (32 or 64; the
+ * tile is 128 node rows x 3 * that many columns); gemm_tile_order: 0 walks node-row tiles
+ * innermost (tiles running together share a B tile in L2), 1 walks instance groups
+ * innermost (they share an Omega row block); bwd_node_range: nodes per work unit of the
+ * batched reverse mode's decoder stage (16..256, a multiple of 16).
+ *
+ * etac_autotune times every candidate on the caller's own step: the forward shapes
+ * (ETAC_ALGO_BATCHED with ETAC_PREC_BF16) on `in` / `out`, and, when grad_disp is not NULL,
+ * the reverse-mode node ranges on that upstream gradient [N*3].  It leaves the fastest
+ * choice in effect, writes the candidates and their milliseconds per step to *result
+ * (host), synchronises `stream`, and overwrites `out`.  Not to be called during stream
+ * capture.  etac_set_tuning applies a stored choice (fields that do not apply to the
+ * model's algorithm are ignored).  Errors: ETAC_ERR_STATE without a batched model,
+ * ETAC_ERR_INVALID_ARG for NULL in/out/result or out-of-range fields. */
+#define ETAC_TUNE_MAX 8
+typedef struct {
+  int32_t gemm_inst_per_tile;
+  int32_t gemm_tile_order;
+  int32_t bwd_node_range;
+  int32_t num_fwd;                     /* forward candidates timed */
+  int32_t fwd_cand[ETAC_TUNE_MAX][2];  /* (instances per tile, tile order) */
+  float fwd_ms[ETAC_TUNE_MAX];
+  int32_t num_bwd;                     /* reverse-mode candidates timed */
+  int32_t bwd_cand[ETAC_TUNE_MAX];     /* node range */
+  float bwd_ms[ETAC_TUNE_MAX];
+} etac_tuning;
+etac_status etac_autotune(etac_ctx* ctx, const etac_step_in* in, const etac_step_out* out,
+                          const float* grad_disp, etac_tuning* result, void* stream);
+etac_status etac_set_tuning(etac_ctx* ctx, const etac_tuning* tuning, void* stream);
+
 /* FP64 evaluation of the plain algorithm, for finite-difference gradient checks only.
  * Device arrays as in etac_step_in but double; params [etac_param_count] double; writes
  * disp [N*3] double.  Uses the context's pads and the mode of `desc`. */

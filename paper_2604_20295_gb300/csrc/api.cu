@@ -77,7 +77,11 @@ struct etac_ctx {
   long long* d_type_woff = nullptr;
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
-  int front_grid = 0, gemm_grid = 0, num_tiles = 0;
+  int front_grid = 0, gemm_grid = 0, num_tiles = 0, tiles_cap = 0;
+  int gemm_gi = 64;      // instances per GEMM tile (tuned: 32 or 64)
+  int gemm_order = 0;    // GEMM tile order (tuned)
+  int r3_range = 0;      // decoder-reverse node range (0: from the SM count; tuned)
+  size_t r3g_cap = 0, spart_cap = 0, d2_cap = 0;
   bool bf16_ready = false, inst_ready = false;
   std::vector<long long> bt_off_h;
   std::vector<int> ninst_h;
@@ -228,6 +232,52 @@ bool encode_bf16_2d(EncodeTiledFn fn, CUtensorMap* m, const void* base, uint64_t
             CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
+void fill_gemm_common(etac_ctx* c, etac::GemmParams& g);
+
+// GEMM tile list for the current tile shape (instances per tile) and order: heaviest tiles
+// first; order 0 walks node-row tiles innermost, so the CTAs working at one time share each B
+// tile through L2; order 1 walks instance groups innermost, sharing each Omega row block
+etac_status build_tiles(etac_ctx* c, cudaStream_t s) {
+  const int gi = c->gemm_gi;
+  std::vector<etac::GemmTile> tiles;
+  for (int t = 0; t < c->T; ++t) {
+    if (!c->ninst_h[t]) continue;
+    const int n = c->type_n[t];
+    if (c->gemm_order == 0) {
+      for (int k0 = 0; k0 < c->ninst_h[t]; k0 += gi)
+        for (int m0 = 0; m0 < n; m0 += 128) tiles.push_back({t, m0, k0, (n + 63) / 64});
+    } else {
+      for (int m0 = 0; m0 < n; m0 += 128)
+        for (int k0 = 0; k0 < c->ninst_h[t]; k0 += gi) tiles.push_back({t, m0, k0, (n + 63) / 64});
+    }
+  }
+  std::stable_sort(tiles.begin(), tiles.end(), [](const etac::GemmTile& x,
+                                                  const etac::GemmTile& y) {
+    return x.nkb > y.nkb;
+  });
+  cudaError_t e = cudaSuccess;
+  if ((int)tiles.size() > c->tiles_cap) {
+    if (c->d_tiles) cudaFree(c->d_tiles);
+    c->d_tiles = nullptr;
+    e = dalloc(&c->d_tiles, tiles.size());
+    if (e != cudaSuccess) return cuda_fail(c, e, "GEMM tile list");
+    c->tiles_cap = (int)tiles.size();
+  }
+  if (!tiles.empty())
+    e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(etac::GemmTile) * tiles.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "GEMM tile list");
+  c->num_tiles = (int)tiles.size();
+  c->gemm_grid = std::max(1, std::min(c->num_sms, c->num_tiles));
+  for (etac::GemmParams* g : {&c->gemm, &c->gemm_bu, &c->gemm_ba}) {
+    g->tiles = c->d_tiles;
+    g->num_tiles = c->num_tiles;
+  }
+  c->alpha_parts = c->gemm_grid;
+  return ETAC_OK;
+}
+
 // Instance bookkeeping shared by the tensor-core forward and the batched reverse mode (once
 // per context): instance order per pad type, per-instance records' indices, contact bit words
 // in instance order, the GEMM tile list, per-pad transform buffers.
@@ -266,20 +316,6 @@ etac_status setup_instances(etac_ctx* c, cudaStream_t s) {
   }
   c->bt_total = bt_total;
   c->ninst_h = ninst;
-  // tiles: node-row tiles innermost, so the CTAs working at one time share each B tile (the
-  // instances' u_hat) through L2 instead of re-reading it from DRAM per row tile
-  std::vector<etac::GemmTile> tiles;
-  for (int t = 0; t < c->T; ++t) {
-    if (!ninst[t]) continue;
-    const int n = c->type_n[t];
-    for (int k0 = 0; k0 < ninst[t]; k0 += 64)
-      for (int m0 = 0; m0 < n; m0 += 128) tiles.push_back({t, m0, k0, (n + 63) / 64});
-  }
-  std::stable_sort(tiles.begin(), tiles.end(), [](const etac::GemmTile& x,
-                                                  const etac::GemmTile& y) {
-    return x.nkb > y.nkb;   // heaviest tiles first
-  });
-  c->num_tiles = (int)tiles.size();
   cudaError_t e = dalloc(&c->d_bt_off, c->T);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_inst, np);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_off, c->T + 1);
@@ -292,7 +328,6 @@ etac_status setup_instances(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_pad_gi, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_base, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_type_woff, (size_t)c->T);
-  if (e == cudaSuccess) e = dalloc(&c->d_tiles, tiles.size());
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_pad_gi, pad_gi.data(), sizeof(int) * np,
                                             cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_base, inst_base.data(),
@@ -309,14 +344,10 @@ etac_status setup_instances(etac_ctx* c, cudaStream_t s) {
                                             sizeof(int) * (c->T + 1), cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_inst_pad, inst_pad.data(), sizeof(int) * np,
                                             cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess && !tiles.empty())
-    e = cudaMemcpyAsync(c->d_tiles, tiles.data(), sizeof(etac::GemmTile) * tiles.size(),
-                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);   // host vectors are pageable
   if (e != cudaSuccess) return cuda_fail(c, e, "instance buffers");
-  c->gemm_grid = std::max(1, std::min(c->num_sms, c->num_tiles));
   c->inst_ready = true;
-  return ETAC_OK;
+  return build_tiles(c, s);
 }
 
 bool tensor_core_shapes_ok(const etac_ctx* c) {
@@ -351,6 +382,22 @@ void fill_gemm_common(etac_ctx* c, etac::GemmParams& g) {
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
 }
 
+// B-operand tensor map of the forward GEMM carries the tile shape (box rows = 3 x instances)
+etac_status encode_fwd_maps(etac_ctx* c) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  etac::GemmParams& g = c->gemm;
+  for (int t = 0; t < c->T; ++t) {
+    const int n = c->type_n[t];
+    const char* om = reinterpret_cast<const char*>(c->d_omega_bf16) + 2 * (size_t)c->omega_off[t];
+    const char* bt = reinterpret_cast<const char*>(c->d_bt) + 2 * (size_t)c->bt_off_h[t];
+    if (!encode_bf16_2d(fn, &g.tmA[t], om, n, n, 128) ||
+        !encode_bf16_2d(fn, &g.tmB[t], bt, n, std::max(1, 3 * c->ninst_h[t]), 3 * c->gemm_gi))
+      return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
+  }
+  return ETAC_OK;
+}
+
 // Buffers and tensor maps of the BF16 tensor-core forward (once per context).
 etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (c->bf16_ready) return ETAC_OK;
@@ -373,18 +420,9 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
   if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
   if (e != cudaSuccess) return cuda_fail(c, e, "BF16 buffers");
-  EncodeTiledFn fn = get_encode_fn();
-  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
   etac::GemmParams& g = c->gemm;
   memset(&g, 0, sizeof g);
-  for (int t = 0; t < c->T; ++t) {
-    const int n = c->type_n[t];
-    const char* om = reinterpret_cast<const char*>(c->d_omega_bf16) + 2 * (size_t)c->omega_off[t];
-    const char* bt = reinterpret_cast<const char*>(c->d_bt) + 2 * (size_t)c->bt_off_h[t];
-    if (!encode_bf16_2d(fn, &g.tmA[t], om, n, n, 128) ||
-        !encode_bf16_2d(fn, &g.tmB[t], bt, n, std::max(1, 3 * c->ninst_h[t]), 192))
-      return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
-  }
+  if ((st = encode_fwd_maps(c)) != ETAC_OK) return st;
   fill_gemm_common(c, g);
   g.h0bf16 = c->d_h0bf16;
   g.negbeta = c->d_negbeta;
@@ -397,16 +435,32 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   return ETAC_OK;
 }
 
-// Buffers and tensor maps of the staged batched reverse mode (once per context).
-etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
-  if (c->bwdb_ready) return ETAC_OK;
-  etac_status st = setup_instances(c, s);
-  if (st != ETAC_OK) return st;
-  const int np = c->E * c->P;
-  const size_t tn = (size_t)c->type_off[c->T];
-  const size_t om = (size_t)c->omega_off[c->T];
-  // decoder-reverse groups (64 instances each), heaviest types first
-  std::vector<etac::R3Group> groups;
+// B-operand tensor maps of the reverse-mode GEMMs (box rows = 3 x instances per tile)
+etac_status encode_bwd_maps(etac_ctx* c) {
+  EncodeTiledFn fn = get_encode_fn();
+  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  for (int which = 0; which < 2; ++which) {
+    etac::GemmParams& g = which == 0 ? c->gemm_bu : c->gemm_ba;
+    const char* ah = reinterpret_cast<const char*>(which == 0 ? c->d_om_hi : c->d_dom_hi);
+    const char* al = reinterpret_cast<const char*>(which == 0 ? c->d_om_lo : c->d_dom_lo);
+    for (int t = 0; t < c->T; ++t) {
+      const int n = c->type_n[t];
+      const size_t oo = 2 * (size_t)c->omega_off[t], bo = 2 * (size_t)c->bt_off_h[t];
+      const uint64_t rows = std::max(1, 3 * c->ninst_h[t]);
+      const uint32_t box = 3 * c->gemm_gi;
+      if (!encode_bf16_2d(fn, &g.tmA[t], ah + oo, n, n, 128) ||
+          !encode_bf16_2d(fn, &g.tmA2[t], al + oo, n, n, 128) ||
+          !encode_bf16_2d(fn, &g.tmB[t], reinterpret_cast<const char*>(c->d_bg_hi) + bo, n, rows, box) ||
+          !encode_bf16_2d(fn, &g.tmB2[t], reinterpret_cast<const char*>(c->d_bg_lo) + bo, n, rows, box))
+        return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
+    }
+  }
+  return ETAC_OK;
+}
+
+// Decoder-reverse work units: (pad type, 64-instance group, node range).  range 0 picks 256
+// nodes, halved (down to 16) until there are at least four units per SM.
+etac_status build_r3(etac_ctx* c, int range, cudaStream_t s) {
   std::vector<long long> a3_toff(c->T, 0);
   std::vector<int> a3_tg(c->T, 0);
   long long a3tot = 0;
@@ -415,15 +469,17 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
     a3_tg[t] = (c->ninst_h[t] + 63) / 64;
     a3tot += (long long)a3_tg[t] * c->type_n[t] * etac::H;
   }
-  // node range per work unit: 256 nodes, halved (down to 16) until there are at least four
-  // units per SM
-  int range = etac::R3_RANGE;
   auto units = [&](int rg) {
     long long u = 0;
     for (int t = 0; t < c->T; ++t) u += (long long)a3_tg[t] * ((c->type_n[t] + rg - 1) / rg);
     return u;
   };
-  while (range > 16 && units(range) < 4LL * c->num_sms) range /= 2;
+  if (range <= 0) {
+    range = etac::R3_RANGE;
+    while (range > 16 && units(range) < 4LL * c->num_sms) range /= 2;
+  }
+  if (range % 16 != 0 || range < 16 || range > etac::R3_RANGE)
+    return fail(c, ETAC_ERR_INVALID_ARG, "decoder-reverse node range must be 16..256 in steps of 16");
   std::vector<long long> s_toff(c->T, 0);
   std::vector<int> s_nr(c->T, 0);
   long long stot = 0;
@@ -432,6 +488,7 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
     s_nr[t] = (c->type_n[t] + range - 1) / range;
     stot += (long long)s_nr[t] * c->ninst_h[t];
   }
+  std::vector<etac::R3Group> groups;
   for (int t = 0; t < c->T; ++t)
     for (int g = 0; g < a3_tg[t]; ++g)
       for (int r = 0; r < s_nr[t]; ++r)
@@ -440,11 +497,51 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   std::stable_sort(groups.begin(), groups.end(), [](const etac::R3Group& x, const etac::R3Group& y) {
     return x.i1 - x.i0 > y.i1 - y.i0;   // largest units first
   });
+  cudaError_t e = cudaSuccess;
+  auto grow = [&](auto** ptr, size_t& cap, size_t need) {
+    if (e != cudaSuccess || need <= cap) return;
+    if (*ptr) cudaFree(*ptr);
+    *ptr = nullptr;
+    e = dalloc(ptr, need);
+    cap = e == cudaSuccess ? need : 0;
+  };
+  grow(&c->d_r3g, c->r3g_cap, groups.size());
+  grow(&c->d_spart, c->spart_cap, (size_t)stot * etac::H);
+  grow(&c->d_d2part, c->d2_cap, groups.size() * 3 * etac::H);
+  if (e == cudaSuccess && !c->d_a3part) e = dalloc(&c->d_a3part, (size_t)a3tot);
+  if (e == cudaSuccess && !c->d_a3_toff) e = dalloc(&c->d_a3_toff, (size_t)c->T);
+  if (e == cudaSuccess && !c->d_a3_tg) e = dalloc(&c->d_a3_tg, (size_t)c->T);
+  if (e == cudaSuccess && !c->d_s_toff) e = dalloc(&c->d_s_toff, (size_t)c->T);
+  if (e == cudaSuccess && !c->d_s_nr) e = dalloc(&c->d_s_nr, (size_t)c->T);
+  if (e == cudaSuccess && !groups.empty())
+    e = cudaMemcpyAsync(c->d_r3g, groups.data(), sizeof(etac::R3Group) * groups.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_toff, a3_toff.data(), sizeof(long long) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_tg, a3_tg.data(), sizeof(int) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_toff, s_toff.data(), sizeof(long long) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_nr, s_nr.data(), sizeof(int) * c->T,
+                                            cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  if (e != cudaSuccess) return cuda_fail(c, e, "decoder-reverse work units");
   c->r3_parts = (int)groups.size();
+  c->r3_range = range;
+  return ETAC_OK;
+}
+
+// Buffers and tensor maps of the staged batched reverse mode (once per context).
+etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
+  if (c->bwdb_ready) return ETAC_OK;
+  etac_status st = setup_instances(c, s);
+  if (st != ETAC_OK) return st;
+  const int np = c->E * c->P;
+  const size_t tn = (size_t)c->type_off[c->T];
+  const size_t om = (size_t)c->omega_off[c->T];
   c->r4_parts = 4 * 2 * c->num_sms;                     // warps of the R4 grid
   c->r4b_parts = (np + 63) / 64;
   c->r5_parts = (int)((tn + 63) / 64);
-  c->alpha_parts = c->gemm_grid;
   cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_om_hi), 2 * om);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_om_lo), 2 * om);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_dom_hi), 2 * om);
@@ -453,54 +550,22 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bg_lo), 2 * (size_t)c->bt_total);
   if (e == cudaSuccess) e = dalloc(&c->d_pr, (size_t)np * etac::PR_STRIDE);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_m, (size_t)np);
-  if (e == cudaSuccess) e = dalloc(&c->d_r3g, groups.size());
-  if (e == cudaSuccess) e = dalloc(&c->d_a3part, (size_t)a3tot);
-  if (e == cudaSuccess) e = dalloc(&c->d_a3_toff, (size_t)c->T);
-  if (e == cudaSuccess) e = dalloc(&c->d_a3_tg, (size_t)c->T);
   if (e == cudaSuccess) e = dalloc(&c->d_a3, tn * etac::H);
-  if (e == cudaSuccess) e = dalloc(&c->d_spart, (size_t)stot * etac::H);
-  if (e == cudaSuccess) e = dalloc(&c->d_s_toff, (size_t)c->T);
-  if (e == cudaSuccess) e = dalloc(&c->d_s_nr, (size_t)c->T);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_toff, s_toff.data(), sizeof(long long) * c->T,
-                                            cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_s_nr, s_nr.data(), sizeof(int) * c->T,
-                                            cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = dalloc(&c->d_d2part, (size_t)c->r3_parts * 3 * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_r4part, (size_t)c->r4_parts * (etac::OFF_B2 + etac::H - etac::OFF_W1));
   if (e == cudaSuccess) e = dalloc(&c->d_r4bpart, (size_t)c->r4b_parts * (etac::OFF_W4 - etac::OFF_WG));
   if (e == cudaSuccess) e = dalloc(&c->d_r5part, (size_t)c->r5_parts * (etac::OFF_W4 - etac::OFF_W1));
-  if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->alpha_parts);
+  if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->num_sms);   // >= GEMM grid
   if (e == cudaSuccess) e = dalloc(&c->d_gsum_part, (size_t)c->r4b_parts * 3);
-  if (e == cudaSuccess && !groups.empty())
-    e = cudaMemcpyAsync(c->d_r3g, groups.data(), sizeof(etac::R3Group) * groups.size(),
-                        cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_toff, a3_toff.data(), sizeof(long long) * c->T,
-                                            cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaMemcpyAsync(c->d_a3_tg, a3_tg.data(), sizeof(int) * c->T,
-                                            cudaMemcpyHostToDevice, s);
-  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) return cuda_fail(c, e, "reverse-mode buffers");
-  EncodeTiledFn fn = get_encode_fn();
-  if (!fn) return fail(c, ETAC_ERR_CUDA, "cuTensorMapEncodeTiled is not available");
+  if ((st = build_r3(c, c->r3_range, s)) != ETAC_OK) return st;
   for (int which = 0; which < 2; ++which) {
     etac::GemmParams& g = which == 0 ? c->gemm_bu : c->gemm_ba;
     memset(&g, 0, sizeof g);
-    const char* ah = reinterpret_cast<const char*>(which == 0 ? c->d_om_hi : c->d_dom_hi);
-    const char* al = reinterpret_cast<const char*>(which == 0 ? c->d_om_lo : c->d_dom_lo);
-    for (int t = 0; t < c->T; ++t) {
-      const int n = c->type_n[t];
-      const size_t oo = 2 * (size_t)c->omega_off[t], bo = 2 * (size_t)c->bt_off_h[t];
-      const uint64_t rows = std::max(1, 3 * c->ninst_h[t]);
-      if (!encode_bf16_2d(fn, &g.tmA[t], ah + oo, n, n, 128) ||
-          !encode_bf16_2d(fn, &g.tmA2[t], al + oo, n, n, 128) ||
-          !encode_bf16_2d(fn, &g.tmB[t], reinterpret_cast<const char*>(c->d_bg_hi) + bo, n, rows, 192) ||
-          !encode_bf16_2d(fn, &g.tmB2[t], reinterpret_cast<const char*>(c->d_bg_lo) + bo, n, rows, 192))
-        return fail(c, ETAC_ERR_CUDA, "tensor map encoding failed for pad type %d", t);
-    }
     fill_gemm_common(c, g);
     g.inst_m = c->d_inst_m;
     g.alpha_part = c->d_alpha_part;   // ws_u / ws_du are bound at launch (allocated later)
   }
+  if ((st = encode_bwd_maps(c)) != ETAC_OK) return st;
   int per_sm = 0;
   e = etac::bwd_pad_occupancy(c->nmax, c->K, &per_sm);
   if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "reverse-mode pad kernel occupancy");
@@ -694,11 +759,11 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
         return fail(c, ETAC_ERR_STATE, "reverse-mode GEMM buffers are not set up");
     }
     int t0 = timing_begin(c, K_BWD_GEMM_U, s);
-    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U),
+    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U, c->gemm_gi),
               "reverse mode: propagation GEMM");
     timing_end(c, t0, s);
     t0 = timing_begin(c, K_BWD_GEMM_A, s);
-    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA),
+    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA, c->gemm_gi),
               "reverse mode: alpha GEMM");
     timing_end(c, t0, s);
   }
@@ -1019,7 +1084,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       g.use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
       g.use_r = c->model.mode != ETAC_MODE_LINEAR_ONLY;
       ts = timing_begin(c, K_GEMM, s);
-      ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s), "BF16 propagation GEMM launch");
+      ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s, etac::GEMM_FWD, c->gemm_gi), "BF16 propagation GEMM launch");
       timing_end(c, ts, s);
       c->has_forward = true;
       return ETAC_OK;
@@ -1110,6 +1175,105 @@ etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_
   ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
   timing_end(c, ts, s);
   return ETAC_OK;
+}
+
+etac_status etac_set_tuning(etac_ctx* c, const etac_tuning* t, void* stream) {
+  if (!c || !t) return fail(c, ETAC_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_model || c->model.algo != ETAC_ALGO_BATCHED)
+    return fail(c, ETAC_ERR_STATE, "tuning applies to a batched model");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (c->inst_ready) {
+    if ((t->gemm_inst_per_tile != 32 && t->gemm_inst_per_tile != 64) ||
+        (t->gemm_tile_order != 0 && t->gemm_tile_order != 1))
+      return fail(c, ETAC_ERR_INVALID_ARG, "GEMM shape: 32 or 64 instances, order 0 or 1");
+    c->gemm_gi = t->gemm_inst_per_tile;
+    c->gemm_order = t->gemm_tile_order;
+    etac_status st = build_tiles(c, s);
+    if (st == ETAC_OK && c->bf16_ready) st = encode_fwd_maps(c);
+    if (st == ETAC_OK && c->bwdb_ready) st = encode_bwd_maps(c);
+    if (st != ETAC_OK) return st;
+  }
+  if (c->bwdb_ready && t->bwd_node_range) return build_r3(c, t->bwd_node_range, s);
+  return ETAC_OK;
+}
+
+etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_out* out,
+                          const float* grad_disp, etac_tuning* r, void* stream) {
+  if (!c || !in || !out || !r) return fail(c, ETAC_ERR_INVALID_ARG, "NULL argument");
+  if (!c->has_model || c->model.algo != ETAC_ALGO_BATCHED)
+    return fail(c, ETAC_ERR_STATE, "autotuning needs a batched model");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  memset(r, 0, sizeof *r);
+  r->gemm_inst_per_tile = c->gemm_gi;
+  r->gemm_tile_order = c->gemm_order;
+  r->bwd_node_range = c->r3_range;
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  ETAC_CUDA(c, cudaEventCreate(&e0), "autotune events");
+  ETAC_CUDA(c, cudaEventCreate(&e1), "autotune events");
+  etac_status st = ETAC_OK;
+  auto timed = [&](auto&& once, int warm, int reps, float* ms) -> etac_status {
+    for (int i = 0; i < warm; ++i) {
+      etac_status q = once();
+      if (q != ETAC_OK) return q;
+    }
+    ETAC_CUDA(c, cudaEventRecord(e0, s), "autotune event");
+    for (int i = 0; i < reps; ++i) {
+      etac_status q = once();
+      if (q != ETAC_OK) return q;
+    }
+    ETAC_CUDA(c, cudaEventRecord(e1, s), "autotune event");
+    ETAC_CUDA(c, cudaEventSynchronize(e1), "autotune event");
+    ETAC_CUDA(c, cudaEventElapsedTime(ms, e0, e1), "autotune event");
+    *ms /= reps;
+    return ETAC_OK;
+  };
+  auto fwd = [&]() { return etac_step_forward(c, in, out, stream); };
+  auto bwd = [&]() { return etac_step_backward(c, grad_disp, nullptr, nullptr, nullptr, nullptr, stream); };
+  etac_tuning t = *r;
+  if (c->bf16_ready && c->model.precision == ETAC_PREC_BF16) {
+    const int cand[4][2] = {{64, 0}, {64, 1}, {32, 0}, {32, 1}};
+    int best = -1;
+    for (int k = 0; k < 4 && st == ETAC_OK; ++k) {
+      t.gemm_inst_per_tile = cand[k][0];
+      t.gemm_tile_order = cand[k][1];
+      t.bwd_node_range = 0;
+      if ((st = etac_set_tuning(c, &t, stream)) != ETAC_OK) break;
+      float ms = 0.f;
+      if ((st = timed(fwd, 2, 5, &ms)) != ETAC_OK) break;
+      r->fwd_cand[k][0] = cand[k][0];
+      r->fwd_cand[k][1] = cand[k][1];
+      r->fwd_ms[k] = ms;
+      r->num_fwd = k + 1;
+      if (best < 0 || ms < r->fwd_ms[best]) best = k;
+    }
+    if (st == ETAC_OK) {
+      t.gemm_inst_per_tile = cand[best][0];
+      t.gemm_tile_order = cand[best][1];
+      t.bwd_node_range = 0;
+      st = etac_set_tuning(c, &t, stream);
+      r->gemm_inst_per_tile = t.gemm_inst_per_tile;
+      r->gemm_tile_order = t.gemm_tile_order;
+    }
+  }
+  if (st == ETAC_OK && grad_disp && c->bwdb_ready && c->model.mode != ETAC_MODE_LINEAR_ONLY) {
+    st = fwd();
+    const int cand[4] = {32, 64, 128, 256};
+    int best = -1;
+    for (int k = 0; k < 4 && st == ETAC_OK; ++k) {
+      if ((st = build_r3(c, cand[k], s)) != ETAC_OK) break;
+      float ms = 0.f;
+      if ((st = timed(bwd, 1, 3, &ms)) != ETAC_OK) break;
+      r->bwd_cand[k] = cand[k];
+      r->bwd_ms[k] = ms;
+      r->num_bwd = k + 1;
+      if (best < 0 || ms < r->bwd_ms[best]) best = k;
+    }
+    if (st == ETAC_OK) st = build_r3(c, cand[best], s);
+  }
+  r->bwd_node_range = c->r3_range;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return st;
 }
 
 etac_status etac_pose_grad_to_quat(const float* poses, const float* twist_grad, float* pose_grad,

@@ -191,7 +191,8 @@ struct GemmParams {
 };
 
 enum { GEMM_FWD = 0, GEMM_BWD_U = 1, GEMM_BWD_ALPHA = 2 };
-cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode = GEMM_FWD);
+// gi: instances per tile (32 or 64; the tile list and B-operand tensor maps must match)
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode, int gi);
 size_t prop_gemm_smem_bytes();
 
 }  // namespace etac

@@ -31,41 +31,45 @@ using namespace sm100;
 namespace {
 
 constexpr int GM = 128;                 // node rows per tile
-constexpr int GI = 64;                  // instances per tile
-constexpr int GN = 3 * GI;              // 192 accumulator columns
 constexpr int GK = 64;                  // nodes per K block (128 B of BF16)
 constexpr int STAGES = 3;
 constexpr int EPI_WARPS = 16;
 constexpr int TMA_WARP = 16, MMA_WARP = 17;
 constexpr int THREADS = 18 * 32;
 constexpr int A_BYTES = GM * GK * 2;    // 16 KiB
-constexpr int B_BYTES = GN * GK * 2;    // 24 KiB
 constexpr uint32_t TMEM_COLS = 512;
 constexpr uint32_t ACC_STRIDE = 256;    // column offset of accumulator 1
-constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
-
-// shared-memory layout (offsets from a 1024-byte aligned base)
 constexpr int DEC = 2;                  // instances per decoder pass (independent MMA chains)
-constexpr int INST_PER_WARP = GI / (EPI_WARPS / 4);
-constexpr size_t SM_A = 0;
-constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
-// per-tile epilogue records, double-buffered (filled one tile ahead with cp.async):
-// -beta (fragment order), (c0, m), node bases, contact words, h0 rows (16-byte chunks
-// XOR-swizzled by row so fragment reads are conflict-free)
-constexpr size_t STG_NB = 0;                                      // 64 x 64 BF16
-constexpr size_t STG_C0 = STG_NB + (size_t)GI * H * 2;            // 64 x float4
-constexpr size_t STG_BASE = STG_C0 + (size_t)GI * 16;             // 64 x int64
-constexpr size_t STG_BITS = STG_BASE + (size_t)GI * 8;            // 64 x 4 words
-constexpr size_t STG_H0 = STG_BITS + (size_t)GI * 16;             // 128 rows x 128 B
-constexpr size_t STG_BYTES = STG_H0 + (size_t)GM * 128;
-constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;          // 16 warps x DEC x 32 x float4
-constexpr size_t SM_STG = SM_R + (size_t)EPI_WARPS * DEC * 32 * 16;
-constexpr size_t SM_BAR = SM_STG + 2 * STG_BYTES;                 // barriers
-constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
-constexpr size_t SM_TOTAL = SM_MISC + 16;
-constexpr size_t SM_ALLOC = SM_TOTAL + 1024;                      // alignment slack
-static_assert(STG_H0 % 128 == 0, "h0 staging rows must be 128-byte aligned");
-static_assert(SM_ALLOC <= 227 * 1024, "shared memory budget");
+
+// Shapes and shared-memory layout (offsets from a 1024-byte aligned base) of a tile of GIT
+// instances (N = 3 GIT accumulator columns).  Per-tile epilogue records are double-buffered
+// (filled one tile ahead with cp.async): -beta (fragment order), (c0, m), node bases, contact
+// words, h0 rows (16-byte chunks XOR-swizzled by row so fragment reads are conflict-free).
+template <int GIT>
+struct GemmShape {
+  static constexpr int GI = GIT;
+  static constexpr int GN = 3 * GI;
+  static constexpr int B_BYTES = GN * GK * 2;
+  static constexpr uint32_t IDESC = sm100::idesc_bf16_f32(GM, GN);
+  static constexpr int INST_PER_WARP = GI / (EPI_WARPS / 4);
+  static constexpr size_t SM_A = 0;
+  static constexpr size_t SM_B = SM_A + (size_t)STAGES * A_BYTES;
+  static constexpr size_t STG_NB = 0;                                  // GI x 64 BF16
+  static constexpr size_t STG_C0 = STG_NB + (size_t)GI * H * 2;        // GI x float4
+  static constexpr size_t STG_BASE = STG_C0 + (size_t)GI * 16;         // GI x int64
+  static constexpr size_t STG_BITS = STG_BASE + (size_t)GI * 8;        // GI x 4 words
+  static constexpr size_t STG_H0 = STG_BITS + (size_t)GI * 16;         // 128 rows x 128 B
+  static constexpr size_t STG_BYTES = STG_H0 + (size_t)GM * 128;
+  static constexpr size_t SM_R = SM_B + (size_t)STAGES * B_BYTES;      // EPI_WARPS x DEC x 32 x float4
+  static constexpr size_t SM_STG = SM_R + (size_t)EPI_WARPS * DEC * 32 * 16;
+  static constexpr size_t SM_BAR = SM_STG + 2 * STG_BYTES;
+  static constexpr size_t SM_MISC = SM_BAR + 8 * (2 * STAGES + 6);
+  static constexpr size_t SM_TOTAL = SM_MISC + 16;
+  static constexpr size_t SM_ALLOC = SM_TOTAL + 1024;                  // alignment slack
+  static_assert(STG_H0 % 128 == 0, "h0 staging rows must be 128-byte aligned");
+  static_assert(SM_ALLOC <= 227 * 1024, "shared memory budget");
+  static_assert(INST_PER_WARP % 4 == 0, "TMEM loads take four instances at a time");
+};
 
 __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
   __nv_bfloat162 v = __floats2bfloat162_rn(lo, hi);
@@ -77,9 +81,18 @@ __device__ __forceinline__ uint32_t pack_bf16x2(float lo, float hi) {
 // FP32-level accuracy): GEMM_BWD_U adds sum_i Omega_ij G_i to dL/du_hat of every active node j;
 // GEMM_BWD_ALPHA accumulates sum_j u_hat_j . sum_i d_ij Omega_ij G_i into per-CTA partials
 // (dL/dalpha is minus their sum).
-template <int MODE>
+template <int MODE, int GIT>
 __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_constant__ GemmParams p) {
   constexpr int SEG = MODE == GEMM_FWD ? 1 : 3;
+  using S = GemmShape<GIT>;
+  constexpr int GI = S::GI;
+  constexpr int B_BYTES = S::B_BYTES;
+  constexpr uint32_t IDESC = S::IDESC;
+  constexpr int INST_PER_WARP = S::INST_PER_WARP;
+  constexpr size_t SM_A = S::SM_A, SM_B = S::SM_B, SM_R = S::SM_R, SM_STG = S::SM_STG,
+                   SM_BAR = S::SM_BAR, SM_MISC = S::SM_MISC;
+  constexpr size_t STG_NB = S::STG_NB, STG_C0 = S::STG_C0, STG_BASE = S::STG_BASE,
+                   STG_BITS = S::STG_BITS, STG_H0 = S::STG_H0, STG_BYTES = S::STG_BYTES;
   extern __shared__ unsigned char smem_raw[];
   unsigned char* smem = reinterpret_cast<unsigned char*>(
       (reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -466,26 +479,32 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
 
 }  // namespace
 
-size_t prop_gemm_smem_bytes() { return SM_ALLOC; }
+size_t prop_gemm_smem_bytes() { return GemmShape<64>::SM_ALLOC; }
 
-template <int MODE>
+template <int MODE, int GIT>
 cudaError_t launch_mode(const GemmParams& p, int grid, cudaStream_t s) {
   static bool configured = false;
+  constexpr size_t smem = GemmShape<GIT>::SM_ALLOC;
   if (!configured) {
-    cudaError_t e = cudaFuncSetAttribute(prop_gemm_kernel<MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)SM_ALLOC);
+    cudaError_t e = cudaFuncSetAttribute(prop_gemm_kernel<MODE, GIT>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = true;
   }
-  prop_gemm_kernel<MODE><<<grid, THREADS, SM_ALLOC, s>>>(p);
+  prop_gemm_kernel<MODE, GIT><<<grid, THREADS, smem, s>>>(p);
   return cudaGetLastError();
 }
 
-cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode) {
-  if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U>(p, grid, s);
-  if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA>(p, grid, s);
-  return launch_mode<GEMM_FWD>(p, grid, s);
+cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int mode, int gi) {
+  if (gi == 32) {
+    if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U, 32>(p, grid, s);
+    if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA, 32>(p, grid, s);
+    return launch_mode<GEMM_FWD, 32>(p, grid, s);
+  }
+  if (gi != 64) return cudaErrorInvalidValue;
+  if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U, 64>(p, grid, s);
+  if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA, 64>(p, grid, s);
+  return launch_mode<GEMM_FWD, 64>(p, grid, s);
 }
 
 }  // namespace etac

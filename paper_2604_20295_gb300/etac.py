@@ -27,7 +27,9 @@ HIDDEN = 64
 EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
            "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
            "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
-           "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat")
+           "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
+           "etac_autotune", "etac_set_tuning")
+TUNE_MAX = 8
 
 _vp = ctypes.c_void_p
 
@@ -45,6 +47,14 @@ class etac_model_desc(ctypes.Structure):
 
 class etac_step_in(ctypes.Structure):
     _fields_ = [("obj_type", _vp), ("obj_dims", _vp), ("obj_pose", _vp), ("pad_pose", _vp)]
+
+
+class etac_tuning(ctypes.Structure):
+    _fields_ = [("gemm_inst_per_tile", ctypes.c_int32), ("gemm_tile_order", ctypes.c_int32),
+                ("bwd_node_range", ctypes.c_int32), ("num_fwd", ctypes.c_int32),
+                ("fwd_cand", (ctypes.c_int32 * 2) * 8), ("fwd_ms", ctypes.c_float * 8),
+                ("num_bwd", ctypes.c_int32), ("bwd_cand", ctypes.c_int32 * 8),
+                ("bwd_ms", ctypes.c_float * 8)]
 
 
 class etac_step_out(ctypes.Structure):
@@ -106,6 +116,11 @@ def lib():
         L.etac_enable_timing.argtypes = [_vp, ctypes.c_int32]
         L.etac_kernel_times.restype = ctypes.c_int
         L.etac_kernel_times.argtypes = [_vp, _vp, ctypes.c_int32, ctypes.POINTER(ctypes.c_int32)]
+        L.etac_autotune.restype = ctypes.c_int
+        L.etac_autotune.argtypes = [_vp, ctypes.POINTER(etac_step_in), ctypes.POINTER(etac_step_out),
+                                    _vp, ctypes.POINTER(etac_tuning), _vp]
+        L.etac_set_tuning.restype = ctypes.c_int
+        L.etac_set_tuning.argtypes = [_vp, ctypes.POINTER(etac_tuning), _vp]
         L.etac_pose_grad_to_quat.restype = ctypes.c_int
         L.etac_pose_grad_to_quat.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
         L.etac_step_forward_noalloc.restype = ctypes.c_int
@@ -178,6 +193,24 @@ def etac_destroy(ctx: int) -> None:
 
 def etac_enable_timing(ctx: int, enable: bool = True) -> None:
     _check(ctx, lib().etac_enable_timing(ctx, int(bool(enable))), "etac_enable_timing")
+
+
+def etac_autotune(ctx: int, step_in, step_out, grad_disp: int = 0, stream: int = 0) -> etac_tuning:
+    r = etac_tuning()
+    _check(ctx, lib().etac_autotune(ctx, ctypes.byref(step_in), ctypes.byref(step_out),
+                                    grad_disp or None, ctypes.byref(r), stream), "etac_autotune")
+    return r
+
+
+def etac_set_tuning(ctx: int, tuning: etac_tuning, stream: int = 0) -> None:
+    _check(ctx, lib().etac_set_tuning(ctx, ctypes.byref(tuning), stream), "etac_set_tuning")
+
+
+def tuning_dict(t: etac_tuning) -> dict:
+    return {"gemm_inst_per_tile": t.gemm_inst_per_tile, "gemm_tile_order": t.gemm_tile_order,
+            "bwd_node_range": t.bwd_node_range,
+            "fwd": [(t.fwd_cand[k][0], t.fwd_cand[k][1], round(t.fwd_ms[k], 4)) for k in range(t.num_fwd)],
+            "bwd": [(t.bwd_cand[k], round(t.bwd_ms[k], 4)) for k in range(t.num_bwd)]}
 
 
 def etac_kernel_times(ctx: int) -> dict:
@@ -284,6 +317,20 @@ class TactileSim:
                            ptr("params"), torch.cuda.current_stream(self.device).cuda_stream)
         self._grad_keepalive = g
         return out
+
+    def autotune(self, grad_disp=None) -> dict:
+        """Times the tile / block shape candidates on this scene's step (and, given an upstream
+        gradient, the reverse mode's node ranges) and keeps the fastest."""
+        g = None if grad_disp is None else grad_disp.contiguous().to(self.torch.float32)
+        t = etac_autotune(self.ctx, self.step_in(), self.step_out(),
+                          0 if g is None else g.data_ptr(),
+                          self.torch.cuda.current_stream(self.device).cuda_stream)
+        return tuning_dict(t)
+
+    def set_tuning(self, inst_per_tile=64, tile_order=0, bwd_node_range=0):
+        t = etac_tuning()
+        t.gemm_inst_per_tile, t.gemm_tile_order, t.bwd_node_range = inst_per_tile, tile_order, bwd_node_range
+        etac_set_tuning(self.ctx, t, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def poll_status(self) -> int:
         return etac_poll_status(self.ctx, self.torch.cuda.current_stream(self.device).cuda_stream)
