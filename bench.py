@@ -200,6 +200,52 @@ def executed_gemm_flops(scene):
     return float((2.0 * n * n * 3.0).sum())
 
 
+def bwd_rooflines(ktimes, scene, work, peaks, nsm):
+    """Per-stage time and roofline of the staged reverse mode.  Algorithmic work per stage (what
+    the reverse of the method needs, not the implementation's recomputation or split products):
+      pad stage   -- read dL/dU (12 B per node), write the passive gradient as the propagation
+                     reverse's operand (BF16, 6 B per node) and u_hat / phi of active nodes
+                     (16 B): HBM;
+      decoder     -- per passive node dz = D2^T g (384 FLOP), dD2 (384 FLOP), the S and A3
+                     sums (128 FLOP): FP32 ALU; its A3 sums read the partials (4 B per type
+                     node and channel per group; counted once per node: HBM);
+      pad reverse -- per pad D1_g^T S and G1^T dag (16.4 kFLOP) and at most 64 routed nodes'
+                     E2 / E1 reverse (2 x (64 + 576 + 192) FLOP per routed channel): FP32 ALU;
+      pad sums    -- per pad the outer products S g^T, dag g0^T (16.4 kFLOP) and dA2 h1^T
+                     (8.2 kFLOP): FP32 ALU;
+      GEMMs       -- 6 FLOP per (passive, active) pair each (dL/du_hat and d alpha): tensor;
+      outputs     -- read the propagated dL/du_hat and write dL/du_hat, dL/dpen (28 B per
+                     node): HBM.
+    FP32 ALU peak = SMs x 128 lanes x 2 FLOP x max SM clock."""
+    nodes = float(scene.total_nodes)
+    npads = float(scene.num_envs * scene.pads_per_env)
+    alu = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    spec = {"bwd_pad_kernel": ("hbm", 18.0 * nodes + 16.0 * work["active"]),
+            "bwd_global_kernel": ("alu", npads * 2.0 * 2 * H * H),
+            "bwd_decoder_kernel": ("alu", 896.0 * work["passive"]),
+            "bwd_reduce_a3_kernel": ("hbm", 4.0 * H * nodes),
+            "bwd_padrev_kernel": ("alu", npads * (2.0 * 2 * H * H + H * 2.0 * (64 + 576 + 192))),
+            "bwd_padsum_kernel": ("alu", npads * (2.0 * 2 * H * H + 2.0 * H * H)),
+            "prop_gemm_kernel<bwd_u>": ("tensor", 6.0 * work["pairs"]),
+            "prop_gemm_kernel<bwd_alpha>": ("tensor", 6.0 * work["pairs"]),
+            "bwd_pose_kernel(+param sums)": ("hbm", 28.0 * nodes)}
+    out = {}
+    for name, (launches, ms) in ktimes.items():
+        t = ms / max(launches, 1) / 1e3
+        ent = {"ms": t * 1e3}
+        if name in spec and t > 0:
+            bound, w = spec[name]
+            if bound == "hbm":
+                a, p, u = w / t / 1e9, peaks["hbm_gbs"], "GB/s"
+            elif bound == "tensor":
+                a, p, u = w / t / 1e12, peaks["bf16_tflops"], "TFLOP/s"
+            else:
+                a, p, u = w / t / 1e12, alu, "TFLOP/s"
+            ent.update(bound=bound, achieved=a, peak=p, unit=u, frac=a / p)
+        out[name] = ent
+    return out
+
+
 def _stats(got, ref_disp, mask_got, mask_ref):
     d = np.linalg.norm(got.astype(np.float64) - ref_disp, axis=1)
     return {"max_abs_mm": float(d.max()), "rms_mm": float(np.sqrt((d ** 2).mean())),
@@ -357,6 +403,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-bwd", action="store_true")
+    ap.add_argument("--no-graph", action="store_true",
+                    help="time eager launches only (default: the step replayed from a CUDA graph)")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the default tile / block shapes instead of measuring them")
     ap.add_argument("--no-configs", action="store_true",
@@ -415,17 +463,58 @@ def main():
     step_ms = timed_steps(sim, args.steps, stream, flush, torch, step_kw)
     if pg:
         pg.barrier()
-    clk = clocks.stop()
     ktimes = X.etac_kernel_times(sim.ctx)
     X.etac_enable_timing(sim.ctx, False)
-    total_s = sum(step_ms) / 1e3
-    if pg:
-        t = torch.tensor([total_s], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        total_s = float(t)
+
+    def max_over_ranks(x):
+        if pg:
+            t = torch.tensor([x], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            x = float(t)
+        return x
+
     nodes = scene.total_nodes
-    value = nodes * args.steps * world / total_s
-    ms_per_step = 1e3 * total_s / args.steps
+    eager_s = max_over_ranks(sum(step_ms) / 1e3)
+    eager = {"value": nodes * args.steps * world / eager_s, "unit": UNIT,
+             "ms_per_step": 1e3 * eager_s / args.steps}
+
+    # ---- the same step captured once in a CUDA graph and replayed K times (the headline)
+    graph = None
+    if not args.no_graph:
+        gs = torch.cuda.Stream(dev)
+        gs.wait_stream(stream)
+        with torch.cuda.stream(gs):
+            sim.step(**step_kw)
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(cg, stream=gs):
+                sim.step(**step_kw)
+        stream.wait_stream(gs)
+        for _ in range(max(3, args.warmup)):
+            cg.replay()
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        for k in range(args.steps):
+            flush.fill_(k & 0xFF)
+            starts[k].record(stream)
+            cg.replay()
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        if pg:
+            pg.barrier()
+        g_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        graph_s = max_over_ranks(sum(g_ms) / 1e3)
+        graph = {"value": nodes * args.steps * world / graph_s, "unit": UNIT,
+                 "ms_per_step": 1e3 * graph_s / args.steps, "launches_per_step":
+                 int(sum(v[0] for v in ktimes.values()) // max(args.steps, 1))}
+        step_ms = g_ms
+        del cg
+    clk = clocks.stop()
+    head = graph or eager
+    value = head["value"]
+    ms_per_step = head["ms_per_step"]
 
     # ---- end to end through the public API with host buffers
     e2e = None
@@ -478,6 +567,8 @@ def main():
         compare[f"{args.precision}_{args.algo}"] = {"value": value, "unit": UNIT,
                                                     "ms_per_step": ms_per_step}
 
+    peaks_early, _ = _peaks()
+    nsm_early = torch.cuda.get_device_properties(dev).multi_processor_count
     # ---- reverse mode (FP32 adjoint): bwd/fwd on this workload and on the 1,024-env layout
     # of 16x16 flat pads (forward FP32 batched there)
     bwd = None
@@ -501,6 +592,14 @@ def main():
         G = torch.randn(sim.disp.shape, device=dev, generator=gen)
         sim.step(**step_kw)
         b_ms = time_bwd(sim, G, 3)
+        # per-stage times of one more reverse pass (events around each stage's launches)
+        X.etac_enable_timing(sim.ctx, True)
+        flush.fill_(2)
+        sim.backward(G)
+        torch.cuda.synchronize()
+        bk = X.etac_kernel_times(sim.ctx)
+        X.etac_enable_timing(sim.ctx, False)
+        bwd_stages = bwd_rooflines(bk, scene, work, peaks_early, nsm_early)
         small = I.sphere_press_scene(1024, seed=7)
         s4 = X.TactileSim(small, device=dev)
         s4.set_model(theta, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
@@ -511,7 +610,8 @@ def main():
         b4 = time_bwd(s4, G4, 10)
         s4.close()
         bwd = {"workload": {"fwd_ms": ms_per_step, "bwd_ms": b_ms, "bwd_fwd": b_ms / ms_per_step,
-                            "fwd": f"{args.precision} {args.algo}", "bwd": "fp32 adjoint"},
+                            "fwd": f"{args.precision} {args.algo}", "bwd": "fp32 adjoint",
+                            "stages": bwd_stages},
                "flat16x16_1024env": {"fwd_ms": sum(f4) / len(f4), "bwd_ms": b4,
                                      "bwd_fwd": b4 / (sum(f4) / len(f4)),
                                      "fwd": "fp32 batched", "bwd": "fp32 adjoint"}}
@@ -621,6 +721,7 @@ def main():
             "roofline_by_kernel": roof_all,
             "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": int(sum(v["launches"] for v in kern.values())),
+            "eager": eager, "graph": graph,
             "clocks": clk, "error_vs_oracle": err, "rungs": compare, "kernels": kern,
             "bwd_fwd": bwd, "configs": configs,
             "active_fraction": work["active"] / nodes,

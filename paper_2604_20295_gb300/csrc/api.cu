@@ -131,13 +131,15 @@ namespace {
 const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_kernel<fp32>",
                               "front_contact_kernel", "prop_gemm_kernel", "front_global_kernel",
                               "backward_kernel", "pad_obj_kernel", "bwd_pad_kernel",
-                              "bwd_global_kernel", "bwd_decoder_kernel(+a3 sums)",
-                              "bwd_padrev_kernel(+pad sums)", "bwd_typenode_kernel",
+                              "bwd_global_kernel", "bwd_decoder_kernel",
+                              "bwd_padrev_kernel", "bwd_typenode_kernel",
                               "prop_gemm_kernel<bwd_u>", "prop_gemm_kernel<bwd_alpha>",
-                              "bwd_pose_kernel(+param sums)"};
+                              "bwd_pose_kernel(+param sums)", "bwd_reduce_a3_kernel",
+                              "bwd_padsum_kernel"};
 enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_PADOBJ = 6,
        K_BWD_PAD = 7, K_BWD_GLOBAL = 8, K_BWD_DECODER = 9, K_BWD_PADREV = 10, K_BWD_TYPENODE = 11,
-       K_BWD_GEMM_U = 12, K_BWD_GEMM_A = 13, K_BWD_POSE = 14, K_COUNT = 15 };
+       K_BWD_GEMM_U = 12, K_BWD_GEMM_A = 13, K_BWD_POSE = 14, K_BWD_A3SUM = 15,
+       K_BWD_PADSUM = 16, K_COUNT = 17 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -539,7 +541,7 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   const int np = c->E * c->P;
   const size_t tn = (size_t)c->type_off[c->T];
   const size_t om = (size_t)c->omega_off[c->T];
-  c->r4_parts = 4 * 2 * c->num_sms;                     // warps of the R4 grid
+  c->r4_parts = 3 * c->num_sms;                         // CTAs of the R4 grid (8 warps each)
   c->r4b_parts = (np + 63) / 64;
   c->r5_parts = (int)((tn + 63) / 64);
   cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_om_hi), 2 * om);
@@ -551,8 +553,8 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_pr, (size_t)np * etac::PR_STRIDE);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_m, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_a3, tn * etac::H);
-  if (e == cudaSuccess) e = dalloc(&c->d_r4part, (size_t)c->r4_parts * (etac::OFF_B2 + etac::H - etac::OFF_W1));
-  if (e == cudaSuccess) e = dalloc(&c->d_r4bpart, (size_t)c->r4b_parts * (etac::OFF_W4 - etac::OFF_WG));
+  if (e == cudaSuccess) e = dalloc(&c->d_r4part, (size_t)c->r4_parts * (etac::OFF_W2 - etac::OFF_W1));
+  if (e == cudaSuccess) e = dalloc(&c->d_r4bpart, (size_t)c->r4b_parts * (etac::OFF_W4 - etac::OFF_W2));
   if (e == cudaSuccess) e = dalloc(&c->d_r5part, (size_t)c->r5_parts * (etac::OFF_W4 - etac::OFF_W1));
   if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->num_sms);   // >= GEMM grid
   if (e == cudaSuccess) e = dalloc(&c->d_gsum_part, (size_t)c->r4b_parts * 3);
@@ -747,7 +749,9 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   if (c->model.mode != ETAC_MODE_LINEAR_ONLY) {
     if ((st = stage(etac::BWD_STAGE_GLOBAL, K_BWD_GLOBAL, "reverse mode: global MLP")) != ETAC_OK ||
         (st = stage(etac::BWD_STAGE_DECODER, K_BWD_DECODER, "reverse mode: decoder")) != ETAC_OK ||
+        (st = stage(etac::BWD_STAGE_A3SUM, K_BWD_A3SUM, "reverse mode: decoder sums")) != ETAC_OK ||
         (st = stage(etac::BWD_STAGE_PADREV, K_BWD_PADREV, "reverse mode: pad reverse")) != ETAC_OK ||
+        (st = stage(etac::BWD_STAGE_PADSUM, K_BWD_PADSUM, "reverse mode: pad sums")) != ETAC_OK ||
         (st = stage(etac::BWD_STAGE_TYPENODE, K_BWD_TYPENODE, "reverse mode: type nodes")) != ETAC_OK)
       return st;
   }

@@ -18,9 +18,10 @@
 //      dD2 = sum G (x) ReLU(h0 + beta);
 //   R3b reduce the A3 partials in group order;
 //   R4 bwd_padrev_kernel (warp per pad): dg = D1_g^T S, dag = dg [ag > 0], dg0 = G1^T dag,
-//      routed to each channel's argmax node, and that node's encoder reverse (E1, E2, and
-//      for an active node dL/du_hat);
-//   R4b sums over pads of S g^T, dag g0^T, S and dag (D1_g, G1 and their biases);
+//      routed to each channel's argmax node as dA2, and the E1 reverse of those nodes (E1,
+//      b1, and for an active node dL/du_hat);
+//   R4b sums over 64-pad chunks of S g^T, dag g0^T, S, dag (D1_g, G1 and their biases) and
+//      of dA2 h1^T, dA2 (E2 and b2);
 //   R5 bwd_typenode_kernel (64 type nodes per CTA): the decoder path's encoder reverse from
 //      A3 (dD1_f, dE2, dE1, biases);
 //   R6 the propagation reverse on tensor cores (prop_gemm.cu, backward modes);
@@ -531,10 +532,10 @@ constexpr int R3_IPW = R3_INST / 8;
 constexpr int R3_NODES = 16;
 
 struct R3Smem {
-  float2 A3[8][R3_NODES][32];          // per-warp A3 of the current node chunk
-  float D2[8][3][H];                   // per-warp dD2 partials
-  float H0[R3_NODES][H];               // h0 rows of the chunk
-  float G[8][R3_IPW][R3_NODES * 3];    // per-warp dL/dU of the chunk
+  float2 A3[8][R3_NODES][32];            // per-warp A3 of the current node chunk
+  float D2[8][3][H];                     // per-warp dD2 partials
+  float H0[2][R3_NODES][H];              // h0 rows of the chunk (double buffer)
+  float4 G[2][8][R3_IPW][R3_NODES];      // per-warp dL/dU of the chunk, (x, y, z, -)
 };
 
 __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
@@ -542,8 +543,6 @@ __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
   R3Smem& sm = *reinterpret_cast<R3Smem*>(smem_r3);
   auto& sA3 = sm.A3;
   auto& sD2 = sm.D2;
-  auto& sH0 = sm.H0;
-  auto& sG = sm.G;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const R3Group grp = a.r3_groups[blockIdx.x];
   const int t = grp.type;
@@ -571,46 +570,71 @@ __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
     mofs[x] = (int)(a.type_woff[t] + (long long)(in ? k : 0) * nw);
     live |= lv ? 1u << x : 0u;
   }
-  float2 d2a = make_float2(0.f, 0.f), d2b = d2a, d2c = d2a;   // dD2 rows 0..2, my channels
-  for (int i0 = grp.i0; i0 < grp.i1; i0 += R3_NODES) {
-    const int cn = min(R3_NODES, grp.i1 - i0);   // nodes in this chunk
-    uint32_t word[R3_IPW];   // the chunk's contact bits of each instance
-#pragma unroll
-    for (int x = 0; x < R3_IPW; ++x)
-      word[x] = ((live >> x) & 1u) ? (a.maskbits[mofs[x] + (i0 >> 5)] >> (i0 & 31)) : 0xffffffffu;
-    // stage the chunk: h0 rows (whole CTA, 16-byte loads) and each warp's dL/dU rows
+  // stage chunk i0 into buffer b with cp.async: h0 rows (whole CTA, 16-byte copies) and this
+  // warp's dL/dU rows of its live instances (4-byte copies into (x, y, z, -) slots)
+  auto stage = [&](int i0, int b) {
+    const int cn = min(R3_NODES, grp.i1 - i0);
+    const float* h0src = a.h0tab + (size_t)(o + i0) * H;
     for (int e = threadIdx.x; e < cn * (H / 4); e += blockDim.x)
-      reinterpret_cast<float4*>(&sH0[0][0])[e] =
-          __ldg(reinterpret_cast<const float4*>(a.h0tab + (size_t)(o + i0) * H) + e);
+      sm100::cp_async16((uint32_t)__cvta_generic_to_shared(&sm.H0[b][0][0]) + 16 * e, h0src + 4 * e, 16);
 #pragma unroll
     for (int x = 0; x < R3_IPW; ++x) {
       if (!((live >> x) & 1u)) continue;
       const float* g = a.grad_disp + gofs[x] + 3 * i0;
-      for (int e = lane; e < 3 * cn; e += 32) sG[warp][x][e] = __ldg(g + e);
+      const uint32_t dst = (uint32_t)__cvta_generic_to_shared(&sm.G[b][warp][x][0]);
+      for (int e = lane; e < 3 * cn; e += 32) {
+        const int r = e / 3, q = e - 3 * r;
+        sm100::cp_async4(dst + 16 * r + 4 * q, g + e, 4);
+      }
+    }
+    sm100::cp_async_commit();
+  };
+  auto words = [&](int i0, uint32_t (&wd)[R3_IPW]) {   // the chunk's contact bits per instance
+#pragma unroll
+    for (int x = 0; x < R3_IPW; ++x)
+      wd[x] = ((live >> x) & 1u) ? (a.maskbits[mofs[x] + (i0 >> 5)] >> (i0 & 31)) : 0xffffffffu;
+  };
+  float2 d2a = make_float2(0.f, 0.f), d2b = d2a, d2c = d2a;   // dD2 rows 0..2, my channels
+  uint32_t word[R3_IPW];
+  if (grp.i0 < grp.i1) {
+    stage(grp.i0, 0);
+    words(grp.i0, word);
+  }
+  int buf = 0;
+  for (int i0 = grp.i0; i0 < grp.i1; i0 += R3_NODES, buf ^= 1) {
+    const int cn = min(R3_NODES, grp.i1 - i0);   // nodes in this chunk
+    const bool more = i0 + R3_NODES < grp.i1;
+    uint32_t wnext[R3_IPW];
+    if (more) {
+      stage(i0 + R3_NODES, buf ^ 1);
+      words(i0 + R3_NODES, wnext);
+      sm100::cp_async_wait_one();
+    } else {
+      sm100::cp_async_wait_all();
     }
     __syncthreads();
+    const float (&sH0)[R3_NODES][H] = sm.H0[buf];
+    const float4 (&sG)[R3_IPW][R3_NODES] = sm.G[buf][warp];
 #pragma unroll 2
     for (int r = 0; r < R3_NODES; ++r) {
-      const int i = i0 + r;
       float2 A3 = make_float2(0.f, 0.f);
       if (r < cn) {
         const float2 h0 = *reinterpret_cast<const float2*>(&sH0[r][2 * lane]);
 #pragma unroll
         for (int x = 0; x < R3_IPW; ++x) {
           if ((word[x] >> r) & 1u) continue;   // active node or no contact: no decoder term
-          const float g0 = sG[warp][x][3 * r], g1 = sG[warp][x][3 * r + 1],
-                      g2 = sG[warp][x][3 * r + 2];
-          float2 dz = __fmul2_rn(w4a, make_float2(g0, g0));
-          dz = __ffma2_rn(w4b, make_float2(g1, g1), dz);
-          dz = __ffma2_rn(w4c, make_float2(g2, g2), dz);
+          const float4 g = sG[x][r];
+          float2 dz = __fmul2_rn(w4a, make_float2(g.x, g.x));
+          dz = __ffma2_rn(w4b, make_float2(g.y, g.y), dz);
+          dz = __ffma2_rn(w4c, make_float2(g.z, g.z), dz);
           const float2 z = __fadd2_rn(h0, beta[x]);
           const float2 da = make_float2(z.x > 0.f ? dz.x : 0.f, z.y > 0.f ? dz.y : 0.f);
           const float2 rz = make_float2(relu(z.x), relu(z.y));
           S[x] = __fadd2_rn(S[x], da);
           A3 = __fadd2_rn(A3, da);
-          d2a = __ffma2_rn(make_float2(g0, g0), rz, d2a);
-          d2b = __ffma2_rn(make_float2(g1, g1), rz, d2b);
-          d2c = __ffma2_rn(make_float2(g2, g2), rz, d2c);
+          d2a = __ffma2_rn(make_float2(g.x, g.x), rz, d2a);
+          d2b = __ffma2_rn(make_float2(g.y, g.y), rz, d2b);
+          d2c = __ffma2_rn(make_float2(g.z, g.z), rz, d2c);
         }
       }
       sA3[warp][r][lane] = A3;
@@ -625,7 +649,10 @@ __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
       for (int w = 1; w < 8; ++w) s2 = __fadd2_rn(s2, sA3[w][r][l]);
       *reinterpret_cast<float2*>(a.a3part + grp.a3off + (size_t)(i0 + r) * H + 2 * l) = s2;
     }
-    __syncthreads();
+    if (more) {
+#pragma unroll
+      for (int x = 0; x < R3_IPW; ++x) word[x] = wnext[x];
+    }
   }
 #pragma unroll
   for (int x = 0; x < R3_IPW; ++x) {
@@ -648,46 +675,62 @@ __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
   }
 }
 
-// A3[type node][c] = sum over the type's groups (in order) of the partials
-__global__ void bwd_reduce_a3_kernel(BwdBatchedArgs a) {
-  const long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+// A3[type node][c] = sum over the type's groups of the partials: eight threads per entry
+// (thread j sums groups j, j + 8, ... in order), combined by a fixed butterfly
+__global__ void __launch_bounds__(256) bwd_reduce_a3_kernel(BwdBatchedArgs a) {
+  const long long e = (blockIdx.x * (long long)blockDim.x + threadIdx.x) >> 3;
+  const int j = threadIdx.x & 7;
   const long long total = (long long)a.total_nodes * H;
-  if (e >= total) return;
-  const int node = (int)(e / H), c = (int)(e % H);
+  const bool in = e < total;
+  const int node = in ? (int)(e / H) : 0, c = (int)(e % H);
   int t = 0;
   while (node >= a.type_off[t + 1]) ++t;
   const int o = a.type_off[t], n = a.type_off[t + 1] - o;
   const float* src = a.a3part + a.a3_toff[t] + (size_t)(node - o) * H + c;
   float s = 0.f;
-  for (int g = 0; g < a.a3_tgroups[t]; ++g) s += src[(size_t)g * n * H];
-  a.a3[e] = s;
+  if (in)
+    for (int g = j; g < a.a3_tgroups[t]; g += 8) s += src[(size_t)g * n * H];
+  s += __shfl_xor_sync(FULL, s, 1);
+  s += __shfl_xor_sync(FULL, s, 2);
+  s += __shfl_xor_sync(FULL, s, 4);
+  if (in && j == 0) a.a3[e] = s;
 }
 
 // ----------------------------------------------------------------------------- R4
-// warp per pad (static assignment): global MLP reverse and the encoder reverse of each
-// channel's argmax node, into per-warp partials of params [OFF_W1, OFF_B2 + 64)
-constexpr int R4_WARPS = 4;
-constexpr int R4_LEN = OFF_B2 + H - OFF_W1;   // E1, b1, E2, b2
-constexpr size_t R4_SMEM = sizeof(float) * (R4_WARPS * (R4_LEN + H)) + sizeof(int) * R4_WARPS * H;
+// warp per pad (static assignment, 8 warps per CTA): the global MLP reverse, dA2 of every
+// channel at its argmax node (ReLU' of the pooled value: the pooled value is that node's
+// ReLU(a2)), and the E1 reverse of each distinct argmax node.  The E1 / b1 partials live in
+// registers (lane l owns units l and l + 32) and are summed over the CTA's warps in warp order.
+// Per pad it records dA2, each channel's slot in the pad's list of distinct argmax nodes and
+// those nodes' inputs, from which R4b sums dE2 and b2 per 64-pad chunk.
+constexpr int R4_WARPS = 8;
+constexpr int R4_LEN = OFF_W2 - OFF_W1;   // E1, b1
+constexpr int R4_WREG = 2 * (NIN + 1) * 32;   // per-warp shared floats (inputs, then partials)
 
-__global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArgs a) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  float* sAccAll = reinterpret_cast<float*>(smem);               // [warp][R4_LEN]
-  float* sH1All = sAccAll + R4_WARPS * R4_LEN;                    // [warp][64]
-  int* sNodeAll = reinterpret_cast<int*>(sH1All + R4_WARPS * H);  // [warp][64]
+__global__ void __launch_bounds__(R4_WARPS * 32, 3) bwd_padrev_kernel(BwdBatchedArgs a) {
+  __shared__ int sNode[R4_WARPS][H];
+  __shared__ __align__(16) float sReg[R4_WARPS][R4_WREG];
   const float* W = a.params;
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  float* acc = sAccAll + (size_t)warp * R4_LEN;
-  int* sNodeW = sNodeAll + warp * H;
-  for (int e = lane; e < R4_LEN; e += 32) acc[e] = 0.f;
-  __syncwarp();
+  int* sNodeW = sNode[warp];
+  float* sX = sReg[warp];   // [slot][NIN] inputs of the pad's distinct argmax nodes
+  float e1[2][NIN], b1[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    b1[h] = 0.f;
+#pragma unroll
+    for (int q = 0; q < NIN; ++q) e1[h][q] = 0.f;
+  }
   const int gw = blockIdx.x * R4_WARPS + warp, nwarps = gridDim.x * R4_WARPS;
   for (int pad = gw; pad < a.num_items; pad += nwarps) {
     if (a.pad_m[pad] == 0) continue;
-    const float* pr = a.pr + (size_t)pad * PR_STRIDE;
+    float* pr = a.pr + (size_t)pad * PR_STRIDE;
     const int ty = a.pad_type[pad];
     const int o = a.type_off[ty];
     const long long base = a.pad_off[pad];
+    const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+    const int rt0 = reinterpret_cast<const int*>(pr)[PR_ROUTE + lane];
+    const int rt1 = reinterpret_cast<const int*>(pr)[PR_ROUTE + 32 + lane];
     // S = dL/dbeta: the decoder partials of the type's node ranges, in range order
     float s0 = 0.f, s1 = 0.f;
     {
@@ -697,9 +740,44 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
         s0 += sp[(size_t)r * ninst * H + lane];
         s1 += sp[(size_t)r * ninst * H + 32 + lane];
       }
-      float* prs = a.pr + (size_t)pad * PR_STRIDE;
-      prs[PR_S + lane] = s0;
-      prs[PR_S + 32 + lane] = s1;
+      pr[PR_S + lane] = s0;
+      pr[PR_S + 32 + lane] = s1;
+    }
+    // routes: the distinct argmax nodes, channels 0..31 first (lowest lane of each node),
+    // then nodes of channels 32..63 that no channel below 32 routes to; slot of each channel
+    int nd = 0;
+    {
+      const unsigned lt = (1u << lane) - 1u;
+      const unsigned m0 = __match_any_sync(FULL, rt0), m1 = __match_any_sync(FULL, rt1);
+      const bool lead0 = (m0 & lt) == 0u;
+      int in0 = -1;   // lowest channel below 32 that routes to rt1
+      for (int l = 31; l >= 0; --l) in0 = __shfl_sync(FULL, rt0, l) == rt1 ? l : in0;
+      const bool lead1 = (m1 & lt) == 0u && in0 < 0;
+      const unsigned b0 = __ballot_sync(FULL, lead0), b1b = __ballot_sync(FULL, lead1);
+      const int my0 = __popc(b0 & lt), my1 = __popc(b0) + __popc(b1b & lt);
+      if (lead0) sNodeW[my0] = rt0;
+      if (lead1) sNodeW[my1] = rt1;
+      nd = __popc(b0) + __popc(b1b);
+      const int slot0 = __shfl_sync(FULL, my0, __ffs(m0) - 1);
+      const int sl1a = __shfl_sync(FULL, slot0, in0 < 0 ? 0 : in0);
+      const int sl1b = __shfl_sync(FULL, my1, __ffs(m1) - 1);
+      reinterpret_cast<int*>(pr)[PR_SLOT + lane] = slot0;
+      reinterpret_cast<int*>(pr)[PR_SLOT + 32 + lane] = in0 >= 0 ? sl1a : sl1b;
+      __syncwarp();
+    }
+    // inputs [p, n, u_hat] of the distinct nodes, one node per lane
+    for (int q = lane; q < nd; q += 32) {
+      const int node = sNodeW[q];
+      const bool act = (bits[node >> 5] >> (node & 31)) & 1u;
+      const float4 u = act ? a.ws_u[base + node] : make_float4(0.f, 0.f, 0.f, 0.f);
+      const float* pp = a.type_pos + 3 * (size_t)(o + node);
+      const float* nn = a.type_nrm + 3 * (size_t)(o + node);
+      const float xv[NIN] = {pp[0], pp[1], pp[2], nn[0], nn[1], nn[2], u.x, u.y, u.z};
+#pragma unroll
+      for (int j = 0; j < NIN; ++j) {
+        sX[q * NIN + j] = xv[j];
+        pr[PR_X + q * NIN + j] = xv[j];
+      }
     }
     // dg = D1_g^T S ; dag = dg [ag > 0] ; dg0 = G1^T dag (weights through L1: rows are
     // read with consecutive lanes on consecutive columns)
@@ -716,10 +794,9 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
         v = fmaf(__ldg(W + OFF_WD + (32 + c) * 2 * H + H + k), __shfl_sync(FULL, s1, c), v);
       dag[h] = pr[PR_AG + k] > 0.f ? v : 0.f;
     }
-    float* prw = a.pr + (size_t)pad * PR_STRIDE;
-    prw[PR_DAG + lane] = dag[0];
-    prw[PR_DAG + 32 + lane] = dag[1];
-    float dg0[2];
+    pr[PR_DAG + lane] = dag[0];
+    pr[PR_DAG + 32 + lane] = dag[1];
+    float d[2];   // dA2 of channel k at its argmax node
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int k = lane + 32 * h;
@@ -729,121 +806,122 @@ __global__ void __launch_bounds__(R4_WARPS * 32) bwd_padrev_kernel(BwdBatchedArg
 #pragma unroll 8
       for (int c = 0; c < 32; ++c)
         v = fmaf(__ldg(W + OFF_WG + (32 + c) * H + k), __shfl_sync(FULL, dag[1], c), v);
-      dg0[h] = v;
+      d[h] = pr[PR_G0 + k] > 0.f ? v : 0.f;
+      pr[PR_D + k] = d[h];
     }
-    // routes: the distinct argmax nodes, channels 0..31 first (lowest lane of each node),
-    // then nodes of channels 32..63 that no channel below 32 routes to
-    const int rt0 = reinterpret_cast<const int*>(pr)[PR_ROUTE + lane];
-    const int rt1 = reinterpret_cast<const int*>(pr)[PR_ROUTE + 32 + lane];
-    int nd = 0;
-    {
-      const unsigned lt = (1u << lane) - 1u;
-      const unsigned m0 = __match_any_sync(FULL, rt0), m1 = __match_any_sync(FULL, rt1);
-      const bool lead0 = (m0 & lt) == 0u;
-      bool in0 = false;   // does rt1 appear among the channels 0..31?
-      for (int l = 0; l < 32; ++l) in0 |= __shfl_sync(FULL, rt0, l) == rt1;
-      const bool lead1 = (m1 & lt) == 0u && !in0;
-      const unsigned b0 = __ballot_sync(FULL, lead0), b1 = __ballot_sync(FULL, lead1);
-      if (lead0) sNodeW[__popc(b0 & lt)] = rt0;
-      if (lead1) sNodeW[__popc(b0) + __popc(b1 & lt)] = rt1;
-      nd = __popc(b0) + __popc(b1);
-      __syncwarp();
-    }
-    const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+    __syncwarp();
+    const unsigned dz0 = __ballot_sync(FULL, d[0] != 0.f), dz1 = __ballot_sync(FULL, d[1] != 0.f);
+    float4 duq[2] = {make_float4(0.f, 0.f, 0.f, 0.f), make_float4(0.f, 0.f, 0.f, 0.f)};
     for (int q = 0; q < nd; ++q) {
       const int node = sNodeW[q];
-      const bool act = (bits[node >> 5] >> (node & 31)) & 1u;
-      const float4 u = act ? a.ws_u[base + node] : make_float4(0.f, 0.f, 0.f, 0.f);
+      // the channels routed to this node with a nonzero dA2
+      unsigned long long cm = (unsigned long long)(__ballot_sync(FULL, rt0 == node) & dz0) |
+                              ((unsigned long long)(__ballot_sync(FULL, rt1 == node) & dz1) << 32);
+      if (cm == 0ull) continue;   // warp-uniform
+      // dh1 = sum over those channels of dA2_c E2[c, :] (lanes over units k)
+      float dh1[2] = {0.f, 0.f};
+      while (cm) {
+        const int c = __ffsll((long long)cm) - 1;
+        cm &= cm - 1;
+        const float g = __shfl_sync(FULL, c < 32 ? d[0] : d[1], c & 31);
+        dh1[0] = fmaf(__ldg(W + OFF_W2 + c * H + lane), g, dh1[0]);
+        dh1[1] = fmaf(__ldg(W + OFF_W2 + c * H + 32 + lane), g, dh1[1]);
+      }
       float x[NIN];
-      x[0] = a.type_pos[3 * (size_t)(o + node)];
-      x[1] = a.type_pos[3 * (size_t)(o + node) + 1];
-      x[2] = a.type_pos[3 * (size_t)(o + node) + 2];
-      x[3] = a.type_nrm[3 * (size_t)(o + node)];
-      x[4] = a.type_nrm[3 * (size_t)(o + node) + 1];
-      x[5] = a.type_nrm[3 * (size_t)(o + node) + 2];
-      x[6] = u.x;
-      x[7] = u.y;
-      x[8] = u.z;
-      // forward of this node: a1, h1 (lanes own units k = lane, lane + 32)
-      float a1[2], h1[2];
+#pragma unroll
+      for (int j = 0; j < NIN; ++j) x[j] = sX[q * NIN + j];
+      // dA1 = dh1 [a1 > 0] (a1 of this node recomputed); dE1 += dA1 x^T; db1;
+      // du_hat = E1[:, 6:9]^T dA1 (kept by lane q mod 32, applied to active nodes below)
+      float du0 = 0.f, du1 = 0.f, du2 = 0.f;
 #pragma unroll
       for (int h = 0; h < 2; ++h) {
         const int k = lane + 32 * h;
         float v = __ldg(W + OFF_B1 + k);
 #pragma unroll
         for (int q2 = 0; q2 < NIN; ++q2) v = fmaf(__ldg(W + OFF_W1 + k * NIN + q2), x[q2], v);
-        a1[h] = v;
-        h1[h] = relu(v);
-      }
-      // the channels routed to this node, one at a time (lanes over units k)
-      unsigned long long cm = (unsigned long long)__ballot_sync(FULL, rt0 == node) |
-                              ((unsigned long long)__ballot_sync(FULL, rt1 == node) << 32);
-      float dh1[2] = {0.f, 0.f};
-      while (cm) {
-        const int c = __ffsll((long long)cm) - 1;
-        cm &= cm - 1;
-        const float w0 = __ldg(W + OFF_W2 + c * H + lane), w1 = __ldg(W + OFF_W2 + c * H + 32 + lane);
-        float a2 = fmaf(w0, h1[0], w1 * h1[1]);
+        const float d1 = v > 0.f ? dh1[h] : 0.f;
 #pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) a2 += __shfl_xor_sync(FULL, a2, sh);
-        a2 += __ldg(W + OFF_B2 + c);
-        const float g = __shfl_sync(FULL, c < 32 ? dg0[0] : dg0[1], c & 31);
-        const float d = a2 > 0.f ? g : 0.f;   // dA2[c]
-        if (d == 0.f) continue;                // warp-uniform
-        acc[OFF_W2 - OFF_W1 + c * H + lane] += d * h1[0];
-        acc[OFF_W2 - OFF_W1 + c * H + 32 + lane] += d * h1[1];
-        if (lane == 0) acc[OFF_B2 - OFF_W1 + c] += d;
-        dh1[0] = fmaf(w0, d, dh1[0]);
-        dh1[1] = fmaf(w1, d, dh1[1]);
-      }
-      if (!__any_sync(FULL, dh1[0] != 0.f || dh1[1] != 0.f)) continue;   // warp-uniform
-      // dA1 = dh1 [a1 > 0]; dE1 += dA1 x^T; db1; du_hat = E1[:, 6:9]^T dA1 (active)
-      float du0 = 0.f, du1 = 0.f, du2 = 0.f;
-#pragma unroll
-      for (int h = 0; h < 2; ++h) {
-        const int k = lane + 32 * h;
-        const float d1 = a1[h] > 0.f ? dh1[h] : 0.f;
-#pragma unroll
-        for (int q2 = 0; q2 < NIN; ++q2) acc[k * NIN + q2] += d1 * x[q2];
-        acc[OFF_B1 - OFF_W1 + k] += d1;
+        for (int q2 = 0; q2 < NIN; ++q2) e1[h][q2] = fmaf(d1, x[q2], e1[h][q2]);
+        b1[h] += d1;
         du0 = fmaf(__ldg(W + OFF_W1 + k * NIN + 6), d1, du0);
         du1 = fmaf(__ldg(W + OFF_W1 + k * NIN + 7), d1, du1);
         du2 = fmaf(__ldg(W + OFF_W1 + k * NIN + 8), d1, du2);
       }
-      if (act) {
 #pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) {
-          du0 += __shfl_xor_sync(FULL, du0, sh);
-          du1 += __shfl_xor_sync(FULL, du1, sh);
-          du2 += __shfl_xor_sync(FULL, du2, sh);
-        }
-        if (lane == 0) {
-          float4 d = a.ws_du[base + node];
-          d.x += du0;
-          d.y += du1;
-          d.z += du2;
-          a.ws_du[base + node] = d;
+      for (int sh = 16; sh > 0; sh >>= 1) {
+        du0 += __shfl_xor_sync(FULL, du0, sh);
+        du1 += __shfl_xor_sync(FULL, du1, sh);
+        du2 += __shfl_xor_sync(FULL, du2, sh);
+      }
+      if (lane == (q & 31)) {
+        if (q < 32) duq[0] = make_float4(du0, du1, du2, 1.f);
+        else duq[1] = make_float4(du0, du1, du2, 1.f);
+      }
+    }
+    // dL/du_hat of the active argmax nodes (distinct nodes: no two lanes share an entry)
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int q = lane + 32 * h;
+      if (q < nd && duq[h].w != 0.f) {
+        const int node = sNodeW[q];
+        if ((bits[node >> 5] >> (node & 31)) & 1u) {
+          float4 dd = a.ws_du[base + node];
+          dd.x += duq[h].x;
+          dd.y += duq[h].y;
+          dd.z += duq[h].z;
+          a.ws_du[base + node] = dd;
         }
       }
-      __syncwarp();
     }
+    __syncwarp();
   }
-  __syncwarp();
-  for (int e = lane; e < R4_LEN; e += 32) a.r4part[(size_t)gw * R4_LEN + e] = acc[e];
+  // the CTA's partial of E1 and b1: warps summed in warp order (the warp's input slots are
+  // reused for its partials once its pads are done)
+  float* sP = sReg[warp];   // [h][q][lane], q = NIN is b1
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+#pragma unroll
+    for (int q = 0; q < NIN; ++q) sP[(h * (NIN + 1) + q) * 32 + lane] = e1[h][q];
+    sP[(h * (NIN + 1) + NIN) * 32 + lane] = b1[h];
+  }
+  __syncthreads();
+  float* out = a.r4part + (size_t)blockIdx.x * R4_LEN;
+  for (int e = threadIdx.x; e < R4_LEN; e += blockDim.x) {
+    const int k = e < H * NIN ? e / NIN : e - H * NIN;   // E1 row k, column e % 9; then b1
+    const int q = e < H * NIN ? e % NIN : NIN;
+    const int idx = ((k >> 5) * (NIN + 1) + q) * 32 + (k & 31);
+    float v = 0.f;
+    for (int w = 0; w < R4_WARPS; ++w) v += sReg[w][idx];
+    out[e] = v;
+  }
 }
 
 // ----------------------------------------------------------------------------- R4b
 // sums over pads (chunks of 64 pads, in order): dD1_g = sum S g^T, db_D1 = sum S,
-// dG1 = sum dag g0^T, db_G1 = sum dag.  Partial layout per chunk: params [OFF_WG, OFF_W4).
+// dG1 = sum dag g0^T, db_G1 = sum dag, and dE2 = sum over (pad, channel c) of
+// dA2_c h1(argmax node of c)^T with db2 = sum dA2; h1 is recomputed from the recorded inputs
+// (thread t owns unit t mod 64 of channels 16 (t / 64) .. + 15).  Partial layout per chunk:
+// params [OFF_W2, OFF_W4).
 constexpr int R4B_PADS = 64;
-constexpr int R4B_LEN = OFF_W4 - OFF_WG;
+constexpr int R4B_LEN = OFF_W4 - OFF_W2;
+constexpr int R4B_GRP = 8;   // pads staged at a time for the dE2 sums
+
+constexpr int R4B_XS = 12;   // padded input row (three 16-byte reads)
+
+struct R4bSmem {
+  float A[R4B_PADS][TLD];             // S or dag per pad
+  float B[R4B_PADS][TLD];             // g or g0 per pad
+  float2 D[R4B_GRP][H];               // (dA2, slot bits) per channel
+  float X[R4B_GRP][H][R4B_XS];        // inputs per slot
+};
 
 __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
-  __shared__ float sA[R4B_PADS][TLD];   // S or dag per pad
-  __shared__ float sB[R4B_PADS][TLD];   // g or g0 per pad
+  extern __shared__ __align__(16) unsigned char smem_r4b[];
+  R4bSmem& sm = *reinterpret_cast<R4bSmem*>(smem_r4b);
   const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
   const int p0 = blockIdx.x * R4B_PADS;
   float* out = a.r4bpart + (size_t)blockIdx.x * R4B_LEN;
+  const float* W = a.params;
   for (int which = 0; which < 2; ++which) {
     const int oa = which == 0 ? PR_S : PR_DAG, ob = which == 0 ? PR_G : PR_G0;
     for (int e = tid; e < R4B_PADS * H; e += 256) {
@@ -851,8 +929,8 @@ __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
       const int pad = p0 + r;
       const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
       const float* pr = a.pr + (size_t)(ok ? pad : 0) * PR_STRIDE;
-      sA[r][c] = ok ? pr[oa + c] : 0.f;
-      sB[r][c] = ok ? pr[ob + c] : 0.f;
+      sm.A[r][c] = ok ? pr[oa + c] : 0.f;
+      sm.B[r][c] = ok ? pr[ob + c] : 0.f;
     }
     __syncthreads();
     float acc[4][4];
@@ -860,20 +938,20 @@ __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
-    for (int r0 = 0; r0 < R4B_PADS; r0 += 64) tile_acc(&sA[r0][0], &sB[r0][0], ti, tj, acc);
+    tile_acc(&sm.A[0][0], &sm.B[0][0], ti, tj, acc);
 #pragma unroll
     for (int i = 0; i < 4; ++i)
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
         const int c = 4 * ti + i, k = 4 * tj + j;
-        if (which == 0) out[OFF_WD - OFF_WG + c * 2 * H + H + k] = acc[i][j];
-        else out[c * H + k] = acc[i][j];
+        if (which == 0) out[OFF_WD - OFF_W2 + c * 2 * H + H + k] = acc[i][j];
+        else out[OFF_WG - OFF_W2 + c * H + k] = acc[i][j];
       }
     if (tid < H) {
       float s = 0.f;
-      for (int r = 0; r < R4B_PADS; ++r) s += sA[r][tid];
-      if (which == 0) out[OFF_BD - OFF_WG + tid] = s;
-      else out[OFF_BG - OFF_WG + tid] = s;
+      for (int r = 0; r < R4B_PADS; ++r) s += sm.A[r][tid];
+      if (which == 0) out[OFF_BD - OFF_W2 + tid] = s;
+      else out[OFF_BG - OFF_W2 + tid] = s;
     }
     if (which == 0 && tid < 3) {   // sum of G over passive nodes (dL/db_D2), this chunk
       float g = 0.f;
@@ -884,9 +962,63 @@ __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
       a.gsum_part[(size_t)blockIdx.x * 3 + tid] = g;
     }
     if (which == 0) {   // the local half of D1 belongs to R5: zeros here
-      for (int e = tid; e < H * H; e += 256) out[OFF_WD - OFF_WG + (e >> 6) * 2 * H + (e & 63)] = 0.f;
+      for (int e = tid; e < H * H; e += 256) out[OFF_WD - OFF_W2 + (e >> 6) * 2 * H + (e & 63)] = 0.f;
     }
     __syncthreads();
+  }
+  // dE2[c][k] for unit k and channels cb .. cb + 15, pads of the chunk in order
+  const int k = tid & (H - 1), cb = (tid >> 6) * 16;
+  float w1[NIN];
+#pragma unroll
+  for (int q = 0; q < NIN; ++q) w1[q] = W[OFF_W1 + k * NIN + q];
+  const float bk = W[OFF_B1 + k];
+  float e2[16], b2[16];
+#pragma unroll
+  for (int j = 0; j < 16; ++j) e2[j] = b2[j] = 0.f;
+  for (int g0 = 0; g0 < R4B_PADS; g0 += R4B_GRP) {
+    for (int e = tid; e < R4B_GRP * H; e += 256) {
+      const int r = e >> 6, c = e & (H - 1);
+      const int pad = p0 + g0 + r;
+      const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
+      const float* pr = a.pr + (size_t)(ok ? pad : 0) * PR_STRIDE;
+      sm.D[r][c] = ok ? make_float2(pr[PR_D + c], __int_as_float(reinterpret_cast<const int*>(pr)[PR_SLOT + c])) : make_float2(0.f, 0.f);
+    }
+    for (int e = tid; e < R4B_GRP * H * NIN; e += 256) {
+      const int r = e / (H * NIN), j = e - r * (H * NIN);
+      const int sl = j / NIN, q = j - sl * NIN;
+      const int pad = p0 + g0 + r;
+      const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
+      sm.X[r][sl][q] = ok ? a.pr[(size_t)pad * PR_STRIDE + PR_X + j] : 0.f;
+    }
+    __syncthreads();
+    for (int r = 0; r < R4B_GRP; ++r) {
+#pragma unroll
+      for (int j = 0; j < 16; ++j) {
+        const float2 ds = sm.D[r][cb + j];   // warp-uniform
+        if (ds.x == 0.f) continue;
+        const float* xr = sm.X[r][__float_as_int(ds.y)];
+        const float4 xa = *reinterpret_cast<const float4*>(xr);
+        const float4 xb = *reinterpret_cast<const float4*>(xr + 4);
+        const float x8 = xr[8];
+        float v0 = fmaf(w1[0], xa.x, bk), v1 = w1[1] * xa.y;
+        v0 = fmaf(w1[2], xa.z, v0);
+        v1 = fmaf(w1[3], xa.w, v1);
+        v0 = fmaf(w1[4], xb.x, v0);
+        v1 = fmaf(w1[5], xb.y, v1);
+        v0 = fmaf(w1[6], xb.z, v0);
+        v1 = fmaf(w1[7], xb.w, v1);
+        v0 = fmaf(w1[8], x8, v0);
+        e2[j] = fmaf(ds.x, relu(v0 + v1), e2[j]);
+        b2[j] += ds.x;
+      }
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int j = 0; j < 16; ++j) out[(cb + j) * H + k] = e2[j];
+  if (k == 0) {
+#pragma unroll
+    for (int j = 0; j < 16; ++j) out[OFF_B2 - OFF_W2 + cb + j] = b2[j];
   }
 }
 
@@ -1082,12 +1214,12 @@ __global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
   const int q = blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= NPARAM) return;
   float s = 0.f;
-  if (q >= OFF_W1 && q < OFF_B2 + H)
+  if (q >= OFF_W1 && q < OFF_W2)
     for (int w = 0; w < a.r4_parts; ++w) s += a.r4part[(size_t)w * R4_LEN + q - OFF_W1];
   if (q >= OFF_W1 && q < OFF_W4)
     for (int b = 0; b < a.r5_parts; ++b) s += a.r5part[(size_t)b * R5_LEN + q - OFF_W1];
-  if (q >= OFF_WG && q < OFF_W4)
-    for (int b = 0; b < a.r4b_parts; ++b) s += a.r4bpart[(size_t)b * R4B_LEN + q - OFF_WG];
+  if (q >= OFF_W2 && q < OFF_W4)
+    for (int b = 0; b < a.r4b_parts; ++b) s += a.r4bpart[(size_t)b * R4B_LEN + q - OFF_W2];
   if (q >= OFF_W4 && q < OFF_W4 + 3 * H)
     for (int b = 0; b < a.r3_parts; ++b) s += a.d2part[(size_t)b * 3 * H + q - OFF_W4];
   if (q >= OFF_B4 && q < OFF_B4 + 3)
@@ -1138,24 +1270,26 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
         c3 = true;
       }
       bwd_decoder_kernel<<<a.r3_parts, 256, sizeof(R3Smem), s>>>(a);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      const long long tot = (long long)a.total_nodes * H;
+      break;
+    }
+    case BWD_STAGE_A3SUM: {
+      const long long tot = (long long)a.total_nodes * H * 8;
       bwd_reduce_a3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a);
       break;
     }
-    case BWD_STAGE_PADREV: {
-      static bool c4 = false;
-      if (!c4) {
-        cudaError_t e = cudaFuncSetAttribute(bwd_padrev_kernel,
-                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)R4_SMEM);
+    case BWD_STAGE_PADREV:
+      bwd_padrev_kernel<<<a.r4_parts, R4_WARPS * 32, 0, s>>>(a);
+      break;
+    case BWD_STAGE_PADSUM: {
+      static bool c4b = false;
+      if (!c4b) {
+        cudaError_t e = cudaFuncSetAttribute(bwd_padsum_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)sizeof(R4bSmem));
         if (e != cudaSuccess) return e;
-        c4 = true;
+        c4b = true;
       }
-      bwd_padrev_kernel<<<a.r4_parts / R4_WARPS, R4_WARPS * 32, R4_SMEM, s>>>(a);
-      cudaError_t e = cudaGetLastError();
-      if (e != cudaSuccess) return e;
-      bwd_padsum_kernel<<<a.r4b_parts, 256, 0, s>>>(a);
+      bwd_padsum_kernel<<<a.r4b_parts, 256, sizeof(R4bSmem), s>>>(a);
       break;
     }
     case BWD_STAGE_TYPENODE: {

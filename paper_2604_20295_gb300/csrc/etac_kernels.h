@@ -240,7 +240,8 @@ cudaError_t launch_reduce_pose(const float* part, int E, int P, int K, float* ou
 // ---------------------------------------------------------------- batched reverse mode (FP32)
 // per-pad records of the staged reverse mode (floats; PR_ROUTE holds int bits)
 constexpr int PR_G0 = 0, PR_AG = 64, PR_G = 128, PR_BETA = 192, PR_S = 256, PR_DAG = 320,
-              PR_ROUTE = 384, PR_GSUM = 448, PR_STRIDE = 452;
+              PR_ROUTE = 384, PR_GSUM = 448, PR_D = 452, PR_SLOT = 516, PR_X = 580,
+              PR_STRIDE = PR_X + 64 * 9 + 4;
 
 struct R3Group {
   int type, k0;        // pad type, first instance of the 64-instance group
@@ -314,8 +315,9 @@ struct BwdBatchedLaunch {
 };
 size_t bwd_pad_smem_bytes(int nmax, int K);
 cudaError_t bwd_pad_occupancy(int nmax, int K, int* blocks_per_sm);
-enum { BWD_STAGE_PAD = 0, BWD_STAGE_GLOBAL, BWD_STAGE_DECODER, BWD_STAGE_PADREV,
-       BWD_STAGE_TYPENODE, BWD_STAGE_POSE, BWD_STAGE_PARAMS };
+enum { BWD_STAGE_PAD = 0, BWD_STAGE_GLOBAL, BWD_STAGE_DECODER, BWD_STAGE_A3SUM,
+       BWD_STAGE_PADREV, BWD_STAGE_PADSUM, BWD_STAGE_TYPENODE, BWD_STAGE_POSE,
+       BWD_STAGE_PARAMS };
 cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunch& l, int stage,
                                   float* grad_params, cudaStream_t s);
 

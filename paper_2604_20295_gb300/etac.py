@@ -215,9 +215,9 @@ def tuning_dict(t: etac_tuning) -> dict:
 
 def etac_kernel_times(ctx: int) -> dict:
     """{kernel name: (launches, summed ms)} since timing was enabled or last read."""
-    buf = (etac_kernel_time * 16)()
+    buf = (etac_kernel_time * 32)()
     n = ctypes.c_int32(0)
-    _check(ctx, lib().etac_kernel_times(ctx, ctypes.addressof(buf), 16, ctypes.byref(n)),
+    _check(ctx, lib().etac_kernel_times(ctx, ctypes.addressof(buf), 32, ctypes.byref(n)),
            "etac_kernel_times")
     return {buf[i].name.decode(): (int(buf[i].launches), float(buf[i].total_ms))
             for i in range(n.value)}

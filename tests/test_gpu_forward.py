@@ -133,16 +133,18 @@ def test_repeat_is_bitwise_deterministic(algo):
     assert np.array_equal(a["disp"], b["disp"]) and np.array_equal(a["mask"], b["mask"])
 
 
-@pytest.mark.parametrize("algo", ALGOS)
-def test_cuda_graph_replay_with_new_inputs(algo):
+@pytest.mark.parametrize("algo,prec", [(a, X.PREC_FP32) for a in ALGOS] +
+                         [(X.ALGO_BATCHED, X.PREC_BF16)])
+def test_cuda_graph_replay_with_new_inputs(algo, prec):
     """The step captured once in a CUDA graph and replayed after the input poses are
-    overwritten in place gives the same result as an eager step on those inputs."""
+    overwritten in place gives the same result as an eager step on those inputs (the BF16
+    step is four launches; the FP32 steps one)."""
     sc0 = I.hand_scene(24, seed=21)
     sc1 = I.hand_scene(24, seed=22)
     th = I.make_params(0)
     sim = X.TactileSim(sc0)
     try:
-        sim.set_model(th, X.MODE_FULL, X.PREC_FP32, algo)
+        sim.set_model(th, X.MODE_FULL, prec, algo)
         s = torch.cuda.Stream()
         s.wait_stream(torch.cuda.current_stream())
         with torch.cuda.stream(s):
@@ -160,7 +162,7 @@ def test_cuda_graph_replay_with_new_inputs(algo):
             g.replay()
             torch.cuda.synchronize()
             got = sim.disp.cpu().numpy().astype(np.float64)
-            eager = run(sc, th, algo=algo)
+            eager = run(sc, th, algo=algo, precision=prec)
             assert np.array_equal(got, eager["disp"])
     finally:
         sim.close()
