@@ -975,27 +975,49 @@ __global__ void __launch_bounds__(256) bwd_padsum_kernel(BwdBatchedArgs a) {
   float e2[16], b2[16];
 #pragma unroll
   for (int j = 0; j < 16; ++j) e2[j] = b2[j] = 0.f;
-  for (int g0 = 0; g0 < R4B_PADS; g0 += R4B_GRP) {
-    for (int e = tid; e < R4B_GRP * H; e += 256) {
-      const int r = e >> 6, c = e & (H - 1);
+  // the chunk's records, R4B_GRP pads at a time: loaded into registers one group ahead,
+  // stored to shared memory, then summed (every channel, including those with dA2 = 0, whose
+  // slot is still a valid node of the pad, so the loop has no branch)
+  constexpr int ND = R4B_GRP * H / 256, NX = R4B_GRP * H * NIN / 256;
+  float2 rd[ND];
+  float rx[NX];
+  auto load = [&](int g0) {
+#pragma unroll
+    for (int u = 0; u < ND; ++u) {
+      const int e = tid + 256 * u, r = e >> 6, c = e & (H - 1);
       const int pad = p0 + g0 + r;
       const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
       const float* pr = a.pr + (size_t)(ok ? pad : 0) * PR_STRIDE;
-      sm.D[r][c] = ok ? make_float2(pr[PR_D + c], __int_as_float(reinterpret_cast<const int*>(pr)[PR_SLOT + c])) : make_float2(0.f, 0.f);
+      rd[u] = ok ? make_float2(pr[PR_D + c], __int_as_float(reinterpret_cast<const int*>(pr)[PR_SLOT + c]))
+                 : make_float2(0.f, 0.f);
     }
-    for (int e = tid; e < R4B_GRP * H * NIN; e += 256) {
-      const int r = e / (H * NIN), j = e - r * (H * NIN);
-      const int sl = j / NIN, q = j - sl * NIN;
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = tid + 256 * u, r = e / (H * NIN), jj = e - r * (H * NIN);
       const int pad = p0 + g0 + r;
       const bool ok = pad < a.num_items && a.pad_m[pad] > 0;
-      sm.X[r][sl][q] = ok ? a.pr[(size_t)pad * PR_STRIDE + PR_X + j] : 0.f;
+      rx[u] = ok ? a.pr[(size_t)pad * PR_STRIDE + PR_X + jj] : 0.f;
+    }
+  };
+  load(0);
+  for (int g0 = 0; g0 < R4B_PADS; g0 += R4B_GRP) {
+#pragma unroll
+    for (int u = 0; u < ND; ++u) {
+      const int e = tid + 256 * u;
+      sm.D[e >> 6][e & (H - 1)] = rd[u];
+    }
+#pragma unroll
+    for (int u = 0; u < NX; ++u) {
+      const int e = tid + 256 * u, r = e / (H * NIN), jj = e - r * (H * NIN);
+      const int sl = jj / NIN;
+      sm.X[r][sl][jj - sl * NIN] = rx[u];
     }
     __syncthreads();
+    if (g0 + R4B_GRP < R4B_PADS) load(g0 + R4B_GRP);
     for (int r = 0; r < R4B_GRP; ++r) {
 #pragma unroll
       for (int j = 0; j < 16; ++j) {
         const float2 ds = sm.D[r][cb + j];   // warp-uniform
-        if (ds.x == 0.f) continue;
         const float* xr = sm.X[r][__float_as_int(ds.y)];
         const float4 xa = *reinterpret_cast<const float4*>(xr);
         const float4 xb = *reinterpret_cast<const float4*>(xr + 4);
