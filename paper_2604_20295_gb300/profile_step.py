@@ -2,6 +2,7 @@
 
     python -m paper_2604_20295_gb300.profile_step --workload hand --envs 4096 --precision bf16
     python -m paper_2604_20295_gb300.profile_step --workload flat16 --envs 1024 --backward
+    python -m paper_2604_20295_gb300.profile_step --outputs count   # outputs of the bench step
 
 Workloads: ``hand`` (5 curved 16x32 fingertips + flat 32x64 palm per env), ``flat16`` (flat
 16x16 pad pressed by a sphere), ``uneven`` (6 pads of 8x8 .. 64x64 nodes, 1-3 primitives).
@@ -27,6 +28,9 @@ def main():
     ap.add_argument("--algo", default="batched", choices=["plain", "batched"])
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--backward", action="store_true")
+    ap.add_argument("--outputs", default="all", choices=["all", "count"],
+                    help="all: displacement, mask, penetration, active counts; count: "
+                         "displacement and active counts (the benchmark's step)")
     args = ap.parse_args()
     B.build()
     if args.workload == "hand":
@@ -41,8 +45,9 @@ def main():
                   X.ALGO_BATCHED if args.algo == "batched" else X.ALGO_PLAIN)
     G = torch.as_tensor(np.random.default_rng(0).normal(size=(sc.total_nodes, 3)),
                         dtype=torch.float32).cuda()
+    kw = {} if args.outputs == "all" else dict(want_mask=False, want_pen=False, want_count=True)
     for _ in range(args.steps):
-        sim.step()
+        sim.step(**kw)
         if args.backward:
             sim.backward(G)
     torch.cuda.synchronize()
