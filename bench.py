@@ -66,6 +66,9 @@ SDF_FLOPS = 40.0   # pad -> object transform (18) + one primitive's SDF and test
 # named, valid only for the source hash recorded with it (null once the kernel changes)
 TRAFFIC = {
     # hand workload, 4,096 envs, one pass of --metrics dram__bytes_read.sum,dram__bytes_write.sum
+    # with the bench step's outputs (displacement and counts: profile_step --outputs count)
+    "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
+                             "sha": "44d5b8938236d439", "bytes": 15.4e6 + 116.5e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                          "sha": "29a5ddf75939fb59", "bytes": 136.3e6 + 127.3e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
@@ -533,27 +536,42 @@ def main():
     value = head["value"]
     ms_per_step = head["ms_per_step"]
 
-    # ---- end to end through the public API with host buffers
+    # ---- end to end through the public API with host buffers: every step copies its inputs
+    # from pinned host memory and its whole displacement back to pinned host memory.  Two
+    # output buffers alternate, so the read-back of step k (on a copy stream) overlaps step
+    # k + 1; a buffer is rewritten only after its copy has finished.
     e2e = None
     if not args.no_e2e:
         pin = lambda a: torch.as_tensor(a).pin_memory()
         h_in = [pin(scene.obj_type), pin(scene.obj_dims), pin(scene.obj_pose), pin(scene.pad_pose)]
         d_in = [sim.obj_type, sim.obj_dims, sim.obj_pose, sim.pad_pose]
-        h_out = torch.empty(sim.disp.shape, dtype=torch.float32).pin_memory()
+        d_out = [sim.disp, torch.empty_like(sim.disp)]
+        h_out = [torch.empty(sim.disp.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
-        d2h = h_out.numel() * 4
-        ke = max(3, args.steps // 2)
+        d2h = h_out[0].numel() * 4
+        ke = max(4, args.steps // 2)
+        cs = torch.cuda.Stream(dev)
+        ready = [torch.cuda.Event() for _ in range(2)]
+        done = [torch.cuda.Event() for _ in range(2)]
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        for _ in range(ke):
+        for k in range(ke):
+            b = k & 1
             for d, h in zip(d_in, h_in):
                 d.copy_(h, non_blocking=True)
-            sim.step(**step_kw)
-            h_out.copy_(sim.disp, non_blocking=True)
+            if k >= 2:
+                stream.wait_event(done[b])
+            sim.step(disp=d_out[b], **step_kw)
+            ready[b].record(stream)
+            cs.wait_event(ready[b])
+            with torch.cuda.stream(cs):
+                h_out[b].copy_(d_out[b], non_blocking=True)
+            done[b].record(cs)
+        stream.wait_stream(cs)
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_s = e0.elapsed_time(e1) / 1e3
@@ -561,8 +579,11 @@ def main():
             t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
             pg.all_reduce(t, op=pg.ReduceOp.MAX)
             e2e_s = float(t)
+        same = bool(torch.equal(h_out[(ke - 1) & 1], d_out[(ke - 1) & 1].cpu()))
         e2e = {"value": nodes * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "steps": ke}
+               "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * e2e_s / ke,
+               "pipelining": "read-back of step k overlaps step k + 1 (two output buffers, "
+                             "copy stream)", "readback_matches_device": same}
 
     # ---- the other rungs on the same GPU and scene (the metric compares BF16 batched with
     # FP32 plain; FP32 batched is the intermediate rung)

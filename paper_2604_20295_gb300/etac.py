@@ -16,6 +16,7 @@ import numpy as np
 from . import build as _build
 
 ETAC_OK = 0
+ERR_INVALID_ARG = 1
 STATUS_NAMES = {0: "ETAC_OK", 1: "ETAC_ERR_INVALID_ARG", 2: "ETAC_ERR_STATE", 3: "ETAC_ERR_CUDA",
                 4: "ETAC_ERR_OOM", 5: "ETAC_ERR_TIMEOUT", 6: "ETAC_ERR_NONFINITE",
                 7: "ETAC_ERR_UNSUPPORTED"}
@@ -285,15 +286,24 @@ class TactileSim:
         return etac_step_in(self.obj_type.data_ptr(), self.obj_dims.data_ptr(),
                             self.obj_pose.data_ptr(), self.pad_pose.data_ptr())
 
-    def step_out(self, want_mask=True, want_pen=True, want_count=True) -> etac_step_out:
-        return etac_step_out(self.disp.data_ptr(), self.mask.data_ptr() if want_mask else None,
+    def step_out(self, want_mask=True, want_pen=True, want_count=True, disp=None) -> etac_step_out:
+        d = self.disp if disp is None else disp
+        return etac_step_out(d.data_ptr(), self.mask.data_ptr() if want_mask else None,
                              self.pen.data_ptr() if want_pen else None,
                              self.count.data_ptr() if want_count else None)
 
-    def step(self, want_mask=True, want_pen=True, want_count=True):
-        etac_step_forward(self.ctx, self.step_in(), self.step_out(want_mask, want_pen, want_count),
+    def step(self, want_mask=True, want_pen=True, want_count=True, disp=None):
+        """One forward step on the current stream.  ``disp`` (a contiguous float32 [N, 3]
+        device tensor) receives the displacement instead of ``self.disp``, e.g. to alternate
+        output buffers while an earlier step's result is copied to the host."""
+        if disp is not None and (disp.shape != self.disp.shape or disp.dtype != self.disp.dtype
+                                 or not disp.is_contiguous() or disp.device != self.disp.device):
+            raise EtacError(ERR_INVALID_ARG, f"disp must be a contiguous float32 "
+                            f"{tuple(self.disp.shape)} tensor on {self.disp.device}")
+        etac_step_forward(self.ctx, self.step_in(),
+                          self.step_out(want_mask, want_pen, want_count, disp),
                           self.torch.cuda.current_stream(self.device).cuda_stream)
-        return self.disp
+        return self.disp if disp is None else disp
 
     def backward(self, grad_disp, want=("params", "obj_pose", "uhat", "pen")):
         """Reverse mode of the last step for dL/d(disp) = grad_disp [N,3] (device tensor).

@@ -189,3 +189,26 @@ def test_fp64_forward_matches_oracle():
             sim.close()
         ref = O.forward(sc, th)
         np.testing.assert_allclose(got, ref["disp"], rtol=1e-11, atol=1e-12)
+
+
+@pytest.mark.parametrize("prec", [X.PREC_FP32, X.PREC_BF16])
+def test_step_into_alternate_output_buffer(prec):
+    """A step written into a caller's buffer equals the step into the context's own buffer, and
+    a buffer of the wrong shape or type is rejected before anything runs."""
+    sc = I.hand_scene(12, seed=31)
+    sim = X.TactileSim(sc)
+    try:
+        sim.set_model(I.make_params(0), X.MODE_FULL, prec, X.ALGO_BATCHED)
+        sim.step()
+        torch.cuda.synchronize()
+        ref = sim.disp.clone()
+        alt = torch.full_like(sim.disp, float("nan"))
+        out = sim.step(disp=alt)
+        torch.cuda.synchronize()
+        assert out is alt and torch.equal(alt, ref)
+        with pytest.raises(X.EtacError):
+            sim.step(disp=torch.empty(3, 3, device=sim.disp.device))
+        with pytest.raises(X.EtacError):
+            sim.step(disp=torch.empty_like(sim.disp, dtype=torch.float64))
+    finally:
+        sim.close()
