@@ -423,6 +423,8 @@ def main():
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--no-compare", action="store_true")
     ap.add_argument("--no-bwd", action="store_true")
+    ap.add_argument("--copy-streams", type=int, default=1,
+                    help="streams the end-to-end read-back is split over")
     ap.add_argument("--no-graph", action="store_true",
                     help="time eager launches only (default: the step replayed from a CUDA graph)")
     ap.add_argument("--no-autotune", action="store_true",
@@ -550,9 +552,12 @@ def main():
         h2d = sum(t.numel() * t.element_size() for t in h_in)
         d2h = h_out[0].numel() * 4
         ke = max(4, args.steps // 2)
-        cs = torch.cuda.Stream(dev)
+        ncs = max(1, args.copy_streams)
+        css = [torch.cuda.Stream(dev) for _ in range(ncs)]
+        rows = sim.disp.shape[0]
+        cuts = [rows * c // (2 * ncs) for c in range(2 * ncs + 1)]   # 2 chunks per copy stream
         ready = [torch.cuda.Event() for _ in range(2)]
-        done = [torch.cuda.Event() for _ in range(2)]
+        done = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -564,14 +569,19 @@ def main():
             for d, h in zip(d_in, h_in):
                 d.copy_(h, non_blocking=True)
             if k >= 2:
-                stream.wait_event(done[b])
+                for ev in done[b]:
+                    stream.wait_event(ev)
             sim.step(disp=d_out[b], **step_kw)
             ready[b].record(stream)
-            cs.wait_event(ready[b])
-            with torch.cuda.stream(cs):
-                h_out[b].copy_(d_out[b], non_blocking=True)
-            done[b].record(cs)
-        stream.wait_stream(cs)
+            for j, cs in enumerate(css):
+                cs.wait_event(ready[b])
+                with torch.cuda.stream(cs):
+                    for c in (2 * j, 2 * j + 1):
+                        h_out[b][cuts[c]:cuts[c + 1]].copy_(d_out[b][cuts[c]:cuts[c + 1]],
+                                                            non_blocking=True)
+                done[b][j].record(cs)
+        for cs in css:
+            stream.wait_stream(cs)
         e1.record(stream)
         torch.cuda.synchronize()
         e2e_s = e0.elapsed_time(e1) / 1e3
@@ -582,8 +592,9 @@ def main():
         same = bool(torch.equal(h_out[(ke - 1) & 1], d_out[(ke - 1) & 1].cpu()))
         e2e = {"value": nodes * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * e2e_s / ke,
-               "pipelining": "read-back of step k overlaps step k + 1 (two output buffers, "
-                             "copy stream)", "readback_matches_device": same}
+               "pipelining": f"read-back of step k overlaps step k + 1 (two output buffers, "
+                             f"{ncs} copy stream(s), {2 * ncs} chunks)",
+               "readback_matches_device": same}
 
     # ---- the other rungs on the same GPU and scene (the metric compares BF16 batched with
     # FP32 plain; FP32 batched is the intermediate rung)
