@@ -53,8 +53,11 @@ typedef enum {
 enum { ETAC_OBJ_NONE = 0, ETAC_OBJ_SPHERE = 1, ETAC_OBJ_BOX = 2, ETAC_OBJ_CYLINDER = 3,
        ETAC_OBJ_CAPSULE = 4 };
 
-/* which terms of Eq. 4 are evaluated (the ablations of Table II) */
-enum { ETAC_MODE_FULL = 0, ETAC_MODE_LINEAR_ONLY = 1, ETAC_MODE_RESIDUAL_ONLY = 2 };
+/* which terms of Eq. 4 are evaluated (the ablations of Table II): both, the decay propagation
+ * of Eq. 1 alone, the residual network alone, or neither (penetration only: active nodes take
+ * u_hat and passive nodes stay at zero, the propagation-free baseline the paper compares with) */
+enum { ETAC_MODE_FULL = 0, ETAC_MODE_LINEAR_ONLY = 1, ETAC_MODE_RESIDUAL_ONLY = 2,
+       ETAC_MODE_PENETRATION_ONLY = 3 };
 
 /* arithmetic of the dense contractions: FP32, or BF16 operands with FP32 accumulation */
 enum { ETAC_PREC_FP32 = 0, ETAC_PREC_BF16 = 1 };

@@ -19,7 +19,7 @@ _SRC = os.path.join(_HERE, "etac_oracle.c")
 _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
-MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY = 0, 1, 2
+MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY, MODE_PENETRATION_ONLY = 0, 1, 2, 3
 
 
 def build(force: bool = False, src: str = _SRC, lib: str = _LIB) -> str:

@@ -41,7 +41,11 @@
 #define NIN 9         /* per-node input: position, normal, displacement */
 
 enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4 };
-enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2 };
+enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2, MODE_PENETRATION_ONLY = 3 };
+/* the terms of Eq. 4 a mode keeps: the Eq. 1 propagation, the residual network; the
+ * penetration-only mode keeps neither (active nodes u_hat, passive nodes zero) */
+static int with_propagation(int mode) { return mode == MODE_FULL || mode == MODE_LINEAR_ONLY; }
+static int with_residual(int mode) { return mode == MODE_FULL || mode == MODE_RESIDUAL_ONLY; }
 
 typedef struct {
   int num_types;
@@ -345,7 +349,7 @@ static void pad_forward(const orc_scene* sc, const orc_params* P, int mode, int 
   }
   for (int i = 0; i < n; ++i)
     for (int a = 0; a < 3; ++a) U[3 * i + a] = s->act[i] ? s->uhat[3 * i + a] : 0.0;
-  if (mode != MODE_RESIDUAL_ONLY) {
+  if (with_propagation(mode)) {
     /* Eq. 1 summed over the active nodes: Omega U_a */
     for (int i = 0; i < n; ++i) {
       if (s->act[i]) continue;
@@ -361,7 +365,7 @@ static void pad_forward(const orc_scene* sc, const orc_params* P, int mode, int 
       for (int a = 0; a < 3; ++a) U[3 * i + a] += l[a];
     }
   }
-  if (mode != MODE_LINEAR_ONLY) {
+  if (with_residual(mode)) {
     pad_network(P, s);
     for (int i = 0; i < n; ++i) {
       if (s->act[i]) continue;
@@ -483,7 +487,7 @@ int orc_backward(const orc_scene* sc, const double* theta, int mode,
       for (int i = 0; i < n; ++i)
         if (s.act[i])
           for (int a = 0; a < 3; ++a) gu[3 * i + a] += Gd[3 * i + a];
-      if (mode != MODE_RESIDUAL_ONLY) {
+      if (with_propagation(mode)) {
         for (int i = 0; i < n; ++i) {
           if (s.act[i]) continue;
           const double* pi_ = s.pos + 3 * i;
@@ -502,7 +506,7 @@ int orc_backward(const orc_scene* sc, const double* theta, int mode,
           }
         }
       }
-      if (mode != MODE_LINEAR_ONLY) {
+      if (with_residual(mode)) {
         double* gf = (double*)calloc((size_t)H * n, sizeof(double));
         double gg[H], gag[H], gg0[H];
         memset(gg, 0, sizeof gg);

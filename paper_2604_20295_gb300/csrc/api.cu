@@ -212,7 +212,7 @@ void free_ctx(etac_ctx* c) {
 
 bool valid_model(const etac_model_desc* d) {
   return d && d->hidden == ETAC_HIDDEN && d->mode >= ETAC_MODE_FULL &&
-         d->mode <= ETAC_MODE_RESIDUAL_ONLY && (d->precision == ETAC_PREC_FP32 ||
+         d->mode <= ETAC_MODE_PENETRATION_ONLY && (d->precision == ETAC_PREC_FP32 ||
          d->precision == ETAC_PREC_BF16) && (d->algo == ETAC_ALGO_PLAIN ||
          d->algo == ETAC_ALGO_BATCHED);
 }
@@ -643,7 +643,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
                              float* grad_uhat, float* grad_pen, float* grad_params,
                              cudaStream_t s) {
   const int EP = c->E * c->P;
-  const bool use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
+  const bool use_l = etac::uses_propagation(c->model.mode);
   // pad -> object transforms of the differentiated step
   etac::FrontArgs f{};
   f.type_pmax = c->d_type_pmax;
@@ -723,7 +723,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   b.alpha_parts = use_l ? c->alpha_parts : 0;
   b.pose_part = c->d_pose_part;
   b.ticket = c->d_ticket;
-  if (c->model.mode == ETAC_MODE_LINEAR_ONLY) {   // no network: only alpha has a gradient
+  if (!etac::uses_residual(c->model.mode)) {   // no network: only alpha has a gradient
     b.r3_parts = b.r4_parts = b.r4b_parts = b.r5_parts = 0;
   }
   {
@@ -746,7 +746,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   };
   etac_status st = stage(etac::BWD_STAGE_PAD, K_BWD_PAD, "reverse mode: pad stage");
   if (st != ETAC_OK) return st;
-  if (c->model.mode != ETAC_MODE_LINEAR_ONLY) {
+  if (etac::uses_residual(c->model.mode)) {
     if ((st = stage(etac::BWD_STAGE_GLOBAL, K_BWD_GLOBAL, "reverse mode: global MLP")) != ETAC_OK ||
         (st = stage(etac::BWD_STAGE_DECODER, K_BWD_DECODER, "reverse mode: decoder")) != ETAC_OK ||
         (st = stage(etac::BWD_STAGE_A3SUM, K_BWD_A3SUM, "reverse mode: decoder sums")) != ETAC_OK ||
@@ -1085,8 +1085,8 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       timing_end(c, ts, s);
       etac::GemmParams& g = c->gemm;
       g.disp = out->disp;
-      g.use_l = c->model.mode != ETAC_MODE_RESIDUAL_ONLY;
-      g.use_r = c->model.mode != ETAC_MODE_LINEAR_ONLY;
+      g.use_l = etac::uses_propagation(c->model.mode);
+      g.use_r = etac::uses_residual(c->model.mode);
       ts = timing_begin(c, K_GEMM, s);
       ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s, etac::GEMM_FWD, c->gemm_gi), "BF16 propagation GEMM launch");
       timing_end(c, ts, s);
@@ -1259,7 +1259,7 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
       r->gemm_tile_order = t.gemm_tile_order;
     }
   }
-  if (st == ETAC_OK && grad_disp && c->bwdb_ready && c->model.mode != ETAC_MODE_LINEAR_ONLY) {
+  if (st == ETAC_OK && grad_disp && c->bwdb_ready && etac::uses_residual(c->model.mode)) {
     st = fwd();
     const int cand[4] = {32, 64, 128, 256};
     int best = -1;

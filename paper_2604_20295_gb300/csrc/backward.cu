@@ -117,7 +117,7 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
   // staging threads: row tr, 16 columns from tq; GEMM threads: 4 x 4 tile (ti, tj)
   const int tr = tid >> 2, tq = (tid & 3) * 16;
   const int ti = tid >> 4, tj = tid & 15;
-  const bool use_l = a.mode != MODE_RESIDUAL_ONLY, use_r = a.mode != MODE_LINEAR_ONLY;
+  const bool use_l = uses_propagation(a.mode), use_r = uses_residual(a.mode);
   float accWdf[4][4], accW2[4][4];   // per-CTA gradient tiles of D1[:, 0:64] and E2
 #pragma unroll
   for (int i = 0; i < 4; ++i)

@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     }
 
     // ---- 2. residual network (factored)
-    if (a.mode != MODE_LINEAR_ONLY) {
+    if (uses_residual(a.mode)) {
     float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
     for (int a0 = 0; a0 < m; a0 += BT) {
       const int aa = a0 + tid;
@@ -275,7 +275,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     for (int i = tid; i < n; i += BT) {
       if (sMask[i]) continue;
       float l0 = 0.f, l1 = 0.f, l2 = 0.f;
-      if (a.mode != MODE_RESIDUAL_ONLY) {
+      if (uses_propagation(a.mode)) {
         const float* col = Om + i;
 #pragma unroll 4
         for (int aa = 0; aa < m; ++aa) {
@@ -287,7 +287,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
           l2 = fmaf(w, u.z, l2);
         }
       }
-      if (a.mode != MODE_LINEAR_ONLY) {
+      if (uses_residual(a.mode)) {
         float r0 = sB4[0], r1 = sB4[1], r2 = sB4[2];
         const float4* hrow = reinterpret_cast<const float4*>(a.h0tab + (size_t)(o + i) * H);
 #pragma unroll

@@ -216,7 +216,7 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
   float* sFv = reinterpret_cast<float*>(wb + L.fmv);
   int* sFi = reinterpret_cast<int*>(wb + L.fmi);
   const unsigned lt = (1u << lane) - 1u;
-  const bool use_r = a.mode != MODE_LINEAR_ONLY, use_l = a.mode != MODE_RESIDUAL_ONLY;
+  const bool use_r = uses_residual(a.mode), use_l = uses_propagation(a.mode);
 
   int next = 0;
   if (lane == 0) next = atomicAdd(a.ticket, 1);

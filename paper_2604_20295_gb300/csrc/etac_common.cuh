@@ -39,7 +39,14 @@ constexpr int OFF_B4 = OFF_W4 + 3 * H;
 constexpr int NPARAM = OFF_B4 + 3;
 
 enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4 };
-enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2 };
+enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2, MODE_PENETRATION_ONLY = 3 };
+// which terms of Eq. 4 a mode evaluates: the propagation L (Eq. 1) and the residual R
+__host__ __device__ __forceinline__ bool uses_propagation(int mode) {
+  return mode == MODE_FULL || mode == MODE_LINEAR_ONLY;
+}
+__host__ __device__ __forceinline__ bool uses_residual(int mode) {
+  return mode == MODE_FULL || mode == MODE_RESIDUAL_ONLY;
+}
 enum { STATUS_OK = 0, STATUS_TIMEOUT = 5, STATUS_NONFINITE = 6 };
 
 __device__ __forceinline__ void latch_status(int* status, int code) {

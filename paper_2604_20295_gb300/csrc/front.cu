@@ -220,7 +220,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   float* sFmax = reinterpret_cast<float*>(wb + L.fmax);
   float* sFm = reinterpret_cast<float*>(wb + L.fmlane) + lane;   // lane's maxima, stride 32
   const unsigned lt = (1u << lane) - 1u;
-  const bool enc = a.mode != MODE_LINEAR_ONLY;
+  const bool enc = uses_residual(a.mode);
 
   // the next work item is fetched while the current one is processed
   int next = 0;
@@ -469,7 +469,7 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
   for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < np; pad += gridDim.x * wpb) {
     const int m = a.pad_m[pad];
     const int gi = a.pad_gi[pad];
-    if (m == 0 || a.mode == MODE_LINEAR_ONLY) {
+    if (m == 0 || !uses_residual(a.mode)) {
       if (lane == 0) a.c0m[gi] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
       continue;
     }

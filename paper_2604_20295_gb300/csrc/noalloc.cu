@@ -106,7 +106,7 @@ extern "C" etac_status etac_step_forward_noalloc(const etac_noalloc_pads* pads, 
       !pads->pad_type || !pads->pad_off || !params || !in || !out || !in->obj_type ||
       !in->obj_dims || !in->obj_pose || !in->pad_pose || !out->disp)
     return noalloc_fail(ETAC_ERR_INVALID_ARG, "etac_step_forward_noalloc: NULL argument");
-  if (mode < ETAC_MODE_FULL || mode > ETAC_MODE_RESIDUAL_ONLY)
+  if (mode < ETAC_MODE_FULL || mode > ETAC_MODE_PENETRATION_ONLY)
     return noalloc_fail(ETAC_ERR_INVALID_ARG, "etac_step_forward_noalloc: unknown mode");
   const int T = pads->num_types;
   if (T < 1 || pads->num_envs < 1 || pads->pads_per_env < 1 || pads->max_objects < 1 ||

@@ -263,7 +263,7 @@ plain_forward_kernel(PlainArgs<T> a) {
   }
 
   // ---- residual network, pass 1: per-node encoder on every node and channel max-pool
-  if (a.mode != MODE_LINEAR_ONLY) {
+  if (uses_residual(a.mode)) {
     // per-warp running channel maxima in shared memory (ReLU outputs are >= 0)
     for (int c = lane; c < H; c += 32) sred[warp * H + c] = T(0);
     __syncwarp();
@@ -320,7 +320,7 @@ plain_forward_kernel(PlainArgs<T> a) {
     if (sidx[i] >= 0) continue;
     const T px = (T)tpos[3 * i], py = (T)tpos[3 * i + 1], pz = (T)tpos[3 * i + 2];
     T out[3] = {T(0), T(0), T(0)};
-    if (a.mode != MODE_RESIDUAL_ONLY) {
+    if (uses_propagation(a.mode)) {
       for (int j = 0; j < m; ++j) {
         const T* q = sap + 6 * j;
         T dx = q[0] - px, dy = q[1] - py, dz = q[2] - pz;
@@ -330,7 +330,7 @@ plain_forward_kernel(PlainArgs<T> a) {
         out[2] = fma(w, q[5], out[2]);
       }
     }
-    if (a.mode != MODE_LINEAR_ONLY) {
+    if (uses_residual(a.mode)) {
       T X[NIN], f[H], r[3];
       X[0] = px; X[1] = py; X[2] = pz;
       X[3] = (T)tnrm[3 * i]; X[4] = (T)tnrm[3 * i + 1]; X[5] = (T)tnrm[3 * i + 2];

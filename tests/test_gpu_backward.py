@@ -64,7 +64,8 @@ ADJ_REL = 2e-3
 
 
 @pytest.mark.parametrize("name", sorted(SCENES))
-@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY])
+@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY,
+                                  X.MODE_PENETRATION_ONLY])
 def test_backward_matches_oracle(name, mode):
     sc = SCENES[name]()
     th = I.make_params(0)

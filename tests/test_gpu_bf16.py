@@ -43,7 +43,8 @@ def check_bf16(scene, theta, mode=X.MODE_FULL):
     return got, ref
 
 
-@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY])
+@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY,
+                                  X.MODE_PENETRATION_ONLY])
 def test_bf16_sphere_press_100_steps(mode):
     check_bf16(I.sphere_press_scene(100, seed=0), I.make_params(0), mode)
 

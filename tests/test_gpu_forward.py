@@ -53,7 +53,8 @@ def check(scene, theta, mode=X.MODE_FULL, **kw):
 
 
 @pytest.mark.parametrize("algo", ALGOS)
-@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY])
+@pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY,
+                                  X.MODE_PENETRATION_ONLY])
 def test_sphere_press_100_steps(mode, algo):
     """16x16 flat pad, sphere r = 5 mm pressed 0-2 mm, 100 seeded steps (one env each)."""
     sc = I.sphere_press_scene(100, seed=0)

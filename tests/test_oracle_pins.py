@@ -77,6 +77,32 @@ def test_sphere_on_flat_pad_closed_form(R, delta, cx, cy):
     np.testing.assert_allclose(out["disp"][a, 1], d[a] * (P[a, 1] - cy) / (R - d[a]), atol=1e-12)
 
 
+@pytest.mark.parametrize("R,delta,cx,cy", [(5.0, 1.3, 0.25, -0.4)])
+def test_penetration_only_is_the_contact_field(R, delta, cx, cy):
+    """Penetration-only mode (no Eq. 1 term, no residual): the same closed-form sphere contact
+    displacement on the active nodes and exactly zero on every passive node.  Its reverse mode
+    passes dL/dU of active nodes straight to u_hat, and no parameter gets a gradient."""
+    sc = _flat_scene(16, 16, obj=(I.OBJ_SPHERE, (R, 0, 0), (cx, cy, R - delta, 0, 0, 0, 1)))
+    th = _theta(seed=3)
+    out = O.forward(sc, th, mode=O.MODE_PENETRATION_ONLY)
+    cx, cy, h = (float(v) for v in sc.obj_pose[:3])
+    R = float(sc.obj_dims[0])
+    P = sc.types[0].pos.astype(np.float64)
+    rho2 = (P[:, 0] - cx) ** 2 + (P[:, 1] - cy) ** 2
+    inside = rho2 + h ** 2 < R * R
+    np.testing.assert_array_equal(out["mask"].astype(bool), inside)
+    d = np.maximum(0.0, R - np.sqrt(rho2 + h ** 2))
+    a = inside
+    np.testing.assert_allclose(out["disp"][a, 2], -d[a] * h / (R - d[a]), atol=1e-12)
+    np.testing.assert_allclose(out["disp"][a, 0], d[a] * (P[a, 0] - cx) / (R - d[a]), atol=1e-12)
+    assert np.all(out["disp"][~a] == 0.0)
+    G = np.random.default_rng(0).normal(size=(sc.total_nodes, 3))
+    g = O.backward(sc, th, G, mode=O.MODE_PENETRATION_ONLY)
+    assert np.all(g["params"] == 0.0)
+    np.testing.assert_array_equal(g["uhat"][a], G[a])
+    assert np.all(g["uhat"][~a] == 0.0)
+
+
 def test_box_face_flat_patch():
     """A box pressed face-down by delta: a node under its footprint is pushed out through the
     nearest face -- the bottom face (penetration delta, displacement (0, 0, -delta)) unless a
