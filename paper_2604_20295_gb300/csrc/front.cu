@@ -18,11 +18,12 @@
 //     outputs are table entries;
 //   * at the end, the max-pool over the passive nodes: the first passive node of each
 //     channel's table order (ranked f0 values), 32 ranks per warp-wide test.
-// front_global_kernel (one warp per pad): global MLP g = ReLU(G1 g0), the decoder's global half
+// front_global_kernel (64 pads per CTA, register-tiled): global MLP g = ReLU(G1 g0), the decoder's global half
 //   beta = D1[:, 64:] g, and the record the propagation GEMM's epilogue needs: -beta in BF16
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
 #include <cuda_bf16.h>
 
+#include "bwd_common.cuh"
 #include "etac_common.cuh"
 #include "etac_kernels.h"
 #include "sm100_ptx.cuh"
@@ -446,78 +447,87 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   }
 }
 
-// one warp per pad; G1 and D1's global half staged transposed so lanes read consecutive units
+// 64 pads per CTA as two register-tiled products over shared memory: G = ReLU(G0 G1^T + b_G1)
+// and B = G D1_g^T (rows: pads); thread (ti, tj) holds pads 4 ti .. + 3 x units 4 tj .. + 3.
+// Then the per-pad epilogue records: -beta in BF16 (MMA-fragment word order) and
+// (D2 beta + b_D2, m).
+constexpr int FG_PADS = 64;
+
 __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
-  __shared__ float sWgT[H * H];   // [k][u] = G1[u][k]
-  __shared__ float sWdT[H * H];   // [k][u] = D1[u][64 + k]
+  __shared__ __align__(16) float sW[H * TLD];    // [k][u] = G1[u][k], then D1[u][64 + k]
+  __shared__ __align__(16) float sX[H * TLD];    // [k][pad]: g0, then g
   __shared__ float sBg[H];
   __shared__ float sW4[3 * H];
-  __shared__ float sB4[4];
   const float* W = a.params;
-  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
-    const int u = e >> 6, k = e & (H - 1);
-    sWgT[k * H + u] = W[OFF_WG + u * H + k];
-    sWdT[k * H + u] = W[OFF_WD + u * 2 * H + H + k];
-  }
-  for (int e = threadIdx.x; e < H; e += blockDim.x) sBg[e] = W[OFF_BG + e];
-  for (int e = threadIdx.x; e < 3 * H; e += blockDim.x) sW4[e] = W[OFF_W4 + e];
-  if (threadIdx.x < 3) sB4[threadIdx.x] = W[OFF_B4 + threadIdx.x];
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int wpb = blockDim.x >> 5;
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const int p0 = blockIdx.x * FG_PADS;
   const int np = a.num_items;
-  for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < np; pad += gridDim.x * wpb) {
-    const int m = a.pad_m[pad];
-    const int gi = a.pad_gi[pad];
-    if (m == 0 || !uses_residual(a.mode)) {
-      if (lane == 0) a.c0m[gi] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
-      continue;
-    }
-    float g0[2];
-    g0[0] = a.g0a[(size_t)pad * H + lane];
-    g0[1] = a.g0a[(size_t)pad * H + 32 + lane];
-    float g[2], beta[2];
+  for (int e = tid; e < H * H; e += 256) {
+    const int u = e >> 6, k = e & (H - 1);
+    sW[k * TLD + u] = W[OFF_WG + u * H + k];
+  }
+  for (int e = tid; e < H; e += 256) sBg[e] = W[OFF_BG + e];
+  for (int e = tid; e < 3 * H; e += 256) sW4[e] = W[OFF_W4 + e];
+  for (int e = tid; e < FG_PADS * H; e += 256) {
+    const int r = e >> 6, k = e & (H - 1), pad = p0 + r;
+    sX[k * TLD + r] = pad < np ? a.g0a[(size_t)pad * H + k] : 0.f;
+  }
+  __syncthreads();
+  float acc[4][4];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = lane + 32 * h;
-      float acc = sBg[u];
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int k = 0; k < 32; ++k) acc = fmaf(sWgT[k * H + u], __shfl_sync(0xffffffffu, g0[0], k), acc);
+    for (int j = 0; j < 4; ++j) acc[i][j] = sBg[4 * tj + j];
+  tile_acc(sX, sW, ti, tj, acc);
+  __syncthreads();   // g0 and G1 are read; g and D1's global half take their places
 #pragma unroll
-      for (int k = 0; k < 32; ++k)
-        acc = fmaf(sWgT[(32 + k) * H + u], __shfl_sync(0xffffffffu, g0[1], k), acc);
-      g[h] = fmaxf(acc, 0.f);
-    }
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int u = lane + 32 * h;
-      float acc = 0.f;
+    for (int j = 0; j < 4; ++j) sX[(4 * tj + j) * TLD + 4 * ti + i] = fmaxf(acc[i][j], 0.f);
+  for (int e = tid; e < H * H; e += 256) {
+    const int u = e >> 6, k = e & (H - 1);
+    sW[k * TLD + u] = W[OFF_WD + u * 2 * H + H + k];
+  }
+  __syncthreads();
 #pragma unroll
-      for (int k = 0; k < 32; ++k) acc = fmaf(sWdT[k * H + u], __shfl_sync(0xffffffffu, g[0], k), acc);
+  for (int i = 0; i < 4; ++i)
 #pragma unroll
-      for (int k = 0; k < 32; ++k)
-        acc = fmaf(sWdT[(32 + k) * H + u], __shfl_sync(0xffffffffu, g[1], k), acc);
-      beta[h] = acc;
-      // -beta in BF16, words (channels 2w, 2w + 1) stored in MMA-fragment order: word
-      // w = 8 s + 4 hh + t goes to position 8 t + 2 s + hh (see the propagation GEMM)
-      __nv_bfloat16 nbv = __float2bfloat16_rn(-acc);
-      const unsigned short mine = *reinterpret_cast<unsigned short*>(&nbv);
-      const unsigned short odd = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)mine, 1);
-      if ((lane & 1) == 0) {
-        const int w = u >> 1, s4 = w >> 3, hh = (w >> 2) & 1, t = w & 3;
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;   // the D1 bias is part of the h0 table
+  tile_acc(sX, sW, ti, tj, acc);
+  const bool res = uses_residual(a.mode);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pad = p0 + 4 * ti + i;
+    const bool ok = pad < np;
+    const int m = ok ? a.pad_m[pad] : 0;
+    const int gi = ok ? a.pad_gi[pad] : 0;
+    const bool live = ok && m > 0 && res;
+    // -beta in BF16: words (channels 2w, 2w + 1), word w = 8 s + 4 hh + t at position
+    // 8 t + 2 s + hh (the propagation GEMM's fragment order); this thread has w = 2 tj, 2 tj + 1
+    if (live) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int w = 2 * tj + h, s4 = w >> 3, hh = (w >> 2) & 1, t = w & 3;
+        __nv_bfloat162 v = __floats2bfloat162_rn(-acc[i][2 * h], -acc[i][2 * h + 1]);
         reinterpret_cast<uint32_t*>(a.negbeta)[(size_t)gi * 32 + 8 * t + 2 * s4 + hh] =
-            (uint32_t)mine | ((uint32_t)odd << 16);
+            *reinterpret_cast<uint32_t*>(&v);
       }
     }
-    float c0[3];
+    // c0 = D2 beta + b_D2: partial over this thread's 4 units, summed over the 16 threads of
+    // the pad (a half warp)
+    float c[3];
 #pragma unroll
     for (int q = 0; q < 3; ++q) {
-      float v = fmaf(sW4[q * H + lane], beta[0], sW4[q * H + 32 + lane] * beta[1]);
+      float v = 0.f;
 #pragma unroll
-      for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
-      c0[q] = v + sB4[q];
+      for (int j = 0; j < 4; ++j) v = fmaf(sW4[q * H + 4 * tj + j], acc[i][j], v);
+#pragma unroll
+      for (int d = 8; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+      c[q] = v + W[OFF_B4 + q];
     }
-    if (lane == 0) a.c0m[gi] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
+    if (ok && tj == 0)
+      a.c0m[gi] = live ? make_float4(c[0], c[1], c[2], __int_as_float(m))
+                       : make_float4(0.f, 0.f, 0.f, __int_as_float(m));
   }
 }
 
