@@ -478,47 +478,66 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
 }
 
 // ----------------------------------------------------------------------------- R2
-// warp per pad: ag = G1 g0 + b_G1, g = ReLU(ag), beta = D1[:, 64:] g (FP32; the decoder's
-// bias rides in the h0 table)
+// 64 pads per CTA, two register-tiled products: ag = G0 G1^T + b_G1, g = ReLU(ag),
+// beta = g D1_g^T (FP32; the decoder's bias rides in the h0 table); thread (ti, tj) holds pads
+// 4 ti .. + 3 x units 4 tj .. + 3
+constexpr int R2_PADS = 64;
+
 __global__ void __launch_bounds__(256) bwd_global_kernel(BwdBatchedArgs a) {
-  __shared__ float sGT[H * H];   // [k][c] = G1[c][k]
-  __shared__ float sDT[H * H];   // [k][c] = D1[c][64 + k]
+  __shared__ __align__(16) float sW[H * TLD];   // [k][c] = G1[c][k], then D1[c][64 + k]
+  __shared__ __align__(16) float sX[H * TLD];   // [k][pad]: g0, then g
   const float* W = a.params;
-  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const int p0 = blockIdx.x * R2_PADS;
+  for (int e = tid; e < H * H; e += 256) {
     const int c = e >> 6, k = e & (H - 1);
-    sGT[k * H + c] = W[OFF_WG + c * H + k];
-    sDT[k * H + c] = W[OFF_WD + c * 2 * H + H + k];
+    sW[k * TLD + c] = W[OFF_WG + c * H + k];
+  }
+  for (int e = tid; e < R2_PADS * H; e += 256) {
+    const int r = e >> 6, k = e & (H - 1), pad = p0 + r;
+    sX[k * TLD + r] = pad < a.num_items ? a.pr[(size_t)pad * PR_STRIDE + PR_G0 + k] : 0.f;
   }
   __syncthreads();
-  const int lane = threadIdx.x & 31, wpb = blockDim.x >> 5;
-  for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < a.num_items; pad += gridDim.x * wpb) {
-    if (a.pad_m[pad] == 0) continue;
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = W[OFF_BG + 4 * tj + j];
+  tile_acc(sX, sW, ti, tj, acc);
+  __syncthreads();   // g0 and G1 are read; g and D1's global half take their places
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pad = p0 + 4 * ti + i;
+    const bool live = pad < a.num_items && a.pad_m[pad] > 0;
+    float* pr = a.pr + (size_t)(live ? pad : 0) * PR_STRIDE;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * tj + j;
+      const float g = relu(acc[i][j]);
+      sX[c * TLD + 4 * ti + i] = g;
+      if (live) {
+        pr[PR_AG + c] = acc[i][j];
+        pr[PR_G + c] = g;
+      }
+    }
+  }
+  for (int e = tid; e < H * H; e += 256) {
+    const int c = e >> 6, k = e & (H - 1);
+    sW[k * TLD + c] = W[OFF_WD + c * 2 * H + H + k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sX, sW, ti, tj, acc);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pad = p0 + 4 * ti + i;
+    if (pad >= a.num_items || a.pad_m[pad] == 0) continue;
     float* pr = a.pr + (size_t)pad * PR_STRIDE;
-    const float x0 = pr[PR_G0 + lane], x1 = pr[PR_G0 + 32 + lane];
-    float ag[2], g[2];
 #pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = lane + 32 * h;
-      float acc = W[OFF_BG + c];
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fmaf(sGT[k * H + c], __shfl_sync(FULL, x0, k), acc);
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fmaf(sGT[(32 + k) * H + c], __shfl_sync(FULL, x1, k), acc);
-      ag[h] = acc;
-      g[h] = relu(acc);
-    }
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int c = lane + 32 * h;
-      float acc = 0.f;   // the D1 bias is part of the h0 table (h0 = D1_f f0 + b_D1)
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fmaf(sDT[k * H + c], __shfl_sync(FULL, g[0], k), acc);
-#pragma unroll 8
-      for (int k = 0; k < 32; ++k) acc = fmaf(sDT[(32 + k) * H + c], __shfl_sync(FULL, g[1], k), acc);
-      pr[PR_AG + c] = ag[h];
-      pr[PR_G + c] = g[h];
-      pr[PR_BETA + c] = acc;
-    }
+    for (int j = 0; j < 4; ++j) pr[PR_BETA + 4 * tj + j] = acc[i][j];
   }
 }
 
@@ -696,10 +715,82 @@ __global__ void __launch_bounds__(256) bwd_reduce_a3_kernel(BwdBatchedArgs a) {
   if (in && j == 0) a.a3[e] = s;
 }
 
+// ----------------------------------------------------------------------------- R4a
+// 64 pads per CTA, two register-tiled products: S = dL/dbeta (the decoder partials of the
+// pad's node ranges, summed in range order), dg = S D1_g, dag = dg [ag > 0], and
+// dA2 = (dag G1) [g0 > 0]: each channel's dA2 at its argmax node (the pooled value is that
+// node's ReLU(a2)).  Records S, dag and dA2 per pad.
+constexpr int R4A_PADS = 64;
+
+__global__ void __launch_bounds__(256) bwd_padmlp_kernel(BwdBatchedArgs a) {
+  __shared__ __align__(16) float sW[H * TLD];   // [u][c] = D1[u][64 + c], then G1[c][k]
+  __shared__ __align__(16) float sX[H * TLD];   // [k][pad]: S, then dag
+  const float* W = a.params;
+  const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
+  const int p0 = blockIdx.x * R4A_PADS;
+  for (int e = tid; e < H * H; e += 256) {
+    const int u = e >> 6, c = e & (H - 1);
+    sW[u * TLD + c] = W[OFF_WD + u * 2 * H + H + c];
+  }
+  for (int e = tid; e < R4A_PADS * H; e += 256) {
+    const int r = e >> 6, k = e & (H - 1), pad = p0 + r;
+    float v = 0.f;
+    if (pad < a.num_items && a.pad_m[pad] > 0) {
+      const int ty = a.pad_type[pad];
+      const int ninst = a.inst_off[ty + 1] - a.inst_off[ty];
+      const float* sp = a.spart + ((size_t)a.s_toff[ty] + a.pad_inst[pad]) * H + k;
+      for (int q = 0; q < a.s_nr[ty]; ++q) v += sp[(size_t)q * ninst * H];
+      a.pr[(size_t)pad * PR_STRIDE + PR_S + k] = v;
+    }
+    sX[k * TLD + r] = v;
+  }
+  __syncthreads();
+  float acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sX, sW, ti, tj, acc);   // dg[pad][c]
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pad = p0 + 4 * ti + i;
+    const bool live = pad < a.num_items && a.pad_m[pad] > 0;
+    float* pr = a.pr + (size_t)(live ? pad : 0) * PR_STRIDE;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int c = 4 * tj + j;
+      const float dag = live && pr[PR_AG + c] > 0.f ? acc[i][j] : 0.f;
+      sX[c * TLD + 4 * ti + i] = dag;
+      if (live) pr[PR_DAG + c] = dag;
+    }
+  }
+  for (int e = tid; e < H * H; e += 256) {
+    const int c = e >> 6, k = e & (H - 1);
+    sW[c * TLD + k] = W[OFF_WG + c * H + k];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+  tile_acc(sX, sW, ti, tj, acc);   // dg0[pad][k]
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int pad = p0 + 4 * ti + i;
+    if (pad >= a.num_items || a.pad_m[pad] == 0) continue;
+    float* pr = a.pr + (size_t)pad * PR_STRIDE;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int k = 4 * tj + j;
+      pr[PR_D + k] = pr[PR_G0 + k] > 0.f ? acc[i][j] : 0.f;
+    }
+  }
+}
+
 // ----------------------------------------------------------------------------- R4
-// warp per pad (static assignment, 8 warps per CTA): the global MLP reverse, dA2 of every
-// channel at its argmax node (ReLU' of the pooled value: the pooled value is that node's
-// ReLU(a2)), and the E1 reverse of each distinct argmax node.  The E1 / b1 partials live in
+// warp per pad (static assignment, 8 warps per CTA), from the dA2 that bwd_padmlp_kernel
+// recorded: the E1 reverse of each distinct argmax node.  The E1 / b1 partials live in
 // registers (lane l owns units l and l + 32) and are summed over the CTA's warps in warp order.
 // Per pad it records dA2, each channel's slot in the pad's list of distinct argmax nodes and
 // those nodes' inputs, from which R4b sums dE2 and b2 per 64-pad chunk.
@@ -731,18 +822,9 @@ __global__ void __launch_bounds__(R4_WARPS * 32, 3) bwd_padrev_kernel(BwdBatched
     const uint32_t* bits = a.maskbits + a.mask_woff[pad];
     const int rt0 = reinterpret_cast<const int*>(pr)[PR_ROUTE + lane];
     const int rt1 = reinterpret_cast<const int*>(pr)[PR_ROUTE + 32 + lane];
-    // S = dL/dbeta: the decoder partials of the type's node ranges, in range order
-    float s0 = 0.f, s1 = 0.f;
-    {
-      const int ninst = a.inst_off[ty + 1] - a.inst_off[ty];
-      const float* sp = a.spart + ((size_t)a.s_toff[ty] + a.pad_inst[pad]) * H;
-      for (int r = 0; r < a.s_nr[ty]; ++r) {
-        s0 += sp[(size_t)r * ninst * H + lane];
-        s1 += sp[(size_t)r * ninst * H + 32 + lane];
-      }
-      pr[PR_S + lane] = s0;
-      pr[PR_S + 32 + lane] = s1;
-    }
+    float d[2];   // dA2 of channel k at its argmax node (bwd_padmlp_kernel)
+    d[0] = pr[PR_D + lane];
+    d[1] = pr[PR_D + 32 + lane];
     // routes: the distinct argmax nodes, channels 0..31 first (lowest lane of each node),
     // then nodes of channels 32..63 that no channel below 32 routes to; slot of each channel
     int nd = 0;
@@ -778,36 +860,6 @@ __global__ void __launch_bounds__(R4_WARPS * 32, 3) bwd_padrev_kernel(BwdBatched
         sX[q * NIN + j] = xv[j];
         pr[PR_X + q * NIN + j] = xv[j];
       }
-    }
-    // dg = D1_g^T S ; dag = dg [ag > 0] ; dg0 = G1^T dag (weights through L1: rows are
-    // read with consecutive lanes on consecutive columns)
-    float dag[2];
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = lane + 32 * h;
-      float v = 0.f;
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c)
-        v = fmaf(__ldg(W + OFF_WD + c * 2 * H + H + k), __shfl_sync(FULL, s0, c), v);
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c)
-        v = fmaf(__ldg(W + OFF_WD + (32 + c) * 2 * H + H + k), __shfl_sync(FULL, s1, c), v);
-      dag[h] = pr[PR_AG + k] > 0.f ? v : 0.f;
-    }
-    pr[PR_DAG + lane] = dag[0];
-    pr[PR_DAG + 32 + lane] = dag[1];
-    float d[2];   // dA2 of channel k at its argmax node
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-      const int k = lane + 32 * h;
-      float v = 0.f;
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c) v = fmaf(__ldg(W + OFF_WG + c * H + k), __shfl_sync(FULL, dag[0], c), v);
-#pragma unroll 8
-      for (int c = 0; c < 32; ++c)
-        v = fmaf(__ldg(W + OFF_WG + (32 + c) * H + k), __shfl_sync(FULL, dag[1], c), v);
-      d[h] = pr[PR_G0 + k] > 0.f ? v : 0.f;
-      pr[PR_D + k] = d[h];
     }
     __syncwarp();
     const unsigned dz0 = __ballot_sync(FULL, d[0] != 0.f), dz1 = __ballot_sync(FULL, d[1] != 0.f);
@@ -1280,7 +1332,7 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       break;
     }
     case BWD_STAGE_GLOBAL:
-      bwd_global_kernel<<<l.r2_grid, 256, 0, s>>>(a);
+      bwd_global_kernel<<<(a.num_items + R2_PADS - 1) / R2_PADS, 256, 0, s>>>(a);
       break;
     case BWD_STAGE_DECODER: {
       static bool c3 = false;
@@ -1299,9 +1351,13 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       bwd_reduce_a3_kernel<<<(unsigned)((tot + 255) / 256), 256, 0, s>>>(a);
       break;
     }
-    case BWD_STAGE_PADREV:
+    case BWD_STAGE_PADREV: {
+      bwd_padmlp_kernel<<<(a.num_items + R4A_PADS - 1) / R4A_PADS, 256, 0, s>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
       bwd_padrev_kernel<<<a.r4_parts, R4_WARPS * 32, 0, s>>>(a);
       break;
+    }
     case BWD_STAGE_PADSUM: {
       static bool c4b = false;
       if (!c4b) {
