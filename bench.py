@@ -66,23 +66,32 @@ SDF_FLOPS = 40.0   # pad -> object transform (18) + one primitive's SDF and test
 # named, valid only for the source hash recorded with it (null once the kernel changes)
 TRAFFIC = {
     # hand workload, 4,096 envs, one pass of --metrics dram__bytes_read.sum,dram__bytes_write.sum
-    # with the bench step's outputs (displacement and counts: profile_step --outputs count)
+    # (profile_step --outputs count: the bench step's outputs); per stage where a stage is
+    # several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "44d5b8938236d439", "bytes": 15.4e6 + 116.5e6},
+                             "sha": "8559166df3ce0a4a", "bytes": 15.3e6 + 116.4e6},
+    "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
+                            "sha": "8559166df3ce0a4a", "bytes": 6.5e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                         "sha": "29a5ddf75939fb59", "bytes": 136.3e6 + 127.3e6},
+                         "sha": "29a5ddf75939fb59", "bytes": 136.4e6 + 127.4e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                "sha": "29a5ddf75939fb59", "bytes": 330.8e6 + 43.9e6},
+                                "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 43.8e6},
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                    "sha": "29a5ddf75939fb59", "bytes": 331.0e6 + 0.5e6},
+                                    "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 0.1e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "a9e29dc2c7b4f93d", "bytes": 248.5e6 + 329.1e6},
+                       "sha": "278264aaac97eded", "bytes": 250.4e6 + 331.1e6},
+    "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
+                          "sha": "278264aaac97eded", "bytes": 8.8e6},
     "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                           "sha": "a9e29dc2c7b4f93d", "bytes": 238.8e6 + 65.4e6},
-    "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "a9e29dc2c7b4f93d", "bytes": 79.4e6 + 14.9e6},
+                           "sha": "278264aaac97eded", "bytes": 238.8e6 + 65.4e6},
+    "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
+                             "sha": "278264aaac97eded", "bytes": 75.5e6},
+    "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
+                          "sha": "278264aaac97eded", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "a9e29dc2c7b4f93d", "bytes": 102.4e6 + 11.7e6},
+                          "sha": "278264aaac97eded", "bytes": 102.4e6 + 12.0e6},
+    "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
+                                     "sha": "278264aaac97eded", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
 }
 
 
@@ -717,7 +726,8 @@ def main():
         byts = npads * (4 * H + 2 * H + 16)               # g0 in, -beta (BF16) and (c0, m) out
         per["front_global_kernel"] = {
             "bound": "hbm", "achieved": byts / t / 1e9, "peak": peaks["hbm_gbs"], "unit": "GB/s",
-            "frac": byts / t / 1e9 / peaks["hbm_gbs"], "traffic": None, "ms": t * 1e3,
+            "frac": byts / t / 1e9 / peaks["hbm_gbs"],
+            "traffic": full_size and traffic_for("front_global_kernel") or None, "ms": t * 1e3,
             "peak_source": f"{peak_src} hbm_gbs"}
         name = max(per, key=lambda k: per[k]["ms"])
         roof = dict(per[name], kernel=name)

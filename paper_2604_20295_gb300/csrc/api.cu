@@ -1079,7 +1079,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
                 "BF16 front launch");
       timing_end(c, ts, s);
       ts = timing_begin(c, K_GLOBAL, s);
-      ETAC_CUDA(c, etac::launch_front_global(f, ((int)EP + 63) / 64, s),
+      ETAC_CUDA(c, etac::launch_front_global(f, c->num_sms, s),
                 "BF16 global-feature launch");
       timing_end(c, ts, s);
       etac::GemmParams& g = c->gemm;

@@ -140,7 +140,7 @@ size_t front_smem_bytes(int nmax, int K);
 cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s);
 cudaError_t front_occupancy(int nmax, int K, int* blocks_per_sm);
 cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s);
-cudaError_t launch_front_global(const FrontArgs& a, int grid, cudaStream_t s);
+cudaError_t launch_front_global(const FrontArgs& a, int num_sms, cudaStream_t s);
 
 size_t batched_smem_bytes(int nmax, int K);
 int batched_threads();

@@ -447,6 +447,82 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   }
 }
 
+// one warp per pad (small batches, where 64-pad tiles would leave most SMs idle); G1 and D1's
+// global half staged transposed so lanes read consecutive units
+__global__ void __launch_bounds__(256) front_global_warp_kernel(FrontArgs a) {
+  __shared__ float sWgT[H * H];   // [k][u] = G1[u][k]
+  __shared__ float sWdT[H * H];   // [k][u] = D1[u][64 + k]
+  __shared__ float sBg[H];
+  __shared__ float sW4[3 * H];
+  __shared__ float sB4[4];
+  const float* W = a.params;
+  for (int e = threadIdx.x; e < H * H; e += blockDim.x) {
+    const int u = e >> 6, k = e & (H - 1);
+    sWgT[k * H + u] = W[OFF_WG + u * H + k];
+    sWdT[k * H + u] = W[OFF_WD + u * 2 * H + H + k];
+  }
+  for (int e = threadIdx.x; e < H; e += blockDim.x) sBg[e] = W[OFF_BG + e];
+  for (int e = threadIdx.x; e < 3 * H; e += blockDim.x) sW4[e] = W[OFF_W4 + e];
+  if (threadIdx.x < 3) sB4[threadIdx.x] = W[OFF_B4 + threadIdx.x];
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int wpb = blockDim.x >> 5;
+  const int np = a.num_items;
+  for (int pad = blockIdx.x * wpb + (threadIdx.x >> 5); pad < np; pad += gridDim.x * wpb) {
+    const int m = a.pad_m[pad];
+    const int gi = a.pad_gi[pad];
+    if (m == 0 || !uses_residual(a.mode)) {
+      if (lane == 0) a.c0m[gi] = make_float4(0.f, 0.f, 0.f, __int_as_float(m));
+      continue;
+    }
+    float g0[2];
+    g0[0] = a.g0a[(size_t)pad * H + lane];
+    g0[1] = a.g0a[(size_t)pad * H + 32 + lane];
+    float g[2], beta[2];
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = lane + 32 * h;
+      float acc = sBg[u];
+#pragma unroll
+      for (int k = 0; k < 32; ++k) acc = fmaf(sWgT[k * H + u], __shfl_sync(0xffffffffu, g0[0], k), acc);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        acc = fmaf(sWgT[(32 + k) * H + u], __shfl_sync(0xffffffffu, g0[1], k), acc);
+      g[h] = fmaxf(acc, 0.f);
+    }
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int u = lane + 32 * h;
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < 32; ++k) acc = fmaf(sWdT[k * H + u], __shfl_sync(0xffffffffu, g[0], k), acc);
+#pragma unroll
+      for (int k = 0; k < 32; ++k)
+        acc = fmaf(sWdT[(32 + k) * H + u], __shfl_sync(0xffffffffu, g[1], k), acc);
+      beta[h] = acc;
+      // -beta in BF16, words (channels 2w, 2w + 1) stored in MMA-fragment order: word
+      // w = 8 s + 4 hh + t goes to position 8 t + 2 s + hh (see the propagation GEMM)
+      __nv_bfloat16 nbv = __float2bfloat16_rn(-acc);
+      const unsigned short mine = *reinterpret_cast<unsigned short*>(&nbv);
+      const unsigned short odd = (unsigned short)__shfl_down_sync(0xffffffffu, (unsigned)mine, 1);
+      if ((lane & 1) == 0) {
+        const int w = u >> 1, s4 = w >> 3, hh = (w >> 2) & 1, t = w & 3;
+        reinterpret_cast<uint32_t*>(a.negbeta)[(size_t)gi * 32 + 8 * t + 2 * s4 + hh] =
+            (uint32_t)mine | ((uint32_t)odd << 16);
+      }
+    }
+    float c0[3];
+#pragma unroll
+    for (int q = 0; q < 3; ++q) {
+      float v = fmaf(sW4[q * H + lane], beta[0], sW4[q * H + 32 + lane] * beta[1]);
+#pragma unroll
+      for (int d = 16; d > 0; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+      c0[q] = v + sB4[q];
+    }
+    if (lane == 0) a.c0m[gi] = make_float4(c0[0], c0[1], c0[2], __int_as_float(m));
+  }
+}
+
 // 64 pads per CTA as two register-tiled products over shared memory: G = ReLU(G0 G1^T + b_G1)
 // and B = G D1_g^T (rows: pads); thread (ti, tj) holds pads 4 ti .. + 3 x units 4 tj .. + 3.
 // Then the per-pad epilogue records: -beta in BF16 (MMA-fragment word order) and
@@ -562,8 +638,12 @@ cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_front_global(const FrontArgs& a, int grid, cudaStream_t s) {
-  front_global_kernel<<<grid, 256, 0, s>>>(a);
+// tiles of 64 pads for batches of at least 64 pads per SM; one warp per pad below that
+cudaError_t launch_front_global(const FrontArgs& a, int num_sms, cudaStream_t s) {
+  if (a.num_items >= 64 * num_sms)
+    front_global_kernel<<<(a.num_items + FG_PADS - 1) / FG_PADS, 256, 0, s>>>(a);
+  else
+    front_global_warp_kernel<<<std::max(1, std::min(4 * num_sms, (a.num_items + 7) / 8)), 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 
