@@ -120,6 +120,12 @@ __device__ __forceinline__ uint32_t bf2_bits(float a, float b) {
 __device__ __forceinline__ float bf_rest(float x) {   // x - BF16(x), itself rounded later
   return x - __bfloat162float(__float2bfloat16_rn(x));
 }
+// The exact (df32) decision of an undecided node, kept out of line: it runs for a thin band of
+// nodes only, and inlined its code crowds the instruction cache of the streaming loop.
+__device__ __noinline__ NodeContact front_refine(const PadObj* po, int K, float3 p, float3 nrm) {
+  return contact_refine(po, K, p, nrm, 0.f);
+}
+
 __device__ __forceinline__ void front_pack_row(uint4* dst, float3 p, float3 nr, const float* u) {
   dst[0] = make_uint4(bf2_bits(p.x, p.y), bf2_bits(p.z, bf_rest(p.x)),
                       bf2_bits(bf_rest(p.y), bf_rest(p.z)), bf2_bits(nr.x, nr.y));
@@ -273,7 +279,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
         i = sCand[ncand - cnt + lane];
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        c = contact_refine(spo, a.K, p, nr, 0.f);
+        c = front_refine(spo, a.K, p, nr);
         front_write_node(a, btrow, n, base, i, c);
         if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       }
