@@ -69,9 +69,9 @@ TRAFFIC = {
     # (profile_step --outputs count: the bench step's outputs); per stage where a stage is
     # several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "8559166df3ce0a4a", "bytes": 15.3e6 + 116.4e6},
+                             "sha": "b23e176faad17a19", "bytes": 14.8e6 + 116.7e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "8559166df3ce0a4a", "bytes": 6.5e6},
+                            "sha": "b23e176faad17a19", "bytes": 6.6e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                          "sha": "29a5ddf75939fb59", "bytes": 136.4e6 + 127.4e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
