@@ -69,3 +69,27 @@ def test_null_context_calls_fail_cleanly(lib):
     assert lib.etac_step_forward(None, None, None, None) == 1
     assert lib.etac_step_backward(None, None, None, None, None, None, None) == 1
     lib.etac_destroy(None)
+
+
+def _header_enums():
+    """name -> value of every `ETAC_NAME = value` in the header's enums."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    return {m.group(1): int(m.group(2)) for m in re.finditer(r"\bETAC_([A-Z0-9_]+)\s*=\s*(\d+)", src)}
+
+
+def test_binding_constants_match_the_header():
+    """The binding's mode, precision, algorithm, object and status numbers are the header's,
+    and the oracle numbers the modes the same way."""
+    import oracle as O
+
+    e = _header_enums()
+    for name in ("MODE_FULL", "MODE_LINEAR_ONLY", "MODE_RESIDUAL_ONLY", "MODE_PENETRATION_ONLY",
+                 "PREC_FP32", "PREC_BF16", "ALGO_PLAIN", "ALGO_BATCHED"):
+        assert getattr(X, name) == e[name], name
+    for name in ("MODE_FULL", "MODE_LINEAR_ONLY", "MODE_RESIDUAL_ONLY", "MODE_PENETRATION_ONLY"):
+        assert getattr(O, name) == e[name], name
+    for name in ("OBJ_NONE", "OBJ_SPHERE", "OBJ_BOX", "OBJ_CYLINDER", "OBJ_CAPSULE"):
+        assert getattr(I, name) == e[name], name
+    for code, label in X.STATUS_NAMES.items():
+        assert e[label[len("ETAC_"):]] == code, label
+    assert X.ERR_INVALID_ARG == e["ERR_INVALID_ARG"]
