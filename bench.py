@@ -347,6 +347,63 @@ def config_c4_fit(I, theta0, with_oracle):
             "param_rel_error_start": err0, "seconds": h["seconds"]}
 
 
+def config_c4_fd(X, I, torch, dev):
+    """The reverse mode against FP64 central differences (h = 1e-6) of the GPU FP64 forward:
+    1 env, one 8x8 flat pad, each primitive; the 6 pose components, alpha and 24 sampled
+    weights.  The adjoint is the batched FP32 reverse mode (the one timed above)."""
+    h = 1e-6
+    out = {"workload": "1 env x 8x8 flat pad per primitive, FP64 central differences, h = 1e-6"}
+    worst = 0.0
+    for name, ot in (("sphere", I.OBJ_SPHERE), ("box", I.OBJ_BOX), ("cylinder", I.OBJ_CYLINDER),
+                     ("capsule", I.OBJ_CAPSULE)):
+        sc = I.grad_scene(ot, seed=0)
+        th = I.make_params(7).astype(np.float64)
+        G = np.random.default_rng(5).normal(size=(sc.total_nodes, 3))
+        sim = X.TactileSim(sc, device=dev)
+        try:
+            sim.set_model(th.astype(np.float32), X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+            sim.step()
+            g = sim.backward(torch.as_tensor(np.asarray(G, np.float32), device=dev))
+            torch.cuda.synchronize()
+            adj_pose = g["obj_pose"].cpu().numpy().astype(np.float64)[0]
+            adj_par = g["params"].cpu().numpy().astype(np.float64)
+
+            def loss(pose, theta):
+                disp = torch.zeros(sc.total_nodes, 3, dtype=torch.float64, device=dev)
+                ten = [torch.as_tensor(np.asarray(v, np.float64), device=dev)
+                       for v in (sc.obj_dims, pose, sc.pad_pose, theta)]
+                X.etac_forward_f64(sim.ctx, X.etac_model_desc(64, 0, 0, 0), sim.obj_type.data_ptr(),
+                                   *[t.data_ptr() for t in ten], disp.data_ptr(),
+                                   torch.cuda.current_stream(dev).cuda_stream)
+                torch.cuda.synchronize()
+                return float((disp.cpu().numpy() * G).sum())
+
+            op = sc.obj_pose.astype(np.float64)
+            fd_pose = np.zeros(6)
+            for a in range(6):
+                def pose(sgn):
+                    o = op.copy()
+                    if a < 3:
+                        o[a] += sgn * h
+                    else:
+                        ax = np.zeros(3)
+                        ax[a - 3] = 1.0
+                        o[3:] = I._qmul(I._axis_angle(ax, sgn * h), o[3:] / np.linalg.norm(o[3:]))
+                    return o
+                fd_pose[a] = (loss(pose(1), th) - loss(pose(-1), th)) / (2 * h)
+            idx = [0] + list(np.random.default_rng(11).choice(np.arange(1, th.size), 24, replace=False))
+            fd_par = np.array([(loss(op, th + h * (np.arange(th.size) == k)) -
+                                loss(op, th - h * (np.arange(th.size) == k))) / (2 * h) for k in idx])
+        finally:
+            sim.close()
+        ep = float(np.abs(adj_pose - fd_pose).max() / max(np.abs(fd_pose).max(), 1e-3))
+        eq = float(np.abs(adj_par[idx] - fd_par).max() / max(np.abs(fd_par).max(), 1e-3))
+        out[name] = {"pose_max_rel_err": ep, "params_max_rel_err": eq}
+        worst = max(worst, ep, eq)
+    out["worst_max_rel_err"] = worst
+    return out
+
+
 def config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle):
     """Scale and unevenness: 16,384 envs x 6 flat pads of 8x8 .. 64x64 nodes (16 pad types),
     1-3 primitives per env; BF16 forward and FP32 reverse mode."""
@@ -769,6 +826,7 @@ def main():
         with_oracle = not args.no_cpu
         configs = {"c3_bf16_single_pad": config_c3(X, I, torch, dev, stream, flush, theta, with_oracle),
                    "c4_fit": config_c4_fit(I, theta, with_oracle),
+                   "c4_fd_check": config_c4_fd(X, I, torch, dev),
                    "c5_uneven_16384": config_c5(X, I, torch, dev, stream, flush, theta, peaks,
                                                 with_oracle)}
 
