@@ -95,6 +95,28 @@ TRAFFIC = {
 }
 
 
+# warp instructions per node of an issue-bound kernel (smsp__inst_executed.sum of one
+# --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
+INSTR = {
+    "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
+                             "sha": "b23e176faad17a19", "per_node": 138151353 / 9437184},
+}
+
+
+def instr_per_node(name):
+    """Recorded warp instructions per node of kernel `name`, or None once its source changed."""
+    import hashlib
+    rec = INSTR.get(name)
+    if not rec:
+        return None
+    try:
+        with open(os.path.join(ROOT, rec["file"]), "rb") as f:
+            sha = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    return rec["per_node"] if sha == rec["sha"] else None
+
+
 def traffic_for(name):
     """Recorded DRAM bytes per launch of kernel `name`, or None when the kernel's source file
     no longer has the hash the capture was taken with."""
@@ -766,6 +788,18 @@ def main():
             "ms": t * 1e3, "peak_source": f"{peak_src} bf16_tflops (burst)",
             "note": "encoder on active nodes (mma.sync) + SDF and max-pool per node; "
                     "HBM bytes are small here (12 B per active node + 4 B per pad)"}
+        ipn = instr_per_node("front_contact_kernel")
+        if ipn is not None:
+            # the bound that explains this kernel: instruction issue (one warp instruction per
+            # scheduler per cycle: SMs x 4 x max SM clock)
+            issue_peak = nsm * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
+            ach = ipn * nodes / t / 1e9
+            per["front_contact_kernel"]["issue"] = {
+                "bound": "issue", "achieved": ach, "peak": issue_peak,
+                "unit": "G warp-instructions/s", "frac": ach / issue_peak,
+                "warp_instructions_per_node": ipn,
+                "peak_source": f"derived: {nsm} SMs x 4 schedulers x "
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}
         t = kern["prop_gemm_kernel"]["ms_per_launch"] / 1e3
         alg = 6.0 * work["pairs"] + 2.0 * 3 * H * work["passive"]
         exe = executed_gemm_flops(scene)
