@@ -43,6 +43,23 @@ def _peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def max_over_ranks(x, pg, device):
+    """The largest of every rank's x (the job's time is its slowest rank's), via the process
+    group `pg` (torch.distributed, or None for one process); float64 tensor on `device`."""
+    if pg is None:
+        return x
+    import torch
+    t = torch.tensor([x], device=device, dtype=torch.float64)
+    pg.all_reduce(t, op=pg.ReduceOp.MAX)
+    return float(t)
+
+
+def job_rate(nodes_per_rank_step, steps, world, seconds):
+    """Whole-job node-steps/s: every rank runs its own replica of the workload (weak scaling),
+    so the job processes nodes x steps x world in the slowest rank's time."""
+    return nodes_per_rank_step * steps * world / seconds
+
+
 def algorithmic_work(scene, counts):
     """FLOPs and bytes the method itself requires per step (implementation overheads such as
     recomputation or padding are not counted).  counts = active nodes per pad."""
@@ -576,16 +593,9 @@ def main():
     ktimes = X.etac_kernel_times(sim.ctx)
     X.etac_enable_timing(sim.ctx, False)
 
-    def max_over_ranks(x):
-        if pg:
-            t = torch.tensor([x], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            x = float(t)
-        return x
-
     nodes = scene.total_nodes
-    eager_s = max_over_ranks(sum(step_ms) / 1e3)
-    eager = {"value": nodes * args.steps * world / eager_s, "unit": UNIT,
+    eager_s = max_over_ranks(sum(step_ms) / 1e3, pg, dev)
+    eager = {"value": job_rate(nodes, args.steps, world, eager_s), "unit": UNIT,
              "ms_per_step": 1e3 * eager_s / args.steps}
 
     # ---- the same step captured once in a CUDA graph and replayed K times (the headline)
@@ -615,8 +625,8 @@ def main():
         if pg:
             pg.barrier()
         g_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
-        graph_s = max_over_ranks(sum(g_ms) / 1e3)
-        graph = {"value": nodes * args.steps * world / graph_s, "unit": UNIT,
+        graph_s = max_over_ranks(sum(g_ms) / 1e3, pg, dev)
+        graph = {"value": job_rate(nodes, args.steps, world, graph_s), "unit": UNIT,
                  "ms_per_step": 1e3 * graph_s / args.steps, "launches_per_step":
                  int(sum(v[0] for v in ktimes.values()) // max(args.steps, 1))}
         step_ms = g_ms
@@ -672,13 +682,9 @@ def main():
             stream.wait_stream(cs)
         e1.record(stream)
         torch.cuda.synchronize()
-        e2e_s = e0.elapsed_time(e1) / 1e3
-        if pg:
-            t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            e2e_s = float(t)
+        e2e_s = max_over_ranks(e0.elapsed_time(e1) / 1e3, pg, dev)
         same = bool(torch.equal(h_out[(ke - 1) & 1], d_out[(ke - 1) & 1].cpu()))
-        e2e = {"value": nodes * ke * world / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d,
+        e2e = {"value": job_rate(nodes, ke, world, e2e_s), "unit": UNIT, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * e2e_s / ke,
                "pipelining": f"read-back of step k overlaps step k + 1 (two output buffers, "
                              f"{ncs} copy stream(s), {2 * ncs} chunks)",
