@@ -86,9 +86,9 @@ TRAFFIC = {
     # (profile_step --outputs count: the bench step's outputs); per stage where a stage is
     # several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "b23e176faad17a19", "bytes": 14.8e6 + 116.7e6},
+                             "sha": "878987f1693a5ed8", "bytes": 14.8e6 + 116.7e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "b23e176faad17a19", "bytes": 6.6e6},
+                            "sha": "878987f1693a5ed8", "bytes": 6.6e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                          "sha": "29a5ddf75939fb59", "bytes": 136.4e6 + 127.4e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
@@ -116,7 +116,7 @@ TRAFFIC = {
 # --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
 INSTR = {
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "b23e176faad17a19", "per_node": 138151353 / 9437184},
+                             "sha": "878987f1693a5ed8", "per_node": 138151353 / 9437184},
 }
 
 

@@ -1,29 +1,11 @@
 // bwd_common.cuh -- pieces shared by the two reverse-mode implementations (per-pad kernel of
-// the plain algorithm, staged pipeline of the batched algorithms): a register-tiled FP32
-// 64 x 64 x 64 product over staged tiles, and the reverse of one active node's contact
-// displacement u_hat = -phi n through its primitive's SDF (ETac Sec. III-A) to the
-// penetration and the object pose.
+// the plain algorithm, staged pipeline of the batched algorithms): the reverse of one active
+// node's contact displacement u_hat = -phi n through its primitive's SDF (ETac Sec. III-A) to
+// the penetration and the object pose.
 #pragma once
 #include "etac_common.cuh"
 
 namespace etac {
-
-constexpr int TLD = H + 4;   // padded row stride of staged 64 x 64 tiles (16-byte aligned)
-
-// acc[i][j] += sum_k A[k][4 ti + i] * B[k][4 tj + j], both operands k-major with stride TLD
-__device__ __forceinline__ void tile_acc(const float* A, const float* B, int ti, int tj,
-                                         float (&acc)[4][4]) {
-#pragma unroll 8
-  for (int k = 0; k < 64; ++k) {
-    const float4 a = *reinterpret_cast<const float4*>(A + k * TLD + 4 * ti);
-    const float4 b = *reinterpret_cast<const float4*>(B + k * TLD + 4 * tj);
-    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i)
-#pragma unroll
-      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
-  }
-}
 
 // Reverse of u_hat = -phi n for one active node (p, nrm) of a pad: du = dL/du_hat in the pad
 // frame.  Returns the object slot, dL/d(penetration) = n . du (n the outward normal, pad

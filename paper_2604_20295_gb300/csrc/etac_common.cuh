@@ -53,6 +53,24 @@ __device__ __forceinline__ void latch_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// ------------------------------------------------------------------ tiled FP32 product
+constexpr int TLD = H + 4;   // padded row stride of staged 64 x 64 tiles (16-byte aligned)
+
+// acc[i][j] += sum_k A[k][4 ti + i] * B[k][4 tj + j], both operands k-major with stride TLD
+__device__ __forceinline__ void tile_acc(const float* A, const float* B, int ti, int tj,
+                                         float (&acc)[4][4]) {
+#pragma unroll 8
+  for (int k = 0; k < 64; ++k) {
+    const float4 a = *reinterpret_cast<const float4*>(A + k * TLD + 4 * ti);
+    const float4 b = *reinterpret_cast<const float4*>(B + k * TLD + 4 * tj);
+    const float av[4] = {a.x, a.y, a.z, a.w}, bv[4] = {b.x, b.y, b.z, b.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) acc[i][j] = fmaf(av[i], bv[j], acc[i][j]);
+  }
+}
+
 // ------------------------------------------------------------------ double-float (df32)
 struct df {
   float hi, lo;

@@ -23,7 +23,6 @@
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
 #include <cuda_bf16.h>
 
-#include "bwd_common.cuh"
 #include "etac_common.cuh"
 #include "etac_kernels.h"
 #include "sm100_ptx.cuh"
