@@ -86,9 +86,9 @@ TRAFFIC = {
     # (profile_step --outputs count: the bench step's outputs); per stage where a stage is
     # several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "878987f1693a5ed8", "bytes": 14.8e6 + 116.7e6},
+                             "sha": "4e653f483cc9c777", "bytes": 14.8e6 + 116.7e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "878987f1693a5ed8", "bytes": 6.6e6},
+                            "sha": "4e653f483cc9c777", "bytes": 6.6e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                          "sha": "29a5ddf75939fb59", "bytes": 136.4e6 + 127.4e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
@@ -96,19 +96,19 @@ TRAFFIC = {
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                                     "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 0.1e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "278264aaac97eded", "bytes": 250.4e6 + 331.1e6},
+                       "sha": "a4299680089ac867", "bytes": 250.4e6 + 331.1e6},
     "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "278264aaac97eded", "bytes": 8.8e6},
+                          "sha": "a4299680089ac867", "bytes": 8.8e6},
     "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                           "sha": "278264aaac97eded", "bytes": 238.8e6 + 65.4e6},
+                           "sha": "a4299680089ac867", "bytes": 238.8e6 + 65.4e6},
     "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                             "sha": "278264aaac97eded", "bytes": 75.5e6},
+                             "sha": "a4299680089ac867", "bytes": 75.5e6},
     "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
-                          "sha": "278264aaac97eded", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
+                          "sha": "a4299680089ac867", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "278264aaac97eded", "bytes": 102.4e6 + 12.0e6},
+                          "sha": "a4299680089ac867", "bytes": 102.4e6 + 12.0e6},
     "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                                     "sha": "278264aaac97eded", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
+                                     "sha": "a4299680089ac867", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
 }
 
 
@@ -116,7 +116,7 @@ TRAFFIC = {
 # --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
 INSTR = {
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "878987f1693a5ed8", "per_node": 138151353 / 9437184},
+                             "sha": "4e653f483cc9c777", "per_node": 138151353 / 9437184},
 }
 
 

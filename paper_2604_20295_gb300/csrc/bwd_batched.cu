@@ -11,15 +11,17 @@
 //      channel maxima of f with their lowest-index argmax: the active nodes' encoder to FP32
 //      accuracy on tensor cores (inputs, activations and weights split into BF16 hi / lo
 //      parts), the passive candidate from the ranked f0 table;
-//   R2 bwd_global_kernel (warp per pad): ag = G1 g0 + b, g = ReLU(ag), beta = D1_g g;
+//   R2 bwd_global_kernel (64 pads per CTA, register-tiled): ag = G1 g0 + b, g = ReLU(ag),
+//      beta = D1_g g;
 //   R3 bwd_decoder_kernel (type x 64-instance groups): for every passive (instance k, node
 //      i), dz = D2^T G_ki and dA3 = dz [h0_i + beta_k > 0]; sums S_k = sum_i dA3 (per pad,
 //      complete), A3_i = sum_k dA3 (per type node, partial per group) and
 //      dD2 = sum G (x) ReLU(h0 + beta);
 //   R3b reduce the A3 partials in group order;
-//   R4 bwd_padrev_kernel (warp per pad): dg = D1_g^T S, dag = dg [ag > 0], dg0 = G1^T dag,
-//      routed to each channel's argmax node as dA2, and the E1 reverse of those nodes (E1,
-//      b1, and for an active node dL/du_hat);
+//   R4a bwd_padmlp_kernel (64 pads per CTA, register-tiled): S from the node-range partials,
+//      dg = D1_g^T S, dag = dg [ag > 0], dA2 = (G1^T dag) [g0 > 0] at each channel's argmax;
+//   R4 bwd_padrev_kernel (warp per pad): the E1 reverse of the distinct argmax nodes (E1, b1,
+//      and for an active node dL/du_hat);
 //   R4b sums over 64-pad chunks of S g^T, dag g0^T, S, dag (D1_g, G1 and their biases) and
 //      of dA2 h1^T, dA2 (E2 and b2);
 //   R5 bwd_typenode_kernel (64 type nodes per CTA): the decoder path's encoder reverse from

@@ -8,17 +8,19 @@
 //   * one FP32 pass sorts each node: certainly outside every object (passive), certainly inside
 //     with no near-tie among the discrete choices (u_hat from FP32 arithmetic, the BF16 step's
 //     error budget), or undecided (a thin band near a surface or a tie);
-//   * undecided nodes go to a short list and take the exact df32 decision 32 at a time, so
+//   * undecided nodes go to a short list and take the exact df32 decision 32 at a time (called
+//     out of line: it runs rarely, and inlined it crowds the loop's instruction cache), so
 //     contact sets equal the exact ones;
 //   * active nodes keep u_hat (Eq. 4 covers passive nodes only), their u_hat goes to the
 //     propagation GEMM's B operand, their contact bit to a per-pad bit field, and they are
 //     pushed on a short stack that the encoder drains 16 at a time on tensor cores (E1
 //     evaluated straight into the m16n8k16 A-fragment layout, E2 as BF16 MMAs with FP32
-//     accumulation); channel maxima stay in registers.  Passive nodes need no encoder: their
-//     outputs are table entries;
+//     accumulation); the running channel maxima live in shared memory between drains.
+//     Passive nodes need no encoder: their outputs are table entries;
 //   * at the end, the max-pool over the passive nodes: the first passive node of each
 //     channel's table order (ranked f0 values), 32 ranks per warp-wide test.
-// front_global_kernel (64 pads per CTA, register-tiled): global MLP g = ReLU(G1 g0), the decoder's global half
+// front_global_kernel (64 pads per CTA, two register-tiled products; one warp per pad for
+//   batches under 64 pads per SM): global MLP g = ReLU(G1 g0), the decoder's global half
 //   beta = D1[:, 64:] g, and the record the propagation GEMM's epilogue needs: -beta in BF16
 //   and D2 beta + b_D2 (ReLU(h0 + beta) = max(h0, -beta) + beta).
 #include <cuda_bf16.h>
