@@ -188,8 +188,10 @@ etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max,
  * choice in effect, writes the candidates and their milliseconds per step to *result
  * (host), synchronises `stream`, and overwrites `out`.  Not to be called during stream
  * capture.  etac_set_tuning applies a stored choice (fields that do not apply to the
- * model's algorithm are ignored).  Errors: ETAC_ERR_STATE without a batched model,
- * ETAC_ERR_INVALID_ARG for NULL in/out/result or out-of-range fields. */
+ * model's algorithm are ignored).  Both may grow the GEMM tile list and the reverse mode's
+ * work-unit list (device memory) for a new shape; steps never allocate.  Errors:
+ * ETAC_ERR_STATE without a batched model, ETAC_ERR_INVALID_ARG for NULL in/out/result or
+ * out-of-range fields, ETAC_ERR_OOM if that growth fails. */
 #define ETAC_TUNE_MAX 8
 typedef struct {
   int32_t gemm_inst_per_tile;

@@ -1,6 +1,8 @@
 // api.cu -- C ABI of libetac (declared in include/etac.h): validation, device buffers and
-// the stream-ordered launch sequences.  No function here allocates device memory after
-// etac_create_pads / etac_set_model, and no step call synchronises the host.
+// the stream-ordered launch sequences.  Device memory is allocated by etac_create_pads and
+// etac_set_model; etac_set_tuning and etac_autotune may grow the GEMM tile list and the
+// reverse mode's work units for a new shape.  No step call (forward or reverse) allocates or
+// synchronises the host.
 #include <cuda_runtime.h>
 
 #include <algorithm>
