@@ -96,19 +96,17 @@ TRAFFIC = {
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
                                     "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 0.1e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "a4299680089ac867", "bytes": 250.4e6 + 331.1e6},
+                       "sha": "090c18348ebdb9dd", "bytes": 250.4e6 + 331.1e6},
     "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "a4299680089ac867", "bytes": 8.8e6},
-    "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                           "sha": "a4299680089ac867", "bytes": 238.8e6 + 65.4e6},
+                          "sha": "090c18348ebdb9dd", "bytes": 8.8e6},
     "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                             "sha": "a4299680089ac867", "bytes": 75.5e6},
+                             "sha": "090c18348ebdb9dd", "bytes": 75.5e6},
     "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
-                          "sha": "a4299680089ac867", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
+                          "sha": "090c18348ebdb9dd", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "a4299680089ac867", "bytes": 102.4e6 + 12.0e6},
+                          "sha": "090c18348ebdb9dd", "bytes": 102.4e6 + 12.0e6},
     "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                                     "sha": "a4299680089ac867", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
+                                     "sha": "090c18348ebdb9dd", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
 }
 
 

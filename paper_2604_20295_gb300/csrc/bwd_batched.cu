@@ -636,7 +636,7 @@ __global__ void __launch_bounds__(256, 2) bwd_decoder_kernel(BwdBatchedArgs a) {
     __syncthreads();
     const float (&sH0)[R3_NODES][H] = sm.H0[buf];
     const float4 (&sG)[R3_IPW][R3_NODES] = sm.G[buf][warp];
-#pragma unroll 2
+#pragma unroll 4
     for (int r = 0; r < R3_NODES; ++r) {
       float2 A3 = make_float2(0.f, 0.f);
       if (r < cn) {
