@@ -7,6 +7,7 @@ import socket
 import subprocess
 import sys
 
+import numpy as np
 import pytest
 import torch
 import torch.distributed as dist
@@ -64,3 +65,18 @@ def test_reference_arm_under_torchrun_prints_once():
     line = json.loads(lines[0])
     assert line["impl"] == "reference" and line["n_gpus"] == 2 and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def test_algorithmic_work_counts():
+    """The roofline numerators on a hand-countable batch: two 16x16 pads with 10 and 0 active
+    nodes and one 8x8 pad with 64 (all active)."""
+    from paper_2604_20295_gb300 import inputs as I
+    sc = I.custom_scene([I.flat_pad(16, 16, 1.0), I.flat_pad(8, 8, 1.0)], [0, 0, 1], {},
+                        [(0, 0, 0, 0, 0, 0, 1)] * 3, 1, 1)
+    w = bench.algorithmic_work(sc, np.array([10, 0, 64]))
+    assert w["active"] == 10 + 64 and w["passive"] == 246        # a pad without contact counts 0
+    assert w["pairs"] == 246 * 10                                # passive x active, per pad
+    enc = 2 * (9 * 64 + 64 * 64)
+    dec = 2 * (64 * 64 + 3 * 64)
+    assert w["literal_flops"] == (256 + 64) * enc + 246 * dec + 6 * 2460
+    assert w["bytes_out"] == 12 * (256 * 2 + 64)
