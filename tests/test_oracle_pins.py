@@ -455,3 +455,96 @@ def test_planted_mistake_is_caught(name, tmp_path):
     ref, _ = TR.step(sc, th)
     failures += not np.allclose(out["disp"], ref.detach().numpy(), rtol=1e-8, atol=1e-9)
     assert failures > 0, f"planted mistake {name} passed every pin"
+
+
+# Planted mistakes in the contact step and in the hand-written reverse mode.
+_MUTANTS_REV = {
+    # every box face pushes along +axis (outward normal sign lost on the negative faces)
+    "box_face_sign": ("g[am] = q[am] >= 0 ? 1.0 : -1.0;", "g[am] = 1.0;"),
+    # capsule segment not clamped to its end caps: the capsule becomes an infinite cylinder
+    "capsule_clamp": ("double cz = q[2] < -h ? -h : (q[2] > h ? h : q[2]);",
+                      "double cz = q[2];"),
+    # d w / d alpha = -d w: sign dropped
+    "alpha_grad_sign": ("gp[0] += -d * w * dot;", "gp[0] += d * w * dot;"),
+    # ReLU gate of the decoder's hidden layer missing in the reverse pass
+    "decoder_relu_gate": ("ga3[c] = s.a3[(size_t)i * H + c] > 0 ? gz : 0.0;", "ga3[c] = gz;"),
+    # max-pool gradient routed to the first channel's argmax instead of each channel's
+    "maxpool_route": ("gf[(size_t)s.amax[c] * H + c] += gg0[c];",
+                      "gf[(size_t)s.amax[0] * H + c] += gg0[c];"),
+    # curvature (Hessian) term of d(-phi grad phi)/dx with the wrong sign
+    "hessian_sign": ("Av[a] += s.phi[i] * Hs[3 * a + b] * vo[b];",
+                     "Av[a] -= s.phi[i] * Hs[3 * a + b] * vo[b];"),
+    # rotation of the outward normal left out of the torque
+    "torque_normal_term": ("gpo[3 + a] += c1[a] - s.phi[i] * c2[a];", "gpo[3 + a] += c1[a];"),
+    # u_hat gradient taken through the normal's input column instead of u_hat's
+    "uhat_input_column": ("acc += P.W1[c * NIN + 6 + a] * ga1[c];",
+                          "acc += P.W1[c * NIN + 3 + a] * ga1[c];"),
+    # penetration gradient projected on the object-frame normal, not the pad-frame one
+    "pen_frame": ("grad_pen[gi] = npd[0] * gu[3 * i] + npd[1] * gu[3 * i + 1] + npd[2] * gu[3 * i + 2];",
+                  "grad_pen[gi] = gobj[0] * gu[3 * i] + gobj[1] * gu[3 * i + 1] + gobj[2] * gu[3 * i + 2];"),
+}
+
+
+def _rev_pin_checks(lib):
+    """The contact closed forms and the reverse-mode pins, run against `lib`; yields one
+    bool per check (True = the check passed)."""
+    # box pressed face-down (centre off the pad's origin so that both x faces are crossed)
+    delta = 0.8
+    sc = _flat_scene(12, 12, obj=(I.OBJ_BOX, (3.0, 2.0, 4.0), (0.25, 0.5, 4.0 - delta, 0, 0, 0, 1)))
+    out = O.forward(sc, _theta(), mode=O.MODE_LINEAR_ONLY, lib=lib)
+    P = sc.types[0].pos
+    inside = (np.abs(P[:, 0] - 0.25) < 3.0) & (np.abs(P[:, 1] - 0.5) < 2.0)
+    side = inside & (3.0 - np.abs(P[:, 0] - 0.25) < 4.0 - float(sc.obj_pose[2]))
+    yield bool(np.array_equal(out["mask"].astype(bool), inside)) and bool(
+        np.allclose(np.abs(out["disp"][side, 0]) * np.sign(P[side, 0] - 0.25),
+                    out["disp"][side, 0], atol=1e-12))
+    # capsule lying along y with its caps inside the pad: the caps round off the contact
+    r, hl = 3.0, 2.0
+    q = (math.sin(-math.pi / 4), 0.0, 0.0, math.cos(-math.pi / 4))
+    sc = _flat_scene(14, 14, obj=(I.OBJ_CAPSULE, (r, hl, 0), (0.0, 0.0, r - 1.0, *q)))
+    pose = np.array([0.0, 0.0, float(sc.obj_pose[2]), *q])
+    out = O.forward(sc, _theta(), mode=O.MODE_LINEAR_ONLY, obj_pose=pose, lib=lib)
+    Pd = sc.types[0].pos.astype(np.float64)
+    cy = np.clip(Pd[:, 1], -hl, hl)
+    dist = np.sqrt(Pd[:, 0] ** 2 + (Pd[:, 1] - cy) ** 2 + pose[2] ** 2)
+    yield bool(np.allclose(out["pen"], np.maximum(0, r - dist), atol=1e-12))
+    # reverse mode vs torch autograd of the restatement, every primitive
+    for ot in (I.OBJ_SPHERE, I.OBJ_BOX, I.OBJ_CYLINDER, I.OBJ_CAPSULE):
+        sc, th, G = _grad_case(ot)
+        fw = O.forward(sc, th, lib=lib)
+        bw = O.backward(sc, th, G, lib=lib)
+        U, leaves = TR.step(sc, th, mask=fw["mask"], pose_leaves=True)
+        gp, gt, gw = torch.autograd.grad((U * torch.tensor(G)).sum(),
+                                         [leaves["params"], leaves["dt"], leaves["dw"]])
+        yield (np.allclose(bw["params"], gp.numpy(), rtol=1e-9, atol=1e-10)
+               and np.allclose(bw["obj_pose"][:, :3], gt.numpy(), rtol=1e-9, atol=1e-10)
+               and np.allclose(bw["obj_pose"][:, 3:], gw.numpy(), rtol=1e-9, atol=1e-10))
+    # u_hat gradient (mask fixed) vs autograd; penetration gradient = its normal projection
+    sc, th, G = _grad_case(I.OBJ_CAPSULE, seed=3)
+    fw = O.forward(sc, th, lib=lib)
+    uh = fw["disp"] * fw["mask"][:, None]
+    bw = O.backward(sc, th, G, mask_override=fw["mask"], uhat_override=uh, lib=lib)
+    U, leaves = TR.step(sc, th, mask=fw["mask"], uhat_override=uh)
+    (gu,) = torch.autograd.grad((U * torch.tensor(G)).sum(), [leaves["uhat"]])
+    yield bool(np.allclose(bw["uhat"], gu.numpy() * fw["mask"][:, None], rtol=1e-9, atol=1e-11))
+    bw2 = O.backward(sc, th, G, lib=lib)
+    act = fw["mask"] > 0
+    nrm = fw["disp"][act] / fw["pen"][act][:, None]
+    yield bool(np.allclose(bw2["pen"][act], (bw2["uhat"][act] * nrm).sum(1), rtol=1e-9, atol=1e-12))
+
+
+def test_reverse_pin_checks_pass_on_the_oracle():
+    assert all(_rev_pin_checks(None))
+
+
+@pytest.mark.parametrize("name", sorted(_MUTANTS_REV))
+def test_planted_reverse_or_contact_mistake_is_caught(name, tmp_path):
+    """A copy of the oracle with one planted mistake in its contact step or its reverse mode
+    fails at least one of the box, capsule-cap, autograd or penetration-projection pins."""
+    src = open(os.path.join(os.path.dirname(O.__file__), "etac_oracle.c")).read()
+    old, new = _MUTANTS_REV[name]
+    assert src.count(old) == 1, name
+    p = tmp_path / "mut.c"
+    p.write_text(src.replace(old, new))
+    lib = O.load_variant(str(p), str(tmp_path / "libmut.so"))
+    assert not all(_rev_pin_checks(lib)), f"planted mistake {name} passed every pin"
