@@ -20,6 +20,7 @@ _LIB = os.path.join(_HERE, "_build", "liboracle.so")
 _lib = None
 
 MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY, MODE_PENETRATION_ONLY = 0, 1, 2, 3
+OBJ_MESH = 5
 
 
 def build(force: bool = False, src: str = _SRC, lib: str = _LIB) -> str:
@@ -40,7 +41,9 @@ class _Scene(ctypes.Structure):
                 ("num_envs", ctypes.c_int), ("pads_per_env", ctypes.c_int),
                 ("max_objects", ctypes.c_int), ("pad_type", ctypes.c_void_p),
                 ("obj_type", ctypes.c_void_p), ("obj_dims", ctypes.c_void_p),
-                ("obj_pose", ctypes.c_void_p), ("pad_pose", ctypes.c_void_p)]
+                ("obj_pose", ctypes.c_void_p), ("pad_pose", ctypes.c_void_p),
+                ("num_meshes", ctypes.c_int), ("mesh_tri_off", ctypes.c_void_p),
+                ("mesh_tri", ctypes.c_void_p)]
 
 
 def _open(path):
@@ -86,11 +89,17 @@ class _Marshalled:
             obj_type=i32(scene.obj_type), obj_dims=f64(scene.obj_dims),
             obj_pose=f64(scene.obj_pose if obj_pose is None else obj_pose),
             pad_pose=f64(scene.pad_pose if pad_pose is None else pad_pose))
+        meshes = list(getattr(scene, "meshes", []))
         a = self.arrs
+        a["mesh_tri_off"] = i32(np.concatenate([[0], np.cumsum([len(m.tris) for m in meshes],
+                                                               dtype=np.int64)]))
+        a["mesh_tri"] = (f64(np.concatenate([m.soup for m in meshes])) if meshes
+                         else np.zeros((1, 3, 3)))
         self.s = _Scene(len(scene.types), _ptr(a["type_n"]), _ptr(a["type_pos"]),
                         _ptr(a["type_nrm"]), scene.num_envs, scene.pads_per_env,
                         scene.max_objects, _ptr(a["pad_type"]), _ptr(a["obj_type"]),
-                        _ptr(a["obj_dims"]), _ptr(a["obj_pose"]), _ptr(a["pad_pose"]))
+                        _ptr(a["obj_dims"]), _ptr(a["obj_pose"]), _ptr(a["pad_pose"]),
+                        len(meshes), _ptr(a["mesh_tri_off"]), _ptr(a["mesh_tri"]))
 
 
 def forward(scene, theta, mode: int = MODE_FULL, mask_override=None, uhat_override=None,
@@ -114,6 +123,21 @@ def forward(scene, theta, mode: int = MODE_FULL, mask_override=None, uhat_overri
                          _ptr(out["pen"]), _ptr(out["active_count"]), int(nthreads))
     if rc != 0:
         raise RuntimeError(f"orc_forward failed ({rc})")
+    return out
+
+
+def mesh_sdf(scene, mesh: int, q, lib=None) -> dict:
+    """Signed distance (negative inside), outward gradient and Hessian of one of the scene's
+    meshes at object-frame points q [n,3] (FP64)."""
+    lib = _load(lib)
+    m = _Marshalled(scene)
+    q = np.ascontiguousarray(q, np.float64).reshape(-1, 3)
+    n = len(q)
+    out = dict(phi=np.zeros(n), grad=np.zeros((n, 3)), hess=np.zeros((n, 3, 3)))
+    rc = lib.orc_mesh_sdf(ctypes.byref(m.s), ctypes.c_int(mesh), ctypes.c_long(n), _ptr(q),
+                          _ptr(out["phi"]), _ptr(out["grad"]), _ptr(out["hess"]))
+    if rc != 0:
+        raise ValueError(f"orc_mesh_sdf failed ({rc})")
     return out
 
 

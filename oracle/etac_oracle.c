@@ -7,8 +7,9 @@
  *
  * What it computes, per environment and per elastomer pad (ETac, Sec. III-A):
  *   1. contact detection with signed distance fields between the pad's surface nodes and the
- *      environment's rigid primitives (Sec. III-A "Overview"): phi = min over objects,
- *      node active iff phi < 0;
+ *      environment's rigid objects (Sec. III-A "Overview"): analytic primitives or closed
+ *      triangle meshes (exact distance to the nearest surface point, sign by the winding
+ *      number); phi = min over objects, node active iff phi < 0;
  *   2. the penalty-style local displacement of an active node: it is moved onto the object
  *      surface along the outward SDF normal, u_hat = -phi * grad(phi) (Sec. III-A, Table I:
  *      3-D element displacement);
@@ -40,7 +41,7 @@
 #define H 64          /* hidden width */
 #define NIN 9         /* per-node input: position, normal, displacement */
 
-enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4 };
+enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4, OBJ_MESH = 5 };
 enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2, MODE_PENETRATION_ONLY = 3 };
 /* the terms of Eq. 4 a mode keeps: the Eq. 1 propagation, the residual network; the
  * penetration-only mode keeps neither (active nodes u_hat, passive nodes zero) */
@@ -58,6 +59,11 @@ typedef struct {
   const double* obj_dims;     /* [E*K*3] */
   const double* obj_pose;     /* [E*K*7] t, q(xyzw) world */
   const double* pad_pose;     /* [E*P*7] world */
+  /* closed triangle meshes for OBJ_MESH objects (obj_dims[0] holds the mesh index) */
+  int num_meshes;
+  const int32_t* mesh_tri_off;  /* [M+1] first triangle of each mesh                  */
+  const double* mesh_tri;       /* [sum T, 3, 3] vertices of each triangle, object frame,
+                                 * counter-clockwise seen from outside                   */
 } orc_scene;
 
 /* parameter views into the flat vector: alpha, then W (row-major out x in) and b per layer */
@@ -188,6 +194,132 @@ static double sdf(int type, const double* dims, const double* q, double* g, doub
   return INFINITY;
 }
 
+/* ----------------------------------------------------------------- triangle meshes */
+
+/* The object-mesh contact of Sec. III-A ("Overview"): signed distance from a node to a
+ * closed triangle mesh, |phi| = distance to the nearest point of the surface, negative
+ * inside.  Written as the plain definition: every triangle is visited. */
+
+/* Closest point of segment [a, b] to p: the projection parameter clamped to [0, 1]. */
+static double seg_closest(const double* p, const double* a, const double* b, double* cp,
+                          double* t_out) {
+  double ab[3] = {b[0] - a[0], b[1] - a[1], b[2] - a[2]};
+  double ap[3] = {p[0] - a[0], p[1] - a[1], p[2] - a[2]};
+  double L2 = ab[0] * ab[0] + ab[1] * ab[1] + ab[2] * ab[2];
+  double t = L2 > 0 ? (ap[0] * ab[0] + ap[1] * ab[1] + ap[2] * ab[2]) / L2 : 0.0;
+  t = t < 0 ? 0 : (t > 1 ? 1 : t);
+  double d2 = 0.0;
+  for (int k = 0; k < 3; ++k) {
+    cp[k] = a[k] + t * ab[k];
+    d2 += (p[k] - cp[k]) * (p[k] - cp[k]);
+  }
+  *t_out = t;
+  return d2;
+}
+
+/* Closest point of triangle (a, b, c) to p.  If the orthogonal projection of p onto the
+ * triangle's plane falls inside the triangle (all barycentric weights >= 0, to within
+ * 1e-12) it is that
+ * projection; otherwise the nearest point lies on the boundary, the closest of the three
+ * edge segments' points.  Writes the point to cp, the feature that holds it to *feat
+ * (0 face, 1 edge, 2 vertex) and the unit direction of the chosen edge to edir; returns the
+ * squared distance. */
+static double tri_closest(const double* p, const double* a, const double* b, const double* c,
+                          double* cp, int* feat, double* edir) {
+  double e0[3], e1[3], n[3], ap[3];
+  for (int k = 0; k < 3; ++k) { e0[k] = b[k] - a[k]; e1[k] = c[k] - a[k]; ap[k] = p[k] - a[k]; }
+  cross(e0, e1, n);
+  double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+  if (nn > 0) {
+    double s = (ap[0] * n[0] + ap[1] * n[1] + ap[2] * n[2]) / nn;
+    double q[3] = {p[0] - s * n[0], p[1] - s * n[1], p[2] - s * n[2]};
+    /* barycentric weights of q from the sub-triangle areas (signed, along n) */
+    double qa[3] = {a[0] - q[0], a[1] - q[1], a[2] - q[2]};
+    double qb[3] = {b[0] - q[0], b[1] - q[1], b[2] - q[2]};
+    double qc[3] = {c[0] - q[0], c[1] - q[1], c[2] - q[2]};
+    double xa[3], xb[3], xc[3];
+    cross(qb, qc, xa);
+    cross(qc, qa, xb);
+    cross(qa, qb, xc);
+    double wa = (xa[0] * n[0] + xa[1] * n[1] + xa[2] * n[2]) / nn;
+    double wb = (xb[0] * n[0] + xb[1] * n[1] + xb[2] * n[2]) / nn;
+    double wc = (xc[0] * n[0] + xc[1] * n[1] + xc[2] * n[2]) / nn;
+    /* a projection on a shared edge of two coplanar triangles counts as the face's point
+     * on both (the tolerance absorbs the rounding of the weights there) */
+    if (wa >= -1e-12 && wb >= -1e-12 && wc >= -1e-12) {
+      for (int k = 0; k < 3; ++k) cp[k] = q[k];
+      *feat = 0;
+      return s * s * nn;
+    }
+  }
+  const double* ends[3][2] = {{a, b}, {b, c}, {c, a}};
+  double best = INFINITY, tb = 0.0;
+  int eb = 0;
+  for (int e = 0; e < 3; ++e) {
+    double cq[3], t;
+    double d2 = seg_closest(p, ends[e][0], ends[e][1], cq, &t);
+    if (d2 < best) { best = d2; tb = t; eb = e; memcpy(cp, cq, sizeof cq); }
+  }
+  *feat = (tb > 0 && tb < 1) ? 1 : 2;
+  double L = 0.0;
+  for (int k = 0; k < 3; ++k) { edir[k] = ends[eb][1][k] - ends[eb][0][k]; L += edir[k] * edir[k]; }
+  L = sqrt(L);
+  for (int k = 0; k < 3; ++k) edir[k] = L > 0 ? edir[k] / L : 0.0;
+  return best;
+}
+
+/* Signed solid angle of triangle (a, b, c) seen from p (van Oosterom and Strackee, 1983).
+ * Its sign is that of (a-p).((b-p)x(c-p)): positive when p lies behind the triangle, on the
+ * side opposite to its normal (b-a)x(c-a), as every point inside a closed mesh does for
+ * triangles wound counter-clockwise seen from outside. */
+static double solid_angle(const double* p, const double* a, const double* b, const double* c) {
+  double A[3], B[3], C[3], bc[3];
+  for (int k = 0; k < 3; ++k) { A[k] = a[k] - p[k]; B[k] = b[k] - p[k]; C[k] = c[k] - p[k]; }
+  double la = sqrt(A[0] * A[0] + A[1] * A[1] + A[2] * A[2]);
+  double lb = sqrt(B[0] * B[0] + B[1] * B[1] + B[2] * B[2]);
+  double lc = sqrt(C[0] * C[0] + C[1] * C[1] + C[2] * C[2]);
+  cross(B, C, bc);
+  double num = A[0] * bc[0] + A[1] * bc[1] + A[2] * bc[2];
+  double den = la * lb * lc + (A[0] * B[0] + A[1] * B[1] + A[2] * B[2]) * lc +
+               (A[0] * C[0] + A[1] * C[1] + A[2] * C[2]) * lb +
+               (B[0] * C[0] + B[1] * C[1] + B[2] * C[2]) * la;
+  return 2.0 * atan2(num, den);
+}
+
+/* Signed distance to mesh `mi` at q (object frame).  The sign comes from the winding
+ * number, the total solid angle over 4 pi: 1 inside a closed, consistently oriented mesh,
+ * 0 outside; inside iff it exceeds 1/2.  The gradient is the outward unit direction
+ * between q and its nearest surface point; the Hessian is zero when that point is interior
+ * to a face, (I - e e^T - g g^T)/dist on an edge of direction e and (I - g g^T)/dist at a
+ * vertex, times the sign.  Ties between triangles keep the lowest index. */
+static double mesh_sdf(const orc_scene* sc, int mi, const double* q, double* g, double Hs[3][3]) {
+  memset(Hs, 0, sizeof(double) * 9);
+  g[0] = g[1] = g[2] = 0.0;
+  if (mi < 0 || mi >= sc->num_meshes) return INFINITY;
+  double best = INFINITY, wind = 0.0, bc[3] = {0, 0, 0}, be[3] = {0, 0, 0};
+  int bf = 0;
+  for (int t = sc->mesh_tri_off[mi]; t < sc->mesh_tri_off[mi + 1]; ++t) {
+    const double* v = sc->mesh_tri + 9 * (size_t)t;
+    double cp[3], ed[3] = {0, 0, 0};
+    int f;
+    double d2 = tri_closest(q, v, v + 3, v + 6, cp, &f, ed);
+    if (d2 < best) { best = d2; bf = f; memcpy(bc, cp, sizeof bc); memcpy(be, ed, sizeof be); }
+    wind += solid_angle(q, v, v + 3, v + 6);
+  }
+  double sgn = wind / (4.0 * M_PI) > 0.5 ? -1.0 : 1.0;
+  double d = sqrt(best);
+  if (d > 0) {
+    for (int a = 0; a < 3; ++a) g[a] = sgn * (q[a] - bc[a]) / d;
+    if (bf > 0)
+      for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) {
+          double P = (a == b) - g[a] * g[b] - (bf == 1 ? be[a] * be[b] : 0.0);
+          Hs[a][b] = sgn * P / d;
+        }
+  }
+  return sgn * d;
+}
+
 /* ----------------------------------------------------------------- per-pad state */
 
 typedef struct {
@@ -255,7 +387,9 @@ static void pad_contact(const orc_scene* sc, int pi, pad_state* s,
       double r[3] = {x[0] - to[0], x[1] - to[1], x[2] - to[2]}, q[3], gg[3], HH[3][3];
       int deg;
       mat_t_vec(Ro[k], r, q);
-      double ph = sdf(ty, sc->obj_dims + 3 * o, q, gg, HH, &deg);
+      double ph = ty == OBJ_MESH
+                      ? (deg = 0, mesh_sdf(sc, (int)sc->obj_dims[3 * o], q, gg, HH))
+                      : sdf(ty, sc->obj_dims + 3 * o, q, gg, HH, &deg);
       if (ph < best) {  /* strict: ties keep the lowest object index */
         best = ph; bk = k; bdeg = deg;
         memcpy(bg, gg, sizeof bg);
@@ -646,5 +780,19 @@ int orc_backward(const orc_scene* sc, const double* theta, int mode,
   free(gpose_p);
   free(D);
   free(offs);
+  return 0;
+}
+
+/* Signed distance, outward gradient [n*3] and Hessian [n*9] of mesh `mesh` of the scene at n
+ * object-frame points q [n*3] (the same routine the contact step calls for OBJ_MESH). */
+int orc_mesh_sdf(const orc_scene* sc, int mesh, long n, const double* q, double* phi,
+                 double* grad, double* hess) {
+  if (mesh < 0 || mesh >= sc->num_meshes) return 1;
+  for (long i = 0; i < n; ++i) {
+    double g[3], Hs[3][3];
+    phi[i] = mesh_sdf(sc, mesh, q + 3 * i, g, Hs);
+    if (grad) memcpy(grad + 3 * i, g, sizeof g);
+    if (hess) memcpy(hess + 9 * i, Hs, sizeof Hs);
+  }
   return 0;
 }

@@ -22,8 +22,9 @@ import math
 
 import numpy as np
 
-# object type codes (the C ABI uses the same numbers)
-OBJ_NONE, OBJ_SPHERE, OBJ_BOX, OBJ_CYLINDER, OBJ_CAPSULE = 0, 1, 2, 3, 4
+# object type codes (the C ABI uses the same numbers; OBJ_MESH objects name a closed
+# triangle mesh of the scene by index in obj_dims[0])
+OBJ_NONE, OBJ_SPHERE, OBJ_BOX, OBJ_CYLINDER, OBJ_CAPSULE, OBJ_MESH = 0, 1, 2, 3, 4, 5
 
 # parameter layout of the propagation model: alpha, then (W, b) for E1, E2, G1, D1, D2
 HIDDEN = 64
@@ -116,6 +117,91 @@ def curved_pad(rows: int, cols: int, pitch: float, radius: float) -> PadType:
                    pos.reshape(-1, 3).astype(np.float32), nrm.reshape(-1, 3).astype(np.float32))
 
 
+# ----------------------------------------------------------------------------- meshes
+
+
+@dataclasses.dataclass
+class Mesh:
+    """A closed triangle mesh in its object frame (mm): triangles wind counter-clockwise
+    seen from outside, so (v1 - v0) x (v2 - v0) points out of the solid."""
+    name: str
+    verts: np.ndarray        # [V,3] float32
+    tris: np.ndarray         # [T,3] int32
+
+    @property
+    def soup(self) -> np.ndarray:
+        """[T,3,3] float32 vertex coordinates of each triangle."""
+        return np.ascontiguousarray(self.verts[self.tris], np.float32)
+
+
+def box_mesh(hx: float, hy: float, hz: float) -> Mesh:
+    """Axis-aligned box of half-extents (hx, hy, hz): 8 vertices, 2 triangles per face."""
+    v = np.array([[sx * hx, sy * hy, sz * hz] for sz in (-1, 1) for sy in (-1, 1)
+                  for sx in (-1, 1)], np.float32)           # index = 4*(z>0) + 2*(y>0) + (x>0)
+    quads = [(0, 2, 3, 1), (4, 5, 7, 6),                    # -z, +z
+             (0, 1, 5, 4), (2, 6, 7, 3),                    # -y, +y
+             (0, 4, 6, 2), (1, 3, 7, 5)]                    # -x, +x
+    t = [(a, b, c) for a, b, c, d in quads] + [(a, c, d) for a, b, c, d in quads]
+    return Mesh(f"box{hx:g}x{hy:g}x{hz:g}", v, np.array(t, np.int32))
+
+
+def icosphere(radius: float, subdiv: int) -> Mesh:
+    """Icosahedron subdivided ``subdiv`` times (each triangle into four), vertices pushed
+    onto the sphere of the given radius; 20 * 4**subdiv triangles."""
+    g = (1.0 + math.sqrt(5.0)) / 2.0
+    v = [(-1, g, 0), (1, g, 0), (-1, -g, 0), (1, -g, 0), (0, -1, g), (0, 1, g), (0, -1, -g),
+         (0, 1, -g), (g, 0, -1), (g, 0, 1), (-g, 0, -1), (-g, 0, 1)]
+    v = [np.array(p, np.float64) / np.linalg.norm(p) for p in v]
+    f = [(0, 11, 5), (0, 5, 1), (0, 1, 7), (0, 7, 10), (0, 10, 11), (1, 5, 9), (5, 11, 4),
+         (11, 10, 2), (10, 7, 6), (7, 1, 8), (3, 9, 4), (3, 4, 2), (3, 2, 6), (3, 6, 8),
+         (3, 8, 9), (4, 9, 5), (2, 4, 11), (6, 2, 10), (8, 6, 7), (9, 8, 1)]
+    for _ in range(subdiv):
+        mid = {}
+
+        def m(a, b):
+            k = (min(a, b), max(a, b))
+            if k not in mid:
+                p = v[a] + v[b]
+                v.append(p / np.linalg.norm(p))
+                mid[k] = len(v) - 1
+            return mid[k]
+        f = [t for a, b, c in f for t in ((a, m(a, b), m(c, a)), (b, m(b, c), m(a, b)),
+                                           (c, m(c, a), m(b, c)), (m(a, b), m(b, c), m(c, a)))]
+    return Mesh(f"icosphere{radius:g}s{subdiv}", (radius * np.array(v)).astype(np.float32),
+                np.array(f, np.int32))
+
+
+def torus_mesh(R: float, r: float, nu: int, nv: int) -> Mesh:
+    """Torus about the z axis (tube radius r at distance R), nu x nv vertex grid; a solid
+    with a hole, for inside/outside tests that a convex shape cannot make."""
+    u = 2 * math.pi * np.arange(nu) / nu
+    w = 2 * math.pi * np.arange(nv) / nv
+    U, W = np.meshgrid(u, w, indexing="ij")
+    v = np.stack([(R + r * np.cos(W)) * np.cos(U), (R + r * np.cos(W)) * np.sin(U),
+                  r * np.sin(W)], -1).reshape(-1, 3)
+    idx = lambda i, j: (i % nu) * nv + (j % nv)
+    t = []
+    for i in range(nu):
+        for j in range(nv):
+            a, b, c, d = idx(i, j), idx(i + 1, j), idx(i + 1, j + 1), idx(i, j + 1)
+            t += [(a, b, c), (a, c, d)]
+    return Mesh(f"torus{R:g}r{r:g}", v.astype(np.float32), np.array(t, np.int32))
+
+
+def rock_mesh(seed: int, radius: float, subdiv: int = 3, amp: float = 0.2) -> Mesh:
+    """Seeded star-shaped 'rock': an icosphere whose vertex radii are scaled by
+    1 + amp * (a smooth random function of direction, |.| <= 1), so the surface stays
+    closed and free of self-intersection for amp < 1."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    base = icosphere(1.0, subdiv)
+    d = base.verts.astype(np.float64)
+    k = rng.normal(size=(6, 3))
+    ph = rng.uniform(0, 2 * math.pi, 6)
+    bump = np.mean(np.cos(d @ k.T * 1.5 + ph), axis=1)
+    v = d * (radius * (1.0 + amp * bump))[:, None]
+    return Mesh(f"rock{seed}r{radius:g}", v.astype(np.float32), base.tris.copy())
+
+
 # ----------------------------------------------------------------------------- scenes
 
 
@@ -132,6 +218,7 @@ class Scene:
     obj_pose: np.ndarray     # [E*K*7] float32 world pose t(3) q(4, xyzw)
     pad_pose: np.ndarray     # [E*P*7] float32 world pose
     name: str = ""
+    meshes: list = dataclasses.field(default_factory=list)   # list[Mesh], for OBJ_MESH
 
     @property
     def type_num_nodes(self) -> np.ndarray:
@@ -168,7 +255,8 @@ class Scene:
                      self.obj_type[ki].copy(),
                      self.obj_dims.reshape(-1, 3)[ki].reshape(-1).copy(),
                      self.obj_pose.reshape(-1, 7)[ki].reshape(-1).copy(),
-                     self.pad_pose.reshape(-1, 7)[pi].reshape(-1).copy(), self.name)
+                     self.pad_pose.reshape(-1, 7)[pi].reshape(-1).copy(), self.name,
+                     list(self.meshes))
 
 
 # --- small rigid-motion helpers used only to place pads (scene construction)
@@ -290,7 +378,7 @@ def place_pad(rng, ptype: PadType, otype: int, dims, obj_t, obj_q, depth: float,
     return np.concatenate([t_pad, q_pad])
 
 
-def _pack(types, E, P, K, pad_type, objs, pad_poses, name):
+def _pack(types, E, P, K, pad_type, objs, pad_poses, name, meshes=()):
     obj_type = np.zeros(E * K, np.int32)
     obj_dims = np.zeros(E * K * 3, np.float32)
     obj_pose = np.zeros(E * K * 7, np.float32)
@@ -300,7 +388,7 @@ def _pack(types, E, P, K, pad_type, objs, pad_poses, name):
         obj_dims[idx * 3: idx * 3 + 3] = dims
         obj_pose[idx * 7: idx * 7 + 7] = pose
     return Scene(types, E, P, K, np.asarray(pad_type, np.int32), obj_type, obj_dims,
-                 obj_pose, np.asarray(pad_poses, np.float32).reshape(-1), name)
+                 obj_pose, np.asarray(pad_poses, np.float32).reshape(-1), name, list(meshes))
 
 
 def sphere_press_scene(steps: int, seed: int, rows: int = 16, cols: int = 16,
@@ -373,11 +461,13 @@ def uneven_scene(num_envs: int, seed: int, max_depth: float = 3.0, max_tilt: flo
 
 
 def custom_scene(types, pad_type, objects, pad_poses, num_envs: int, max_objects: int,
-                 name: str = "custom") -> Scene:
+                 name: str = "custom", meshes=()) -> Scene:
     """Scene from explicit parts: ``objects`` maps a flat object slot (env * K + k) to
-    (type, dims[3], pose[7]); ``pad_poses`` lists one world pose per pad instance."""
+    (type, dims[3], pose[7]); ``pad_poses`` lists one world pose per pad instance; an
+    OBJ_MESH object's dims[0] indexes ``meshes``."""
     P = len(pad_type) // num_envs
-    return _pack(list(types), num_envs, P, max_objects, pad_type, objects, pad_poses, name)
+    return _pack(list(types), num_envs, P, max_objects, pad_type, objects, pad_poses, name,
+                 meshes)
 
 
 def grad_scene(otype: int = OBJ_CAPSULE, rows: int = 8, cols: int = 8, pitch: float = 1.0,
