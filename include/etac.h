@@ -224,6 +224,68 @@ const char* etac_last_error(const etac_ctx* ctx);
 /* Frees the context and its device memory (synchronises the device first). NULL is a no-op. */
 void etac_destroy(etac_ctx* ctx);
 
+/* ---- Triangle-mesh objects: acceleration structure (host side).
+ *
+ * ETac detects contact with signed distance fields between the nodes and object meshes
+ * (Sec. III-A, "Overview").  For a closed triangle mesh the signed distance at a point q is
+ * the distance to the nearest surface point c, negative inside; the sign follows from the
+ * pseudo-normal n_F of the feature F (face, edge or vertex) that holds c: q is inside iff
+ * (q - c) . n_F < 0 (Baerentzen and Aanaes, 2005).  A query visits the triangles listed for
+ * the grid cell that holds q, never the whole mesh.
+ *
+ * etac_mesh_accel_build validates a mesh and builds, on the host, a uniform grid of cubic
+ * cells over the mesh's bounding box.  Every cell is classified by the exact distance d from
+ * its centre to the surface against its half-diagonal r:
+ *   ETAC_CELL_OUTSIDE  no surface point within r and the centre is outside: every point of
+ *                      the cell is outside (no candidates);
+ *   ETAC_CELL_INSIDE   no surface point within r and the centre is inside: every point of
+ *                      the cell is inside;
+ *   ETAC_CELL_SURFACE  the surface may cross the cell.
+ * INSIDE and SURFACE cells list every triangle whose distance from the centre is at most
+ * d + 2r (+ a slack of 1e-5 cell + 1e-6 mm), which contains the nearest triangle of every
+ * point of the cell.  Points outside the grid are outside the mesh.
+ *
+ * The mesh (host arrays, read during the call): vertices [V*3] in the object frame (mm);
+ * triangles [T*3] vertex indices wound counter-clockwise seen from outside.  It must be
+ * closed and consistently oriented: every directed edge occurs exactly once and its
+ * reverse exactly once; no triangle may have zero area.  `grid` is the number of cells
+ * along the longest side of the bounding box, in [1, 512] (0 picks 32).  Errors:
+ * ETAC_ERR_INVALID_ARG (message from etac_last_error(NULL)) for a NULL pointer, an index
+ * out of range, a degenerate triangle, an open or inconsistently wound mesh, or a grid whose
+ * cell or candidate count exceeds 2^24 cells / 2^28 candidates; ETAC_ERR_OOM if host memory
+ * runs out.  The structure is owned by the caller until etac_mesh_accel_destroy (NULL is a
+ * no-op); etac_mesh_accel_get_view fills *view with pointers into it, valid until then.
+ * Host-only: needs no GPU.  Building is deterministic (same mesh, same bytes). */
+enum { ETAC_CELL_OUTSIDE = 0, ETAC_CELL_INSIDE = 1, ETAC_CELL_SURFACE = 2 };
+typedef struct {
+  int32_t num_verts;
+  int32_t num_tris;
+  const float* verts;      /* host [V*3] */
+  const int32_t* tris;     /* host [T*3] */
+  int32_t grid;            /* cells along the longest side, 0 = 32 */
+} etac_mesh_desc;
+
+typedef struct {
+  float origin[3];             /* object-frame corner of cell (0, 0, 0)                       */
+  float cell;                  /* cell edge (mm); cell (i, j, k) spans origin + [i, i+1) cell  */
+  int32_t dims[3];             /* cells along x, y, z; cell index = (k * dims[1] + j) * dims[0] + i */
+  int32_t num_tris;
+  int64_t num_cand;            /* total candidate entries                                      */
+  const int32_t* cell_start;   /* [C+1] first candidate of each cell, C = dims product         */
+  const uint8_t* cell_kind;    /* [C] ETAC_CELL_*                                              */
+  const int32_t* cand;         /* [num_cand] triangle indices, ascending within a cell         */
+  const float* tri;            /* [T*16] per triangle: a, b, c, unit face normal (xyz + 0)     */
+  const float* pseudo;         /* [T*24] per triangle: unit pseudo-normals of edges ab, bc, ca
+                                  and vertices a, b, c (xyz + 0); an edge's is the normalised
+                                  sum of its two faces' normals, a vertex's the normalised
+                                  angle-weighted sum of its faces' normals                   */
+} etac_mesh_accel_view;
+
+typedef struct etac_mesh_accel etac_mesh_accel;
+etac_status etac_mesh_accel_build(etac_mesh_accel** out, const etac_mesh_desc* desc);
+etac_status etac_mesh_accel_get_view(const etac_mesh_accel* accel, etac_mesh_accel_view* view);
+void etac_mesh_accel_destroy(etac_mesh_accel* accel);
+
 /* ---- Forward step for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this entry point exists for integration.  Some callers must

@@ -32,7 +32,8 @@ def _nvcc() -> str:
 
 
 def sources() -> list:
-    return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
+    """CUDA sources and host-only C++ sources (both compiled by nvcc)."""
+    return sorted(glob.glob(os.path.join(CSRC, "*.cu")) + glob.glob(os.path.join(CSRC, "*.cpp")))
 
 
 def _deps() -> list:
@@ -57,7 +58,7 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     flags = NVCC_FLAGS + list(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.basename(src)[:-3] + ".o")
+        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v")

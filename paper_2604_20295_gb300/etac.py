@@ -29,7 +29,9 @@ EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set
            "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
            "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
            "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
-           "etac_autotune", "etac_set_tuning")
+           "etac_autotune", "etac_set_tuning", "etac_mesh_accel_build",
+           "etac_mesh_accel_get_view", "etac_mesh_accel_destroy")
+CELL_OUTSIDE, CELL_INSIDE, CELL_SURFACE = 0, 1, 2
 TUNE_MAX = 8
 
 _vp = ctypes.c_void_p
@@ -73,6 +75,18 @@ class etac_noalloc_pads(ctypes.Structure):
 class etac_kernel_time(ctypes.Structure):
     _fields_ = [("name", ctypes.c_char * 48), ("launches", ctypes.c_int32),
                 ("total_ms", ctypes.c_float)]
+
+
+class etac_mesh_desc(ctypes.Structure):
+    _fields_ = [("num_verts", ctypes.c_int32), ("num_tris", ctypes.c_int32),
+                ("verts", _vp), ("tris", _vp), ("grid", ctypes.c_int32)]
+
+
+class etac_mesh_accel_view(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_float * 3), ("cell", ctypes.c_float),
+                ("dims", ctypes.c_int32 * 3), ("num_tris", ctypes.c_int32),
+                ("num_cand", ctypes.c_int64), ("cell_start", _vp), ("cell_kind", _vp),
+                ("cand", _vp), ("tri", _vp), ("pseudo", _vp)]
 
 
 class EtacError(RuntimeError):
@@ -126,6 +140,12 @@ def lib():
         L.etac_pose_grad_to_quat.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
         L.etac_step_forward_noalloc.restype = ctypes.c_int
         L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+        L.etac_mesh_accel_build.restype = ctypes.c_int
+        L.etac_mesh_accel_build.argtypes = [ctypes.POINTER(_vp), _vp]
+        L.etac_mesh_accel_get_view.restype = ctypes.c_int
+        L.etac_mesh_accel_get_view.argtypes = [_vp, ctypes.POINTER(etac_mesh_accel_view)]
+        L.etac_mesh_accel_destroy.restype = None
+        L.etac_mesh_accel_destroy.argtypes = [_vp]
         _lib = L
     return _lib
 
@@ -152,6 +172,49 @@ def etac_create_pads(desc: etac_pads_desc, stream: int = 0) -> int:
     _check(None, lib().etac_create_pads(ctypes.byref(out), ctypes.addressof(desc), stream),
            "etac_create_pads")
     return out.value
+
+
+def etac_mesh_accel_build(desc: etac_mesh_desc) -> int:
+    out = _vp()
+    _check(None, lib().etac_mesh_accel_build(ctypes.byref(out), ctypes.addressof(desc)),
+           "etac_mesh_accel_build")
+    return out.value
+
+
+def etac_mesh_accel_get_view(accel: int) -> etac_mesh_accel_view:
+    v = etac_mesh_accel_view()
+    _check(None, lib().etac_mesh_accel_get_view(accel, ctypes.byref(v)), "etac_mesh_accel_get_view")
+    return v
+
+
+def etac_mesh_accel_destroy(accel: int) -> None:
+    lib().etac_mesh_accel_destroy(accel)
+
+
+def mesh_accel(verts, tris, grid: int = 0) -> dict:
+    """Builds the host acceleration structure of a closed triangle mesh (verts [V,3] float32,
+    tris [T,3] int32) and returns copies of its arrays as numpy (host only, no GPU)."""
+    v = np.ascontiguousarray(verts, np.float32)
+    t = np.ascontiguousarray(tris, np.int32)
+    h = etac_mesh_accel_build(etac_mesh_desc(len(v), len(t), v.ctypes.data, t.ctypes.data, grid))
+    try:
+        w = etac_mesh_accel_get_view(h)
+        C = int(w.dims[0]) * int(w.dims[1]) * int(w.dims[2])
+        T = int(w.num_tris)
+
+        def arr(ptr, ctype, n, dtype):
+            if n == 0:
+                return np.zeros(0, dtype)
+            return np.ctypeslib.as_array(ctypes.cast(ptr, ctypes.POINTER(ctype)), (n,)).astype(dtype)
+        return dict(origin=np.array(w.origin[:], np.float32), cell=float(w.cell),
+                    dims=tuple(int(d) for d in w.dims), num_tris=T,
+                    cell_start=arr(w.cell_start, ctypes.c_int32, C + 1, np.int32),
+                    cell_kind=arr(w.cell_kind, ctypes.c_uint8, C, np.uint8),
+                    cand=arr(w.cand, ctypes.c_int32, int(w.num_cand), np.int32),
+                    tri=arr(w.tri, ctypes.c_float, 16 * T, np.float32).reshape(T, 4, 4),
+                    pseudo=arr(w.pseudo, ctypes.c_float, 24 * T, np.float32).reshape(T, 6, 4))
+    finally:
+        etac_mesh_accel_destroy(h)
 
 
 def etac_set_model(ctx: int, desc: etac_model_desc, params: int, stream: int = 0) -> None:
