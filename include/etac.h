@@ -286,6 +286,27 @@ etac_status etac_mesh_accel_build(etac_mesh_accel** out, const etac_mesh_desc* d
 etac_status etac_mesh_accel_get_view(const etac_mesh_accel* accel, etac_mesh_accel_view* view);
 void etac_mesh_accel_destroy(etac_mesh_accel* accel);
 
+/* Device copy of a mesh's acceleration structure, and the signed-distance query on it.
+ *
+ * etac_mesh_gpu_create allocates device memory for the arrays of `accel` and copies them on
+ * `stream`, then synchronises `stream` (the accel may be destroyed once it returns).  Errors:
+ * ETAC_ERR_INVALID_ARG (NULL), ETAC_ERR_OOM, ETAC_ERR_CUDA.  etac_mesh_gpu_destroy
+ * synchronises the device and frees it (NULL is a no-op).
+ *
+ * etac_mesh_sdf_query evaluates, for n points q [n*3] (device, object frame, mm), the signed
+ * distance phi [n] to the mesh (negative inside) and, when grad is not NULL, its outward
+ * unit gradient grad [n*3], in FP32 on `stream` (no synchronisation).  A point outside the
+ * grid or in an ETAC_CELL_OUTSIDE cell is outside and gets phi = +INFINITY and a zero
+ * gradient (its distance is not computed); a non-finite point counts as outside.  Ties
+ * between equally near triangles go to the lowest index.  The nearest surface point is
+ * q - phi * grad.  Arrays must be 4-byte aligned and must not overlap.  Errors:
+ * ETAC_ERR_INVALID_ARG (NULL, n < 0, misalignment), ETAC_ERR_CUDA (launch failure). */
+typedef struct etac_mesh_gpu etac_mesh_gpu;
+etac_status etac_mesh_gpu_create(etac_mesh_gpu** out, const etac_mesh_accel* accel, void* stream);
+etac_status etac_mesh_sdf_query(const etac_mesh_gpu* mesh, int64_t n, const float* q, float* phi,
+                                float* grad, void* stream);
+void etac_mesh_gpu_destroy(etac_mesh_gpu* mesh);
+
 /* ---- Forward step for callers that cannot allocate device memory.
  *
  * The paper has no counterpart: this entry point exists for integration.  Some callers must

@@ -30,7 +30,8 @@ EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set
            "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
            "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
            "etac_autotune", "etac_set_tuning", "etac_mesh_accel_build",
-           "etac_mesh_accel_get_view", "etac_mesh_accel_destroy")
+           "etac_mesh_accel_get_view", "etac_mesh_accel_destroy", "etac_mesh_gpu_create",
+           "etac_mesh_sdf_query", "etac_mesh_gpu_destroy")
 CELL_OUTSIDE, CELL_INSIDE, CELL_SURFACE = 0, 1, 2
 TUNE_MAX = 8
 
@@ -146,6 +147,12 @@ def lib():
         L.etac_mesh_accel_get_view.argtypes = [_vp, ctypes.POINTER(etac_mesh_accel_view)]
         L.etac_mesh_accel_destroy.restype = None
         L.etac_mesh_accel_destroy.argtypes = [_vp]
+        L.etac_mesh_gpu_create.restype = ctypes.c_int
+        L.etac_mesh_gpu_create.argtypes = [ctypes.POINTER(_vp), _vp, _vp]
+        L.etac_mesh_sdf_query.restype = ctypes.c_int
+        L.etac_mesh_sdf_query.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
+        L.etac_mesh_gpu_destroy.restype = None
+        L.etac_mesh_gpu_destroy.argtypes = [_vp]
         _lib = L
     return _lib
 
@@ -215,6 +222,59 @@ def mesh_accel(verts, tris, grid: int = 0) -> dict:
                     pseudo=arr(w.pseudo, ctypes.c_float, 24 * T, np.float32).reshape(T, 6, 4))
     finally:
         etac_mesh_accel_destroy(h)
+
+
+def etac_mesh_gpu_create(accel: int, stream: int = 0) -> int:
+    out = _vp()
+    _check(None, lib().etac_mesh_gpu_create(ctypes.byref(out), accel, stream), "etac_mesh_gpu_create")
+    return out.value
+
+
+def etac_mesh_sdf_query(mesh: int, n: int, q: int, phi: int, grad: int = 0, stream: int = 0) -> None:
+    _check(None, lib().etac_mesh_sdf_query(mesh, n, q, phi, grad or None, stream),
+           "etac_mesh_sdf_query")
+
+
+def etac_mesh_gpu_destroy(mesh: int) -> None:
+    lib().etac_mesh_gpu_destroy(mesh)
+
+
+class MeshSDF:
+    """A closed triangle mesh resident on the GPU for signed-distance queries (builds the
+    host acceleration structure, copies it to the device, frees the host copy)."""
+
+    def __init__(self, verts, tris, grid: int = 0, stream: int = 0):
+        v = np.ascontiguousarray(verts, np.float32)
+        t = np.ascontiguousarray(tris, np.int32)
+        acc = etac_mesh_accel_build(etac_mesh_desc(len(v), len(t), v.ctypes.data, t.ctypes.data, grid))
+        try:
+            self.handle = etac_mesh_gpu_create(acc, stream)
+        finally:
+            etac_mesh_accel_destroy(acc)
+
+    def query(self, q, stream=None):
+        """phi [n] and grad [n,3] (float32 CUDA tensors) at object-frame points q [n,3]
+        (a float32 CUDA tensor); +inf where a point is outside without a computed distance."""
+        import torch
+        if not (q.is_cuda and q.dtype == torch.float32 and q.is_contiguous() and q.shape[-1] == 3):
+            raise ValueError("q must be a contiguous float32 CUDA tensor of shape [n, 3]")
+        n = q.numel() // 3
+        phi = torch.empty(n, dtype=torch.float32, device=q.device)
+        grad = torch.empty(n, 3, dtype=torch.float32, device=q.device)
+        st = torch.cuda.current_stream().cuda_stream if stream is None else stream
+        etac_mesh_sdf_query(self.handle, n, q.data_ptr(), phi.data_ptr(), grad.data_ptr(), st)
+        return phi, grad
+
+    def close(self):
+        if getattr(self, "handle", None):
+            etac_mesh_gpu_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def etac_set_model(ctx: int, desc: etac_model_desc, params: int, stream: int = 0) -> None:
