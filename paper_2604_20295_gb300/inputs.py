@@ -305,9 +305,18 @@ def uniform_quat(rng) -> np.ndarray:
                      b * math.sin(2 * math.pi * u3), b * math.cos(2 * math.pi * u3)])
 
 
-def _support(rng, otype: int, dims) -> tuple:
-    """A surface point of the primitive and its outward unit normal, object frame,
+def _support(rng, otype: int, dims, mesh=None) -> tuple:
+    """A surface point of the primitive (or mesh) and its outward unit normal, object frame,
     sampled with probability proportional to area."""
+    if otype == OBJ_MESH:
+        V = mesh.verts.astype(np.float64)[mesh.tris]
+        n = np.cross(V[:, 1] - V[:, 0], V[:, 2] - V[:, 0])
+        area = np.linalg.norm(n, axis=1)
+        t = int(rng.choice(len(area), p=area / area.sum()))
+        u, v = rng.random(2)
+        if u + v > 1:
+            u, v = 1 - u, 1 - v
+        return V[t, 0] + u * (V[t, 1] - V[t, 0]) + v * (V[t, 2] - V[t, 0]), n[t] / area[t]
     if otype == OBJ_SPHERE:
         u = rng.normal(size=3)
         u /= np.linalg.norm(u)
@@ -359,11 +368,11 @@ def random_object(rng) -> tuple:
 
 
 def place_pad(rng, ptype: PadType, otype: int, dims, obj_t, obj_q, depth: float,
-              max_tilt: float) -> np.ndarray:
+              max_tilt: float, mesh=None) -> np.ndarray:
     """World pose of a pad whose randomly chosen node sits ``depth`` mm inside the object
     below a random surface point, pad normal opposing the surface normal, random spin about
     the normal and a random tilt (<= max_tilt rad) about an axis through that node."""
-    s, ns = _support(rng, otype, dims)
+    s, ns = _support(rng, otype, dims, mesh)
     i0 = int(rng.integers(ptype.n))
     p0, n0 = ptype.pos[i0].astype(np.float64), ptype.nrm[i0].astype(np.float64)
     q_align = _q_from_to(n0, -ns)
@@ -458,6 +467,30 @@ def uneven_scene(num_envs: int, seed: int, max_depth: float = 3.0, max_tilt: flo
             pads.append(place_pad(rng, types[ti], ot, dims, t, q,
                                   rng.uniform(0.0, max_depth), max_tilt))
     return _pack(types, num_envs, P, K, pad_type, objs, pads, name)
+
+
+def mesh_scene(num_envs: int, seed: int, num_meshes: int = 4, max_depth: float = 3.0,
+               max_tilt: float = 0.35, name: str = "hand-mesh") -> Scene:
+    """The hand layout of ``hand_scene`` (5 curved 16x32 fingertips + a flat 32x64 palm per
+    env) pressed into seeded rock meshes (1,280 triangles, radius U[10, 30] mm) instead of
+    primitives: ``num_meshes`` shared meshes, one per env chosen uniformly, uniform rotation,
+    t ~ U[-40, 40]^3, pads placed as in ``hand_scene`` with depth U[0, max_depth]."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    meshes = [rock_mesh(seed * 1000 + i, float(rng.uniform(10, 30)), subdiv=3)
+              for i in range(num_meshes)]
+    types = [curved_pad(16, 32, 1.0, 8.0), flat_pad(32, 64, 1.0)]
+    P, K = 6, 1
+    pad_type = np.tile(np.array([0, 0, 0, 0, 0, 1], np.int32), num_envs)
+    objs, pads = {}, []
+    for e in range(num_envs):
+        mi = int(rng.integers(num_meshes))
+        q = uniform_quat(rng)
+        t = rng.uniform(-40, 40, 3)
+        objs[e] = (OBJ_MESH, (mi, 0, 0), (*t, *q))
+        for k in range(P):
+            pads.append(place_pad(rng, types[pad_type[e * P + k]], OBJ_MESH, None, t, q,
+                                  rng.uniform(0.0, max_depth), max_tilt, meshes[mi]))
+    return _pack(types, num_envs, P, K, pad_type, objs, pads, name, meshes)
 
 
 def custom_scene(types, pad_type, objects, pad_poses, num_envs: int, max_objects: int,

@@ -10,8 +10,7 @@ from paper_2604_20295_gb300 import build as B
 from paper_2604_20295_gb300 import etac as X
 from paper_2604_20295_gb300 import inputs as I
 
-pytestmark = [pytest.mark.gpu_candidate,
-              pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")]
+pytestmark = pytest.mark.gpu
 
 MESHES = {
     "box": lambda: I.box_mesh(3.0, 2.0, 4.0),
