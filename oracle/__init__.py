@@ -126,6 +126,32 @@ def forward(scene, theta, mode: int = MODE_FULL, mask_override=None, uhat_overri
     return out
 
 
+def regressor_param_count(lib=None) -> int:
+    lib = _load(lib)
+    lib.orc_regressor_param_count.restype = ctypes.c_size_t
+    return int(lib.orc_regressor_param_count())
+
+
+def regress(scene, disp, rparams, nthreads: int = 0, lib=None) -> dict:
+    """Real-to-sim taxel regressor on every pad: taxels [pads, 8] from the displacement field
+    disp [N, 3] (pad frame) and the pads' geometry; attn [N] = each node's softmax weight
+    within its pad (FP64)."""
+    lib = _load(lib)
+    m = _Marshalled(scene)
+    N = scene.total_nodes
+    d = np.ascontiguousarray(disp, np.float64).reshape(N, 3)
+    rp = np.ascontiguousarray(rparams, np.float64)
+    if rp.size != regressor_param_count(lib):
+        raise ValueError(f"regressor parameters: {rp.size} values, want {regressor_param_count(lib)}")
+    npads = scene.num_envs * scene.pads_per_env
+    out = dict(taxels=np.zeros((npads, 8)), attn=np.zeros(N))
+    rc = lib.orc_regress(ctypes.byref(m.s), _ptr(d), _ptr(rp), _ptr(out["taxels"]),
+                         _ptr(out["attn"]), ctypes.c_int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_regress failed ({rc})")
+    return out
+
+
 def mesh_sdf(scene, mesh: int, q, lib=None) -> dict:
     """Signed distance (negative inside), outward gradient and Hessian of one of the scene's
     meshes at object-frame points q [n,3] (FP64)."""

@@ -22,6 +22,9 @@
  * Everything is written literally (no factoring, no tiling) in double precision.  A pad
  * with no active node outputs zero displacement.
  *
+ * orc_regress is the real-to-sim taxel regressor of the appendix ("Modeling Real Sensors"),
+ * which maps a pad's displacement field to its sensor's eight taxel outputs.
+ *
  * orc_backward is the hand-derived reverse mode of the same steps (mask held fixed,
  * ReLU'(0) = 0, max-pool gradient routed to the lowest-index maximiser).  Pose gradients
  * are taken with respect to each object's world translation and a world-frame rotation
@@ -794,5 +797,102 @@ int orc_mesh_sdf(const orc_scene* sc, int mesh, long n, const double* q, double*
     if (grad) memcpy(grad + 3 * i, g, sizeof g);
     if (hess) memcpy(hess + 9 * i, Hs, sizeof Hs);
   }
+  return 0;
+}
+
+/* ----------------------------------------------------------------- taxel regressor */
+
+/* Real-to-sim taxel regressor (appendix "Modeling Real Sensors"): a PointNet-style network
+ * from a pad's simulated displacement field to the outputs of the real sensor's eight
+ * pressure taxels, with residual connections and attention pooling in place of max pooling.
+ * The appendix fixes the attention MLP ([256, 128, 1], tanh) and the softmax; the encoder
+ * widths, the residual layer and the head are readings (the figure is not in the text):
+ *   x_i = [p_i, n_i, U_i]                           (9, pad frame)
+ *   h1 = relu(R1 x + b), h2 = relu(R2 h1 + b), h3 = relu(R3 h2 + b)   (64, 128, 256)
+ *   f_i = h3 + relu(R4 h3 + b)                      (256, residual)
+ *   a_i = A2 tanh(A1 f_i + b) + b                   (attention score)
+ *   alpha = softmax over the pad's nodes of a       (computed as exp(a_i - max a) / sum)
+ *   g = sum_i alpha_i f_i
+ *   y = H2 relu(H1 g + b) + b                       (8 taxels)
+ * Parameters: W (row-major, out x in) then b for R1, R2, R3, R4, A1, A2, H1, H2. */
+#define RT 8
+static const int reg_dims[8][2] = {{64, 9}, {128, 64}, {256, 128}, {256, 256},
+                                   {128, 256}, {1, 128}, {128, 256}, {RT, 128}};
+
+size_t orc_regressor_param_count(void) {
+  size_t n = 0;
+  for (int l = 0; l < 8; ++l) n += (size_t)reg_dims[l][0] * reg_dims[l][1] + reg_dims[l][0];
+  return n;
+}
+
+/* y = W x + b for layer l of the flat regressor vector */
+static void reg_layer(const double* rp, int l, const double* x, double* y) {
+  size_t off = 0;
+  for (int k = 0; k < l; ++k) off += (size_t)reg_dims[k][0] * reg_dims[k][1] + reg_dims[k][0];
+  int o = reg_dims[l][0], in = reg_dims[l][1];
+  const double* W = rp + off;
+  const double* b = W + (size_t)o * in;
+  for (int r = 0; r < o; ++r) {
+    double acc = b[r];
+    for (int c = 0; c < in; ++c) acc += W[(size_t)r * in + c] * x[c];
+    y[r] = acc;
+  }
+}
+
+/* disp [N*3] (pad frame) -> taxels [pads*8]; attn [N] (optional) receives the softmax
+ * weights of every node within its pad. */
+int orc_regress(const orc_scene* sc, const double* disp, const double* rp, double* taxels,
+                double* attn, int nthreads) {
+  long N;
+  long* offs = make_offsets(sc, &N);
+  int np = sc->num_envs * sc->pads_per_env;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int p = 0; p < np; ++p) {
+    int t = sc->pad_type[p], n = sc->type_n[t];
+    const double* pos = type_ptr(sc, sc->type_pos, t);
+    const double* nrm = type_ptr(sc, sc->type_nrm, t);
+    long base = offs[p];
+    double* f = (double*)malloc(sizeof(double) * 256 * (size_t)(n > 0 ? n : 1));
+    double* a = (double*)malloc(sizeof(double) * (size_t)(n > 0 ? n : 1));
+    for (int i = 0; i < n; ++i) {
+      double x[9], h1[64], h2[128], h3[256], h4[256], s1[128], s;
+      for (int k = 0; k < 3; ++k) {
+        x[k] = pos[3 * i + k];
+        x[3 + k] = nrm[3 * i + k];
+        x[6 + k] = disp[3 * (base + i) + k];
+      }
+      reg_layer(rp, 0, x, h1);
+      for (int k = 0; k < 64; ++k) h1[k] = relu(h1[k]);
+      reg_layer(rp, 1, h1, h2);
+      for (int k = 0; k < 128; ++k) h2[k] = relu(h2[k]);
+      reg_layer(rp, 2, h2, h3);
+      for (int k = 0; k < 256; ++k) h3[k] = relu(h3[k]);
+      reg_layer(rp, 3, h3, h4);
+      for (int k = 0; k < 256; ++k) f[(size_t)i * 256 + k] = h3[k] + relu(h4[k]);
+      reg_layer(rp, 4, f + (size_t)i * 256, s1);
+      for (int k = 0; k < 128; ++k) s1[k] = tanh(s1[k]);
+      reg_layer(rp, 5, s1, &s);
+      a[i] = s;
+    }
+    double mx = -INFINITY, Z = 0.0, g[256], z[128], y[RT];
+    for (int i = 0; i < n; ++i) mx = a[i] > mx ? a[i] : mx;
+    for (int i = 0; i < n; ++i) { a[i] = exp(a[i] - mx); Z += a[i]; }
+    for (int k = 0; k < 256; ++k) g[k] = 0.0;
+    for (int i = 0; i < n; ++i) {
+      double al = a[i] / Z;
+      if (attn) attn[base + i] = al;
+      for (int k = 0; k < 256; ++k) g[k] += al * f[(size_t)i * 256 + k];
+    }
+    reg_layer(rp, 6, g, z);
+    for (int k = 0; k < 128; ++k) z[k] = relu(z[k]);
+    reg_layer(rp, 7, z, y);
+    for (int k = 0; k < RT; ++k) taxels[(size_t)p * RT + k] = n > 0 ? y[k] : 0.0;
+    free(f);
+    free(a);
+  }
+  free(offs);
   return 0;
 }

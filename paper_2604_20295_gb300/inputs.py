@@ -73,6 +73,41 @@ def make_params(seed: int, d2_scale: float = 0.1) -> np.ndarray:
     return theta.astype(np.float32)
 
 
+
+# parameter layout of the real-to-sim taxel regressor (appendix "Modeling Real Sensors"):
+# a per-node encoder with a residual layer, an attention MLP of widths [256, 128, 1] with
+# tanh, softmax pooling over the pad's nodes, and a head to the sensor's eight taxels; each
+# layer is W (row-major, out x in) followed by b
+REG_TAXELS = 8
+REG_LAYERS = (("R1", 64, 9), ("R2", 128, 64), ("R3", 256, 128), ("R4", 256, 256),
+              ("A1", 128, 256), ("A2", 1, 128), ("H1", 128, 256), ("H2", REG_TAXELS, 128))
+
+
+def regressor_param_count() -> int:
+    return sum(o * i + o for _, o, i in REG_LAYERS)
+
+
+def regressor_param_slices() -> dict:
+    out, off = {}, 0
+    for name, o, i in REG_LAYERS:
+        out["W" + name] = (off, o * i, (o, i))
+        off += o * i
+        out["b" + name] = (off, o, (o,))
+        off += o
+    return out
+
+
+def make_regressor_params(seed: int) -> np.ndarray:
+    """Regressor parameters from PCG64(seed): W, b ~ U(-1/sqrt(fan_in), 1/sqrt(fan_in))."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    theta = np.empty(regressor_param_count(), np.float64)
+    off = 0
+    for _, o, i in REG_LAYERS:
+        bound = 1.0 / math.sqrt(i)
+        theta[off:off + o * i + o] = rng.uniform(-bound, bound, o * i + o)
+        off += o * i + o
+    return theta.astype(np.float32)
+
 # ----------------------------------------------------------------------------- pads
 
 
