@@ -216,6 +216,24 @@ etac_status etac_forward_f64(etac_ctx* ctx, const etac_model_desc* desc,
                              const double* obj_pose, const double* pad_pose,
                              const double* params, double* disp, void* stream);
 
+/* ---- Real-to-sim taxel regressor (appendix "Modeling Real Sensors").
+ * A PointNet-style network from each pad's displacement field to the outputs of its real
+ * sensor's ETAC_TAXELS pressure taxels, with a residual layer and softmax attention pooling:
+ *   x_i = [p_i, n_i, U_i] (pad frame);  h1 = relu(R1 x + b) (64);  h2 = relu(R2 h1 + b) (128);
+ *   h3 = relu(R3 h2 + b) (256);  f_i = h3 + relu(R4 h3 + b) (256);
+ *   a_i = A2 tanh(A1 f_i + b) + b (A1: 256 -> 128, the appendix's [256, 128, 1] MLP);
+ *   alpha = softmax of a over the pad's nodes;  g = sum_i alpha_i f_i;
+ *   y = H2 relu(H1 g + b) + b (256 -> 128 -> ETAC_TAXELS).
+ * rparams: device FP32 [ETAC_REGRESSOR_PARAMS], each layer's W (row-major, out x in) then b,
+ * in the order R1, R2, R3, R4, A1, A2, H1, H2.  disp: device [N*3], e.g. the output of
+ * etac_step_forward.  Writes taxels [E*P*ETAC_TAXELS] and, when attn is not NULL, each node's
+ * softmax weight attn [N].  Uses the context's pads; needs no model.  FP32, enqueued on
+ * `stream`.  Errors: ETAC_ERR_INVALID_ARG (NULL or misaligned pointer), ETAC_ERR_CUDA. */
+#define ETAC_TAXELS 8
+#define ETAC_REGRESSOR_PARAMS 174729
+etac_status etac_regress(etac_ctx* ctx, const float* disp, const float* rparams, float* taxels,
+                         float* attn, void* stream);
+
 /* Message of the last failed call on this context (or, when ctx is NULL, of the last failed
  * etac_create_pads / etac_step_forward_noalloc on this thread).  Valid until the next call
  * on the same context. */

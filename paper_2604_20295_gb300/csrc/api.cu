@@ -1340,6 +1340,38 @@ etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int
   return ETAC_OK;
 }
 
+etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, float* taxels,
+                         float* attn, void* stream) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!disp || !rparams || !taxels || !aligned(disp, 4) || !aligned(rparams, 4) ||
+      !aligned(taxels, 4) || !aligned(attn, 4))
+    return fail(c, ETAC_ERR_INVALID_ARG, "NULL or misaligned pointer");
+  // layer shapes (out, in) in the order of the flat vector: R1 R2 R3 R4 A1 A2 H1 H2
+  static const int dims[8][2] = {{64, 9}, {128, 64}, {256, 128}, {256, 256},
+                                 {128, 256}, {1, 128}, {128, 256}, {ETAC_TAXELS, 128}};
+  etac::RegArgs a{};
+  size_t off = 0;
+  for (int l = 0; l < 8; ++l) {
+    a.W[l] = rparams + off;
+    off += (size_t)dims[l][0] * dims[l][1];
+    a.b[l] = rparams + off;
+    off += (size_t)dims[l][0];
+  }
+  if (off != ETAC_REGRESSOR_PARAMS) return fail(c, ETAC_ERR_STATE, "regressor layout mismatch");
+  a.type_pos = c->d_type_pos;
+  a.type_nrm = c->d_type_nrm;
+  a.type_off = c->d_type_off;
+  a.pad_type = c->d_pad_type;
+  a.pad_off = c->d_pad_off;
+  a.num_pads = c->E * c->P;
+  a.disp = disp;
+  a.taxels = taxels;
+  a.attn = attn;
+  ETAC_CUDA(c, etac::launch_regress_plain(a, c->num_sms, reinterpret_cast<cudaStream_t>(stream)),
+            "regressor launch");
+  return ETAC_OK;
+}
+
 etac_status etac_enable_timing(etac_ctx* c, int32_t enable) {
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (enable && c->ev.empty()) {

@@ -322,3 +322,24 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
                                   float* grad_params, cudaStream_t s);
 
 }  // namespace etac
+
+namespace etac {
+
+// ---------------------------------------------------------------- taxel regressor
+struct RegArgs {
+  const float* type_pos;      // [sum n, 3]
+  const float* type_nrm;      // [sum n, 3]
+  const int* type_off;        // [T+1]
+  const int* pad_type;        // [E*P]
+  const long long* pad_off;   // [E*P+1]
+  int num_pads;
+  const float* disp;          // [N, 3] pad frame
+  const float* W[8];          // R1, R2, R3, R4, A1, A2, H1, H2 (row-major, out x in)
+  const float* b[8];
+  float* taxels;              // [E*P, 8]
+  float* attn;                // [N] softmax weights (optional)
+};
+
+cudaError_t launch_regress_plain(const RegArgs& a, int num_sms, cudaStream_t s);
+
+}  // namespace etac

@@ -31,7 +31,9 @@ EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set
            "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
            "etac_autotune", "etac_set_tuning", "etac_mesh_accel_build",
            "etac_mesh_accel_get_view", "etac_mesh_accel_destroy", "etac_mesh_gpu_create",
-           "etac_mesh_sdf_query", "etac_mesh_gpu_destroy")
+           "etac_mesh_sdf_query", "etac_mesh_gpu_destroy", "etac_regress")
+TAXELS = 8
+REGRESSOR_PARAMS = 174729
 CELL_OUTSIDE, CELL_INSIDE, CELL_SURFACE = 0, 1, 2
 TUNE_MAX = 8
 
@@ -153,6 +155,8 @@ def lib():
         L.etac_mesh_sdf_query.argtypes = [_vp, ctypes.c_int64, _vp, _vp, _vp, _vp]
         L.etac_mesh_gpu_destroy.restype = None
         L.etac_mesh_gpu_destroy.argtypes = [_vp]
+        L.etac_regress.restype = ctypes.c_int
+        L.etac_regress.argtypes = [_vp] * 6
         _lib = L
     return _lib
 
@@ -222,6 +226,11 @@ def mesh_accel(verts, tris, grid: int = 0) -> dict:
                     pseudo=arr(w.pseudo, ctypes.c_float, 24 * T, np.float32).reshape(T, 6, 4))
     finally:
         etac_mesh_accel_destroy(h)
+
+
+def etac_regress(ctx: int, disp: int, rparams: int, taxels: int, attn: int = 0,
+                 stream: int = 0) -> None:
+    _check(ctx, lib().etac_regress(ctx, disp, rparams, taxels, attn or None, stream), "etac_regress")
 
 
 def etac_mesh_gpu_create(accel: int, stream: int = 0) -> int:
@@ -414,6 +423,26 @@ class TactileSim:
         return etac_step_out(d.data_ptr(), self.mask.data_ptr() if want_mask else None,
                              self.pen.data_ptr() if want_pen else None,
                              self.count.data_ptr() if want_count else None)
+
+    def regress(self, rparams, disp=None, want_attn=True):
+        """Real-to-sim taxel regressor on every pad: taxels [E*P, 8] (and each node's softmax
+        weight [N]) from a displacement field (default: the last step's) and the regressor's
+        flat FP32 parameters (a device tensor or array of REGRESSOR_PARAMS values)."""
+        torch = self.torch
+        rp = torch.as_tensor(np.asarray(rparams, np.float32) if not torch.is_tensor(rparams)
+                             else rparams, dtype=torch.float32).to(self.device).contiguous()
+        if rp.numel() != REGRESSOR_PARAMS:
+            raise ValueError(f"regressor parameters: {rp.numel()} values, want {REGRESSOR_PARAMS}")
+        d = self.disp if disp is None else disp
+        if not (d.is_cuda and d.dtype == torch.float32 and d.is_contiguous() and d.numel() == 3 * self.N):
+            raise ValueError("disp must be a contiguous float32 CUDA tensor of shape [N, 3]")
+        npads = self.scene.num_envs * self.scene.pads_per_env
+        taxels = torch.empty(npads, TAXELS, dtype=torch.float32, device=self.device)
+        attn = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_attn else None
+        etac_regress(self.ctx, d.data_ptr(), rp.data_ptr(), taxels.data_ptr(),
+                     attn.data_ptr() if want_attn else 0,
+                     torch.cuda.current_stream(self.device).cuda_stream)
+        return taxels, attn
 
     def step(self, want_mask=True, want_pen=True, want_count=True, disp=None):
         """One forward step on the current stream.  ``disp`` (a contiguous float32 [N, 3]

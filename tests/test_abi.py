@@ -93,3 +93,10 @@ def test_binding_constants_match_the_header():
     for code, label in X.STATUS_NAMES.items():
         assert e[label[len("ETAC_"):]] == code, label
     assert X.ERR_INVALID_ARG == e["ERR_INVALID_ARG"]
+    for name in ("CELL_OUTSIDE", "CELL_INSIDE", "CELL_SURFACE"):
+        assert getattr(X, name) == e[name], name
+    defs = {m.group(1): int(m.group(2)) for m in
+            re.finditer(r"#define ETAC_([A-Z0-9_]+)\s+(\d+)\b", open(HEADER).read())}
+    assert X.TAXELS == defs["TAXELS"] == I.REG_TAXELS
+    assert X.REGRESSOR_PARAMS == defs["REGRESSOR_PARAMS"] == I.regressor_param_count()
+    assert O.regressor_param_count() == I.regressor_param_count()
