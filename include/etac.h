@@ -47,7 +47,7 @@ typedef enum {
   ETAC_ERR_OOM = 4,          /* device allocation failed                                   */
   ETAC_ERR_TIMEOUT = 5,      /* device status: a bounded wait gave up                      */
   ETAC_ERR_NONFINITE = 6,    /* device status: a pose held NaN / Inf (those pads output 0) */
-  ETAC_ERR_UNSUPPORTED = 7   /* valid request this build does not implement                */
+  ETAC_ERR_UNSUPPORTED = 7   /* valid request the library does not implement               */
 } etac_status;
 
 enum { ETAC_OBJ_NONE = 0, ETAC_OBJ_SPHERE = 1, ETAC_OBJ_BOX = 2, ETAC_OBJ_CYLINDER = 3,
