@@ -330,9 +330,9 @@ void etac_mesh_gpu_destroy(etac_mesh_gpu* mesh);
  * The paper has no counterpart: this entry point exists for integration.  Some callers must
  * not allocate GPU memory while they run: a host application that hands the whole device
  * heap to its own pool allocator up front (physics engines commonly do), a real-time
- * control loop in which an allocation's latency or failure is not acceptable, or code that
- * is being recorded into a CUDA graph, where cudaMalloc is not permitted.  Such callers
- * cannot use etac_create_pads / etac_set_model, which allocate.
+ * control loop in which an allocation's latency or failure is not acceptable, or a plugin
+ * that its host program hands device pointers and no allocator.  Such callers cannot use
+ * etac_create_pads / etac_set_model, which allocate.
  *
  * etac_step_forward_noalloc runs the batched FP32 forward (ETAC_ALGO_BATCHED,
  * ETAC_PREC_FP32) from device pointers only.  The caller passes every input (pad geometry,

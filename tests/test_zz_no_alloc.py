@@ -1,9 +1,9 @@
 """The no-allocation forward entry point (etac_step_forward_noalloc).
 
 Callers that may not allocate device memory while they run -- an application that hands
-the whole device heap to its own pool allocator, a real-time loop, or code being recorded
-into a CUDA graph -- use this entry point: its scratch lives in a static device array in the
-library.  It must give the same displacements as the regular batched FP32 entry point, on
+the whole device heap to its own pool allocator, a real-time loop, or a plugin whose host
+program gives it device pointers and no allocator -- use this entry point: its scratch lives
+in a static device array in the library.  It must give the same displacements as the regular batched FP32 entry point, on
 two calls in a row (the second call reuses the array the first one left behind).  This file
 is collected last so that a stop at the first failure has already run every other test.
 """
