@@ -155,6 +155,39 @@ def test_cylinder_and_capsule_side_closed_form():
         np.testing.assert_allclose(out["disp"][a, 2], -d[a] * h / dist[a], atol=1e-12)
 
 
+def _cylinder_cap_case(lib=None):
+    """Upright cylinder (axis along the pad normal) pressed cap-down by delta: a node within
+    the radius, at distance rho from the axis, is inside with penetration min(r - rho, delta).
+    It leaves through the nearer of the side (radially, ties go radial) and the bottom cap
+    (straight down by delta).  Returns the oracle's output and the closed form of the mask,
+    the penetration and the active nodes' displacement."""
+    r, hl, cx, cy = 3.5, 4.0, 0.3, -0.2
+    sc = _flat_scene(12, 12, obj=(I.OBJ_CYLINDER, (r, hl, 0), (cx, cy, hl - 0.7, 0, 0, 0, 1)))
+    out = O.forward(sc, _theta(), mode=O.MODE_LINEAR_ONLY, lib=lib)
+    cx, cy = float(sc.obj_pose[0]), float(sc.obj_pose[1])  # stored float32 position
+    delta = hl - float(sc.obj_pose[2])
+    P = sc.types[0].pos.astype(np.float64)
+    dxy = P[:, :2] - (cx, cy)
+    rho = np.hypot(dxy[:, 0], dxy[:, 1])
+    inside = rho < r
+    pen = np.where(inside, np.minimum(r - rho, delta), 0.0)
+    disp = np.zeros_like(P)
+    radial = inside & (r - rho <= delta)
+    cap = inside & ~radial
+    disp[radial, :2] = (r - rho[radial])[:, None] * dxy[radial] / rho[radial][:, None]
+    disp[cap, 2] = -delta
+    return out, inside, pen, disp
+
+
+def test_cylinder_cap_flat_patch():
+    out, inside, pen, disp = _cylinder_cap_case()
+    np.testing.assert_array_equal(out["mask"].astype(bool), inside)
+    np.testing.assert_allclose(out["pen"], pen, atol=1e-12)
+    np.testing.assert_allclose(out["disp"][inside], disp[inside], atol=1e-12)
+    # both exits occur on this patch
+    assert (np.abs(disp[inside, 2]) > 0).sum() >= 8 and (np.abs(disp[inside, 0]) > 0).sum() >= 8
+
+
 def test_pad_pose_frame():
     """Outputs are in the pad frame: rotating and translating both pad and object by the same
     rigid motion leaves every output unchanged."""
@@ -461,6 +494,10 @@ def test_planted_mistake_is_caught(name, tmp_path):
 _MUTANTS_REV = {
     # every box face pushes along +axis (outward normal sign lost on the negative faces)
     "box_face_sign": ("g[am] = q[am] >= 0 ? 1.0 : -1.0;", "g[am] = 1.0;"),
+    # cylinder cap normal always +z: the bottom cap pushes nodes up into the object
+    "cylinder_cap_sign": ("    g[2] = sz;\n    return dz;", "    g[2] = 1.0;\n    return dz;"),
+    # cylinder side and cap distances swapped when choosing the exit
+    "cylinder_exit_choice": ("if (dr >= dz) {", "if (dr <= dz) {"),
     # capsule segment not clamped to its end caps: the capsule becomes an infinite cylinder
     "capsule_clamp": ("double cz = q[2] < -h ? -h : (q[2] > h ? h : q[2]);",
                       "double cz = q[2];"),
@@ -508,6 +545,11 @@ def _rev_pin_checks(lib):
     cy = np.clip(Pd[:, 1], -hl, hl)
     dist = np.sqrt(Pd[:, 0] ** 2 + (Pd[:, 1] - cy) ** 2 + pose[2] ** 2)
     yield bool(np.allclose(out["pen"], np.maximum(0, r - dist), atol=1e-12))
+    # upright cylinder pressed cap-down: side and cap exits
+    out, inside, pen, disp = _cylinder_cap_case(lib)
+    yield (bool(np.array_equal(out["mask"].astype(bool), inside))
+           and bool(np.allclose(out["pen"], pen, atol=1e-12))
+           and bool(np.allclose(out["disp"][inside], disp[inside], atol=1e-12)))
     # reverse mode vs torch autograd of the restatement, every primitive
     for ot in (I.OBJ_SPHERE, I.OBJ_BOX, I.OBJ_CYLINDER, I.OBJ_CAPSULE):
         sc, th, G = _grad_case(ot)
@@ -540,7 +582,8 @@ def test_reverse_pin_checks_pass_on_the_oracle():
 @pytest.mark.parametrize("name", sorted(_MUTANTS_REV))
 def test_planted_reverse_or_contact_mistake_is_caught(name, tmp_path):
     """A copy of the oracle with one planted mistake in its contact step or its reverse mode
-    fails at least one of the box, capsule-cap, autograd or penetration-projection pins."""
+    fails at least one of the box, capsule-cap, cylinder-cap, autograd or
+    penetration-projection pins."""
     src = open(os.path.join(os.path.dirname(O.__file__), "etac_oracle.c")).read()
     old, new = _MUTANTS_REV[name]
     assert src.count(old) == 1, name
