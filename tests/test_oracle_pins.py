@@ -453,6 +453,19 @@ _MUTANTS = {
     # wrong concat order of the global feature
     "concat_index": ("acc += P->Wd[c * 2 * H + H + k] * s->g[k];",
                      "acc += P->Wd[c * 2 * H + k] * s->g[k];"),
+    # ReLU of the global MLP left out
+    "global_relu": ("s->g[c] = relu(acc);", "s->g[c] = acc;"),
+    # max-pool over the passive nodes only (the pool covers all n nodes)
+    "pool_passive_only": ("if (fv > s->g0[c]) { s->g0[c] = fv; s->amax[c] = i; }",
+                          "if (!s->act[i] && fv > s->g0[c]) { s->g0[c] = fv; s->amax[c] = i; }"),
+    # squared distance in the decay of Eq. 1
+    "squared_distance": ("double w = exp(-P->alpha * sqrt(dx * dx + dy * dy + dz * dz));",
+                         "double w = exp(-P->alpha * (dx * dx + dy * dy + dz * dz));"),
+    # propagation added to the active nodes too (Eq. 1 applies to passive nodes only)
+    "propagate_into_active": ("      if (s->act[i]) continue;\n      const double* pi_",
+                              "      const double* pi_"),
+    # first encoder layer without its bias
+    "e1_bias": ("double acc = P->b1[c];", "double acc = 0.0;"),
 }
 
 
