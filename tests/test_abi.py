@@ -100,3 +100,48 @@ def test_binding_constants_match_the_header():
     assert X.TAXELS == defs["TAXELS"] == I.REG_TAXELS
     assert X.REGRESSOR_PARAMS == defs["REGRESSOR_PARAMS"] == I.regressor_param_count()
     assert O.regressor_param_count() == I.regressor_param_count()
+
+
+def _noalloc_scratch_bytes(type_nodes, num_pads):
+    """Bytes of static scratch that the no-allocation step needs, restated from the limit
+    the header gives: 896 B per pad-type node, 4 B per same-type node pair and 4 B per pad
+    instance, each array starting on a 256-byte boundary (plus the queue counter, the status
+    word, the Omega offsets and the per-type extents)."""
+    up = lambda b: (b + 255) // 256 * 256
+    T, tn = len(type_nodes), sum(type_nodes)
+    nn2 = sum(n * n for n in type_nodes)
+    return (up(4) + up(4) + up(8 * (T + 1)) + up(4 * T) + up(4 * num_pads)
+            + 3 * up(4 * 64 * tn) + up(2 * 64 * tn) + up(4 * nn2))
+
+
+def test_noalloc_host_checks_need_no_gpu(lib):
+    """etac_step_forward_noalloc rejects bad arguments and batches beyond its static scratch
+    on the host, before any CUDA call: every case here fails before the library would read a
+    device pointer, so the placeholder addresses below are never dereferenced."""
+    fake = np.zeros(16, np.int64)            # stands in for device pointers
+    ptr = fake.ctypes.data
+    sin = X.etac_step_in(ptr, ptr, ptr, ptr)
+    sout = X.etac_step_out(ptr, None, None, None)
+
+    def call(tn, mode=0, envs=1, ppe=1, K=1):
+        tn = np.ascontiguousarray(tn, np.int32)
+        pads = X.etac_noalloc_pads(len(tn), tn.ctypes.data, ptr, ptr, ptr, envs, ppe, K, ptr,
+                                   ptr)
+        with pytest.raises(X.EtacError) as e:
+            X.etac_step_forward_noalloc(pads, mode, ptr, sin, sout, 0)
+        assert e.value.status == X.ERR_INVALID_ARG
+        return str(e.value)
+
+    assert lib.etac_step_forward_noalloc(None, 0, None, None, None, None) == X.ERR_INVALID_ARG
+    assert "NULL" in X.etac_last_error(0)
+    assert "unknown mode" in call([256], mode=4)
+    assert "bad sizes" in call([256], K=9)
+    assert "pad type size" in call([256, 0])
+    assert "pad type size" in call([4097])
+    # past the 32 MiB scratch: the message gives the bytes needed, as the header's limit says
+    for tn, pads in (([4096] * 16, 1), ([4096], 1), ([2048] * 2, 4), ([256], 9_000_000)):
+        need = _noalloc_scratch_bytes(tn, pads)
+        assert need > 32 << 20
+        msg = call(tn, envs=pads)
+        assert f"need {need} bytes of scratch" in msg, msg
+        assert f"holds {32 << 20} bytes" in msg
