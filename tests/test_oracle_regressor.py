@@ -116,6 +116,14 @@ _MUTANTS = {
                           "(void)0;"),
     "inputs_swapped": ("x[3 + k] = nrm[3 * i + k];\n        x[6 + k] = disp[3 * (base + i) + k];",
                        "x[6 + k] = nrm[3 * i + k];\n        x[3 + k] = disp[3 * (base + i) + k];"),
+    # softmax exponent with the wrong sign (weights favour the lowest scores)
+    "softmax_sign": ("a[i] = exp(a[i] - mx);", "a[i] = exp(mx - a[i]);"),
+    # attention scored on the encoder output before the residual layer
+    "attention_before_residual": ("reg_layer(rp, 4, f + (size_t)i * 256, s1);",
+                                  "reg_layer(rp, 4, h3, s1);"),
+    # every layer's weight read transposed (column-major instead of out x in row-major)
+    "weights_transposed": ("acc += W[(size_t)r * in + c] * x[c];",
+                           "acc += W[(size_t)c * o + r] * x[c];"),
 }
 
 
