@@ -145,3 +145,31 @@ def test_noalloc_host_checks_need_no_gpu(lib):
         msg = call(tn, envs=pads)
         assert f"need {need} bytes of scratch" in msg, msg
         assert f"holds {32 << 20} bytes" in msg
+
+
+def test_create_rejects_empty_and_oversized_descriptions(lib):
+    """Empty batches (no environments, no pads per env, no pad types), pad types of 0 or
+    more than ETAC_MAX_PAD_NODES nodes and non-finite geometry are rejected on the host with
+    ETAC_ERR_INVALID_ARG and a message, before any GPU work."""
+    def attempt(tn, envs=1, ppe=1, T=None, pos=None, K=1):
+        tn = np.ascontiguousarray(tn, np.int32)
+        n = max(int(tn.sum()), 1)
+        pos = np.zeros((n, 3), np.float32) if pos is None else pos
+        nrm = np.tile(np.float32([0, 0, 1]), (n, 1))
+        pt = np.zeros(max(envs * ppe, 1), np.int32)
+        d = X.etac_pads_desc(len(tn) if T is None else T, tn.ctypes.data, pos.ctypes.data,
+                             nrm.ctypes.data, envs, ppe, pt.ctypes.data, K)
+        with pytest.raises(X.EtacError) as e:
+            X.etac_create_pads(d)
+        assert e.value.status == X.ERR_INVALID_ARG
+        return X.etac_last_error(0)
+
+    assert ">= 1" in attempt([16], envs=0)
+    assert ">= 1" in attempt([16], ppe=0)
+    assert "num_types" in attempt([16], T=0)
+    assert "0 nodes" in attempt([0])
+    assert "4097 nodes" in attempt([4097])
+    bad = np.zeros((16, 3), np.float32)
+    bad[5, 1] = np.nan
+    assert "non-finite" in attempt([16], pos=bad)
+    assert "max_objects" in attempt([16], K=0)
