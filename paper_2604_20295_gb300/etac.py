@@ -373,6 +373,17 @@ def etac_step_forward_noalloc(pads: etac_noalloc_pads, mode: int, params: int,
 # ------------------------------------------------------------------ convenience owner
 
 
+def _device_f32(t, device, numel: int, what: str):
+    """``t`` (tensor or array) as a contiguous float32 tensor on ``device`` holding exactly
+    ``numel`` values; the library reads that many floats from the pointer it is given, so a
+    host tensor or a short buffer is rejected here instead of reaching a kernel."""
+    import torch
+    t = torch.as_tensor(t).to(device=device, dtype=torch.float32).contiguous()
+    if t.numel() != numel:
+        raise EtacError(ERR_INVALID_ARG, f"{what} has {t.numel()} values, expected {numel}")
+    return t
+
+
 class TactileSim:
     """Owns an etac context for one batch of pads (a ``Scene`` from ``inputs``) together with
     device tensors for its inputs and outputs.  ``step()`` runs one forward on the current
@@ -409,8 +420,9 @@ class TactileSim:
 
     def set_model(self, params, mode=MODE_FULL, precision=PREC_FP32, algo=ALGO_PLAIN):
         torch = self.torch
-        self.params = torch.as_tensor(params, dtype=torch.float32).to(self.device).contiguous()
-        self.model = etac_model_desc(HIDDEN, mode, precision, algo)
+        model = etac_model_desc(HIDDEN, mode, precision, algo)
+        self.params = _device_f32(params, self.device, etac_param_count(model), "params")
+        self.model = model
         etac_set_model(self.ctx, self.model, self.params.data_ptr(),
                        torch.cuda.current_stream(self.device).cuda_stream)
 
@@ -462,7 +474,7 @@ class TactileSim:
         Returns a dict with any of: params [P], obj_pose [E*K, 6] (dL/dt, dL/d omega),
         uhat [N, 3], pen [N]."""
         torch = self.torch
-        g = grad_disp.contiguous().to(torch.float32)
+        g = _device_f32(grad_disp, self.device, 3 * self.N, "grad_disp")
         out = {}
         f32 = dict(dtype=torch.float32, device=self.device)
         sc = self.scene
@@ -483,7 +495,8 @@ class TactileSim:
     def autotune(self, grad_disp=None) -> dict:
         """Times the tile / block shape candidates on this scene's step (and, given an upstream
         gradient, the reverse mode's node ranges) and keeps the fastest."""
-        g = None if grad_disp is None else grad_disp.contiguous().to(self.torch.float32)
+        g = None if grad_disp is None else _device_f32(grad_disp, self.device, 3 * self.N,
+                                                       "grad_disp")
         t = etac_autotune(self.ctx, self.step_in(), self.step_out(),
                           0 if g is None else g.data_ptr(),
                           self.torch.cuda.current_stream(self.device).cuda_stream)
@@ -527,7 +540,7 @@ def make_step_function():
         @staticmethod
         def forward(ctx, sim, params, obj_pose):
             stream = torch.cuda.current_stream(sim.device).cuda_stream
-            p = params.detach().contiguous().to(torch.float32)
+            p = params.detach().to(device=sim.device, dtype=torch.float32).contiguous()
             if getattr(sim, "params", None) is None or not torch.equal(sim.params, p):
                 m = sim.model
                 sim.set_model(p, m.mode, m.precision, m.algo)

@@ -173,3 +173,20 @@ def test_create_rejects_empty_and_oversized_descriptions(lib):
     bad[5, 1] = np.nan
     assert "non-finite" in attempt([16], pos=bad)
     assert "max_objects" in attempt([16], K=0)
+
+
+def test_binding_converts_and_sizes_device_buffers():
+    """The binding hands the library float32 buffers of exactly the size it reads: arrays and
+    other dtypes are converted, and a buffer of the wrong size is refused before any call."""
+    import torch
+
+    cpu = torch.device("cpu")
+    t = X._device_f32(np.arange(6, dtype=np.float64).reshape(2, 3), cpu, 6, "x")
+    assert t.dtype == torch.float32 and t.is_contiguous() and t.tolist() == [[0, 1, 2], [3, 4, 5]]
+    nc = torch.arange(12, dtype=torch.float32).reshape(3, 4)[:, :3]
+    assert not nc.is_contiguous()
+    c = X._device_f32(nc, cpu, 9, "x")
+    assert c.is_contiguous() and torch.equal(c, nc)
+    with pytest.raises(X.EtacError) as e:
+        X._device_f32(torch.zeros(17411), cpu, 17412, "params")
+    assert e.value.status == X.ERR_INVALID_ARG and "17411 values, expected 17412" in str(e.value)
