@@ -213,6 +213,14 @@ def oracle_rate(scene, theta, sample_envs, nthreads=0):
     return sub.total_nodes / dt, dt, sub.total_nodes
 
 
+def oracle_single_core(scene, theta, sample_envs):
+    """The oracle's single-thread rate on a small env sample.  OpenMP keeps the thread count
+    set for a call, so the all-core count is put back afterwards (one env, untimed)."""
+    rate, dt, nn = oracle_rate(scene, theta, sample_envs, nthreads=1)
+    oracle_rate(scene, theta, sample_envs[:1], nthreads=cpu_cores())
+    return rate, dt, nn
+
+
 def run_reference(args, scene, theta, rank, world):
     if rank != 0:
         return
@@ -841,6 +849,10 @@ def main():
         cpu = {"value": sub.total_nodes / dt, "unit": UNIT, "cores": cpu_cores(), "kind": "oracle",
                "sample": f"{len(envs)} random envs ({sub.total_nodes} nodes) of the workload, one "
                          f"forward step, FP64 C oracle, OpenMP over pads, {dt:.1f} s"}
+        r1, dt1, nn1 = oracle_single_core(scene, theta, envs[:16])
+        cpu["single_core"] = {"value": r1, "unit": UNIT, "cores": 1,
+                              "sample": f"{min(len(envs), 16)} of those envs ({nn1} nodes), one "
+                                        f"thread, {dt1:.1f} s"}
         # stated error of this run's output on the same envs (mask-matched pads)
         sim.step(want_mask=True, want_pen=False, want_count=True)
         torch.cuda.synchronize()

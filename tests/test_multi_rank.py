@@ -80,3 +80,17 @@ def test_algorithmic_work_counts():
     dec = 2 * (64 * 64 + 3 * 64)
     assert w["literal_flops"] == (256 + 64) * enc + 246 * dec + 6 * 2460
     assert w["bytes_out"] == 12 * (256 * 2 + 64)
+
+
+def test_oracle_single_core_rate_is_bounded_and_leaves_all_cores():
+    """The bench's single-thread oracle figure runs on a few envs, and later oracle calls go
+    back to every core (OpenMP keeps the last thread count it was given)."""
+    from paper_2604_20295_gb300 import inputs as I
+    sc = I.hand_scene(4, seed=2)
+    th = I.make_params(0)
+    rate, dt, nn = bench.oracle_single_core(sc, th, np.arange(2))
+    assert rate > 0 and dt > 0 and nn == 2 * (5 * 512 + 2048)
+    if bench.cpu_cores() > 1:
+        import oracle
+        omp = oracle._load()          # OpenMP's own query, found through the oracle's library
+        assert omp.omp_get_max_threads() == bench.cpu_cores()
