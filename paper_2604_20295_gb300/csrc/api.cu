@@ -860,9 +860,9 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
   for (int64_t p = 0; p < np; ++p) {
     int t = c->pad_type[p];
     if (t < 0 || t >= c->T) {
-      free_ctx(c);
+      free_ctx(c);   // the message takes the type count from the description, not from c
       return fail(nullptr, ETAC_ERR_INVALID_ARG, "pad %lld has type %d (num_types %d)",
-                  (long long)p, t, c->T);
+                  (long long)p, t, d->num_types);
     }
     c->pad_off[p + 1] = c->pad_off[p] + c->type_n[t];
   }
