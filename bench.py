@@ -360,7 +360,13 @@ def config_c3(X, I, torch, dev, stream, flush, theta, with_oracle):
                                               runs["bf16_batched"]["us_per_launch"])
     if with_oracle:
         import oracle
+        t0 = time.perf_counter()
         ref = oracle.forward(sc, theta)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sc.total_nodes / dt, "unit": UNIT, "cores": cpu_cores(),
+                               "kind": "oracle", "us_per_step": 1e6 * dt / sc.num_envs,
+                               "sample": f"all {sc.num_envs} steps ({sc.total_nodes} nodes), "
+                                         f"FP64 forward, OpenMP over pads, {dt:.3f} s"}
         for name in runs:
             out[f"{name}_error"] = _stats(runs[name]["disp"], ref["disp"], runs[name]["mask"],
                                           ref["mask"])
@@ -510,7 +516,14 @@ def config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle):
         torch.cuda.synchronize()
         offs = sc.node_offsets
         idx = np.concatenate([np.arange(offs[e * 6], offs[e * 6 + 6]) for e in envs])
+        t0 = time.perf_counter()
         ref = oracle.forward(sub, theta)
+        dt = time.perf_counter() - t0
+        out["cpu_baseline"] = {"value": sub.total_nodes / dt, "unit": UNIT, "cores": cpu_cores(),
+                               "kind": "oracle",
+                               "sample": f"{len(envs)} random envs ({sub.total_nodes} nodes) of "
+                                         f"this workload, FP64 forward, OpenMP over pads, "
+                                         f"{dt:.1f} s"}
         out["error_vs_oracle"] = dict(_stats(sim.disp.cpu().numpy()[idx], ref["disp"],
                                              sim.mask.cpu().numpy()[idx], ref["mask"]),
                                       envs=len(envs))
