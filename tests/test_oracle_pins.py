@@ -604,3 +604,23 @@ def test_planted_reverse_or_contact_mistake_is_caught(name, tmp_path):
     p.write_text(src.replace(old, new))
     lib = O.load_variant(str(p), str(tmp_path / "libmut.so"))
     assert not all(_rev_pin_checks(lib)), f"planted mistake {name} passed every pin"
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    """The oracle parallelises over pads only: the forward and the per-node and pose gradients
+    are bitwise the same on 1 and 4 threads; the parameter gradient, summed per thread before
+    the threads are combined, agrees to FP64 rounding."""
+    sc = I.uneven_scene(6, seed=3)
+    th = _theta(seed=1)
+    G = np.random.default_rng(0).normal(size=(sc.total_nodes, 3))
+    try:
+        f1, f4 = O.forward(sc, th, nthreads=1), O.forward(sc, th, nthreads=4)
+        b1, b4 = O.backward(sc, th, G, nthreads=1), O.backward(sc, th, G, nthreads=4)
+    finally:
+        O.forward(_flat_scene(2, 2), th, nthreads=len(os.sched_getaffinity(0)))
+    for k in f1:
+        np.testing.assert_array_equal(f1[k], f4[k])
+    for k in ("obj_pose", "uhat", "pen"):
+        np.testing.assert_array_equal(b1[k], b4[k])
+    np.testing.assert_allclose(b1["params"], b4["params"], rtol=1e-10,
+                               atol=1e-12 * np.abs(b1["params"]).max())
