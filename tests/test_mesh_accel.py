@@ -186,3 +186,43 @@ def test_box_normals_closed_form():
         for k in range(3):
             np.testing.assert_allclose(acc["pseudo"][t, 3 + k, :3],
                                        np.sign(V[tri[k]]) / math.sqrt(3.0), atol=1e-7)
+
+
+def test_varied_and_corrupted_meshes_seeded_fuzz():
+    """Seeded variations of the generated meshes at many grid sizes build, and keep the
+    structure's invariants (monotone cell starts, every candidate a valid triangle); the same
+    meshes with a flipped triangle, a NaN vertex, an index moved out of range or triangles
+    removed are rejected with ETAC_ERR_INVALID_ARG, never built."""
+    rng = np.random.default_rng(11)
+    gens = [lambda: I.box_mesh(*rng.uniform(0.5, 20, 3)),
+            lambda: I.icosphere(float(rng.uniform(1, 30)), int(rng.integers(0, 3))),
+            lambda: I.torus_mesh(float(rng.uniform(5, 15)), float(rng.uniform(1, 4)),
+                                 int(rng.integers(6, 30)), int(rng.integers(4, 16))),
+            lambda: I.rock_mesh(int(rng.integers(100)), float(rng.uniform(3, 20)),
+                                subdiv=int(rng.integers(0, 3)), amp=float(rng.uniform(0, 0.5)))]
+    for it in range(120):
+        m = gens[it % len(gens)]()
+        v, t = m.verts.copy(), m.tris.copy()
+        corrupt = it % 5
+        if corrupt == 1:
+            k = rng.integers(len(t))
+            t[k] = t[k][::-1]
+        elif corrupt == 2:
+            v[rng.integers(len(v)), rng.integers(3)] = np.nan
+        elif corrupt == 3:
+            t[rng.integers(len(t)), rng.integers(3)] = len(v) + int(rng.integers(0, 3))
+        elif corrupt == 4:
+            t = t[: len(t) - int(rng.integers(1, 3))]
+        grid = int(rng.choice([0, 1, 2, 3, 7, 16, 33, 64]))
+        if corrupt:
+            with pytest.raises(X.EtacError) as e:
+                X.mesh_accel(v, t, grid)
+            assert e.value.status == X.ERR_INVALID_ARG, (it, corrupt)
+            continue
+        acc = X.mesh_accel(v, t, grid)
+        cs = acc["cell_start"]
+        assert cs[0] == 0 and cs[-1] == len(acc["cand"]) and np.all(np.diff(cs) >= 0), it
+        assert len(cs) == np.prod(acc["dims"]) + 1
+        assert acc["cand"].size == 0 or (acc["cand"].min() >= 0
+                                         and acc["cand"].max() < acc["num_tris"]), it
+        assert acc["num_tris"] == len(t)
