@@ -1,6 +1,7 @@
 """The seeded synthetic workloads have the shapes and contact statistics the workloads call
 for (CPU only; contact measured with the FP64 oracle on a sample of environments)."""
 import numpy as np
+import pytest
 
 import oracle as O
 from paper_2604_20295_gb300 import inputs as I
@@ -60,3 +61,22 @@ def test_uneven_scene_types():
     assert sizes == [64, 256, 1024, 4096] and len(sc.types) <= 16
     nobj = (sc.obj_type.reshape(sc.num_envs, sc.max_objects) != I.OBJ_NONE).sum(axis=1)
     assert nobj.min() >= 1 and nobj.max() <= 3
+
+
+@pytest.mark.parametrize("make", [lambda: I.hand_scene(12, seed=2),
+                                  lambda: I.uneven_scene(10, seed=4)])
+def test_subset_matches_slices_of_the_full_scene(make):
+    """A subset of environments (used to sample the oracle against a full-size GPU run) has
+    the same nodes, in the same order, as the matching slices of the full scene: the oracle's
+    output on the subset equals the full output at those environments' node ranges."""
+    sc = make()
+    th = I.make_params(0)
+    envs = np.array([0, 3, 7, 9])
+    full = O.forward(sc, th)
+    sub = O.forward(sc.subset(envs), th)
+    P = sc.pads_per_env
+    offs = sc.node_offsets
+    idx = np.concatenate([np.arange(offs[e * P], offs[e * P + P]) for e in envs])
+    np.testing.assert_array_equal(sub["disp"], full["disp"][idx])
+    np.testing.assert_array_equal(sub["mask"], full["mask"][idx])
+    assert sc.subset(envs).total_nodes == len(idx)
