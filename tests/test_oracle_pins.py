@@ -245,6 +245,30 @@ def test_single_indenter_node_contact():
     np.testing.assert_allclose(out["disp"][j + 2], [0, 0, -delta / 4], rtol=1e-13, atol=0)
 
 
+def test_linear_response_monotone_in_indentation():
+    """Eq. 1 alone, a sphere (r = 5 mm) pressed into a flat pad deeper and deeper over the
+    configured 0-2 mm range: the contact set only grows, every active node's u_hat points
+    further down (|q| shrinks, so R - |q| grows faster than the normal tilts), and Eq. 1
+    sums those with positive weights over a growing set.  So a node that stays active, or
+    stays passive, moves strictly further down.  (A node that turns active takes its own
+    small penetration in place of what its neighbours propagated to it, so no monotonicity
+    holds across that switch.)"""
+    R, cx, cy = 5.0, 0.25, -0.5
+    prev_z, prev_mask, grew = None, None, 0
+    for delta in np.linspace(0.125, 2.0, 16):
+        sc = _flat_scene(16, 16, obj=(I.OBJ_SPHERE, (R, 0, 0), (cx, cy, R - delta, 0, 0, 0, 1)))
+        out = O.forward(sc, _theta(), mode=O.MODE_LINEAR_ONLY)
+        z, mask = out["disp"][:, 2], out["mask"].astype(bool)
+        assert mask.any()
+        if prev_z is not None:
+            assert np.all(mask[prev_mask]), delta                    # contact set grows
+            same = mask == prev_mask
+            grew += int((~same).any())
+            assert np.all(z[same] < prev_z[same]), (delta, np.max(z[same] - prev_z[same]))
+        prev_z, prev_mask = z, mask
+    assert grew >= 8 and prev_mask.sum() > 40     # the sweep crosses many contact sets
+
+
 def test_monotone_decay_with_distance():
     """For alpha > 0 the propagated magnitude from one active node strictly decreases with
     distance."""
