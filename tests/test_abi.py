@@ -190,3 +190,41 @@ def test_binding_converts_and_sizes_device_buffers():
     with pytest.raises(X.EtacError) as e:
         X._device_f32(torch.zeros(17411), cpu, 17412, "params")
     assert e.value.status == X.ERR_INVALID_ARG and "17411 values, expected 17412" in str(e.value)
+
+
+_STRUCTS = ("etac_pads_desc", "etac_model_desc", "etac_step_in", "etac_step_out", "etac_tuning",
+            "etac_kernel_time", "etac_mesh_desc", "etac_mesh_accel_view", "etac_noalloc_pads")
+
+
+def test_binding_structs_match_the_header_layout(tmp_path):
+    """Every struct the binding passes by address has the header's size and field offsets:
+    a C program built against include/etac.h prints sizeof / offsetof, compared with ctypes."""
+    import shutil
+    import subprocess
+
+    cc = shutil.which("gcc") or shutil.which("cc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "etac.h"', "int main(void) {"]
+    for s in _STRUCTS:
+        ct = getattr(X, s)
+        lines.append(f'  printf("{s} size %zu\\n", sizeof({s}));')
+        for f, _ in ct._fields_:
+            lines.append(f'  printf("{s} {f} %zu\\n", offsetof({s}, {f}));')
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.check_call([cc, "-std=c11", "-I" + os.path.dirname(HEADER), str(src), "-o", str(exe)])
+    got = {}
+    for line in subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n"):
+        if line:
+            s, f, v = line.split()
+            got[(s, f)] = int(v)
+    for s in _STRUCTS:
+        ct = getattr(X, s)
+        assert got[(s, "size")] == ctypes.sizeof(ct), s
+        for f, _ in ct._fields_:
+            assert got[(s, f)] == getattr(ct, f).offset, (s, f)
+    assert sorted(set(re.findall(r"\}\s*(etac_[a-z_]+)\s*;", open(HEADER).read())) - {"etac_status"}) \
+        == sorted(_STRUCTS)
