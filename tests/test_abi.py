@@ -228,3 +228,18 @@ def test_binding_structs_match_the_header_layout(tmp_path):
             assert got[(s, f)] == getattr(ct, f).offset, (s, f)
     assert sorted(set(re.findall(r"\}\s*(etac_[a-z_]+)\s*;", open(HEADER).read())) - {"etac_status"}) \
         == sorted(_STRUCTS)
+
+
+def test_binding_prototypes_match_the_header(lib):
+    """Each declared function has argument types set in the binding, as many as the header's
+    prototype takes, and a C int result where the header returns etac_status."""
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    protos = re.findall(r"\b(etac_status|size_t|int64_t|void|const char\*)\s+(etac_[a-z0-9_]+)"
+                        r"\s*\(([^)]*)\)\s*;", src)
+    assert sorted(p[1] for p in protos) == _declared()
+    for ret, name, args in protos:
+        fn = getattr(lib, name)
+        n = 0 if args.strip() in ("", "void") else args.count(",") + 1
+        assert fn.argtypes is not None and len(fn.argtypes) == n, name
+        if ret == "etac_status":
+            assert fn.restype is ctypes.c_int, name
