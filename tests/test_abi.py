@@ -243,3 +243,19 @@ def test_binding_prototypes_match_the_header(lib):
         assert fn.argtypes is not None and len(fn.argtypes) == n, name
         if ret == "etac_status":
             assert fn.restype is ctypes.c_int, name
+
+
+def test_library_exports_only_declared_entry_points(lib):
+    """The C-linkage etac_* symbols the library exports are exactly the header's entry points
+    (read from the library's dynamic symbol table with nm)."""
+    import shutil
+    import subprocess
+
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm is not installed")
+    out = subprocess.run([nm, "-D", "--defined-only", B.LIB], capture_output=True, text=True,
+                         check=True).stdout
+    exported = sorted({f[2] for f in (l.split() for l in out.splitlines())
+                       if len(f) == 3 and f[1] == "T" and f[2].startswith("etac_")})
+    assert exported == _declared()
