@@ -126,6 +126,48 @@ def forward(scene, theta, mode: int = MODE_FULL, mask_override=None, uhat_overri
     return out
 
 
+def pool_margin(scene, theta, mask_override=None, uhat_override=None, nthreads: int = 0,
+                lib=None) -> dict:
+    """Margin of every pad's max-pool choice per channel (FP64): top2 [pads, 64, 2] = the
+    nodes holding the largest and second-largest feature (ties to the lower index, -1 when
+    none), gap [pads, 64] = (f_top1 - f_top2) / f_top1 (inf when f_top1 <= 0)."""
+    lib = _load(lib)
+    m = _Marshalled(scene)
+    th = np.ascontiguousarray(theta, np.float64)
+    mo = None if mask_override is None else np.ascontiguousarray(mask_override, np.uint8)
+    uo = None if uhat_override is None else np.ascontiguousarray(uhat_override, np.float64)
+    npads = scene.num_envs * scene.pads_per_env
+    out = dict(top2=np.zeros((npads, 64, 2), np.int32), gap=np.zeros((npads, 64)))
+    lib.orc_pool_margin.restype = ctypes.c_int
+    rc = lib.orc_pool_margin(ctypes.byref(m.s), _ptr(th), _ptr(mo), _ptr(uo), _ptr(out["top2"]),
+                             _ptr(out["gap"]), ctypes.c_int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_pool_margin failed ({rc})")
+    return out
+
+
+MARGIN_KINDS = ("relu_passive", "relu_active_max", "relu_global", "pool_active", "pool_passive")
+
+
+def decision_margin(scene, theta, mask_override=None, uhat_override=None, nthreads: int = 0,
+                    lib=None) -> np.ndarray:
+    """[pads, 5] smallest relative margin of each kind of discrete decision the reverse mode
+    of the residual network takes on each pad (see MARGIN_KINDS and orc_decision_margin):
+    ReLU margins |a| / (|b| + sum |w x|), max-pool gaps (f1 - f2) / f1; inf where none."""
+    lib = _load(lib)
+    m = _Marshalled(scene)
+    th = np.ascontiguousarray(theta, np.float64)
+    mo = None if mask_override is None else np.ascontiguousarray(mask_override, np.uint8)
+    uo = None if uhat_override is None else np.ascontiguousarray(uhat_override, np.float64)
+    out = np.zeros((scene.num_envs * scene.pads_per_env, 5))
+    lib.orc_decision_margin.restype = ctypes.c_int
+    rc = lib.orc_decision_margin(ctypes.byref(m.s), _ptr(th), _ptr(mo), _ptr(uo), _ptr(out),
+                                 ctypes.c_int(nthreads))
+    if rc != 0:
+        raise RuntimeError(f"orc_decision_margin failed ({rc})")
+    return out
+
+
 def regressor_param_count(lib=None) -> int:
     lib = _load(lib)
     lib.orc_regressor_param_count.restype = ctypes.c_size_t

@@ -786,6 +786,161 @@ int orc_backward(const orc_scene* sc, const double* theta, int mode,
   return 0;
 }
 
+/* Margin of the max-pool's discrete choice (Sec. III-A 2: g0_c = max over the pad's n nodes of
+ * f_ic).  For every pad p and channel c: top2[2 (64 p + c)] = the node holding the largest f_ic
+ * and top2[... + 1] = the node holding the second largest (ties to the lower index; -1 when the
+ * pad has one node), gap[64 p + c] = (f_top1 - f_top2) / f_top1 (INFINITY when f_top1 <= 0 or
+ * the pad has one node).  The reverse mode routes a channel's gradient to its top node, so a
+ * small gap flags a choice that a lower-precision evaluation of f may take differently.  The
+ * contact step (and mask_ovr / uhat_ovr) are those of orc_forward; pads without contact are
+ * reported too (their output is zero, so nothing is routed). */
+int orc_pool_margin(const orc_scene* sc, const double* theta, const unsigned char* mask_ovr,
+                    const double* uhat_ovr, int32_t* top2, double* gap, int nthreads) {
+  orc_params P;
+  if (sc->max_objects > 8) return 1;
+  view_params(theta, &P);
+  long N;
+  long* offs = make_offsets(sc, &N);
+  int np = sc->num_envs * sc->pads_per_env;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int p = 0; p < np; ++p) {
+    int t = sc->pad_type[p];
+    pad_state s;
+    pad_alloc(&s, sc->type_n[t]);
+    s.pos = type_ptr(sc, sc->type_pos, t);
+    s.nrm = type_ptr(sc, sc->type_nrm, t);
+    pad_contact(sc, p, &s, mask_ovr, uhat_ovr, offs[p]);
+    pad_network(&P, &s);
+    for (int c = 0; c < H; ++c) {
+      int i1 = -1, i2 = -1;
+      for (int i = 0; i < s.n; ++i) {
+        double v = s.f[(size_t)i * H + c];
+        if (i1 < 0 || v > s.f[(size_t)i1 * H + c]) {
+          i2 = i1;
+          i1 = i;
+        } else if (i2 < 0 || v > s.f[(size_t)i2 * H + c]) {
+          i2 = i;
+        }
+      }
+      double f1 = s.f[(size_t)i1 * H + c];
+      top2[2 * ((size_t)p * H + c)] = i1;
+      top2[2 * ((size_t)p * H + c) + 1] = i2;
+      gap[(size_t)p * H + c] =
+          (i2 < 0 || !(f1 > 0.0)) ? INFINITY : (f1 - s.f[(size_t)i2 * H + c]) / f1;
+    }
+    pad_free(&s);
+  }
+  free(offs);
+  return 0;
+}
+
+/* |x| / s, the margin of a ReLU or comparison decision on x relative to the scale s of the
+ * terms it sums (INFINITY when s == 0: nothing to decide) */
+static double rel_margin(double x, double s) { return s > 0.0 ? fabs(x) / s : INFINITY; }
+
+/* Margins of every discrete decision that the reverse mode of the residual network takes
+ * (Sec. III-A 2), per pad, as the smallest relative margin of each kind:
+ *   margin[5 p + 0]  ReLU of E1 and E2 at passive nodes (the decoder path), and ReLU of the
+ *                    decoder's hidden layer D1 at passive nodes;
+ *   margin[5 p + 1]  ReLU of E1 and E2 at active nodes that hold a channel's maximum;
+ *   margin[5 p + 2]  ReLU of the global layer G1;
+ *   margin[5 p + 3]  max-pool: (f_top1 - f_top2) / f_top1 for channels whose top two nodes
+ *                    include an active node (with f_top1 > 0);
+ *   margin[5 p + 4]  the same for channels whose top two nodes are both passive.
+ * A ReLU margin is |a| / (|b| + sum_k |w_k x_k|) for pre-activation a = b + sum_k w_k x_k.
+ * Pads without contact output zero and take no decision: INFINITY throughout.  The contact
+ * step (and mask_ovr / uhat_ovr) are those of orc_forward. */
+int orc_decision_margin(const orc_scene* sc, const double* theta, const unsigned char* mask_ovr,
+                        const double* uhat_ovr, double* margin, int nthreads) {
+  orc_params P;
+  if (sc->max_objects > 8) return 1;
+  view_params(theta, &P);
+  long N;
+  long* offs = make_offsets(sc, &N);
+  int np = sc->num_envs * sc->pads_per_env;
+#ifdef _OPENMP
+  if (nthreads > 0) omp_set_num_threads(nthreads);
+#pragma omp parallel for schedule(dynamic, 1)
+#endif
+  for (int p = 0; p < np; ++p) {
+    int t = sc->pad_type[p];
+    pad_state s;
+    pad_alloc(&s, sc->type_n[t]);
+    s.pos = type_ptr(sc, sc->type_pos, t);
+    s.nrm = type_ptr(sc, sc->type_nrm, t);
+    pad_contact(sc, p, &s, mask_ovr, uhat_ovr, offs[p]);
+    double mg[5] = {INFINITY, INFINITY, INFINITY, INFINITY, INFINITY};
+    if (s.m > 0) {
+      pad_network(&P, &s);
+      unsigned char* holds_max = (unsigned char*)calloc(s.n, 1);
+      for (int c = 0; c < H; ++c) holds_max[s.amax[c]] = 1;
+      for (int i = 0; i < s.n; ++i) {
+        if (s.act[i] && !holds_max[i]) continue;   /* its features reach no output */
+        int kind = s.act[i] ? 1 : 0;
+        double X[NIN], z1[H];
+        for (int a = 0; a < 3; ++a) {
+          X[a] = s.pos[3 * i + a];
+          X[3 + a] = s.nrm[3 * i + a];
+          X[6 + a] = s.uhat[3 * i + a];
+        }
+        for (int c = 0; c < H; ++c) {
+          double sc1 = fabs(P.b1[c]);
+          for (int k = 0; k < NIN; ++k) sc1 += fabs(P.W1[c * NIN + k] * X[k]);
+          double a1 = s.a1[(size_t)i * H + c];
+          z1[c] = relu(a1);
+          double mv = rel_margin(a1, sc1);
+          if (mv < mg[kind]) mg[kind] = mv;
+        }
+        for (int c = 0; c < H; ++c) {
+          double sc2 = fabs(P.b2[c]);
+          for (int k = 0; k < H; ++k) sc2 += fabs(P.W2[c * H + k] * z1[k]);
+          double mv = rel_margin(s.a2[(size_t)i * H + c], sc2);
+          if (mv < mg[kind]) mg[kind] = mv;
+        }
+        if (!s.act[i])
+          for (int c = 0; c < H; ++c) {
+            double sc3 = fabs(P.bd[c]);
+            for (int k = 0; k < H; ++k) sc3 += fabs(P.Wd[c * 2 * H + k] * s.f[(size_t)i * H + k]);
+            for (int k = 0; k < H; ++k) sc3 += fabs(P.Wd[c * 2 * H + H + k] * s.g[k]);
+            double mv = rel_margin(s.a3[(size_t)i * H + c], sc3);
+            if (mv < mg[0]) mg[0] = mv;
+          }
+      }
+      free(holds_max);
+      for (int c = 0; c < H; ++c) {
+        double scg = fabs(P.bg[c]);
+        for (int k = 0; k < H; ++k) scg += fabs(P.Wg[c * H + k] * s.g0[k]);
+        double mv = rel_margin(s.ag[c], scg);
+        if (mv < mg[2]) mg[2] = mv;
+        /* top two nodes of channel c (ties to the lower index) */
+        int i1 = -1, i2 = -1;
+        for (int i = 0; i < s.n; ++i) {
+          double v = s.f[(size_t)i * H + c];
+          if (i1 < 0 || v > s.f[(size_t)i1 * H + c]) {
+            i2 = i1;
+            i1 = i;
+          } else if (i2 < 0 || v > s.f[(size_t)i2 * H + c]) {
+            i2 = i;
+          }
+        }
+        double f1 = s.f[(size_t)i1 * H + c];
+        if (i2 >= 0 && f1 > 0.0) {
+          double gp = (f1 - s.f[(size_t)i2 * H + c]) / f1;
+          int kind = (s.act[i1] || s.act[i2]) ? 3 : 4;
+          if (gp < mg[kind]) mg[kind] = gp;
+        }
+      }
+    }
+    for (int q = 0; q < 5; ++q) margin[5 * (size_t)p + q] = mg[q];
+    pad_free(&s);
+  }
+  free(offs);
+  return 0;
+}
+
 /* Signed distance, outward gradient [n*3] and Hessian [n*9] of mesh `mesh` of the scene at n
  * object-frame points q [n*3] (the same routine the contact step calls for OBJ_MESH). */
 int orc_mesh_sdf(const orc_scene* sc, int mesh, long n, const double* q, double* phi,

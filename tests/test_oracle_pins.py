@@ -390,6 +390,90 @@ def test_forward_matches_torch_restatement(mode):
         np.testing.assert_allclose(out["disp"], ref.detach().numpy(), rtol=1e-10, atol=1e-11)
 
 
+def test_pool_margin_matches_torch_features():
+    """The max-pool margin report equals the top two channel features of the torch
+    restatement (library linear / relu, torch.topk) on every pad: the nodes and the relative
+    gap; a pad of one node has no second node and an infinite gap."""
+    th = _theta(seed=4)
+    P = TR.theta_tensors(th)[1]
+    for sc in [_small_hand(), I.sphere_press_scene(3, seed=3),
+               I.uneven_scene(2, seed=2), I.sphere_press_scene(1, seed=0, rows=1, cols=1)]:
+        fw = O.forward(sc, th)
+        r = O.pool_margin(sc, th)
+        offs = sc.node_offsets
+        for p in range(len(offs) - 1):
+            t = sc.types[sc.pad_type[p]]
+            a, b = offs[p], offs[p + 1]
+            X = torch.tensor(np.concatenate(
+                [t.pos, t.nrm, fw["disp"][a:b] * fw["mask"][a:b, None]], 1))
+            f = torch.relu(torch.nn.functional.linear(
+                torch.relu(torch.nn.functional.linear(X, P["WE1"], P["bE1"])), P["WE2"], P["bE2"]))
+            if b - a == 1:
+                assert np.all(r["top2"][p, :, 1] == -1) and np.all(np.isinf(r["gap"][p]))
+                continue
+            # stable descending order: equal values keep the lower node first
+            order = np.argsort(-f.numpy(), axis=0, kind="stable")[:2].T
+            np.testing.assert_array_equal(r["top2"][p], order)
+            v = f.numpy()
+            top, sec = v[order[:, 0], np.arange(64)], v[order[:, 1], np.arange(64)]
+            want = np.where(top > 0, (top - sec) / np.where(top > 0, top, 1), np.inf)
+            np.testing.assert_allclose(r["gap"][p], want, rtol=1e-9, atol=1e-15)
+
+
+def test_decision_margin_matches_torch_restatement():
+    """The oracle's report of the reverse mode's decision margins equals the same margins
+    computed from an independent torch restatement of the network (library linear / relu /
+    amax): per pad, the smallest relative ReLU margin at passive nodes (E1, E2, D1), at the
+    active nodes holding a channel maximum (E1, E2), of the global layer, and the max-pool
+    gaps with and without an active node among the top two."""
+    th = _theta(seed=4)
+    P = TR.theta_tensors(th)[1]
+    lin = torch.nn.functional.linear
+    for sc in [_small_hand(), I.sphere_press_scene(3, seed=3), I.uneven_scene(2, seed=2)]:
+        fw = O.forward(sc, th)
+        got = O.decision_margin(sc, th)
+        offs = sc.node_offsets
+        for p in range(len(offs) - 1):
+            a, b = offs[p], offs[p + 1]
+            m = fw["mask"][a:b] != 0
+            if not m.any():
+                assert np.all(np.isinf(got[p]))
+                continue
+            t = sc.types[sc.pad_type[p]]
+            X = torch.tensor(np.concatenate([t.pos, t.nrm, fw["disp"][a:b] * m[:, None]], 1))
+            a1 = lin(X, P["WE1"], P["bE1"])
+            s1 = lin(X.abs(), P["WE1"].abs(), P["bE1"].abs())
+            z1 = torch.relu(a1)
+            a2 = lin(z1, P["WE2"], P["bE2"])
+            s2 = lin(z1, P["WE2"].abs(), P["bE2"].abs())
+            f = torch.relu(a2)
+            g0, am = f.max(0)
+            ag = lin(g0, P["WG1"], P["bG1"])
+            sg = lin(g0, P["WG1"].abs(), P["bG1"].abs())
+            g = torch.relu(ag)
+            cat = torch.cat([f, g.expand(len(f), -1)], 1)
+            a3 = lin(cat, P["WD1"], P["bD1"])
+            s3 = lin(cat, P["WD1"].abs(), P["bD1"].abs())
+            rm = lambda x, sc_: torch.where(sc_ > 0, x.abs() / sc_, torch.full_like(x, np.inf))
+            holds = torch.zeros(len(f), dtype=torch.bool)
+            holds[am] = True
+            mt = torch.tensor(m)
+            pas, amx = ~mt, mt & holds
+            lo = lambda t_: float(t_.min()) if t_.numel() else np.inf
+            want = [min(lo(rm(a1, s1)[pas]), lo(rm(a2, s2)[pas]), lo(rm(a3, s3)[pas])),
+                    min(lo(rm(a1, s1)[amx]), lo(rm(a2, s2)[amx])), lo(rm(ag, sg))]
+            order = np.argsort(-f.numpy(), axis=0, kind="stable")[:2].T
+            v = f.numpy()
+            gaps = {3: np.inf, 4: np.inf}
+            for c in range(64):
+                i1, i2 = order[c]
+                if v[i1, c] > 0:
+                    k = 3 if (m[i1] or m[i2]) else 4
+                    gaps[k] = min(gaps[k], (v[i1, c] - v[i2, c]) / v[i1, c])
+            want = [float(w) for w in want] + [gaps[3], gaps[4]]
+            np.testing.assert_allclose(got[p], want, rtol=1e-9, atol=1e-15)
+
+
 # ----------------------------------------------------------------- reverse mode
 
 
