@@ -93,13 +93,29 @@ typedef struct {
   int32_t algo;        /* ETAC_ALGO_*                                                      */
 } etac_model_desc;
 
-/* Per-step inputs (device pointers, borrowed). */
+/* Per-step inputs (device pointers, borrowed).
+ *
+ * Mode A (active_mask_in and active_disp_in NULL): the library finds the contact itself, with
+ * the SDFs of the env's objects (Sec. III-A "Overview"); the four object / pad arrays are
+ * required.
+ * Mode B (both given): the caller supplies the contact result of an external pipeline (a mesh
+ * or FEM contact solver, recorded data): the active set and the active nodes' local
+ * displacements u_hat, which are the propagation input U_a of Eq. 1 and Eq. 4.  No SDF is
+ * evaluated and the object / pad arrays are not read (they may be NULL); the penetration
+ * output reads 0 for every node; in the reverse mode dL/du_hat is the gradient with respect
+ * to active_disp_in, and the object-pose and penetration gradients are zero.  The reverse mode
+ * of a mode-B step reads these two buffers again: they are retained (borrowed) until the
+ * step's etac_step_backward has been enqueued, and must not change before then.  Giving only
+ * one of the two is ETAC_ERR_INVALID_ARG. */
 typedef struct {
   const int32_t* obj_type;   /* [E*K] ETAC_OBJ_*; ETAC_OBJ_NONE slots are ignored           */
   const float* obj_dims;     /* [E*K*3] sphere (r,-,-); box half-extents (hx,hy,hz);
                                 cylinder / capsule (r, half-length along local z, -)       */
   const float* obj_pose;     /* [E*K*7] world pose of each object                           */
   const float* pad_pose;     /* [E*P*7] world pose of each pad instance                     */
+  const float* active_disp_in;     /* mode B: [N*3] u_hat of active nodes, pad frame (mm);
+                                      entries of passive nodes are ignored                  */
+  const uint8_t* active_mask_in;   /* mode B: [N] nonzero = active                         */
 } etac_step_in;
 
 /* Per-step outputs (device pointers, borrowed; NULL = not wanted, except disp). */
@@ -136,7 +152,15 @@ etac_status etac_set_model(etac_ctx* ctx, const etac_model_desc* desc, const flo
 etac_status etac_step_forward(etac_ctx* ctx, const etac_step_in* in, const etac_step_out* out,
                               void* stream);
 
-/* Reverse mode of the last etac_step_forward on this context (FP32, hand-written).
+/* Id of the last etac_step_forward enqueued on this context: 1 for the first, then 2, 3, ...
+ * (0 before any).  Host-side bookkeeping: no GPU work. */
+etac_status etac_last_step(const etac_ctx* ctx, uint64_t* step_id);
+
+/* Reverse mode (FP32, hand-written) of the forward step `step_id` on this context (the id
+ * etac_last_step gave right after that forward).  The context keeps the saved state of its
+ * last forward only, so any other id is refused with ETAC_ERR_STATE (nothing is enqueued):
+ * a caller that ran several forwards before differentiating them must re-run the one it
+ * differentiates.  step_id = 0 means "the last forward", unchecked.
  * grad_disp [N*3] is dL/d(disp).  Outputs are overwritten (not accumulated); any may be
  * NULL: grad_obj_pose [E*K*6] = (dL/dt world, dL/d omega) with the rotation increment
  * exp([omega]x) applied on the left about the object origin; grad_uhat [N*3] = dL/d u_hat of
@@ -144,9 +168,9 @@ etac_status etac_step_forward(etac_ctx* ctx, const etac_step_in* in, const etac_
  * with u_hat = penetration * outward normal (0 on passive nodes); grad_params [P] for the
  * flat parameter vector.  The contact set is held fixed.  ETAC_ERR_STATE without a prior
  * forward. */
-etac_status etac_step_backward(etac_ctx* ctx, const float* grad_disp, float* grad_obj_pose,
-                               float* grad_uhat, float* grad_penetration, float* grad_params,
-                               void* stream);
+etac_status etac_step_backward(etac_ctx* ctx, uint64_t step_id, const float* grad_disp,
+                               float* grad_obj_pose, float* grad_uhat, float* grad_penetration,
+                               float* grad_params, void* stream);
 
 /* Chain rule from the pose gradient of etac_step_backward to the 7-float pose layout: given
  * poses [count*7] (t, q) and their twist gradients [count*6] (dL/dt, dL/d omega with the
@@ -155,6 +179,20 @@ etac_status etac_step_backward(etac_ctx* ctx, const float* grad_disp, float* gra
  * Device pointers; enqueued on `stream`. */
 etac_status etac_pose_grad_to_quat(const float* poses, const float* twist_grad, float* pose_grad,
                                    int64_t count, void* stream);
+
+/* ---- Failure-path test hook (the paper has no counterpart; for tests only).
+ * Every wait inside the library's kernels is bounded: a wait that runs out latches
+ * ETAC_ERR_TIMEOUT in the device status word, and the kernel winds down (it waits, bounded,
+ * for its own copies and tensor-core operations in flight and frees its tensor memory) and
+ * returns, leaving the context usable.  This hook lets a test make such a wait run out
+ * without any fault: for the following forward steps of a batched BF16 model, the
+ * propagation GEMM's load producer does not issue the loads of the first K block of GEMM
+ * tile `tile` (nothing else is loaded by that CTA), so its MMA issuer's wait on them gives up
+ * after `wait_limit_ns` (0: the default 2 s; at most 2 s); the pads of that CTA's tiles are
+ * left unwritten.  tile = -1 turns the hook off and restores the default limit.
+ * ETAC_ERR_STATE without a batched BF16 model; ETAC_ERR_INVALID_ARG for a tile outside
+ * [-1, number of tiles) or a limit above 2 s. */
+etac_status etac_test_withhold_load(etac_ctx* ctx, int32_t tile, uint64_t wait_limit_ns);
 
 /* Reads and clears the device status word (synchronises `stream`).  *device_status receives
  * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE. */
@@ -337,40 +375,62 @@ void etac_mesh_gpu_destroy(etac_mesh_gpu* mesh);
  * etac_step_forward_noalloc runs the batched FP32 forward (ETAC_ALGO_BATCHED,
  * ETAC_PREC_FP32) from device pointers only.  The caller passes every input (pad geometry,
  * parameters, poses) and every output; the scratch the step needs (work-queue counter, status
- * word, per-pad-type tables) lives in one static device array of ETAC_NOALLOC_SCRATCH_BYTES
+ * words, per-pad-type tables) lives in one static device array of ETAC_NOALLOC_SCRATCH_BYTES
  * inside the library, which every GPU that loads the library holds until the process exits.
  * The call allocates and frees nothing.  Limits: the scratch must hold
  * 896 bytes per pad-type node, 4 bytes per (node, node) pair of every pad type, and 4 bytes
  * per pad instance (plus alignment); larger batches are rejected with ETAC_ERR_INVALID_ARG
- * and a message giving the bytes needed.
+ * and a message giving the bytes needed.  A pad type too large for the batched kernel's
+ * shared memory gives ETAC_ERR_UNSUPPORTED, as etac_set_model does.
+ *
+ * What is checked, and where:
+ *   - on the host, before anything is enqueued: NULL pointers, mode, num_types, num_envs,
+ *     pads_per_env, max_objects and every type_num_nodes entry (range), and the scratch size
+ *     those imply;
+ *   - on the device, by the first kernel of the call, before any other kernel indexes with
+ *     them: type_off must start at 0 and its differences must be node counts in
+ *     [1, max type_num_nodes] whose sum and sum of squares equal those of type_num_nodes;
+ *     every pad_type must lie in [0, num_types); pad_off must start at 0 and step by each
+ *     pad's node count.  If any of these fails, no output is written and the status word
+ *     reads ETAC_ERR_INVALID_ARG;
+ *   - trusted, not checked: that every device array holds the number of elements given
+ *     below (type_pos / type_nrm [sum n, 3], pad_type [E*P], pad_off [E*P+1], params
+ *     [etac_param_count], the step inputs, and outputs of pad_off[E*P] nodes), that alpha
+ *     > 0, and that the arrays do not overlap the outputs.
+ *
+ * device_status (optional, device int32 [1]) receives, in stream order after the step,
+ * ETAC_OK, ETAC_ERR_INVALID_ARG (device-side geometry checks failed, nothing written) or
+ * ETAC_ERR_NONFINITE (a pose held NaN / Inf; those pads output zero).
  *
  * The first call on each device looks up the device address of the static array (once, with
- * that device current), so make that first call before any stream capture.  Every call
- * rebuilds the tables from `params` and clears the counter it needs, so calls are
- * independent, but all calls share the one array: calls that overlap on the GPU (different
- * streams, or different host threads on one device) race and give wrong results.
- * Non-finite poses zero the affected pads but are not reported (there is no context to hold
- * the status word).  Errors are read with etac_last_error(NULL). */
+ * that device current) and keeps it for the life of the process, so make that first call
+ * before any stream capture, and do not call this entry point after a cudaDeviceReset (the
+ * kept address would be stale).  Every call rebuilds the tables from `params` and clears the
+ * words it needs, so calls are independent, but all calls share the one array: calls that
+ * overlap on the GPU (different streams, or different host threads on one device) race and
+ * give wrong results.  Errors found on the host are read with etac_last_error(NULL). */
 #define ETAC_NOALLOC_SCRATCH_BYTES (32u << 20)
 
 typedef struct {
   int32_t num_types;             /* T >= 1                                                    */
   const int32_t* type_num_nodes; /* HOST [T] node count per pad type (sizes and validation)    */
-  const int32_t* type_off;       /* device [T+1] prefix sums of type_num_nodes                  */
+  const int32_t* type_off;       /* device [T+1] prefix sums of type_num_nodes (checked)        */
   const float* type_pos;         /* device [sum n, 3] undeformed positions, pad frame (mm)     */
   const float* type_nrm;         /* device [sum n, 3] unit outward normals                      */
   int32_t num_envs;              /* >= 1                                                        */
   int32_t pads_per_env;          /* >= 1                                                        */
   int32_t max_objects;           /* K in [1, ETAC_MAX_OBJECTS]                                  */
-  const int32_t* pad_type;       /* device [E*P] pad type of each pad instance                  */
-  const int64_t* pad_off;        /* device [E*P+1] first flat node index of each pad instance   */
+  const int32_t* pad_type;       /* device [E*P] pad type of each pad instance (checked)        */
+  const int64_t* pad_off;        /* device [E*P+1] first flat node index of each pad (checked)  */
 } etac_noalloc_pads;
 
 /* mode: ETAC_MODE_*; params: device FP32 [etac_param_count] (alpha must be > 0, unchecked);
- * in / out as for etac_step_forward (device pointers).  Enqueues work on `stream` only. */
+ * in / out as for etac_step_forward (device pointers); device_status optional (see above).
+ * Enqueues work on `stream` only. */
 etac_status etac_step_forward_noalloc(const etac_noalloc_pads* pads, int32_t mode,
                                       const float* params, const etac_step_in* in,
-                                      const etac_step_out* out, void* stream);
+                                      const etac_step_out* out, int32_t* device_status,
+                                      void* stream);
 
 #ifdef __cplusplus
 }

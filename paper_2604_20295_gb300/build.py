@@ -2,6 +2,10 @@
 
 ``python -m paper_2604_20295_gb300.build`` or ``build()``; the library lands in
 ``paper_2604_20295_gb300/_build/libetac.so`` and is rebuilt when a source or header is newer.
+``build(variant=...)`` builds a variant of the same sources with extra defines into its own
+folder (``_build/<variant>/libetac.so``); the binding loads it when ``ETAC_LIBRARY`` names it.
+Variants: ``outline_refine`` (the exact contact decision as an out-of-line call in every
+kernel, to show that inlining does not change the results).
 """
 from __future__ import annotations
 
@@ -42,23 +46,35 @@ def _deps() -> list:
             [os.path.abspath(__file__)])
 
 
-def _stale() -> bool:
-    if not os.path.exists(LIB):
+VARIANTS = {"outline_refine": ["-DETAC_OUTLINE_REFINE"]}
+
+
+def variant_lib(variant: str) -> str:
+    return os.path.join(OUT_DIR, variant, "libetac.so")
+
+
+def _stale(lib: str = LIB) -> bool:
+    if not os.path.exists(lib):
         return True
-    t = os.path.getmtime(LIB)
+    t = os.path.getmtime(lib)
     return any(os.path.getmtime(p) > t for p in _deps())
 
 
-def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
+def build(force: bool = False, verbose: bool = False, extra_flags=(), variant: str = None) -> str:
     """Compile every CUDA source for sm_103a and link libetac.so (no-op when up to date)."""
-    if not force and not _stale():
-        return LIB
-    os.makedirs(OUT_DIR, exist_ok=True)
+    out_dir, lib = OUT_DIR, LIB
+    if variant is not None:
+        extra_flags = list(extra_flags) + VARIANTS[variant]
+        out_dir = os.path.join(OUT_DIR, variant)
+        lib = variant_lib(variant)
+    if not force and not _stale(lib):
+        return lib
+    os.makedirs(out_dir, exist_ok=True)
     nvcc = _nvcc()
     flags = NVCC_FLAGS + list(extra_flags)
 
     def compile_one(src):
-        obj = os.path.join(OUT_DIR, os.path.splitext(os.path.basename(src))[0] + ".o")
+        obj = os.path.join(out_dir, os.path.splitext(os.path.basename(src))[0] + ".o")
         cmd = [nvcc] + ARCH + flags + ["-c", src, "-o", obj]
         if verbose:
             cmd.append("-Xptxas=-v")
@@ -72,13 +88,13 @@ def build(force: bool = False, verbose: bool = False, extra_flags=()) -> str:
     srcs = sources()
     with cf.ThreadPoolExecutor(max_workers=min(len(srcs), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, srcs))
-    tmp = LIB + f".tmp{os.getpid()}"
+    tmp = lib + f".tmp{os.getpid()}"
     cmd = [nvcc] + ARCH + ["-shared", "-o", tmp] + objs
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"link of libetac.so failed:\n{r.stderr}")
-    os.replace(tmp, LIB)
-    return LIB
+    os.replace(tmp, lib)
+    return lib
 
 
 if __name__ == "__main__":

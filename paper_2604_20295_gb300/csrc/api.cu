@@ -39,6 +39,10 @@ struct etac_ctx {
   float* d_params = nullptr;
   // state of the last forward (device copies of its inputs)
   bool has_forward = false;
+  uint64_t step_id = 0;   // id of the last forward enqueued on this context (1, 2, ...)
+  // mode B of the last forward: the caller's active set and u_hat (borrowed), else null
+  const uint8_t* given_mask = nullptr;
+  const float* given_uhat = nullptr;
   int* d_saved_obj_type = nullptr;
   float* d_saved_obj_dims = nullptr;
   float* d_saved_obj_pose = nullptr;
@@ -71,6 +75,8 @@ struct etac_ctx {
   long long* d_mask_woff = nullptr;
   int* d_pad_m = nullptr;
   float* d_g0a = nullptr;
+  int* d_g0arg = nullptr;      // [E*P][64] maximising node of g0 (FP32 batched forward)
+  bool fwd_recorded = false;   // the last forward recorded g0 / d_g0arg for the reverse
   float2* d_ranked = nullptr;
   etac::PadObj* d_padobj = nullptr;
   int* d_pad_bad = nullptr;
@@ -206,7 +212,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_a3_toff, c->d_a3_tg, c->d_a3, c->d_d2part, c->d_r4part, c->d_r4bpart,
                   c->d_r5part, c->d_alpha_part, c->d_gsum_part, c->d_spart, c->d_s_toff,
                   c->d_s_nr, c->d_ws_idx, c->d_ws_u,
-                  c->d_ws_du, c->d_pose_part, c->d_param_part};
+                  c->d_ws_du, c->d_pose_part, c->d_param_part, c->d_g0arg};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -384,6 +390,7 @@ void fill_gemm_common(etac_ctx* c, etac::GemmParams& g) {
   g.params = c->d_params;
   g.status = c->d_status;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
+  g.test_withhold = 0;
 }
 
 // B-operand tensor map of the forward GEMM carries the tile shape (box rows = 3 x instances)
@@ -422,7 +429,7 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bt), 2 * (size_t)c->bt_total);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
-  if (e == cudaSuccess) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
+  if (e == cudaSuccess && !c->d_g0a) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
   if (e != cudaSuccess) return cuda_fail(c, e, "BF16 buffers");
   etac::GemmParams& g = c->gemm;
   memset(&g, 0, sizeof g);
@@ -560,6 +567,8 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_r5part, (size_t)c->r5_parts * (etac::OFF_W4 - etac::OFF_W1));
   if (e == cudaSuccess) e = dalloc(&c->d_alpha_part, (size_t)c->num_sms);   // >= GEMM grid
   if (e == cudaSuccess) e = dalloc(&c->d_gsum_part, (size_t)c->r4b_parts * 3);
+  if (e == cudaSuccess && !c->d_g0a) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
+  if (e == cudaSuccess) e = dalloc(&c->d_g0arg, (size_t)np * etac::H);
   if (e != cudaSuccess) return cuda_fail(c, e, "reverse-mode buffers");
   if ((st = build_r3(c, c->r3_range, s)) != ETAC_OK) return st;
   for (int which = 0; which < 2; ++which) {
@@ -659,6 +668,8 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   f.pad_pose = c->d_saved_pad_pose;
   f.padobj = c->d_padobj;
   f.pad_bad = c->d_pad_bad;
+  f.mask_in = c->given_mask;
+  f.uhat_in = c->given_uhat;
   int ts = timing_begin(c, K_PADOBJ, s);
   ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
   timing_end(c, ts, s);
@@ -696,6 +707,10 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   b.bg_hi = c->d_bg_hi;
   b.bg_lo = c->d_bg_lo;
   b.mode = c->model.mode;
+  b.mask_in = c->given_mask;
+  b.uhat_in = c->given_uhat;
+  b.g0rec = c->fwd_recorded ? c->d_g0a : nullptr;
+  b.g0arg = c->fwd_recorded ? c->d_g0arg : nullptr;
   b.grad_disp = grad_disp;
   b.grad_uhat = grad_uhat;
   b.grad_pen = grad_pen;
@@ -844,16 +859,20 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
   }
   const int total_type_nodes = c->type_off[c->T];
   c->type_pmax.assign(c->T, 0.f);
+  // type_pmax: the largest Euclidean |p| of the type's nodes (the screening margin's bound)
   for (int t = 0; t < c->T; ++t)
     for (int i = c->type_off[t]; i < c->type_off[t + 1]; ++i) {
+      double p2 = 0.0;
       for (int q = 0; q < 3; ++q) {
         float v = d->type_pos[3 * i + q], w = d->type_nrm[3 * i + q];
         if (!std::isfinite(v) || !std::isfinite(w)) {
           free_ctx(c);
           return fail(nullptr, ETAC_ERR_INVALID_ARG, "non-finite node geometry (type %d)", t);
         }
-        c->type_pmax[t] = std::max(c->type_pmax[t], std::fabs(v));
+        p2 += (double)v * v;
       }
+      // rounded up so that the FP32 value is never below the exact norm
+      c->type_pmax[t] = std::max(c->type_pmax[t], std::nextafter((float)std::sqrt(p2), INFINITY));
     }
   c->pad_type.assign(d->pad_type, d->pad_type + np);
   c->pad_off.resize(np + 1, 0);
@@ -978,24 +997,37 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->has_model) return fail(c, ETAC_ERR_STATE, "etac_set_model has not been called");
   if (!in || !out) return fail(c, ETAC_ERR_INVALID_ARG, "in/out is NULL");
-  if (!in->obj_type || !in->obj_dims || !in->obj_pose || !in->pad_pose || !out->disp)
+  const bool given = in->active_mask_in != nullptr;
+  if (given != (in->active_disp_in != nullptr))
+    return fail(c, ETAC_ERR_INVALID_ARG,
+                "active_mask_in and active_disp_in must be given together (or neither)");
+  if ((!given && (!in->obj_type || !in->obj_dims || !in->obj_pose || !in->pad_pose)) ||
+      !out->disp)
     return fail(c, ETAC_ERR_INVALID_ARG, "required input/output pointer is NULL");
-  if (!aligned(in->obj_type, 4) || !aligned(in->obj_dims, 4) || !aligned(in->obj_pose, 4) ||
-      !aligned(in->pad_pose, 4) || !aligned(out->disp, 4) ||
+  if ((!given && (!aligned(in->obj_type, 4) || !aligned(in->obj_dims, 4) ||
+                  !aligned(in->obj_pose, 4) || !aligned(in->pad_pose, 4))) ||
+      (given && !aligned(in->active_disp_in, 4)) || !aligned(out->disp, 4) ||
       (out->penetration && !aligned(out->penetration, 4)) ||
       (out->active_count && !aligned(out->active_count, 4)))
     return fail(c, ETAC_ERR_INVALID_ARG, "pointer not 4-byte aligned");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   const size_t EK = (size_t)c->E * c->K, EP = (size_t)c->E * c->P;
-  // keep this step's inputs for the reverse mode
-  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_type, in->obj_type, sizeof(int) * EK,
-                               cudaMemcpyDeviceToDevice, s), "save inputs");
-  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_dims, in->obj_dims, sizeof(float) * EK * 3,
-                               cudaMemcpyDeviceToDevice, s), "save inputs");
-  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_pose, in->obj_pose, sizeof(float) * EK * 7,
-                               cudaMemcpyDeviceToDevice, s), "save inputs");
-  ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_pad_pose, in->pad_pose, sizeof(float) * EP * 7,
-                               cudaMemcpyDeviceToDevice, s), "save inputs");
+  // keep this step's inputs for the reverse mode (mode B: the caller's buffers, borrowed)
+  if (!given) {
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_type, in->obj_type, sizeof(int) * EK,
+                                 cudaMemcpyDeviceToDevice, s), "save inputs");
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_dims, in->obj_dims, sizeof(float) * EK * 3,
+                                 cudaMemcpyDeviceToDevice, s), "save inputs");
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_obj_pose, in->obj_pose, sizeof(float) * EK * 7,
+                                 cudaMemcpyDeviceToDevice, s), "save inputs");
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_saved_pad_pose, in->pad_pose, sizeof(float) * EP * 7,
+                                 cudaMemcpyDeviceToDevice, s), "save inputs");
+  }
+  // a forward that fails from here on leaves no state to differentiate
+  c->has_forward = false;
+  c->fwd_recorded = false;
+  c->given_mask = in->active_mask_in;
+  c->given_uhat = in->active_disp_in;
   if (c->model.algo == ETAC_ALGO_BATCHED) {
     etac::BatchedArgs b{};
     b.type_pos = c->d_type_pos;
@@ -1027,6 +1059,13 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.count = out->active_count;
     b.ticket = c->d_ticket;
     b.status = c->d_status;
+    b.mask_in = c->given_mask;
+    b.uhat_in = c->given_uhat;
+    // the FP32 forward records each pad's max-pool state for the staged reverse mode
+    const bool record = c->bwdb_ready && c->d_g0arg && c->model.precision == ETAC_PREC_FP32;
+    b.g0rec = record ? c->d_g0a : nullptr;
+    b.g0arg = record ? c->d_g0arg : nullptr;
+    c->fwd_recorded = record;
     ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
     if (c->model.precision == ETAC_PREC_BF16) {
       etac::FrontArgs f{};
@@ -1069,6 +1108,8 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.pad_gi = c->d_pad_gi;
       f.padobj = c->d_padobj;
       f.pad_bad = c->d_pad_bad;
+      f.mask_in = c->given_mask;
+      f.uhat_in = c->given_uhat;
       if (!f.padobj || !f.pad_bad || !f.pad_gi || !c->gemm.inst_base || !c->gemm.type_woff || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
           !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
@@ -1092,6 +1133,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s, etac::GEMM_FWD, c->gemm_gi), "BF16 propagation GEMM launch");
       timing_end(c, ts, s);
       c->has_forward = true;
+      ++c->step_id;
       return ETAC_OK;
     }
     const int ts = timing_begin(c, K_BATCHED, s);
@@ -1099,6 +1141,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
               "batched forward launch");
     timing_end(c, ts, s);
     c->has_forward = true;
+    ++c->step_id;
     return ETAC_OK;
   }
   etac::PlainArgs<float> a{};
@@ -1122,18 +1165,46 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
   a.pen = out->penetration;
   a.count = out->active_count;
   a.status = c->d_status;
+  a.mask_in = c->given_mask;
+  a.uhat_in = c->given_uhat;
   const int ts = timing_begin(c, K_PLAIN, s);
   ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
   timing_end(c, ts, s);
   c->has_forward = true;
+  ++c->step_id;
   return ETAC_OK;
 }
 
-etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_obj_pose,
-                               float* grad_uhat, float* grad_penetration, float* grad_params,
-                               void* stream) {
+etac_status etac_test_withhold_load(etac_ctx* c, int32_t tile, uint64_t wait_limit_ns) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (!c->has_model || c->model.algo != ETAC_ALGO_BATCHED ||
+      c->model.precision != ETAC_PREC_BF16 || !c->bf16_ready)
+    return fail(c, ETAC_ERR_STATE, "the load hook applies to a batched BF16 model");
+  if (tile < -1 || tile >= c->num_tiles)
+    return fail(c, ETAC_ERR_INVALID_ARG, "tile %d outside [-1, %d)", tile, c->num_tiles);
+  if (wait_limit_ns > 2000000000ull)
+    return fail(c, ETAC_ERR_INVALID_ARG, "wait limit above 2 s");
+  c->gemm.test_withhold = tile + 1;
+  c->gemm.timeout_ns = wait_limit_ns ? wait_limit_ns : 2000000000ull;
+  return ETAC_OK;
+}
+
+etac_status etac_last_step(const etac_ctx* c, uint64_t* step_id) {
+  if (!c || !step_id) return fail(nullptr, ETAC_ERR_INVALID_ARG, "NULL argument");
+  *step_id = c->has_forward ? c->step_id : 0;
+  return ETAC_OK;
+}
+
+etac_status etac_step_backward(etac_ctx* c, uint64_t step_id, const float* grad_disp,
+                               float* grad_obj_pose, float* grad_uhat, float* grad_penetration,
+                               float* grad_params, void* stream) {
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->has_forward) return fail(c, ETAC_ERR_STATE, "no forward step to differentiate");
+  if (step_id != 0 && step_id != c->step_id)
+    return fail(c, ETAC_ERR_STATE,
+                "step %llu is not the last forward on this context (last: %llu); its saved "
+                "state has been overwritten",
+                (unsigned long long)step_id, (unsigned long long)c->step_id);
   if (!grad_disp) return fail(c, ETAC_ERR_INVALID_ARG, "grad_disp is NULL");
   if (!aligned(grad_disp, 4) || (grad_obj_pose && !aligned(grad_obj_pose, 4)) ||
       (grad_uhat && !aligned(grad_uhat, 4)) || (grad_penetration && !aligned(grad_penetration, 4)) ||
@@ -1176,6 +1247,8 @@ etac_status etac_step_backward(etac_ctx* c, const float* grad_disp, float* grad_
   b.ws_du = c->d_ws_du;
   b.pose_part = c->d_pose_part;
   b.param_part = c->d_param_part;
+  b.mask_in = c->given_mask;
+  b.uhat_in = c->given_uhat;
   const int ts = timing_begin(c, K_BWD, s);
   ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
   timing_end(c, ts, s);
@@ -1233,7 +1306,9 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
     return ETAC_OK;
   };
   auto fwd = [&]() { return etac_step_forward(c, in, out, stream); };
-  auto bwd = [&]() { return etac_step_backward(c, grad_disp, nullptr, nullptr, nullptr, nullptr, stream); };
+  auto bwd = [&]() {
+    return etac_step_backward(c, 0, grad_disp, nullptr, nullptr, nullptr, nullptr, stream);
+  };
   etac_tuning t = *r;
   if (c->bf16_ready && c->model.precision == ETAC_PREC_BF16) {
     const int cand[4][2] = {{64, 0}, {64, 1}, {32, 0}, {32, 1}};

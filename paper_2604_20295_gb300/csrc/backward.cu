@@ -146,7 +146,8 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
     for (int w = tid; w < nwords; w += BB) sBits[w] = 0u;
     for (int k = tid; k < a.K * 6; k += BB) a.pose_part[(size_t)pad * a.K * 6 + k] = 0.f;
     __syncthreads();
-    if (tid < a.K) {
+    const bool given = a.mask_in != nullptr;   // mode B: the forward's contact was supplied
+    if (tid < a.K && !given) {
       const int ob = env * a.K + tid;
       const float* op = a.obj_pose + 7 * (size_t)ob;
       const float* pp = a.pad_pose + 7 * (size_t)pad;
@@ -170,8 +171,9 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
       NodeContact c;
       c.active = false;
       if (i < n && !invalid)
-        c = contact_node(spo, a.K, make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]),
-                         make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]));
+        c = given ? contact_given(a.mask_in, a.uhat_in, base + i)
+                  : contact_node(spo, a.K, make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]),
+                                 make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]));
       const unsigned bal = __ballot_sync(0xffffffffu, c.active);
       if (lane == 0) {
         sCnt[4 + warp] = __popc(bal);
@@ -615,16 +617,20 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
     for (int k = 0; k < MAX_K; ++k)
 #pragma unroll
       for (int q = 0; q < 6; ++q) pose[k][q] = 0.f;
-    const float* pp = a.pad_pose + 7 * (size_t)pad;
-    float Rp[3][3];
-    quat_to_mat<float>(pp + 3, Rp);
+    const float* pp = given ? nullptr : a.pad_pose + 7 * (size_t)pad;
+    float Rp[3][3] = {};
+    if (!given) quat_to_mat<float>(pp + 3, Rp);
     for (int s = tid; s < m; s += BB) {
       const int i = wIdx[s];
       const float4 du = wDU[s];
       const float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
       const float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-      const NodePoseGrad pg = node_pose_grad(spo, a.K, p, nr, make_float3(du.x, du.y, du.z), Rp, pp,
-                                             a.obj_pose + 7 * (size_t)env * a.K);
+      NodePoseGrad pg;
+      pg.k = -1;   // mode B: no SDF, so no penetration or pose gradient
+      pg.pen = 0.f;
+      if (!given)
+        pg = node_pose_grad(spo, a.K, p, nr, make_float3(du.x, du.y, du.z), Rp, pp,
+                            a.obj_pose + 7 * (size_t)env * a.K);
       if (a.grad_uhat) {
         float* g = a.grad_uhat + 3 * (base + i);
         g[0] = du.x;

@@ -23,7 +23,7 @@ constexpr int BW = BT / 32;
 
 struct BatchedSmem {
   // byte offsets of every shared array for a given nmax / K
-  size_t w2, b2, w1u, w4, b4, g, beta, red, actu, actidx, mask, warp, po, total;
+  size_t w2, b2, w1u, w4, b4, g, beta, red, redi, actu, actidx, mask, warp, po, total;
   __host__ __device__ BatchedSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -39,6 +39,7 @@ struct BatchedSmem {
     g = take(sizeof(float) * H);
     beta = take(sizeof(float) * H);
     red = take(sizeof(float) * BW * H);
+    redi = take(sizeof(int) * BW * H);
     actu = take(sizeof(float4) * (size_t)nmax);
     actidx = take(sizeof(int16_t) * (size_t)nmax);
     mask = take(sizeof(uint8_t) * (size_t)nmax);
@@ -50,6 +51,7 @@ struct BatchedSmem {
 
 __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
+  if (a.skip && *a.skip) return;
   __shared__ int s_item;
   const BatchedSmem L(a.nmax, a.K);
   float* sW2 = reinterpret_cast<float*>(smem + L.w2);
@@ -60,6 +62,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   float* sG = reinterpret_cast<float*>(smem + L.g);
   float* sBeta = reinterpret_cast<float*>(smem + L.beta);
   float* sRed = reinterpret_cast<float*>(smem + L.red);
+  int* sRedI = reinterpret_cast<int*>(smem + L.redi);   // maximising node per (warp, channel)
   float4* sActU = reinterpret_cast<float4*>(smem + L.actu);
   int16_t* sActIdx = reinterpret_cast<int16_t*>(smem + L.actidx);
   uint8_t* sMask = reinterpret_cast<uint8_t*>(smem + L.mask);
@@ -98,7 +101,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     const float* tpos = a.type_pos + 3 * (size_t)o;
     const float* tnrm = a.type_nrm + 3 * (size_t)o;
 
-    if (tid < a.K) {
+    const bool given = a.mask_in != nullptr;   // mode B: contact supplied by the caller
+    if (tid < a.K && !given) {
       const int ob = env * a.K + tid;
       const float* op = a.obj_pose + 7 * (size_t)ob;
       const float* pp = a.pad_pose + 7 * (size_t)pad;
@@ -136,7 +140,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       if (i < n) {
         float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        c = contact_node(spo, a.K, p, nr);
+        c = given ? contact_given(a.mask_in, a.uhat_in, base + i) : contact_node(spo, a.K, p, nr);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, c.active);
       if (lane == 0) sWarp[warp] = __popc(bal);
@@ -177,6 +181,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     // ---- 2. residual network (factored)
     if (uses_residual(a.mode)) {
     float fm0 = 0.f, fm1 = 0.f;   // running max of channels lane and lane + 32
+    int fi0 = 0x7fffffff, fi1 = 0x7fffffff;   // their lowest-index maximiser (node)
     for (int a0 = 0; a0 < m; a0 += BT) {
       const int aa = a0 + tid;
       const bool live = aa < m;
@@ -215,7 +220,19 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         const float f = live ? fmaxf(acc, 0.f) : 0.f;
         // f >= 0, so unsigned order of the bit patterns is the float order
         const float mx = __uint_as_float(__reduce_max_sync(0xffffffffu, __float_as_uint(f)));
-        if (c < 32) {
+        if (a.g0arg) {
+          // the lowest active slot holding the maximum: slots are in node order
+          const unsigned hold = __ballot_sync(0xffffffffu, live && f == mx);
+          const int node = hold ? (int)sActIdx[a0 + 32 * warp + __ffs(hold) - 1] : 0x7fffffff;
+          if (lane == (c & 31)) {
+            float& fm = c < 32 ? fm0 : fm1;
+            int& fi = c < 32 ? fi0 : fi1;
+            if (mx > fm || (mx == fm && node < fi)) {
+              fm = mx;
+              fi = node;
+            }
+          }
+        } else if (c < 32) {
           if (lane == c) fm0 = fmaxf(fm0, mx);
         } else {
           if (lane == c - 32) fm1 = fmaxf(fm1, mx);
@@ -224,23 +241,47 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     }
     sRed[warp * H + lane] = fm0;
     sRed[warp * H + 32 + lane] = fm1;
+    if (a.g0arg) {
+      sRedI[warp * H + lane] = fi0;
+      sRedI[warp * H + 32 + lane] = fi1;
+    }
     __syncthreads();
     
 
       if (tid < H) {
         float g0 = 0.f;
+        int gi = 0x7fffffff;
 #pragma unroll
-        for (int w = 0; w < BW; ++w) g0 = fmaxf(g0, sRed[w * H + tid]);
+        for (int w = 0; w < BW; ++w) {
+          const float v = sRed[w * H + tid];
+          if (a.g0arg) {
+            const int id = sRedI[w * H + tid];
+            if (v > g0 || (v == g0 && id < gi)) {
+              g0 = v;
+              gi = id;
+            }
+          } else {
+            g0 = fmaxf(g0, v);
+          }
+        }
         // passive maximum: first passive node in this channel's descending order of f0
         const int16_t* ord = a.order + (size_t)H * o + (size_t)tid * n;
         for (int r = 0; r < n; ++r) {
           const int idx = ord[r];
           if (!sMask[idx]) {
-            g0 = fmaxf(g0, __ldg(a.f0tab + (size_t)(o + idx) * H + tid));
+            const float v = __ldg(a.f0tab + (size_t)(o + idx) * H + tid);
+            if (v > g0 || (v == g0 && idx < gi)) {
+              g0 = v;
+              gi = idx;
+            }
             break;
           }
         }
         sG[tid] = g0;
+        if (a.g0arg) {   // the forward state the reverse mode differentiates
+          a.g0rec[(size_t)pad * H + tid] = g0;
+          a.g0arg[(size_t)pad * H + tid] = gi;
+        }
       }
       __syncthreads();
       {

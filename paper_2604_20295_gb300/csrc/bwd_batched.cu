@@ -8,9 +8,10 @@
 //   R1 bwd_pad_kernel (warp per pad): contact (same decisions as the forward), u_hat and phi
 //      of the active nodes, dL/du_hat's direct term, the passive upstream gradient G as the
 //      split BF16 B operand of the propagation reverse, sum G over passive nodes, and the
-//      channel maxima of f with their lowest-index argmax: the active nodes' encoder to FP32
-//      accuracy on tensor cores (inputs, activations and weights split into BF16 hi / lo
-//      parts), the passive candidate from the ranked f0 table;
+//      channel maxima of f with their lowest-index argmax, either recorded by the forward
+//      (FP32 batched models) or recomputed: the active nodes' encoder to FP32 accuracy on
+//      tensor cores (inputs, activations and weights split into three BF16 parts), the
+//      passive candidate from the ranked f0 table;
 //   R2 bwd_global_kernel (64 pads per CTA, register-tiled): ag = G1 g0 + b, g = ReLU(ag),
 //      beta = D1_g g;
 //   R3 bwd_decoder_kernel (type x 64-instance groups): for every passive (instance k, node
@@ -56,15 +57,18 @@ __device__ __forceinline__ uint32_t bf2(float a, float b) {
 __device__ __forceinline__ float bfr(float x) {   // x - BF16(x)
   return x - __bfloat162float(__float2bfloat16_rn(x));
 }
-// hi = BF16 pair of (a, b), lo = BF16 pair of the remainders: a ~ hi + lo to ~16 bits
-__device__ __forceinline__ void split2(float a, float b, uint32_t& hi, uint32_t& lo) {
-  hi = bf2(a, b);
-  lo = bf2(bfr(a), bfr(b));
+// Three-part split of an FP32 value into BF16 parts x = x0 + x1 + x2 + r with |r| <= 2^-24 |x|
+// (each part holds the next 8 significant bits of the remainder), applied to a pair.
+__device__ __forceinline__ void split3(float a, float b, uint32_t& p0, uint32_t& p1, uint32_t& p2) {
+  const float a1 = bfr(a), b1 = bfr(b);
+  p0 = bf2(a, b);
+  p1 = bf2(a1, b1);
+  p2 = bf2(bfr(a1), bfr(b1));
 }
 
 // ----------------------------------------------------------------------------- R1
 struct R1Smem {
-  size_t w1f, w2h, w2l, b2, warp0, warp_bytes, po, bits, pend, pnode, cand, fmv, fmi, total;
+  size_t w1f, w2f, b2, warp0, warp_bytes, po, bits, pend, pnode, cand, fmv, fmi, total;
   __host__ __device__ R1Smem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -72,9 +76,8 @@ struct R1Smem {
       o = (o + bytes + 15) & ~size_t(15);
       return r;
     };
-    w1f = take(sizeof(uint2) * 2 * 2 * 8 * 32);   // [part][k step][n tile][lane]
-    w2h = take(sizeof(uint2) * 8 * 4 * 32);       // [n tile][k step][lane]
-    w2l = take(sizeof(uint2) * 8 * 4 * 32);
+    w1f = take(sizeof(uint2) * 3 * 2 * 8 * 32);   // [part][k step][n tile][lane]
+    w2f = take(sizeof(uint2) * 3 * 8 * 4 * 32);   // [part][n tile][k step][lane]
     b2 = take(sizeof(float) * H);
     warp0 = o;
     o = 0;
@@ -90,31 +93,42 @@ struct R1Smem {
   }
 };
 
-// E1 input row of an active node, 32 BF16: [p_hi, p_lo, n_hi, n_lo, u_hi, u_lo, 1, 0 ...]
+// E1 input row of an active node, 32 BF16: the three-part splits [x0, x1, x2] of x = [p, n,
+// u_hat] (9 values each), then 1 (the bias column), then zeros.
 __device__ __forceinline__ void pack_row32(uint4* dst, float3 p, float3 nr, const float* u) {
-  dst[0] = make_uint4(bf2(p.x, p.y), bf2(p.z, bfr(p.x)), bf2(bfr(p.y), bfr(p.z)), bf2(nr.x, nr.y));
-  dst[1] = make_uint4(bf2(nr.z, bfr(nr.x)), bf2(bfr(nr.y), bfr(nr.z)), bf2(u[0], u[1]),
-                      bf2(u[2], bfr(u[0])));
-  dst[2] = make_uint4(bf2(bfr(u[1]), bfr(u[2])), bf2(1.f, 0.f), 0u, 0u);
-  dst[3] = make_uint4(0u, 0u, 0u, 0u);
+  const float x[9] = {p.x, p.y, p.z, nr.x, nr.y, nr.z, u[0], u[1], u[2]};
+  float v[32];
+#pragma unroll
+  for (int k = 0; k < 9; ++k) {
+    const float r1 = bfr(x[k]);
+    v[k] = x[k];
+    v[9 + k] = r1;
+    v[18 + k] = bfr(r1);
+  }
+  v[27] = 1.f;
+#pragma unroll
+  for (int k = 28; k < 32; ++k) v[k] = 0.f;
+#pragma unroll
+  for (int q = 0; q < 4; ++q)
+    dst[q] = make_uint4(bf2(v[8 * q], v[8 * q + 1]), bf2(v[8 * q + 2], v[8 * q + 3]),
+                        bf2(v[8 * q + 4], v[8 * q + 5]), bf2(v[8 * q + 6], v[8 * q + 7]));
 }
 
 // W1 column read by E1 input k of the 32-wide row (-1: bias, -2: zero)
 __device__ __forceinline__ int w1_col(int k) {
-  if (k < 6) return k % 3;
-  if (k < 12) return 3 + (k - 6) % 3;
-  if (k < 18) return 6 + (k - 12) % 3;
-  return k == 18 ? -1 : -2;
+  if (k < 27) return k % 9;
+  return k == 27 ? -1 : -2;
 }
 
-// Encoder of up to 16 active rows to FP32 accuracy: h1 = ReLU(W1 x + b1) (x and W1 split), the
-// E2 input split into BF16 hi + lo and E2 split, three products (hi hi, lo hi, hi lo); then
-// f = ReLU(E2 h1 + b2) folded into the per-lane running maxima with their node (lowest index
-// wins ties).
+// Encoder of up to 16 active rows to FP32 accuracy on BF16 tensor cores.  Every operand is
+// split into three BF16 parts (x = x0 + x1 + x2 to 2^-24): E1 multiplies the row of input
+// parts by the three parts of W1 (all nine products, accumulated in FP32); E2 splits
+// h1 = ReLU(E1) and W2 the same way and keeps the six products whose parts sum to at most the
+// third (the three dropped ones are below 2^-24 of the result).  Then f = ReLU(E2 h1 + b2) is
+// folded into the per-lane running maxima with their node (lowest index wins ties).
 __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], uint32_t rows,
                                            const int* node, int cnt, const uint2* sW1f,
-                                           const uint2* sW2h, const uint2* sW2l,
-                                           const float* sB2, int lane) {
+                                           const uint2* sW2f, const float* sB2, int lane) {
   const int grp = lane >> 2, tig = lane & 3;
   const bool v0 = grp < cnt, v1 = grp + 8 < cnt;
   const int n0 = v0 ? node[grp] : 0x7fffffff, n1 = v1 ? node[grp + 8] : 0x7fffffff;
@@ -123,7 +137,7 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
   for (int ks = 0; ks < 2; ++ks)
     sm100::ldmatrix_x4(rows + (uint32_t)((lane & 15) * 64 + (lane >> 4) * 16 + ks * 32), ax[ks][0],
                        ax[ks][1], ax[ks][2], ax[ks][3]);
-  uint32_t ah[4][4], al[4][4];
+  uint32_t ah[3][4][4];
 #pragma unroll
   for (int s4 = 0; s4 < 4; ++s4) {
     float h[2][4];
@@ -134,27 +148,33 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
 #pragma unroll
       for (int ks = 0; ks < 2; ++ks)
 #pragma unroll
-        for (int part = 0; part < 2; ++part) {
+        for (int part = 0; part < 3; ++part) {
           const uint2 bb = sW1f[((part * 2 + ks) * 8 + nt) * 32 + lane];
           sm100::mma_bf16_16816(acc, ax[ks], bb.x, bb.y, acc);
         }
 #pragma unroll
       for (int q = 0; q < 4; ++q) h[t][q] = relu(acc[q]);
     }
-    split2(h[0][0], h[0][1], ah[s4][0], al[s4][0]);
-    split2(h[0][2], h[0][3], ah[s4][1], al[s4][1]);
-    split2(h[1][0], h[1][1], ah[s4][2], al[s4][2]);
-    split2(h[1][2], h[1][3], ah[s4][3], al[s4][3]);
+    split3(h[0][0], h[0][1], ah[0][s4][0], ah[1][s4][0], ah[2][s4][0]);
+    split3(h[0][2], h[0][3], ah[0][s4][1], ah[1][s4][1], ah[2][s4][1]);
+    split3(h[1][0], h[1][1], ah[0][s4][2], ah[1][s4][2], ah[2][s4][2]);
+    split3(h[1][2], h[1][3], ah[0][s4][3], ah[1][s4][3], ah[2][s4][3]);
   }
 #pragma unroll
   for (int nt = 0; nt < 8; ++nt) {
     float acc[4] = {0.f, 0.f, 0.f, 0.f};
 #pragma unroll
     for (int s4 = 0; s4 < 4; ++s4) {
-      const uint2 bh = sW2h[(nt * 4 + s4) * 32 + lane], bl = sW2l[(nt * 4 + s4) * 32 + lane];
-      sm100::mma_bf16_16816(acc, ah[s4], bh.x, bh.y, acc);
-      sm100::mma_bf16_16816(acc, al[s4], bh.x, bh.y, acc);
-      sm100::mma_bf16_16816(acc, ah[s4], bl.x, bl.y, acc);
+      const uint2 b0 = sW2f[((0 * 8 + nt) * 4 + s4) * 32 + lane];
+      const uint2 b1 = sW2f[((1 * 8 + nt) * 4 + s4) * 32 + lane];
+      const uint2 b2 = sW2f[((2 * 8 + nt) * 4 + s4) * 32 + lane];
+      // smallest products first
+      sm100::mma_bf16_16816(acc, ah[2][s4], b0.x, b0.y, acc);
+      sm100::mma_bf16_16816(acc, ah[1][s4], b1.x, b1.y, acc);
+      sm100::mma_bf16_16816(acc, ah[0][s4], b2.x, b2.y, acc);
+      sm100::mma_bf16_16816(acc, ah[1][s4], b0.x, b0.y, acc);
+      sm100::mma_bf16_16816(acc, ah[0][s4], b1.x, b1.y, acc);
+      sm100::mma_bf16_16816(acc, ah[0][s4], b0.x, b0.y, acc);
     }
 #pragma unroll
     for (int e = 0; e < 2; ++e) {
@@ -176,34 +196,36 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const R1Smem L(a.nmax, a.K);
   uint2* sW1f = reinterpret_cast<uint2*>(smem + L.w1f);
-  uint2* sW2h = reinterpret_cast<uint2*>(smem + L.w2h);
-  uint2* sW2l = reinterpret_cast<uint2*>(smem + L.w2l);
+  uint2* sW2f = reinterpret_cast<uint2*>(smem + L.w2f);
   float* sB2 = reinterpret_cast<float*>(smem + L.b2);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const float* W = a.params;
-  for (int e = tid; e < 2 * 2 * 8 * 32; e += RT) {
+  // the part `part` (0..2) of the three-part BF16 split of w
+  auto wpart = [](float w, int part) {
+    float r = w;
+    for (int q = 0; q < part; ++q) r = bfr(r);
+    return __float2bfloat16_rn(r);
+  };
+  for (int e = tid; e < 3 * 2 * 8 * 32; e += RT) {
     const int l = e & 31, nt = (e >> 5) & 7, ks = (e >> 8) & 1, part = e >> 9;
     const int n = 8 * nt + (l >> 2), k0 = 16 * ks + 2 * (l & 3);
     auto wv = [&](int k) {
       const int col = w1_col(k);
       const float w = col == -1 ? W[OFF_B1 + n] : (col == -2 ? 0.f : W[OFF_W1 + n * NIN + col]);
-      const __nv_bfloat16 h = __float2bfloat16_rn(w);
-      return part == 0 ? h : __float2bfloat16_rn(w - __bfloat162float(h));
+      return wpart(w, part);
     };
     __nv_bfloat162 lo = __halves2bfloat162(wv(k0), wv(k0 + 1));
     __nv_bfloat162 hi = __halves2bfloat162(wv(k0 + 8), wv(k0 + 9));
     sW1f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
   }
-  for (int e = tid; e < 8 * 4 * 32; e += RT) {
-    const int l = e & 31, s4 = (e >> 5) & 3, nt = e >> 7;
+  for (int e = tid; e < 3 * 8 * 4 * 32; e += RT) {
+    const int l = e & 31, s4 = (e >> 5) & 3, nt = (e >> 7) & 7, part = e >> 10;
     const int n = 8 * nt + (l >> 2), k = 16 * s4 + 2 * (l & 3);
-    const float w[4] = {W[OFF_W2 + n * H + k], W[OFF_W2 + n * H + k + 1], W[OFF_W2 + n * H + k + 8],
-                        W[OFF_W2 + n * H + k + 9]};
-    uint32_t h01, l01, h89, l89;
-    split2(w[0], w[1], h01, l01);
-    split2(w[2], w[3], h89, l89);
-    sW2h[e] = make_uint2(h01, h89);
-    sW2l[e] = make_uint2(l01, l89);
+    __nv_bfloat162 lo = __halves2bfloat162(wpart(W[OFF_W2 + n * H + k], part),
+                                           wpart(W[OFF_W2 + n * H + k + 1], part));
+    __nv_bfloat162 hi = __halves2bfloat162(wpart(W[OFF_W2 + n * H + k + 8], part),
+                                           wpart(W[OFF_W2 + n * H + k + 9], part));
+    sW2f[e] = make_uint2(*reinterpret_cast<uint32_t*>(&lo), *reinterpret_cast<uint32_t*>(&hi));
   }
   for (int i = tid; i < H; i += RT) sB2[i] = W[OFF_B2 + i];
   __syncthreads();
@@ -218,7 +240,10 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
   float* sFv = reinterpret_cast<float*>(wb + L.fmv);
   int* sFi = reinterpret_cast<int*>(wb + L.fmi);
   const unsigned lt = (1u << lane) - 1u;
-  const bool use_r = uses_residual(a.mode), use_l = uses_propagation(a.mode);
+  const bool use_l = uses_propagation(a.mode);
+  // the max-pool state: recorded by the forward (FP32 batched models), else recomputed here
+  const bool rec = a.g0rec != nullptr;
+  const bool use_r = uses_residual(a.mode) && !rec;
 
   int next = 0;
   if (lane == 0) next = atomicAdd(a.ticket, 1);
@@ -318,7 +343,7 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
       while (npend > keep) {
         const int cnt = min(16, npend);
         bwd_encode(fv, fi, sPend_addr + 64u * (uint32_t)(npend - cnt), sPNode + npend - cnt, cnt,
-                   sW1f, sW2h, sW2l, sB2, lane);
+                   sW1f, sW2f, sB2, lane);
         npend -= cnt;
       }
       __syncwarp();
@@ -336,7 +361,12 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
       if (i < n && !invalid) {
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        cls = contact_classify(spo, a.K, p, nr, gap, &c);
+        if (a.mask_in) {   // mode B: the forward's caller-supplied contact (never in the band)
+          c = contact_given(a.mask_in, a.uhat_in, base + i);
+          cls = c.active ? CONTACT_FAST : CONTACT_OUT;
+        } else {
+          cls = contact_classify(spo, a.K, p, nr, gap, &c);
+        }
       }
       if (i < n && cls != CONTACT_BAND) decided(i, c, p, nr, false);
       const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
@@ -377,10 +407,18 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
       a.pad_m[pad] = m;
       a.inst_m[gi] = m;
       // dL/db_D2 sums G over passive nodes of pads with contact (no decoder in LINEAR_ONLY)
-      const bool dec = m > 0 && use_r;
+      const bool dec = m > 0 && uses_residual(a.mode);
       pr[PR_GSUM + 0] = dec ? gs0 : 0.f;
       pr[PR_GSUM + 1] = dec ? gs1 : 0.f;
       pr[PR_GSUM + 2] = dec ? gs2 : 0.f;
+    }
+    if (m > 0 && rec && uses_residual(a.mode)) {
+#pragma unroll
+      for (int h = 0; h < 2; ++h) {
+        const int c = lane + 32 * h;
+        pr[PR_G0 + c] = a.g0rec[(size_t)pad * H + c];
+        reinterpret_cast<int*>(pr)[PR_ROUTE + c] = a.g0arg[(size_t)pad * H + c];
+      }
     }
     if (m == 0 || !use_r) continue;
 
@@ -1229,9 +1267,10 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
     }
     __syncwarp();
     const uint32_t* bits = a.maskbits + a.mask_woff[pad];
-    const float* pp = a.pad_pose + 7 * (size_t)pad;
-    float Rp[3][3];
-    quat_to_mat<float>(pp + 3, Rp);
+    const bool given = a.mask_in != nullptr;   // mode B: no SDF, no pose or penetration gradient
+    const float* pp = given ? nullptr : a.pad_pose + 7 * (size_t)pad;
+    float Rp[3][3] = {};
+    if (!given) quat_to_mat<float>(pp + 3, Rp);
     float pose[MAX_K][6];
 #pragma unroll
     for (int k = 0; k < MAX_K; ++k)
@@ -1248,8 +1287,10 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
                                      a.type_pos[3 * (size_t)(o + i) + 2]);
         const float3 nr = make_float3(a.type_nrm[3 * (size_t)(o + i)], a.type_nrm[3 * (size_t)(o + i) + 1],
                                       a.type_nrm[3 * (size_t)(o + i) + 2]);
-        const NodePoseGrad pg =
-            node_pose_grad(spo, a.K, p, nr, du, Rp, pp, a.obj_pose + 7 * (size_t)env * a.K);
+        NodePoseGrad pg;
+        pg.k = -1;
+        pg.pen = 0.f;
+        if (!given) pg = node_pose_grad(spo, a.K, p, nr, du, Rp, pp, a.obj_pose + 7 * (size_t)env * a.K);
         pen = pg.pen;
 #pragma unroll
         for (int k = 0; k < MAX_K; ++k) {

@@ -211,7 +211,7 @@ __device__ __forceinline__ bool finite7(const float* a) {
   return ok && (a[3] != 0.f || a[4] != 0.f || a[5] != 0.f || a[6] != 0.f);
 }
 
-// pmax: max |p| over the pad's nodes (bounds the FP32 rounding of R p)
+// pmax: the largest Euclidean |p| over the pad's nodes (bounds the FP32 rounding of R p)
 __device__ inline void setup_pad_obj(const float* obj_pose, int type, const float* dims,
                                      const float* pad_pose, float pmax, PadObj* o) {
   df Rk[3][3], Rp[3][3];
@@ -220,7 +220,7 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
   df d[3];
 #pragma unroll
   for (int a = 0; a < 3; ++a) d[a] = two_sum(pad_pose[a], -obj_pose[a]);   // exact
-  float tmax = 0.f;
+  float tt = 0.f;
 #pragma unroll
   for (int a = 0; a < 3; ++a) {
 #pragma unroll
@@ -236,8 +236,10 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
     acc = df_add(acc, df_mul(Rk[2][a], d[2]));
     o->td[a] = acc;
     o->t[a] = df_f(acc);
-    tmax = fmaxf(tmax, fabsf(o->t[a]));
+    tt = fmaf(o->t[a], o->t[a], tt);
   }
+  // |t| (Euclidean), raised by 2^-20 relative to cover the rounding of its own evaluation
+  const float tmax = sqrtf(tt) * (1.f + 0x1p-20f);
   o->type = type;
   o->dims[0] = dims[0];
   o->dims[1] = dims[1];
@@ -245,7 +247,8 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
   // FP32 error of phi: R rounded to FP32 (u |p|), the three FMAs of q = R p + t
   // (3u (sqrt(3) |p| + |t|) per component), the SDF's squares, root and differences
   // (~2.5u |q| + u (|q| + size)) and |q| <= |p| + |t| give |phi32 - phi| < 16u (|t| + |p| + size)
-  // with u = 2^-24; tau = 3e-6 (~50u) of those magnitudes is a 3x margin (plus 1e-5 mm).
+  // with u = 2^-24 and |t|, |p| Euclidean norms; tau = 3e-6 (~50u) of those magnitudes is a 3x
+  // margin (plus 1e-5 mm).  size bounds the SDF's own magnitudes: the largest dimension.
   float size = fmaxf(fmaxf(fabsf(dims[0]), fabsf(dims[1])), fabsf(dims[2]));
   o->tau = 1e-5f + 3e-6f * (tmax + pmax + size);
 }
@@ -396,8 +399,15 @@ __device__ inline bool contact_screen(const PadObj* po, int K, float3 p, float* 
   return maybe;
 }
 
-// Exact (df32) contact decision and displacement of a node that passed the screen.
-__device__ inline NodeContact contact_refine(const PadObj* po, int K, float3 p, float3 nrm,
+// Exact (df32) contact decision and displacement of a node that passed the screen.  Built
+// inline; the ETAC_OUTLINE_REFINE build makes it an out-of-line call in every kernel (the
+// library's tests check that both builds give the same results).
+#ifdef ETAC_OUTLINE_REFINE
+#define ETAC_REFINE_LINKAGE static __device__ __noinline__
+#else
+#define ETAC_REFINE_LINKAGE __device__ inline
+#endif
+ETAC_REFINE_LINKAGE NodeContact contact_refine(const PadObj* po, int K, float3 p, float3 nrm,
                                              float phi32, SdfIn* detail = nullptr) {
   NodeContact r;
   r.phi = phi32;
@@ -549,6 +559,21 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
   r->u[1] = s * (o.R[1] * g0 + o.R[4] * g1 + o.R[7] * g2);
   r->u[2] = s * (o.R[2] * g0 + o.R[5] * g1 + o.R[8] * g2);
   return CONTACT_FAST;
+}
+
+// Contact supplied by the caller ("mode B": an external contact pipeline gives the active set
+// and u_hat, the propagation input U_a of Eq. 4, in the pad frame): no SDF is evaluated, the
+// node's penetration reads zero (phi = -0 so that -phi = +0) and no object is attached.
+__device__ __forceinline__ NodeContact contact_given(const uint8_t* mask_in, const float* uhat_in,
+                                                     long long node) {
+  NodeContact r;
+  r.k = -1;
+  r.phi = -0.f;
+  r.active = mask_in[node] != 0;
+  r.u[0] = r.active ? uhat_in[3 * node] : 0.f;
+  r.u[1] = r.active ? uhat_in[3 * node + 1] : 0.f;
+  r.u[2] = r.active ? uhat_in[3 * node + 2] : 0.f;
+  return r;
 }
 
 // Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).

@@ -30,6 +30,8 @@ struct PlainArgs {
   T* pen;                     // optional
   int* count;                 // optional
   int* status;                // device status word
+  const uint8_t* mask_in;     // mode B (both or neither): caller's active set [N] and
+  const float* uhat_in;       //   u_hat [N*3]; objects are then not read (FP32 only)
 };
 
 template <typename T>
@@ -63,6 +65,7 @@ struct TablesArgs {
   void* om_lo;
   void* dom_hi;
   void* dom_lo;
+  const int* skip;              // optional: when *skip != 0 the kernels return at once
 };
 cudaError_t launch_tables(const TablesArgs& a, int nmax, cudaStream_t s);
 
@@ -94,6 +97,11 @@ struct BatchedArgs {
   int* count;
   int* ticket;                  // work-queue counter, zero at launch
   int* status;
+  const int* skip;              // optional: when *skip != 0 the kernel returns at once
+  const uint8_t* mask_in;       // mode B: caller's active set [N] and u_hat [N*3]
+  const float* uhat_in;
+  float* g0rec;                 // optional [E*P][64]: each pad's max-pooled feature g0 and
+  int* g0arg;                   //   its lowest-index maximising node (for the reverse mode)
 };
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s);
 
@@ -135,6 +143,8 @@ struct FrontArgs {
   float4* c0m;                  // [sum I_t] by instance
   PadObj* padobj;               // [E*P][K] pad -> object transforms
   int* pad_bad;                 // [E*P] 1 when a pose or size held NaN / Inf
+  const uint8_t* mask_in;       // mode B: caller's active set [N] and u_hat [N*3]
+  const float* uhat_in;
 };
 size_t front_smem_bytes(int nmax, int K);
 cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s);
@@ -183,6 +193,9 @@ struct GemmParams {
   int use_l, use_r;
   int* status;
   unsigned long long timeout_ns;
+  // failure-path tests only: 1 + the tile whose first K block the producer withholds (its
+  // TMA loads are never issued, so the MMA issuer's bounded wait runs out); 0 = off
+  int test_withhold;
   // reverse modes
   const int* inst_m;                 // [sum I_t] active count by instance
   const float4* ws_u;                // [N] (u_hat, phi) of active nodes
@@ -230,6 +243,8 @@ struct BackwardArgs {
   float4* ws_du;               // [N]
   float* pose_part;            // [E*P*K*6]
   float* param_part;           // [grid * NPARAM]
+  const uint8_t* mask_in;      // mode B: the forward's caller-supplied active set and u_hat
+  const float* uhat_in;
 };
 size_t backward_smem_bytes(int nmax, int K);
 cudaError_t launch_backward(const BackwardArgs& a, int grid, cudaStream_t s);
@@ -309,6 +324,10 @@ struct BwdBatchedArgs {
   int alpha_parts;
   float* pose_part;
   int* ticket;
+  const uint8_t* mask_in;      // mode B: the forward's caller-supplied active set and u_hat
+  const float* uhat_in;
+  const float* g0rec;          // the forward's recorded g0 and maximising nodes [E*P][64], or
+  const int* g0arg;            //   null: R1 recomputes the active nodes' encoder
 };
 struct BwdBatchedLaunch {
   int r1_grid, r2_grid, r7_grid;

@@ -71,6 +71,13 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
   const int pad = blockIdx.x * blockDim.x + threadIdx.x;
   if (pad >= a.num_items) return;
   const int env = pad / a.P;
+  if (a.mask_in) {   // mode B: contact supplied by the caller, no object is read
+    PadObj po{};
+    po.type = OBJ_NONE;
+    for (int k = 0; k < a.K; ++k) a.padobj[(size_t)pad * a.K + k] = po;
+    a.pad_bad[pad] = 0;
+    return;
+  }
   const float* pp = a.pad_pose + 7 * (size_t)pad;
   const float pmax = a.type_pmax[a.pad_type[pad]];
   int bad = 0;
@@ -322,7 +329,12 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       if (i < n && !invalid) {
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        cls = contact_classify(spo, a.K, p, nr, gap, &c);
+        if (a.mask_in) {   // mode B: the caller's contact is final (never in the band)
+          c = contact_given(a.mask_in, a.uhat_in, base + i);
+          cls = c.active ? CONTACT_FAST : CONTACT_OUT;
+        } else {
+          cls = contact_classify(spo, a.K, p, nr, gap, &c);
+        }
       }
       if (i < n && cls != CONTACT_BAND) front_write_node(a, btrow, n, base, i, c);
       const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);

@@ -150,7 +150,8 @@ plain_forward_kernel(PlainArgs<T> a) {
   const T alpha = gp[OFF_ALPHA];
   if (tid == 0) scnt[PLAIN_THREADS + 1] = 0;   // invalid-input flag
   __syncthreads();
-  if (tid < a.K) {
+  const bool given = a.mask_in != nullptr;     // mode B: contact supplied by the caller
+  if (tid < a.K && !given) {
     const int o = env * a.K + tid;
     const T* op = a.obj_pose + 7 * (size_t)o;
     const T* pp = a.pad_pose + 7 * (size_t)pad;
@@ -198,7 +199,8 @@ plain_forward_kernel(PlainArgs<T> a) {
     if constexpr (sizeof(T) == 4) {
       float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
       float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-      NodeContact c = contact_node(spo, a.K, p, nr);
+      NodeContact c = given ? contact_given(a.mask_in, a.uhat_in, base + i)
+                            : contact_node(spo, a.K, p, nr);
       act = c.active;
       u[0] = c.u[0]; u[1] = c.u[1]; u[2] = c.u[2];
       pen = act ? -c.phi : 0.f;

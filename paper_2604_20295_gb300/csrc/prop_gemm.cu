@@ -148,11 +148,20 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       int stage = 0;
       uint32_t phase = 0;
       int issued = 0;
-      for (int tile = blockIdx.x; tile < p.num_tiles && !*s_abort; tile += gridDim.x) {
+      bool withheld = false;
+      for (int tile = blockIdx.x; tile < p.num_tiles && !*s_abort && !withheld;
+           tile += gridDim.x) {
         const GemmTile T = p.tiles[tile];
         for (int kb = 0; kb < SEG * T.nkb; ++kb) {
           if (!mbar_wait(&empty[stage], phase ^ 1u, s_abort, limit)) {
             *s_abort = 1;
+            break;
+          }
+          if (p.test_withhold == tile + 1) {
+            // failure-path test: this stage's loads are never issued and nothing more is
+            // loaded; the copies issued before it are consumed (and so have landed) before the
+            // MMA issuer reaches this stage and gives up on it
+            withheld = true;
             break;
           }
           const int seg = kb / T.nkb, kk = kb - seg * T.nkb;

@@ -15,46 +15,53 @@
 
 namespace etac {
 
+// Evaluated in FP64 and rounded once to FP32: the passive max-pool takes, per channel, the
+// first passive node of the descending f0 order, so that order must be the exact one.  Two
+// nodes of a type can hold f0 values a few 1e-6 apart (measured on the flat 16 x 16 pad), within
+// the error of an FP32 evaluation; rounding the FP64 values keeps their order (rounding is
+// monotone) unless they are within half an FP32 ulp.  Once per etac_set_model.
 __global__ void __launch_bounds__(128) tables_node_kernel(TablesArgs a) {
+  if (a.skip && *a.skip) return;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= a.total_nodes) return;
   const float* W = a.params;
-  float X[6];
+  double X[6];
 #pragma unroll
   for (int q = 0; q < 3; ++q) {
     X[q] = a.type_pos[3 * i + q];
     X[3 + q] = a.type_nrm[3 * i + q];
   }
-  float z[H], f[H];
-#pragma unroll
+  double z[H], f[H];
+#pragma unroll 4
   for (int c = 0; c < H; ++c) {
-    float acc = W[OFF_B1 + c];
+    double acc = W[OFF_B1 + c];
 #pragma unroll
-    for (int k = 0; k < 6; ++k) acc = fmaf(W[OFF_W1 + c * NIN + k], X[k], acc);
-    a.ctab[(size_t)i * H + c] = acc;
-    z[c] = fmaxf(acc, 0.f);
-  }
-#pragma unroll
-  for (int c = 0; c < H; ++c) {
-    float acc = W[OFF_B2 + c];
-#pragma unroll
-    for (int k = 0; k < H; ++k) acc = fmaf(W[OFF_W2 + c * H + k], z[k], acc);
-    f[c] = fmaxf(acc, 0.f);
-    a.f0tab[(size_t)i * H + c] = f[c];
+    for (int k = 0; k < 6; ++k) acc = fma((double)W[OFF_W1 + c * NIN + k], X[k], acc);
+    a.ctab[(size_t)i * H + c] = (float)acc;
+    z[c] = acc > 0.0 ? acc : 0.0;
   }
 #pragma unroll 1
   for (int c = 0; c < H; ++c) {
-    float acc = W[OFF_BD + c];
-#pragma unroll
-    for (int k = 0; k < H; ++k) acc = fmaf(W[OFF_WD + c * 2 * H + k], f[k], acc);
-    a.h0tab[(size_t)i * H + c] = acc;
-    if (a.h0bf16) reinterpret_cast<__nv_bfloat16*>(a.h0bf16)[(size_t)i * H + c] = __float2bfloat16_rn(acc);
+    double acc = W[OFF_B2 + c];
+#pragma unroll 8
+    for (int k = 0; k < H; ++k) acc = fma((double)W[OFF_W2 + c * H + k], z[k], acc);
+    f[c] = acc > 0.0 ? acc : 0.0;
+    a.f0tab[(size_t)i * H + c] = (float)f[c];
+  }
+#pragma unroll 1
+  for (int c = 0; c < H; ++c) {
+    double acc = W[OFF_BD + c];
+#pragma unroll 8
+    for (int k = 0; k < H; ++k) acc = fma((double)W[OFF_WD + c * 2 * H + k], f[k], acc);
+    a.h0tab[(size_t)i * H + c] = (float)acc;
+    if (a.h0bf16) reinterpret_cast<__nv_bfloat16*>(a.h0bf16)[(size_t)i * H + c] = __double2bfloat16(acc);
   }
 }
 
 // one block per (type, channel): rank of every node in descending f0 order, ties -> lower index
 __global__ void __launch_bounds__(256) tables_order_kernel(TablesArgs a) {
   extern __shared__ float col[];
+  if (a.skip && *a.skip) return;
   const int t = blockIdx.x, u = blockIdx.y;
   const int o = a.type_off[t], n = a.type_off[t + 1] - o;
   for (int i = threadIdx.x; i < n; i += blockDim.x) col[i] = a.f0tab[(size_t)(o + i) * H + u];
@@ -73,6 +80,7 @@ __global__ void __launch_bounds__(256) tables_order_kernel(TablesArgs a) {
 }
 
 __global__ void __launch_bounds__(256) tables_omega_kernel(TablesArgs a) {
+  if (a.skip && *a.skip) return;
   const float alpha = a.params[OFF_ALPHA];
   const long long total = a.omega_off[a.num_types];
   for (long long idx = blockIdx.x * (long long)blockDim.x + threadIdx.x; idx < total;

@@ -26,10 +26,11 @@ ALGO_PLAIN, ALGO_BATCHED = 0, 1
 HIDDEN = 64
 
 EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set_model",
-           "etac_step_forward", "etac_step_backward", "etac_poll_status", "etac_forward_f64",
+           "etac_step_forward", "etac_step_backward", "etac_last_step", "etac_poll_status",
+           "etac_forward_f64",
            "etac_last_error", "etac_destroy", "etac_step_forward_noalloc",
            "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
-           "etac_autotune", "etac_set_tuning", "etac_mesh_accel_build",
+           "etac_autotune", "etac_set_tuning", "etac_test_withhold_load", "etac_mesh_accel_build",
            "etac_mesh_accel_get_view", "etac_mesh_accel_destroy", "etac_mesh_gpu_create",
            "etac_mesh_sdf_query", "etac_mesh_gpu_destroy", "etac_regress")
 TAXELS = 8
@@ -52,7 +53,8 @@ class etac_model_desc(ctypes.Structure):
 
 
 class etac_step_in(ctypes.Structure):
-    _fields_ = [("obj_type", _vp), ("obj_dims", _vp), ("obj_pose", _vp), ("pad_pose", _vp)]
+    _fields_ = [("obj_type", _vp), ("obj_dims", _vp), ("obj_pose", _vp), ("pad_pose", _vp),
+                ("active_disp_in", _vp), ("active_mask_in", _vp)]
 
 
 class etac_tuning(ctypes.Structure):
@@ -102,10 +104,11 @@ _lib = None
 
 
 def lib():
-    """The loaded libetac.so (raises if it has not been built)."""
+    """The loaded libetac.so (raises if it has not been built).  ``ETAC_LIBRARY`` may name
+    another build of the same sources (a variant from ``build.build(variant=...)``)."""
     global _lib
     if _lib is None:
-        path = _build.LIB
+        path = os.environ.get("ETAC_LIBRARY") or _build.LIB
         if not os.path.exists(path):
             raise RuntimeError(f"{path} is missing: build it with paper_2604_20295_gb300.build.build()"
                                " (CUDA toolkit required); there is no CPU fallback")
@@ -121,7 +124,11 @@ def lib():
         L.etac_step_forward.restype = ctypes.c_int
         L.etac_step_forward.argtypes = [_vp, _vp, _vp, _vp]
         L.etac_step_backward.restype = ctypes.c_int
-        L.etac_step_backward.argtypes = [_vp] * 7
+        L.etac_step_backward.argtypes = [_vp, ctypes.c_uint64] + [_vp] * 6
+        L.etac_test_withhold_load.restype = ctypes.c_int
+        L.etac_test_withhold_load.argtypes = [_vp, ctypes.c_int32, ctypes.c_uint64]
+        L.etac_last_step.restype = ctypes.c_int
+        L.etac_last_step.argtypes = [_vp, ctypes.POINTER(ctypes.c_uint64)]
         L.etac_poll_status.restype = ctypes.c_int
         L.etac_poll_status.argtypes = [_vp, ctypes.POINTER(ctypes.c_int32), _vp]
         L.etac_forward_f64.restype = ctypes.c_int
@@ -142,7 +149,7 @@ def lib():
         L.etac_pose_grad_to_quat.restype = ctypes.c_int
         L.etac_pose_grad_to_quat.argtypes = [_vp, _vp, _vp, ctypes.c_int64, _vp]
         L.etac_step_forward_noalloc.restype = ctypes.c_int
-        L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp]
+        L.etac_step_forward_noalloc.argtypes = [_vp, ctypes.c_int32, _vp, _vp, _vp, _vp, _vp]
         L.etac_mesh_accel_build.restype = ctypes.c_int
         L.etac_mesh_accel_build.argtypes = [ctypes.POINTER(_vp), _vp]
         L.etac_mesh_accel_get_view.restype = ctypes.c_int
@@ -295,10 +302,23 @@ def etac_step_forward(ctx: int, sin: etac_step_in, sout: etac_step_out, stream: 
            "etac_step_forward")
 
 
+def etac_test_withhold_load(ctx: int, tile: int, wait_limit_ns: int = 0) -> None:
+    """Failure-path tests only: see include/etac.h."""
+    _check(ctx, lib().etac_test_withhold_load(ctx, tile, wait_limit_ns), "etac_test_withhold_load")
+
+
+def etac_last_step(ctx: int) -> int:
+    v = ctypes.c_uint64(0)
+    _check(ctx, lib().etac_last_step(ctx, ctypes.byref(v)), "etac_last_step")
+    return int(v.value)
+
+
 def etac_step_backward(ctx: int, grad_disp: int, grad_obj_pose: int = 0, grad_uhat: int = 0,
-                       grad_penetration: int = 0, grad_params: int = 0, stream: int = 0) -> None:
-    _check(ctx, lib().etac_step_backward(ctx, grad_disp, grad_obj_pose or None, grad_uhat or None,
-                                         grad_penetration or None, grad_params or None, stream),
+                       grad_penetration: int = 0, grad_params: int = 0, stream: int = 0,
+                       step_id: int = 0) -> None:
+    _check(ctx, lib().etac_step_backward(ctx, step_id, grad_disp, grad_obj_pose or None,
+                                         grad_uhat or None, grad_penetration or None,
+                                         grad_params or None, stream),
            "etac_step_backward")
 
 
@@ -363,11 +383,14 @@ def etac_pose_grad_to_quat(poses: int, twist_grad: int, pose_grad: int, count: i
 
 
 def etac_step_forward_noalloc(pads: etac_noalloc_pads, mode: int, params: int,
-                              sin: etac_step_in, sout: etac_step_out, stream: int = 0) -> None:
-    """Batched FP32 forward that allocates nothing (scratch in a static device array)."""
+                              sin: etac_step_in, sout: etac_step_out, device_status: int = 0,
+                              stream: int = 0) -> None:
+    """Batched FP32 forward that allocates nothing (scratch in a static device array);
+    ``device_status`` is an optional device int32 that receives the step's status word."""
     _check(None, lib().etac_step_forward_noalloc(ctypes.addressof(pads), mode, params,
                                                  ctypes.addressof(sin), ctypes.addressof(sout),
-                                                 stream), "etac_step_forward_noalloc")
+                                                 device_status or None, stream),
+           "etac_step_forward_noalloc")
 
 
 # ------------------------------------------------------------------ convenience owner
@@ -426,9 +449,14 @@ class TactileSim:
         etac_set_model(self.ctx, self.model, self.params.data_ptr(),
                        torch.cuda.current_stream(self.device).cuda_stream)
 
-    def step_in(self) -> etac_step_in:
-        return etac_step_in(self.obj_type.data_ptr(), self.obj_dims.data_ptr(),
-                            self.obj_pose.data_ptr(), self.pad_pose.data_ptr())
+    def step_in(self, given=None) -> etac_step_in:
+        """Step inputs; ``given`` = (u_hat [N, 3] float32, mask [N] uint8) device tensors
+        selects mode B (the caller's contact result; objects are not read)."""
+        if given is None:
+            return etac_step_in(self.obj_type.data_ptr(), self.obj_dims.data_ptr(),
+                                self.obj_pose.data_ptr(), self.pad_pose.data_ptr())
+        u, m = given
+        return etac_step_in(None, None, None, None, u.data_ptr(), m.data_ptr())
 
     def step_out(self, want_mask=True, want_pen=True, want_count=True, disp=None) -> etac_step_out:
         d = self.disp if disp is None else disp
@@ -456,23 +484,43 @@ class TactileSim:
                      torch.cuda.current_stream(self.device).cuda_stream)
         return taxels, attn
 
-    def step(self, want_mask=True, want_pen=True, want_count=True, disp=None):
+    def step(self, want_mask=True, want_pen=True, want_count=True, disp=None, uhat_in=None,
+             mask_in=None):
         """One forward step on the current stream.  ``disp`` (a contiguous float32 [N, 3]
         device tensor) receives the displacement instead of ``self.disp``, e.g. to alternate
-        output buffers while an earlier step's result is copied to the host."""
+        output buffers while an earlier step's result is copied to the host.  ``uhat_in``
+        ([N, 3] float32) and ``mask_in`` ([N] uint8), both device tensors, select mode B: the
+        contact result comes from the caller (kept referenced here until the next step, since
+        the reverse mode reads them again)."""
         if disp is not None and (disp.shape != self.disp.shape or disp.dtype != self.disp.dtype
                                  or not disp.is_contiguous() or disp.device != self.disp.device):
             raise EtacError(ERR_INVALID_ARG, f"disp must be a contiguous float32 "
                             f"{tuple(self.disp.shape)} tensor on {self.disp.device}")
-        etac_step_forward(self.ctx, self.step_in(),
+        given = None
+        if uhat_in is not None or mask_in is not None:
+            torch = self.torch
+            if uhat_in is None or mask_in is None:
+                raise EtacError(ERR_INVALID_ARG, "uhat_in and mask_in go together")
+            u = _device_f32(uhat_in, self.device, 3 * self.N, "uhat_in")
+            m = torch.as_tensor(mask_in).to(device=self.device, dtype=torch.uint8).contiguous()
+            if m.numel() != self.N:
+                raise EtacError(ERR_INVALID_ARG, f"mask_in has {m.numel()} values, expected {self.N}")
+            given = (u, m)
+        self._given = given
+        etac_step_forward(self.ctx, self.step_in(given),
                           self.step_out(want_mask, want_pen, want_count, disp),
                           self.torch.cuda.current_stream(self.device).cuda_stream)
         return self.disp if disp is None else disp
 
-    def backward(self, grad_disp, want=("params", "obj_pose", "uhat", "pen")):
-        """Reverse mode of the last step for dL/d(disp) = grad_disp [N,3] (device tensor).
-        Returns a dict with any of: params [P], obj_pose [E*K, 6] (dL/dt, dL/d omega),
-        uhat [N, 3], pen [N]."""
+    def last_step(self) -> int:
+        """Id of the last forward step on this context (etac_last_step)."""
+        return etac_last_step(self.ctx)
+
+    def backward(self, grad_disp, want=("params", "obj_pose", "uhat", "pen"), step_id=0):
+        """Reverse mode of a step for dL/d(disp) = grad_disp [N,3] (device tensor): the step
+        ``step_id`` (from ``last_step()``; the library refuses one that is no longer the
+        last), or the last step when 0.  Returns a dict with any of: params [P], obj_pose
+        [E*K, 6] (dL/dt, dL/d omega), uhat [N, 3], pen [N]."""
         torch = self.torch
         g = _device_f32(grad_disp, self.device, 3 * self.N, "grad_disp")
         out = {}
@@ -488,7 +536,8 @@ class TactileSim:
             out["pen"] = torch.empty(self.N, **f32)
         ptr = lambda k: out[k].data_ptr() if k in out else 0
         etac_step_backward(self.ctx, g.data_ptr(), ptr("obj_pose"), ptr("uhat"), ptr("pen"),
-                           ptr("params"), torch.cuda.current_stream(self.device).cuda_stream)
+                           ptr("params"), torch.cuda.current_stream(self.device).cuda_stream,
+                           step_id)
         self._grad_keepalive = g
         return out
 
@@ -533,27 +582,37 @@ def make_step_function():
     ``ETacStep.apply(sim, params, obj_pose)`` copies params and poses into ``sim`` (the
     model is re-set when params change), runs the forward and returns a copy of the
     displacement; backward returns dL/dparams and dL/d(obj_pose) in the 7-float pose layout.
-    All arithmetic runs in the library's kernels."""
+    The context keeps the saved state of its last forward only, so each apply records the
+    step id the library gave it; when a later apply on the same ``sim`` has replaced that
+    state (a multi-step rollout), backward first re-runs this step's forward from its saved
+    params and pose, then differentiates it under its new id.  All arithmetic runs in the
+    library's kernels."""
     import torch
+
+    def _run(sim, p, pose):
+        if getattr(sim, "params", None) is None or not torch.equal(sim.params, p):
+            m = sim.model
+            sim.set_model(p, m.mode, m.precision, m.algo)
+        sim.obj_pose.copy_(pose)
+        disp = sim.step().clone()
+        return disp, sim.last_step()
 
     class ETacStep(torch.autograd.Function):
         @staticmethod
         def forward(ctx, sim, params, obj_pose):
-            stream = torch.cuda.current_stream(sim.device).cuda_stream
             p = params.detach().to(device=sim.device, dtype=torch.float32).contiguous()
-            if getattr(sim, "params", None) is None or not torch.equal(sim.params, p):
-                m = sim.model
-                sim.set_model(p, m.mode, m.precision, m.algo)
-            sim.obj_pose.copy_(obj_pose.detach().reshape(-1))
-            disp = sim.step().clone()
-            ctx.sim = sim
-            ctx.stream = stream
+            pose = obj_pose.detach().reshape(-1).to(device=sim.device, dtype=torch.float32)
+            disp, sid = _run(sim, p, pose)
+            ctx.sim, ctx.step_id = sim, sid
+            ctx.params, ctx.pose = p.clone(), pose.clone()
             return disp
 
         @staticmethod
         def backward(ctx, grad_disp):
-            sim = ctx.sim
-            g = sim.backward(grad_disp, want=("params", "obj_pose"))
+            sim, sid = ctx.sim, ctx.step_id
+            if sim.last_step() != sid:
+                _, sid = _run(sim, ctx.params, ctx.pose)
+            g = sim.backward(grad_disp, want=("params", "obj_pose"), step_id=sid)
             pose7 = torch.empty(sim.obj_pose.numel(), dtype=torch.float32, device=sim.device)
             etac_pose_grad_to_quat(sim.obj_pose.data_ptr(), g["obj_pose"].data_ptr(),
                                    pose7.data_ptr(), sim.obj_pose.numel() // 7,

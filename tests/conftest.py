@@ -11,5 +11,3 @@ if ROOT not in sys.path:
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (sm_103a) and the built library")
     config.addinivalue_line("markers", "slow: long-running CPU test")
-    config.addinivalue_line("markers", "gpu_candidate: needs a CUDA GPU; a kernel kept out of "
-                            "the gpu suite until it has passed on a GB300 (skipped without one)")

@@ -67,7 +67,7 @@ def test_null_context_calls_fail_cleanly(lib):
     m = X.etac_model_desc(64, 0, 0, 0)
     assert lib.etac_set_model(None, ctypes.addressof(m), None, None) == 1
     assert lib.etac_step_forward(None, None, None, None) == 1
-    assert lib.etac_step_backward(None, None, None, None, None, None, None) == 1
+    assert lib.etac_step_backward(None, 0, None, None, None, None, None, None) == 1
     lib.etac_destroy(None)
 
 
@@ -106,11 +106,11 @@ def _noalloc_scratch_bytes(type_nodes, num_pads):
     """Bytes of static scratch that the no-allocation step needs, restated from the limit
     the header gives: 896 B per pad-type node, 4 B per same-type node pair and 4 B per pad
     instance, each array starting on a 256-byte boundary (plus the queue counter, the status
-    word, the Omega offsets and the per-type extents)."""
+    word, the invalid-input word, the Omega offsets and the per-type extents)."""
     up = lambda b: (b + 255) // 256 * 256
     T, tn = len(type_nodes), sum(type_nodes)
     nn2 = sum(n * n for n in type_nodes)
-    return (up(4) + up(4) + up(8 * (T + 1)) + up(4 * T) + up(4 * num_pads)
+    return (up(4) + up(4) + up(4) + up(8 * (T + 1)) + up(4 * T) + up(4 * num_pads)
             + 3 * up(4 * 64 * tn) + up(2 * 64 * tn) + up(4 * nn2))
 
 
@@ -132,7 +132,7 @@ def test_noalloc_host_checks_need_no_gpu(lib):
         assert e.value.status == X.ERR_INVALID_ARG
         return str(e.value)
 
-    assert lib.etac_step_forward_noalloc(None, 0, None, None, None, None) == X.ERR_INVALID_ARG
+    assert lib.etac_step_forward_noalloc(None, 0, None, None, None, None, None) == X.ERR_INVALID_ARG
     assert "NULL" in X.etac_last_error(0)
     assert "unknown mode" in call([256], mode=4)
     assert "bad sizes" in call([256], K=9)

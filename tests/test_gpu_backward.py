@@ -24,29 +24,28 @@ def built():
     assert torch.cuda.is_available()
 
 
-def gpu_grads(scene, theta, G, mode=X.MODE_FULL, algo=X.ALGO_BATCHED, prec=X.PREC_FP32):
+def gpu_grads(scene, theta, G, mode=X.MODE_FULL, algo=X.ALGO_BATCHED, prec=X.PREC_FP32,
+              condition=False):
+    """Forward + reverse mode on the GPU.  With ``condition`` the upstream gradient of pads
+    whose max-pool choice is a near-tie is zeroed first (tests.parity.condition_upstream);
+    the gradient used is returned as out["G"]."""
     sim = X.TactileSim(scene)
     try:
         sim.set_model(theta, mode, prec, algo)
         sim.step()
+        torch.cuda.synchronize()
+        mask = sim.mask.cpu().numpy()
+        dropped = []
+        if condition:
+            G, dropped = PT.condition_upstream(scene, theta, G, mask, mode)
         g = sim.backward(torch.as_tensor(np.asarray(G, np.float32)).cuda())
         torch.cuda.synchronize()
         out = {k: v.cpu().numpy().astype(np.float64) for k, v in g.items()}
-        out["mask"] = sim.mask.cpu().numpy()
+        out["mask"] = mask
         out["status"] = sim.poll_status()
+        out["G"], out["dropped"] = np.asarray(G, np.float64), dropped
     finally:
         sim.close()
-    return out
-
-
-def rel_err(a, b):
-    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-30))
-
-
-def layer_errors(ga, gb):
-    out = {}
-    for k, (s, n, _) in I.param_slices().items():
-        out[k] = rel_err(ga[s:s + n], gb[s:s + n])
     return out
 
 
@@ -57,31 +56,25 @@ SCENES = {
 }
 
 
-# A random-sign upstream gradient makes every parameter gradient a sum of ~N terms that
-# cancel down to ~sqrt(N) of their absolute mass, so FP32 accumulation carries a relative
-# error of about N * 2^-24 (~7e-4 for the 12k-node scenes); the bound below allows for that.
-ADJ_REL = 2e-3
-
-
 @pytest.mark.parametrize("name", sorted(SCENES))
 @pytest.mark.parametrize("mode", [X.MODE_FULL, X.MODE_LINEAR_ONLY, X.MODE_RESIDUAL_ONLY,
                                   X.MODE_PENETRATION_ONLY])
 def test_backward_matches_oracle(name, mode):
+    """Every entry of every gradient against the oracle's reverse mode (tests.parity:
+    |g - g_ref| <= 1e-4 (|g_ref| + block max))."""
     sc = SCENES[name]()
     th = I.make_params(0)
     G = np.random.default_rng(1).normal(size=(sc.total_nodes, 3))
-    got = gpu_grads(sc, th, G, mode)
+    got = gpu_grads(sc, th, G, mode, condition=True)
     assert got["status"] == 0
-    ref_f, _ = PT.oracle_forward_matching(sc, th, mode, got["mask"])
-    ref = O.backward(sc, th, G, mode=mode, mask_override=got["mask"])
-    errs = layer_errors(got["params"], ref["params"])
-    bad = {k: v for k, v in errs.items() if v > ADJ_REL and np.linalg.norm(ref["params"]) > 0}
-    print(f"{name} mode {mode}: worst layer rel err {max(errs.values()):.2e}, pose "
-          f"{rel_err(got['obj_pose'], ref['obj_pose']):.2e}, uhat {rel_err(got['uhat'], ref['uhat']):.2e}")
-    assert not bad, bad
-    assert rel_err(got["obj_pose"], ref["obj_pose"]) < ADJ_REL
-    assert rel_err(got["uhat"], ref["uhat"]) < ADJ_REL
-    assert rel_err(got["pen"], ref["pen"]) < ADJ_REL
+    npads = sc.num_envs * sc.pads_per_env
+    assert len(got["dropped"]) <= npads // 2, got["dropped"]
+    PT.oracle_forward_matching(sc, th, mode, got["mask"])
+    ref = O.backward(sc, th, got.pop("G"), mode=mode, mask_override=got["mask"])
+    ref["obj_pose"] = ref["obj_pose"].reshape(got["obj_pose"].shape)
+    worst = PT.assert_grads_close(got, ref, I.param_slices())
+    print(f"{name} mode {mode}: worst entry ratio {worst:.2e}, "
+          f"{len(got['dropped'])} of {npads} pads dropped (decisions within 1e-6 of their kinks)")
 
 
 def _f64_forward(sim, sc, th, obj_pose):
@@ -214,3 +207,65 @@ def test_fit_reduces_loss():
     hist = F.fit(sc, th0, target, iters=40, lr=3e-3)
     assert hist["loss"][-1] < 0.5 * hist["loss"][0], hist["loss"][::10]
     assert abs(hist["params"][0] - th_t[0]) < abs(th0[0] - th_t[0])
+
+
+def test_backward_refuses_a_step_that_is_not_the_last():
+    """The context keeps only its last forward's state: differentiating an earlier step id
+    fails with ETAC_ERR_STATE and enqueues nothing; the last id (and 0) work."""
+    sc = I.sphere_press_scene(8, seed=1)
+    th = I.make_params(0)
+    G = torch.as_tensor(np.random.default_rng(3).normal(size=(sc.total_nodes, 3)),
+                        dtype=torch.float32).cuda()
+    sim = X.TactileSim(sc)
+    try:
+        sim.set_model(th, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+        assert sim.last_step() == 0
+        sim.step()
+        first = sim.last_step()
+        sim.step()
+        second = sim.last_step()
+        assert second == first + 1
+        with pytest.raises(X.EtacError) as e:
+            sim.backward(G, step_id=first)
+        assert e.value.status == 2 and "not the last forward" in str(e.value)
+        a = sim.backward(G, step_id=second)
+        b = sim.backward(G)
+        for k in a:
+            assert torch.equal(a[k], b[k]), k
+    finally:
+        sim.close()
+
+
+def test_autograd_rollout_of_two_steps_on_one_context():
+    """Two ETacStep.apply calls on one context before backward (a two-step rollout): each
+    step's gradient equals that step differentiated on its own, although the second forward
+    replaced the context's saved state of the first."""
+    sc = I.grad_scene(I.OBJ_SPHERE, seed=1)
+    th = I.make_params(2)
+    rng = np.random.default_rng(4)
+    G1, G2 = (torch.as_tensor(rng.normal(size=(sc.total_nodes, 3)), dtype=torch.float32).cuda()
+              for _ in range(2))
+    pose0 = torch.as_tensor(sc.obj_pose, dtype=torch.float32).cuda().reshape(-1)
+    pose1 = pose0.clone()
+    pose1[2] -= 0.3                                   # the second step presses deeper
+    sim = X.TactileSim(sc)
+    try:
+        sim.set_model(th, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+        Step = X.make_step_function()
+        p = torch.as_tensor(th).cuda().requires_grad_(True)
+        q0 = pose0.clone().requires_grad_(True)
+        q1 = pose1.clone().requires_grad_(True)
+        d0 = Step.apply(sim, p, q0)
+        d1 = Step.apply(sim, p, q1)
+        ((d0 * G1).sum() + (d1 * G2).sum()).backward()
+        single = []
+        for pose, G in ((pose0, G1), (pose1, G2)):
+            pp = torch.as_tensor(th).cuda().requires_grad_(True)
+            qq = pose.clone().requires_grad_(True)
+            (Step.apply(sim, pp, qq) * G).sum().backward()
+            single.append((pp.grad, qq.grad))
+        torch.testing.assert_close(p.grad, single[0][0] + single[1][0], rtol=1e-5, atol=1e-6)
+        torch.testing.assert_close(q0.grad, single[0][1], rtol=0, atol=0)
+        torch.testing.assert_close(q1.grad, single[1][1], rtol=0, atol=0)
+    finally:
+        sim.close()

@@ -13,9 +13,7 @@ from paper_2604_20295_gb300 import build as B
 from paper_2604_20295_gb300 import etac as X
 from paper_2604_20295_gb300 import inputs as I
 
-# cases that have passed on a GB300 are in the gpu suite; the rest wait as candidates
-_NO_GPU = pytest.mark.skipif(not torch.cuda.is_available(), reason="needs a CUDA GPU")
-_CANDIDATE = [pytest.mark.gpu_candidate, _NO_GPU]
+pytestmark = pytest.mark.gpu
 
 REL, ABS = 1e-4, 1e-6
 
@@ -44,9 +42,7 @@ def _run(scene, disp32, rp, want_attn=True):
         sim.close()
 
 
-@pytest.mark.parametrize("scene", [pytest.param("hand", marks=pytest.mark.gpu),
-                                   pytest.param("uneven", marks=_CANDIDATE),
-                                   pytest.param("ragged", marks=pytest.mark.gpu)])
+@pytest.mark.parametrize("scene", ["hand", "uneven", "ragged"])
 def test_regressor_matches_the_oracle(scene):
     if scene == "hand":
         sc = I.hand_scene(16, seed=3).subset([0, 7, 11])
@@ -63,8 +59,6 @@ def test_regressor_matches_the_oracle(scene):
     _check(y, a, ref)
 
 
-@pytest.mark.gpu_candidate
-@_NO_GPU
 def test_regressor_on_a_gpu_step_field_and_without_attention():
     sc = I.hand_scene(8, seed=6)
     rp = I.make_regressor_params(9)
