@@ -25,6 +25,16 @@ struct etac_ctx {
   std::vector<int> pad_type;
   std::vector<long long> pad_off;
   std::vector<float> type_pmax;
+  // node blocks of every pad type for the BF16 front kernel's outside test
+  std::vector<int16_t> blk_perm;     // [sum n] nodes in block order, type t at type_off[t]
+  std::vector<float4> blk_sphere;    // [sum nb] block bounding spheres (centre, radius)
+  std::vector<int> type_boff;        // [T] first block of each type
+  int16_t* d_blk_perm = nullptr;
+  float* d_blk_pos = nullptr;        // [sum n, 3] positions and normals in block order
+  float* d_blk_nrm = nullptr;
+  float4* d_blk_sphere = nullptr;
+  int* d_type_boff = nullptr;
+  uint32_t* d_btbits = nullptr;      // nodes whose B-operand entries are nonzero (front kernel)
   // device geometry
   float* d_type_pos = nullptr;
   float* d_type_nrm = nullptr;
@@ -86,6 +96,7 @@ struct etac_ctx {
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0, num_tiles = 0, tiles_cap = 0;
+  long long mask_words = 0;   // contact-bit words of all pads (instance order)
   int gemm_gi = 64;      // instances per GEMM tile (tuned: 32 or 64)
   int gemm_order = 0;    // GEMM tile order (tuned)
   int r3_range = 0;      // decoder-reverse node range (0: from the SM count; tuned)
@@ -212,10 +223,57 @@ void free_ctx(etac_ctx* c) {
                   c->d_a3_toff, c->d_a3_tg, c->d_a3, c->d_d2part, c->d_r4part, c->d_r4bpart,
                   c->d_r5part, c->d_alpha_part, c->d_gsum_part, c->d_spart, c->d_s_toff,
                   c->d_s_nr, c->d_ws_idx, c->d_ws_u,
-                  c->d_ws_du, c->d_pose_part, c->d_param_part, c->d_g0arg};
+                  c->d_ws_du, c->d_pose_part, c->d_param_part, c->d_g0arg,
+                  c->d_blk_perm, c->d_blk_sphere, c->d_type_boff, c->d_btbits,
+                  c->d_blk_pos, c->d_blk_nrm};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
+}
+
+// Node blocks of one pad type for the front kernel's outside test: the nodes in Morton order
+// of their pad-frame positions (10 bits per axis over the type's bounding box, ties by node
+// index), 32 per block, each block with the centroid of its nodes and the largest distance
+// of a node from it, rounded up.  On a grid the blocks are 4 x 8 or 8 x 4 patches.
+void build_blocks(const float* pos, int n, int16_t* perm, std::vector<float4>& sph) {
+  double lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+  for (int i = 0; i < n; ++i)
+    for (int q = 0; q < 3; ++q) {
+      lo[q] = std::min(lo[q], (double)pos[3 * i + q]);
+      hi[q] = std::max(hi[q], (double)pos[3 * i + q]);
+    }
+  std::vector<std::pair<uint64_t, int>> key(n);
+  for (int i = 0; i < n; ++i) {
+    uint64_t code = 0;
+    uint32_t g[3];
+    for (int q = 0; q < 3; ++q) {
+      const double span = hi[q] - lo[q];
+      g[q] = span > 0 ? (uint32_t)std::min(1023.0, std::floor((pos[3 * i + q] - lo[q]) / span * 1023.0 + 0.5)) : 0u;
+    }
+    for (int bit = 9; bit >= 0; --bit)
+      for (int q = 0; q < 3; ++q) code = (code << 1) | ((g[q] >> bit) & 1u);
+    key[i] = {code, i};
+  }
+  std::sort(key.begin(), key.end());
+  for (int i = 0; i < n; ++i) perm[i] = (int16_t)key[i].second;
+  for (int b0 = 0; b0 < n; b0 += 32) {
+    const int b1 = std::min(n, b0 + 32);
+    double c[3] = {0, 0, 0};
+    for (int s = b0; s < b1; ++s)
+      for (int q = 0; q < 3; ++q) c[q] += pos[3 * perm[s] + q];
+    float cf[3];
+    for (int q = 0; q < 3; ++q) cf[q] = (float)(c[q] / (b1 - b0));
+    double r = 0.0;
+    for (int s = b0; s < b1; ++s) {
+      double d2 = 0.0;
+      for (int q = 0; q < 3; ++q) {
+        const double d = (double)pos[3 * perm[s] + q] - (double)cf[q];
+        d2 += d * d;
+      }
+      r = std::max(r, std::sqrt(d2));
+    }
+    sph.push_back(make_float4(cf[0], cf[1], cf[2], std::nextafter((float)r, INFINITY) + 1e-6f));
+  }
 }
 
 bool valid_model(const etac_model_desc* d) {
@@ -331,6 +389,7 @@ etac_status setup_instances(etac_ctx* c, cudaStream_t s) {
   if (e == cudaSuccess) e = dalloc(&c->d_inst_off, c->T + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_inst_pad, np);
   if (e == cudaSuccess) e = dalloc(&c->d_maskbits, (size_t)woff[np]);
+  c->mask_words = woff[np];
   if (e == cudaSuccess) e = dalloc(&c->d_mask_woff, (size_t)np + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_pad_m, (size_t)np);
   if (e == cudaSuccess) e = dalloc(&c->d_padobj, (size_t)np * c->K);
@@ -427,6 +486,11 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   cudaError_t e = dalloc(reinterpret_cast<char**>(&c->d_omega_bf16), 2 * (size_t)c->omega_off[c->T]);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_h0bf16), 2 * tn * etac::H);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_bt), 2 * (size_t)c->bt_total);
+  // the front kernel rewrites only the B-operand entries of nodes that are or were active,
+  // so both start at zero
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_bt, 0, 2 * (size_t)c->bt_total, s);
+  if (e == cudaSuccess) e = dalloc(&c->d_btbits, (size_t)c->mask_words);
+  if (e == cudaSuccess) e = cudaMemsetAsync(c->d_btbits, 0, sizeof(uint32_t) * c->mask_words, s);
   if (e == cudaSuccess) e = dalloc(reinterpret_cast<char**>(&c->d_negbeta), 2 * (size_t)np * etac::H);
   if (e == cudaSuccess) e = dalloc(&c->d_c0m, np);
   if (e == cudaSuccess && !c->d_g0a) e = dalloc(&c->d_g0a, (size_t)np * etac::H);
@@ -874,6 +938,13 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
       // rounded up so that the FP32 value is never below the exact norm
       c->type_pmax[t] = std::max(c->type_pmax[t], std::nextafter((float)std::sqrt(p2), INFINITY));
     }
+  c->blk_perm.resize(total_type_nodes);
+  c->type_boff.assign(c->T, 0);
+  for (int t = 0; t < c->T; ++t) {
+    c->type_boff[t] = (int)c->blk_sphere.size();
+    build_blocks(d->type_pos + 3 * (size_t)c->type_off[t], c->type_n[t],
+                 c->blk_perm.data() + c->type_off[t], c->blk_sphere);
+  }
   c->pad_type.assign(d->pad_type, d->pad_type + np);
   c->pad_off.resize(np + 1, 0);
   for (int64_t p = 0; p < np; ++p) {
@@ -914,6 +985,35 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
   if (e == cudaSuccess) e = dalloc(&c->d_omega_off, c->T + 1);
   if (e == cudaSuccess) e = dalloc(&c->d_item_pad, np);
   if (e == cudaSuccess) e = dalloc(&c->d_ticket, 4);
+  if (e == cudaSuccess) e = dalloc(&c->d_blk_perm, c->blk_perm.size());
+  if (e == cudaSuccess) e = dalloc(&c->d_blk_sphere, c->blk_sphere.size());
+  if (e == cudaSuccess) e = dalloc(&c->d_type_boff, c->T);
+  std::vector<float> bpos(3 * (size_t)total_type_nodes), bnrm(3 * (size_t)total_type_nodes);
+  for (int t = 0; t < c->T; ++t)
+    for (int s = 0; s < c->type_n[t]; ++s) {
+      const size_t src = c->type_off[t] + (size_t)c->blk_perm[c->type_off[t] + s];
+      for (int q = 0; q < 3; ++q) {
+        bpos[3 * ((size_t)c->type_off[t] + s) + q] = d->type_pos[3 * src + q];
+        bnrm[3 * ((size_t)c->type_off[t] + s) + q] = d->type_nrm[3 * src + q];
+      }
+    }
+  if (e == cudaSuccess) e = dalloc(&c->d_blk_pos, bpos.size());
+  if (e == cudaSuccess) e = dalloc(&c->d_blk_nrm, bnrm.size());
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_blk_pos, bpos.data(), sizeof(float) * bpos.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_blk_nrm, bnrm.data(), sizeof(float) * bnrm.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_blk_perm, c->blk_perm.data(), sizeof(int16_t) * c->blk_perm.size(),
+                        cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_blk_sphere, c->blk_sphere.data(),
+                        sizeof(float4) * c->blk_sphere.size(), cudaMemcpyHostToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(c->d_type_boff, c->type_boff.data(), sizeof(int) * c->T,
+                        cudaMemcpyHostToDevice, s);
   if (e == cudaSuccess)
     e = cudaMemcpyAsync(c->d_omega_off, c->omega_off.data(), sizeof(long long) * (c->T + 1),
                         cudaMemcpyHostToDevice, s);
@@ -1110,7 +1210,13 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.pad_bad = c->d_pad_bad;
       f.mask_in = c->given_mask;
       f.uhat_in = c->given_uhat;
-      if (!f.padobj || !f.pad_bad || !f.pad_gi || !c->gemm.inst_base || !c->gemm.type_woff || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
+      f.blk_perm = c->d_blk_perm;
+      f.blk_pos = c->d_blk_pos;
+      f.blk_nrm = c->d_blk_nrm;
+      f.blk_sphere = c->d_blk_sphere;
+      f.type_boff = c->d_type_boff;
+      f.btbits = c->d_btbits;
+      if (!f.blk_perm || !f.blk_pos || !f.blk_nrm || !f.blk_sphere || !f.type_boff || !f.btbits || !f.padobj || !f.pad_bad || !f.pad_gi || !c->gemm.inst_base || !c->gemm.type_woff || !f.bt || !f.bt_off || !f.pad_inst || !f.negbeta || !f.c0m || !f.maskbits ||
           !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");

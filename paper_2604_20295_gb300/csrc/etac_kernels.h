@@ -145,6 +145,12 @@ struct FrontArgs {
   int* pad_bad;                 // [E*P] 1 when a pose or size held NaN / Inf
   const uint8_t* mask_in;       // mode B: caller's active set [N] and u_hat [N*3]
   const float* uhat_in;
+  const int16_t* blk_perm;      // [sum n] nodes of each type in block order (32 per block)
+  const float* blk_pos;         // [sum n, 3] positions and normals in that order
+  const float* blk_nrm;
+  const float4* blk_sphere;     // [sum nb] block bounding spheres: centroid, radius
+  const int* type_boff;         // [T] first block of each type
+  uint32_t* btbits;             // nodes whose B-operand entries are nonzero (mask_woff layout)
 };
 size_t front_smem_bytes(int nmax, int K);
 cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s);

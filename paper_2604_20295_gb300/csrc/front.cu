@@ -41,7 +41,7 @@ constexpr unsigned FULL = 0xffffffffu;
 
 // shared weights, then one region per warp
 struct FrontSmem {
-  size_t w2f, w1f, b2, warp0, warp_bytes, po, bits, pend_a, cand, fmax, fmlane, total;
+  size_t w2f, w1f, b2, warp0, warp_bytes, po, bits, obits, pend_a, cand, fmax, fmlane, total;
   __host__ __device__ FrontSmem(int nmax, int K) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
@@ -56,6 +56,7 @@ struct FrontSmem {
     o = 0;
     po = take(sizeof(PadObj) * (size_t)K);
     bits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
+    obits = take(sizeof(uint32_t) * (size_t)((nmax + 31) / 32));
     pend_a = take(sizeof(uint4) * 2 * PEND);
     cand = take(sizeof(int16_t) * CANDCAP);
     fmax = take(sizeof(float) * H);
@@ -100,13 +101,17 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
   a.pad_bad[pad] = bad;
 }
 
-// Writes a decided node's outputs: the B-operand row entries, mask, penetration and, for an
-// active node, its displacement (= u_hat).
+// Writes a decided node's outputs: the B-operand row entries (only when the node is active
+// or was active in the previous step: the other entries are zero already), mask,
+// penetration and, for an active node, its displacement (= u_hat).
 __device__ __forceinline__ void front_write_node(const FrontArgs& a, __nv_bfloat16* btrow, int n,
-                                                 long long base, int i, const NodeContact& c) {
-  btrow[i] = __float2bfloat16_rn(c.u[0]);
-  btrow[n + i] = __float2bfloat16_rn(c.u[1]);
-  btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
+                                                 long long base, int i, const NodeContact& c,
+                                                 bool was) {
+  if (c.active || was) {
+    btrow[i] = __float2bfloat16_rn(c.u[0]);
+    btrow[n + i] = __float2bfloat16_rn(c.u[1]);
+    btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
+  }
   if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
   if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
   if (c.active) {
@@ -229,6 +234,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   unsigned char* wb = smem + L.warp0 + (size_t)warp * L.warp_bytes;
   PadObj* spo = reinterpret_cast<PadObj*>(wb + L.po);
   uint32_t* sBits = reinterpret_cast<uint32_t*>(wb + L.bits);
+  uint32_t* sOld = reinterpret_cast<uint32_t*>(wb + L.obits);   // previous B-operand bits
   uint4* sPendA = reinterpret_cast<uint4*>(wb + L.pend_a);
   const uint32_t sPendA_addr = (uint32_t)__cvta_generic_to_shared(sPendA);
   int16_t* sCand = reinterpret_cast<int16_t*>(wb + L.cand);
@@ -288,7 +294,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
         c = front_refine(spo, a.K, p, nr);
-        front_write_node(a, btrow, n, base, i, c);
+        front_write_node(a, btrow, n, base, i, c, (sOld[i >> 5] >> (i & 31)) & 1u);
         if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       }
       ncand -= cnt;
@@ -317,8 +323,62 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       __syncwarp();
     };
 
+    // the previous step's B-operand bits of this pad; this step's contact bits start clear
+    uint32_t* btb = a.btbits + a.mask_woff[pad];
+    for (int w = lane; w < nwords; w += 32) {
+      sOld[w] = btb[w];
+      sBits[w] = 0u;
+    }
+    __syncwarp();
+    // nodes in blocks of 32 (Morton order of their positions), each with a bounding sphere:
+    // the SDF is 1-Lipschitz, so a block whose centroid lies farther than its radius plus
+    // twice the FP32 error bound from every object holds passive nodes only (exactly), and
+    // its nodes skip the transform and the SDF.  Lane l tests blocks l, l + 32, ... up front,
+    // so the tests' loads overlap; the loop reads the pad's block-ordered positions,
+    // normals and node indices.
+    const int nb = (n + 31) >> 5;
+    const int16_t* bperm = a.blk_perm + o;
+    const float* bpos = a.blk_pos + 3 * (size_t)o;
+    const float* bnrm = a.blk_nrm + 3 * (size_t)o;
+    const float4* bsph = a.blk_sphere + a.type_boff[ty];
+    uint32_t cull[4] = {0u, 0u, 0u, 0u};   // blocks 32 w + l known passive (nb <= 128)
+    if (!invalid && !a.mask_in) {
+#pragma unroll
+      for (int w4 = 0; w4 < 4; ++w4) {
+        const int b = 32 * w4 + lane;
+        bool out = false;
+        if (b < nb) {
+          const float4 sc = bsph[b];
+          out = true;
+          for (int k = 0; k < a.K; ++k) {
+            const PadObj& ob = spo[k];
+            if (ob.type == OBJ_NONE) continue;
+            float3 q;
+            q.x = fmaf(ob.R[0], sc.x, fmaf(ob.R[1], sc.y, fmaf(ob.R[2], sc.z, ob.t[0])));
+            q.y = fmaf(ob.R[3], sc.x, fmaf(ob.R[4], sc.y, fmaf(ob.R[5], sc.z, ob.t[1])));
+            q.z = fmaf(ob.R[6], sc.x, fmaf(ob.R[7], sc.y, fmaf(ob.R[8], sc.z, ob.t[2])));
+            out &= sdf_f32(ob.type, ob.dims, q) >= sc.w + 2.f * ob.tau;
+          }
+        }
+        cull[w4] = __ballot_sync(FULL, out);
+      }
+    }
     for (int r0 = 0; r0 < n; r0 += 32) {
-      const int i = r0 + lane;
+      const bool live = r0 + lane < n;
+      const int i = live ? (int)bperm[r0 + lane] : 0;
+      const int b = r0 >> 5;
+      const uint32_t cw = b < 32 ? cull[0] : (b < 64 ? cull[1] : (b < 96 ? cull[2] : cull[3]));
+      if (invalid || ((cw >> (b & 31)) & 1u)) {   // warp-uniform: the whole block is passive
+        if (live) {
+          NodeContact c;
+          c.active = false;
+          c.phi = 0.f;
+          c.k = -1;
+          c.u[0] = c.u[1] = c.u[2] = 0.f;
+          front_write_node(a, btrow, n, base, i, c, (sOld[i >> 5] >> (i & 31)) & 1u);
+        }
+        continue;
+      }
       int cls = CONTACT_OUT;
       NodeContact c;
       c.active = false;
@@ -326,9 +386,10 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       c.k = -1;
       c.u[0] = c.u[1] = c.u[2] = 0.f;
       float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
-      if (i < n && !invalid) {
-        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
-        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+      if (live) {
+        const int s3 = 3 * (r0 + lane);
+        p = make_float3(bpos[s3], bpos[s3 + 1], bpos[s3 + 2]);
+        nr = make_float3(bnrm[s3], bnrm[s3 + 1], bnrm[s3 + 2]);
         if (a.mask_in) {   // mode B: the caller's contact is final (never in the band)
           c = contact_given(a.mask_in, a.uhat_in, base + i);
           cls = c.active ? CONTACT_FAST : CONTACT_OUT;
@@ -336,10 +397,11 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
           cls = contact_classify(spo, a.K, p, nr, gap, &c);
         }
       }
-      if (i < n && cls != CONTACT_BAND) front_write_node(a, btrow, n, base, i, c);
+      if (live && cls != CONTACT_BAND)
+        front_write_node(a, btrow, n, base, i, c, (sOld[i >> 5] >> (i & 31)) & 1u);
       const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
       const unsigned bC = __ballot_sync(FULL, cls == CONTACT_BAND);
-      if (lane == 0) sBits[r0 >> 5] = bA;
+      if (cls == CONTACT_FAST) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       if (cls == CONTACT_FAST && enc) {
         const int q = npend + __popc(bA & lt);
         front_pack_row(sPendA + 2 * q, p, nr, c.u);
@@ -361,7 +423,11 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
     }
     drain(0);
 
-    for (int w = lane; w < nwords; w += 32) a.maskbits[a.mask_woff[pad] + w] = sBits[w];
+    __syncwarp();
+    for (int w = lane; w < nwords; w += 32) {
+      a.maskbits[a.mask_woff[pad] + w] = sBits[w];
+      btb[w] = sBits[w];
+    }
     if (lane == 0) {
       if (a.count) a.count[pad] = m;
       a.pad_m[pad] = m;
@@ -390,7 +456,8 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
     // max-pool over the passive nodes: the first passive node in each channel's descending
     // order of f0.  First step: lane l tests ranks 0..3 of channels l and l + 32, which settles
     // most channels.  Walks are long-tailed (the top of a channel's order can sit inside the
-    // contact patch), so the rest go warp-wide: 8 channels per batch, 32 ranks per test.
+    // contact patch; on the hand workload 1 % of them pass rank 116), so the rest go
+    // warp-wide: 4 channels per batch, 256 ranks per test.
     {
       const float2* rk = a.ranked + (size_t)H * o;
       const float2* row0 = rk + (size_t)lane * n;
@@ -421,32 +488,45 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       }
       unsigned long long open = (unsigned long long)__ballot_sync(FULL, !done0) |
                                 ((unsigned long long)__ballot_sync(FULL, !done1) << 32);
+      // channels still open: the first passive node of each channel's descending order, up
+      // to WB channels at a time; lane l tests ranks q0 + 8 l .. + 7 of the node-index order
+      // (one 16-byte load per channel), so one test covers 256 ranks
+      const int16_t* ord = a.order + (size_t)H * o;
+      constexpr int WB = 4;
       while (open) {   // warp-uniform
-        int ch[8];
-        bool dn[8];
-        float bv[8];
+        int ch[WB];
+        bool dn[WB];
+        float bv[WB];
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < WB; ++c) {
           ch[c] = open ? __ffsll((long long)open) - 1 : -1;
           if (open) open &= open - 1;
           dn[c] = ch[c] < 0;
           bv[c] = 0.f;
         }
-        for (int q0 = 4; q0 < n; q0 += 32) {
-          const int r = q0 + lane;
-          float2 e[8];
+        for (int q0 = 0; q0 < n; q0 += 256) {
+          const int r = q0 + 8 * lane;
+          uint4 w[WB];
 #pragma unroll
-          for (int c = 0; c < 8; ++c)
-            e[c] = (!dn[c] && r < n) ? __ldg(rk + (size_t)ch[c] * n + r)
-                                     : make_float2(0.f, __int_as_float(0));
+          for (int c = 0; c < WB; ++c)
+            w[c] = (!dn[c] && r < n)
+                       ? __ldg(reinterpret_cast<const uint4*>(ord + (size_t)ch[c] * n + r))
+                       : make_uint4(0u, 0u, 0u, 0u);
           bool all = true;
 #pragma unroll
-          for (int c = 0; c < 8; ++c) {
-            const int idx = __float_as_int(e[c].y);
-            const bool passive = !dn[c] && r < n && !((sBits[idx >> 5] >> (idx & 31)) & 1u);
-            const unsigned bal = __ballot_sync(FULL, passive);
-            if (bal) {
-              bv[c] = __shfl_sync(FULL, e[c].x, __ffs(bal) - 1);
+          for (int c = 0; c < WB; ++c) {
+            int cand = 0x7fffffff;
+            if (!dn[c] && r < n) {
+              const uint32_t wv[4] = {w[c].x, w[c].y, w[c].z, w[c].w};
+#pragma unroll
+              for (int j = 7; j >= 0; --j) {   // the lowest passive position wins
+                const int idx = (int)((wv[j >> 1] >> (16 * (j & 1))) & 0xffffu);
+                if (!((sBits[idx >> 5] >> (idx & 31)) & 1u)) cand = 8 * lane + j;
+              }
+            }
+            const int first = __reduce_min_sync(FULL, cand);
+            if (!dn[c] && first != 0x7fffffff) {
+              bv[c] = __ldg(rk + (size_t)ch[c] * n + q0 + first).x;
               dn[c] = true;
             }
             all &= dn[c];
@@ -454,7 +534,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
           if (all) break;
         }
 #pragma unroll
-        for (int c = 0; c < 8; ++c) {
+        for (int c = 0; c < WB; ++c) {
           if (ch[c] == lane) best0 = bv[c];
           if (ch[c] == lane + 32) best1 = bv[c];
         }

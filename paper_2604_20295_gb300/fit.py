@@ -42,7 +42,7 @@ def fit(scene, theta0, target_disp, iters: int = 200, lr: float = 1e-3, betas=(0
             loss = float((diff * diff).sum()) / (3 * npas)
             losses.append(loss)
             norms.append(float(diff.norm()))
-            alphas.append(float(params[0]))
+            alphas.append(float(params.detach()[0]))
             if log_every and it % log_every == 0:
                 print(f"iter {it:4d} loss {loss:.6e} |dU| {norms[-1]:.4e} alpha {alphas[-1]:.5f}")
             if it == iters:
@@ -56,6 +56,25 @@ def fit(scene, theta0, target_disp, iters: int = 200, lr: float = 1e-3, betas=(0
         torch.cuda.synchronize()
         return {"loss": losses, "norm": norms, "alpha": alphas,
                 "params": params.detach().cpu().numpy(), "seconds": time.perf_counter() - t0}
+    finally:
+        sim.close()
+
+
+def passive_rms(scene, theta, target_disp, mode: int = X.MODE_FULL, algo: int = X.ALGO_BATCHED,
+                device: str = "cuda") -> float:
+    """Root-mean-square error (mm) of the passive nodes' displacements of the model `theta`
+    against `target_disp` on `scene` (the quantity Eq. 5 fits), one FP32 forward step."""
+    import torch
+
+    sim = X.TactileSim(scene, device=device)
+    try:
+        sim.set_model(theta, mode, X.PREC_FP32, algo)
+        disp = sim.step()
+        passive = sim.mask == 0
+        target = torch.as_tensor(np.asarray(target_disp, np.float32), device=sim.device)
+        diff = (disp - target) * passive[:, None]
+        n = max(int(passive.sum()), 1)
+        return float(torch.sqrt((diff * diff).sum() / (3 * n)))
     finally:
         sim.close()
 

@@ -80,3 +80,38 @@ def test_bf16_repeat_is_bitwise_deterministic():
     a = run(sc, I.make_params(0), algo=X.ALGO_BATCHED, precision=X.PREC_BF16)
     b = run(sc, I.make_params(0), algo=X.ALGO_BATCHED, precision=X.PREC_BF16, steps=3)
     assert np.array_equal(a["disp"], b["disp"])
+
+
+def test_bf16_step_after_other_steps_on_the_context():
+    """The BF16 front kernel rewrites only the B-operand entries of nodes that are or were
+    active.  Steps on other inputs, and an FP32 model's forward and reverse mode on the same
+    context in between, must leave the next BF16 step bitwise equal to a fresh context's."""
+    sa, sb = I.hand_scene(16, seed=31), I.hand_scene(16, seed=32)
+    th = I.make_params(0)
+    sim = X.TactileSim(sa)
+    try:
+        def load(sc):
+            for k in ("obj_type", "obj_dims", "obj_pose", "pad_pose"):
+                getattr(sim, k).copy_(torch.as_tensor(getattr(sc, k)))
+        sim.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        sim.step()
+        load(sb)
+        sim.set_model(th, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+        sim.step()
+        sim.backward(torch.ones(sb.total_nodes, 3, device="cuda"))
+        sim.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        for sc in (sb, sa):
+            load(sc)
+            sim.step()
+            torch.cuda.synchronize()
+            got = sim.disp.cpu().numpy()
+            fresh = X.TactileSim(sc)
+            try:
+                fresh.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+                fresh.step()
+                torch.cuda.synchronize()
+                assert np.array_equal(got, fresh.disp.cpu().numpy())
+            finally:
+                fresh.close()
+    finally:
+        sim.close()
