@@ -51,7 +51,7 @@ typedef enum {
 } etac_status;
 
 enum { ETAC_OBJ_NONE = 0, ETAC_OBJ_SPHERE = 1, ETAC_OBJ_BOX = 2, ETAC_OBJ_CYLINDER = 3,
-       ETAC_OBJ_CAPSULE = 4 };
+       ETAC_OBJ_CAPSULE = 4, ETAC_OBJ_MESH = 5 };
 
 /* which terms of Eq. 4 are evaluated (the ablations of Table II): both, the decay propagation
  * of Eq. 1 alone, the residual network alone, or neither (penetration only: active nodes take
@@ -110,7 +110,8 @@ typedef struct {
 typedef struct {
   const int32_t* obj_type;   /* [E*K] ETAC_OBJ_*; ETAC_OBJ_NONE slots are ignored           */
   const float* obj_dims;     /* [E*K*3] sphere (r,-,-); box half-extents (hx,hy,hz);
-                                cylinder / capsule (r, half-length along local z, -)       */
+                                cylinder / capsule (r, half-length along local z, -);
+                                mesh (index among etac_set_meshes' meshes, -, -)           */
   const float* obj_pose;     /* [E*K*7] world pose of each object                           */
   const float* pad_pose;     /* [E*P*7] world pose of each pad instance                     */
   const float* active_disp_in;     /* mode B: [N*3] u_hat of active nodes, pad frame (mm);
@@ -144,6 +145,22 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* desc, void* s
  * the batched algorithm.  Not capturable in a CUDA graph. */
 etac_status etac_set_model(etac_ctx* ctx, const etac_model_desc* desc, const float* params,
                            void* stream);
+
+/* Closed triangle meshes for ETAC_OBJ_MESH objects (ETac Sec. III-A "Overview": contact by
+ * signed distance between the nodes and object meshes).  `meshes` [count] are device meshes
+ * from etac_mesh_gpu_create (declared below); an object of type ETAC_OBJ_MESH names one by
+ * its index in obj_dims[0] (an index outside [0, count) leaves the slot empty).  The meshes
+ * are borrowed: they must outlive every step that uses them.  Replaces the previous list;
+ * count 0 clears it.  Copies a small table to the device and synchronises `stream`; not
+ * capturable.  The FP32 screen and the FP32 path for nodes certainly inside use the mesh's
+ * grid and candidate lists (Voronoi-region nearest points, pseudo-normal sign); nodes within
+ * a few um of the surface, or with two nearly equal nearest triangles, take the decision
+ * and u_hat in FP64.  The FP64 finite-difference evaluation (etac_forward_f64) treats mesh
+ * slots as empty.  Errors: ETAC_ERR_INVALID_ARG (NULL ctx, count < 0, a NULL mesh),
+ * ETAC_ERR_OOM, ETAC_ERR_CUDA. */
+typedef struct etac_mesh_gpu etac_mesh_gpu;
+etac_status etac_set_meshes(etac_ctx* ctx, const etac_mesh_gpu* const* meshes, int32_t count,
+                            void* stream);
 
 /* One forward step (ETac Sec. III-A, Eq. 1 and Eq. 4) for every pad of the batch.  Enqueues
  * work on `stream` only (no host synchronisation, no allocation), so it can be captured in
@@ -218,10 +235,13 @@ etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max,
  * tile is 128 node rows x 3 * that many columns); gemm_tile_order: 0 walks node-row tiles
  * innermost (tiles running together share a B tile in L2), 1 walks instance groups
  * innermost (they share an Omega row block); bwd_node_range: nodes per work unit of the
- * batched reverse mode's decoder stage (16..256, a multiple of 16).
+ * batched reverse mode's decoder stage (16..256, a multiple of 16); front_ctas_per_sm: CTAs
+ * per SM of the BF16 step's persistent contact / encoder kernel (1 .. the occupancy maximum,
+ * which is also what 0 selects).
  *
  * etac_autotune times every candidate on the caller's own step: the forward shapes
- * (ETAC_ALGO_BATCHED with ETAC_PREC_BF16) on `in` / `out`, and, when grad_disp is not NULL,
+ * (ETAC_ALGO_BATCHED with ETAC_PREC_BF16: GEMM tiles, then the front kernel's CTAs per SM)
+ * on `in` / `out`, and, when grad_disp is not NULL,
  * the reverse-mode node ranges on that upstream gradient [N*3].  It leaves the fastest
  * choice in effect, writes the candidates and their milliseconds per step to *result
  * (host), synchronises `stream`, and overwrites `out`.  Not to be called during stream
@@ -241,6 +261,10 @@ typedef struct {
   int32_t num_bwd;                     /* reverse-mode candidates timed */
   int32_t bwd_cand[ETAC_TUNE_MAX];     /* node range */
   float bwd_ms[ETAC_TUNE_MAX];
+  int32_t front_ctas_per_sm;
+  int32_t num_front;                   /* front-kernel candidates timed */
+  int32_t front_cand[ETAC_TUNE_MAX];   /* CTAs per SM */
+  float front_ms[ETAC_TUNE_MAX];
 } etac_tuning;
 etac_status etac_autotune(etac_ctx* ctx, const etac_step_in* in, const etac_step_out* out,
                           const float* grad_disp, etac_tuning* result, void* stream);
@@ -357,7 +381,6 @@ void etac_mesh_accel_destroy(etac_mesh_accel* accel);
  * between equally near triangles go to the lowest index.  The nearest surface point is
  * q - phi * grad.  Arrays must be 4-byte aligned and must not overlap.  Errors:
  * ETAC_ERR_INVALID_ARG (NULL, n < 0, misalignment), ETAC_ERR_CUDA (launch failure). */
-typedef struct etac_mesh_gpu etac_mesh_gpu;
 etac_status etac_mesh_gpu_create(etac_mesh_gpu** out, const etac_mesh_accel* accel, void* stream);
 etac_status etac_mesh_sdf_query(const etac_mesh_gpu* mesh, int64_t n, const float* q, float* phi,
                                 float* grad, void* stream);

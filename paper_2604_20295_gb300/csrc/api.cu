@@ -34,6 +34,9 @@ struct etac_ctx {
   float* d_blk_nrm = nullptr;
   float4* d_blk_sphere = nullptr;
   int* d_type_boff = nullptr;
+  // meshes of ETAC_OBJ_MESH objects (etac_set_meshes; the meshes themselves are borrowed)
+  etac::MeshDev* d_meshes = nullptr;
+  int num_meshes = 0, meshes_cap = 0;
   uint32_t* d_btbits = nullptr;      // nodes whose B-operand entries are nonzero (front kernel)
   // device geometry
   float* d_type_pos = nullptr;
@@ -96,6 +99,7 @@ struct etac_ctx {
   etac::GemmTile* d_tiles = nullptr;
   etac::GemmParams gemm{};
   int front_grid = 0, gemm_grid = 0, num_tiles = 0, tiles_cap = 0;
+  int front_max_per_sm = 0;   // occupancy limit of the front kernel (CTAs per SM)
   long long mask_words = 0;   // contact-bit words of all pads (instance order)
   int gemm_gi = 64;      // instances per GEMM tile (tuned: 32 or 64)
   int gemm_order = 0;    // GEMM tile order (tuned)
@@ -225,7 +229,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_s_nr, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part, c->d_g0arg,
                   c->d_blk_perm, c->d_blk_sphere, c->d_type_boff, c->d_btbits,
-                  c->d_blk_pos, c->d_blk_nrm};
+                  c->d_blk_pos, c->d_blk_nrm, c->d_meshes};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -506,6 +510,7 @@ etac_status setup_bf16(etac_ctx* c, cudaStream_t s) {
   e = etac::front_occupancy(c->nmax, c->K, &per_sm);
   if (e != cudaSuccess || per_sm < 1) return cuda_fail(c, e, "front kernel occupancy");
   c->front_grid = per_sm * c->num_sms;
+  c->front_max_per_sm = per_sm;
   c->bf16_ready = true;
   return ETAC_OK;
 }
@@ -734,6 +739,8 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   f.pad_bad = c->d_pad_bad;
   f.mask_in = c->given_mask;
   f.uhat_in = c->given_uhat;
+  f.meshes = c->d_meshes;
+  f.num_meshes = c->num_meshes;
   int ts = timing_begin(c, K_PADOBJ, s);
   ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
   timing_end(c, ts, s);
@@ -775,6 +782,7 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   b.uhat_in = c->given_uhat;
   b.g0rec = c->fwd_recorded ? c->d_g0a : nullptr;
   b.g0arg = c->fwd_recorded ? c->d_g0arg : nullptr;
+  b.has_meshes = c->num_meshes > 0;
   b.grad_disp = grad_disp;
   b.grad_uhat = grad_uhat;
   b.grad_pen = grad_pen;
@@ -1161,6 +1169,8 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.status = c->d_status;
     b.mask_in = c->given_mask;
     b.uhat_in = c->given_uhat;
+    b.meshes = c->d_meshes;
+    b.num_meshes = c->num_meshes;
     // the FP32 forward records each pad's max-pool state for the staged reverse mode
     const bool record = c->bwdb_ready && c->d_g0arg && c->model.precision == ETAC_PREC_FP32;
     b.g0rec = record ? c->d_g0a : nullptr;
@@ -1210,6 +1220,8 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.pad_bad = c->d_pad_bad;
       f.mask_in = c->given_mask;
       f.uhat_in = c->given_uhat;
+      f.meshes = c->d_meshes;
+      f.num_meshes = c->num_meshes;
       f.blk_perm = c->d_blk_perm;
       f.blk_pos = c->d_blk_pos;
       f.blk_nrm = c->d_blk_nrm;
@@ -1273,11 +1285,44 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
   a.status = c->d_status;
   a.mask_in = c->given_mask;
   a.uhat_in = c->given_uhat;
+  a.meshes = c->d_meshes;
+  a.num_meshes = c->num_meshes;
   const int ts = timing_begin(c, K_PLAIN, s);
   ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
   timing_end(c, ts, s);
   c->has_forward = true;
   ++c->step_id;
+  return ETAC_OK;
+}
+
+etac_status etac_set_meshes(etac_ctx* c, const etac_mesh_gpu* const* meshes, int32_t count,
+                            void* stream) {
+  if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
+  if (count < 0 || (count > 0 && !meshes))
+    return fail(c, ETAC_ERR_INVALID_ARG, "meshes: count %d with %s list", count,
+                meshes ? "a" : "a NULL");
+  std::vector<etac::MeshDev> h(count);
+  for (int i = 0; i < count; ++i) {
+    if (!meshes[i]) return fail(c, ETAC_ERR_INVALID_ARG, "mesh %d is NULL", i);
+    etac::mesh_dev_view(meshes[i], &h[i]);
+  }
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (count > c->meshes_cap) {
+    if (c->d_meshes) {
+      ETAC_CUDA(c, cudaStreamSynchronize(s), "mesh table");
+      cudaFree(c->d_meshes);
+      c->d_meshes = nullptr;
+      c->meshes_cap = 0;
+    }
+    cudaError_t e = dalloc(&c->d_meshes, (size_t)count);
+    if (e != cudaSuccess) return cuda_fail(c, e, "mesh table");
+    c->meshes_cap = count;
+  }
+  if (count > 0)
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_meshes, h.data(), sizeof(etac::MeshDev) * count,
+                                 cudaMemcpyHostToDevice, s), "mesh table");
+  ETAC_CUDA(c, cudaStreamSynchronize(s), "mesh table");   // h is pageable and goes away
+  c->num_meshes = count;
   return ETAC_OK;
 }
 
@@ -1355,6 +1400,8 @@ etac_status etac_step_backward(etac_ctx* c, uint64_t step_id, const float* grad_
   b.param_part = c->d_param_part;
   b.mask_in = c->given_mask;
   b.uhat_in = c->given_uhat;
+  b.meshes = c->d_meshes;
+  b.num_meshes = c->num_meshes;
   const int ts = timing_begin(c, K_BWD, s);
   ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
   timing_end(c, ts, s);
@@ -1377,6 +1424,13 @@ etac_status etac_set_tuning(etac_ctx* c, const etac_tuning* t, void* stream) {
     if (st == ETAC_OK && c->bwdb_ready) st = encode_bwd_maps(c);
     if (st != ETAC_OK) return st;
   }
+  if (c->bf16_ready && c->model.precision == ETAC_PREC_BF16) {
+    if (t->front_ctas_per_sm < 0 || t->front_ctas_per_sm > c->front_max_per_sm)
+      return fail(c, ETAC_ERR_INVALID_ARG, "front_ctas_per_sm %d outside [0, %d]",
+                  t->front_ctas_per_sm, c->front_max_per_sm);
+    c->front_grid =
+        (t->front_ctas_per_sm ? t->front_ctas_per_sm : c->front_max_per_sm) * c->num_sms;
+  }
   if (c->bwdb_ready && t->bwd_node_range) return build_r3(c, t->bwd_node_range, s);
   return ETAC_OK;
 }
@@ -1391,6 +1445,7 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
   r->gemm_inst_per_tile = c->gemm_gi;
   r->gemm_tile_order = c->gemm_order;
   r->bwd_node_range = c->r3_range;
+  r->front_ctas_per_sm = c->num_sms ? c->front_grid / c->num_sms : 0;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ETAC_CUDA(c, cudaEventCreate(&e0), "autotune events");
   ETAC_CUDA(c, cudaEventCreate(&e1), "autotune events");
@@ -1439,6 +1494,23 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
       st = etac_set_tuning(c, &t, stream);
       r->gemm_inst_per_tile = t.gemm_inst_per_tile;
       r->gemm_tile_order = t.gemm_tile_order;
+    }
+    // then the front kernel's CTAs per SM (its persistent grid) with the chosen GEMM tiles
+    int bestf = -1;
+    for (int k = 1; k <= c->front_max_per_sm && k <= ETAC_TUNE_MAX && st == ETAC_OK; ++k) {
+      t.front_ctas_per_sm = k;
+      if ((st = etac_set_tuning(c, &t, stream)) != ETAC_OK) break;
+      float ms = 0.f;
+      if ((st = timed(fwd, 2, 5, &ms)) != ETAC_OK) break;
+      r->front_cand[k - 1] = k;
+      r->front_ms[k - 1] = ms;
+      r->num_front = k;
+      if (bestf < 0 || ms < r->front_ms[bestf]) bestf = k - 1;
+    }
+    if (st == ETAC_OK && bestf >= 0) {
+      t.front_ctas_per_sm = bestf + 1;
+      st = etac_set_tuning(c, &t, stream);
+      r->front_ctas_per_sm = t.front_ctas_per_sm;
     }
   }
   if (st == ETAC_OK && grad_disp && c->bwdb_ready && etac::uses_residual(c->model.mode)) {

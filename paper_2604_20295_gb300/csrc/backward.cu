@@ -153,14 +153,16 @@ __global__ void __launch_bounds__(BB, 1) backward_kernel(BackwardArgs a) {
       const float* pp = a.pad_pose + 7 * (size_t)pad;
       const float* od = a.obj_dims + 3 * (size_t)ob;
       int type = a.obj_type[ob];
-      if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+      if (type < OBJ_NONE || type > OBJ_MESH) type = OBJ_NONE;
+      const MeshDev* mesh = nullptr;
+      if (type == OBJ_MESH && !(mesh = object_mesh(od, a.meshes, a.num_meshes))) type = OBJ_NONE;
       const bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
                       isfinite(od[2]);
       if (!ok && type != OBJ_NONE) {
         sCnt[1] = 1;
         type = OBJ_NONE;
       }
-      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
+      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid], mesh);
     }
     __syncthreads();
     const bool invalid = sCnt[1] != 0;

@@ -49,6 +49,8 @@ struct BatchedSmem {
   }
 };
 
+// MESH: the context has mesh objects (the mesh queries are compiled in)
+template <bool MESH>
 __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip && *a.skip) return;
@@ -108,14 +110,16 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       const float* pp = a.pad_pose + 7 * (size_t)pad;
       const float* od = a.obj_dims + 3 * (size_t)ob;
       int type = a.obj_type[ob];
-      if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+      if (type < OBJ_NONE || type > OBJ_MESH) type = OBJ_NONE;
+      const MeshDev* mesh = nullptr;
+      if (type == OBJ_MESH && !(mesh = object_mesh(od, a.meshes, a.num_meshes))) type = OBJ_NONE;
       bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
                 isfinite(od[2]);
       if (!ok && type != OBJ_NONE) {
         sWarp[BW] = 1;
         type = OBJ_NONE;
       }
-      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
+      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid], mesh);
     }
     __syncthreads();
     if (sWarp[BW]) {
@@ -140,7 +144,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       if (i < n) {
         float3 p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         float3 nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        c = given ? contact_given(a.mask_in, a.uhat_in, base + i) : contact_node(spo, a.K, p, nr);
+        c = given ? contact_given(a.mask_in, a.uhat_in, base + i)
+                  : contact_node<MESH>(spo, a.K, p, nr);
       }
       const unsigned bal = __ballot_sync(0xffffffffu, c.active);
       if (lane == 0) sWarp[warp] = __popc(bal);
@@ -362,8 +367,11 @@ int batched_threads() { return BT; }
 static cudaError_t configure(size_t smem) {
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel,
+    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(batched_forward_kernel<true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
@@ -374,15 +382,22 @@ cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
   size_t smem = batched_smem_bytes(nmax, K);
   cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, batched_forward_kernel, BT,
-                                                       smem);
+  int a = 0, b = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batched_forward_kernel<false>, BT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_forward_kernel<true>, BT, smem);
+  *blocks_per_sm = a < b ? a : b;   // the grid suits either instantiation
+  return e;
 }
 
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s) {
   size_t smem = batched_smem_bytes(a.nmax, a.K);
   cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  batched_forward_kernel<<<grid, BT, smem, s>>>(a);
+  if (a.num_meshes > 0)
+    batched_forward_kernel<true><<<grid, BT, smem, s>>>(a);
+  else
+    batched_forward_kernel<false><<<grid, BT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

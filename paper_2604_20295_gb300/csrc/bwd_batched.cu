@@ -192,6 +192,8 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
   }
 }
 
+// MESH: the context has mesh objects (the mesh queries are compiled in)
+template <bool MESH>
 __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const R1Smem L(a.nmax, a.K);
@@ -324,7 +326,7 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
         i = sCand[ncand - cnt + lane];
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        c = contact_refine(spo, a.K, p, nr, 0.f);
+        c = contact_refine<MESH>(spo, a.K, p, nr, 0.f);
         decided(i, c, p, nr, true);
         if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       }
@@ -365,7 +367,7 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
           c = contact_given(a.mask_in, a.uhat_in, base + i);
           cls = c.active ? CONTACT_FAST : CONTACT_OUT;
         } else {
-          cls = contact_classify(spo, a.K, p, nr, gap, &c);
+          cls = contact_classify<MESH>(spo, a.K, p, nr, gap, &c);
         }
       }
       if (i < n && cls != CONTACT_BAND) decided(i, c, p, nr, false);
@@ -1352,10 +1354,18 @@ size_t bwd_pad_smem_bytes(int nmax, int K) { return R1Smem(nmax, K).total; }
 
 cudaError_t bwd_pad_occupancy(int nmax, int K, int* blocks_per_sm) {
   const size_t smem = R1Smem(nmax, K).total;
-  cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)smem);
+  cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel<false>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(bwd_pad_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, bwd_pad_kernel, RT, smem);
+  int a = 0, b = 0;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, bwd_pad_kernel<false>, RT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, bwd_pad_kernel<true>, RT, smem);
+  *blocks_per_sm = a < b ? a : b;   // the grid suits either instantiation
+  return e;
 }
 
 // one stage of the staged reverse mode (BWD_STAGE_*), launched on stream s
@@ -1366,12 +1376,18 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       const size_t smem = R1Smem(a.nmax, a.K).total;
       static size_t configured = 0;
       if (smem > configured) {
-        cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel,
+        cudaError_t e = cudaFuncSetAttribute(bwd_pad_kernel<false>,
                                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(bwd_pad_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return e;
         configured = smem;
       }
-      bwd_pad_kernel<<<l.r1_grid, RT, smem, s>>>(a);
+      if (a.has_meshes)
+        bwd_pad_kernel<true><<<l.r1_grid, RT, smem, s>>>(a);
+      else
+        bwd_pad_kernel<false><<<l.r1_grid, RT, smem, s>>>(a);
       break;
     }
     case BWD_STAGE_GLOBAL:

@@ -43,7 +43,12 @@ __device__ inline NodePoseGrad node_pose_grad(const PadObj* spo, int K, float3 p
   const float phi = c.phi;
   const float gv = sd.g[0] * vo[0] + sd.g[1] * vo[1] + sd.g[2] * vo[2];
   float Av[3] = {sd.g[0] * gv, sd.g[1] * gv, sd.g[2] * gv};
-  if (!sd.deg && sd.hk != 0) {
+  if (sd.hk >= 3) {
+    // mesh edge (hk 3, direction e) or vertex (hk 4): phi = -(distance to the feature), whose
+    // Hessian times phi is the projector I - g g^T (- e e^T on an edge)
+    const float ev = sd.hk == 3 ? sd.e[0] * vo[0] + sd.e[1] * vo[1] + sd.e[2] * vo[2] : 0.f;
+    for (int q = 0; q < 3; ++q) Av[q] += vo[q] - sd.g[q] * gv - sd.e[q] * ev;
+  } else if (!sd.deg && sd.hk != 0) {
     float Hv[3];
     if (sd.hk == 1) {
       // spherical: (P - g g^T) vo / L, P = I except on a capsule's side (z row dropped)

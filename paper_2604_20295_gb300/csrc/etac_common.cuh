@@ -18,6 +18,8 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "mesh_common.cuh"
+
 namespace etac {
 
 constexpr int H = 64;     // hidden width
@@ -38,7 +40,7 @@ constexpr int OFF_W4 = OFF_BD + H;
 constexpr int OFF_B4 = OFF_W4 + 3 * H;
 constexpr int NPARAM = OFF_B4 + 3;
 
-enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4 };
+enum { OBJ_NONE = 0, OBJ_SPHERE = 1, OBJ_BOX = 2, OBJ_CYLINDER = 3, OBJ_CAPSULE = 4, OBJ_MESH = 5 };
 enum { MODE_FULL = 0, MODE_LINEAR_ONLY = 1, MODE_RESIDUAL_ONLY = 2, MODE_PENETRATION_ONLY = 3 };
 // which terms of Eq. 4 a mode evaluates: the propagation L (Eq. 1) and the residual R
 __host__ __device__ __forceinline__ bool uses_propagation(int mode) {
@@ -202,7 +204,17 @@ struct PadObj {
   float dims[3];
   float tau;   // |phi_fp32 - phi| < tau for every node of this pad
   int type;    // OBJ_*; OBJ_NONE when the slot is empty
+  const MeshDev* mesh;   // OBJ_MESH: the mesh (dims[0] holds its index)
 };
+
+// The mesh an OBJ_MESH object names (dims[0] = its index among the context's meshes), or
+// null when the index is not one of them.
+__device__ __forceinline__ const MeshDev* object_mesh(const float* dims, const MeshDev* meshes,
+                                                      int num_meshes) {
+  const float f = dims[0];
+  const int i = (int)f;
+  return (meshes && f >= 0.f && f < (float)num_meshes && (float)i == f) ? meshes + i : nullptr;
+}
 
 __device__ __forceinline__ bool finite7(const float* a) {
   bool ok = true;
@@ -213,7 +225,8 @@ __device__ __forceinline__ bool finite7(const float* a) {
 
 // pmax: the largest Euclidean |p| over the pad's nodes (bounds the FP32 rounding of R p)
 __device__ inline void setup_pad_obj(const float* obj_pose, int type, const float* dims,
-                                     const float* pad_pose, float pmax, PadObj* o) {
+                                     const float* pad_pose, float pmax, PadObj* o,
+                                     const MeshDev* mesh = nullptr) {
   df Rk[3][3], Rp[3][3];
   quat_to_mat_df(obj_pose + 3, Rk);
   quat_to_mat_df(pad_pose + 3, Rp);
@@ -241,6 +254,7 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
   // |t| (Euclidean), raised by 2^-20 relative to cover the rounding of its own evaluation
   const float tmax = sqrtf(tt) * (1.f + 0x1p-20f);
   o->type = type;
+  o->mesh = mesh;
   o->dims[0] = dims[0];
   o->dims[1] = dims[1];
   o->dims[2] = dims[2];
@@ -251,6 +265,13 @@ __device__ inline void setup_pad_obj(const float* obj_pose, int type, const floa
   // margin (plus 1e-5 mm).  size bounds the SDF's own magnitudes: the largest dimension.
   float size = fmaxf(fmaxf(fabsf(dims[0]), fabsf(dims[1])), fabsf(dims[2]));
   o->tau = 1e-5f + 3e-6f * (tmax + pmax + size);
+  if (type == OBJ_MESH) {
+    // the mesh query's FP32 nearest-point arithmetic (Voronoi tests, projections, a root)
+    // runs on coordinates up to |t| + |p| and mesh extents; 2e-5 (~340 u) of those
+    // magnitudes bounds it with room to spare, and nodes inside this margin (a few um) take
+    // the FP64 decision
+    o->tau = 1e-4f + 2e-5f * (tmax + pmax + (mesh ? mesh->extent : 0.f));
+  }
 }
 
 // ------------------------------------------------------------------ signed distances
@@ -276,25 +297,60 @@ __device__ __forceinline__ float sdf_f32(int type, const float* dims, float3 q) 
   return INFINITY;
 }
 
+// FP32 signed distance of object slot o at object-frame point q (screening and culling).
+// MESH = false compiles the mesh query out (kernels launched for contexts without meshes:
+// the query's out-of-line call would cost the streaming loops registers).
+template <bool MESH = true>
+__device__ __forceinline__ float sdf_obj_f32(const PadObj& o, float3 q) {
+  if (MESH && o.type == OBJ_MESH) return o.mesh ? mesh_f32(*o.mesh, q).phi : INFINITY;
+  return sdf_f32(o.type, o.dims, q);
+}
+
 // Signed distance in df32 where the node may be inside.  Returns true and sets phi < 0 when
 // q is strictly inside; g receives the outward unit normal (object frame, FP32), hk the
 // Hessian kind for the reverse mode (0 none, 1 spherical about hc, 2 radial about the z
-// axis), deg whether the normal is undefined at q.
+// axis, 3 a mesh edge of direction e, 4 a mesh vertex), deg whether the normal is undefined
+// at q.
 struct SdfIn {
   df phi;
   float g[3];
   float qf[3];
+  float e[3];
   int hk;
   bool deg;
 };
 
-__device__ inline bool sdf_inside_df(int type, const float* dims, const df q[3], SdfIn* s) {
+// A mesh object's exact decision: FP64 from the df32 point (hi + lo is exact in double).
+// Inside, the outward normal is the direction from the node to its nearest surface point.
+__device__ inline bool mesh_inside(const MeshDev& m, const df q[3], SdfIn* s) {
+  const double qd[3] = {(double)q[0].hi + (double)q[0].lo, (double)q[1].hi + (double)q[1].lo,
+                        (double)q[2].hi + (double)q[2].lo};
+  const MeshF64 r = mesh_f64(m, qd);
+  if (!(r.phi < 0.0)) return false;
+  const double d = -r.phi;
+  const float hi = (float)r.phi;
+  s->phi = {hi, (float)(r.phi - (double)hi)};
+  s->g[0] = (float)((r.c[0] - qd[0]) / d);
+  s->g[1] = (float)((r.c[1] - qd[1]) / d);
+  s->g[2] = (float)((r.c[2] - qd[2]) / d);
+  s->hk = r.feat == 1 ? 3 : (r.feat == 2 ? 4 : 0);
+  s->e[0] = (float)r.e[0];
+  s->e[1] = (float)r.e[1];
+  s->e[2] = (float)r.e[2];
+  return true;
+}
+
+template <bool MESH = true>
+__device__ inline bool sdf_inside_df(int type, const float* dims, const df q[3], SdfIn* s,
+                                     const MeshDev* mesh = nullptr) {
   s->deg = false;
   s->hk = 0;
   s->qf[0] = df_f(q[0]);
   s->qf[1] = df_f(q[1]);
   s->qf[2] = df_f(q[2]);
   s->g[0] = s->g[1] = s->g[2] = 0.f;
+  s->e[0] = s->e[1] = s->e[2] = 0.f;
+  if (MESH && type == OBJ_MESH) return mesh && mesh_inside(*mesh, q, s);
   if (type == OBJ_SPHERE) {
     df L = df_sqrt(df_add(df_add(df_sq(q[0]), df_sq(q[1])), df_sq(q[2])));
     s->phi = df_sub(L, df_from(dims[0]));
@@ -381,6 +437,7 @@ struct NodeContact {
 
 // FP32 screen: false when the node is certainly outside every object (|error| < tau);
 // *phi32 receives the FP32 minimum signed distance.
+template <bool MESH = true>
 __device__ inline bool contact_screen(const PadObj* po, int K, float3 p, float* phi32) {
   float best = INFINITY;
   bool maybe = false;
@@ -391,7 +448,7 @@ __device__ inline bool contact_screen(const PadObj* po, int K, float3 p, float* 
     q.x = fmaf(o.R[0], p.x, fmaf(o.R[1], p.y, fmaf(o.R[2], p.z, o.t[0])));
     q.y = fmaf(o.R[3], p.x, fmaf(o.R[4], p.y, fmaf(o.R[5], p.z, o.t[1])));
     q.z = fmaf(o.R[6], p.x, fmaf(o.R[7], p.y, fmaf(o.R[8], p.z, o.t[2])));
-    const float ph = sdf_f32(o.type, o.dims, q);
+    const float ph = sdf_obj_f32<MESH>(o, q);
     best = fminf(best, ph);
     maybe |= ph < o.tau;
   }
@@ -407,6 +464,7 @@ __device__ inline bool contact_screen(const PadObj* po, int K, float3 p, float* 
 #else
 #define ETAC_REFINE_LINKAGE __device__ inline
 #endif
+template <bool MESH = true>
 ETAC_REFINE_LINKAGE NodeContact contact_refine(const PadObj* po, int K, float3 p, float3 nrm,
                                              float phi32, SdfIn* detail = nullptr) {
   NodeContact r;
@@ -427,7 +485,7 @@ ETAC_REFINE_LINKAGE NodeContact contact_refine(const PadObj* po, int K, float3 p
       q[a] = df_add(acc, o.td[a]);
     }
     SdfIn s;
-    if (sdf_inside_df(o.type, o.dims, q, &s)) {
+    if (sdf_inside_df<MESH>(o.type, o.dims, q, &s, o.mesh)) {
       if (r.k < 0 || df_lt(s.phi, best)) {   // strict: ties keep the lowest object
         best = s.phi;
         bs = s;
@@ -463,6 +521,7 @@ ETAC_REFINE_LINKAGE NodeContact contact_refine(const PadObj* po, int K, float3 p
 //                 (|FP32 error| < tau <= gap / 2) and *r holds u_hat from FP32 arithmetic;
 //   CONTACT_BAND  anything else: contact_refine decides exactly.
 enum { CONTACT_OUT = 0, CONTACT_FAST = 1, CONTACT_BAND = 2 };
+template <bool MESH = true>
 __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3 nrm, float gap,
                                        NodeContact* r) {
   // pass 1: FP32 distance to every object; far-outside nodes stop here
@@ -477,7 +536,7 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
     q.x = fmaf(o.R[0], p.x, fmaf(o.R[1], p.y, fmaf(o.R[2], p.z, o.t[0])));
     q.y = fmaf(o.R[3], p.x, fmaf(o.R[4], p.y, fmaf(o.R[5], p.z, o.t[1])));
     q.z = fmaf(o.R[6], p.x, fmaf(o.R[7], p.y, fmaf(o.R[8], p.z, o.t[2])));
-    const float ph = sdf_f32(o.type, o.dims, q);
+    const float ph = sdf_obj_f32<MESH>(o, q);
     maybe |= ph < o.tau;
     if (ph < best) {
       second = best;
@@ -495,7 +554,17 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
   const float3 q = bq;
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, margin = INFINITY;
   bool deg = false;
-  if (o.type == OBJ_SPHERE || o.type == OBJ_CAPSULE) {
+  if (MESH && o.type == OBJ_MESH) {
+    // the nearest point again (pass 1 kept only the distance); a runner-up within rounding
+    // at another point leaves the choice of u_hat to the exact path
+    const MeshF32 r = mesh_f32(*o.mesh, q);
+    const float d = -r.phi;
+    if (r.tie || !(d > 0.f)) return CONTACT_BAND;
+    const float id = 1.f / d;
+    g0 = (r.c.x - q.x) * id;
+    g1 = (r.c.y - q.y) * id;
+    g2 = (r.c.z - q.z) * id;
+  } else if (o.type == OBJ_SPHERE || o.type == OBJ_CAPSULE) {
     float vz = q.z;
     if (o.type == OBJ_CAPSULE) vz = q.z - fminf(fmaxf(q.z, -o.dims[1]), o.dims[1]);
     const float L = sqrtf(q.x * q.x + q.y * q.y + vz * vz);
@@ -577,10 +646,11 @@ __device__ __forceinline__ NodeContact contact_given(const uint8_t* mask_in, con
 }
 
 // Contact at node (p, nrm) of a pad against its K object slots (po[k], empty slots skipped).
+template <bool MESH = true>
 __device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, float3 nrm,
                                            SdfIn* detail = nullptr) {
   float phi32;
-  if (!contact_screen(po, K, p, &phi32)) {
+  if (!contact_screen<MESH>(po, K, p, &phi32)) {
     NodeContact r;
     r.phi = phi32;
     r.u[0] = r.u[1] = r.u[2] = 0.f;
@@ -588,7 +658,7 @@ __device__ inline NodeContact contact_node(const PadObj* po, int K, float3 p, fl
     r.active = false;
     return r;
   }
-  return contact_refine(po, K, p, nrm, phi32, detail);
+  return contact_refine<MESH>(po, K, p, nrm, phi32, detail);
 }
 
 // ------------------------------------------------------------------ FP64 variant

@@ -7,7 +7,12 @@
 
 #include "etac_common.cuh"
 
+struct etac_mesh_gpu;
+
 namespace etac {
+
+// device view of a mesh made by etac_mesh_gpu_create (mesh_query.cu)
+void mesh_dev_view(const etac_mesh_gpu* g, MeshDev* d);
 
 // ---------------------------------------------------------------- plain algorithm
 template <typename T>
@@ -32,6 +37,8 @@ struct PlainArgs {
   int* status;                // device status word
   const uint8_t* mask_in;     // mode B (both or neither): caller's active set [N] and
   const float* uhat_in;       //   u_hat [N*3]; objects are then not read (FP32 only)
+  const MeshDev* meshes;      // the context's meshes (OBJ_MESH objects), may be null
+  int num_meshes;
 };
 
 template <typename T>
@@ -102,6 +109,8 @@ struct BatchedArgs {
   const float* uhat_in;
   float* g0rec;                 // optional [E*P][64]: each pad's max-pooled feature g0 and
   int* g0arg;                   //   its lowest-index maximising node (for the reverse mode)
+  const MeshDev* meshes;        // the context's meshes (OBJ_MESH objects), may be null
+  int num_meshes;
 };
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s);
 
@@ -151,6 +160,8 @@ struct FrontArgs {
   const float4* blk_sphere;     // [sum nb] block bounding spheres: centroid, radius
   const int* type_boff;         // [T] first block of each type
   uint32_t* btbits;             // nodes whose B-operand entries are nonzero (mask_woff layout)
+  const MeshDev* meshes;        // the context's meshes (OBJ_MESH objects), may be null
+  int num_meshes;
 };
 size_t front_smem_bytes(int nmax, int K);
 cudaError_t launch_pad_obj(const FrontArgs& a, cudaStream_t s);
@@ -251,6 +262,8 @@ struct BackwardArgs {
   float* param_part;           // [grid * NPARAM]
   const uint8_t* mask_in;      // mode B: the forward's caller-supplied active set and u_hat
   const float* uhat_in;
+  const MeshDev* meshes;       // the context's meshes (OBJ_MESH objects), may be null
+  int num_meshes;
 };
 size_t backward_smem_bytes(int nmax, int K);
 cudaError_t launch_backward(const BackwardArgs& a, int grid, cudaStream_t s);
@@ -334,6 +347,7 @@ struct BwdBatchedArgs {
   const float* uhat_in;
   const float* g0rec;          // the forward's recorded g0 and maximising nodes [E*P][64], or
   const int* g0arg;            //   null: R1 recomputes the active nodes' encoder
+  int has_meshes;               // the context has mesh objects (selects the kernels' build)
 };
 struct BwdBatchedLaunch {
   int r1_grid, r2_grid, r7_grid;

@@ -87,7 +87,9 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
     const float* op = a.obj_pose + 7 * (size_t)ob;
     const float* od = a.obj_dims + 3 * (size_t)ob;
     int type = a.obj_type[ob];
-    if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+    if (type < OBJ_NONE || type > OBJ_MESH) type = OBJ_NONE;
+    const MeshDev* mesh = nullptr;
+    if (type == OBJ_MESH && !(mesh = object_mesh(od, a.meshes, a.num_meshes))) type = OBJ_NONE;
     const bool ok = finite7(op) && finite7(pp) && isfinite(od[0]) && isfinite(od[1]) &&
                     isfinite(od[2]);
     if (!ok && type != OBJ_NONE) {
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
       type = OBJ_NONE;
     }
     PadObj po;
-    setup_pad_obj(op, type, od, pp, pmax, &po);
+    setup_pad_obj(op, type, od, pp, pmax, &po, mesh);
     a.padobj[(size_t)pad * a.K + k] = po;
   }
   a.pad_bad[pad] = bad;
@@ -135,8 +137,9 @@ __device__ __forceinline__ float bf_rest(float x) {   // x - BF16(x), itself rou
 }
 // The exact (df32) decision of an undecided node, kept out of line: it runs for a thin band of
 // nodes only, and inlined its code crowds the instruction cache of the streaming loop.
+template <bool MESH>
 __device__ __noinline__ NodeContact front_refine(const PadObj* po, int K, float3 p, float3 nrm) {
-  return contact_refine(po, K, p, nrm, 0.f);
+  return contact_refine<MESH>(po, K, p, nrm, 0.f);
 }
 
 __device__ __forceinline__ void front_pack_row(uint4* dst, float3 p, float3 nr, const float* u) {
@@ -196,6 +199,9 @@ __device__ __forceinline__ void front_encode(float (&fm)[8][2], uint32_t rows, i
   }
 }
 
+// MESH: the context has mesh objects (the FP32 mesh query is compiled in; without meshes it
+// is left out, so its out-of-line call costs the streaming loop no registers)
+template <bool MESH>
 __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const FrontSmem L(a.nmax, a.K);
@@ -293,7 +299,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
         i = sCand[ncand - cnt + lane];
         p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
         nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        c = front_refine(spo, a.K, p, nr);
+        c = front_refine<MESH>(spo, a.K, p, nr);
         front_write_node(a, btrow, n, base, i, c, (sOld[i >> 5] >> (i & 31)) & 1u);
         if (c.active) atomicOr(&sBits[i >> 5], 1u << (i & 31));
       }
@@ -357,7 +363,10 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
             q.x = fmaf(ob.R[0], sc.x, fmaf(ob.R[1], sc.y, fmaf(ob.R[2], sc.z, ob.t[0])));
             q.y = fmaf(ob.R[3], sc.x, fmaf(ob.R[4], sc.y, fmaf(ob.R[5], sc.z, ob.t[1])));
             q.z = fmaf(ob.R[6], sc.x, fmaf(ob.R[7], sc.y, fmaf(ob.R[8], sc.z, ob.t[2])));
-            out &= sdf_f32(ob.type, ob.dims, q) >= sc.w + 2.f * ob.tau;
+            // a mesh reports +inf (outside, distance not computed) in cells known to be
+            // outside: that proves nothing about the rest of the block
+            const float ph = sdf_obj_f32<MESH>(ob, q);
+            out &= ph != INFINITY && ph >= sc.w + 2.f * ob.tau;
           }
         }
         cull[w4] = __ballot_sync(FULL, out);
@@ -394,7 +403,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
           c = contact_given(a.mask_in, a.uhat_in, base + i);
           cls = c.active ? CONTACT_FAST : CONTACT_OUT;
         } else {
-          cls = contact_classify(spo, a.K, p, nr, gap, &c);
+          cls = contact_classify<MESH>(spo, a.K, p, nr, gap, &c);
         }
       }
       if (live && cls != CONTACT_BAND)
@@ -711,24 +720,34 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
 size_t front_smem_bytes(int nmax, int K) { return FrontSmem(nmax, K).total; }
 
 cudaError_t front_occupancy(int nmax, int K, int* blocks_per_sm) {
+  // both instantiations share the launch bounds (64 registers) and the shared memory
   const size_t smem = front_smem_bytes(nmax, K);
-  cudaError_t e = cudaFuncSetAttribute(front_contact_kernel,
+  cudaError_t e = cudaFuncSetAttribute(front_contact_kernel<false>,
                                        cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(front_contact_kernel<true>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, front_contact_kernel, FT,
-                                                       smem);
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, front_contact_kernel<false>,
+                                                       FT, smem);
 }
 
 cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s) {
   const size_t smem = front_smem_bytes(a.nmax, a.K);
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(front_contact_kernel,
+    cudaError_t e = cudaFuncSetAttribute(front_contact_kernel<false>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e == cudaSuccess)
+      e = cudaFuncSetAttribute(front_contact_kernel<true>,
+                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
-  front_contact_kernel<<<grid, FT, smem, s>>>(a);
+  if (a.num_meshes > 0)
+    front_contact_kernel<true><<<grid, FT, smem, s>>>(a);
+  else
+    front_contact_kernel<false><<<grid, FT, smem, s>>>(a);
   return cudaGetLastError();
 }
 

@@ -26,6 +26,7 @@
 #include <string>
 
 #include "etac.h"
+#include "mesh_common.cuh"
 
 namespace etac {
 void set_context_free_error(const std::string& msg);   // api.cu: read by etac_last_error(NULL)
@@ -56,56 +57,7 @@ struct MeshArgs {
   const float4* __restrict__ pseudo;
 };
 
-// feature codes: -1 face, 0..2 edges ab, bc, ca, 3..5 vertices a, b, c (pseudo-normal order)
-__device__ __forceinline__ float nearest_on_triangle(float3 p, float3 a, float3 b, float3 c,
-                                                     float3* cp, int* feat) {
-  const float3 ab = make_float3(b.x - a.x, b.y - a.y, b.z - a.z);
-  const float3 ac = make_float3(c.x - a.x, c.y - a.y, c.z - a.z);
-  const float3 ap = make_float3(p.x - a.x, p.y - a.y, p.z - a.z);
-  const float d1 = ab.x * ap.x + ab.y * ap.y + ab.z * ap.z;
-  const float d2 = ac.x * ap.x + ac.y * ap.y + ac.z * ap.z;
-  float3 q;
-  int f;
-  if (d1 <= 0.f && d2 <= 0.f) {
-    q = a; f = 3;
-  } else {
-    const float3 bp = make_float3(p.x - b.x, p.y - b.y, p.z - b.z);
-    const float d3 = ab.x * bp.x + ab.y * bp.y + ab.z * bp.z;
-    const float d4 = ac.x * bp.x + ac.y * bp.y + ac.z * bp.z;
-    const float vc = d1 * d4 - d3 * d2;
-    if (d3 >= 0.f && d4 <= d3) {
-      q = b; f = 4;
-    } else if (vc <= 0.f && d1 >= 0.f && d3 <= 0.f) {
-      const float v = d1 / (d1 - d3);
-      q = make_float3(a.x + v * ab.x, a.y + v * ab.y, a.z + v * ab.z); f = 0;
-    } else {
-      const float3 cq = make_float3(p.x - c.x, p.y - c.y, p.z - c.z);
-      const float d5 = ab.x * cq.x + ab.y * cq.y + ab.z * cq.z;
-      const float d6 = ac.x * cq.x + ac.y * cq.y + ac.z * cq.z;
-      const float vb = d5 * d2 - d1 * d6;
-      const float va = d3 * d6 - d5 * d4;
-      if (d6 >= 0.f && d5 <= d6) {
-        q = c; f = 5;
-      } else if (vb <= 0.f && d2 >= 0.f && d6 <= 0.f) {
-        const float w = d2 / (d2 - d6);
-        q = make_float3(a.x + w * ac.x, a.y + w * ac.y, a.z + w * ac.z); f = 2;
-      } else if (va <= 0.f && (d4 - d3) >= 0.f && (d5 - d6) >= 0.f) {
-        const float w = (d4 - d3) / ((d4 - d3) + (d5 - d6));
-        q = make_float3(b.x + w * (c.x - b.x), b.y + w * (c.y - b.y), b.z + w * (c.z - b.z)); f = 1;
-      } else {
-        const float s = 1.f / (va + vb + vc);
-        const float v = vb * s, w = vc * s;
-        q = make_float3(a.x + v * ab.x + w * ac.x, a.y + v * ab.y + w * ac.y,
-                        a.z + v * ab.z + w * ac.z);
-        f = -1;
-      }
-    }
-  }
-  *cp = q;
-  *feat = f;
-  const float dx = p.x - q.x, dy = p.y - q.y, dz = p.z - q.z;
-  return dx * dx + dy * dy + dz * dz;
-}
+using etac::nearest_on_triangle;   // mesh_common.cuh: Voronoi-region nearest point
 
 __global__ void __launch_bounds__(256) mesh_sdf_kernel(MeshArgs m, int64_t n,
                                                        const float* __restrict__ q,
@@ -181,6 +133,29 @@ void free_mesh(etac_mesh_gpu* g) {
 }
 
 }  // namespace
+
+namespace etac {
+// device view of a mesh for the contact step (etac_set_meshes)
+void mesh_dev_view(const etac_mesh_gpu* g, MeshDev* d) {
+  d->ox = g->origin[0];
+  d->oy = g->origin[1];
+  d->oz = g->origin[2];
+  d->cell = g->cell;
+  d->nx = g->dims[0];
+  d->ny = g->dims[1];
+  d->nz = g->dims[2];
+  float ext = 0.f;
+  for (int a = 0; a < 3; ++a)
+    ext = std::max(ext, std::max(std::fabs(g->origin[a]),
+                                 std::fabs(g->origin[a] + g->cell * (float)g->dims[a])));
+  d->extent = ext * 1.7320508f;   // the bounding box corner's distance bounds |x| (sqrt 3)
+  d->cell_start = g->cell_start;
+  d->cell_kind = g->cell_kind;
+  d->cand = g->cand;
+  d->tri = g->tri;
+  d->pseudo = g->pseudo;
+}
+}  // namespace etac
 
 extern "C" {
 

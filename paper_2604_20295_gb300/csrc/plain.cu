@@ -162,14 +162,17 @@ plain_forward_kernel(PlainArgs<T> a) {
     for (int i = 0; i < 3; ++i) ok &= isfinite(od[i]);
     ok &= (op[3] != T(0) || op[4] != T(0) || op[5] != T(0) || op[6] != T(0));
     ok &= (pp[3] != T(0) || pp[4] != T(0) || pp[5] != T(0) || pp[6] != T(0));
-    if (type < OBJ_NONE || type > OBJ_CAPSULE) type = OBJ_NONE;
+    if (type < OBJ_NONE || type > OBJ_MESH) type = OBJ_NONE;
     if (!ok && type != OBJ_NONE) {
       scnt[PLAIN_THREADS + 1] = 1;
       type = OBJ_NONE;
     }
     if constexpr (sizeof(T) == 4) {
-      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid]);
+      const MeshDev* mesh = nullptr;
+      if (type == OBJ_MESH && !(mesh = object_mesh(od, a.meshes, a.num_meshes))) type = OBJ_NONE;
+      setup_pad_obj(op, type, od, pp, a.type_pmax[ty], &spo[tid], mesh);
     } else {
+      if (type == OBJ_MESH) type = OBJ_NONE;   // the FP64 check covers the primitives
       setup_pad_obj64(op, type, od, pp, &spo[tid]);
     }
   }

@@ -32,7 +32,7 @@ EXPORTS = ("etac_param_count", "etac_total_nodes", "etac_create_pads", "etac_set
            "etac_enable_timing", "etac_kernel_times", "etac_pose_grad_to_quat",
            "etac_autotune", "etac_set_tuning", "etac_test_withhold_load", "etac_mesh_accel_build",
            "etac_mesh_accel_get_view", "etac_mesh_accel_destroy", "etac_mesh_gpu_create",
-           "etac_mesh_sdf_query", "etac_mesh_gpu_destroy", "etac_regress")
+           "etac_mesh_sdf_query", "etac_mesh_gpu_destroy", "etac_regress", "etac_set_meshes")
 TAXELS = 8
 REGRESSOR_PARAMS = 174729
 CELL_OUTSIDE, CELL_INSIDE, CELL_SURFACE = 0, 1, 2
@@ -62,7 +62,9 @@ class etac_tuning(ctypes.Structure):
                 ("bwd_node_range", ctypes.c_int32), ("num_fwd", ctypes.c_int32),
                 ("fwd_cand", (ctypes.c_int32 * 2) * 8), ("fwd_ms", ctypes.c_float * 8),
                 ("num_bwd", ctypes.c_int32), ("bwd_cand", ctypes.c_int32 * 8),
-                ("bwd_ms", ctypes.c_float * 8)]
+                ("bwd_ms", ctypes.c_float * 8), ("front_ctas_per_sm", ctypes.c_int32),
+                ("num_front", ctypes.c_int32), ("front_cand", ctypes.c_int32 * 8),
+                ("front_ms", ctypes.c_float * 8)]
 
 
 class etac_step_out(ctypes.Structure):
@@ -164,6 +166,8 @@ def lib():
         L.etac_mesh_gpu_destroy.argtypes = [_vp]
         L.etac_regress.restype = ctypes.c_int
         L.etac_regress.argtypes = [_vp] * 6
+        L.etac_set_meshes.restype = ctypes.c_int
+        L.etac_set_meshes.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
         _lib = L
     return _lib
 
@@ -249,6 +253,13 @@ def etac_mesh_gpu_create(accel: int, stream: int = 0) -> int:
 def etac_mesh_sdf_query(mesh: int, n: int, q: int, phi: int, grad: int = 0, stream: int = 0) -> None:
     _check(None, lib().etac_mesh_sdf_query(mesh, n, q, phi, grad or None, stream),
            "etac_mesh_sdf_query")
+
+
+def etac_set_meshes(ctx: int, meshes, stream: int = 0) -> None:
+    """Meshes (device mesh handles) of the context's ETAC_OBJ_MESH objects, by index."""
+    arr = (_vp * max(len(meshes), 1))(*[int(m) for m in meshes])
+    _check(ctx, lib().etac_set_meshes(ctx, arr if len(meshes) else None, len(meshes), stream),
+           "etac_set_meshes")
 
 
 def etac_mesh_gpu_destroy(mesh: int) -> None:
@@ -363,7 +374,9 @@ def tuning_dict(t: etac_tuning) -> dict:
     return {"gemm_inst_per_tile": t.gemm_inst_per_tile, "gemm_tile_order": t.gemm_tile_order,
             "bwd_node_range": t.bwd_node_range,
             "fwd": [(t.fwd_cand[k][0], t.fwd_cand[k][1], round(t.fwd_ms[k], 4)) for k in range(t.num_fwd)],
-            "bwd": [(t.bwd_cand[k], round(t.bwd_ms[k], 4)) for k in range(t.num_bwd)]}
+            "bwd": [(t.bwd_cand[k], round(t.bwd_ms[k], 4)) for k in range(t.num_bwd)],
+            "front_ctas_per_sm": t.front_ctas_per_sm,
+            "front": [(t.front_cand[k], round(t.front_ms[k], 4)) for k in range(t.num_front)]}
 
 
 def etac_kernel_times(ctx: int) -> dict:
@@ -448,6 +461,16 @@ class TactileSim:
         self.model = model
         etac_set_model(self.ctx, self.model, self.params.data_ptr(),
                        torch.cuda.current_stream(self.device).cuda_stream)
+
+    def set_meshes(self, meshes=None):
+        """Builds device meshes for the scene's meshes (``scene.meshes``, or the given list of
+        ``MeshSDF``) and hands them to the context for OBJ_MESH objects; they stay owned by
+        this object."""
+        if meshes is None:
+            meshes = [MeshSDF(m.verts, m.tris) for m in self.scene.meshes]
+        self._meshes = list(meshes)
+        etac_set_meshes(self.ctx, [m.handle for m in self._meshes],
+                        self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def step_in(self, given=None) -> etac_step_in:
         """Step inputs; ``given`` = (u_hat [N, 3] float32, mask [N] uint8) device tensors
@@ -541,19 +564,52 @@ class TactileSim:
         self._grad_keepalive = g
         return out
 
-    def autotune(self, grad_disp=None) -> dict:
+    def tuning_key(self, with_reverse: bool) -> str:
+        """What a tuning choice depends on: the GPU (name, SM count), the pad-type histogram
+        (node count and instances of each type), objects per env and the model's mode,
+        precision and algorithm."""
+        props = self.torch.cuda.get_device_properties(self.device)
+        sc = self.scene
+        inst = np.bincount(np.asarray(sc.pad_type), minlength=len(sc.types))
+        hist = ",".join(f"{int(n)}x{int(k)}" for n, k in zip(sc.type_num_nodes, inst))
+        m = self.model
+        return (f"{props.name}|sms={props.multi_processor_count}|types={hist}|K={sc.max_objects}|"
+                f"mode={m.mode}|prec={m.precision}|algo={m.algo}|reverse={int(with_reverse)}")
+
+    def autotune(self, grad_disp=None, cache=None) -> dict:
         """Times the tile / block shape candidates on this scene's step (and, given an upstream
-        gradient, the reverse mode's node ranges) and keeps the fastest."""
+        gradient, the reverse mode's node ranges) and keeps the fastest.  ``cache`` (a JSON
+        file path) stores each choice under ``tuning_key``; a later call with the same key
+        applies the stored choice without timing (the result then has "cached": True)."""
+        import json
+        key = self.tuning_key(grad_disp is not None)
+        table = {}
+        if cache is not None and os.path.exists(cache):
+            with open(cache) as f:
+                table = json.load(f)
+            if key in table:
+                d = table[key]
+                self.set_tuning(d["gemm_inst_per_tile"], d["gemm_tile_order"], d["bwd_node_range"],
+                                d.get("front_ctas_per_sm", 0))
+                return dict(d, cached=True)
         g = None if grad_disp is None else _device_f32(grad_disp, self.device, 3 * self.N,
                                                        "grad_disp")
         t = etac_autotune(self.ctx, self.step_in(), self.step_out(),
                           0 if g is None else g.data_ptr(),
                           self.torch.cuda.current_stream(self.device).cuda_stream)
-        return tuning_dict(t)
+        d = tuning_dict(t)
+        if cache is not None:
+            table[key] = d
+            tmp = f"{cache}.tmp{os.getpid()}"
+            with open(tmp, "w") as f:
+                json.dump(table, f, indent=1)
+            os.replace(tmp, cache)
+        return dict(d, cached=False)
 
-    def set_tuning(self, inst_per_tile=64, tile_order=0, bwd_node_range=0):
+    def set_tuning(self, inst_per_tile=64, tile_order=0, bwd_node_range=0, front_ctas_per_sm=0):
         t = etac_tuning()
         t.gemm_inst_per_tile, t.gemm_tile_order, t.bwd_node_range = inst_per_tile, tile_order, bwd_node_range
+        t.front_ctas_per_sm = front_ctas_per_sm
         etac_set_tuning(self.ctx, t, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def poll_status(self) -> int:

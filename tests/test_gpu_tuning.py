@@ -100,6 +100,8 @@ def test_autotune_picks_a_timed_candidate_and_stays_correct():
         assert (t["gemm_inst_per_tile"], t["gemm_tile_order"]) == best[:2]
         assert t["bwd_node_range"] == min(t["bwd"], key=lambda c: c[1])[0]
         assert all(ms > 0 for _, _, ms in t["fwd"]) and all(ms > 0 for _, ms in t["bwd"])
+        assert len(t["front"]) >= 1 and all(ms > 0 for _, ms in t["front"])
+        assert t["front_ctas_per_sm"] == min(t["front"], key=lambda c: c[1])[0]
         sub = [0, 17, 50, 95]
         scs = sc.subset(sub)
         sim.step()
@@ -126,9 +128,46 @@ def test_set_tuning_rejects_bad_shapes():
             sim.set_tuning(64, 2, 0)
         with pytest.raises(X.EtacError):
             sim.set_tuning(64, 0, 40)
+        with pytest.raises(X.EtacError):
+            sim.set_tuning(64, 0, 0, front_ctas_per_sm=99)
         sim.set_tuning(32, 1, 64)   # valid; the context keeps working
         sim.step()
         torch.cuda.synchronize()
         assert sim.poll_status() == 0
     finally:
         sim.close()
+
+
+def test_tuning_cache_applies_a_stored_choice(tmp_path):
+    """A choice stored under the tuning key (GPU, pad-type histogram, objects, model) is
+    applied by a later context of the same key without timing, and the step stays correct;
+    another workload has another key."""
+    cache = str(tmp_path / "tuning.json")
+    sc = I.hand_scene(48, seed=12)
+    th = I.make_params(0)
+    first = X.TactileSim(sc)
+    try:
+        first.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        t1 = first.autotune(cache=cache)
+        assert not t1["cached"]
+        key = first.tuning_key(False)
+    finally:
+        first.close()
+    again = X.TactileSim(sc)
+    try:
+        again.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        assert again.tuning_key(False) == key
+        t2 = again.autotune(cache=cache)
+        assert t2["cached"]
+        for k in ("gemm_inst_per_tile", "gemm_tile_order", "front_ctas_per_sm"):
+            assert t2[k] == t1[k]
+        mask = _forward_check(again, sc, th)
+        assert mask.any()
+    finally:
+        again.close()
+    other = X.TactileSim(I.uneven_scene(4, seed=1))
+    try:
+        other.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        assert other.tuning_key(False) != key
+    finally:
+        other.close()
