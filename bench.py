@@ -429,6 +429,86 @@ def config_fit_at_scale(I, theta0, with_oracle):
             "oracle_target_seconds": t_oracle}
 
 
+def config_mesh(X, I, torch, dev, stream, flush, theta, with_oracle):
+    """Mesh contact in the step: the hand layout (4,096 envs, 18.9 M nodes) pressed into four
+    seeded rock meshes (1,280 triangles each), through the C ABI: the BF16 step and the FP32
+    batched step with their kernels, and (with the oracle) the error of the BF16 step on a
+    sample of envs against the FP64 oracle's mesh contact."""
+    sc = I.mesh_scene(4096, seed=2)
+    kw = dict(want_mask=True, want_pen=False, want_count=True)
+    out = {"workload": "hand layout 4096 envs x rock meshes (4 x 1280 triangles)",
+           "nodes_per_step": sc.total_nodes}
+    for name, prec in (("bf16_batched", X.PREC_BF16), ("fp32_batched", X.PREC_FP32)):
+        sim = X.TactileSim(sc, device=dev)
+        try:
+            sim.set_model(theta, X.MODE_FULL, prec, X.ALGO_BATCHED)
+            sim.set_meshes()
+            for _ in range(3):
+                sim.step(**kw)
+            torch.cuda.synchronize()
+            X.etac_enable_timing(sim.ctx, True)
+            ms = timed_steps(sim, 5, stream, flush, torch, kw)
+            kt = X.etac_kernel_times(sim.ctx)
+            X.etac_enable_timing(sim.ctx, False)
+            out[name] = {"ms_per_step": sum(ms) / len(ms),
+                         "node_steps_per_s": sc.total_nodes * 1e3 / (sum(ms) / len(ms)),
+                         "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+                         "active_fraction": float(sim.mask.float().mean())}
+            if with_oracle and prec == X.PREC_BF16:
+                import oracle
+                envs = np.sort(np.random.default_rng(3).choice(sc.num_envs, 32, replace=False))
+                sub = sc.subset(envs)
+                offs = sc.node_offsets
+                idx = np.concatenate([np.arange(offs[e * 6], offs[e * 6 + 6]) for e in envs])
+                ref = oracle.forward(sub, theta, mask_override=sim.mask.cpu().numpy()[idx])
+                got = sim.disp.cpu().numpy()[idx].astype(np.float64)
+                d = np.linalg.norm(got - ref["disp"], axis=1)
+                out[name]["error_vs_oracle"] = dict(
+                    max_abs_mm=float(d.max()), rms_mm=float(np.sqrt((d ** 2).mean())),
+                    envs=len(envs),
+                    mask_mismatch_nodes=int((oracle.forward(sub, theta)["mask"] !=
+                                             sim.mask.cpu().numpy()[idx]).sum()))
+        finally:
+            sim.close()
+    return out
+
+
+def config_regressor(X, I, torch, dev, stream, flush, theta):
+    """The real-to-sim taxel regressor (appendix "Modeling Real Sensors") on the BF16 step's
+    displacement field of the hand layout, 4,096 envs: time per launch of the FP32 kernel and
+    its rate against the FP32 CUDA-core peak (279,936 FLOP per node of the per-node MLPs)."""
+    sc = I.hand_scene(4096, seed=2)
+    rp = I.make_regressor_params(0)
+    sim = X.TactileSim(sc, device=dev)
+    try:
+        sim.set_model(theta, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
+        sim.step()
+        rpt = torch.as_tensor(rp, device=dev)
+        for _ in range(2):
+            sim.regress(rpt, want_attn=False)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        reps = 3
+        e0.record(stream)
+        for _ in range(reps):
+            sim.regress(rpt, want_attn=False)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1) / reps
+    finally:
+        sim.close()
+    flops = 279936.0 * sc.total_nodes
+    peaks, _ = _peaks()
+    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+    fma_peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"workload": "hand layout 4096 envs (18.9 M nodes), seeded regressor weights",
+            "ms_per_launch": ms, "node_per_s": sc.total_nodes * 1e3 / ms,
+            "roofline": {"bound": "alu", "achieved": flops / ms / 1e9, "peak": fma_peak,
+                         "unit": "TFLOP/s", "frac": flops / ms / 1e9 / fma_peak,
+                         "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x "
+                                        f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
+
+
 def config_c4_fd(X, I, torch, dev):
     """The reverse mode against FP64 central differences (h = 1e-6) of the GPU FP64 forward:
     1 env, one 8x8 flat pad, each primitive; the 6 pose components, alpha and 24 sampled
@@ -926,6 +1006,9 @@ def main():
                    "c4_fit": config_c4_fit(I, theta, with_oracle),
                    "c4_fd_check": config_c4_fd(X, I, torch, dev),
                    "fit_at_scale_hand4096": config_fit_at_scale(I, theta, with_oracle),
+                   "mesh_hand4096": config_mesh(X, I, torch, dev, stream, flush, theta,
+                                                with_oracle),
+                   "regressor_hand4096": config_regressor(X, I, torch, dev, stream, flush, theta),
                    "c5_uneven_16384": config_c5(X, I, torch, dev, stream, flush, theta, peaks,
                                                 with_oracle)}
 
