@@ -286,15 +286,23 @@ etac_status etac_forward_f64(etac_ctx* ctx, const etac_model_desc* desc,
  *   a_i = A2 tanh(A1 f_i + b) + b (A1: 256 -> 128, the appendix's [256, 128, 1] MLP);
  *   alpha = softmax of a over the pad's nodes;  g = sum_i alpha_i f_i;
  *   y = H2 relu(H1 g + b) + b (256 -> 128 -> ETAC_TAXELS).
- * rparams: device FP32 [ETAC_REGRESSOR_PARAMS], each layer's W (row-major, out x in) then b,
- * in the order R1, R2, R3, R4, A1, A2, H1, H2.  disp: device [N*3], e.g. the output of
- * etac_step_forward.  Writes taxels [E*P*ETAC_TAXELS] and, when attn is not NULL, each node's
- * softmax weight attn [N].  Uses the context's pads; needs no model.  FP32, enqueued on
- * `stream`.  Errors: ETAC_ERR_INVALID_ARG (NULL or misaligned pointer), ETAC_ERR_CUDA. */
+ * rparams: device FP32 [ETAC_REGRESSOR_PARAMS] (16-byte aligned), each layer's W (row-major,
+ * out x in) then b, in the order R1, R2, R3, R4, A1, A2, H1, H2.  disp: device [N*3], e.g. the
+ * output of etac_step_forward.  Writes taxels [E*P*ETAC_TAXELS] and, when attn is not NULL, each
+ * node's softmax weight attn [N].  Uses the context's pads; needs no model.  Enqueued on
+ * `stream`; all pointers are borrowed.
+ * precision ETAC_PREC_BF16: the per-node layers R1..A1 on the tensor cores (BF16 weights and
+ *   activations, FP32 accumulation; x enters split into two BF16 parts), score, softmax, pooling
+ *   and head in FP32.  Two launches (the BF16 weight images, then the network); the first call
+ *   on a context also builds its pad-to-SM schedule.  A device-side wait that runs out latches
+ *   ETAC_ERR_TIMEOUT in the status word (etac_poll_status).
+ * precision ETAC_PREC_FP32: every layer in FP32 on the CUDA cores (the unoptimised rung).
+ * Errors: ETAC_ERR_INVALID_ARG (NULL or misaligned pointer, unknown precision), ETAC_ERR_OOM,
+ * ETAC_ERR_CUDA. */
 #define ETAC_TAXELS 8
 #define ETAC_REGRESSOR_PARAMS 174729
 etac_status etac_regress(etac_ctx* ctx, const float* disp, const float* rparams, float* taxels,
-                         float* attn, void* stream);
+                         float* attn, int32_t precision, void* stream);
 
 /* Message of the last failed call on this context (or, when ctx is NULL, of the last failed
  * etac_create_pads / etac_step_forward_noalloc on this thread).  Valid until the next call

@@ -6,6 +6,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <functional>
+#include <queue>
+#include <utility>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -144,6 +147,11 @@ struct etac_ctx {
   float* d_pose_part = nullptr;
   float* d_param_part = nullptr;
   int bwd_grid = 0;
+  // taxel regressor, tensor-core form: BF16 weight images and the slot schedule
+  unsigned char* d_reg_wimg = nullptr;
+  int* d_reg_sched = nullptr;        // [slots + 1] offsets | [E*P] pads | [slots] tile counts
+  std::vector<int> reg_sched_h;
+  int reg_grid = 0;
   bool timing = false;
   std::vector<cudaEvent_t> ev;       // 2 * ETAC_TIMING_SLOTS
   std::vector<int> ev_kernel;        // kernel id per used slot
@@ -158,11 +166,12 @@ const char* kKernelNames[] = {"plain_forward_kernel<float>", "batched_forward_ke
                               "bwd_padrev_kernel", "bwd_typenode_kernel",
                               "prop_gemm_kernel<bwd_u>", "prop_gemm_kernel<bwd_alpha>",
                               "bwd_pose_kernel(+param sums)", "bwd_reduce_a3_kernel",
-                              "bwd_padsum_kernel"};
+                              "bwd_padsum_kernel", "regress_pack_kernel", "regress_tc_kernel",
+                              "regress_plain_kernel"};
 enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD = 5, K_PADOBJ = 6,
        K_BWD_PAD = 7, K_BWD_GLOBAL = 8, K_BWD_DECODER = 9, K_BWD_PADREV = 10, K_BWD_TYPENODE = 11,
        K_BWD_GEMM_U = 12, K_BWD_GEMM_A = 13, K_BWD_POSE = 14, K_BWD_A3SUM = 15,
-       K_BWD_PADSUM = 16, K_COUNT = 17 };
+       K_BWD_PADSUM = 16, K_REG_PACK = 17, K_REG_TC = 18, K_REG_PLAIN = 19, K_COUNT = 20 };
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
@@ -229,7 +238,7 @@ void free_ctx(etac_ctx* c) {
                   c->d_s_nr, c->d_ws_idx, c->d_ws_u,
                   c->d_ws_du, c->d_pose_part, c->d_param_part, c->d_g0arg,
                   c->d_blk_perm, c->d_blk_sphere, c->d_type_boff, c->d_btbits,
-                  c->d_blk_pos, c->d_blk_nrm, c->d_meshes};
+                  c->d_blk_pos, c->d_blk_nrm, c->d_meshes, c->d_reg_wimg, c->d_reg_sched};
   for (void* p : ptrs)
     if (p) cudaFree(p);
   delete c;
@@ -1593,12 +1602,56 @@ etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int
   return ETAC_OK;
 }
 
+namespace {
+
+// Work of the tensor-core regressor: whole pads to slots (two per CTA, one CTA per SM), the
+// longest first, each to the slot with the fewest 128-node tiles so far (LPT).
+void build_regress_schedule(etac_ctx* c) {
+  const int num_pads = c->E * c->P;
+  const int grid = std::max(1, std::min(c->num_sms, (num_pads + 1) / 2));
+  const int slots = 2 * grid;
+  std::vector<int> tiles(num_pads), order(num_pads);
+  for (int p = 0; p < num_pads; ++p) {
+    tiles[p] = (c->type_n[c->pad_type[p]] + 127) / 128;
+    order[p] = p;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return tiles[x] > tiles[y]; });
+  using Load = std::pair<long long, int>;   // (tiles so far, slot)
+  std::priority_queue<Load, std::vector<Load>, std::greater<Load>> heap;
+  for (int s = 0; s < slots; ++s) heap.push({0, s});
+  std::vector<std::vector<int>> lists(slots);
+  for (int p : order) {
+    Load l = heap.top();
+    heap.pop();
+    lists[l.second].push_back(p);
+    heap.push({l.first + tiles[p], l.second});
+  }
+  std::vector<int>& h = c->reg_sched_h;
+  h.assign((size_t)slots + 1 + num_pads + slots, 0);
+  int at = 0;
+  for (int s = 0; s < slots; ++s) {
+    h[s] = at;
+    int nt = 0;
+    for (int p : lists[s]) {
+      h[slots + 1 + at++] = p;
+      nt += tiles[p];
+    }
+    h[slots + 1 + num_pads + s] = nt;
+  }
+  h[slots] = at;
+  c->reg_grid = grid;
+}
+
+}  // namespace
+
 etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, float* taxels,
-                         float* attn, void* stream) {
+                         float* attn, int32_t precision, void* stream) {
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
-  if (!disp || !rparams || !taxels || !aligned(disp, 4) || !aligned(rparams, 4) ||
+  if (!disp || !rparams || !taxels || !aligned(disp, 4) || !aligned(rparams, 16) ||
       !aligned(taxels, 4) || !aligned(attn, 4))
     return fail(c, ETAC_ERR_INVALID_ARG, "NULL or misaligned pointer");
+  if (precision != ETAC_PREC_FP32 && precision != ETAC_PREC_BF16)
+    return fail(c, ETAC_ERR_INVALID_ARG, "precision must be ETAC_PREC_FP32 or ETAC_PREC_BF16");
   // layer shapes (out, in) in the order of the flat vector: R1 R2 R3 R4 A1 A2 H1 H2
   static const int dims[8][2] = {{64, 9}, {128, 64}, {256, 128}, {256, 256},
                                  {128, 256}, {1, 128}, {128, 256}, {ETAC_TAXELS, 128}};
@@ -1620,8 +1673,36 @@ etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, f
   a.disp = disp;
   a.taxels = taxels;
   a.attn = attn;
-  ETAC_CUDA(c, etac::launch_regress_plain(a, c->num_sms, reinterpret_cast<cudaStream_t>(stream)),
-            "regressor launch");
+  cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (precision == ETAC_PREC_FP32) {
+    const int ts = timing_begin(c, K_REG_PLAIN, s);
+    ETAC_CUDA(c, etac::launch_regress_plain(a, c->num_sms, s), "regressor launch");
+    timing_end(c, ts, s);
+    return ETAC_OK;
+  }
+  if (!c->d_reg_sched) {
+    build_regress_schedule(c);
+    ETAC_CUDA(c, dalloc(&c->d_reg_wimg, (size_t)etac::REG_TC_IMAGE_BYTES), "regressor weights");
+    ETAC_CUDA(c, dalloc(&c->d_reg_sched, c->reg_sched_h.size()), "regressor schedule");
+    ETAC_CUDA(c, cudaMemcpyAsync(c->d_reg_sched, c->reg_sched_h.data(),
+                                 c->reg_sched_h.size() * sizeof(int), cudaMemcpyHostToDevice, s),
+              "regressor schedule copy");
+  }
+  const int slots = 2 * c->reg_grid, num_pads = c->E * c->P;
+  etac::RegTcArgs t{};
+  t.r = a;
+  t.wimg = c->d_reg_wimg;
+  t.slot_off = c->d_reg_sched;
+  t.slot_pads = c->d_reg_sched + slots + 1;
+  t.slot_tiles = c->d_reg_sched + slots + 1 + num_pads;
+  t.status = c->d_status;
+  t.timeout_ns = c->gemm.timeout_ns ? c->gemm.timeout_ns : 2000000000ull;
+  int ts = timing_begin(c, K_REG_PACK, s);
+  ETAC_CUDA(c, etac::launch_regress_pack(a, c->d_reg_wimg, s), "regressor weight images");
+  timing_end(c, ts, s);
+  ts = timing_begin(c, K_REG_TC, s);
+  ETAC_CUDA(c, etac::launch_regress_tc(t, c->reg_grid, s), "regressor launch");
+  timing_end(c, ts, s);
   return ETAC_OK;
 }
 

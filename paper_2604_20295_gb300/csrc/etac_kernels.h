@@ -381,4 +381,22 @@ struct RegArgs {
 
 cudaError_t launch_regress_plain(const RegArgs& a, int num_sms, cudaStream_t s);
 
+// Tensor-core regressor (regress_tc.cu).  Slot s (two per CTA) runs the encoder over the pads
+// slot_pads[slot_off[s] .. slot_off[s + 1]) in order; slot_tiles[s] is their number of
+// 128-node tiles.  wimg holds the BF16 weight images of the five per-node layers
+// (REG_TC_IMAGE_BYTES, written by launch_regress_pack).
+constexpr int REG_TC_IMAGE_BYTES = 286720;
+struct RegTcArgs {
+  RegArgs r;
+  const unsigned char* wimg;
+  const int* slot_off;        // [num_slots + 1]
+  const int* slot_pads;       // [num_pads]
+  const int* slot_tiles;      // [num_slots]
+  int* status;
+  unsigned long long timeout_ns;
+};
+cudaError_t launch_regress_pack(const RegArgs& a, unsigned char* wimg, cudaStream_t s);
+cudaError_t launch_regress_tc(const RegTcArgs& a, int grid, cudaStream_t s);
+size_t regress_tc_smem_bytes();
+
 }  // namespace etac

@@ -165,7 +165,7 @@ def lib():
         L.etac_mesh_gpu_destroy.restype = None
         L.etac_mesh_gpu_destroy.argtypes = [_vp]
         L.etac_regress.restype = ctypes.c_int
-        L.etac_regress.argtypes = [_vp] * 6
+        L.etac_regress.argtypes = [_vp] * 5 + [ctypes.c_int32, _vp]
         L.etac_set_meshes.restype = ctypes.c_int
         L.etac_set_meshes.argtypes = [_vp, _vp, ctypes.c_int32, _vp]
         _lib = L
@@ -240,8 +240,9 @@ def mesh_accel(verts, tris, grid: int = 0) -> dict:
 
 
 def etac_regress(ctx: int, disp: int, rparams: int, taxels: int, attn: int = 0,
-                 stream: int = 0) -> None:
-    _check(ctx, lib().etac_regress(ctx, disp, rparams, taxels, attn or None, stream), "etac_regress")
+                 precision: int = PREC_BF16, stream: int = 0) -> None:
+    _check(ctx, lib().etac_regress(ctx, disp, rparams, taxels, attn or None, precision, stream),
+           "etac_regress")
 
 
 def etac_mesh_gpu_create(accel: int, stream: int = 0) -> int:
@@ -487,10 +488,12 @@ class TactileSim:
                              self.pen.data_ptr() if want_pen else None,
                              self.count.data_ptr() if want_count else None)
 
-    def regress(self, rparams, disp=None, want_attn=True):
+    def regress(self, rparams, disp=None, want_attn=True, precision=None):
         """Real-to-sim taxel regressor on every pad: taxels [E*P, 8] (and each node's softmax
         weight [N]) from a displacement field (default: the last step's) and the regressor's
-        flat FP32 parameters (a device tensor or array of REGRESSOR_PARAMS values)."""
+        flat FP32 parameters (a device tensor or array of REGRESSOR_PARAMS values).
+        ``precision``: PREC_BF16 (default; the per-node layers on the tensor cores) or
+        PREC_FP32 (all layers in FP32 on the CUDA cores)."""
         torch = self.torch
         rp = torch.as_tensor(np.asarray(rparams, np.float32) if not torch.is_tensor(rparams)
                              else rparams, dtype=torch.float32).to(self.device).contiguous()
@@ -504,6 +507,7 @@ class TactileSim:
         attn = torch.empty(self.N, dtype=torch.float32, device=self.device) if want_attn else None
         etac_regress(self.ctx, d.data_ptr(), rp.data_ptr(), taxels.data_ptr(),
                      attn.data_ptr() if want_attn else 0,
+                     PREC_BF16 if precision is None else precision,
                      torch.cuda.current_stream(self.device).cuda_stream)
         return taxels, attn
 
