@@ -473,40 +473,76 @@ def config_mesh(X, I, torch, dev, stream, flush, theta, with_oracle):
     return out
 
 
-def config_regressor(X, I, torch, dev, stream, flush, theta):
+def config_regressor(X, I, torch, dev, stream, theta, with_oracle):
     """The real-to-sim taxel regressor (appendix "Modeling Real Sensors") on the BF16 step's
-    displacement field of the hand layout, 4,096 envs: time per launch of the FP32 kernel and
-    its rate against the FP32 CUDA-core peak (279,936 FLOP per node of the per-node MLPs)."""
+    displacement field of the hand layout, 4,096 envs (18.9 M nodes, 24,576 pads), through the
+    C ABI: the tensor-core path (per-node layers in BF16 with FP32 accumulation) per call and
+    per kernel, its rate against the measured BF16 tensor peak (279,936 FLOP per node in the
+    per-node layers), and (with the oracle) its error on three envs against the FP64 oracle,
+    on the FP32 weights and on the same weights rounded to BF16.  The field (226 MB) is larger
+    than L2, so calls are timed back to back."""
     sc = I.hand_scene(4096, seed=2)
     rp = I.make_regressor_params(0)
     sim = X.TactileSim(sc, device=dev)
+    out = {"workload": "hand layout 4096 envs (18.9 M nodes, 24,576 pads), seeded regressor "
+                       "weights, BF16 step field"}
     try:
         sim.set_model(theta, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
-        sim.step()
+        disp = sim.step().clone()
         rpt = torch.as_tensor(rp, device=dev)
-        for _ in range(2):
-            sim.regress(rpt, want_attn=False)
+        for _ in range(3):
+            sim.regress(rpt, disp=disp, want_attn=False)
         torch.cuda.synchronize()
+        X.etac_enable_timing(sim.ctx, True)
+        reps = 10
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        reps = 3
         e0.record(stream)
         for _ in range(reps):
-            sim.regress(rpt, want_attn=False)
+            sim.regress(rpt, disp=disp, want_attn=False)
         e1.record(stream)
         torch.cuda.synchronize()
         ms = e0.elapsed_time(e1) / reps
+        kt = X.etac_kernel_times(sim.ctx)
+        X.etac_enable_timing(sim.ctx, False)
+        assert sim.poll_status() == 0, "regressor status"
+        y, a = sim.regress(rpt, disp=disp)
+        torch.cuda.synchronize()
+        envs = [0, 2047, 4095]
+        P, offs = sc.pads_per_env, sc.node_offsets
+        rows = np.concatenate([np.arange(offs[e * P], offs[(e + 1) * P]) for e in envs])
+        pads = np.concatenate([np.arange(e * P, (e + 1) * P) for e in envs])
+        d_s = disp.cpu().numpy()[rows].astype(np.float64)
+        y_s = y.cpu().numpy()[pads].astype(np.float64)
     finally:
         sim.close()
     flops = 279936.0 * sc.total_nodes
-    peaks, _ = _peaks()
-    nsm = torch.cuda.get_device_properties(dev).multi_processor_count
-    fma_peak = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
-    return {"workload": "hand layout 4096 envs (18.9 M nodes), seeded regressor weights",
-            "ms_per_launch": ms, "node_per_s": sc.total_nodes * 1e3 / ms,
-            "roofline": {"bound": "alu", "achieved": flops / ms / 1e9, "peak": fma_peak,
-                         "unit": "TFLOP/s", "frac": flops / ms / 1e9 / fma_peak,
-                         "peak_source": f"derived: {nsm} SMs x 128 FP32 lanes x 2 x "
-                                        f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}}
+    peaks, src = _peaks()
+    k_ms = kt["regress_tc_kernel"][1] / max(kt["regress_tc_kernel"][0], 1)
+    ach = flops / k_ms / 1e9
+    out.update({"ms_per_call": ms, "node_per_s": sc.total_nodes * 1e3 / ms,
+                "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+                "roofline": {"bound": "tensor", "kernel": "regress_tc_kernel",
+                             "achieved": ach, "peak": peaks["bf16_tflops"], "unit": "TFLOP/s",
+                             "frac": ach / peaks["bf16_tflops"],
+                             "peak_source": f"{src} bf16_tflops (burst)",
+                             "flop_per_node": 279936}})
+    if with_oracle:
+        import oracle
+        sub = sc.subset(envs)
+        rp64 = rp.astype(np.float64)
+        rpb = rp64.copy()
+        sl = I.regressor_param_slices()
+        for k in ("WR1", "WR2", "WR3", "WR4", "WA1"):
+            s0, n, _ = sl[k]
+            rpb[s0:s0 + n] = torch.as_tensor(rp[s0:s0 + n]).to(torch.bfloat16).double().numpy()
+        err = {}
+        for name, w in (("fp32_weights", rp64), ("bf16_weights", rpb)):
+            ref = oracle.regress(sub, d_s, w)["taxels"]
+            scale = np.abs(ref).max(axis=1)
+            err[name] = {"max_abs": float(np.abs(y_s - ref).max()),
+                         "max_pad_rel": float((np.abs(y_s - ref).max(axis=1) / scale).max())}
+        out["error_vs_oracle"] = dict(err, envs=len(envs), pads=len(pads))
+    return out
 
 
 def config_c4_fd(X, I, torch, dev):
@@ -666,6 +702,9 @@ def main():
                     help="keep the default tile / block shapes instead of measuring them")
     ap.add_argument("--no-configs", action="store_true",
                     help="skip the single-pad BF16, calibration and 16,384-env uneven sections")
+    ap.add_argument("--configs", default="all",
+                    help="comma-separated names of the sections to run (c3, c4_fit, c4_fd, "
+                         "fit_at_scale, mesh, regressor, c5), or all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -1002,15 +1041,21 @@ def main():
         sim.close()
         sim = None
         with_oracle = not args.no_cpu
-        configs = {"c3_bf16_single_pad": config_c3(X, I, torch, dev, stream, flush, theta, with_oracle),
-                   "c4_fit": config_c4_fit(I, theta, with_oracle),
-                   "c4_fd_check": config_c4_fd(X, I, torch, dev),
-                   "fit_at_scale_hand4096": config_fit_at_scale(I, theta, with_oracle),
-                   "mesh_hand4096": config_mesh(X, I, torch, dev, stream, flush, theta,
-                                                with_oracle),
-                   "regressor_hand4096": config_regressor(X, I, torch, dev, stream, flush, theta),
-                   "c5_uneven_16384": config_c5(X, I, torch, dev, stream, flush, theta, peaks,
-                                                with_oracle)}
+        sections = {
+            "c3": ("c3_bf16_single_pad",
+                   lambda: config_c3(X, I, torch, dev, stream, flush, theta, with_oracle)),
+            "c4_fit": ("c4_fit", lambda: config_c4_fit(I, theta, with_oracle)),
+            "c4_fd": ("c4_fd_check", lambda: config_c4_fd(X, I, torch, dev)),
+            "fit_at_scale": ("fit_at_scale_hand4096",
+                             lambda: config_fit_at_scale(I, theta, with_oracle)),
+            "mesh": ("mesh_hand4096",
+                     lambda: config_mesh(X, I, torch, dev, stream, flush, theta, with_oracle)),
+            "regressor": ("regressor_hand4096",
+                          lambda: config_regressor(X, I, torch, dev, stream, theta, with_oracle)),
+            "c5": ("c5_uneven_16384",
+                   lambda: config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle))}
+        wanted = list(sections) if args.configs == "all" else args.configs.split(",")
+        configs = {sections[k][0]: sections[k][1]() for k in wanted}
 
     # the metric's two comparisons, early in the line: BF16 batched over FP32 plain on this
     # workload, and the reverse mode's time over the forward's

@@ -147,41 +147,59 @@ __global__ void regress_pack_kernel(const RegArgs a, unsigned char* img) {
   }
 }
 
-// Epilogue of layer L for one thread: node row r (TMEM lane), column half h.  Layers 0-3 write
-// the next A operand; layer 4 returns the partial attention score over its 64 columns.
+// Each epilogue thread keeps the biases of its column half in registers, lane-distributed:
+// bias of column h * HALF + 32 x + lane of layer l in hb[hb_off(l) + x]; A2's weights of the
+// half at hb_off(5).  A value reaches the lanes that need it by a warp shuffle.
+__host__ __device__ constexpr int hb_off(int l) {
+  return l == 0 ? 0 : l == 1 ? 1 : l == 2 ? 3 : l == 3 ? 7 : l == 4 ? 11 : 13;
+}
+constexpr int HB = 15;
+
+// waits for this thread's tensor-memory loads; the registers of the last load are in-out
+// operands, so no use of them is scheduled before the wait
+__device__ __forceinline__ void tc_wait_ld_into(uint32_t (&r)[16]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;"
+               : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
+                 "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
+                 "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15])
+               :
+               : "memory");
+}
+
+// Epilogue of layer L for one thread: node row r (TMEM lane), column half h, in chunks of 16
+// columns with the next chunk's tensor-memory load in flight.  Layers 0-3 write the next A
+// operand; layer 4 returns the partial attention score over its 64 columns.
 template <int L>
-__device__ __forceinline__ float epi_layer(const RegArgs& a, uint32_t trow, uint32_t act_u, int r,
-                                           int h) {
-  constexpr int HALF = lay_n(L) / 2;
-  const float* bias = a.b[L];
+__device__ __forceinline__ float epi_layer(const float (&hb)[HB], uint32_t trow, uint32_t act_u,
+                                           int r, int h) {
+  constexpr int HALF = lay_n(L) / 2, NCH = HALF / 16;
+  const uint32_t tcol = trow + (uint32_t)(h * HALF);
   float part = 0.f;
-#pragma unroll 1
-  for (int c0 = h * HALF; c0 < (h + 1) * HALF; c0 += 16) {
-    uint32_t v[16];
-    tc_ld_32x32b_x16(trow + (uint32_t)c0, v);
-    tc_wait_ld();
+  uint32_t v[2][16];
+  tc_ld_32x32b_x16(tcol, v[0]);
+  tc_wait_ld_into(v[0]);
+#pragma unroll
+  for (int ch = 0; ch < NCH; ++ch) {
+    if (ch + 1 < NCH) tc_ld_32x32b_x16(tcol + 16u * (ch + 1), v[(ch + 1) & 1]);
+    const uint32_t* vv = v[ch & 1];
     float y[16];
 #pragma unroll
-    for (int i = 0; i < 16; i += 4) {
-      const float4 b4 = __ldg(reinterpret_cast<const float4*>(bias + c0 + i));
-      y[i] = __uint_as_float(v[i]) + b4.x;
-      y[i + 1] = __uint_as_float(v[i + 1]) + b4.y;
-      y[i + 2] = __uint_as_float(v[i + 2]) + b4.z;
-      y[i + 3] = __uint_as_float(v[i + 3]) + b4.w;
+    for (int i = 0; i < 16; ++i) {
+      const int k = 16 * ch + i;   // column within the half
+      y[i] = __uint_as_float(vv[i]) +
+             __shfl_sync(0xffffffffu, hb[hb_off(L) + (k >> 5)], k & 31);
     }
     if constexpr (L == 4) {
-      const float* A2 = a.W[5];
 #pragma unroll
-      for (int i = 0; i < 16; i += 4) {
-        const float4 w4 = __ldg(reinterpret_cast<const float4*>(A2 + c0 + i));
-        part = fmaf(w4.x, tanh_approx(y[i]), part);
-        part = fmaf(w4.y, tanh_approx(y[i + 1]), part);
-        part = fmaf(w4.z, tanh_approx(y[i + 2]), part);
-        part = fmaf(w4.w, tanh_approx(y[i + 3]), part);
+      for (int i = 0; i < 16; ++i) {
+        const int k = 16 * ch + i;
+        part = fmaf(__shfl_sync(0xffffffffu, hb[hb_off(5) + (k >> 5)], k & 31),
+                    tanh_approx(y[i]), part);
       }
     } else {
-      const uint32_t blk = act_u + (uint32_t)(c0 >> 6) * KB_BYTES;
-      const int j0 = (c0 & 63) >> 3;
+      const int c = h * HALF + 16 * ch;
+      const uint32_t blk = act_u + (uint32_t)(c >> 6) * KB_BYTES;
+      const int j0 = (c & 63) >> 3;
 #pragma unroll
       for (int i = 0; i < 16; ++i) y[i] = fmaxf(y[i], 0.f);
       if constexpr (L == 3) {
@@ -204,6 +222,7 @@ __device__ __forceinline__ float epi_layer(const RegArgs& a, uint32_t trow, uint
                      pack2(z[4], z[5]), pack2(z[6], z[7]));
       }
     }
+    if (ch + 1 < NCH) tc_wait_ld_into(v[(ch + 1) & 1]);
   }
   return part;
 }
@@ -352,6 +371,15 @@ __global__ void __launch_bounds__(THREADS, 1) regress_tc_kernel(const __grid_con
     const int bar_pair = 1 + 4 * s + q;        // the two warps of rows 32 q .. 32 q + 31
     const int bar_slot = 9 + s;
     float* sc = reinterpret_cast<float*>(act);
+    float hb[HB];
+#pragma unroll
+    for (int l = 0; l < NL; ++l) {
+      const int half = lay_n(l) / 2;
+#pragma unroll
+      for (int x = 0; x < half / 32; ++x) hb[hb_off(l) + x] = __ldg(a.b[l] + h * half + 32 * x + lane);
+    }
+#pragma unroll
+    for (int x = 0; x < 2; ++x) hb[hb_off(5) + x] = __ldg(a.W[5] + h * 64 + 32 * x + lane);
     uint32_t accc = 0;
     int round = 0;
     bool stopped = false;
@@ -405,11 +433,11 @@ __global__ void __launch_bounds__(THREADS, 1) regress_tc_kernel(const __grid_con
           __syncwarp();
           ++accc;
           tc_fence_after();
-          if (l == 0) epi_layer<0>(a, trow, act_u, r, h);
-          if (l == 1) epi_layer<1>(a, trow, act_u, r, h);
-          if (l == 2) epi_layer<2>(a, trow, act_u, r, h);
-          if (l == 3) epi_layer<3>(a, trow, act_u, r, h);
-          if (l == 4) part = epi_layer<4>(a, trow, act_u, r, h);
+          if (l == 0) epi_layer<0>(hb, trow, act_u, r, h);
+          if (l == 1) epi_layer<1>(hb, trow, act_u, r, h);
+          if (l == 2) epi_layer<2>(hb, trow, act_u, r, h);
+          if (l == 3) epi_layer<3>(hb, trow, act_u, r, h);
+          if (l == 4) part = epi_layer<4>(hb, trow, act_u, r, h);
           if (l < NL - 1) {
             fence_proxy_async_smem();
             tc_fence_before();

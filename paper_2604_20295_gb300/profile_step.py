@@ -3,6 +3,7 @@
     python -m paper_2604_20295_gb300.profile_step --workload hand --envs 4096 --precision bf16
     python -m paper_2604_20295_gb300.profile_step --workload flat16 --envs 1024 --backward
     python -m paper_2604_20295_gb300.profile_step --outputs count   # outputs of the bench step
+    python -m paper_2604_20295_gb300.profile_step --envs 1024 --regress 3  # + taxel regressor
 
 Workloads: ``hand`` (5 curved 16x32 fingertips + flat 32x64 palm per env), ``flat16`` (flat
 16x16 pad pressed by a sphere), ``uneven`` (6 pads of 8x8 .. 64x64 nodes, 1-3 primitives).
@@ -31,6 +32,9 @@ def main():
     ap.add_argument("--outputs", default="all", choices=["all", "count"],
                     help="all: displacement, mask, penetration, active counts; count: "
                          "displacement and active counts (the benchmark's step)")
+    ap.add_argument("--regress", type=int, default=0,
+                    help="then run the taxel regressor (tensor-core path) this many times on "
+                         "the last step's field")
     args = ap.parse_args()
     B.build()
     if args.workload == "hand":
@@ -50,10 +54,16 @@ def main():
         sim.step(**kw)
         if args.backward:
             sim.backward(G)
+    extra = ""
+    if args.regress:
+        rp = torch.as_tensor(I.make_regressor_params(0)).cuda()
+        for _ in range(args.regress):
+            y, _ = sim.regress(rp, want_attn=False)
+        extra = f" |taxels|={float(y.abs().sum()):.6e}"
     torch.cuda.synchronize()
     status = sim.poll_status()
     print(f"{args.workload} envs={args.envs} nodes={sc.total_nodes} status={status} "
-          f"|disp|={float(sim.disp.abs().sum()):.6e}")
+          f"|disp|={float(sim.disp.abs().sum()):.6e}{extra}")
     sim.close()
     if status != 0:
         raise SystemExit(f"device status {status}")
