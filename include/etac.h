@@ -47,7 +47,9 @@ typedef enum {
   ETAC_ERR_OOM = 4,          /* device allocation failed                                   */
   ETAC_ERR_TIMEOUT = 5,      /* device status: a bounded wait gave up                      */
   ETAC_ERR_NONFINITE = 6,    /* device status: a pose held NaN / Inf (those pads output 0) */
-  ETAC_ERR_UNSUPPORTED = 7   /* valid request the library does not implement               */
+  ETAC_ERR_UNSUPPORTED = 7,  /* valid request the library does not implement               */
+  ETAC_ERR_BOUNDS = 8        /* device status, ETAC_BOUNDS build only: an index check failed
+                                (the access was skipped)                                    */
 } etac_status;
 
 enum { ETAC_OBJ_NONE = 0, ETAC_OBJ_SPHERE = 1, ETAC_OBJ_BOX = 2, ETAC_OBJ_CYLINDER = 3,
@@ -212,7 +214,8 @@ etac_status etac_pose_grad_to_quat(const float* poses, const float* twist_grad, 
 etac_status etac_test_withhold_load(etac_ctx* ctx, int32_t tile, uint64_t wait_limit_ns);
 
 /* Reads and clears the device status word (synchronises `stream`).  *device_status receives
- * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE. */
+ * ETAC_OK or the first latched ETAC_ERR_TIMEOUT / ETAC_ERR_NONFINITE (or, in the ETAC_BOUNDS
+ * build, ETAC_ERR_BOUNDS). */
 etac_status etac_poll_status(etac_ctx* ctx, int32_t* device_status, void* stream);
 
 /* ---- Per-kernel timing (profiling aid; the paper has no counterpart).

@@ -5,7 +5,9 @@
 ``build(variant=...)`` builds a variant of the same sources with extra defines into its own
 folder (``_build/<variant>/libetac.so``); the binding loads it when ``ETAC_LIBRARY`` names it.
 Variants: ``outline_refine`` (the exact contact decision as an out-of-line call in every
-kernel, to show that inlining does not change the results).
+kernel, to show that inlining does not change the results); ``bounds`` (ETAC_BOUNDS: index
+checks on the forward kernels' and the regressor's global writes, which latch ETAC_ERR_BOUNDS
+in the device status word and skip the access instead of faulting).
 """
 from __future__ import annotations
 
@@ -46,7 +48,7 @@ def _deps() -> list:
             [os.path.abspath(__file__)])
 
 
-VARIANTS = {"outline_refine": ["-DETAC_OUTLINE_REFINE"]}
+VARIANTS = {"outline_refine": ["-DETAC_OUTLINE_REFINE"], "bounds": ["-DETAC_BOUNDS"]}
 
 
 def variant_lib(variant: str) -> str:

@@ -4,6 +4,7 @@
 // reverse mode's work units for a new shape.  No step call (forward or reverse) allocates or
 // synchronises the host.
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include <algorithm>
 #include <functional>
@@ -175,6 +176,7 @@ enum { K_PLAIN = 0, K_BATCHED = 1, K_FRONT = 2, K_GEMM = 3, K_GLOBAL = 4, K_BWD 
 
 // records the start event of a timed launch; returns the slot or -1
 int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
+  nvtxRangePushA(kKernelNames[kernel]);
   if (!c->timing || c->ev_used >= ETAC_TIMING_SLOTS) return -1;
   const int slot = c->ev_used++;
   c->ev_kernel[slot] = kernel;
@@ -183,7 +185,33 @@ int timing_begin(etac_ctx* c, int kernel, cudaStream_t s) {
 }
 void timing_end(etac_ctx* c, int slot, cudaStream_t s) {
   if (slot >= 0) cudaEventRecord(c->ev[2 * slot + 1], s);
+  nvtxRangePop();
 }
+
+// An API call as a named NVTX range (nested around its launches' ranges).
+struct NvtxScope {
+  explicit NvtxScope(const char* name) { nvtxRangePushA(name); }
+  ~NvtxScope() { nvtxRangePop(); }
+  NvtxScope(const NvtxScope&) = delete;
+  NvtxScope& operator=(const NvtxScope&) = delete;
+};
+
+// One kernel launch as a named region: an NVTX range with the kernel's name (seen by a
+// profiler that attaches an NVTX tool, a no-op otherwise) and, while timing is on, a CUDA event
+// pair on the launch stream.  Scoped, so an early error return still closes both.
+class TimedLaunch {
+ public:
+  TimedLaunch(etac_ctx* c, int kernel, cudaStream_t s)
+      : c_(c), s_(s), slot_(timing_begin(c, kernel, s)) {}
+  ~TimedLaunch() { timing_end(c_, slot_, s_); }
+  TimedLaunch(const TimedLaunch&) = delete;
+  TimedLaunch& operator=(const TimedLaunch&) = delete;
+
+ private:
+  etac_ctx* c_;
+  cudaStream_t s_;
+  int slot_;
+};
 }  // namespace
 
 namespace {
@@ -461,6 +489,7 @@ void fill_gemm_common(etac_ctx* c, etac::GemmParams& g) {
   g.maskbits = c->d_maskbits;
   g.params = c->d_params;
   g.status = c->d_status;
+  g.num_nodes = c->N;
   g.timeout_ns = 2000000000ull;   // 2 s per wait: far beyond any legitimate stall
   g.test_withhold = 0;
 }
@@ -750,9 +779,10 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   f.uhat_in = c->given_uhat;
   f.meshes = c->d_meshes;
   f.num_meshes = c->num_meshes;
-  int ts = timing_begin(c, K_PADOBJ, s);
-  ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
-  timing_end(c, ts, s);
+  {
+    TimedLaunch tl_(c, K_PADOBJ, s);
+    ETAC_CUDA(c, etac::launch_pad_obj(f, s), "reverse mode: pad transforms");
+  }
   ETAC_CUDA(c, cudaMemsetAsync(c->d_ticket, 0, sizeof(int), s), "reset work queue");
   etac::BwdBatchedArgs b{};
   b.type_pos = c->d_type_pos;
@@ -837,9 +867,10 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
   l.r2_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
   l.r7_grid = std::max(1, std::min(4 * c->num_sms, (EP + 7) / 8));
   auto stage = [&](int st, int slot, const char* what) -> etac_status {
-    const int t0 = timing_begin(c, slot, s);
-    ETAC_CUDA(c, etac::launch_backward_stage(b, l, st, grad_params, s), what);
-    timing_end(c, t0, s);
+    {
+      TimedLaunch tl_(c, slot, s);
+      ETAC_CUDA(c, etac::launch_backward_stage(b, l, st, grad_params, s), what);
+    }
     return ETAC_OK;
   };
   etac_status st = stage(etac::BWD_STAGE_PAD, K_BWD_PAD, "reverse mode: pad stage");
@@ -860,14 +891,16 @@ etac_status backward_batched(etac_ctx* c, const float* grad_disp, float* grad_ob
       if (!g->ws_u || !g->ws_du || !g->inst_m || !g->alpha_part || !g->tiles)
         return fail(c, ETAC_ERR_STATE, "reverse-mode GEMM buffers are not set up");
     }
-    int t0 = timing_begin(c, K_BWD_GEMM_U, s);
-    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U, c->gemm_gi),
-              "reverse mode: propagation GEMM");
-    timing_end(c, t0, s);
-    t0 = timing_begin(c, K_BWD_GEMM_A, s);
-    ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA, c->gemm_gi),
-              "reverse mode: alpha GEMM");
-    timing_end(c, t0, s);
+    {
+      TimedLaunch tl_(c, K_BWD_GEMM_U, s);
+      ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_bu, c->gemm_grid, s, etac::GEMM_BWD_U, c->gemm_gi),
+                "reverse mode: propagation GEMM");
+    }
+    {
+      TimedLaunch tl_(c, K_BWD_GEMM_A, s);
+      ETAC_CUDA(c, etac::launch_prop_gemm(c->gemm_ba, c->gemm_grid, s, etac::GEMM_BWD_ALPHA, c->gemm_gi),
+                "reverse mode: alpha GEMM");
+    }
   }
   if ((st = stage(etac::BWD_STAGE_POSE, K_BWD_POSE, "reverse mode: outputs")) != ETAC_OK ||
       (st = stage(etac::BWD_STAGE_PARAMS, K_BWD_POSE, "reverse mode: parameter sums")) != ETAC_OK)
@@ -908,6 +941,7 @@ int64_t etac_total_nodes(const etac_pads_desc* d) {
 }
 
 etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stream) {
+  NvtxScope nvtx_("etac_create_pads");
   if (!out) return fail(nullptr, ETAC_ERR_INVALID_ARG, "out is NULL");
   *out = nullptr;
   if (!d) return fail(nullptr, ETAC_ERR_INVALID_ARG, "desc is NULL");
@@ -1073,6 +1107,7 @@ etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* d, void* stre
 
 etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float* params,
                            void* stream) {
+  NvtxScope nvtx_("etac_set_model");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!valid_model(desc))
     return fail(c, ETAC_ERR_INVALID_ARG,
@@ -1111,6 +1146,7 @@ etac_status etac_set_model(etac_ctx* c, const etac_model_desc* desc, const float
 
 etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_step_out* out,
                               void* stream) {
+  NvtxScope nvtx_("etac_step_forward");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->has_model) return fail(c, ETAC_ERR_STATE, "etac_set_model has not been called");
   if (!in || !out) return fail(c, ETAC_ERR_INVALID_ARG, "in/out is NULL");
@@ -1152,6 +1188,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.type_pmax = c->d_type_pmax;
     b.type_off = c->d_type_off;
     b.omega_off = c->d_omega_off;
+    b.num_nodes = c->N;
     b.pad_type = c->d_pad_type;
     b.pad_off = c->d_pad_off;
     b.item_pad = c->d_item_pad;
@@ -1195,6 +1232,9 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
       f.pad_type = c->d_pad_type;
       f.pad_off = c->d_pad_off;
       f.item_pad = c->d_item_pad;
+      f.num_nodes = c->N;
+      f.bt_total = c->bt_total;
+      f.mask_words = c->mask_words;
       f.num_items = (int)EP;
       f.P = c->P;
       f.K = c->K;
@@ -1241,37 +1281,43 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
           !f.mask_woff || !f.pad_m || !f.g0a || !f.ranked || !c->gemm.tiles || !c->gemm.h0bf16 ||
           !c->gemm.maskbits)
         return fail(c, ETAC_ERR_STATE, "BF16 buffers are not set up");
-      int ts = timing_begin(c, K_PADOBJ, s);
-      ETAC_CUDA(c, etac::launch_pad_obj(f, s), "pad transforms launch");
-      timing_end(c, ts, s);
-      ts = timing_begin(c, K_FRONT, s);
-      ETAC_CUDA(c, etac::launch_front_contact(f, std::min<int>(c->front_grid, (int)EP), s),
-                "BF16 front launch");
-      timing_end(c, ts, s);
-      ts = timing_begin(c, K_GLOBAL, s);
-      ETAC_CUDA(c, etac::launch_front_global(f, c->num_sms, s),
-                "BF16 global-feature launch");
-      timing_end(c, ts, s);
+      {
+        TimedLaunch tl_(c, K_PADOBJ, s);
+        ETAC_CUDA(c, etac::launch_pad_obj(f, s), "pad transforms launch");
+      }
+      {
+        TimedLaunch tl_(c, K_FRONT, s);
+        ETAC_CUDA(c, etac::launch_front_contact(f, std::min<int>(c->front_grid, (int)EP), s),
+                  "BF16 front launch");
+      }
+      {
+        TimedLaunch tl_(c, K_GLOBAL, s);
+        ETAC_CUDA(c, etac::launch_front_global(f, c->num_sms, s),
+                  "BF16 global-feature launch");
+      }
       etac::GemmParams& g = c->gemm;
       g.disp = out->disp;
       g.use_l = etac::uses_propagation(c->model.mode);
       g.use_r = etac::uses_residual(c->model.mode);
-      ts = timing_begin(c, K_GEMM, s);
-      ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s, etac::GEMM_FWD, c->gemm_gi), "BF16 propagation GEMM launch");
-      timing_end(c, ts, s);
+      {
+        TimedLaunch tl_(c, K_GEMM, s);
+        ETAC_CUDA(c, etac::launch_prop_gemm(g, c->gemm_grid, s, etac::GEMM_FWD, c->gemm_gi), "BF16 propagation GEMM launch");
+      }
       c->has_forward = true;
       ++c->step_id;
       return ETAC_OK;
     }
-    const int ts = timing_begin(c, K_BATCHED, s);
-    ETAC_CUDA(c, etac::launch_batched_forward(b, std::min<int>(c->batched_grid, (int)EP), s),
-              "batched forward launch");
-    timing_end(c, ts, s);
+    {
+      TimedLaunch tl_(c, K_BATCHED, s);
+      ETAC_CUDA(c, etac::launch_batched_forward(b, std::min<int>(c->batched_grid, (int)EP), s),
+                "batched forward launch");
+    }
     c->has_forward = true;
     ++c->step_id;
     return ETAC_OK;
   }
   etac::PlainArgs<float> a{};
+  a.num_nodes = c->N;
   a.type_pos = c->d_type_pos;
   a.type_nrm = c->d_type_nrm;
   a.type_pmax = c->d_type_pmax;
@@ -1296,9 +1342,10 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
   a.uhat_in = c->given_uhat;
   a.meshes = c->d_meshes;
   a.num_meshes = c->num_meshes;
-  const int ts = timing_begin(c, K_PLAIN, s);
-  ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
-  timing_end(c, ts, s);
+  {
+    TimedLaunch tl_(c, K_PLAIN, s);
+    ETAC_CUDA(c, etac::launch_plain_forward<float>(a, (int)EP, s), "plain forward launch");
+  }
   c->has_forward = true;
   ++c->step_id;
   return ETAC_OK;
@@ -1306,6 +1353,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
 
 etac_status etac_set_meshes(etac_ctx* c, const etac_mesh_gpu* const* meshes, int32_t count,
                             void* stream) {
+  NvtxScope nvtx_("etac_set_meshes");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (count < 0 || (count > 0 && !meshes))
     return fail(c, ETAC_ERR_INVALID_ARG, "meshes: count %d with %s list", count,
@@ -1358,6 +1406,7 @@ etac_status etac_last_step(const etac_ctx* c, uint64_t* step_id) {
 etac_status etac_step_backward(etac_ctx* c, uint64_t step_id, const float* grad_disp,
                                float* grad_obj_pose, float* grad_uhat, float* grad_penetration,
                                float* grad_params, void* stream) {
+  NvtxScope nvtx_("etac_step_backward");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!c->has_forward) return fail(c, ETAC_ERR_STATE, "no forward step to differentiate");
   if (step_id != 0 && step_id != c->step_id)
@@ -1411,9 +1460,10 @@ etac_status etac_step_backward(etac_ctx* c, uint64_t step_id, const float* grad_
   b.uhat_in = c->given_uhat;
   b.meshes = c->d_meshes;
   b.num_meshes = c->num_meshes;
-  const int ts = timing_begin(c, K_BWD, s);
-  ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
-  timing_end(c, ts, s);
+  {
+    TimedLaunch tl_(c, K_BWD, s);
+    ETAC_CUDA(c, etac::launch_backward(b, c->bwd_grid, s), "reverse-mode launch");
+  }
   return ETAC_OK;
 }
 
@@ -1446,6 +1496,7 @@ etac_status etac_set_tuning(etac_ctx* c, const etac_tuning* t, void* stream) {
 
 etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_out* out,
                           const float* grad_disp, etac_tuning* r, void* stream) {
+  NvtxScope nvtx_("etac_autotune");
   if (!c || !in || !out || !r) return fail(c, ETAC_ERR_INVALID_ARG, "NULL argument");
   if (!c->has_model || c->model.algo != ETAC_ALGO_BATCHED)
     return fail(c, ETAC_ERR_STATE, "autotuning needs a batched model");
@@ -1570,6 +1621,7 @@ etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int
                              const double* obj_dims, const double* obj_pose,
                              const double* pad_pose, const double* params, double* disp,
                              void* stream) {
+  NvtxScope nvtx_("etac_forward_f64");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!valid_model(desc)) return fail(c, ETAC_ERR_INVALID_ARG, "bad model desc");
   if (!obj_type || !obj_dims || !obj_pose || !pad_pose || !params || !disp ||
@@ -1579,6 +1631,7 @@ etac_status etac_forward_f64(etac_ctx* c, const etac_model_desc* desc, const int
   if (etac::plain_smem_f64(c->nmax, c->K) > 227 * 1024)
     return fail(c, ETAC_ERR_UNSUPPORTED, "pad type too large for the FP64 check (max ~1500 nodes)");
   etac::PlainArgs<double> a{};
+  a.num_nodes = c->N;
   a.type_pos = c->d_type_pos;
   a.type_nrm = c->d_type_nrm;
   a.type_pmax = c->d_type_pmax;
@@ -1646,6 +1699,7 @@ void build_regress_schedule(etac_ctx* c) {
 
 etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, float* taxels,
                          float* attn, int32_t precision, void* stream) {
+  NvtxScope nvtx_("etac_regress");
   if (!c) return fail(nullptr, ETAC_ERR_INVALID_ARG, "ctx is NULL");
   if (!disp || !rparams || !taxels || !aligned(disp, 4) || !aligned(rparams, 16) ||
       !aligned(taxels, 4) || !aligned(attn, 4))
@@ -1670,14 +1724,16 @@ etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, f
   a.pad_type = c->d_pad_type;
   a.pad_off = c->d_pad_off;
   a.num_pads = c->E * c->P;
+  a.num_nodes = c->N;
   a.disp = disp;
   a.taxels = taxels;
   a.attn = attn;
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
   if (precision == ETAC_PREC_FP32) {
-    const int ts = timing_begin(c, K_REG_PLAIN, s);
-    ETAC_CUDA(c, etac::launch_regress_plain(a, c->num_sms, s), "regressor launch");
-    timing_end(c, ts, s);
+    {
+      TimedLaunch tl_(c, K_REG_PLAIN, s);
+      ETAC_CUDA(c, etac::launch_regress_plain(a, c->num_sms, s), "regressor launch");
+    }
     return ETAC_OK;
   }
   if (!c->d_reg_sched) {
@@ -1697,12 +1753,14 @@ etac_status etac_regress(etac_ctx* c, const float* disp, const float* rparams, f
   t.slot_tiles = c->d_reg_sched + slots + 1 + num_pads;
   t.status = c->d_status;
   t.timeout_ns = c->gemm.timeout_ns ? c->gemm.timeout_ns : 2000000000ull;
-  int ts = timing_begin(c, K_REG_PACK, s);
-  ETAC_CUDA(c, etac::launch_regress_pack(a, c->d_reg_wimg, s), "regressor weight images");
-  timing_end(c, ts, s);
-  ts = timing_begin(c, K_REG_TC, s);
-  ETAC_CUDA(c, etac::launch_regress_tc(t, c->reg_grid, s), "regressor launch");
-  timing_end(c, ts, s);
+  {
+    TimedLaunch tl_(c, K_REG_PACK, s);
+    ETAC_CUDA(c, etac::launch_regress_pack(a, c->d_reg_wimg, s), "regressor weight images");
+  }
+  {
+    TimedLaunch tl_(c, K_REG_TC, s);
+    ETAC_CUDA(c, etac::launch_regress_tc(t, c->reg_grid, s), "regressor launch");
+  }
   return ETAC_OK;
 }
 

@@ -102,6 +102,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
     const long long base = a.pad_off[pad];
     const float* tpos = a.type_pos + 3 * (size_t)o;
     const float* tnrm = a.type_nrm + 3 * (size_t)o;
+    if (!ETAC_IN(a.status, base + n - 1, a.num_nodes)) continue;   // block-uniform
 
     const bool given = a.mask_in != nullptr;   // mode B: contact supplied by the caller
     if (tid < a.K && !given) {

@@ -49,11 +49,26 @@ __host__ __device__ __forceinline__ bool uses_propagation(int mode) {
 __host__ __device__ __forceinline__ bool uses_residual(int mode) {
   return mode == MODE_FULL || mode == MODE_RESIDUAL_ONLY;
 }
-enum { STATUS_OK = 0, STATUS_TIMEOUT = 5, STATUS_NONFINITE = 6 };
+enum { STATUS_OK = 0, STATUS_TIMEOUT = 5, STATUS_NONFINITE = 6, STATUS_BOUNDS = 8 };
 
 __device__ __forceinline__ void latch_status(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
+
+// Index checks of the ETAC_BOUNDS build (build variant "bounds"): ETAC_IN(status, i, n) is true
+// when 0 <= i < n; otherwise it latches ETAC_ERR_BOUNDS in the device status word and is false,
+// and the access it guards is skipped (no trap, no fault).  In the regular build it is the
+// constant true and costs nothing.
+__device__ __forceinline__ bool bounds_ok(int* status, long long i, long long n) {
+  if (i >= 0 && i < n) return true;
+  latch_status(status, STATUS_BOUNDS);
+  return false;
+}
+#ifdef ETAC_BOUNDS
+#define ETAC_IN(status, i, n) ::etac::bounds_ok((status), (long long)(i), (long long)(n))
+#else
+#define ETAC_IN(status, i, n) true
+#endif
 
 // ------------------------------------------------------------------ tiled FP32 product
 constexpr int TLD = H + 4;   // padded row stride of staged 64 x 64 tiles (16-byte aligned)

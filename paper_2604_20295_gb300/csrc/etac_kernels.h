@@ -35,6 +35,7 @@ struct PlainArgs {
   T* pen;                     // optional
   int* count;                 // optional
   int* status;                // device status word
+  long long num_nodes;         // nodes of all pad instances (index checks of the bounds build)
   const uint8_t* mask_in;     // mode B (both or neither): caller's active set [N] and
   const float* uhat_in;       //   u_hat [N*3]; objects are then not read (FP32 only)
   const MeshDev* meshes;      // the context's meshes (OBJ_MESH objects), may be null
@@ -104,6 +105,7 @@ struct BatchedArgs {
   int* count;
   int* ticket;                  // work-queue counter, zero at launch
   int* status;
+  long long num_nodes;         // nodes of all pad instances (index checks of the bounds build)
   const int* skip;              // optional: when *skip != 0 the kernel returns at once
   const uint8_t* mask_in;       // mode B: caller's active set [N] and u_hat [N*3]
   const float* uhat_in;
@@ -140,6 +142,9 @@ struct FrontArgs {
   int* count;
   int* ticket;
   int* status;
+  long long num_nodes;         // nodes of all pad instances (index checks of the bounds build)
+  long long bt_total;          // B-operand entries (BF16) of all types
+  long long mask_words;        // contact-bit words of all pads
   void* bt;                     // BF16 B operand, type t at bt_off[t]: [3 * I_t][n_t]
   const long long* bt_off;
   const int* pad_inst;
@@ -209,6 +214,7 @@ struct GemmParams {
   float* disp;
   int use_l, use_r;
   int* status;
+  long long num_nodes;         // nodes of all pad instances (index checks of the bounds build)
   unsigned long long timeout_ns;
   // failure-path tests only: 1 + the tile whose first K block the producer withholds (its
   // TMA loads are never issued, so the MMA issuer's bounded wait runs out); 0 = off
@@ -377,6 +383,7 @@ struct RegArgs {
   const float* b[8];
   float* taxels;              // [E*P, 8]
   float* attn;                // [N] softmax weights (optional)
+  long long num_nodes;        // N (index checks of the bounds build)
 };
 
 cudaError_t launch_regress_plain(const RegArgs& a, int num_sms, cudaStream_t s);

@@ -109,11 +109,14 @@ __global__ void __launch_bounds__(256) pad_obj_kernel(FrontArgs a) {
 __device__ __forceinline__ void front_write_node(const FrontArgs& a, __nv_bfloat16* btrow, int n,
                                                  long long base, int i, const NodeContact& c,
                                                  bool was) {
-  if (c.active || was) {
+  if ((c.active || was) &&
+      ETAC_IN(a.status, btrow - reinterpret_cast<const __nv_bfloat16*>(a.bt) + 2 * n + i,
+              a.bt_total)) {
     btrow[i] = __float2bfloat16_rn(c.u[0]);
     btrow[n + i] = __float2bfloat16_rn(c.u[1]);
     btrow[2 * n + i] = __float2bfloat16_rn(c.u[2]);
   }
+  if (!ETAC_IN(a.status, base + i, a.num_nodes)) return;
   if (a.mask) a.mask[base + i] = c.active ? 1 : 0;
   if (a.pen) a.pen[base + i] = c.active ? -c.phi : 0.f;
   if (c.active) {
@@ -434,17 +437,19 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
 
     __syncwarp();
     for (int w = lane; w < nwords; w += 32) {
+      if (!ETAC_IN(a.status, a.mask_woff[pad] + w, a.mask_words)) break;
       a.maskbits[a.mask_woff[pad] + w] = sBits[w];
       btb[w] = sBits[w];
     }
     if (lane == 0) {
-      if (a.count) a.count[pad] = m;
+      if (a.count && ETAC_IN(a.status, pad, a.num_items)) a.count[pad] = m;
       a.pad_m[pad] = m;
       if (invalid) latch_status(a.status, STATUS_NONFINITE);
     }
     if (m == 0) {   // no contact (or invalid pose): the whole pad is at rest
       float* d = a.disp + 3 * base;
-      for (int e = lane; e < 3 * n; e += 32) d[e] = 0.f;
+      if (ETAC_IN(a.status, base + n - 1, a.num_nodes))
+        for (int e = lane; e < 3 * n; e += 32) d[e] = 0.f;
       continue;
     }
     if (!enc) continue;
@@ -548,8 +553,10 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
           if (ch[c] == lane + 32) best1 = bv[c];
         }
       }
-      a.g0a[(size_t)pad * H + lane] = fmaxf(best0, sFmax[lane]);
-      a.g0a[(size_t)pad * H + lane + 32] = fmaxf(best1, sFmax[lane + 32]);
+      if (ETAC_IN(a.status, pad, a.num_items)) {
+        a.g0a[(size_t)pad * H + lane] = fmaxf(best0, sFmax[lane]);
+        a.g0a[(size_t)pad * H + lane + 32] = fmaxf(best1, sFmax[lane + 32]);
+      }
     }
     __syncwarp();
   }

@@ -12,6 +12,8 @@
 // frees memory.
 #include <cuda_runtime.h>
 
+#include <climits>
+
 #include <mutex>
 #include <string>
 
@@ -250,6 +252,9 @@ extern "C" etac_status etac_step_forward_noalloc(const etac_noalloc_pads* pads, 
     return noalloc_fail(ETAC_ERR_CUDA, std::string("tables launch: ") + cudaGetErrorString(e));
 
   etac::BatchedArgs b{};
+  // the instance offsets are checked against the type sizes by the prepare kernel (a mismatch
+  // stops the step), so the index checks of the bounds build only bound each pad's own range
+  b.num_nodes = LLONG_MAX;
   b.type_pos = pads->type_pos;
   b.type_nrm = pads->type_nrm;
   b.type_pmax = pmax;

@@ -118,6 +118,7 @@ plain_forward_kernel(PlainArgs<T> a) {
   const float* tpos = a.type_pos + 3 * (size_t)a.type_off[ty];
   const float* tnrm = a.type_nrm + 3 * (size_t)a.type_off[ty];
   const long long base = a.pad_off[pad];
+  if (!ETAC_IN(a.status, base + n - 1, a.num_nodes)) return;   // block-uniform
 
   T* sp = reinterpret_cast<T*>(smem);
   T* sap = sp + S_TOTAL;              // [nmax][6] active nodes: p, u_hat

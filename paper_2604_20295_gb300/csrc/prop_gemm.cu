@@ -21,6 +21,8 @@
 // the CTA winds down (waiting, bounded, for its in-flight copies and MMAs before freeing TMEM).
 #include <cuda_bf16.h>
 
+#include <climits>
+
 #include "etac_common.cuh"
 #include "etac_kernels.h"
 #include "sm100_ptx.cuh"
@@ -104,7 +106,10 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
   uint32_t* s_tmem = reinterpret_cast<uint32_t*>(smem + SM_MISC);
   volatile int* s_abort = reinterpret_cast<volatile int*>(smem + SM_MISC + 4);
   volatile int* s_never = reinterpret_cast<volatile int*>(smem + SM_MISC + 8);      // stays 0
-  volatile int* s_epi_stop = reinterpret_cast<volatile int*>(smem + SM_MISC + 12);  // epilogue
+  // first epilogue tile (local index) at which a wait failed: INT_MAX while none has.  Every
+  // epilogue warp compares it with its own tile after the tile's barrier, so a failure in a
+  // later tile (written while a slow warp still reads) cannot make that warp leave early.
+  int* s_epi_stop = reinterpret_cast<int*>(smem + SM_MISC + 12);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   if (threadIdx.x == 0) {
@@ -119,7 +124,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
     mbar_init(drain, 1);
     *s_abort = 0;
     *s_never = 0;
-    *s_epi_stop = 0;
+    *s_epi_stop = INT_MAX;
     fence_mbar_init();
   }
   if (warp == TMA_WARP && lane == 0) {
@@ -331,11 +336,11 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
       const bool row_ok = i < n_t;
       if (!mbar_wait(&acc_full[b], acc_phase, s_abort, limit)) {
         *s_abort = 1;
-        *s_epi_stop = 1;
+        atomicMin(s_epi_stop, local);
       }
       // every epilogue warp takes the same decision (the flag is only written before here)
       named_bar_sync(2, EPI_WARPS * 32);
-      if (*s_epi_stop) break;
+      if (*reinterpret_cast<volatile int*>(s_epi_stop) <= local) break;
       tc_fence_after();
       const uint32_t tbase = tmem + (uint32_t)b * ACC_STRIDE + ((uint32_t)(32 * q) << 16);
 #pragma unroll 1
@@ -364,6 +369,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
             const float l0 = __uint_as_float(lv4[3 * x]), l1 = __uint_as_float(lv4[3 * x + 1]),
                         l2 = __uint_as_float(lv4[3 * x + 2]);
             const long long node = s_base[inst] + i;
+            if (!ETAC_IN(p.status, node, p.num_nodes)) continue;
             if constexpr (MODE == GEMM_BWD_U) {
               float4 d = p.ws_du[node];
               d.x += l0;
@@ -450,6 +456,7 @@ __global__ void __launch_bounds__(THREADS, 1) prop_gemm_kernel(const __grid_cons
               u1 += r[x].y + cm.y;
               u2 += r[x].z + cm.z;
             }
+            if (!ETAC_IN(p.status, s_base[inst] + i, p.num_nodes)) continue;
             float* d = p.disp + 3 * (s_base[inst] + i);
             d[0] = u0;
             d[1] = u1;

@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(THREADS, 1) regress_tc_kernel(const __grid_con
           uint32_t w[16];
 #pragma unroll
           for (int i = 0; i < 16; ++i) w[i] = 0u;
-          if (h == 0 && r < m) {
+          if (h == 0 && r < m && ETAC_IN(p.status, base + j0 + r, a.num_nodes)) {
             const int node = t0 + j0 + r;
             const float* pp = a.type_pos + 3 * (size_t)node;
             const float* nn = a.type_nrm + 3 * (size_t)node;
@@ -455,7 +455,8 @@ __global__ void __launch_bounds__(THREADS, 1) regress_tc_kernel(const __grid_con
         tc_wait_ld();
         const float score = (h == 0 ? part + other : other + part) + __ldg(a.b[5]);
         const bool valid = r < m;
-        if (a.attn && h == 0 && valid) a.attn[base + j0 + r] = score;   // rescaled at pad end
+        if (a.attn && h == 0 && valid && ETAC_IN(p.status, base + j0 + r, a.num_nodes))
+          a.attn[base + j0 + r] = score;   // rescaled at pad end
         // ---- online softmax pooling over this warp's rows
         const int rows = min(32, m - 32 * q);
         if (rows > 0) {
@@ -540,9 +541,10 @@ __global__ void __launch_bounds__(THREADS, 1) regress_tc_kernel(const __grid_con
         for (int k = lane; k < 128; k += 32) acc = fmaf(__ldg(H2 + lw * 128 + k), sc[SC_z + k], acc);
 #pragma unroll
         for (int sh = 16; sh > 0; sh >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, sh);
-        if (lane == 0) a.taxels[(size_t)pad * 8 + lw] = acc + __ldg(a.b[7] + lw);
+        if (lane == 0 && ETAC_IN(p.status, pad, a.num_pads))
+          a.taxels[(size_t)pad * 8 + lw] = acc + __ldg(a.b[7] + lw);
       }
-      if (a.attn) {
+      if (a.attn && ETAC_IN(p.status, base + n - 1, a.num_nodes)) {
         const float invZ = 1.f / Zt;
         for (int i = c; i < n; i += 256) a.attn[base + i] = __expf(a.attn[base + i] - Mx) * invZ;
       }

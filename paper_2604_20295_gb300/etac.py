@@ -19,7 +19,7 @@ ETAC_OK = 0
 ERR_INVALID_ARG = 1
 STATUS_NAMES = {0: "ETAC_OK", 1: "ETAC_ERR_INVALID_ARG", 2: "ETAC_ERR_STATE", 3: "ETAC_ERR_CUDA",
                 4: "ETAC_ERR_OOM", 5: "ETAC_ERR_TIMEOUT", 6: "ETAC_ERR_NONFINITE",
-                7: "ETAC_ERR_UNSUPPORTED"}
+                7: "ETAC_ERR_UNSUPPORTED", 8: "ETAC_ERR_BOUNDS"}
 MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY, MODE_PENETRATION_ONLY = 0, 1, 2, 3
 PREC_FP32, PREC_BF16 = 0, 1
 ALGO_PLAIN, ALGO_BATCHED = 0, 1
