@@ -602,6 +602,64 @@ def config_c4_fd(X, I, torch, dev):
     return out
 
 
+def config_c5_continuous(X, I, torch, dev, stream, flush, theta, peaks, with_oracle):
+    """The continuous-pitch variant of the uneven workload: 2,048 envs x 6 flat pads of
+    8x8 .. 64x64 nodes, each pad with its own pitch ~U[0.5, 2] mm (12,288 pad types, so no
+    Omega table is shared: at 16,384 envs the tables would need 1.7 TB), 1-3 primitives per
+    env.  The batched FP32 step with Omega on the fly (the library's own choice here), timed
+    per step and per kernel, its rate over the propagation pairs against the special-function
+    pipe (each pair takes one sqrt and one exp), and its error on sampled envs against the
+    oracle.  2,048 of the 16,384 envs keep the per-type node tables at 24 GB."""
+    sc = I.uneven_continuous_scene(2048, seed=5)
+    sim = X.TactileSim(sc, device=dev)
+    out = {"workload": "uneven-continuous-pitch-2048env-6pads-8x8..64x64 (12,288 pad types)",
+           "nodes_per_step": sc.total_nodes}
+    try:
+        sim.set_model(theta, X.MODE_FULL, X.PREC_FP32, X.ALGO_BATCHED)
+        kw = dict(want_mask=False, want_pen=False, want_count=True)
+        for _ in range(3):
+            sim.step(**kw)
+        torch.cuda.synchronize()
+        counts = sim.count.cpu().numpy()
+        work = algorithmic_work(sc, counts)
+        X.etac_enable_timing(sim.ctx, True)
+        ms = timed_steps(sim, 5, stream, flush, torch, kw)
+        kt = X.etac_kernel_times(sim.ctx)
+        X.etac_enable_timing(sim.ctx, False)
+        fwd_ms = sum(ms) / len(ms)
+        nsm = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = peaks.get("sm_max_mhz", 2070.0)
+        sfu_peak = nsm * 16 * mhz * 1e6 / 1e12   # special-function ops per second (x 1e12)
+        k_ms = kt["batched_forward_kernel<fp32>"][1] / max(kt["batched_forward_kernel<fp32>"][0], 1)
+        ach = 2.0 * work["pairs"] / k_ms / 1e9
+        out.update({"omega": "on the fly (the tables would exceed the 4 GiB cache limit)",
+                    "fwd_ms": fwd_ms, "fwd_node_steps_per_s": sc.total_nodes * 1e3 / fwd_ms,
+                    "active_fraction": work["active"] / sc.total_nodes,
+                    "pairs": work["pairs"],
+                    "kernels_ms": {k: v[1] / max(v[0], 1) for k, v in kt.items()},
+                    "roofline": {"bound": "alu", "kernel": "batched_forward_kernel<fp32>",
+                                 "achieved": ach, "peak": sfu_peak, "unit": "Tops/s",
+                                 "frac": ach / sfu_peak,
+                                 "peak_source": f"derived: {nsm} SMs x 16 special-function "
+                                                f"ops/clk x {mhz} MHz; 2 ops (sqrt, exp) per "
+                                                f"(passive, active) pair"}})
+        if with_oracle:
+            import oracle
+            envs = np.sort(np.random.default_rng(9).choice(sc.num_envs, 16, replace=False))
+            sub = sc.subset(envs)
+            sim.step(want_mask=True, want_pen=False, want_count=True)
+            torch.cuda.synchronize()
+            offs = sc.node_offsets
+            idx = np.concatenate([np.arange(offs[e * 6], offs[e * 6 + 6]) for e in envs])
+            ref = oracle.forward(sub, theta)
+            out["error_vs_oracle"] = dict(_stats(sim.disp.cpu().numpy()[idx], ref["disp"],
+                                                 sim.mask.cpu().numpy()[idx], ref["mask"]),
+                                          envs=len(envs))
+    finally:
+        sim.close()
+    return out
+
+
 def config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle):
     """Scale and unevenness: 16,384 envs x 6 flat pads of 8x8 .. 64x64 nodes (16 pad types),
     1-3 primitives per env; BF16 forward and FP32 reverse mode."""
@@ -704,7 +762,7 @@ def main():
                     help="skip the single-pad BF16, calibration and 16,384-env uneven sections")
     ap.add_argument("--configs", default="all",
                     help="comma-separated names of the sections to run (c3, c4_fit, c4_fd, "
-                         "fit_at_scale, mesh, regressor, c5), or all")
+                         "fit_at_scale, mesh, regressor, c5, c5_continuous), or all")
     args = ap.parse_args()
     args.warmup = max(args.warmup, 3)
 
@@ -1053,7 +1111,10 @@ def main():
             "regressor": ("regressor_hand4096",
                           lambda: config_regressor(X, I, torch, dev, stream, theta, with_oracle)),
             "c5": ("c5_uneven_16384",
-                   lambda: config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle))}
+                   lambda: config_c5(X, I, torch, dev, stream, flush, theta, peaks, with_oracle)),
+            "c5_continuous": ("c5_continuous_pitch_2048",
+                              lambda: config_c5_continuous(X, I, torch, dev, stream, flush, theta,
+                                                           peaks, with_oracle))}
         wanted = list(sections) if args.configs == "all" else args.configs.split(",")
         configs = {sections[k][0]: sections[k][1]() for k in wanted}
 

@@ -240,7 +240,8 @@ etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max,
  * innermost (they share an Omega row block); bwd_node_range: nodes per work unit of the
  * batched reverse mode's decoder stage (16..256, a multiple of 16); front_ctas_per_sm: CTAs
  * per SM of the BF16 step's persistent contact / encoder kernel (1 .. the occupancy maximum,
- * which is also what 0 selects).
+ * which is also what 0 selects); omega_source: where the batched FP32 step takes Omega
+ * (ETAC_OMEGA_*, below; etac_autotune times the table against on the fly when the table fits).
  *
  * etac_autotune times every candidate on the caller's own step: the forward shapes
  * (ETAC_ALGO_BATCHED with ETAC_PREC_BF16: GEMM tiles, then the front kernel's CTAs per SM)
@@ -268,7 +269,15 @@ typedef struct {
   int32_t num_front;                   /* front-kernel candidates timed */
   int32_t front_cand[ETAC_TUNE_MAX];   /* CTAs per SM */
   float front_ms[ETAC_TUNE_MAX];
+  int32_t omega_source;                /* ETAC_OMEGA_* (batched FP32 only) */
+  float omega_ms[2];                   /* forward ms with the table, on the fly (0: not timed) */
 } etac_tuning;
+/* Source of Omega (Eq. 1) in the batched FP32 step: AUTO takes the per-type table when all
+ * tables together fit in 4 GiB (otherwise, e.g. for pads of per-instance geometry, the kernel
+ * evaluates exp(-alpha |p_j - p_i|) on the fly, with the table's own FP32 expression, so both
+ * give the same bits); TABLE insists on the table (ETAC_ERR_UNSUPPORTED when too large);
+ * ON_THE_FLY never builds it. */
+enum { ETAC_OMEGA_AUTO = 0, ETAC_OMEGA_TABLE = 1, ETAC_OMEGA_ON_THE_FLY = 2 };
 etac_status etac_autotune(etac_ctx* ctx, const etac_step_in* in, const etac_step_out* out,
                           const float* grad_disp, etac_tuning* result, void* stream);
 etac_status etac_set_tuning(etac_ctx* ctx, const etac_tuning* tuning, void* stream);

@@ -76,6 +76,10 @@ struct etac_ctx {
   float* d_h0tab = nullptr;
   int16_t* d_order = nullptr;
   float* d_omega = nullptr;
+  // batched FP32: Omega from the per-type table, or on the fly (exp of the distance, in the
+  // kernel) when the table would exceed kOmegaTableMaxBytes or the caller chose it
+  bool omega_otf = false;
+  int omega_pref = -1;   // etac_set_tuning: -1 no choice, 0 table, 1 on the fly
   void* d_omega_bf16 = nullptr;
   bool tables_ready = false;
   int batched_grid = 0;
@@ -694,6 +698,10 @@ etac_status setup_bwdb(etac_ctx* c, cudaStream_t s) {
   return ETAC_OK;
 }
 
+// Largest per-type Omega table (FP32) the batched algorithm caches; beyond it (pads of
+// per-instance geometry, many large types) Omega is evaluated on the fly.
+constexpr size_t kOmegaTableMaxBytes = size_t(4) << 30;
+
 etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t s) {
   const size_t tn = (size_t)c->type_off[c->T];
   const size_t om = (size_t)c->omega_off[c->T];
@@ -707,8 +715,14 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate per-type tables");
   }
   const bool batched = desc->algo == ETAC_ALGO_BATCHED;
-  const bool need32 = batched && desc->precision == ETAC_PREC_FP32;
+  const bool fp32b = batched && desc->precision == ETAC_PREC_FP32;
+  const bool fits = om * sizeof(float) <= kOmegaTableMaxBytes;
+  if (fp32b && c->omega_pref == 0 && !fits)
+    return fail(c, ETAC_ERR_UNSUPPORTED, "Omega table of %zu bytes exceeds %zu: on the fly only",
+                om * sizeof(float), kOmegaTableMaxBytes);
+  const bool need32 = fp32b && fits && c->omega_pref != 1;
   const bool need16 = batched && desc->precision == ETAC_PREC_BF16;
+  c->omega_otf = fp32b && !need32;
   if (need32 && !c->d_omega) {
     e = dalloc(&c->d_omega, om);
     if (e != cudaSuccess) return cuda_fail(c, e, "allocate Omega table");
@@ -1205,7 +1219,7 @@ etac_status etac_step_forward(etac_ctx* c, const etac_step_in* in, const etac_st
     b.f0tab = c->d_f0tab;
     b.h0tab = c->d_h0tab;
     b.order = c->d_order;
-    b.omega = c->d_omega;
+    b.omega = c->omega_otf ? nullptr : c->d_omega;
     b.mode = c->model.mode;
     b.disp = out->disp;
     b.mask = out->active_mask;
@@ -1472,6 +1486,21 @@ etac_status etac_set_tuning(etac_ctx* c, const etac_tuning* t, void* stream) {
   if (!c->has_model || c->model.algo != ETAC_ALGO_BATCHED)
     return fail(c, ETAC_ERR_STATE, "tuning applies to a batched model");
   cudaStream_t s = reinterpret_cast<cudaStream_t>(stream);
+  if (c->model.precision == ETAC_PREC_FP32) {
+    if (t->omega_source < ETAC_OMEGA_AUTO || t->omega_source > ETAC_OMEGA_ON_THE_FLY)
+      return fail(c, ETAC_ERR_INVALID_ARG, "omega_source %d unknown", t->omega_source);
+    const int pref = t->omega_source == ETAC_OMEGA_TABLE ? 0
+                     : t->omega_source == ETAC_OMEGA_ON_THE_FLY ? 1 : -1;
+    if (pref != c->omega_pref) {
+      const int old = c->omega_pref;
+      c->omega_pref = pref;
+      etac_status st = build_tables(c, &c->model, s);   // builds the table if now needed
+      if (st != ETAC_OK) {
+        c->omega_pref = old;
+        return st;
+      }
+    }
+  }
   if (c->inst_ready) {
     if ((t->gemm_inst_per_tile != 32 && t->gemm_inst_per_tile != 64) ||
         (t->gemm_tile_order != 0 && t->gemm_tile_order != 1))
@@ -1506,6 +1535,9 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
   r->gemm_tile_order = c->gemm_order;
   r->bwd_node_range = c->r3_range;
   r->front_ctas_per_sm = c->num_sms ? c->front_grid / c->num_sms : 0;
+  r->omega_source = c->omega_pref == 0   ? ETAC_OMEGA_TABLE
+                    : c->omega_pref == 1 ? ETAC_OMEGA_ON_THE_FLY
+                                         : ETAC_OMEGA_AUTO;
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   ETAC_CUDA(c, cudaEventCreate(&e0), "autotune events");
   ETAC_CUDA(c, cudaEventCreate(&e1), "autotune events");
@@ -1571,6 +1603,21 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
       t.front_ctas_per_sm = bestf + 1;
       st = etac_set_tuning(c, &t, stream);
       r->front_ctas_per_sm = t.front_ctas_per_sm;
+    }
+  }
+  if (st == ETAC_OK && c->model.precision == ETAC_PREC_FP32 &&
+      (size_t)c->omega_off[c->T] * sizeof(float) <= kOmegaTableMaxBytes) {
+    // the batched FP32 step: Omega from the table against on the fly
+    const int src[2] = {ETAC_OMEGA_TABLE, ETAC_OMEGA_ON_THE_FLY};
+    for (int k = 0; k < 2 && st == ETAC_OK; ++k) {
+      t.omega_source = src[k];
+      if ((st = etac_set_tuning(c, &t, stream)) != ETAC_OK) break;
+      if ((st = timed(fwd, 2, 5, &r->omega_ms[k])) != ETAC_OK) break;
+    }
+    if (st == ETAC_OK) {
+      t.omega_source = r->omega_ms[1] < r->omega_ms[0] ? ETAC_OMEGA_ON_THE_FLY : ETAC_OMEGA_TABLE;
+      st = etac_set_tuning(c, &t, stream);
+      r->omega_source = t.omega_source;
     }
   }
   if (st == ETAC_OK && grad_disp && c->bwdb_ready && etac::uses_residual(c->model.mode)) {

@@ -10,7 +10,9 @@
 //      outputs f0_i are table entries, so the channel max-pool over them is the first
 //      passive node in the table's per-channel order; global MLP; decoder global half
 //      beta = D1[:, 64:128] g;
-//   3. every passive node: Omega U_a (Eq. 1, Omega from the per-type table) plus
+//   3. every passive node: Omega U_a (Eq. 1, Omega from the per-type table, or evaluated on
+//      the fly, exp(-alpha |p_j - p_i|) with the table's own FP32 expression, when the table
+//      would not fit or is not wanted: pads of per-instance geometry defeat caching) plus
 //      Phi_p = D2 ReLU(h0_i + beta) + b (Eq. 4).
 // The algebra equals the literal network exactly; only rounding order differs.
 #include "etac_common.cuh"
@@ -49,8 +51,9 @@ struct BatchedSmem {
   }
 };
 
-// MESH: the context has mesh objects (the mesh queries are compiled in)
-template <bool MESH>
+// MESH: the context has mesh objects (the mesh queries are compiled in); OTF: Omega on the fly
+// (a.omega is null)
+template <bool MESH, bool OTF>
 __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip && *a.skip) return;
@@ -318,20 +321,38 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 
 
     // ---- 3. passive nodes: Eq. 4
-    const float* Om = a.omega + a.omega_off[ty];
+    const float* Om = OTF ? nullptr : a.omega + a.omega_off[ty];
     for (int i = tid; i < n; i += BT) {
       if (sMask[i]) continue;
       float l0 = 0.f, l1 = 0.f, l2 = 0.f;
       if (uses_propagation(a.mode)) {
-        const float* col = Om + i;
+        if constexpr (OTF) {
+          // Omega_ji = exp(-alpha |p_j - p_i|), the per-type table's expression (bit for bit);
+          // every lane reads the same active node's position (a broadcast load)
+          const float alpha = W[OFF_ALPHA];
+          const float pix = tpos[3 * i], piy = tpos[3 * i + 1], piz = tpos[3 * i + 2];
 #pragma unroll 4
-        for (int aa = 0; aa < m; ++aa) {
-          const int j = sActIdx[aa];
-          const float4 u = sActU[aa];
-          const float w = __ldg(col + (size_t)j * n);
-          l0 = fmaf(w, u.x, l0);
-          l1 = fmaf(w, u.y, l1);
-          l2 = fmaf(w, u.z, l2);
+          for (int aa = 0; aa < m; ++aa) {
+            const int j = sActIdx[aa];
+            const float4 u = sActU[aa];
+            const float dx = tpos[3 * j] - pix, dy = tpos[3 * j + 1] - piy,
+                        dz = tpos[3 * j + 2] - piz;
+            const float w = expf(-alpha * sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))));
+            l0 = fmaf(w, u.x, l0);
+            l1 = fmaf(w, u.y, l1);
+            l2 = fmaf(w, u.z, l2);
+          }
+        } else {
+          const float* col = Om + i;
+#pragma unroll 4
+          for (int aa = 0; aa < m; ++aa) {
+            const int j = sActIdx[aa];
+            const float4 u = sActU[aa];
+            const float w = __ldg(col + (size_t)j * n);
+            l0 = fmaf(w, u.x, l0);
+            l1 = fmaf(w, u.y, l1);
+            l2 = fmaf(w, u.z, l2);
+          }
         }
       }
       if (uses_residual(a.mode)) {
@@ -365,14 +386,19 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 size_t batched_smem_bytes(int nmax, int K) { return BatchedSmem(nmax, K).total; }
 int batched_threads() { return BT; }
 
+template <bool MESH, bool OTF>
+static cudaError_t configure_one(size_t smem) {
+  return cudaFuncSetAttribute(batched_forward_kernel<MESH, OTF>,
+                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+}
+
 static cudaError_t configure(size_t smem) {
   static size_t configured = 0;
   if (smem > configured) {
-    cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel<false>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e == cudaSuccess)
-      e = cudaFuncSetAttribute(batched_forward_kernel<true>,
-                               cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaError_t e = configure_one<false, false>(smem);
+    if (e == cudaSuccess) e = configure_one<true, false>(smem);
+    if (e == cudaSuccess) e = configure_one<false, true>(smem);
+    if (e == cudaSuccess) e = configure_one<true, true>(smem);
     if (e != cudaSuccess) return e;
     configured = smem;
   }
@@ -383,11 +409,21 @@ cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
   size_t smem = batched_smem_bytes(nmax, K);
   cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  int a = 0, b = 0;
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&a, batched_forward_kernel<false>, BT, smem);
+  int occ[4] = {0, 0, 0, 0};
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batched_forward_kernel<false, false>,
+                                                    BT, smem);
   if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, batched_forward_kernel<true>, BT, smem);
-  *blocks_per_sm = a < b ? a : b;   // the grid suits either instantiation
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batched_forward_kernel<true, false>,
+                                                      BT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batched_forward_kernel<false, true>,
+                                                      BT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], batched_forward_kernel<true, true>,
+                                                      BT, smem);
+  int lo = occ[0];
+  for (int k = 1; k < 4; ++k) lo = occ[k] < lo ? occ[k] : lo;
+  *blocks_per_sm = lo;   // the grid suits every instantiation
   return e;
 }
 
@@ -395,10 +431,14 @@ cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t 
   size_t smem = batched_smem_bytes(a.nmax, a.K);
   cudaError_t e = configure(smem);
   if (e != cudaSuccess) return e;
-  if (a.num_meshes > 0)
-    batched_forward_kernel<true><<<grid, BT, smem, s>>>(a);
-  else
-    batched_forward_kernel<false><<<grid, BT, smem, s>>>(a);
+  const bool otf = a.omega == nullptr;
+  if (a.num_meshes > 0) {
+    if (otf) batched_forward_kernel<true, true><<<grid, BT, smem, s>>>(a);
+    else batched_forward_kernel<true, false><<<grid, BT, smem, s>>>(a);
+  } else {
+    if (otf) batched_forward_kernel<false, true><<<grid, BT, smem, s>>>(a);
+    else batched_forward_kernel<false, false><<<grid, BT, smem, s>>>(a);
+  }
   return cudaGetLastError();
 }
 

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(256) tables_omega_kernel(TablesArgs a) {
     const float* pj = a.type_pos + 3 * (size_t)(o + j);
     const float* pi = a.type_pos + 3 * (size_t)(o + i);
     const float dx = pj[0] - pi[0], dy = pj[1] - pi[1], dz = pj[2] - pi[2];
-    const float d = sqrtf(dx * dx + dy * dy + dz * dz);
+    const float d = sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx)));
     const float w = expf(-alpha * d);
     if (a.omega) a.omega[idx] = w;
     if (a.omega_bf16) reinterpret_cast<__nv_bfloat16*>(a.omega_bf16)[idx] = __float2bfloat16_rn(w);

@@ -22,6 +22,7 @@ STATUS_NAMES = {0: "ETAC_OK", 1: "ETAC_ERR_INVALID_ARG", 2: "ETAC_ERR_STATE", 3:
                 7: "ETAC_ERR_UNSUPPORTED", 8: "ETAC_ERR_BOUNDS"}
 MODE_FULL, MODE_LINEAR_ONLY, MODE_RESIDUAL_ONLY, MODE_PENETRATION_ONLY = 0, 1, 2, 3
 PREC_FP32, PREC_BF16 = 0, 1
+OMEGA_AUTO, OMEGA_TABLE, OMEGA_ON_THE_FLY = 0, 1, 2
 ALGO_PLAIN, ALGO_BATCHED = 0, 1
 HIDDEN = 64
 
@@ -64,7 +65,8 @@ class etac_tuning(ctypes.Structure):
                 ("num_bwd", ctypes.c_int32), ("bwd_cand", ctypes.c_int32 * 8),
                 ("bwd_ms", ctypes.c_float * 8), ("front_ctas_per_sm", ctypes.c_int32),
                 ("num_front", ctypes.c_int32), ("front_cand", ctypes.c_int32 * 8),
-                ("front_ms", ctypes.c_float * 8)]
+                ("front_ms", ctypes.c_float * 8), ("omega_source", ctypes.c_int32),
+                ("omega_ms", ctypes.c_float * 2)]
 
 
 class etac_step_out(ctypes.Structure):
@@ -377,7 +379,9 @@ def tuning_dict(t: etac_tuning) -> dict:
             "fwd": [(t.fwd_cand[k][0], t.fwd_cand[k][1], round(t.fwd_ms[k], 4)) for k in range(t.num_fwd)],
             "bwd": [(t.bwd_cand[k], round(t.bwd_ms[k], 4)) for k in range(t.num_bwd)],
             "front_ctas_per_sm": t.front_ctas_per_sm,
-            "front": [(t.front_cand[k], round(t.front_ms[k], 4)) for k in range(t.num_front)]}
+            "front": [(t.front_cand[k], round(t.front_ms[k], 4)) for k in range(t.num_front)],
+            "omega_source": t.omega_source,
+            "omega_ms": [round(t.omega_ms[0], 4), round(t.omega_ms[1], 4)]}
 
 
 def etac_kernel_times(ctx: int) -> dict:
@@ -594,7 +598,7 @@ class TactileSim:
             if key in table:
                 d = table[key]
                 self.set_tuning(d["gemm_inst_per_tile"], d["gemm_tile_order"], d["bwd_node_range"],
-                                d.get("front_ctas_per_sm", 0))
+                                d.get("front_ctas_per_sm", 0), d.get("omega_source", 0))
                 return dict(d, cached=True)
         g = None if grad_disp is None else _device_f32(grad_disp, self.device, 3 * self.N,
                                                        "grad_disp")
@@ -610,10 +614,14 @@ class TactileSim:
             os.replace(tmp, cache)
         return dict(d, cached=False)
 
-    def set_tuning(self, inst_per_tile=64, tile_order=0, bwd_node_range=0, front_ctas_per_sm=0):
+    def set_tuning(self, inst_per_tile=64, tile_order=0, bwd_node_range=0, front_ctas_per_sm=0,
+                   omega_source=0):
+        """Applies tile / block shapes (see etac_tuning in etac.h); ``omega_source`` is one of
+        OMEGA_AUTO, OMEGA_TABLE, OMEGA_ON_THE_FLY (batched FP32 only)."""
         t = etac_tuning()
         t.gemm_inst_per_tile, t.gemm_tile_order, t.bwd_node_range = inst_per_tile, tile_order, bwd_node_range
         t.front_ctas_per_sm = front_ctas_per_sm
+        t.omega_source = omega_source
         etac_set_tuning(self.ctx, t, self.torch.cuda.current_stream(self.device).cuda_stream)
 
     def poll_status(self) -> int:

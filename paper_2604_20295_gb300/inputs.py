@@ -504,6 +504,35 @@ def uneven_scene(num_envs: int, seed: int, max_depth: float = 3.0, max_tilt: flo
     return _pack(types, num_envs, P, K, pad_type, objs, pads, name)
 
 
+def uneven_continuous_scene(num_envs: int, seed: int, max_depth: float = 3.0,
+                            max_tilt: float = 0.35, name: str = "uneven-continuous-pitch") -> Scene:
+    """``uneven_scene`` with a continuous pitch: every pad instance draws its resolution from
+    {8x8, 16x16, 32x32, 64x64} and its own pitch from U[0.5, 2.0] mm, so every pad is its own
+    type (no two share geometry: per-type Omega tables cannot be reused), with 1-3 seeded
+    primitives per env, each pad touching one of them."""
+    rng = np.random.Generator(np.random.PCG64(seed))
+    res = (8, 16, 32, 64)
+    P, K = 6, 3
+    types, objs, pads = [], {}, []
+    for e in range(num_envs):
+        nobj = int(rng.integers(1, 4))
+        placed = []
+        for k in range(nobj):
+            ot, dims = random_object(rng)
+            q = uniform_quat(rng)
+            t = rng.uniform(-40.0, 40.0, 3)
+            objs[e * K + k] = (ot, dims, np.concatenate([t, q]))
+            placed.append((ot, dims, t, q))
+        for s in range(P):
+            r = res[int(rng.integers(len(res)))]
+            ty = flat_pad(r, r, float(rng.uniform(0.5, 2.0)))
+            types.append(ty)
+            ot, dims, t, q = placed[int(rng.integers(nobj))]
+            pads.append(place_pad(rng, ty, ot, dims, t, q, rng.uniform(0.0, max_depth), max_tilt))
+    pad_type = np.arange(num_envs * P, dtype=np.int32)
+    return _pack(types, num_envs, P, K, pad_type, objs, pads, name)
+
+
 def mesh_scene(num_envs: int, seed: int, num_meshes: int = 4, max_depth: float = 3.0,
                max_tilt: float = 0.35, name: str = "hand-mesh") -> Scene:
     """The hand layout of ``hand_scene`` (5 curved 16x32 fingertips + a flat 32x64 palm per

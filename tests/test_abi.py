@@ -84,7 +84,8 @@ def test_binding_constants_match_the_header():
 
     e = _header_enums()
     for name in ("MODE_FULL", "MODE_LINEAR_ONLY", "MODE_RESIDUAL_ONLY", "MODE_PENETRATION_ONLY",
-                 "PREC_FP32", "PREC_BF16", "ALGO_PLAIN", "ALGO_BATCHED"):
+                 "PREC_FP32", "PREC_BF16", "ALGO_PLAIN", "ALGO_BATCHED", "OMEGA_AUTO",
+                 "OMEGA_TABLE", "OMEGA_ON_THE_FLY"):
         assert getattr(X, name) == e[name], name
     for name in ("MODE_FULL", "MODE_LINEAR_ONLY", "MODE_RESIDUAL_ONLY", "MODE_PENETRATION_ONLY"):
         assert getattr(O, name) == e[name], name
