@@ -287,15 +287,23 @@ def bwd_rooflines(ktimes, scene, work, peaks, nsm):
                      (8.2 kFLOP): FP32 ALU;
       GEMMs       -- 6 FLOP per (passive, active) pair each (dL/du_hat and d alpha): tensor;
       outputs     -- read the propagated dL/du_hat and write dL/du_hat, dL/dpen (28 B per
-                     node): HBM.
+                     node): HBM;
+      A3 sums     -- read the per-64-instance partials of each type node and channel once and
+                     write their sums: HBM.
     FP32 ALU peak = SMs x 128 lanes x 2 FLOP x max SM clock."""
     nodes = float(scene.total_nodes)
     npads = float(scene.num_envs * scene.pads_per_env)
     alu = nsm * 128 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    # the A3 sums (decoder reverse, per type node and channel) are reduced from one partial per
+    # group of 64 instances of the type: read every partial once, write the sums (HBM bytes of
+    # the implementation's reduction; the method itself only needs the sums)
+    inst = np.bincount(np.asarray(scene.pad_type), minlength=len(scene.types))
+    tn = np.asarray(scene.type_num_nodes, np.float64)
+    a3_bytes = float((4.0 * H * tn * (np.ceil(inst / 64.0) + 1.0)).sum())
     spec = {"bwd_pad_kernel": ("hbm", 18.0 * nodes + 16.0 * work["active"]),
             "bwd_global_kernel": ("alu", npads * 2.0 * 2 * H * H),
             "bwd_decoder_kernel": ("alu", 896.0 * work["passive"]),
-            "bwd_reduce_a3_kernel": ("hbm", 4.0 * H * nodes),
+            "bwd_reduce_a3_kernel": ("hbm", a3_bytes),
             "bwd_padrev_kernel": ("alu", npads * (2.0 * 2 * H * H + H * 2.0 * (64 + 576 + 192))),
             "bwd_padsum_kernel": ("alu", npads * (2.0 * 2 * H * H + 2.0 * H * H)),
             "prop_gemm_kernel<bwd_u>": ("tensor", 6.0 * work["pairs"]),

@@ -471,7 +471,8 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
     // order of f0.  First step: lane l tests ranks 0..3 of channels l and l + 32, which settles
     // most channels.  Walks are long-tailed (the top of a channel's order can sit inside the
     // contact patch; on the hand workload 1 % of them pass rank 116), so the rest go
-    // warp-wide: 4 channels per batch, 256 ranks per test.
+    // warp-wide: 2 channels per batch, 256 ranks per test (2 measured faster than 4: fewer
+    // registers live across the test).
     {
       const float2* rk = a.ranked + (size_t)H * o;
       const float2* row0 = rk + (size_t)lane * n;
@@ -506,7 +507,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       // to WB channels at a time; lane l tests ranks q0 + 8 l .. + 7 of the node-index order
       // (one 16-byte load per channel), so one test covers 256 ranks
       const int16_t* ord = a.order + (size_t)H * o;
-      constexpr int WB = 4;
+      constexpr int WB = 2;
       while (open) {   // warp-uniform
         int ch[WB];
         bool dn[WB];
