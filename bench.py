@@ -81,31 +81,34 @@ NIN_H = 9 * H
 # dram__bytes_read.sum + dram__bytes_write.sum per launch from one ncu capture of the kernel
 # named, valid only for the source hash recorded with it (null once the kernel changes)
 TRAFFIC = {
-    # hand workload, 4,096 envs, one pass of --metrics dram__bytes_read.sum,dram__bytes_write.sum
-    # (profile_step --outputs count: the bench step's outputs); per stage where a stage is
-    # several kernels
+    # hand workload, 4,096 envs, one pass of --metrics
+    # gpu__time_duration.sum,dram__bytes_read.sum,dram__bytes_write.sum (profile_step --outputs
+    # count: the bench step's outputs; --backward for the reverse stages); per stage where a
+    # stage is several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "4e653f483cc9c777", "bytes": 14.8e6 + 116.7e6},
+                             "sha": "9fa6bda4a56330f6", "bytes": 43.2e6 + 59.2e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "4e653f483cc9c777", "bytes": 6.6e6},
+                            "sha": "9fa6bda4a56330f6", "bytes": 6.5e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                         "sha": "29a5ddf75939fb59", "bytes": 136.4e6 + 127.4e6},
+                         "sha": "d795d4bc8b4db663", "bytes": 136.4e6 + 127.6e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 43.8e6},
+                                "sha": "d795d4bc8b4db663", "bytes": 331.5e6 + 44.2e6},
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                    "sha": "29a5ddf75939fb59", "bytes": 330.9e6 + 0.1e6},
+                                    "sha": "d795d4bc8b4db663", "bytes": 330.8e6 + 0.1e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "090c18348ebdb9dd", "bytes": 250.4e6 + 331.1e6},
+                       "sha": "71d600ef4ad25d5d", "bytes": 250.4e6 + 328.8e6},
     "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "090c18348ebdb9dd", "bytes": 8.8e6},
+                          "sha": "71d600ef4ad25d5d", "bytes": 8.8e6},
+    "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
+                           "sha": "71d600ef4ad25d5d", "bytes": 238.9e6 + 65.9e6},
     "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                             "sha": "090c18348ebdb9dd", "bytes": 75.5e6},
+                             "sha": "71d600ef4ad25d5d", "bytes": 75.5e6 + 0.1e6},
     "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
-                          "sha": "090c18348ebdb9dd", "bytes": 34.3e6 + 52.3e6 + 2.6e6},
+                          "sha": "71d600ef4ad25d5d", "bytes": 52.3e6 + 2.5e6 + 34.2e6 + 0.1e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "090c18348ebdb9dd", "bytes": 102.4e6 + 12.0e6},
+                          "sha": "71d600ef4ad25d5d", "bytes": 102.4e6 + 11.7e6},
     "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                                     "sha": "090c18348ebdb9dd", "bytes": 112.7e6 + 318.2e6 + 30.3e6},
+                                     "sha": "71d600ef4ad25d5d", "bytes": 93.7e6 + 260.8e6 + 30.3e6},
 }
 
 
@@ -113,7 +116,7 @@ TRAFFIC = {
 # --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
 INSTR = {
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "4e653f483cc9c777", "per_node": 138151353 / 9437184},
+                             "sha": "9fa6bda4a56330f6", "per_node": 115785795 / 9437184},
 }
 
 
