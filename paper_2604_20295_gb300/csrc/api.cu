@@ -737,9 +737,9 @@ etac_status build_tables(etac_ctx* c, const etac_model_desc* desc, cudaStream_t 
     etac_status st = setup_bwdb(c, s);
     if (st != ETAC_OK) return st;
   }
-  if (batched && !c->batched_grid) {
+  if (batched) {   // the grid of the instantiation in effect (Omega table or on the fly)
     int per_sm = 0;
-    e = etac::batched_occupancy(c->nmax, c->K, &per_sm);
+    e = etac::batched_occupancy(c->nmax, c->K, c->omega_otf, &per_sm);
     if (e != cudaSuccess) return cuda_fail(c, e, "batched occupancy");
     if (per_sm < 1) return fail(c, ETAC_ERR_UNSUPPORTED, "batched kernel does not fit an SM");
     c->batched_grid = per_sm * c->num_sms;

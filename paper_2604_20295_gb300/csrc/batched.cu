@@ -25,8 +25,8 @@ constexpr int BW = BT / 32;
 
 struct BatchedSmem {
   // byte offsets of every shared array for a given nmax / K
-  size_t w2, b2, w1u, w4, b4, g, beta, red, redi, actu, actidx, mask, warp, po, total;
-  __host__ __device__ BatchedSmem(int nmax, int K) {
+  size_t w2, b2, w1u, w4, b4, g, beta, red, redi, actu, actp, actidx, mask, warp, po, total;
+  __host__ __device__ BatchedSmem(int nmax, int K, bool otf) {
     size_t o = 0;
     auto take = [&](size_t bytes) {
       size_t r = o;
@@ -42,7 +42,8 @@ struct BatchedSmem {
     beta = take(sizeof(float) * H);
     red = take(sizeof(float) * BW * H);
     redi = take(sizeof(int) * BW * H);
-    actu = take(sizeof(float4) * (size_t)nmax);
+    actu = take(sizeof(float4) * (size_t)nmax);     // u_hat (and, on the fly, p.x in w)
+    actp = take(otf ? sizeof(float2) * (size_t)nmax : 0);   // on the fly: p.y, p.z
     actidx = take(sizeof(int16_t) * (size_t)nmax);
     mask = take(sizeof(uint8_t) * (size_t)nmax);
     warp = take(sizeof(int) * (BW + 4));
@@ -58,7 +59,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (a.skip && *a.skip) return;
   __shared__ int s_item;
-  const BatchedSmem L(a.nmax, a.K);
+  const BatchedSmem L(a.nmax, a.K, OTF);
   float* sW2 = reinterpret_cast<float*>(smem + L.w2);
   float* sB2 = reinterpret_cast<float*>(smem + L.b2);
   float* sW1u = reinterpret_cast<float*>(smem + L.w1u);   // [H][4]: weights on u_hat
@@ -69,6 +70,7 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
   float* sRed = reinterpret_cast<float*>(smem + L.red);
   int* sRedI = reinterpret_cast<int*>(smem + L.redi);   // maximising node per (warp, channel)
   float4* sActU = reinterpret_cast<float4*>(smem + L.actu);
+  float2* sActP = reinterpret_cast<float2*>(smem + L.actp);   // OTF only
   int16_t* sActIdx = reinterpret_cast<int16_t*>(smem + L.actidx);
   uint8_t* sMask = reinterpret_cast<uint8_t*>(smem + L.mask);
   int* sWarp = reinterpret_cast<int*>(smem + L.warp);
@@ -168,7 +170,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
         if (c.active) {
           const int slot = m + woff + __popc(bal & lt_mask);
           sActIdx[slot] = (int16_t)i;
-          sActU[slot] = make_float4(c.u[0], c.u[1], c.u[2], 0.f);
+          sActU[slot] = make_float4(c.u[0], c.u[1], c.u[2], OTF ? tpos[3 * i] : 0.f);
+          if (OTF) sActP[slot] = make_float2(tpos[3 * i + 1], tpos[3 * i + 2]);
           float* d = a.disp + 3 * (base + i);
           d[0] = c.u[0];
           d[1] = c.u[1];
@@ -321,40 +324,8 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
 
 
     // ---- 3. passive nodes: Eq. 4
-    const float* Om = OTF ? nullptr : a.omega + a.omega_off[ty];
-    for (int i = tid; i < n; i += BT) {
-      if (sMask[i]) continue;
-      float l0 = 0.f, l1 = 0.f, l2 = 0.f;
-      if (uses_propagation(a.mode)) {
-        if constexpr (OTF) {
-          // Omega_ji = exp(-alpha |p_j - p_i|), the per-type table's expression (bit for bit);
-          // every lane reads the same active node's position (a broadcast load)
-          const float alpha = W[OFF_ALPHA];
-          const float pix = tpos[3 * i], piy = tpos[3 * i + 1], piz = tpos[3 * i + 2];
-#pragma unroll 4
-          for (int aa = 0; aa < m; ++aa) {
-            const int j = sActIdx[aa];
-            const float4 u = sActU[aa];
-            const float dx = tpos[3 * j] - pix, dy = tpos[3 * j + 1] - piy,
-                        dz = tpos[3 * j + 2] - piz;
-            const float w = expf(-alpha * sqrtf(fmaf(dz, dz, fmaf(dy, dy, dx * dx))));
-            l0 = fmaf(w, u.x, l0);
-            l1 = fmaf(w, u.y, l1);
-            l2 = fmaf(w, u.z, l2);
-          }
-        } else {
-          const float* col = Om + i;
-#pragma unroll 4
-          for (int aa = 0; aa < m; ++aa) {
-            const int j = sActIdx[aa];
-            const float4 u = sActU[aa];
-            const float w = __ldg(col + (size_t)j * n);
-            l0 = fmaf(w, u.x, l0);
-            l1 = fmaf(w, u.y, l1);
-            l2 = fmaf(w, u.z, l2);
-          }
-        }
-      }
+    // residual of passive node i and the store (l: its propagated term)
+    auto finish = [&](int i, float l0, float l1, float l2) {
       if (uses_residual(a.mode)) {
         float r0 = sB4[0], r1 = sB4[1], r2 = sB4[2];
         const float4* hrow = reinterpret_cast<const float4*>(a.h0tab + (size_t)(o + i) * H);
@@ -379,66 +350,119 @@ __global__ void __launch_bounds__(BT, 2) batched_forward_kernel(BatchedArgs a) {
       d[0] = l0;
       d[1] = l1;
       d[2] = l2;
+    };
+    if constexpr (OTF) {
+      // Omega_ji = exp(-alpha |p_j - p_i|), the per-type table's expression (bit for bit),
+      // with the active node's position staged in shared memory beside its u_hat.  Each thread
+      // takes two passive nodes at a time (two independent chains; each node still sums its
+      // active nodes in order)
+      const float alpha = W[OFF_ALPHA];
+      for (int i = tid; i < n; i += 2 * BT) {
+        const int i2 = i + BT;
+        const bool pa = !sMask[i], pb = i2 < n && !sMask[i2];
+        if (!pa && !pb) continue;
+        float a0 = 0.f, a1 = 0.f, a2 = 0.f, b0 = 0.f, b1 = 0.f, b2 = 0.f;
+        if (uses_propagation(a.mode)) {
+          const int ib = pb ? i2 : i;
+          const float pax = tpos[3 * i], pay = tpos[3 * i + 1], paz = tpos[3 * i + 2];
+          const float pbx = tpos[3 * ib], pby = tpos[3 * ib + 1], pbz = tpos[3 * ib + 2];
+#pragma unroll 2
+          for (int aa = 0; aa < m; ++aa) {
+            const float4 u = sActU[aa];
+            const float2 pyz = sActP[aa];
+            const float dxa = u.w - pax, dya = pyz.x - pay, dza = pyz.y - paz;
+            const float dxb = u.w - pbx, dyb = pyz.x - pby, dzb = pyz.y - pbz;
+            const float wa = expf(-alpha * sqrtf(fmaf(dza, dza, fmaf(dya, dya, dxa * dxa))));
+            const float wb = expf(-alpha * sqrtf(fmaf(dzb, dzb, fmaf(dyb, dyb, dxb * dxb))));
+            a0 = fmaf(wa, u.x, a0);
+            a1 = fmaf(wa, u.y, a1);
+            a2 = fmaf(wa, u.z, a2);
+            b0 = fmaf(wb, u.x, b0);
+            b1 = fmaf(wb, u.y, b1);
+            b2 = fmaf(wb, u.z, b2);
+          }
+        }
+        if (pa) finish(i, a0, a1, a2);
+        if (pb) finish(i2, b0, b1, b2);
+      }
+    } else {
+      const float* Om = a.omega + a.omega_off[ty];
+      for (int i = tid; i < n; i += BT) {
+        if (sMask[i]) continue;
+        float l0 = 0.f, l1 = 0.f, l2 = 0.f;
+        if (uses_propagation(a.mode)) {
+          const float* col = Om + i;
+#pragma unroll 4
+          for (int aa = 0; aa < m; ++aa) {
+            const int j = sActIdx[aa];
+            const float4 u = sActU[aa];
+            const float w = __ldg(col + (size_t)j * n);
+            l0 = fmaf(w, u.x, l0);
+            l1 = fmaf(w, u.y, l1);
+            l2 = fmaf(w, u.z, l2);
+          }
+        }
+        finish(i, l0, l1, l2);
+      }
     }
   }
 }
 
-size_t batched_smem_bytes(int nmax, int K) { return BatchedSmem(nmax, K).total; }
+size_t batched_smem_bytes(int nmax, int K, bool otf) { return BatchedSmem(nmax, K, otf).total; }
 int batched_threads() { return BT; }
 
 template <bool MESH, bool OTF>
-static cudaError_t configure_one(size_t smem) {
-  return cudaFuncSetAttribute(batched_forward_kernel<MESH, OTF>,
-                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-}
-
-static cudaError_t configure(size_t smem) {
+static cudaError_t configure_one(int nmax, int K) {
   static size_t configured = 0;
-  if (smem > configured) {
-    cudaError_t e = configure_one<false, false>(smem);
-    if (e == cudaSuccess) e = configure_one<true, false>(smem);
-    if (e == cudaSuccess) e = configure_one<false, true>(smem);
-    if (e == cudaSuccess) e = configure_one<true, true>(smem);
-    if (e != cudaSuccess) return e;
-    configured = smem;
-  }
-  return cudaSuccess;
-}
-
-cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm) {
-  size_t smem = batched_smem_bytes(nmax, K);
-  cudaError_t e = configure(smem);
-  if (e != cudaSuccess) return e;
-  int occ[4] = {0, 0, 0, 0};
-  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[0], batched_forward_kernel<false, false>,
-                                                    BT, smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[1], batched_forward_kernel<true, false>,
-                                                      BT, smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[2], batched_forward_kernel<false, true>,
-                                                      BT, smem);
-  if (e == cudaSuccess)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ[3], batched_forward_kernel<true, true>,
-                                                      BT, smem);
-  int lo = occ[0];
-  for (int k = 1; k < 4; ++k) lo = occ[k] < lo ? occ[k] : lo;
-  *blocks_per_sm = lo;   // the grid suits every instantiation
+  const size_t smem = BatchedSmem(nmax, K, OTF).total;
+  if (smem <= configured) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(batched_forward_kernel<MESH, OTF>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e == cudaSuccess) configured = smem;
   return e;
 }
 
+template <bool OTF>
+static cudaError_t occupancy_pair(int nmax, int K, int* per_sm) {
+  const size_t smem = BatchedSmem(nmax, K, OTF).total;
+  cudaError_t e = configure_one<false, OTF>(nmax, K);
+  if (e == cudaSuccess) e = configure_one<true, OTF>(nmax, K);
+  int x = 0, y = 0;
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&x, batched_forward_kernel<false, OTF>, BT, smem);
+  if (e == cudaSuccess)
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&y, batched_forward_kernel<true, OTF>, BT, smem);
+  *per_sm = x < y ? x : y;   // the grid suits the mesh and the primitive instantiation
+  return e;
+}
+
+cudaError_t batched_occupancy(int nmax, int K, bool otf, int* blocks_per_sm) {
+  return otf ? occupancy_pair<true>(nmax, K, blocks_per_sm)
+             : occupancy_pair<false>(nmax, K, blocks_per_sm);
+}
+
 cudaError_t launch_batched_forward(const BatchedArgs& a, int grid, cudaStream_t s) {
-  size_t smem = batched_smem_bytes(a.nmax, a.K);
-  cudaError_t e = configure(smem);
-  if (e != cudaSuccess) return e;
   const bool otf = a.omega == nullptr;
+  const size_t smem = BatchedSmem(a.nmax, a.K, otf).total;
+  cudaError_t e = cudaSuccess;
   if (a.num_meshes > 0) {
-    if (otf) batched_forward_kernel<true, true><<<grid, BT, smem, s>>>(a);
-    else batched_forward_kernel<true, false><<<grid, BT, smem, s>>>(a);
+    if (otf) {
+      if ((e = configure_one<true, true>(a.nmax, a.K)) == cudaSuccess)
+        batched_forward_kernel<true, true><<<grid, BT, smem, s>>>(a);
+    } else {
+      if ((e = configure_one<true, false>(a.nmax, a.K)) == cudaSuccess)
+        batched_forward_kernel<true, false><<<grid, BT, smem, s>>>(a);
+    }
   } else {
-    if (otf) batched_forward_kernel<false, true><<<grid, BT, smem, s>>>(a);
-    else batched_forward_kernel<false, false><<<grid, BT, smem, s>>>(a);
+    if (otf) {
+      if ((e = configure_one<false, true>(a.nmax, a.K)) == cudaSuccess)
+        batched_forward_kernel<false, true><<<grid, BT, smem, s>>>(a);
+    } else {
+      if ((e = configure_one<false, false>(a.nmax, a.K)) == cudaSuccess)
+        batched_forward_kernel<false, false><<<grid, BT, smem, s>>>(a);
+    }
   }
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 

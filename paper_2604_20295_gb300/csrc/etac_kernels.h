@@ -174,9 +174,9 @@ cudaError_t front_occupancy(int nmax, int K, int* blocks_per_sm);
 cudaError_t launch_front_contact(const FrontArgs& a, int grid, cudaStream_t s);
 cudaError_t launch_front_global(const FrontArgs& a, int num_sms, cudaStream_t s);
 
-size_t batched_smem_bytes(int nmax, int K);
+size_t batched_smem_bytes(int nmax, int K, bool otf = false);
 int batched_threads();
-cudaError_t batched_occupancy(int nmax, int K, int* blocks_per_sm);
+cudaError_t batched_occupancy(int nmax, int K, bool otf, int* blocks_per_sm);
 
 }  // namespace etac
 

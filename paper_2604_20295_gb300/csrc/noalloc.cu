@@ -208,7 +208,7 @@ extern "C" etac_status etac_step_forward_noalloc(const etac_noalloc_pads* pads, 
     nsm = g_num_sms[dev];
   }
   int per_sm = 0;
-  e = etac::batched_occupancy(nmax, pads->max_objects, &per_sm);
+  e = etac::batched_occupancy(nmax, pads->max_objects, false, &per_sm);
   if (e != cudaSuccess)
     return noalloc_fail(ETAC_ERR_CUDA, std::string("etac_step_forward_noalloc: occupancy query: ") +
                                            cudaGetErrorString(e));
