@@ -1039,15 +1039,23 @@ def main():
         ipn = instr_per_node("front_contact_kernel")
         if ipn is not None:
             # the bound that explains this kernel: instruction issue (one warp instruction per
-            # scheduler per cycle: SMs x 4 x max SM clock)
+            # scheduler per cycle: SMs x 4 x max SM clock); its tensor figure stays beside it
             issue_peak = nsm * 4 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e9
             ach = ipn * nodes / t / 1e9
-            per["front_contact_kernel"]["issue"] = {
+            tensor = per["front_contact_kernel"]
+            per["front_contact_kernel"] = {
                 "bound": "issue", "achieved": ach, "peak": issue_peak,
                 "unit": "G warp-instructions/s", "frac": ach / issue_peak,
+                "traffic": tensor["traffic"], "ms": tensor["ms"],
                 "warp_instructions_per_node": ipn,
                 "peak_source": f"derived: {nsm} SMs x 4 schedulers x "
-                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz"}
+                               f"{peaks.get('sm_max_mhz', 2070.0)} MHz",
+                "note": "instruction issue binds this kernel (contact classification, the "
+                        "mma.sync encoder drains and the max-pool walk); achieved = ncu warp "
+                        "instructions per node x nodes / event time; the rest of its cycles "
+                        "are latency (instruction fetch and mma.sync dependency stalls)",
+                "tensor": {k: tensor[k] for k in ("bound", "achieved", "peak", "unit", "frac",
+                                                  "peak_source", "note")}}
         t = kern["prop_gemm_kernel"]["ms_per_launch"] / 1e3
         alg = 6.0 * work["pairs"] + 2.0 * 3 * H * work["passive"]
         exe = executed_gemm_flops(scene)
