@@ -28,7 +28,9 @@
 //   R5 bwd_typenode_kernel (64 type nodes per CTA): the decoder path's encoder reverse from
 //      A3 (dD1_f, dE2, dE1, biases);
 //   R6 the propagation reverse on tensor cores (prop_gemm.cu, backward modes);
-//   R7 bwd_pose_kernel (warp per pad): outputs dL/du_hat, dL/dpen and the pose partials.
+//   R7 bwd_fill_kernel (streaming): outputs dL/du_hat and the passive dL/dpen;
+//      bwd_pose_kernel (warp per pad, the pad's active nodes compacted into a queue so every
+//      lane takes one): the active dL/dpen and the pose partials.
 // Every sum runs in a fixed order (static work assignment, partials reduced in index order),
 // so the result is bitwise repeatable.
 #include <cuda_bf16.h>
@@ -1250,17 +1252,52 @@ __global__ void __launch_bounds__(256) bwd_typenode_kernel(BwdBatchedArgs a) {
 // ----------------------------------------------------------------------------- R7
 // warp per pad: dL/du_hat and dL/dpen per node, and the pose partials (active nodes in
 // node order)
+// R7a: dL/du_hat (the propagated sum for active nodes, 0 for passive ones) and, for passive
+// nodes, dL/dpen = 0: a streaming pass over every node, warp per pad (the active nodes'
+// penetration gradients come from R7b)
+__global__ void __launch_bounds__(256) bwd_fill_kernel(BwdBatchedArgs a) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
+  for (int pad = blockIdx.x * wpb + warp; pad < a.num_items; pad += gridDim.x * wpb) {
+    const int ty = a.pad_type[pad];
+    const int n = a.type_off[ty + 1] - a.type_off[ty];
+    const long long base = a.pad_off[pad];
+    const int m = a.pad_m[pad];
+    const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+    for (int i = lane; i < n; i += 32) {
+      const bool act = m > 0 && ((bits[i >> 5] >> (i & 31)) & 1u);
+      if (a.grad_uhat) {
+        float4 d = make_float4(0.f, 0.f, 0.f, 0.f);
+        if (act) d = a.ws_du[base + i];
+        float* g = a.grad_uhat + 3 * (base + i);
+        g[0] = d.x;
+        g[1] = d.y;
+        g[2] = d.z;
+      }
+      if (a.grad_pen && !act) a.grad_pen[base + i] = 0.f;
+    }
+  }
+}
+
+// R7b: the active nodes' dL/dpen and pose partials through the SDF gradient and Hessian, warp
+// per pad.  The pad's active nodes are compacted (in node order) into a per-warp queue, so all
+// 32 lanes of a pass take one active node each; lane l takes queue entries l, l + 32, ... of the
+// pad, and the partials are summed over lanes in a fixed order.
+constexpr int POSE_Q = 64;   // per-warp queue of active nodes (<= 31 pending + 32 of a word)
 __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
   PadObj* spo = reinterpret_cast<PadObj*>(smem) + (size_t)warp * a.K;
+  int16_t* sq = reinterpret_cast<int16_t*>(smem + sizeof(PadObj) * (size_t)wpb * a.K) +
+                (size_t)warp * POSE_Q;
+  const unsigned lt = (1u << lane) - 1u;
   for (int pad = blockIdx.x * wpb + warp; pad < a.num_items; pad += gridDim.x * wpb) {
+    const int m = a.pad_m[pad];
+    if (m == 0) continue;   // warp-uniform
     const int ty = a.pad_type[pad];
     const int o = a.type_off[ty];
     const int n = a.type_off[ty + 1] - o;
     const int env = pad / a.P;
     const long long base = a.pad_off[pad];
-    const int m = a.pad_m[pad];
     {
       const int* src = reinterpret_cast<const int*>(a.padobj + (size_t)pad * a.K);
       int* dst = reinterpret_cast<int*>(spo);
@@ -1278,13 +1315,12 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
     for (int k = 0; k < MAX_K; ++k)
 #pragma unroll
       for (int q = 0; q < 6; ++q) pose[k][q] = 0.f;
-    for (int i = lane; i < n; i += 32) {
-      const bool act = m > 0 && ((bits[i >> 5] >> (i & 31)) & 1u);
-      float3 du = make_float3(0.f, 0.f, 0.f);
-      float pen = 0.f;
-      if (act) {
+    // one active node per lane (lane < cnt): its penetration gradient and pose partials
+    auto run = [&](int cnt) {
+      if (lane < cnt) {
+        const int i = sq[lane];
         const float4 d = a.ws_du[base + i];
-        du = make_float3(d.x, d.y, d.z);
+        const float3 du = make_float3(d.x, d.y, d.z);
         const float3 p = make_float3(a.type_pos[3 * (size_t)(o + i)], a.type_pos[3 * (size_t)(o + i) + 1],
                                      a.type_pos[3 * (size_t)(o + i) + 2]);
         const float3 nr = make_float3(a.type_nrm[3 * (size_t)(o + i)], a.type_nrm[3 * (size_t)(o + i) + 1],
@@ -1293,7 +1329,6 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
         pg.k = -1;
         pg.pen = 0.f;
         if (!given) pg = node_pose_grad(spo, a.K, p, nr, du, Rp, pp, a.obj_pose + 7 * (size_t)env * a.K);
-        pen = pg.pen;
 #pragma unroll
         for (int k = 0; k < MAX_K; ++k) {
           if (k != pg.k) continue;
@@ -1303,15 +1338,29 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
             pose[k][3 + q] += pg.w[q];
           }
         }
+        if (a.grad_pen) a.grad_pen[base + i] = pg.pen;
       }
-      if (a.grad_uhat) {
-        float* g = a.grad_uhat + 3 * (base + i);
-        g[0] = du.x;
-        g[1] = du.y;
-        g[2] = du.z;
+      __syncwarp();
+    };
+    int npend = 0;   // warp-uniform
+    const int nwords = (n + 31) >> 5;
+    for (int w = 0; w < nwords; ++w) {
+      const uint32_t bw = bits[w];   // every lane reads the same word
+      if (bw & (1u << lane)) sq[npend + __popc(bw & lt)] = (int16_t)(32 * w + lane);
+      npend += __popc(bw);
+      __syncwarp();
+      if (npend >= 32) {
+        run(32);
+        // the rest of the queue moves to the front (at most 31 entries)
+        const int rest = npend - 32;
+        const int16_t v = lane < rest ? sq[32 + lane] : (int16_t)0;
+        __syncwarp();
+        if (lane < rest) sq[lane] = v;
+        npend = rest;
+        __syncwarp();
       }
-      if (a.grad_pen) a.grad_pen[base + i] = pen;
     }
+    if (npend > 0) run(npend);
     for (int k = 0; k < a.K; ++k)
 #pragma unroll
       for (int q = 0; q < 6; ++q) {
@@ -1324,6 +1373,11 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
         if (lane == 0) a.pose_part[((size_t)pad * a.K + k) * 6 + q] = v;
       }
     __syncwarp();
+  }
+  // pads without contact: zero pose partials (every warp covers its own pads)
+  for (int pad = blockIdx.x * wpb + warp; pad < a.num_items; pad += gridDim.x * wpb) {
+    if (a.pad_m[pad] != 0) continue;
+    for (int e = lane; e < 6 * a.K; e += 32) a.pose_part[(size_t)pad * a.K * 6 + e] = 0.f;
   }
 }
 
@@ -1442,7 +1496,8 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       break;
     }
     case BWD_STAGE_POSE:
-      bwd_pose_kernel<<<l.r7_grid, 256, sizeof(PadObj) * 8 * a.K, s>>>(a);
+      bwd_fill_kernel<<<l.r7_grid, 256, 0, s>>>(a);
+      bwd_pose_kernel<<<l.r7_grid, 256, (sizeof(PadObj) * a.K + sizeof(int16_t) * POSE_Q) * 8, s>>>(a);
       break;
     case BWD_STAGE_PARAMS:
       if (grad_params) bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
