@@ -135,14 +135,17 @@ size_t etac_param_count(const etac_model_desc* desc);
 /* Total node count N of a pad description (0 if invalid). */
 int64_t etac_total_nodes(const etac_pads_desc* desc);
 
-/* Create a context for a fixed batch of pads.  Copies the geometry to the device and
- * allocates every buffer a later step needs (steps never allocate).  `stream` orders the
- * copies.  On success *out owns device memory until etac_destroy. */
+/* Create a context for a fixed batch of pads: the surface nodes P and their normals N of
+ * every pad type (Sec. III-A: the sensor skin's node set, undeformed, pad frame) and the type
+ * of each pad instance.  Copies the geometry to the device and allocates every buffer a later
+ * step needs (steps never allocate).  `stream` orders the copies.  On success *out owns
+ * device memory until etac_destroy. */
 etac_status etac_create_pads(etac_ctx** out, const etac_pads_desc* desc, void* stream);
 
-/* Set (or replace) the propagation model.  `params` is a device FP32 vector of
- * etac_param_count(desc) floats, copied on `stream` (the caller may reuse it once the call
- * returns).  Synchronises `stream` once to validate alpha (finite and > 0, else
+/* Set (or replace) the propagation model: the decay rate alpha of Eq. 1 and the residual
+ * network of Sec. III-A 2 (encoder, max-pool, global MLP, decoder; Eq. 4 sums the two terms).
+ * `params` is a device FP32 vector of etac_param_count(desc) floats, copied on `stream` (the
+ * caller may reuse it once the call returns).  Synchronises `stream` once to validate alpha (finite and > 0, else
  * ETAC_ERR_INVALID_ARG and the previous model stays).  Rebuilds the per-pad-type tables of
  * the batched algorithm.  Not capturable in a CUDA graph. */
 etac_status etac_set_model(etac_ctx* ctx, const etac_model_desc* desc, const float* params,
