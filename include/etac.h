@@ -237,7 +237,7 @@ etac_status etac_enable_timing(etac_ctx* ctx, int32_t enable);
 etac_status etac_kernel_times(etac_ctx* ctx, etac_kernel_time* out, int32_t max, int32_t* count);
 
 /* ---- Tile and block shapes picked by measurement (the paper has no counterpart).
- * gemm_inst_per_tile: pad instances per tile of the BF16 propagation GEMM (32 or 64; the
+ * gemm_inst_per_tile: pad instances per tile of the BF16 propagation GEMM (32, 64 or 80; the
  * tile is 128 node rows x 3 * that many columns); gemm_tile_order: 0 walks node-row tiles
  * innermost (tiles running together share a B tile in L2), 1 walks instance groups
  * innermost (they share an Omega row block); bwd_node_range: nodes per work unit of the

@@ -109,7 +109,7 @@ struct etac_ctx {
   int front_grid = 0, gemm_grid = 0, num_tiles = 0, tiles_cap = 0;
   int front_max_per_sm = 0;   // occupancy limit of the front kernel (CTAs per SM)
   long long mask_words = 0;   // contact-bit words of all pads (instance order)
-  int gemm_gi = 64;      // instances per GEMM tile (tuned: 32 or 64)
+  int gemm_gi = 64;      // instances per GEMM tile (tuned: 32, 64 or 80)
   int gemm_order = 0;    // GEMM tile order (tuned)
   int r3_range = 0;      // decoder-reverse node range (0: from the SM count; tuned)
   size_t r3g_cap = 0, spart_cap = 0, d2_cap = 0;
@@ -1502,9 +1502,10 @@ etac_status etac_set_tuning(etac_ctx* c, const etac_tuning* t, void* stream) {
     }
   }
   if (c->inst_ready) {
-    if ((t->gemm_inst_per_tile != 32 && t->gemm_inst_per_tile != 64) ||
+    if ((t->gemm_inst_per_tile != 32 && t->gemm_inst_per_tile != 64 &&
+         t->gemm_inst_per_tile != 80) ||
         (t->gemm_tile_order != 0 && t->gemm_tile_order != 1))
-      return fail(c, ETAC_ERR_INVALID_ARG, "GEMM shape: 32 or 64 instances, order 0 or 1");
+      return fail(c, ETAC_ERR_INVALID_ARG, "GEMM shape: 32, 64 or 80 instances, order 0 or 1");
     c->gemm_gi = t->gemm_inst_per_tile;
     c->gemm_order = t->gemm_tile_order;
     etac_status st = build_tiles(c, s);
@@ -1564,9 +1565,9 @@ etac_status etac_autotune(etac_ctx* c, const etac_step_in* in, const etac_step_o
   };
   etac_tuning t = *r;
   if (c->bf16_ready && c->model.precision == ETAC_PREC_BF16) {
-    const int cand[4][2] = {{64, 0}, {64, 1}, {32, 0}, {32, 1}};
+    const int cand[6][2] = {{64, 0}, {64, 1}, {80, 0}, {80, 1}, {32, 0}, {32, 1}};
     int best = -1;
-    for (int k = 0; k < 4 && st == ETAC_OK; ++k) {
+    for (int k = 0; k < 6 && st == ETAC_OK; ++k) {
       t.gemm_inst_per_tile = cand[k][0];
       t.gemm_tile_order = cand[k][1];
       t.bwd_node_range = 0;

@@ -517,6 +517,11 @@ cudaError_t launch_prop_gemm(const GemmParams& p, int grid, cudaStream_t s, int 
     if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA, 32>(p, grid, s);
     return launch_mode<GEMM_FWD, 32>(p, grid, s);
   }
+  if (gi == 80) {
+    if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U, 80>(p, grid, s);
+    if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA, 80>(p, grid, s);
+    return launch_mode<GEMM_FWD, 80>(p, grid, s);
+  }
   if (gi != 64) return cudaErrorInvalidValue;
   if (mode == GEMM_BWD_U) return launch_mode<GEMM_BWD_U, 64>(p, grid, s);
   if (mode == GEMM_BWD_ALPHA) return launch_mode<GEMM_BWD_ALPHA, 64>(p, grid, s);

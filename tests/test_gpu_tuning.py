@@ -1,5 +1,5 @@
 """GPU tests of the measured tile / block shape choice (etac_autotune, etac_set_tuning): every
-propagation-GEMM shape (32 or 64 instances per tile, both tile orders) and every node range
+propagation-GEMM shape (32, 64 or 80 instances per tile, both tile orders) and every node range
 of the reverse mode's decoder stage must give the oracle's results within the same bounds as
 the default shapes; the autotuner returns candidates it timed and leaves a valid choice in
 effect."""
@@ -54,7 +54,7 @@ def _backward_check(sim, sc, th, G, mask):
     PT.assert_grads_close(got, ref, I.param_slices())
 
 
-@pytest.mark.parametrize("gi,order", [(64, 0), (64, 1), (32, 0), (32, 1)])
+@pytest.mark.parametrize("gi,order", [(64, 0), (64, 1), (80, 0), (80, 1), (32, 0), (32, 1)])
 def test_every_gemm_shape_matches_oracle(gi, order):
     sc = _scene()
     th = I.make_params(1)
@@ -95,7 +95,7 @@ def test_autotune_picks_a_timed_candidate_and_stays_correct():
         sim.set_model(th, X.MODE_FULL, X.PREC_BF16, X.ALGO_BATCHED)
         t = sim.autotune(torch.as_tensor(np.asarray(G, np.float32)).cuda())
         print("autotune:", t)
-        assert len(t["fwd"]) == 4 and len(t["bwd"]) == 4
+        assert len(t["fwd"]) == 6 and len(t["bwd"]) == 4
         best = min(t["fwd"], key=lambda c: c[2])
         assert (t["gemm_inst_per_tile"], t["gemm_tile_order"]) == best[:2]
         assert t["bwd_node_range"] == min(t["bwd"], key=lambda c: c[1])[0]
