@@ -894,6 +894,19 @@ def main():
         cuts = [rows * c // (2 * ncs) for c in range(2 * ncs + 1)]   # 2 chunks per copy stream
         ready = [torch.cuda.Event() for _ in range(2)]
         done = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
+        # the link alone: the same read-back with no step beside it (3 copies, events on the
+        # copy stream), so that the end-to-end rate can be put against what the link carries
+        torch.cuda.synchronize()
+        l0 = torch.cuda.Event(enable_timing=True)
+        l1 = torch.cuda.Event(enable_timing=True)
+        with torch.cuda.stream(css[0]):
+            h_out[0].copy_(d_out[0], non_blocking=True)
+            l0.record(css[0])
+            for _ in range(3):
+                h_out[0].copy_(d_out[0], non_blocking=True)
+            l1.record(css[0])
+        torch.cuda.synchronize()
+        link_gbs = 3 * d2h / (l0.elapsed_time(l1) * 1e6)
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -926,7 +939,9 @@ def main():
                "d2h_bytes_per_step": d2h, "steps": ke, "ms_per_step": 1e3 * e2e_s / ke,
                "pipelining": f"read-back of step k overlaps step k + 1 (two output buffers, "
                              f"{ncs} copy stream(s), {2 * ncs} chunks)",
-               "readback_matches_device": same}
+               "readback_matches_device": same,
+               "d2h_link_gbs": link_gbs,
+               "d2h_frac_of_link": d2h * ke / e2e_s / 1e9 / link_gbs}
 
     # ---- the other rungs on the same GPU and scene (the metric compares BF16 batched with
     # FP32 plain; FP32 batched is the intermediate rung)

@@ -142,53 +142,66 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
   uint32_t ah[3][4][4];
 #pragma unroll
   for (int s4 = 0; s4 < 4; ++s4) {
+    // the two n tiles of this k step as independent MMA chains, interleaved
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+#pragma unroll
+    for (int ks = 0; ks < 2; ++ks)
+#pragma unroll
+      for (int part = 0; part < 3; ++part)
+#pragma unroll
+        for (int t = 0; t < 2; ++t) {
+          const uint2 bb = sW1f[((part * 2 + ks) * 8 + 2 * s4 + t) * 32 + lane];
+          sm100::mma_bf16_16816(acc[t], ax[ks], bb.x, bb.y, acc[t]);
+        }
     float h[2][4];
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int nt = 2 * s4 + t;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
+    for (int t = 0; t < 2; ++t)
 #pragma unroll
-      for (int ks = 0; ks < 2; ++ks)
-#pragma unroll
-        for (int part = 0; part < 3; ++part) {
-          const uint2 bb = sW1f[((part * 2 + ks) * 8 + nt) * 32 + lane];
-          sm100::mma_bf16_16816(acc, ax[ks], bb.x, bb.y, acc);
-        }
-#pragma unroll
-      for (int q = 0; q < 4; ++q) h[t][q] = relu(acc[q]);
-    }
+      for (int q = 0; q < 4; ++q) h[t][q] = relu(acc[t][q]);
     split3(h[0][0], h[0][1], ah[0][s4][0], ah[1][s4][0], ah[2][s4][0]);
     split3(h[0][2], h[0][3], ah[0][s4][1], ah[1][s4][1], ah[2][s4][1]);
     split3(h[1][0], h[1][1], ah[0][s4][2], ah[1][s4][2], ah[2][s4][2]);
     split3(h[1][2], h[1][3], ah[0][s4][3], ah[1][s4][3], ah[2][s4][3]);
   }
+  // E2 in two halves of four n tiles: four independent MMA chains per half, interleaved; each
+  // chain keeps its order (k steps ascending, smallest products first)
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int half = 0; half < 2; ++half) {
+    float acc[4][4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
 #pragma unroll
     for (int s4 = 0; s4 < 4; ++s4) {
-      const uint2 b0 = sW2f[((0 * 8 + nt) * 4 + s4) * 32 + lane];
-      const uint2 b1 = sW2f[((1 * 8 + nt) * 4 + s4) * 32 + lane];
-      const uint2 b2 = sW2f[((2 * 8 + nt) * 4 + s4) * 32 + lane];
-      // smallest products first
-      sm100::mma_bf16_16816(acc, ah[2][s4], b0.x, b0.y, acc);
-      sm100::mma_bf16_16816(acc, ah[1][s4], b1.x, b1.y, acc);
-      sm100::mma_bf16_16816(acc, ah[0][s4], b2.x, b2.y, acc);
-      sm100::mma_bf16_16816(acc, ah[1][s4], b0.x, b0.y, acc);
-      sm100::mma_bf16_16816(acc, ah[0][s4], b1.x, b1.y, acc);
-      sm100::mma_bf16_16816(acc, ah[0][s4], b0.x, b0.y, acc);
+#pragma unroll
+      for (int pr = 0; pr < 6; ++pr) {
+        // products (A part, W part): (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+        const int ap = pr == 0 ? 2 : (pr == 1 || pr == 3 ? 1 : 0);
+        const int wp = pr == 2 ? 2 : (pr == 1 || pr == 4 ? 1 : 0);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int nt = 4 * half + j;
+          const uint2 bw = sW2f[((wp * 8 + nt) * 4 + s4) * 32 + lane];
+          sm100::mma_bf16_16816(acc[j], ah[ap][s4], bw.x, bw.y, acc[j]);
+        }
+      }
     }
 #pragma unroll
-    for (int e = 0; e < 2; ++e) {
-      const float b = sB2[8 * nt + 2 * tig + e];
-      const float f0 = relu(acc[e] + b), f1 = relu(acc[2 + e] + b);
-      if (v0 && (f0 > fv[nt][e] || (f0 == fv[nt][e] && n0 < fi[nt][e]))) {
-        fv[nt][e] = f0;
-        fi[nt][e] = n0;
-      }
-      if (v1 && (f1 > fv[nt][e] || (f1 == fv[nt][e] && n1 < fi[nt][e]))) {
-        fv[nt][e] = f1;
-        fi[nt][e] = n1;
+    for (int j = 0; j < 4; ++j) {
+      const int nt = 4 * half + j;
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const float b = sB2[8 * nt + 2 * tig + e];
+        const float f0 = relu(acc[j][e] + b), f1 = relu(acc[j][2 + e] + b);
+        if (v0 && (f0 > fv[nt][e] || (f0 == fv[nt][e] && n0 < fi[nt][e]))) {
+          fv[nt][e] = f0;
+          fi[nt][e] = n0;
+        }
+        if (v1 && (f1 > fv[nt][e] || (f1 == fv[nt][e] && n1 < fi[nt][e]))) {
+          fv[nt][e] = f1;
+          fi[nt][e] = n1;
+        }
       }
     }
   }
@@ -1281,14 +1294,30 @@ __global__ void __launch_bounds__(256) bwd_fill_kernel(BwdBatchedArgs a) {
 // R7b: the active nodes' dL/dpen and pose partials through the SDF gradient and Hessian, warp
 // per pad.  The pad's active nodes are compacted (in node order) into a per-warp queue, so all
 // 32 lanes of a pass take one active node each; lane l takes queue entries l, l + 32, ... of the
-// pad, and the partials are summed over lanes in a fixed order.
+// pad and adds its terms, in that order, to its own column of the warp's pose accumulators in
+// shared memory ([object][6][lane]: no bank conflicts, no registers held per object slot); the
+// columns are then summed over lanes in a fixed order.
 constexpr int POSE_Q = 64;   // per-warp queue of active nodes (<= 31 pending + 32 of a word)
-__global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
+constexpr int POSE_T = 128;  // threads per CTA (95 registers: 5 CTAs per SM)
+struct PoseSmem {
+  size_t po, q, acc, warp_bytes;
+  __host__ __device__ explicit PoseSmem(int K) {
+    po = 0;
+    q = sizeof(PadObj) * (size_t)K;
+    acc = (q + sizeof(int16_t) * POSE_Q + 15) & ~size_t(15);
+    warp_bytes = acc + sizeof(float) * 6 * 32 * (size_t)K;
+  }
+  __host__ __device__ size_t total() const { return warp_bytes * (POSE_T / 32); }
+};
+template <bool MESH>
+__global__ void __launch_bounds__(POSE_T) bwd_pose_kernel(BwdBatchedArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, wpb = blockDim.x >> 5;
-  PadObj* spo = reinterpret_cast<PadObj*>(smem) + (size_t)warp * a.K;
-  int16_t* sq = reinterpret_cast<int16_t*>(smem + sizeof(PadObj) * (size_t)wpb * a.K) +
-                (size_t)warp * POSE_Q;
+  const PoseSmem L(a.K);
+  unsigned char* wb = smem + (size_t)warp * L.warp_bytes;
+  PadObj* spo = reinterpret_cast<PadObj*>(wb + L.po);
+  int16_t* sq = reinterpret_cast<int16_t*>(wb + L.q);
+  float* sacc = reinterpret_cast<float*>(wb + L.acc);   // [k][6][32]
   const unsigned lt = (1u << lane) - 1u;
   for (int pad = blockIdx.x * wpb + warp; pad < a.num_items; pad += gridDim.x * wpb) {
     const int m = a.pad_m[pad];
@@ -1304,41 +1333,38 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
       const int words = a.K * (int)(sizeof(PadObj) / 4);
       for (int e = lane; e < words; e += 32) dst[e] = src[e];
     }
+    for (int e = 0; e < 6 * a.K; ++e) sacc[32 * e + lane] = 0.f;
     __syncwarp();
     const uint32_t* bits = a.maskbits + a.mask_woff[pad];
     const bool given = a.mask_in != nullptr;   // mode B: no SDF, no pose or penetration gradient
     const float* pp = given ? nullptr : a.pad_pose + 7 * (size_t)pad;
     float Rp[3][3] = {};
     if (!given) quat_to_mat<float>(pp + 3, Rp);
-    float pose[MAX_K][6];
-#pragma unroll
-    for (int k = 0; k < MAX_K; ++k)
-#pragma unroll
-      for (int q = 0; q < 6; ++q) pose[k][q] = 0.f;
+    const float* op_env = a.obj_pose + 7 * (size_t)env * a.K;
     // one active node per lane (lane < cnt): its penetration gradient and pose partials
     auto run = [&](int cnt) {
       if (lane < cnt) {
         const int i = sq[lane];
         const float4 d = a.ws_du[base + i];
         const float3 du = make_float3(d.x, d.y, d.z);
-        const float3 p = make_float3(a.type_pos[3 * (size_t)(o + i)], a.type_pos[3 * (size_t)(o + i) + 1],
-                                     a.type_pos[3 * (size_t)(o + i) + 2]);
-        const float3 nr = make_float3(a.type_nrm[3 * (size_t)(o + i)], a.type_nrm[3 * (size_t)(o + i) + 1],
-                                      a.type_nrm[3 * (size_t)(o + i) + 2]);
-        NodePoseGrad pg;
-        pg.k = -1;
-        pg.pen = 0.f;
-        if (!given) pg = node_pose_grad(spo, a.K, p, nr, du, Rp, pp, a.obj_pose + 7 * (size_t)env * a.K);
+        const float* tp = a.type_pos + 3 * (size_t)(o + i);
+        const float* tn = a.type_nrm + 3 * (size_t)(o + i);
+        const float3 p = make_float3(tp[0], tp[1], tp[2]);
+        const float3 nr = make_float3(tn[0], tn[1], tn[2]);
+        float pen = 0.f;
+        if (!given) {
+          const NodePoseGrad pg = node_pose_grad<MESH>(spo, a.K, p, nr, du, Rp, pp, op_env);
+          pen = pg.pen;
+          if (pg.k >= 0) {
+            float* ac = sacc + (size_t)pg.k * 6 * 32 + lane;
 #pragma unroll
-        for (int k = 0; k < MAX_K; ++k) {
-          if (k != pg.k) continue;
-#pragma unroll
-          for (int q = 0; q < 3; ++q) {
-            pose[k][q] += pg.t[q];
-            pose[k][3 + q] += pg.w[q];
+            for (int q = 0; q < 3; ++q) {
+              ac[32 * q] += pg.t[q];
+              ac[32 * (3 + q)] += pg.w[q];
+            }
           }
         }
-        if (a.grad_pen) a.grad_pen[base + i] = pg.pen;
+        if (a.grad_pen) a.grad_pen[base + i] = pen;
       }
       __syncwarp();
     };
@@ -1361,17 +1387,12 @@ __global__ void __launch_bounds__(256) bwd_pose_kernel(BwdBatchedArgs a) {
       }
     }
     if (npend > 0) run(npend);
-    for (int k = 0; k < a.K; ++k)
+    for (int e = 0; e < 6 * a.K; ++e) {
+      float v = sacc[32 * e + lane];
 #pragma unroll
-      for (int q = 0; q < 6; ++q) {
-        float v = 0.f;
-#pragma unroll
-        for (int kk = 0; kk < MAX_K; ++kk)
-          if (kk == k) v = pose[kk][q];
-#pragma unroll
-        for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(FULL, v, sh);
-        if (lane == 0) a.pose_part[((size_t)pad * a.K + k) * 6 + q] = v;
-      }
+      for (int sh = 16; sh > 0; sh >>= 1) v += __shfl_xor_sync(FULL, v, sh);
+      if (lane == 0) a.pose_part[(size_t)pad * a.K * 6 + e] = v;
+    }
     __syncwarp();
   }
   // pads without contact: zero pose partials (every warp covers its own pads)
@@ -1496,9 +1517,28 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       break;
     }
     case BWD_STAGE_POSE:
+    {
       bwd_fill_kernel<<<l.r7_grid, 256, 0, s>>>(a);
-      bwd_pose_kernel<<<l.r7_grid, 256, (sizeof(PadObj) * a.K + sizeof(int16_t) * POSE_Q) * 8, s>>>(a);
+      cudaError_t e = cudaGetLastError();
+      if (e != cudaSuccess) return e;
+      const size_t smem = PoseSmem(a.K).total();
+      static size_t configured = 0;
+      if (smem > configured) {
+        e = cudaFuncSetAttribute(bwd_pose_kernel<false>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e == cudaSuccess)
+          e = cudaFuncSetAttribute(bwd_pose_kernel<true>,
+                                   cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return e;
+        configured = smem;
+      }
+      const int grid = l.r7_grid * (256 / POSE_T);   // r7_grid counts 8-warp CTAs
+      if (a.has_meshes)
+        bwd_pose_kernel<true><<<grid, POSE_T, smem, s>>>(a);
+      else
+        bwd_pose_kernel<false><<<grid, POSE_T, smem, s>>>(a);
       break;
+    }
     case BWD_STAGE_PARAMS:
       if (grad_params) bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
       break;

@@ -18,13 +18,20 @@ struct NodePoseGrad {
   float t[3], w[3];
 };
 
+// MESH: mesh objects may occur (their queries are compiled in).
+template <bool MESH = true>
 __device__ inline NodePoseGrad node_pose_grad(const PadObj* spo, int K, float3 p, float3 nr,
                                               float3 du, const float (&Rp)[3][3],
                                               const float* pp, const float* op_env) {
   NodePoseGrad out;
   SdfIn sd;
-  const NodeContact c = contact_node(spo, K, p, nr, &sd);
+  const NodeContact c = contact_node<MESH>(spo, K, p, nr, &sd);
   out.k = c.k;
+  if (c.k < 0) {   // not in contact (the callers pass active nodes only)
+    out.pen = 0.f;
+    for (int q = 0; q < 3; ++q) out.t[q] = out.w[q] = 0.f;
+    return out;
+  }
   const PadObj& po = spo[c.k];
   // outward normal in the pad frame: R_rel^T g
   const float npx = po.R[0] * sd.g[0] + po.R[3] * sd.g[1] + po.R[6] * sd.g[2];
@@ -43,7 +50,7 @@ __device__ inline NodePoseGrad node_pose_grad(const PadObj* spo, int K, float3 p
   const float phi = c.phi;
   const float gv = sd.g[0] * vo[0] + sd.g[1] * vo[1] + sd.g[2] * vo[2];
   float Av[3] = {sd.g[0] * gv, sd.g[1] * gv, sd.g[2] * gv};
-  if (sd.hk >= 3) {
+  if (MESH && sd.hk >= 3) {
     // mesh edge (hk 3, direction e) or vertex (hk 4): phi = -(distance to the feature), whose
     // Hessian times phi is the projector I - g g^T (- e e^T on an edge)
     const float ev = sd.hk == 3 ? sd.e[0] * vo[0] + sd.e[1] * vo[1] + sd.e[2] * vo[2] : 0.f;

@@ -395,7 +395,12 @@ __device__ inline bool sdf_inside_df(int type, const float* dims, const df q[3],
       }
     }
     s->phi = best;
-    s->g[am] = df_isneg(q[am]) ? -1.f : 1.f;
+    // selects, not an indexed store: keeps *s in registers
+    const bool neg = am == 0 ? df_isneg(q[0]) : (am == 1 ? df_isneg(q[1]) : df_isneg(q[2]));
+    const float sg = neg ? -1.f : 1.f;
+    s->g[0] = am == 0 ? sg : 0.f;
+    s->g[1] = am == 1 ? sg : 0.f;
+    s->g[2] = am == 2 ? sg : 0.f;
     return true;
   }
   if (type == OBJ_CYLINDER) {
