@@ -169,36 +169,45 @@ __device__ __forceinline__ void front_encode(float (&fm)[8][2], uint32_t rows, i
   uint32_t af[4][4];
 #pragma unroll
   for (int s4 = 0; s4 < 4; ++s4) {
-    float h[2][4];
+    // n tiles 2 s4 and 2 s4 + 1 as two interleaved chains (W1 hi, then lo)
+    float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
-    for (int t = 0; t < 2; ++t) {
-      const int nt = 2 * s4 + t;
-      float acc[4] = {0.f, 0.f, 0.f, 0.f};
-      const uint2 bh = sW1f[nt * 32 + lane], bl = sW1f[(8 + nt) * 32 + lane];
-      sm100::mma_bf16_16816(acc, ax, bh.x, bh.y, acc);
-      sm100::mma_bf16_16816(acc, ax, bl.x, bl.y, acc);
+    for (int part = 0; part < 2; ++part)
 #pragma unroll
-      for (int q = 0; q < 4; ++q) h[t][q] = fmaxf(acc[q], 0.f);
-    }
-    __nv_bfloat162 p0 = __floats2bfloat162_rn(h[0][0], h[0][1]);
-    __nv_bfloat162 p1 = __floats2bfloat162_rn(h[0][2], h[0][3]);
-    __nv_bfloat162 p2 = __floats2bfloat162_rn(h[1][0], h[1][1]);
-    __nv_bfloat162 p3 = __floats2bfloat162_rn(h[1][2], h[1][3]);
+      for (int t = 0; t < 2; ++t) {
+        const uint2 b = sW1f[(8 * part + 2 * s4 + t) * 32 + lane];
+        sm100::mma_bf16_16816(acc[t], ax, b.x, b.y, acc[t]);
+      }
+    __nv_bfloat162 p0 = __floats2bfloat162_rn(fmaxf(acc[0][0], 0.f), fmaxf(acc[0][1], 0.f));
+    __nv_bfloat162 p1 = __floats2bfloat162_rn(fmaxf(acc[0][2], 0.f), fmaxf(acc[0][3], 0.f));
+    __nv_bfloat162 p2 = __floats2bfloat162_rn(fmaxf(acc[1][0], 0.f), fmaxf(acc[1][1], 0.f));
+    __nv_bfloat162 p3 = __floats2bfloat162_rn(fmaxf(acc[1][2], 0.f), fmaxf(acc[1][3], 0.f));
     af[s4][0] = *reinterpret_cast<uint32_t*>(&p0);
     af[s4][1] = *reinterpret_cast<uint32_t*>(&p1);
     af[s4][2] = *reinterpret_cast<uint32_t*>(&p2);
     af[s4][3] = *reinterpret_cast<uint32_t*>(&p3);
   }
+  // E2 in two halves of four n tiles, four interleaved chains each (k steps ascending)
 #pragma unroll
-  for (int nt = 0; nt < 8; ++nt) {
-    float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  for (int half = 0; half < 2; ++half) {
+    float acc[4][4];
 #pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-      const uint2 bb = sW2f[(nt * 4 + s4) * 32 + lane];
-      sm100::mma_bf16_16816(acc, af[s4], bb.x, bb.y, acc);
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
+#pragma unroll
+    for (int s4 = 0; s4 < 4; ++s4)
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const uint2 bb = sW2f[((4 * half + j) * 4 + s4) * 32 + lane];
+        sm100::mma_bf16_16816(acc[j], af[s4], bb.x, bb.y, acc[j]);
+      }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int nt = 4 * half + j;
+      fm[nt][0] = fmaxf(fm[nt][0], fmaxf(v0 ? acc[j][0] : -INFINITY, v1 ? acc[j][2] : -INFINITY));
+      fm[nt][1] = fmaxf(fm[nt][1], fmaxf(v0 ? acc[j][1] : -INFINITY, v1 ? acc[j][3] : -INFINITY));
     }
-    fm[nt][0] = fmaxf(fm[nt][0], fmaxf(v0 ? acc[0] : -INFINITY, v1 ? acc[2] : -INFINITY));
-    fm[nt][1] = fmaxf(fm[nt][1], fmaxf(v0 ? acc[1] : -INFINITY, v1 ? acc[3] : -INFINITY));
   }
 }
 
