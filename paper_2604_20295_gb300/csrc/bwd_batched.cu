@@ -1341,6 +1341,8 @@ __global__ void __launch_bounds__(POSE_T) bwd_pose_kernel(BwdBatchedArgs a) {
     float Rp[3][3] = {};
     if (!given) quat_to_mat<float>(pp + 3, Rp);
     const float* op_env = a.obj_pose + 7 * (size_t)env * a.K;
+    float gap = 0.f;
+    for (int k = 0; k < a.K; ++k) gap = fmaxf(gap, 2.f * spo[k].tau);
     // one active node per lane (lane < cnt): its penetration gradient and pose partials
     auto run = [&](int cnt) {
       if (lane < cnt) {
@@ -1353,7 +1355,7 @@ __global__ void __launch_bounds__(POSE_T) bwd_pose_kernel(BwdBatchedArgs a) {
         const float3 nr = make_float3(tn[0], tn[1], tn[2]);
         float pen = 0.f;
         if (!given) {
-          const NodePoseGrad pg = node_pose_grad<MESH>(spo, a.K, p, nr, du, Rp, pp, op_env);
+          const NodePoseGrad pg = node_pose_grad<MESH>(spo, a.K, p, nr, du, Rp, pp, op_env, gap);
           pen = pg.pen;
           if (pg.k >= 0) {
             float* ac = sacc + (size_t)pg.k * 6 * 32 + lane;

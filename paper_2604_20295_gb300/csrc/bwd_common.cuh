@@ -18,14 +18,33 @@ struct NodePoseGrad {
   float t[3], w[3];
 };
 
-// MESH: mesh objects may occur (their queries are compiled in).
+// The node's contact and SDF feature from df32 arithmetic, out of line (the fast path below
+// covers most nodes).
+template <bool MESH>
+__device__ __noinline__ NodeContact pose_contact_exact(const PadObj* spo, int K, float3 p,
+                                                       float3 nr, SdfIn* sd) {
+  return contact_node<MESH>(spo, K, p, nr, sd);
+}
+
+// MESH: mesh objects may occur (their queries are compiled in).  gap > 0 (twice the largest
+// FP32 error bound of the pad's objects, as the forward classifies with): nodes that
+// contact_classify decides in FP32 take their feature from it, the others from df32; gap <= 0:
+// df32 for every node.  Either way the discrete choices (object, face, wall) are the exact ones.
 template <bool MESH = true>
 __device__ inline NodePoseGrad node_pose_grad(const PadObj* spo, int K, float3 p, float3 nr,
                                               float3 du, const float (&Rp)[3][3],
-                                              const float* pp, const float* op_env) {
+                                              const float* pp, const float* op_env,
+                                              float gap = 0.f) {
   NodePoseGrad out;
   SdfIn sd;
-  const NodeContact c = contact_node<MESH>(spo, K, p, nr, &sd);
+  NodeContact c;
+  int cls = CONTACT_BAND;
+  if (gap > 0.f) cls = contact_classify<MESH>(spo, K, p, nr, gap, &c, &sd);
+  if (cls != CONTACT_FAST) {
+    SdfIn se;   // only this copy's address leaves the function: sd stays in registers
+    c = pose_contact_exact<MESH>(spo, K, p, nr, &se);
+    sd = se;
+  }
   out.k = c.k;
   if (c.k < 0) {   // not in contact (the callers pass active nodes only)
     out.pen = 0.f;

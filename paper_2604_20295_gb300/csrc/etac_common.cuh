@@ -540,10 +540,13 @@ ETAC_REFINE_LINKAGE NodeContact contact_refine(const PadObj* po, int K, float3 p
 //                 cylinder) is within `gap` of a tie: the choices equal the exact ones
 //                 (|FP32 error| < tau <= gap / 2) and *r holds u_hat from FP32 arithmetic;
 //   CONTACT_BAND  anything else: contact_refine decides exactly.
+// With `detail`, a FAST node also receives its SDF feature (object-frame point, normal, Hessian
+// kind) in FP32, as contact_refine gives it from df32; mesh objects then go to the band, where
+// contact_refine finds their face, edge or vertex.
 enum { CONTACT_OUT = 0, CONTACT_FAST = 1, CONTACT_BAND = 2 };
 template <bool MESH = true>
 __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3 nrm, float gap,
-                                       NodeContact* r) {
+                                       NodeContact* r, SdfIn* detail = nullptr) {
   // pass 1: FP32 distance to every object; far-outside nodes stop here
   float best = INFINITY, second = INFINITY;
   bool maybe = false;
@@ -574,7 +577,9 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
   const float3 q = bq;
   float g0 = 0.f, g1 = 0.f, g2 = 0.f, margin = INFINITY;
   bool deg = false;
+  int hk = 0;   // Hessian kind, as sdf_inside_df reports it
   if (MESH && o.type == OBJ_MESH) {
+    if (detail) return CONTACT_BAND;
     // the nearest point again (pass 1 kept only the distance); a runner-up within rounding
     // at another point leaves the choice of u_hat to the exact path
     const MeshF32 r = mesh_f32(*o.mesh, q);
@@ -593,6 +598,7 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
       g0 = q.x * il;
       g1 = q.y * il;
       g2 = vz * il;
+      hk = 1;
     } else {
       deg = true;
     }
@@ -627,6 +633,7 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
         const float ir = 1.f / rho;
         g0 = q.x * ir;
         g1 = q.y * ir;
+        hk = 2;
       } else {
         deg = true;
       }
@@ -647,6 +654,18 @@ __device__ inline int contact_classify(const PadObj* po, int K, float3 p, float3
   r->u[0] = s * (o.R[0] * g0 + o.R[3] * g1 + o.R[6] * g2);
   r->u[1] = s * (o.R[1] * g0 + o.R[4] * g1 + o.R[7] * g2);
   r->u[2] = s * (o.R[2] * g0 + o.R[5] * g1 + o.R[8] * g2);
+  if (detail) {
+    detail->phi = df_from(best);
+    detail->g[0] = g0;
+    detail->g[1] = g1;
+    detail->g[2] = g2;
+    detail->qf[0] = q.x;
+    detail->qf[1] = q.y;
+    detail->qf[2] = q.z;
+    detail->e[0] = detail->e[1] = detail->e[2] = 0.f;
+    detail->hk = hk;
+    detail->deg = deg;
+  }
   return CONTACT_FAST;
 }
 
