@@ -139,10 +139,17 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
   for (int ks = 0; ks < 2; ++ks)
     sm100::ldmatrix_x4(rows + (uint32_t)((lane & 15) * 64 + (lane >> 4) * 16 + ks * 32), ax[ks][0],
                        ax[ks][1], ax[ks][2], ax[ks][3]);
-  uint32_t ah[3][4][4];
+  // E2's k step s4 reads h columns 16 s4 .. 16 s4 + 15, which E1's n tiles 2 s4 and 2 s4 + 1
+  // produce: E1 runs one k step ahead of E2, so only that step's split parts are live.  The
+  // eight E2 n tiles are independent MMA chains, interleaved; each keeps its order (k steps
+  // ascending, smallest products first).
+  float acc2[8][4];
 #pragma unroll
-  for (int s4 = 0; s4 < 4; ++s4) {
-    // the two n tiles of this k step as independent MMA chains, interleaved
+  for (int nt = 0; nt < 8; ++nt)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc2[nt][q] = 0.f;
+#pragma unroll 1
+  for (int s4 = 0; s4 < 4; ++s4) {   // rolled: a quarter of the code, for the instruction cache
     float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
 #pragma unroll
     for (int ks = 0; ks < 2; ++ks)
@@ -153,55 +160,36 @@ __device__ __forceinline__ void bwd_encode(float (&fv)[8][2], int (&fi)[8][2], u
           const uint2 bb = sW1f[((part * 2 + ks) * 8 + 2 * s4 + t) * 32 + lane];
           sm100::mma_bf16_16816(acc[t], ax[ks], bb.x, bb.y, acc[t]);
         }
-    float h[2][4];
+    uint32_t ah[3][4];
+    split3(relu(acc[0][0]), relu(acc[0][1]), ah[0][0], ah[1][0], ah[2][0]);
+    split3(relu(acc[0][2]), relu(acc[0][3]), ah[0][1], ah[1][1], ah[2][1]);
+    split3(relu(acc[1][0]), relu(acc[1][1]), ah[0][2], ah[1][2], ah[2][2]);
+    split3(relu(acc[1][2]), relu(acc[1][3]), ah[0][3], ah[1][3], ah[2][3]);
 #pragma unroll
-    for (int t = 0; t < 2; ++t)
+    for (int pr = 0; pr < 6; ++pr) {
+      // products (A part, W part): (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
+      const int ap = pr == 0 ? 2 : (pr == 1 || pr == 3 ? 1 : 0);
+      const int wp = pr == 2 ? 2 : (pr == 1 || pr == 4 ? 1 : 0);
 #pragma unroll
-      for (int q = 0; q < 4; ++q) h[t][q] = relu(acc[t][q]);
-    split3(h[0][0], h[0][1], ah[0][s4][0], ah[1][s4][0], ah[2][s4][0]);
-    split3(h[0][2], h[0][3], ah[0][s4][1], ah[1][s4][1], ah[2][s4][1]);
-    split3(h[1][0], h[1][1], ah[0][s4][2], ah[1][s4][2], ah[2][s4][2]);
-    split3(h[1][2], h[1][3], ah[0][s4][3], ah[1][s4][3], ah[2][s4][3]);
-  }
-  // E2 in two halves of four n tiles: four independent MMA chains per half, interleaved; each
-  // chain keeps its order (k steps ascending, smallest products first)
-#pragma unroll
-  for (int half = 0; half < 2; ++half) {
-    float acc[4][4];
-#pragma unroll
-    for (int j = 0; j < 4; ++j)
-#pragma unroll
-      for (int q = 0; q < 4; ++q) acc[j][q] = 0.f;
-#pragma unroll
-    for (int s4 = 0; s4 < 4; ++s4) {
-#pragma unroll
-      for (int pr = 0; pr < 6; ++pr) {
-        // products (A part, W part): (2,0) (1,1) (0,2) (1,0) (0,1) (0,0)
-        const int ap = pr == 0 ? 2 : (pr == 1 || pr == 3 ? 1 : 0);
-        const int wp = pr == 2 ? 2 : (pr == 1 || pr == 4 ? 1 : 0);
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int nt = 4 * half + j;
-          const uint2 bw = sW2f[((wp * 8 + nt) * 4 + s4) * 32 + lane];
-          sm100::mma_bf16_16816(acc[j], ah[ap][s4], bw.x, bw.y, acc[j]);
-        }
+      for (int nt = 0; nt < 8; ++nt) {
+        const uint2 bw = sW2f[((wp * 8 + nt) * 4 + s4) * 32 + lane];
+        sm100::mma_bf16_16816(acc2[nt], ah[ap], bw.x, bw.y, acc2[nt]);
       }
     }
+  }
 #pragma unroll
-    for (int j = 0; j < 4; ++j) {
-      const int nt = 4 * half + j;
+  for (int nt = 0; nt < 8; ++nt) {
 #pragma unroll
-      for (int e = 0; e < 2; ++e) {
-        const float b = sB2[8 * nt + 2 * tig + e];
-        const float f0 = relu(acc[j][e] + b), f1 = relu(acc[j][2 + e] + b);
-        if (v0 && (f0 > fv[nt][e] || (f0 == fv[nt][e] && n0 < fi[nt][e]))) {
-          fv[nt][e] = f0;
-          fi[nt][e] = n0;
-        }
-        if (v1 && (f1 > fv[nt][e] || (f1 == fv[nt][e] && n1 < fi[nt][e]))) {
-          fv[nt][e] = f1;
-          fi[nt][e] = n1;
-        }
+    for (int e = 0; e < 2; ++e) {
+      const float b = sB2[8 * nt + 2 * tig + e];
+      const float f0 = relu(acc2[nt][e] + b), f1 = relu(acc2[nt][2 + e] + b);
+      if (v0 && (f0 > fv[nt][e] || (f0 == fv[nt][e] && n0 < fi[nt][e]))) {
+        fv[nt][e] = f0;
+        fi[nt][e] = n0;
+      }
+      if (v1 && (f1 > fv[nt][e] || (f1 == fv[nt][e] && n1 < fi[nt][e]))) {
+        fv[nt][e] = f1;
+        fi[nt][e] = n1;
       }
     }
   }
@@ -366,50 +354,56 @@ __global__ void __launch_bounds__(RT, 2) bwd_pad_kernel(BwdBatchedArgs a) {
       __syncwarp();
     };
 
-    for (int r0 = 0; r0 < n; r0 += 32) {
-      const int i = r0 + lane;
-      int cls = CONTACT_OUT;
-      NodeContact c;
-      c.active = false;
-      c.phi = 0.f;
-      c.k = -1;
-      c.u[0] = c.u[1] = c.u[2] = 0.f;
-      float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
-      if (i < n && !invalid) {
-        p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
-        nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
-        if (a.mask_in) {   // mode B: the forward's caller-supplied contact (never in the band)
-          c = contact_given(a.mask_in, a.uhat_in, base + i);
-          cls = c.active ? CONTACT_FAST : CONTACT_OUT;
-        } else {
-          cls = contact_classify<MESH>(spo, a.K, p, nr, gap, &c);
-        }
-      }
-      if (i < n && cls != CONTACT_BAND) decided(i, c, p, nr, false);
-      const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
-      const unsigned bC = __ballot_sync(FULL, cls == CONTACT_BAND);
-      if (lane == 0) sBits[r0 >> 5] = bA;
-      if (cls == CONTACT_FAST && use_r) {
-        const int q = npend + __popc(bA & lt);
-        sPNode[q] = i;
-        pack_row32(sPend + 4 * q, p, nr, c.u);
-      }
-      if (cls == CONTACT_BAND) sCand[ncand + __popc(bC & lt)] = (int16_t)i;
-      m += __popc(bA);
-      if (use_r) npend += __popc(bA);
-      ncand += __popc(bC);
-      __syncwarp();
-      drain(15);
-      if (ncand > RCAND - 32) {
+    // One step per iteration: a 32-node row (classification) or a batch of undecided nodes (the
+    // exact path), then encoder tiles.  The encoder has this one call site, so its code exists
+    // once (the instruction cache is the kernel's first stall); the order of rows, batches and
+    // tiles is that of classifying every row with a batch whenever the queue nears full.
+    int r0 = 0;
+    bool force = false;   // warp-uniform: the candidate queue is nearly full
+    for (;;) {
+      if (force || (r0 >= n && ncand > 0)) {
         refine_batch();
-        drain(15);
+        force = false;
+      } else if (r0 < n) {
+        const int i = r0 + lane;
+        int cls = CONTACT_OUT;
+        NodeContact c;
+        c.active = false;
+        c.phi = 0.f;
+        c.k = -1;
+        c.u[0] = c.u[1] = c.u[2] = 0.f;
+        float3 p = make_float3(0.f, 0.f, 0.f), nr = p;
+        if (i < n && !invalid) {
+          p = make_float3(tpos[3 * i], tpos[3 * i + 1], tpos[3 * i + 2]);
+          nr = make_float3(tnrm[3 * i], tnrm[3 * i + 1], tnrm[3 * i + 2]);
+          if (a.mask_in) {   // mode B: the forward's caller-supplied contact (never in the band)
+            c = contact_given(a.mask_in, a.uhat_in, base + i);
+            cls = c.active ? CONTACT_FAST : CONTACT_OUT;
+          } else {
+            cls = contact_classify<MESH>(spo, a.K, p, nr, gap, &c);
+          }
+        }
+        if (i < n && cls != CONTACT_BAND) decided(i, c, p, nr, false);
+        const unsigned bA = __ballot_sync(FULL, cls == CONTACT_FAST);
+        const unsigned bC = __ballot_sync(FULL, cls == CONTACT_BAND);
+        if (lane == 0) sBits[r0 >> 5] = bA;
+        if (cls == CONTACT_FAST && use_r) {
+          const int q = npend + __popc(bA & lt);
+          sPNode[q] = i;
+          pack_row32(sPend + 4 * q, p, nr, c.u);
+        }
+        if (cls == CONTACT_BAND) sCand[ncand + __popc(bC & lt)] = (int16_t)i;
+        m += __popc(bA);
+        if (use_r) npend += __popc(bA);
+        ncand += __popc(bC);
+        __syncwarp();
+        r0 += 32;
+        force = ncand > RCAND - 32;
       }
+      const bool last = r0 >= n && ncand == 0;
+      drain(last ? 0 : 15);
+      if (last) break;
     }
-    while (ncand > 0) {
-      refine_batch();
-      drain(15);
-    }
-    drain(0);
 
     const int gi = a.pad_gi[pad];
     for (int w = lane; w < nwords; w += 32) a.maskbits[a.mask_woff[pad] + w] = sBits[w];

@@ -384,7 +384,11 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
         cull[w4] = __ballot_sync(FULL, out);
       }
     }
-    for (int r0 = 0; r0 < n; r0 += 32) {
+    // One step per iteration: a 32-node row (classification) or a batch of undecided nodes (the
+    // exact path), then encoder tiles.  The encoder has this one call site, so its code exists
+    // once (instruction fetch is the kernel's first stall); the order of rows, batches and tiles
+    // is that of classifying every row with a batch whenever the queue nears full.
+    auto row = [&](int r0) {
       const bool live = r0 + lane < n;
       const int i = live ? (int)bperm[r0 + lane] : 0;
       const int b = r0 >> 5;
@@ -398,7 +402,7 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
           c.u[0] = c.u[1] = c.u[2] = 0.f;
           front_write_node(a, btrow, n, base, i, c, (sOld[i >> 5] >> (i & 31)) & 1u);
         }
-        continue;
+        return;
       }
       int cls = CONTACT_OUT;
       NodeContact c;
@@ -432,17 +436,22 @@ __global__ void __launch_bounds__(FT, 4) front_contact_kernel(FrontArgs a) {
       if (enc) npend += __popc(bA);
       ncand += __popc(bC);
       __syncwarp();
-      drain(15);
-      if (ncand > CANDCAP - 32) {
+    };
+    int r0 = 0;
+    bool force = false;   // warp-uniform: the candidate queue is nearly full
+    for (;;) {
+      if (force || (r0 >= n && ncand > 0)) {
         refine_batch();
-        drain(15);
+        force = false;
+      } else if (r0 < n) {
+        row(r0);
+        r0 += 32;
+        force = ncand > CANDCAP - 32;
       }
+      const bool last = r0 >= n && ncand == 0;
+      drain(last ? 0 : 15);
+      if (last) break;
     }
-    while (ncand > 0) {
-      refine_batch();
-      drain(15);
-    }
-    drain(0);
 
     __syncwarp();
     for (int w = lane; w < nwords; w += 32) {
