@@ -86,31 +86,31 @@ TRAFFIC = {
     # count: the bench step's outputs; --backward for the reverse stages); per stage where a
     # stage is several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "2987577bb6008849", "bytes": 42.77e6 + 59.87e6},
+                             "sha": "32e9a0c60af3a867", "bytes": 42.69e6 + 59.28e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "2987577bb6008849", "bytes": 6.55e6},
+                            "sha": "32e9a0c60af3a867", "bytes": 6.55e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                         "sha": "59f10d54de88bcd0", "bytes": 136.35e6 + 127.48e6},
+                         "sha": "59f10d54de88bcd0", "bytes": 136.37e6 + 127.66e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                "sha": "59f10d54de88bcd0", "bytes": 332.80e6 + 44.23e6},
+                                "sha": "59f10d54de88bcd0", "bytes": 331.26e6 + 44.22e6},
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                    "sha": "59f10d54de88bcd0", "bytes": 331.19e6 + 0.16e6},
+                                    "sha": "59f10d54de88bcd0", "bytes": 330.91e6 + 0.23e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "b0091c82cedb8054", "bytes": 249.00e6 + 333.13e6},
+                       "sha": "7b2c2bdb85f7af99", "bytes": 246.35e6 + 325.27e6},
     "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "b0091c82cedb8054", "bytes": 8.81e6 + 0.01e6},
+                          "sha": "7b2c2bdb85f7af99", "bytes": 8.81e6 + 0.01e6},
     "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                           "sha": "b0091c82cedb8054", "bytes": 238.86e6 + 65.57e6},
+                           "sha": "7b2c2bdb85f7af99", "bytes": 238.83e6 + 65.60e6},
     "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                             "sha": "b0091c82cedb8054", "bytes": 75.51e6 + 0.01e6},
+                             "sha": "7b2c2bdb85f7af99", "bytes": 75.51e6 + 0.07e6},
     "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
-                          "sha": "b0091c82cedb8054", "bytes": 52.27e6 + 2.55e6 + 34.23e6 + 0.08e6},
+                          "sha": "7b2c2bdb85f7af99", "bytes": 52.28e6 + 2.47e6 + 34.23e6 + 0.07e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "b0091c82cedb8054", "bytes": 102.40e6 + 11.77e6},
+                          "sha": "7b2c2bdb85f7af99", "bytes": 102.42e6 + 11.60e6},
     # bwd_fill_kernel + bwd_pose_kernel + bwd_reduce_params_kernel
     "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                                     "sha": "b0091c82cedb8054",
-                                     "bytes": 95.15e6 + 227.87e6 + 97.72e6 + 7.44e6 + 30.29e6},
+                                     "sha": "7b2c2bdb85f7af99",
+                                     "bytes": 95.18e6 + 227.98e6 + 97.74e6 + 7.36e6 + 30.29e6},
 }
 
 
@@ -118,7 +118,7 @@ TRAFFIC = {
 # --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
 INSTR = {
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "2987577bb6008849", "per_node": 113459739 / 9437184},
+                             "sha": "32e9a0c60af3a867", "per_node": 122214527 / 9437184},
 }
 
 
