@@ -870,8 +870,18 @@ def main():
                  "ms_per_step": 1e3 * graph_s / args.steps, "launches_per_step":
                  int(sum(v[0] for v in ktimes.values()) // max(args.steps, 1))}
         step_ms = g_ms
+        # untimed replays of the same step for about a second, so that the clock sampler
+        # (one nvidia-smi reading per 200 ms) sees the GPU under this load several times: the
+        # timed steps alone last a few milliseconds
+        soak = max(1, int(1.0 / max(g_ms[0] / 1e3, 1e-5)))
+        for _ in range(soak):
+            cg.replay()
+        torch.cuda.synchronize()
         del cg
     clk = clocks.stop()
+    if clk is not None:
+        clk["sampled_over"] = ("warm-up, the timed steps and about 1 s of untimed replays of the "
+                               "same step right after them")
     head = graph or eager
     value = head["value"]
     ms_per_step = head["ms_per_step"]
