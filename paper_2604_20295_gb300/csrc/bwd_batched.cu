@@ -1270,6 +1270,7 @@ __global__ void __launch_bounds__(256) bwd_fill_kernel(BwdBatchedArgs a) {
     const long long base = a.pad_off[pad];
     const int m = a.pad_m[pad];
     const uint32_t* bits = a.maskbits + a.mask_woff[pad];
+#pragma unroll 4
     for (int i = lane; i < n; i += 32) {
       const bool act = m > 0 && ((bits[i >> 5] >> (i & 31)) & 1u);
       if (a.grad_uhat) {
@@ -1399,24 +1400,32 @@ __global__ void __launch_bounds__(POSE_T) bwd_pose_kernel(BwdBatchedArgs a) {
 }
 
 // ----------------------------------------------------------------------------- final sums
-// grad_params[q]: the sums of every stage's partials that cover q, each in partial order
-__global__ void bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
-  const int q = blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= NPARAM) return;
+// grad_params[q]: the sums of every stage's partials that cover q.  Eight threads per
+// parameter: thread j sums partials j, j + 8, ... of each stage in order, and a fixed
+// butterfly combines the eight (one thread per parameter left a few warps per SM, each
+// walking hundreds of partials in sequence)
+__global__ void __launch_bounds__(256) bwd_reduce_params_kernel(BwdBatchedArgs a, float* out) {
+  const int q = (int)((blockIdx.x * blockDim.x + threadIdx.x) >> 3);
+  const int j = threadIdx.x & 7;
   float s = 0.f;
-  if (q >= OFF_W1 && q < OFF_W2)
-    for (int w = 0; w < a.r4_parts; ++w) s += a.r4part[(size_t)w * R4_LEN + q - OFF_W1];
-  if (q >= OFF_W1 && q < OFF_W4)
-    for (int b = 0; b < a.r5_parts; ++b) s += a.r5part[(size_t)b * R5_LEN + q - OFF_W1];
-  if (q >= OFF_W2 && q < OFF_W4)
-    for (int b = 0; b < a.r4b_parts; ++b) s += a.r4bpart[(size_t)b * R4B_LEN + q - OFF_W2];
-  if (q >= OFF_W4 && q < OFF_W4 + 3 * H)
-    for (int b = 0; b < a.r3_parts; ++b) s += a.d2part[(size_t)b * 3 * H + q - OFF_W4];
-  if (q >= OFF_B4 && q < OFF_B4 + 3)
-    for (int b = 0; b < a.r4b_parts; ++b) s += a.gsum_part[(size_t)b * 3 + q - OFF_B4];
-  if (q == OFF_ALPHA)
-    for (int b = 0; b < a.alpha_parts; ++b) s -= a.alpha_part[b];
-  out[q] = s;
+  if (q < NPARAM) {
+    if (q >= OFF_W1 && q < OFF_W2)
+      for (int w = j; w < a.r4_parts; w += 8) s += a.r4part[(size_t)w * R4_LEN + q - OFF_W1];
+    if (q >= OFF_W1 && q < OFF_W4)
+      for (int b = j; b < a.r5_parts; b += 8) s += a.r5part[(size_t)b * R5_LEN + q - OFF_W1];
+    if (q >= OFF_W2 && q < OFF_W4)
+      for (int b = j; b < a.r4b_parts; b += 8) s += a.r4bpart[(size_t)b * R4B_LEN + q - OFF_W2];
+    if (q >= OFF_W4 && q < OFF_W4 + 3 * H)
+      for (int b = j; b < a.r3_parts; b += 8) s += a.d2part[(size_t)b * 3 * H + q - OFF_W4];
+    if (q >= OFF_B4 && q < OFF_B4 + 3)
+      for (int b = j; b < a.r4b_parts; b += 8) s += a.gsum_part[(size_t)b * 3 + q - OFF_B4];
+    if (q == OFF_ALPHA)
+      for (int b = j; b < a.alpha_parts; b += 8) s -= a.alpha_part[b];
+  }
+  s += __shfl_xor_sync(FULL, s, 1);
+  s += __shfl_xor_sync(FULL, s, 2);
+  s += __shfl_xor_sync(FULL, s, 4);
+  if (q < NPARAM && j == 0) out[q] = s;
 }
 
 }  // namespace
@@ -1536,7 +1545,7 @@ cudaError_t launch_backward_stage(const BwdBatchedArgs& a, const BwdBatchedLaunc
       break;
     }
     case BWD_STAGE_PARAMS:
-      if (grad_params) bwd_reduce_params_kernel<<<(NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
+      if (grad_params) bwd_reduce_params_kernel<<<(8 * NPARAM + 255) / 256, 256, 0, s>>>(a, grad_params);
       break;
     default:
       return cudaErrorInvalidValue;
