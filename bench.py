@@ -86,31 +86,31 @@ TRAFFIC = {
     # count: the bench step's outputs; --backward for the reverse stages); per stage where a
     # stage is several kernels
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "32e9a0c60af3a867", "bytes": 42.69e6 + 59.28e6},
+                             "sha": "56c1d146a20d5381", "bytes": 42.75e6 + 59.40e6},
     "front_global_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                            "sha": "32e9a0c60af3a867", "bytes": 6.55e6},
+                            "sha": "56c1d146a20d5381", "bytes": 6.55e6},
     "prop_gemm_kernel": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                         "sha": "59f10d54de88bcd0", "bytes": 136.37e6 + 127.66e6},
+                         "sha": "59f10d54de88bcd0", "bytes": 136.38e6 + 127.49e6},
     "prop_gemm_kernel<bwd_u>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                "sha": "59f10d54de88bcd0", "bytes": 331.26e6 + 44.22e6},
+                                "sha": "59f10d54de88bcd0", "bytes": 332.76e6 + 44.29e6},
     "prop_gemm_kernel<bwd_alpha>": {"file": "paper_2604_20295_gb300/csrc/prop_gemm.cu",
-                                    "sha": "59f10d54de88bcd0", "bytes": 330.91e6 + 0.23e6},
+                                    "sha": "59f10d54de88bcd0", "bytes": 331.07e6 + 0.16e6},
     "bwd_pad_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                       "sha": "7b2c2bdb85f7af99", "bytes": 246.35e6 + 325.27e6},
+                       "sha": "7c174cf342576933", "bytes": 246.44e6 + 325.39e6},
     "bwd_global_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "7b2c2bdb85f7af99", "bytes": 8.81e6 + 0.01e6},
+                          "sha": "7c174cf342576933", "bytes": 8.81e6 + 0.01e6},
     "bwd_decoder_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                           "sha": "7b2c2bdb85f7af99", "bytes": 238.83e6 + 65.60e6},
+                           "sha": "7c174cf342576933", "bytes": 238.84e6 + 65.62e6},
     "bwd_reduce_a3_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                             "sha": "7b2c2bdb85f7af99", "bytes": 75.51e6 + 0.07e6},
+                             "sha": "7c174cf342576933", "bytes": 75.51e6 + 0.02e6},
     "bwd_padrev_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",   # + padmlp
-                          "sha": "7b2c2bdb85f7af99", "bytes": 52.28e6 + 2.47e6 + 34.23e6 + 0.07e6},
+                          "sha": "7c174cf342576933", "bytes": 52.27e6 + 2.45e6 + 34.23e6 + 0.07e6},
     "bwd_padsum_kernel": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                          "sha": "7b2c2bdb85f7af99", "bytes": 102.42e6 + 11.60e6},
+                          "sha": "7c174cf342576933", "bytes": 102.40e6 + 11.75e6},
     # bwd_fill_kernel + bwd_pose_kernel + bwd_reduce_params_kernel
     "bwd_pose_kernel(+param sums)": {"file": "paper_2604_20295_gb300/csrc/bwd_batched.cu",
-                                     "sha": "7b2c2bdb85f7af99",
-                                     "bytes": 95.18e6 + 227.98e6 + 97.74e6 + 7.36e6 + 30.29e6},
+                                     "sha": "7c174cf342576933",
+                                     "bytes": 95.16e6 + 228.16e6 + 97.71e6 + 7.37e6 + 30.29e6},
 }
 
 
@@ -118,7 +118,7 @@ TRAFFIC = {
 # --set full capture, hand workload at 2,048 envs = 9,437,184 nodes), valid for the source hash
 INSTR = {
     "front_contact_kernel": {"file": "paper_2604_20295_gb300/csrc/front.cu",
-                             "sha": "32e9a0c60af3a867", "per_node": 122214527 / 9437184},
+                             "sha": "56c1d146a20d5381", "per_node": 122214527 / 9437184},
 }
 
 

@@ -662,6 +662,7 @@ __global__ void __launch_bounds__(256) front_global_warp_kernel(FrontArgs a) {
 // Then the per-pad epilogue records: -beta in BF16 (MMA-fragment word order) and
 // (D2 beta + b_D2, m).
 constexpr int FG_PADS = 64;
+static_assert(FG_PADS == H, "the staging loops map pad rows like unit rows");
 
 __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
   __shared__ __align__(16) float sW[H * TLD];    // [k][u] = G1[u][k], then D1[u][64 + k]
@@ -672,15 +673,25 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
   const int tid = threadIdx.x, ti = tid >> 4, tj = tid & 15;
   const int p0 = blockIdx.x * FG_PADS;
   const int np = a.num_items;
-  for (int e = tid; e < H * H; e += 256) {
-    const int u = e >> 6, k = e & (H - 1);
-    sW[k * TLD + u] = W[OFF_WG + u * H + k];
+  // every global load of the kernel is issued up front (G1, g0 and D1's global half, 16 of
+  // each per thread), so their latencies overlap; D1 waits in registers until G1 is consumed
+  constexpr int PER = H * H / 256;   // 16
+  float wg[PER], xg[PER], wd[PER];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = tid + 256 * t, u = e >> 6, k = e & (H - 1);
+    const int r = e >> 6, pad = p0 + r;
+    wg[t] = W[OFF_WG + u * H + k];
+    xg[t] = pad < np ? a.g0a[(size_t)pad * H + k] : 0.f;
+    wd[t] = W[OFF_WD + u * 2 * H + H + k];
   }
   for (int e = tid; e < H; e += 256) sBg[e] = W[OFF_BG + e];
   for (int e = tid; e < 3 * H; e += 256) sW4[e] = W[OFF_W4 + e];
-  for (int e = tid; e < FG_PADS * H; e += 256) {
-    const int r = e >> 6, k = e & (H - 1), pad = p0 + r;
-    sX[k * TLD + r] = pad < np ? a.g0a[(size_t)pad * H + k] : 0.f;
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = tid + 256 * t, u = e >> 6, k = e & (H - 1);
+    sW[k * TLD + u] = wg[t];
+    sX[k * TLD + u] = xg[t];   // u doubles as the pad row here (FG_PADS == H)
   }
   __syncthreads();
   float acc[4][4];
@@ -694,9 +705,10 @@ __global__ void __launch_bounds__(256) front_global_kernel(FrontArgs a) {
   for (int i = 0; i < 4; ++i)
 #pragma unroll
     for (int j = 0; j < 4; ++j) sX[(4 * tj + j) * TLD + 4 * ti + i] = fmaxf(acc[i][j], 0.f);
-  for (int e = tid; e < H * H; e += 256) {
-    const int u = e >> 6, k = e & (H - 1);
-    sW[k * TLD + u] = W[OFF_WD + u * 2 * H + H + k];
+#pragma unroll
+  for (int t = 0; t < PER; ++t) {
+    const int e = tid + 256 * t, u = e >> 6, k = e & (H - 1);
+    sW[k * TLD + u] = wd[t];
   }
   __syncthreads();
 #pragma unroll
