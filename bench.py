@@ -207,6 +207,27 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def gpu_local_cpus(torch, dev):
+    """The CPUs of the GPU's own NUMA node that this process may use (Linux sysfs
+    local_cpulist of the GPU's PCI function), or None where the system does not say."""
+    try:
+        p = torch.cuda.get_device_properties(dev)
+        bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
+        with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
+            text = f.read().strip()
+        cpus = set()
+        for part in text.split(","):
+            if "-" in part:
+                lo, hi = part.split("-")
+                cpus.update(range(int(lo), int(hi) + 1))
+            elif part:
+                cpus.add(int(part))
+        cpus &= os.sched_getaffinity(0)
+        return cpus or None
+    except Exception:
+        return None
+
+
 def oracle_rate(scene, theta, sample_envs, nthreads=0):
     """Times the FP64 oracle (as it stands) on a bounded env sample; node-steps/s."""
     import oracle
@@ -892,11 +913,23 @@ def main():
     # k + 1; a buffer is rewritten only after its copy has finished.
     e2e = None
     if not args.no_e2e:
-        pin = lambda a: torch.as_tensor(a).pin_memory()
-        h_in = [pin(scene.obj_type), pin(scene.obj_dims), pin(scene.obj_pose), pin(scene.pad_pose)]
+        # the pinned buffers are allocated (and so placed) from the CPUs of the GPU's own NUMA
+        # node when the system names them; the process's CPU set is restored afterwards
+        local = gpu_local_cpus(torch, dev)
+        saved = os.sched_getaffinity(0) if local else None
+        try:
+            if local:
+                os.sched_setaffinity(0, local)
+            pin = lambda a: torch.as_tensor(a).pin_memory()
+            h_in = [pin(scene.obj_type), pin(scene.obj_dims), pin(scene.obj_pose),
+                    pin(scene.pad_pose)]
+            h_out = [torch.empty(sim.disp.shape, dtype=torch.float32, pin_memory=True)
+                     for _ in range(2)]
+        finally:
+            if saved:
+                os.sched_setaffinity(0, saved)
         d_in = [sim.obj_type, sim.obj_dims, sim.obj_pose, sim.pad_pose]
         d_out = [sim.disp, torch.empty_like(sim.disp)]
-        h_out = [torch.empty(sim.disp.shape, dtype=torch.float32).pin_memory() for _ in range(2)]
         h2d = sum(t.numel() * t.element_size() for t in h_in)
         d2h = h_out[0].numel() * 4
         ke = max(20, args.steps)   # enough steps that filling the copy pipeline is amortised
@@ -909,16 +942,19 @@ def main():
         # the link alone: the same read-back with no step beside it (3 copies, events on the
         # copy stream), so that the end-to-end rate can be put against what the link carries
         torch.cuda.synchronize()
-        l0 = torch.cuda.Event(enable_timing=True)
-        l1 = torch.cuda.Event(enable_timing=True)
-        with torch.cuda.stream(css[0]):
-            h_out[0].copy_(d_out[0], non_blocking=True)
-            l0.record(css[0])
-            for _ in range(3):
-                h_out[0].copy_(d_out[0], non_blocking=True)
-            l1.record(css[0])
-        torch.cuda.synchronize()
-        link_gbs = 3 * d2h / (l0.elapsed_time(l1) * 1e6)
+        link = []
+        for b in range(2):
+            l0 = torch.cuda.Event(enable_timing=True)
+            l1 = torch.cuda.Event(enable_timing=True)
+            with torch.cuda.stream(css[0]):
+                h_out[b].copy_(d_out[b], non_blocking=True)
+                l0.record(css[0])
+                for _ in range(3):
+                    h_out[b].copy_(d_out[b], non_blocking=True)
+                l1.record(css[0])
+            torch.cuda.synchronize()
+            link.append(3 * d2h / (l0.elapsed_time(l1) * 1e6))
+        link_gbs = min(link)
         if pg:
             pg.barrier()
         torch.cuda.synchronize()
@@ -953,6 +989,9 @@ def main():
                              f"{ncs} copy stream(s), {2 * ncs} chunks)",
                "readback_matches_device": same,
                "d2h_link_gbs": link_gbs,
+               "d2h_link_gbs_per_buffer": link,
+               "host_buffers_cpus": (f"{len(local)} CPUs local to the GPU" if local
+                                     else "the process's CPU set"),
                "d2h_frac_of_link": d2h * ke / e2e_s / 1e9 / link_gbs}
 
     # ---- the other rungs on the same GPU and scene (the metric compares BF16 batched with
