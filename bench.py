@@ -207,6 +207,19 @@ def cpu_cores():
         return os.cpu_count() or 1
 
 
+def parse_cpulist(text):
+    """The CPU set of a Linux cpulist string ("0-3,8,10-11")."""
+    cpus = set()
+    for part in text.strip().split(","):
+        part = part.strip()
+        if "-" in part:
+            lo, hi = part.split("-")
+            cpus.update(range(int(lo), int(hi) + 1))
+        elif part:
+            cpus.add(int(part))
+    return cpus
+
+
 def gpu_local_cpus(torch, dev):
     """The CPUs of the GPU's own NUMA node that this process may use (Linux sysfs
     local_cpulist of the GPU's PCI function), or None where the system does not say."""
@@ -214,14 +227,7 @@ def gpu_local_cpus(torch, dev):
         p = torch.cuda.get_device_properties(dev)
         bus = f"{p.pci_domain_id:04x}:{p.pci_bus_id:02x}:{p.pci_device_id:02x}.0"
         with open(f"/sys/bus/pci/devices/{bus}/local_cpulist") as f:
-            text = f.read().strip()
-        cpus = set()
-        for part in text.split(","):
-            if "-" in part:
-                lo, hi = part.split("-")
-                cpus.update(range(int(lo), int(hi) + 1))
-            elif part:
-                cpus.add(int(part))
+            cpus = parse_cpulist(f.read())
         cpus &= os.sched_getaffinity(0)
         return cpus or None
     except Exception:

@@ -94,3 +94,13 @@ def test_oracle_single_core_rate_is_bounded_and_leaves_all_cores():
         import oracle
         omp = oracle._load()          # OpenMP's own query, found through the oracle's library
         assert omp.omp_get_max_threads() == bench.cpu_cores()
+
+
+def test_cpulist_parsing_and_no_gpu_locality_without_a_gpu():
+    import torch
+    assert bench.parse_cpulist("0-3,8,10-11\n") == {0, 1, 2, 3, 8, 10, 11}
+    assert bench.parse_cpulist("") == set()
+    assert bench.parse_cpulist("5") == {5}
+    if not torch.cuda.is_available():
+        assert bench.gpu_local_cpus(torch, 0) is None
+
