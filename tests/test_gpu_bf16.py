@@ -49,6 +49,56 @@ def test_bf16_sphere_press_100_steps(mode):
     check_bf16(I.sphere_press_scene(100, seed=0), I.make_params(0), mode)
 
 
+def propagation_bound(scene, theta, mask, ref):
+    """Entry-wise bound on the BF16 propagation term (Eq. 1, Omega U_a) of every passive node,
+    derived from the arithmetic of the tensor-core contraction: Omega (an FP32 exp, within
+    1e-6 relative) and u_hat are each rounded once to BF16 (8 significant bits, round to
+    nearest: relative error at most 2^-8 each, so a product is within 2^-7 + 2^-16 of its
+    exact value); the products are exact in FP32 and summed in FP32 (m terms: at most
+    m 2^-24 relative of the sum of magnitudes); u_hat itself comes from FP32 arithmetic,
+    within 1e-5 |u_hat| + 1e-4 mm of the oracle's.  So
+        |L_ic - L_ref,ic| <= (2^-7 + 2^-16 + 1e-5 + 1e-6 + m 2^-24) sum_j Omega_ij |u_jc|
+                             + 1e-4 sum_j Omega_ij
+    over the pad's m active nodes j, with the oracle's u_hat."""
+    alpha = float(theta[0])
+    offs = scene.node_offsets
+    bound = np.zeros((scene.total_nodes, 3))
+    for p in range(len(scene.pad_type)):
+        a, b = offs[p], offs[p + 1]
+        act = mask[a:b] > 0
+        m = int(act.sum())
+        if m == 0:
+            continue
+        pos = scene.types[scene.pad_type[p]].pos.astype(np.float64)
+        om = np.exp(-alpha * np.linalg.norm(pos[:, None, :] - pos[None, act, :], axis=2))
+        u = np.abs(ref["disp"][a:b][act])
+        rel = 2.0 ** -7 + 2.0 ** -16 + 1e-5 + 1e-6 + m * 2.0 ** -24
+        bound[a:b] = rel * (om @ u) + 1e-4 * om.sum(1)[:, None]
+    return bound
+
+
+@pytest.mark.parametrize("which", ["sphere_press", "hand"])
+def test_bf16_propagation_within_its_rounding_bound(which):
+    """The tensor-core contraction alone (LINEAR_ONLY: passive nodes get Omega U_a), entry by
+    entry against the bound its BF16 operands and FP32 sums imply."""
+    if which == "sphere_press":
+        sc = I.sphere_press_scene(100, seed=0)
+    else:
+        sc = I.hand_scene(256, seed=3).subset(np.random.default_rng(1).choice(256, 24, replace=False))
+    th = I.make_params(0)
+    got = run(sc, th, X.MODE_LINEAR_ONLY, algo=X.ALGO_BATCHED, precision=X.PREC_BF16)
+    assert got["status"] == 0
+    ref, _ = PT.oracle_forward_matching(sc, th, X.MODE_LINEAR_ONLY, got["mask"])
+    pas = got["mask"] == 0
+    bound = propagation_bound(sc, th, got["mask"], ref)
+    err = np.abs(got["disp"] - ref["disp"])[pas]
+    b = bound[pas]
+    worst = float((err / np.maximum(b, 1e-300)).max()) if err.size else 0.0
+    print(f"BF16 propagation {which}: worst error / derived bound {worst:.3f}")
+    assert np.all(err <= b), f"worst error / bound {worst:.3f}"
+    assert (got["mask"] > 0).sum() > 0
+
+
 def test_bf16_hand_scene_sampled_envs():
     full = I.hand_scene(512, seed=3)
     sc = full.subset(np.random.default_rng(0).choice(512, 40, replace=False))
